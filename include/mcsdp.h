@@ -1,0 +1,170 @@
+/*
+ * mcsdp.h — C ABI of libmcsdp, a single-GPU (sm_103a) implementation of the hot path of the
+ * matrix-completion primal-dual interior-point method (MC-PDIPM) of Yamashita & Nakata,
+ * "Fast implementation for semidefinite programs with positive matrix completion".
+ *
+ * Problem (Sec. 1, problems (P) and (D)):
+ *     (P) min A_0 . X   s.t.  A_k . X = b_k (k = 1..m),  X psd
+ *     (D) max b^T z     s.t.  sum_k A_k z_k + Y = A_0,    Y psd
+ * X is kept only on the extended sparsity pattern E (a chordal extension of the aggregate
+ * pattern, Sec. 2.1) as X̄; the max-determinant completion X̂ is reached through the factor of
+ * its inverse X̂^{-1} = L̂ L̂^T (Algorithm 1, Sec. 3.1) and Y^{-1} through Y = N N^T.
+ *
+ * Conventions shared by every entry point
+ *   - All sizes are in elements; indices are 0-based.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA global memory of the
+ *     device the context was created on, valid for the context's stream.
+ *   - The caller owns every pointer it passes; the library copies what it keeps and never frees
+ *     caller memory.  Every call returns an mcsdp_status and never aborts the process;
+ *     mcsdp_last_error() gives a one-line message for the last failing call on a context.
+ *   - Work is issued on the stream given to mcsdp_create; calls that return host results
+ *     synchronise that stream only (never the whole device).
+ *   - "Layout" arrays hold one FP64 value per stored entry of the supernodal factor structure
+ *     of E (nnz_layout entries, see mcsdp_sym_info): supernode s is a column-major block of
+ *     nrow_s x ncol_s values (rows = the clique C_s in elimination order, columns = S_s);
+ *     entries above the diagonal of the leading ncol_s x ncol_s block are unused and zero.
+ *     X̄, Y, dX, L̂ and N all use this layout (the memory of L̂ equals that of N, Sec. 3.1).
+ *   - Constraint vectors (b, z, dz, g) are in the caller's constraint order.
+ */
+#ifndef MCSDP_H
+#define MCSDP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mcsdp_ctx mcsdp_ctx; /* opaque, library-owned */
+
+typedef enum {
+  MCSDP_OK = 0,
+  MCSDP_ERR_ARG = 1,      /* invalid argument or input data */
+  MCSDP_ERR_NOT_PD = 2,   /* a clique block of X̄, Y or the SCM is not positive definite */
+  MCSDP_ERR_MAXITER = 3,  /* iteration limit reached before the stopping criterion */
+  MCSDP_ERR_STALL = 4,    /* step lengths collapsed */
+  MCSDP_ERR_NUMERIC = 5,  /* NaN or Inf met */
+  MCSDP_ERR_CUDA = 6,     /* a CUDA call failed (message in mcsdp_last_error) */
+  MCSDP_ERR_OOM = 7,      /* workspace too small / allocation failed */
+  MCSDP_ERR_TIMEOUT = 8,  /* a bounded device wait gave up */
+  MCSDP_ERR_STATE = 9     /* call not valid in the context's state (e.g. no workspace) */
+} mcsdp_status;
+
+/* Problem data, host memory, caller-owned.  One symmetric block of order n.
+ * form = 0 (SDPA): entries of F_0..F_m with c (length m): the library solves the paper's (P)
+ *        with A_0 = -F_0, A_k = F_k, b = c (SDPA's dual is the paper's primal; SDPA's x = -z).
+ * form = 1 (paper): mat 0 is A_0 itself and c is b.
+ * Entries are the upper triangle (row <= col) of each matrix; mat in [0, m]; duplicates of
+ * (mat, row, col) and row > col are rejected with MCSDP_ERR_ARG. */
+typedef struct {
+  int32_t n, m;
+  int32_t form;
+  const double *c;   /* length m */
+  int64_t nnz;
+  const int32_t *mat, *row, *col;
+  const double *val;
+} mcsdp_problem;
+
+/* Options; pass NULL for defaults.  The paper gives no parameter values ("default parameters",
+ * Sec. 4); defaults: beta 0.1, gamma 0.9, gap_tol = feas_tol = 1e-7, max_iter 60.
+ * device < 0 builds a host-only context: the symbolic analysis runs and can be exported, every
+ * compute call returns MCSDP_ERR_STATE (used to test the host layer without a GPU). */
+typedef struct {
+  double beta, gamma, gap_tol, feas_tol;
+  int32_t max_iter;
+  int32_t precision;     /* 0 = FP64 (the only form implemented; others -> MCSDP_ERR_ARG) */
+  int64_t timeout_cycles;/* bound on any device spin-wait; 0 = library default */
+  int32_t device;        /* CUDA device ordinal, or -1 for host-only */
+  int32_t verbose;       /* 1 = one log line per iteration on stderr */
+  int32_t panel_max;     /* max columns per SCM panel group (<= 96); 0 = default 80 */
+  int32_t group_max;     /* max constraints per SCM group (<= 64); 0 = default 64 */
+  double panel_budget_mb;/* bound on the SCM panel buffers; 0 = default 1024 MB */
+} mcsdp_options;
+
+void mcsdp_default_options(mcsdp_options *opt);
+
+/* Validates and copies the problem, runs the host symbolic analysis (aggregate pattern,
+ * minimum-degree ordering, elimination tree, fundamental supernodes = cliques C_r with S_r
+ * first, running-intersection order; Sec. 2.1 and the CHOLMOD supernode reading of Sec. 3.1)
+ * and prepares device-side tables.  cuda_stream is a cudaStream_t (NULL = legacy default). */
+mcsdp_status mcsdp_create(const mcsdp_problem *prob, const mcsdp_options *opt, void *cuda_stream,
+                          mcsdp_ctx **out);
+void mcsdp_destroy(mcsdp_ctx *ctx);
+const char *mcsdp_last_error(const mcsdp_ctx *ctx);
+
+/* Device workspace: the library allocates nothing on the device by itself; the caller passes
+ * one device buffer of at least mcsdp_workspace_size() bytes (e.g. a torch tensor), 256-byte
+ * aligned.  mcsdp_set_workspace uploads the symbolic tables into it; the buffer must stay
+ * valid until mcsdp_destroy or the next mcsdp_set_workspace. */
+mcsdp_status mcsdp_workspace_size(const mcsdp_ctx *ctx, size_t *bytes);
+mcsdp_status mcsdp_set_workspace(mcsdp_ctx *ctx, void *dev_ptr, size_t bytes);
+
+/* Sizes of the symbolic structure. */
+typedef struct {
+  int32_t n, m, nsuper, ngroup, max_nrow, max_ncol, tree_height;
+  int64_t nnz_layout;   /* stored values per layout array */
+  int64_t nnz_lower_E;  /* entries of lower(E) including the diagonal */
+  int64_t nslot;        /* distinct lower positions of the aggregate pattern */
+} mcsdp_sym_info;
+mcsdp_status mcsdp_sym_info_get(const mcsdp_ctx *ctx, mcsdp_sym_info *info);
+
+/* Exports the symbolic structure into caller host arrays (any pointer may be NULL):
+ *   perm[n]            new (elimination) index -> caller's row/column index
+ *   sn_col[nsuper+1]   first column of each supernode (new indices)
+ *   sn_rowptr[nsuper+1], sn_rows[sn_rowptr[nsuper]]  clique C_s rows (new indices, ascending,
+ *                      the ncol_s own columns first)
+ *   sn_valptr[nsuper+1] offset of each supernode block in a layout array
+ *   con_order[m]       internal SCM constraint order -> caller's constraint index */
+mcsdp_status mcsdp_sym_export(const mcsdp_ctx *ctx, int32_t *perm, int32_t *sn_col,
+                              int64_t *sn_rowptr, int32_t *sn_rows, int64_t *sn_valptr,
+                              int32_t *con_order);
+
+/* Full solve (Sec. 2.2 Steps 0-4 with the MC reformulation).  Starts from the iterate set by
+ * mcsdp_set_iterate, else from X̄ = I on E and a dual-feasible z0 (z0 = 0 when A_0 is positive
+ * definite; for max-cut-shaped problems where every A_k = e_k e_k^T, z0_k = -(sum_j |A_0 kj|)-1);
+ * otherwise the caller must set a dual-feasible start.  The final iterate stays on the device
+ * (mcsdp_get_iterate). */
+typedef struct {
+  double pobj, dobj, gap, pinf, dinf, mu;
+  int32_t iters, status;
+  double seconds;       /* wall time of the loop measured with CUDA events */
+  double t_scm, t_chol, t_pmat, t_other; /* per-phase seconds (S-ELEMENTS, S-CHOLESKY, P-MATRIX,
+                                            rest), CUDA events */
+} mcsdp_result;
+mcsdp_status mcsdp_solve(mcsdp_ctx *ctx, mcsdp_result *res);
+
+/* Iterate in device memory: Xbar_layout[nnz_layout] (X̄ on E), z[m]; Y is derived as
+ * A_0 - sum z_k A_k.  Any pointer may be NULL (then not copied). */
+mcsdp_status mcsdp_set_iterate(mcsdp_ctx *ctx, const double *Xbar_layout_dev, const double *z_dev);
+mcsdp_status mcsdp_get_iterate(const mcsdp_ctx *ctx, double *Xbar_layout_dev, double *z_dev,
+                               double *Y_layout_dev);
+
+/* SCM assembly at the iterate (X̄ on E, z) given in device memory (eq. newSCM2, Sec. 3.1):
+ * K2 (Y = N N^T), K1 (Algorithm 1: L̂ from X̄), K3 (B_ij = A_i . (X̂ A_j Y^{-1})).
+ * Writes the lower triangle (i >= j, caller's constraint order) of B into B_dev, column-major
+ * with leading dimension ldb >= m; the strict upper triangle is not touched.
+ * h_dev (may be NULL) receives h_i = A_i . Y^{-1}.  precision must be 0 (FP64). */
+mcsdp_status mcsdp_scm_assemble(mcsdp_ctx *ctx, const double *Xbar_layout_dev, const double *z_dev,
+                                double *B_dev, int64_t ldb, double *h_dev, int32_t precision);
+
+/* One Newton step at the iterate (X̄, z) (Sec. 2.2 eqs. SCE, dX, newdX2, primal_length2):
+ * outputs dz[m], dX on E (layout), dY on the layout, the step lengths alpha_p, alpha_d (host) and
+ * mu (host).  The iterate itself is not changed. */
+mcsdp_status mcsdp_newton_step(mcsdp_ctx *ctx, const double *Xbar_layout_dev, const double *z_dev,
+                               double *dz_dev, double *dX_layout_dev, double *dY_layout_dev,
+                               double *alpha_p, double *alpha_d, double *mu);
+
+/* Factors at the iterate: L̂ (Algorithm 1) and N (Y = N N^T) in the layout (device). */
+mcsdp_status mcsdp_factors(mcsdp_ctx *ctx, const double *Xbar_layout_dev, const double *z_dev,
+                           double *Lhat_layout_dev, double *N_layout_dev);
+
+/* Differentiation of the solution (implicit differentiation of the central-path KKT system).
+ * Not implemented: returns MCSDP_ERR_STATE. */
+mcsdp_status mcsdp_backward(mcsdp_ctx *ctx, const double *gX_layout_dev, const double *gz_dev,
+                            double *gC_dev, double *gb_dev, double *gA_dev);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCSDP_H */

@@ -1,0 +1,188 @@
+"""Python binding of libmcsdp: argument marshalling only.  Device memory and streams come from
+PyTorch; every step of the method runs in the library's CUDA kernels.  There is no CPU path: if
+the library or a GPU is missing the calls raise."""
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from .build import build as build_library
+
+
+class MCSDPError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_lib.STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(t):
+    return C.c_void_p(0) if t is None else C.c_void_p(t.data_ptr())
+
+
+class Problem:
+    """One SDP (paper notation: A_0 objective, A_k constraints, b) bound to a CUDA device.
+
+    mat/row/col/val list the upper triangle (row <= col) of A_0..A_m (mat 0 = A_0) when
+    form=1, or of SDPA's F_0..F_m with c = b when form=0."""
+
+    def __init__(self, n, m, b, mat, row, col, val, form=1, device=0, **options):
+        self._L = _lib.load()
+        self._ctx = C.c_void_p()
+        self.n, self.m = int(n), int(m)
+        self._b = np.ascontiguousarray(b, dtype=np.float64)
+        self._mat = np.ascontiguousarray(mat, dtype=np.int32)
+        self._row = np.ascontiguousarray(row, dtype=np.int32)
+        self._col = np.ascontiguousarray(col, dtype=np.int32)
+        self._val = np.ascontiguousarray(val, dtype=np.float64)
+        prob = _lib.Problem_t(self.n, self.m, int(form),
+                              self._b.ctypes.data_as(C.POINTER(C.c_double)), len(self._val),
+                              self._mat.ctypes.data_as(C.POINTER(C.c_int32)),
+                              self._row.ctypes.data_as(C.POINTER(C.c_int32)),
+                              self._col.ctypes.data_as(C.POINTER(C.c_int32)),
+                              self._val.ctypes.data_as(C.POINTER(C.c_double)))
+        opt = _lib.Options_t()
+        self._L.mcsdp_default_options(C.byref(opt))
+        for k, v in options.items():
+            setattr(opt, k, v)
+        opt.device = int(device)
+        self.device = int(device)
+        stream = None
+        if self.device >= 0:
+            self.torch_device = torch.device("cuda", self.device)
+            stream = C.c_void_p(torch.cuda.current_stream(self.torch_device).cuda_stream)
+        st = self._L.mcsdp_create(C.byref(prob), C.byref(opt), stream, C.byref(self._ctx))
+        self._check(st)
+        self.info = self.sym_info()
+        if self.device >= 0:
+            nbytes = C.c_size_t()
+            self._check(self._L.mcsdp_workspace_size(self._ctx, C.byref(nbytes)))
+            self.workspace = torch.empty(max(int(nbytes.value), 256), dtype=torch.uint8,
+                                         device=self.torch_device)
+            self._check(self._L.mcsdp_set_workspace(self._ctx, _ptr(self.workspace),
+                                                    self.workspace.numel()))
+
+    @classmethod
+    def from_instance(cls, inst, device=0, **options):
+        return cls(inst.n, inst.m, inst.b, inst.mat, inst.row, inst.col, inst.val, form=1,
+                   device=device, **options)
+
+    def _check(self, st):
+        if st != 0:
+            msg = self._L.mcsdp_last_error(self._ctx).decode() if self._ctx else ""
+            raise MCSDPError(st, msg)
+
+    def __del__(self):
+        try:
+            if getattr(self, "_ctx", None) and self._ctx.value:
+                self._L.mcsdp_destroy(self._ctx)
+                self._ctx = C.c_void_p()
+        except Exception:
+            pass
+
+    # ---- structure ----
+    def sym_info(self):
+        info = _lib.SymInfo_t()
+        self._check(self._L.mcsdp_sym_info_get(self._ctx, C.byref(info)))
+        return {f: getattr(info, f) for f, _ in info._fields_}
+
+    def sym_export(self):
+        i = self.info
+        perm = np.zeros(i["n"], np.int32)
+        sn_col = np.zeros(i["nsuper"] + 1, np.int32)
+        sn_rowptr = np.zeros(i["nsuper"] + 1, np.int64)
+        self._check(self._L.mcsdp_sym_export(self._ctx, None, None, sn_rowptr.ctypes.data_as(C.c_void_p),
+                                             None, None, None))
+        sn_rows = np.zeros(int(sn_rowptr[-1]), np.int32)
+        sn_valptr = np.zeros(i["nsuper"] + 1, np.int64)
+        con_order = np.zeros(i["m"], np.int32)
+        self._check(self._L.mcsdp_sym_export(
+            self._ctx, perm.ctypes.data_as(C.c_void_p), sn_col.ctypes.data_as(C.c_void_p),
+            sn_rowptr.ctypes.data_as(C.c_void_p), sn_rows.ctypes.data_as(C.c_void_p),
+            sn_valptr.ctypes.data_as(C.c_void_p), con_order.ctypes.data_as(C.c_void_p)))
+        return dict(perm=perm, sn_col=sn_col, sn_rowptr=sn_rowptr, sn_rows=sn_rows,
+                    sn_valptr=sn_valptr, con_order=con_order)
+
+    def layout_index(self):
+        """For every layout value: (row, col) in the caller's indices and a mask of the stored
+        lower entries (index bookkeeping only)."""
+        s = self.sym_export()
+        nnz = int(s["sn_valptr"][-1])
+        r_new = np.full(nnz, -1, np.int64)
+        c_new = np.full(nnz, -1, np.int64)
+        for t in range(len(s["sn_col"]) - 1):
+            rows = s["sn_rows"][s["sn_rowptr"][t]:s["sn_rowptr"][t + 1]]
+            c0, c1 = s["sn_col"][t], s["sn_col"][t + 1]
+            nr = len(rows)
+            base = int(s["sn_valptr"][t])
+            for lc in range(c1 - c0):
+                r_new[base + lc * nr: base + (lc + 1) * nr] = rows
+                c_new[base + lc * nr: base + (lc + 1) * nr] = c0 + lc
+        valid = r_new >= c_new
+        perm = s["perm"].astype(np.int64)
+        return perm[np.where(valid, r_new, 0)], perm[np.where(valid, c_new, 0)], valid, s
+
+    # ---- device calls ----
+    def _dev(self, a, n):
+        if a is None:
+            return None
+        t = torch.as_tensor(a, dtype=torch.float64, device=self.torch_device).contiguous()
+        assert t.numel() == n, (t.numel(), n)
+        return t
+
+    def zeros_layout(self):
+        return torch.zeros(self.info["nnz_layout"], dtype=torch.float64, device=self.torch_device)
+
+    def set_iterate(self, Xbar_layout=None, z=None):
+        X = self._dev(Xbar_layout, self.info["nnz_layout"])
+        zz = self._dev(z, self.m)
+        self._check(self._L.mcsdp_set_iterate(self._ctx, _ptr(X), _ptr(zz)))
+
+    def get_iterate(self):
+        X = self.zeros_layout()
+        Y = self.zeros_layout()
+        z = torch.zeros(self.m, dtype=torch.float64, device=self.torch_device)
+        self._check(self._L.mcsdp_get_iterate(self._ctx, _ptr(X), _ptr(z), _ptr(Y)))
+        return X, z, Y
+
+    def solve(self):
+        r = _lib.Result_t()
+        st = self._L.mcsdp_solve(self._ctx, C.byref(r))
+        out = {f: getattr(r, f) for f, _ in r._fields_}
+        out["status_name"] = _lib.STATUS.get(st, st)
+        if st not in (0, 3):
+            self._check(st)
+        return out
+
+    def scm_assemble(self, Xbar_layout, z, out=None):
+        X = self._dev(Xbar_layout, self.info["nnz_layout"])
+        zz = self._dev(z, self.m)
+        B = out if out is not None else torch.zeros(self.m, self.m, dtype=torch.float64,
+                                                    device=self.torch_device)
+        h = torch.zeros(self.m, dtype=torch.float64, device=self.torch_device)
+        # B is filled column-major (lower triangle, i >= j): a row-major torch tensor viewed
+        # transposed has that layout
+        Bt = B.t()
+        assert Bt.stride(0) == 1
+        self._check(self._L.mcsdp_scm_assemble(self._ctx, _ptr(X), _ptr(zz), _ptr(B), self.m,
+                                               _ptr(h), 0))
+        return Bt, h
+
+    def newton_step(self, Xbar_layout, z):
+        X = self._dev(Xbar_layout, self.info["nnz_layout"])
+        zz = self._dev(z, self.m)
+        dz = torch.zeros(self.m, dtype=torch.float64, device=self.torch_device)
+        dX = self.zeros_layout()
+        dY = self.zeros_layout()
+        ap, ad, mu = C.c_double(), C.c_double(), C.c_double()
+        self._check(self._L.mcsdp_newton_step(self._ctx, _ptr(X), _ptr(zz), _ptr(dz), _ptr(dX),
+                                              _ptr(dY), C.byref(ap), C.byref(ad), C.byref(mu)))
+        return dict(dz=dz, dX=dX, dY=dY, alpha_p=ap.value, alpha_d=ad.value, mu=mu.value)
+
+    def factors(self, Xbar_layout, z):
+        X = self._dev(Xbar_layout, self.info["nnz_layout"])
+        zz = self._dev(z, self.m)
+        Lh = self.zeros_layout()
+        N = self.zeros_layout()
+        self._check(self._L.mcsdp_factors(self._ctx, _ptr(X), _ptr(zz), _ptr(Lh), _ptr(N)))
+        return Lh, N

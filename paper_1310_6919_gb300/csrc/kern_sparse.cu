@@ -1,0 +1,521 @@
+// Sparse-structure kernels of the MC-PDIPM iteration:
+//   K2  Y = N N^T (supernodal, left-looking, one level of the supernode tree per launch)
+//   K1  Algorithm 1 (Sec. 3.1): L̂ with X̂^{-1} = L̂ L̂^T, one CTA per clique
+//   K5  Y / dY on the aggregate pattern
+//   K6  P-MATRIX (eq. newdX2), one warp per column
+//   K7  clique-wise primal step length (eq. primal_length2)
+//   K8  scalars and update
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "warp_solve.cuh"
+
+namespace mcsdp {
+
+// ---------------------------------------------------------------------------------------------
+// K5: out[slot] = c0 * A_0[slot] + c1 * sum_k vec[k] A_k[slot]
+__global__ void k_slot_combine(DevSym S, double *out, const double *__restrict__ vec, double c0,
+                               double c1) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S.nslot;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int q = S.slot_ptr[s]; q < S.slot_ptr[s + 1]; ++q) {
+      int k = S.slot_k[q];
+      if (k > 0) acc = fma(S.slot_val[q], vec[k - 1], acc);
+    }
+    out[S.slot_off[s]] = c0 * S.slot_a0[s] + c1 * acc;
+  }
+}
+
+void launch_slot_combine(const DevSym &S, double *out, const double *vec, double c0, double c1,
+                         cudaStream_t st) {
+  int blocks = (int)((S.nslot + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  k_slot_combine<<<blocks, 256, 0, st>>>(S, out, vec, c0, c1);
+}
+
+// ---------------------------------------------------------------------------------------------
+// dense Cholesky of an nrow x ncol column-major panel in shared memory (lower, in place):
+// the leading ncol x ncol block is factored, the rows below are solved against it.
+__device__ void chol_panel_smem(double *F, int nrow, int ncol, int *status_word, int flag) {
+  __shared__ double s_inv;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  for (int j = 0; j < ncol; ++j) {
+    if (tid == 0) {
+      double d = F[j + (int64_t)j * nrow];
+      if (!(d > 0.0)) {
+        atomicOr(status_word, flag);
+        d = 1.0;
+      }
+      d = sqrt(d);
+      F[j + (int64_t)j * nrow] = d;
+      s_inv = 1.0 / d;
+    }
+    __syncthreads();
+    const double iv = s_inv;
+    for (int i = j + 1 + tid; i < nrow; i += bd) F[i + (int64_t)j * nrow] *= iv;
+    __syncthreads();
+    const int w = ncol - j - 1, hgt = nrow - j - 1;
+    for (int idx = tid; idx < w * hgt; idx += bd) {
+      int kk = j + 1 + idx / hgt, ii = j + 1 + idx % hgt;
+      if (ii >= kk) F[ii + (int64_t)kk * nrow] -= F[ii + (int64_t)j * nrow] * F[kk + (int64_t)j * nrow];
+    }
+    __syncthreads();
+  }
+}
+
+// K2 for one level: CTA (supernode in level, candidate).  Frontal block F = (Ybase + a dY)
+// restricted to C_t x S_t, minus updates from the descendants listed for t, then factored.
+__global__ void k_ychol(DevSym S, int lvl_begin, const double *__restrict__ alpha,
+                        const double *__restrict__ Yb, const double *__restrict__ dY, double *Nbuf,
+                        double *dinv, int *status) {
+  extern __shared__ double F[];
+  const int t = S.lvl_sn[lvl_begin + blockIdx.x];
+  const int c = blockIdx.y;
+  if (*(volatile int *)&status[c] & ST_NOT_PD) return;
+  double *N = Nbuf + (int64_t)c * S.nnzL;
+  double *dv = dinv + (int64_t)c * S.n;
+  const double a = alpha ? alpha[c] : 0.0;
+  const int64_t r0 = S.sn_rowptr[t];
+  const int nrow = (int)(S.sn_rowptr[t + 1] - r0);
+  const int c0 = S.sn_col[t], ncol = S.sn_col[t + 1] - c0;
+  const int64_t v0 = S.sn_valptr[t];
+  const int sz = nrow * ncol;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  for (int i = tid; i < sz; i += bd) F[i] = dY ? fma(a, dY[v0 + i], Yb[v0 + i]) : Yb[v0 + i];
+  __syncthreads();
+  for (int u = S.upd_ptr[t]; u < S.upd_ptr[t + 1]; ++u) {
+    const int s = S.upd_src[u], p1 = S.upd_p1[u], p2 = S.upd_p2[u];
+    const int *rel = S.upd_rel + S.upd_relptr[u];
+    const int snrow = (int)(S.sn_rowptr[s + 1] - S.sn_rowptr[s]);
+    const int sncol = S.sn_col[s + 1] - S.sn_col[s];
+    const double *Ls = N + S.sn_valptr[s];
+    const int na = snrow - p1, nb = p2 - p1;
+    for (int idx = tid; idx < na * nb; idx += bd) {
+      const int ia = idx % na, ib = idx / na;
+      if (ia < ib) continue;
+      double acc = 0.0;
+      for (int k = 0; k < sncol; ++k)
+        acc = fma(Ls[p1 + ia + (int64_t)k * snrow], Ls[p1 + ib + (int64_t)k * snrow], acc);
+      F[rel[ia] + (int64_t)rel[ib] * nrow] -= acc;
+    }
+    __syncthreads();
+  }
+  chol_panel_smem(F, nrow, ncol, &status[c], ST_NOT_PD);
+  for (int i = tid; i < sz; i += bd) N[v0 + i] = F[i];
+  for (int j = tid; j < ncol; j += bd) dv[c0 + j] = 1.0 / F[j + (int64_t)j * nrow];
+}
+
+size_t ychol_smem_bytes(const DevSym &S) { return (size_t)S.max_nrow * S.max_ncol * 8; }
+
+void launch_ychol_level(const DevSym &S, int lvl_begin, int lvl_count, int ncand,
+                        const double *alpha, const double *Yb, const double *dY, double *Nbuf,
+                        double *dinv, int *status, cudaStream_t st) {
+  dim3 grid(lvl_count, ncand);
+  const size_t smem = ychol_smem_bytes(S);
+  static size_t configured = 0;
+  if (smem > configured) {
+    cudaFuncSetAttribute(k_ychol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = smem;
+  }
+  k_ychol<<<grid, 256, smem, st>>>(S, lvl_begin, alpha, Yb, dY, Nbuf, dinv, status);
+}
+
+// ---------------------------------------------------------------------------------------------
+// K1: Algorithm 1.  For clique r with k = |C_r|: the reversed block P X̄_CC P (Step 2-1) is
+// Cholesky-factored, M = chol(P X̄_CC P) (Step 2-2); L_r = P M^{-T} P (Step 2-3) and its first
+// |S_r| columns are stored as L̂_{C_r S_r} (Step 3).
+__global__ void k_alg1(DevSym S, const double *__restrict__ X, double *Lh, double *dinvL,
+                       int *status) {
+  extern __shared__ double sm[];
+  const int r = blockIdx.x;
+  const int64_t r0 = S.sn_rowptr[r];
+  const int k = (int)(S.sn_rowptr[r + 1] - r0);
+  const int c0 = S.sn_col[r], ns = S.sn_col[r + 1] - c0;
+  const int64_t v0 = S.sn_valptr[r];
+  double *A = sm;                      // k x k
+  double *T = sm + (int64_t)k * k;     // k x k, inverse of M
+  double *rd = T + (int64_t)k * k;     // k reciprocals of the diagonal of M
+  const int tid = threadIdx.x, bd = blockDim.x;
+  for (int idx = tid; idx < k * k; idx += bd) {
+    const int a = idx % k, b = idx / k;
+    if (a < b) continue;
+    const double v = clique_entry(S, X, r, a, b);
+    A[(k - 1 - a) + (int64_t)(k - 1 - b) * k] = v;
+    A[(k - 1 - b) + (int64_t)(k - 1 - a) * k] = v;
+  }
+  __syncthreads();
+  chol_panel_smem(A, k, k, status, ST_NOT_PD);
+  for (int j = tid; j < k; j += bd) rd[j] = 1.0 / A[j + (int64_t)j * k];
+  __syncthreads();
+  // T = M^{-1}, lower triangular, one thread per column
+  for (int j = tid; j < k; j += bd) {
+    T[j + (int64_t)j * k] = rd[j];
+    for (int i = j + 1; i < k; ++i) {
+      double s = 0.0;
+      for (int l = j; l < i; ++l) s = fma(A[i + (int64_t)l * k], T[l + (int64_t)j * k], s);
+      T[i + (int64_t)j * k] = -s * rd[i];
+    }
+  }
+  __syncthreads();
+  // L_r[a][b] = (P M^{-T} P)[a][b] = T[k-1-b][k-1-a]
+  for (int idx = tid; idx < k * ns; idx += bd) {
+    const int a = idx % k, b = idx / k;
+    Lh[v0 + idx] = (a >= b) ? T[(k - 1 - b) + (int64_t)(k - 1 - a) * k] : 0.0;
+  }
+  for (int b = tid; b < ns; b += bd) dinvL[c0 + b] = 1.0 / T[(k - 1 - b) + (int64_t)(k - 1 - b) * k];
+}
+
+size_t alg1_smem_bytes(const DevSym &S) {
+  return ((size_t)2 * S.max_nrow * S.max_nrow + S.max_nrow) * 8;
+}
+
+void launch_alg1(const DevSym &S, const double *X, double *Lh, double *dinvL, int *status,
+                 cudaStream_t st) {
+  const size_t smem = alg1_smem_bytes(S);
+  static size_t configured = 0;
+  if (smem > configured) {
+    cudaFuncSetAttribute(k_alg1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = smem;
+  }
+  k_alg1<<<S.ns, 256, smem, st>>>(S, X, Lh, dinvL, status);
+}
+
+// ---------------------------------------------------------------------------------------------
+// K6: P-MATRIX, eq. (newdX2), column k per warp:
+//   y = N^{-T} N^{-1} e_k         (Y^{-1} e_k)
+//   w = L̂^{-T} L̂^{-1} (dY y)      (X̂ dY Y^{-1} e_k)
+// and the entries on E are stored: Y^{-1} on lower(E), M = X̂ dY Y^{-1} at (i, k) for rows i of
+// column k (Mlow) and at the transposed position for rows i < k (Mup).
+
+__global__ void k_pmatrix(DevSym S, const double *__restrict__ Lh, const double *__restrict__ dinvL,
+                          const double *__restrict__ N, const double *__restrict__ dinvN,
+                          const double *__restrict__ dY, double *YinvE, double *Mlow, double *Mup,
+                          int wpb) {
+  extern __shared__ double sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x * wpb + warp;
+  if (k >= S.n) return;
+  const int n = S.n;
+  double *y = sm + (int64_t)warp * 2 * n;
+  double *w = y + n;
+  for (int i = lane; i < n; i += 32) y[i] = (i == k) ? 1.0 : 0.0;
+  __syncwarp();
+  for (int s = S.col2sn[k]; s >= 0; s = S.sn_parent[s]) warp_fwd_sn(S, N, dinvN, y, s, lane);
+  for (int s = S.ns - 1; s >= 0; --s) warp_bwd_sn(S, N, dinvN, y, s, lane);
+  const int t = S.col2sn[k];
+  const int64_t r0 = S.sn_rowptr[t];
+  const int nrow = (int)(S.sn_rowptr[t + 1] - r0);
+  const int lc = k - S.sn_col[t];
+  const int64_t cbase = S.sn_valptr[t] + (int64_t)lc * nrow;
+  for (int p = lc + lane; p < nrow; p += 32) YinvE[cbase + p] = y[S.rows[r0 + p]];
+  for (int i = lane; i < n; i += 32) {
+    double acc = 0.0;
+    for (int q = S.arow_ptr[i]; q < S.arow_ptr[i + 1]; ++q)
+      acc = fma(dY[S.arow_off[q]], y[S.arow_col[q]], acc);
+    w[i] = acc;
+  }
+  __syncwarp();
+  for (int s = 0; s < S.ns; ++s) warp_fwd_sn(S, Lh, dinvL, w, s, lane);
+  for (int s = S.ns - 1; s >= 0; --s) warp_bwd_sn(S, Lh, dinvL, w, s, lane);
+  for (int p = lc + lane; p < nrow; p += 32) Mlow[cbase + p] = w[S.rows[r0 + p]];
+  for (int q = S.rs_ptr[k] + lane; q < S.rs_ptr[k + 1]; q += 32) Mup[S.rs_off[q]] = w[S.rs_col[q]];
+}
+
+void launch_pmatrix(const DevSym &S, const double *Lh, const double *dinvL, const double *N,
+                    const double *dinvN, const double *dY, double *YinvE, double *Mlow,
+                    double *Mup, cudaStream_t st) {
+  size_t per = (size_t)2 * S.n * 8;
+  int wpb = (int)((200 * 1024) / per);
+  if (wpb > 4) wpb = 4;
+  if (wpb < 1) wpb = 1;
+  int blocks = (S.n + wpb - 1) / wpb;
+  static size_t configured = 0;
+  if (per * wpb > configured) {
+    cudaFuncSetAttribute(k_pmatrix, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(per * wpb));
+    configured = per * wpb;
+  }
+  k_pmatrix<<<blocks, 32 * wpb, per * wpb, st>>>(S, Lh, dinvL, N, dinvN, dY, YinvE, Mlow, Mup, wpb);
+}
+
+// dX on lower(E): beta mu Y^{-1} - X̄ - (M + M^T)/2   (eq. dX with the symmetrisation)
+__global__ void k_dx_combine(DevSym S, double betamu, const double *__restrict__ X,
+                             const double *__restrict__ YinvE, const double *__restrict__ Mlow,
+                             const double *__restrict__ Mup, double *dX) {
+  const int s = blockIdx.x;
+  const int nrow = (int)(S.sn_rowptr[s + 1] - S.sn_rowptr[s]);
+  const int ncol = S.sn_col[s + 1] - S.sn_col[s];
+  const int64_t v0 = S.sn_valptr[s];
+  for (int idx = threadIdx.x; idx < nrow * ncol; idx += blockDim.x) {
+    const int p = idx % nrow, lc = idx / nrow;
+    const int64_t o = v0 + idx;
+    double v;
+    if (p < lc) v = 0.0;
+    else if (p == lc) v = betamu * YinvE[o] - X[o] - Mlow[o];
+    else v = betamu * YinvE[o] - X[o] - 0.5 * (Mlow[o] + Mup[o]);
+    dX[o] = v;
+  }
+}
+
+void launch_dx_combine(const DevSym &S, double betamu, const double *X, const double *YinvE,
+                       const double *Mlow, const double *Mup, double *dX, cudaStream_t st) {
+  k_dx_combine<<<S.ns, 128, 0, st>>>(S, betamu, X, YinvE, Mlow, Mup, dX);
+}
+
+// ---------------------------------------------------------------------------------------------
+// K7: alpha_r = max{alpha in (0,1] : X̄_CC + alpha dX_CC psd} (eq. primal_length2):
+// X̄_CC = L L^T, W = L^{-1} dX_CC L^{-T}, Householder tridiagonalisation of W, smallest
+// eigenvalue by Sturm-count multisection; alpha_r = min(1, -1/lambda_min).
+__device__ int sturm_count(const double *d, const double *e, int k, double sig) {
+  int cnt = 0;
+  double q = d[0] - sig;
+  if (q < 0) ++cnt;
+  for (int i = 1; i < k; ++i) {
+    if (q == 0.0) q = 1e-300;
+    q = (d[i] - sig) - e[i - 1] * e[i - 1] / q;
+    if (q < 0) ++cnt;
+  }
+  return cnt;
+}
+
+__global__ void k_primal_step(DevSym S, const double *__restrict__ X, const double *__restrict__ D,
+                              double *alpha_r, int *status) {
+  extern __shared__ double sm[];
+  __shared__ double red[32];
+  __shared__ double sh[4];
+  const int r = blockIdx.x;
+  const int64_t r0 = S.sn_rowptr[r];
+  const int k = (int)(S.sn_rowptr[r + 1] - r0);
+  double *Xs = sm;
+  double *W = Xs + (int64_t)k * k;
+  double *rd = W + (int64_t)k * k;
+  double *dd = rd + k;
+  double *ee = dd + k;
+  double *v = ee + k;
+  double *q = v + k;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  for (int idx = tid; idx < k * k; idx += bd) {
+    const int a = idx % k, b = idx / k;
+    if (a < b) continue;
+    const double xv = clique_entry(S, X, r, a, b);
+    const double dv = clique_entry(S, D, r, a, b);
+    Xs[a + (int64_t)b * k] = xv;
+    Xs[b + (int64_t)a * k] = xv;
+    W[a + (int64_t)b * k] = dv;
+    W[b + (int64_t)a * k] = dv;
+  }
+  __syncthreads();
+  chol_panel_smem(Xs, k, k, status, ST_NOT_PD);
+  for (int j = tid; j < k; j += bd) rd[j] = 1.0 / Xs[j + (int64_t)j * k];
+  __syncthreads();
+  for (int pass = 0; pass < 2; ++pass) {
+    // W <- L^{-1} W (columns independent), then transpose
+    for (int col = tid; col < k; col += bd) {
+      double *wc = W + (int64_t)col * k;
+      for (int i = 0; i < k; ++i) {
+        double s = wc[i];
+        for (int l = 0; l < i; ++l) s = fma(-Xs[i + (int64_t)l * k], wc[l], s);
+        wc[i] = s * rd[i];
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < k * k; idx += bd) {
+      const int a = idx % k, b = idx / k;
+      if (a < b) {
+        double t1 = W[a + (int64_t)b * k];
+        W[a + (int64_t)b * k] = W[b + (int64_t)a * k];
+        W[b + (int64_t)a * k] = t1;
+      }
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < k * k; idx += bd) {
+    const int a = idx % k, b = idx / k;
+    if (a < b) {
+      double m = 0.5 * (W[a + (int64_t)b * k] + W[b + (int64_t)a * k]);
+      W[a + (int64_t)b * k] = m;
+      W[b + (int64_t)a * k] = m;
+    }
+  }
+  __syncthreads();
+  // Householder tridiagonalisation of the symmetric k x k matrix W
+  for (int j = 0; j + 2 < k; ++j) {
+    const int mlen = k - j - 1;
+    double part = 0.0;
+    for (int i = tid; i < mlen; i += bd) {
+      double x = W[(j + 1 + i) + (int64_t)j * k];
+      part += x * x;
+    }
+    const double ss = block_reduce_sum(part, red);
+    const double x0 = W[(j + 1) + (int64_t)j * k];
+    if (ss - x0 * x0 <= 1e-300 * (ss + 1e-300) || ss == 0.0) {
+      if (tid == 0) { ee[j] = x0; dd[j] = W[j + (int64_t)j * k]; }
+      __syncthreads();
+      continue;
+    }
+    const double alpha = x0 >= 0 ? -sqrt(ss) : sqrt(ss);
+    const double vn2 = ss - x0 * x0 + (x0 - alpha) * (x0 - alpha);
+    const double tau = 2.0 / vn2;
+    for (int i = tid; i < mlen; i += bd) v[i] = (i == 0) ? (x0 - alpha) : W[(j + 1 + i) + (int64_t)j * k];
+    __syncthreads();
+    double pv = 0.0;
+    for (int i = tid; i < mlen; i += bd) {
+      double s = 0.0;
+      for (int l = 0; l < mlen; ++l) s = fma(W[(j + 1 + i) + (int64_t)(j + 1 + l) * k], v[l], s);
+      q[i] = tau * s;
+      pv += q[i] * v[i];
+    }
+    const double K = 0.5 * tau * block_reduce_sum(pv, red);
+    for (int i = tid; i < mlen; i += bd) q[i] -= K * v[i];
+    __syncthreads();
+    for (int idx = tid; idx < mlen * mlen; idx += bd) {
+      const int i = idx % mlen, l = idx / mlen;
+      W[(j + 1 + i) + (int64_t)(j + 1 + l) * k] -= v[i] * q[l] + q[i] * v[l];
+    }
+    if (tid == 0) { ee[j] = alpha; dd[j] = W[j + (int64_t)j * k]; }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (k >= 2) {
+      dd[k - 2] = W[(k - 2) + (int64_t)(k - 2) * k];
+      ee[k - 2] = W[(k - 1) + (int64_t)(k - 2) * k];
+    }
+    dd[k - 1] = W[(k - 1) + (int64_t)(k - 1) * k];
+  }
+  __syncthreads();
+  if (tid < 32) {
+    const int lane = tid;
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < k; ++i) {
+      double rad = (i > 0 ? fabs(ee[i - 1]) : 0.0) + (i + 1 < k ? fabs(ee[i]) : 0.0);
+      lo = fmin(lo, dd[i] - rad);
+      hi = fmax(hi, dd[i] + rad);
+    }
+    lo -= 1e-12 * (fabs(lo) + 1.0);
+    hi += 1e-12 * (fabs(hi) + 1.0);
+    for (int it = 0; it < 64; ++it) {
+      const double sig = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+      const int c = sturm_count(dd, ee, k, sig);
+      const unsigned ball = __ballot_sync(0xffffffffu, c >= 1);
+      const double s31 = __shfl_sync(0xffffffffu, sig, 31);
+      if (ball == 0u) {
+        lo = s31;
+      } else {
+        const int f = __ffs(ball) - 1;
+        const double sf = __shfl_sync(0xffffffffu, sig, f);
+        const double sp = __shfl_sync(0xffffffffu, sig, f > 0 ? f - 1 : 0);
+        hi = sf;
+        if (f > 0) lo = sp;
+      }
+      if (hi - lo <= 4e-16 * fmax(fabs(lo), fabs(hi)) + 1e-300) break;
+    }
+    if (lane == 0) {
+      const double lam = 0.5 * (lo + hi);
+      sh[0] = lam < -1.0 ? -1.0 / lam : 1.0;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) alpha_r[r] = sh[0];
+}
+
+size_t primal_step_smem_bytes(const DevSym &S) {
+  return ((size_t)2 * S.max_nrow * S.max_nrow + 5 * (size_t)S.max_nrow) * 8;
+}
+
+void launch_primal_step(const DevSym &S, const double *X, const double *D, double *alpha_r,
+                        int *status, cudaStream_t st) {
+  const size_t smem = primal_step_smem_bytes(S);
+  static size_t configured = 0;
+  if (smem > configured) {
+    cudaFuncSetAttribute(k_primal_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = smem;
+  }
+  k_primal_step<<<S.ns, 256, smem, st>>>(S, X, D, alpha_r, status);
+}
+
+// ---------------------------------------------------------------------------------------------
+// K8: scalars, single CTA, fixed-order reductions (bitwise reproducible)
+__global__ void k_measures(DevSym S, const double *__restrict__ X, const double *__restrict__ Y,
+                           const double *__restrict__ z, const double *__restrict__ alpha_r,
+                           double *scal) {
+  __shared__ double red[32];
+  const int tid = threadIdx.x, bd = blockDim.x;
+  double xy = 0.0, pobj = 0.0;
+  for (int64_t s = tid; s < S.nslot; s += bd) {
+    const int64_t o = S.slot_off[s];
+    const double mult = (S.slot_i[s] == S.slot_j[s]) ? 1.0 : 2.0;
+    xy += mult * X[o] * Y[o];
+    pobj += mult * S.slot_a0[s] * X[o];
+  }
+  double pinf = 0.0, dobj = 0.0, maxb = 0.0;
+  for (int k = tid; k < S.m; k += bd) {
+    double ax = 0.0;
+    for (int q = S.con_ptr[k]; q < S.con_ptr[k + 1]; ++q) ax = fma(S.con_w[q], X[S.con_off[q]], ax);
+    pinf = fmax(pinf, fabs(ax - S.b[k]));
+    dobj = fma(S.b[k], z[k], dobj);
+    maxb = fmax(maxb, fabs(S.b[k]));
+  }
+  double amin = 1.0;
+  if (alpha_r)
+    for (int r = tid; r < S.ns; r += bd) amin = fmin(amin, alpha_r[r]);
+  xy = block_reduce_sum(xy, red);
+  pobj = block_reduce_sum(pobj, red);
+  dobj = block_reduce_sum(dobj, red);
+  // max / min reductions
+  __shared__ double mx[3][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    pinf = fmax(pinf, __shfl_down_sync(0xffffffffu, pinf, o));
+    maxb = fmax(maxb, __shfl_down_sync(0xffffffffu, maxb, o));
+    amin = fmin(amin, __shfl_down_sync(0xffffffffu, amin, o));
+  }
+  if ((tid & 31) == 0) { mx[0][tid >> 5] = pinf; mx[1][tid >> 5] = maxb; mx[2][tid >> 5] = amin; }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, b2 = 0.0, c = 1.0;
+    for (int i = 0; i < (bd + 31) / 32; ++i) { a = fmax(a, mx[0][i]); b2 = fmax(b2, mx[1][i]); c = fmin(c, mx[2][i]); }
+    scal[0] = xy;
+    scal[1] = pobj;
+    scal[2] = dobj;
+    scal[3] = a;
+    scal[4] = b2;
+    scal[5] = c;
+  }
+}
+
+void launch_measures(const DevSym &S, const double *X, const double *Y, const double *z,
+                     const double *alpha_r, double *scal, cudaStream_t st) {
+  k_measures<<<1, 1024, 0, st>>>(S, X, Y, z, alpha_r, scal);
+}
+
+__global__ void k_update(int64_t nnz, double *X, const double *__restrict__ dX, double ap, int m,
+                         double *z, const double *__restrict__ dz, double ad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nnz;
+       i += (int64_t)gridDim.x * blockDim.x)
+    X[i] = fma(ap, dX[i], X[i]);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x)
+    z[i] = fma(ad, dz[i], z[i]);
+}
+
+void launch_update(const DevSym &S, double *X, const double *dX, double ap, double *z,
+                   const double *dz, double ad, cudaStream_t st) {
+  int blocks = (int)((S.nnzL + 255) / 256);
+  if (blocks > 2048) blocks = 2048;
+  k_update<<<blocks, 256, 0, st>>>(S.nnzL, X, dX, ap, S.m, z, dz, ad);
+}
+
+__global__ void k_set_identity(DevSym S, double *X) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < S.n; j += gridDim.x * blockDim.x) {
+    const int t = S.col2sn[j];
+    const int nrow = (int)(S.sn_rowptr[t + 1] - S.sn_rowptr[t]);
+    const int lc = j - S.sn_col[t];
+    X[S.sn_valptr[t] + lc + (int64_t)lc * nrow] = 1.0;
+  }
+}
+
+void launch_set_identity(const DevSym &S, double *X, cudaStream_t st) {
+  k_set_identity<<<(S.n + 255) / 256, 256, 0, st>>>(S, X);
+}
+
+}  // namespace mcsdp

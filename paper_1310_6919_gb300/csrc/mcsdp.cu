@@ -1,0 +1,805 @@
+// libmcsdp: C ABI, context, workspace and the MC-PDIPM driver loop (Sec. 2.2 Steps 0-4 with the
+// matrix-completion reformulation of Sec. 3.1).  All arithmetic of the iteration runs in the
+// kernels of kern_*.cu; the host only sequences them and reads back a few scalars per iteration.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <set>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/mcsdp.h"
+#include "internal.h"
+#include "symbolic.h"
+
+using namespace mcsdp;
+
+namespace {
+
+struct Upload {
+  size_t off;
+  const void *src;
+  size_t bytes;
+};
+
+struct Chunk {
+  int g0, g1;
+  int64_t rhs_begin;
+  int nrhs;
+  int64_t tile_begin;
+  int ntiles;
+};
+
+constexpr int NCAND = 8;  // candidates per dual step-length round
+
+}  // namespace
+
+struct mcsdp_ctx {
+  std::string err;
+  mcsdp_options opt;
+  ProblemData P;
+  Symbolic S;
+  cudaStream_t stream = nullptr;
+  int device = -1;
+  bool host_only = false;
+  // workspace plan
+  size_t ws_bytes = 0;
+  std::vector<Upload> uploads;
+  std::map<std::string, size_t> off;
+  char *ws = nullptr;
+  size_t ws_have = 0;
+  DevSym D{};
+  int64_t ldb = 0;
+  int pmax = 0;
+  std::vector<Chunk> chunks;
+  std::vector<int> rhs_all;
+  std::vector<int2> tiles_all;
+  std::vector<int64_t> panoff_all;  // per group, offset within its chunk buffer
+  std::vector<double> z0_default;
+  bool z0_ok = false;
+  bool iterate_set = false;
+  cudaEvent_t ev[8] = {};
+  // device buffers
+  double *Xbar = nullptr, *z = nullptr, *Ylay = nullptr, *N = nullptr, *dinvN = nullptr;
+  double *Lh = nullptr, *dinvL = nullptr, *dY = nullptr, *dX = nullptr, *YinvE = nullptr;
+  double *Mlow = nullptr, *Mup = nullptr, *B = nullptr, *hvec = nullptr, *xs = nullptr;
+  double *dz = nullptr, *pan = nullptr, *Ncand = nullptr, *dinvCand = nullptr;
+  double *alpha_c = nullptr, *alpha_r = nullptr, *scal = nullptr;
+  int *status = nullptr, *rhs_dev = nullptr;
+  int2 *tiles_dev = nullptr;
+  int64_t *panoff_dev = nullptr;
+};
+
+namespace {
+
+mcsdp_status fail(mcsdp_ctx *c, mcsdp_status s, const std::string &msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define CUDA_TRY(ctx, call)                                                                    \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return fail(ctx, MCSDP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+  } while (0)
+
+#define KCHECK(ctx)                                                                            \
+  do {                                                                                         \
+    cudaError_t e_ = cudaGetLastError();                                                       \
+    if (e_ != cudaSuccess)                                                                     \
+      return fail(ctx, MCSDP_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
+
+template <class T>
+void plan_table(mcsdp_ctx *c, size_t &cur, const std::string &name, const std::vector<T> &v) {
+  c->off[name] = cur;
+  if (!v.empty()) c->uploads.push_back({cur, v.data(), v.size() * sizeof(T)});
+  cur += al(std::max<size_t>(v.size() * sizeof(T), 8));
+}
+
+void plan_buf(mcsdp_ctx *c, size_t &cur, const std::string &name, size_t bytes) {
+  c->off[name] = cur;
+  cur += al(std::max<size_t>(bytes, 8));
+}
+
+void plan_workspace(mcsdp_ctx *c) {
+  Symbolic &S = c->S;
+  const int64_t nnzL = S.sn_valptr[S.ns];
+  const int n = S.n, m = S.m;
+  size_t cur = 0;
+  c->uploads.clear();
+  plan_table(c, cur, "sn_col", S.sn_col);
+  plan_table(c, cur, "sn_rowptr", S.sn_rowptr);
+  plan_table(c, cur, "rows", S.rows);
+  plan_table(c, cur, "sn_valptr", S.sn_valptr);
+  plan_table(c, cur, "sn_parent", S.sn_parent);
+  plan_table(c, cur, "col2sn", S.col2sn);
+  plan_table(c, cur, "lvl_sn", S.lvl_sn);
+  plan_table(c, cur, "upd_ptr", S.upd_ptr);
+  plan_table(c, cur, "upd_src", S.upd_src);
+  plan_table(c, cur, "upd_p1", S.upd_p1);
+  plan_table(c, cur, "upd_p2", S.upd_p2);
+  plan_table(c, cur, "upd_relptr", S.upd_relptr);
+  plan_table(c, cur, "upd_rel", S.upd_rel);
+  plan_table(c, cur, "slot_i", S.slot_i);
+  plan_table(c, cur, "slot_j", S.slot_j);
+  plan_table(c, cur, "slot_off", S.slot_off);
+  plan_table(c, cur, "slot_ptr", S.slot_ptr);
+  plan_table(c, cur, "slot_k", S.slot_k);
+  plan_table(c, cur, "slot_val", S.slot_val);
+  plan_table(c, cur, "slot_a0", S.slot_a0);
+  plan_table(c, cur, "con_ptr", S.con_ptr);
+  plan_table(c, cur, "con_off", S.con_off);
+  plan_table(c, cur, "con_w", S.con_w);
+  plan_table(c, cur, "arow_ptr", S.arow_ptr);
+  plan_table(c, cur, "arow_col", S.arow_col);
+  plan_table(c, cur, "arow_off", S.arow_off);
+  plan_table(c, cur, "rs_ptr", S.rs_ptr);
+  plan_table(c, cur, "rs_col", S.rs_col);
+  plan_table(c, cur, "rs_off", S.rs_off);
+  plan_table(c, cur, "con_order", S.con_order);
+  plan_table(c, cur, "grp_cptr", S.grp_cptr);
+  plan_table(c, cur, "grp_pptr", S.grp_pptr);
+  plan_table(c, cur, "grp_cols", S.grp_cols);
+  plan_table(c, cur, "grp_rowoff", S.grp_rowoff);
+  plan_table(c, cur, "anz_ptr", S.anz_ptr);
+  plan_table(c, cur, "anz_a", S.anz_a);
+  plan_table(c, cur, "anz_b", S.anz_b);
+  plan_table(c, cur, "anz_v", S.anz_v);
+  plan_table(c, cur, "reach_ptr", S.reach_ptr);
+  plan_table(c, cur, "need_ptr", S.need_ptr);
+  plan_table(c, cur, "reach_sn", S.reach_sn);
+  plan_table(c, cur, "need_sn", S.need_sn);
+  plan_table(c, cur, "b", c->P.b);
+  // SCM chunk plan
+  c->chunks.clear();
+  c->rhs_all.clear();
+  c->tiles_all.clear();
+  c->panoff_all.assign(S.ngroup, 0);
+  const int R = S.grp_pptr[S.ngroup];
+  const double budget = (c->opt.panel_budget_mb > 0 ? c->opt.panel_budget_mb : 1024.0) * 1048576.0;
+  size_t pan_max = 0;
+  c->pmax = 0;
+  for (int g = 0; g < S.ngroup;) {
+    Chunk ch{};
+    ch.g0 = g;
+    ch.rhs_begin = (int64_t)c->rhs_all.size();
+    ch.tile_begin = (int64_t)c->tiles_all.size();
+    size_t bytes = 0;
+    while (g < S.ngroup) {
+      const int pg = S.grp_pptr[g + 1] - S.grp_pptr[g];
+      const size_t gb = (size_t)2 * (R - S.grp_pptr[g]) * pg * 8;
+      if (g > ch.g0 && bytes + gb > budget) break;
+      c->panoff_all[g] = (int64_t)(bytes / 8);
+      bytes += gb;
+      c->pmax = std::max(c->pmax, pg);
+      for (int which = 0; which < 2; ++which)
+        for (int cc = 0; cc < pg; ++cc) c->rhs_all.push_back((g << 9) | (which << 8) | cc);
+      for (int h = g; h < S.ngroup; ++h) c->tiles_all.push_back(make_int2(h, g));
+      ++g;
+    }
+    ch.g1 = g;
+    ch.nrhs = (int)((int64_t)c->rhs_all.size() - ch.rhs_begin);
+    ch.ntiles = (int)((int64_t)c->tiles_all.size() - ch.tile_begin);
+    c->chunks.push_back(ch);
+    pan_max = std::max(pan_max, bytes);
+  }
+  plan_table(c, cur, "rhs", c->rhs_all);
+  plan_table(c, cur, "tiles", c->tiles_all);
+  plan_table(c, cur, "panoff", c->panoff_all);
+  // iteration buffers
+  c->ldb = ((int64_t)m + 1 + 31) / 32 * 32;
+  plan_buf(c, cur, "Xbar", nnzL * 8);
+  plan_buf(c, cur, "z", (size_t)m * 8);
+  plan_buf(c, cur, "Ylay", nnzL * 8);
+  plan_buf(c, cur, "N", nnzL * 8);
+  plan_buf(c, cur, "dinvN", (size_t)n * 8);
+  plan_buf(c, cur, "Lh", nnzL * 8);
+  plan_buf(c, cur, "dinvL", (size_t)n * 8);
+  plan_buf(c, cur, "dY", nnzL * 8);
+  plan_buf(c, cur, "dX", nnzL * 8);
+  plan_buf(c, cur, "YinvE", nnzL * 8);
+  plan_buf(c, cur, "Mlow", nnzL * 8);
+  plan_buf(c, cur, "Mup", nnzL * 8);
+  plan_buf(c, cur, "B", (size_t)c->ldb * m * 8);
+  plan_buf(c, cur, "hvec", (size_t)m * 8);
+  plan_buf(c, cur, "xs", (size_t)m * 8);
+  plan_buf(c, cur, "dz", (size_t)m * 8);
+  plan_buf(c, cur, "pan", pan_max);
+  plan_buf(c, cur, "Ncand", (size_t)NCAND * nnzL * 8);
+  plan_buf(c, cur, "dinvCand", (size_t)NCAND * n * 8);
+  plan_buf(c, cur, "alpha_c", NCAND * 8);
+  plan_buf(c, cur, "alpha_r", (size_t)S.ns * 8);
+  plan_buf(c, cur, "scal", 16 * 8);
+  plan_buf(c, cur, "status", 16 * 4);
+  c->ws_bytes = cur;
+}
+
+template <class T>
+T *wsp(mcsdp_ctx *c, const char *name) {
+  return reinterpret_cast<T *>(c->ws + c->off.at(name));
+}
+
+void bind_pointers(mcsdp_ctx *c) {
+  Symbolic &S = c->S;
+  DevSym &D = c->D;
+  D.n = S.n;
+  D.m = S.m;
+  D.ns = S.ns;
+  D.ngroup = S.ngroup;
+  D.max_nrow = S.max_nrow;
+  D.max_ncol = S.max_ncol;
+  D.nnzL = S.sn_valptr[S.ns];
+  D.nslot = S.nslot;
+  D.sn_col = wsp<int>(c, "sn_col");
+  D.sn_rowptr = wsp<int64_t>(c, "sn_rowptr");
+  D.rows = wsp<int>(c, "rows");
+  D.sn_valptr = wsp<int64_t>(c, "sn_valptr");
+  D.sn_parent = wsp<int>(c, "sn_parent");
+  D.col2sn = wsp<int>(c, "col2sn");
+  D.lvl_sn = wsp<int>(c, "lvl_sn");
+  D.upd_ptr = wsp<int>(c, "upd_ptr");
+  D.upd_src = wsp<int>(c, "upd_src");
+  D.upd_p1 = wsp<int>(c, "upd_p1");
+  D.upd_p2 = wsp<int>(c, "upd_p2");
+  D.upd_relptr = wsp<int64_t>(c, "upd_relptr");
+  D.upd_rel = wsp<int>(c, "upd_rel");
+  D.slot_i = wsp<int>(c, "slot_i");
+  D.slot_j = wsp<int>(c, "slot_j");
+  D.slot_off = wsp<int64_t>(c, "slot_off");
+  D.slot_ptr = wsp<int>(c, "slot_ptr");
+  D.slot_k = wsp<int>(c, "slot_k");
+  D.slot_val = wsp<double>(c, "slot_val");
+  D.slot_a0 = wsp<double>(c, "slot_a0");
+  D.con_ptr = wsp<int>(c, "con_ptr");
+  D.con_off = wsp<int64_t>(c, "con_off");
+  D.con_w = wsp<double>(c, "con_w");
+  D.arow_ptr = wsp<int>(c, "arow_ptr");
+  D.arow_col = wsp<int>(c, "arow_col");
+  D.arow_off = wsp<int64_t>(c, "arow_off");
+  D.rs_ptr = wsp<int>(c, "rs_ptr");
+  D.rs_col = wsp<int>(c, "rs_col");
+  D.rs_off = wsp<int64_t>(c, "rs_off");
+  D.con_order = wsp<int>(c, "con_order");
+  D.grp_cptr = wsp<int>(c, "grp_cptr");
+  D.grp_pptr = wsp<int>(c, "grp_pptr");
+  D.grp_cols = wsp<int>(c, "grp_cols");
+  D.grp_rowoff = wsp<int64_t>(c, "grp_rowoff");
+  D.anz_ptr = wsp<int>(c, "anz_ptr");
+  D.anz_a = wsp<int16_t>(c, "anz_a");
+  D.anz_b = wsp<int16_t>(c, "anz_b");
+  D.anz_v = wsp<double>(c, "anz_v");
+  D.reach_ptr = wsp<int64_t>(c, "reach_ptr");
+  D.need_ptr = wsp<int64_t>(c, "need_ptr");
+  D.reach_sn = wsp<int>(c, "reach_sn");
+  D.need_sn = wsp<int>(c, "need_sn");
+  D.b = wsp<double>(c, "b");
+  c->Xbar = wsp<double>(c, "Xbar");
+  c->z = wsp<double>(c, "z");
+  c->Ylay = wsp<double>(c, "Ylay");
+  c->N = wsp<double>(c, "N");
+  c->dinvN = wsp<double>(c, "dinvN");
+  c->Lh = wsp<double>(c, "Lh");
+  c->dinvL = wsp<double>(c, "dinvL");
+  c->dY = wsp<double>(c, "dY");
+  c->dX = wsp<double>(c, "dX");
+  c->YinvE = wsp<double>(c, "YinvE");
+  c->Mlow = wsp<double>(c, "Mlow");
+  c->Mup = wsp<double>(c, "Mup");
+  c->B = wsp<double>(c, "B");
+  c->hvec = wsp<double>(c, "hvec");
+  c->xs = wsp<double>(c, "xs");
+  c->dz = wsp<double>(c, "dz");
+  c->pan = wsp<double>(c, "pan");
+  c->Ncand = wsp<double>(c, "Ncand");
+  c->dinvCand = wsp<double>(c, "dinvCand");
+  c->alpha_c = wsp<double>(c, "alpha_c");
+  c->alpha_r = wsp<double>(c, "alpha_r");
+  c->scal = wsp<double>(c, "scal");
+  c->status = wsp<int>(c, "status");
+  c->rhs_dev = wsp<int>(c, "rhs");
+  c->tiles_dev = wsp<int2>(c, "tiles");
+  c->panoff_dev = wsp<int64_t>(c, "panoff");
+}
+
+mcsdp_status ready(mcsdp_ctx *c) {
+  if (!c) return MCSDP_ERR_ARG;
+  if (c->host_only) return fail(c, MCSDP_ERR_STATE, "host-only context: no device work");
+  if (!c->ws) return fail(c, MCSDP_ERR_STATE, "no workspace: call mcsdp_set_workspace first");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  return MCSDP_OK;
+}
+
+mcsdp_status read_status(mcsdp_ctx *c, int *h, int count) {
+  CUDA_TRY(c, cudaMemcpyAsync(h, c->status, count * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return MCSDP_OK;
+}
+
+// ---- phases ----
+
+mcsdp_status phase_Y(mcsdp_ctx *c, const double *z) {
+  CUDA_TRY(c, cudaMemsetAsync(c->Ylay, 0, c->D.nnzL * 8, c->stream));
+  launch_slot_combine(c->D, c->Ylay, z, 1.0, -1.0, c->stream);
+  KCHECK(c);
+  return MCSDP_OK;
+}
+
+// K2 on ncand candidates Y + alpha_c dY (ncand = 1 and dY = NULL for Y itself).
+mcsdp_status phase_ychol(mcsdp_ctx *c, int ncand, const double *alpha, const double *Yb,
+                         const double *dY, double *Nbuf, double *dinv, int *status) {
+  const Symbolic &S = c->S;
+  if (ychol_smem_bytes(c->D) > 220 * 1024)
+    return fail(c, MCSDP_ERR_ARG, "supernode too large for the shared-memory Cholesky kernel");
+  for (int l = 0; l < S.height; ++l) {
+    launch_ychol_level(c->D, S.lvl_ptr[l], S.lvl_ptr[l + 1] - S.lvl_ptr[l], ncand, alpha, Yb, dY,
+                       Nbuf, dinv, status, c->stream);
+  }
+  KCHECK(c);
+  return MCSDP_OK;
+}
+
+mcsdp_status factor_Y(mcsdp_ctx *c) {
+  CUDA_TRY(c, cudaMemsetAsync(c->status, 0, 16 * sizeof(int), c->stream));
+  mcsdp_status s = phase_ychol(c, 1, nullptr, c->Ylay, nullptr, c->N, c->dinvN, c->status);
+  if (s) return s;
+  return MCSDP_OK;
+}
+
+mcsdp_status factor_X(mcsdp_ctx *c, const double *Xbar) {
+  if (alg1_smem_bytes(c->D) > 220 * 1024)
+    return fail(c, MCSDP_ERR_ARG, "clique too large for the shared-memory Algorithm 1 kernel");
+  launch_alg1(c->D, Xbar, c->Lh, c->dinvL, c->status + 1, c->stream);
+  KCHECK(c);
+  return MCSDP_OK;
+}
+
+mcsdp_status phase_scm(mcsdp_ctx *c) {
+  for (const Chunk &ch : c->chunks) {
+    launch_scm_panels(c->D, ch.g0, ch.g1, c->Lh, c->dinvL, c->N, c->dinvN, c->pan,
+                      c->panoff_dev + ch.g0, c->rhs_dev + ch.rhs_begin, ch.nrhs, c->stream);
+    KCHECK(c);
+    launch_scm_tiles(c->D, c->tiles_dev + ch.tile_begin, ch.ntiles, ch.g0, c->pan,
+                     c->panoff_dev + ch.g0, c->B, c->ldb, c->hvec, c->pmax, c->stream);
+    KCHECK(c);
+  }
+  return MCSDP_OK;
+}
+
+struct IterOut {
+  double mu, pobj, dobj, gap, pinf, ap, ad;
+};
+
+// Computes the Newton direction at (Xbar, z) into c->dz, c->dY, c->dX and the step lengths.
+// Requires Ylay/N/Lh already factored at the iterate.
+mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, float *tms) {
+  const double beta = c->opt.beta;
+  const int m = c->S.m;
+  cudaEventRecord(c->ev[0], c->stream);
+  mcsdp_status s = phase_scm(c);
+  if (s) return s;
+  cudaEventRecord(c->ev[1], c->stream);
+  launch_rhs_border(c->D, c->B, c->ldb, c->hvec, beta * mu, c->stream);
+  dense_chol_bordered(c->B, c->ldb, m, c->status + 2, c->stream);
+  dense_backsolve(c->B, c->ldb, m, c->xs, c->stream);
+  launch_dz_to_user(c->D, c->xs, c->dz, c->stream);
+  KCHECK(c);
+  cudaEventRecord(c->ev[2], c->stream);
+  CUDA_TRY(c, cudaMemsetAsync(c->dY, 0, c->D.nnzL * 8, c->stream));
+  launch_slot_combine(c->D, c->dY, c->dz, 0.0, -1.0, c->stream);
+  launch_pmatrix(c->D, c->Lh, c->dinvL, c->N, c->dinvN, c->dY, c->YinvE, c->Mlow, c->Mup, c->stream);
+  launch_dx_combine(c->D, beta * mu, Xbar, c->YinvE, c->Mlow, c->Mup, c->dX, c->stream);
+  KCHECK(c);
+  cudaEventRecord(c->ev[3], c->stream);
+  // primal step (eq. primal_length2)
+  launch_primal_step(c->D, Xbar, c->dX, c->alpha_r, c->status + 3, c->stream);
+  launch_measures(c->D, Xbar, c->Ylay, c->z, c->alpha_r, c->scal, c->stream);
+  KCHECK(c);
+  double sc[8];
+  int st[4];
+  CUDA_TRY(c, cudaMemcpyAsync(sc, c->scal, 6 * 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(st, c->status, 4 * 4, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (st[2] & ST_NOT_PD) return fail(c, MCSDP_ERR_NOT_PD, "Schur complement matrix is not positive definite");
+  o.ap = sc[5];
+  // dual step: bisection on the success of Y + alpha dY = N N^T (K2 on candidates)
+  double lo = 0.0, hi = -1.0;  // largest passing, smallest failing
+  double cand[NCAND];
+  const double first[NCAND] = {1.0, 0.9, 0.75, 0.5, 0.25, 0.1, 0.03, 0.01};
+  for (int round = 0; round < 6; ++round) {
+    if (round == 0) {
+      for (int i = 0; i < NCAND; ++i) cand[i] = first[i];
+    } else {
+      const double L = lo, H = (hi < 0 ? 1.0 : hi);
+      if (lo == 0.0 && hi > 0) {  // everything failed so far: go geometric below hi
+        for (int i = 0; i < NCAND; ++i) cand[i] = hi * std::pow(0.3, i + 1);
+      } else {
+        for (int i = 0; i < NCAND; ++i) cand[i] = L + (H - L) * (double)(i + 1) / (NCAND + 1);
+      }
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(c->alpha_c, cand, NCAND * 8, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->status + 8, 0, NCAND * sizeof(int), c->stream));
+    s = phase_ychol(c, NCAND, c->alpha_c, c->Ylay, c->dY, c->Ncand, c->dinvCand, c->status + 8);
+    if (s) return s;
+    int cs[NCAND];
+    CUDA_TRY(c, cudaMemcpyAsync(cs, c->status + 8, NCAND * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < NCAND; ++i) {
+      if (cs[i] == 0) lo = std::max(lo, cand[i]);
+      else hi = (hi < 0) ? cand[i] : std::min(hi, cand[i]);
+    }
+    if (lo >= 1.0) break;
+    if (lo > 0 && hi > 0 && (hi - lo) <= 1e-3 * lo) break;
+  }
+  if (lo <= 0.0) return fail(c, MCSDP_ERR_STALL, "dual step length collapsed");
+  o.ad = std::min(lo, 1.0);
+  cudaEventRecord(c->ev[4], c->stream);
+  if (tms) {
+    CUDA_TRY(c, cudaEventSynchronize(c->ev[4]));
+    float a, b, d, e;
+    cudaEventElapsedTime(&a, c->ev[0], c->ev[1]);
+    cudaEventElapsedTime(&b, c->ev[1], c->ev[2]);
+    cudaEventElapsedTime(&d, c->ev[2], c->ev[3]);
+    cudaEventElapsedTime(&e, c->ev[3], c->ev[4]);
+    tms[0] += a;
+    tms[1] += b;
+    tms[2] += d;
+    tms[3] += e;
+  }
+  return MCSDP_OK;
+}
+
+// Y, N, L̂ and the scalars at the current iterate (c->Xbar, c->z)
+mcsdp_status prepare(mcsdp_ctx *c, const double *Xbar, const double *z, double *scal_host) {
+  mcsdp_status s = phase_Y(c, z);
+  if (s) return s;
+  s = factor_Y(c);
+  if (s) return s;
+  s = factor_X(c, Xbar);
+  if (s) return s;
+  launch_measures(c->D, Xbar, c->Ylay, z, nullptr, c->scal, c->stream);
+  KCHECK(c);
+  int st[4];
+  if (scal_host) CUDA_TRY(c, cudaMemcpyAsync(scal_host, c->scal, 6 * 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(st, c->status, 4 * 4, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (st[0] & ST_NOT_PD) return fail(c, MCSDP_ERR_NOT_PD, "Y = A_0 - sum z_k A_k is not positive definite");
+  if (st[1] & ST_NOT_PD) return fail(c, MCSDP_ERR_NOT_PD, "a clique block of X̄ is not positive definite");
+  return MCSDP_OK;
+}
+
+mcsdp_status set_default_start(mcsdp_ctx *c) {
+  CUDA_TRY(c, cudaMemsetAsync(c->Xbar, 0, c->D.nnzL * 8, c->stream));
+  launch_set_identity(c->D, c->Xbar, c->stream);
+  KCHECK(c);
+  CUDA_TRY(c, cudaMemcpyAsync(c->z, c->z0_default.data(), (size_t)c->S.m * 8, cudaMemcpyHostToDevice,
+                              c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return MCSDP_OK;
+}
+
+}  // namespace
+
+// =============================================================================================
+extern "C" {
+
+void mcsdp_default_options(mcsdp_options *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->beta = 0.1;
+  o->gamma = 0.9;
+  o->gap_tol = 1e-7;
+  o->feas_tol = 1e-7;
+  o->max_iter = 60;
+  o->precision = 0;
+  o->timeout_cycles = 0;
+  o->device = 0;
+  o->verbose = 0;
+  o->panel_max = 80;
+  o->group_max = 64;
+  o->panel_budget_mb = 1024.0;
+}
+
+const char *mcsdp_last_error(const mcsdp_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+mcsdp_status mcsdp_create(const mcsdp_problem *p, const mcsdp_options *opt, void *stream,
+                          mcsdp_ctx **out) {
+  if (!out) return MCSDP_ERR_ARG;
+  *out = nullptr;
+  mcsdp_ctx *c = new mcsdp_ctx();
+  if (opt) c->opt = *opt;
+  else mcsdp_default_options(&c->opt);
+  *out = c;
+  if (!p) return fail(c, MCSDP_ERR_ARG, "problem is NULL");
+  if (p->n <= 0 || p->m <= 0) return fail(c, MCSDP_ERR_ARG, "n and m must be positive");
+  if (p->nnz < 0 || (p->nnz > 0 && (!p->mat || !p->row || !p->col || !p->val)))
+    return fail(c, MCSDP_ERR_ARG, "entry arrays missing");
+  if (!p->c) return fail(c, MCSDP_ERR_ARG, "c/b vector missing");
+  if (p->form != 0 && p->form != 1) return fail(c, MCSDP_ERR_ARG, "form must be 0 (SDPA) or 1 (paper)");
+  if (c->opt.precision != 0) return fail(c, MCSDP_ERR_ARG, "only precision 0 (FP64) is implemented");
+  if (c->opt.panel_max <= 0) c->opt.panel_max = 80;
+  if (c->opt.panel_max > 96) return fail(c, MCSDP_ERR_ARG, "panel_max must be <= 96");
+  if (c->opt.group_max <= 0) c->opt.group_max = 64;
+  if (c->opt.group_max > 64) return fail(c, MCSDP_ERR_ARG, "group_max must be <= 64");
+  if (!(c->opt.beta > 0 && c->opt.beta < 1) || !(c->opt.gamma > 0 && c->opt.gamma < 1))
+    return fail(c, MCSDP_ERR_ARG, "beta and gamma must lie in (0, 1)");
+  ProblemData &P = c->P;
+  P.n = p->n;
+  P.m = p->m;
+  P.b.assign(p->c, p->c + p->m);
+  std::set<std::tuple<int, int, int>> seen;
+  for (int64_t t = 0; t < p->nnz; ++t) {
+    int k = p->mat[t], i = p->row[t], j = p->col[t];
+    double v = p->val[t];
+    if (k < 0 || k > p->m || i < 0 || j < 0 || i >= p->n || j >= p->n)
+      return fail(c, MCSDP_ERR_ARG, "entry " + std::to_string(t) + ": index out of range");
+    if (i > j) return fail(c, MCSDP_ERR_ARG, "entry " + std::to_string(t) + ": row > col (give the upper triangle)");
+    if (!std::isfinite(v)) return fail(c, MCSDP_ERR_ARG, "entry " + std::to_string(t) + ": not finite");
+    if (!seen.insert({k, i, j}).second)
+      return fail(c, MCSDP_ERR_ARG, "entry " + std::to_string(t) + ": duplicate (mat,row,col)");
+    if (v == 0.0) continue;
+    if (k == 0 && p->form == 0) v = -v;  // A_0 = -F_0
+    P.mat.push_back(k);
+    P.row.push_back(i);
+    P.col.push_back(j);
+    P.val.push_back(v);
+  }
+  for (double v : P.b)
+    if (!std::isfinite(v)) return fail(c, MCSDP_ERR_ARG, "b/c not finite");
+  SymbolicOptions so;
+  so.panel_max = c->opt.panel_max;
+  so.group_max = c->opt.group_max;
+  std::string e = analyze(P, so, c->S);
+  if (!e.empty()) return fail(c, MCSDP_ERR_ARG, e);
+  // default dual start
+  c->z0_default.assign(P.m, 0.0);
+  if (c->S.unit_diag_constraints) {
+    std::vector<double> rowabs(P.n, 0.0);
+    for (size_t t = 0; t < P.row.size(); ++t)
+      if (P.mat[t] == 0) {
+        rowabs[P.row[t]] += std::fabs(P.val[t]);
+        if (P.row[t] != P.col[t]) rowabs[P.col[t]] += std::fabs(P.val[t]);
+      }
+    for (size_t t = 0; t < P.row.size(); ++t)
+      if (P.mat[t] > 0) c->z0_default[P.mat[t] - 1] = -rowabs[P.row[t]] - 1.0;
+  }
+  plan_workspace(c);
+  c->host_only = c->opt.device < 0;
+  c->stream = (cudaStream_t)stream;
+  if (!c->host_only) {
+    c->device = c->opt.device;
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    for (int i = 0; i < 8; ++i) CUDA_TRY(c, cudaEventCreate(&c->ev[i]));
+  }
+  c->err.clear();
+  return MCSDP_OK;
+}
+
+void mcsdp_destroy(mcsdp_ctx *c) {
+  if (!c) return;
+  if (!c->host_only && c->device >= 0) {
+    cudaSetDevice(c->device);
+    for (int i = 0; i < 8; ++i)
+      if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  }
+  delete c;
+}
+
+mcsdp_status mcsdp_workspace_size(const mcsdp_ctx *c, size_t *bytes) {
+  if (!c || !bytes) return MCSDP_ERR_ARG;
+  *bytes = c->ws_bytes;
+  return MCSDP_OK;
+}
+
+mcsdp_status mcsdp_set_workspace(mcsdp_ctx *c, void *ptr, size_t bytes) {
+  if (!c) return MCSDP_ERR_ARG;
+  if (c->host_only) return fail(c, MCSDP_ERR_STATE, "host-only context");
+  if (!ptr || bytes < c->ws_bytes) return fail(c, MCSDP_ERR_OOM, "workspace smaller than mcsdp_workspace_size");
+  if (((uintptr_t)ptr & 255) != 0) return fail(c, MCSDP_ERR_ARG, "workspace must be 256-byte aligned");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  c->ws = (char *)ptr;
+  c->ws_have = bytes;
+  bind_pointers(c);
+  for (const Upload &u : c->uploads)
+    CUDA_TRY(c, cudaMemcpyAsync(c->ws + u.off, u.src, u.bytes, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->B, 0, (size_t)c->ldb * c->S.m * 8, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->iterate_set = false;
+  return MCSDP_OK;
+}
+
+mcsdp_status mcsdp_sym_info_get(const mcsdp_ctx *c, mcsdp_sym_info *info) {
+  if (!c || !info) return MCSDP_ERR_ARG;
+  const Symbolic &S = c->S;
+  info->n = S.n;
+  info->m = S.m;
+  info->nsuper = S.ns;
+  info->ngroup = S.ngroup;
+  info->max_nrow = S.max_nrow;
+  info->max_ncol = S.max_ncol;
+  info->tree_height = S.height;
+  info->nnz_layout = S.ns ? S.sn_valptr[S.ns] : 0;
+  info->nnz_lower_E = S.nnz_lower_E;
+  info->nslot = S.nslot;
+  return MCSDP_OK;
+}
+
+mcsdp_status mcsdp_sym_export(const mcsdp_ctx *c, int32_t *perm, int32_t *sn_col, int64_t *sn_rowptr,
+                              int32_t *sn_rows, int64_t *sn_valptr, int32_t *con_order) {
+  if (!c) return MCSDP_ERR_ARG;
+  const Symbolic &S = c->S;
+  if (perm) std::copy(S.perm.begin(), S.perm.end(), perm);
+  if (sn_col) std::copy(S.sn_col.begin(), S.sn_col.end(), sn_col);
+  if (sn_rowptr) std::copy(S.sn_rowptr.begin(), S.sn_rowptr.end(), sn_rowptr);
+  if (sn_rows) std::copy(S.rows.begin(), S.rows.end(), sn_rows);
+  if (sn_valptr) std::copy(S.sn_valptr.begin(), S.sn_valptr.end(), sn_valptr);
+  if (con_order) std::copy(S.con_order.begin(), S.con_order.end(), con_order);
+  return MCSDP_OK;
+}
+
+mcsdp_status mcsdp_set_iterate(mcsdp_ctx *c, const double *Xbar, const double *z) {
+  mcsdp_status s = ready(c);
+  if (s) return s;
+  if (!c->iterate_set) {
+    s = set_default_start(c);
+    if (s) return s;
+  }
+  if (Xbar) CUDA_TRY(c, cudaMemcpyAsync(c->Xbar, Xbar, c->D.nnzL * 8, cudaMemcpyDeviceToDevice, c->stream));
+  if (z) CUDA_TRY(c, cudaMemcpyAsync(c->z, z, (size_t)c->S.m * 8, cudaMemcpyDeviceToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->iterate_set = true;
+  return MCSDP_OK;
+}
+
+mcsdp_status mcsdp_get_iterate(const mcsdp_ctx *cc, double *Xbar, double *z, double *Y) {
+  mcsdp_ctx *c = const_cast<mcsdp_ctx *>(cc);
+  mcsdp_status s = ready(c);
+  if (s) return s;
+  if (Xbar) CUDA_TRY(c, cudaMemcpyAsync(Xbar, c->Xbar, c->D.nnzL * 8, cudaMemcpyDeviceToDevice, c->stream));
+  if (z) CUDA_TRY(c, cudaMemcpyAsync(z, c->z, (size_t)c->S.m * 8, cudaMemcpyDeviceToDevice, c->stream));
+  if (Y) CUDA_TRY(c, cudaMemcpyAsync(Y, c->Ylay, c->D.nnzL * 8, cudaMemcpyDeviceToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return MCSDP_OK;
+}
+
+mcsdp_status mcsdp_factors(mcsdp_ctx *c, const double *Xbar, const double *z, double *Lh, double *N) {
+  mcsdp_status s = ready(c);
+  if (s) return s;
+  s = prepare(c, Xbar, z, nullptr);
+  if (s) return s;
+  if (Lh) CUDA_TRY(c, cudaMemcpyAsync(Lh, c->Lh, c->D.nnzL * 8, cudaMemcpyDeviceToDevice, c->stream));
+  if (N) CUDA_TRY(c, cudaMemcpyAsync(N, c->N, c->D.nnzL * 8, cudaMemcpyDeviceToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return MCSDP_OK;
+}
+
+mcsdp_status mcsdp_scm_assemble(mcsdp_ctx *c, const double *Xbar, const double *z, double *Bout,
+                                int64_t ldb, double *h, int32_t precision) {
+  mcsdp_status s = ready(c);
+  if (s) return s;
+  if (precision != 0) return fail(c, MCSDP_ERR_ARG, "only precision 0 (FP64) is implemented");
+  if (!Xbar || !z || !Bout || ldb < c->S.m) return fail(c, MCSDP_ERR_ARG, "bad arguments");
+  s = phase_Y(c, z);
+  if (s) return s;
+  s = factor_Y(c);
+  if (s) return s;
+  s = factor_X(c, Xbar);
+  if (s) return s;
+  s = phase_scm(c);
+  if (s) return s;
+  launch_B_to_user(c->D, c->B, c->ldb, Bout, ldb, c->hvec, h, c->stream);
+  KCHECK(c);
+  int st[4];
+  s = read_status(c, st, 4);
+  if (s) return s;
+  if (st[0] & ST_NOT_PD) return fail(c, MCSDP_ERR_NOT_PD, "Y is not positive definite");
+  if (st[1] & ST_NOT_PD) return fail(c, MCSDP_ERR_NOT_PD, "a clique block of X̄ is not positive definite");
+  return MCSDP_OK;
+}
+
+mcsdp_status mcsdp_newton_step(mcsdp_ctx *c, const double *Xbar, const double *z, double *dz,
+                               double *dX, double *dY, double *ap, double *ad, double *mu) {
+  mcsdp_status s = ready(c);
+  if (s) return s;
+  if (!Xbar || !z) return fail(c, MCSDP_ERR_ARG, "Xbar and z are required");
+  // the iterate lives in the context buffers during the step
+  CUDA_TRY(c, cudaMemcpyAsync(c->z, z, (size_t)c->S.m * 8, cudaMemcpyDeviceToDevice, c->stream));
+  double sc[8];
+  s = prepare(c, Xbar, c->z, sc);
+  if (s) return s;
+  const double muv = sc[0] / c->S.n;
+  IterOut o{};
+  s = direction(c, Xbar, muv, o, nullptr);
+  if (s) return s;
+  if (dz) CUDA_TRY(c, cudaMemcpyAsync(dz, c->dz, (size_t)c->S.m * 8, cudaMemcpyDeviceToDevice, c->stream));
+  if (dX) CUDA_TRY(c, cudaMemcpyAsync(dX, c->dX, c->D.nnzL * 8, cudaMemcpyDeviceToDevice, c->stream));
+  if (dY) CUDA_TRY(c, cudaMemcpyAsync(dY, c->dY, c->D.nnzL * 8, cudaMemcpyDeviceToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (ap) *ap = o.ap;
+  if (ad) *ad = o.ad;
+  if (mu) *mu = muv;
+  return MCSDP_OK;
+}
+
+mcsdp_status mcsdp_solve(mcsdp_ctx *c, mcsdp_result *res) {
+  mcsdp_status s = ready(c);
+  if (s) return s;
+  if (!c->iterate_set) {
+    s = set_default_start(c);
+    if (s) return s;
+    c->iterate_set = true;
+  }
+  mcsdp_result r{};
+  float tms[4] = {0, 0, 0, 0};
+  cudaEvent_t t0 = c->ev[6], t1 = c->ev[7];
+  cudaEventRecord(t0, c->stream);
+  const int n = c->S.n;
+  mcsdp_status final_status = MCSDP_ERR_MAXITER;
+  for (int it = 0; it <= c->opt.max_iter; ++it) {
+    double sc[8];
+    s = prepare(c, c->Xbar, c->z, sc);
+    if (s) {
+      if (it == 0 && s == MCSDP_ERR_NOT_PD && c->err.find("Y =") != std::string::npos)
+        c->err += " at the start: give a dual-feasible z with mcsdp_set_iterate";
+      return s;
+    }
+    const double mu = sc[0] / n, pobj = sc[1], dobj = sc[2];
+    const double gap = std::fabs(pobj - dobj) / std::max(1.0, (std::fabs(pobj) + std::fabs(dobj)) / 2);
+    const double pinf = sc[3] / std::max(1.0, sc[4]);
+    r.pobj = pobj;
+    r.dobj = dobj;
+    r.gap = gap;
+    r.pinf = pinf;
+    r.dinf = 0.0;
+    r.mu = mu;
+    r.iters = it;
+    if (!std::isfinite(pobj) || !std::isfinite(dobj) || !std::isfinite(mu)) {
+      final_status = MCSDP_ERR_NUMERIC;
+      c->err = "NaN/Inf in the iterate";
+      break;
+    }
+    if (gap <= c->opt.gap_tol && pinf <= c->opt.feas_tol) {
+      final_status = MCSDP_OK;
+      break;
+    }
+    if (it == c->opt.max_iter) break;
+    IterOut o{};
+    s = direction(c, c->Xbar, mu, o, tms);
+    if (s) {
+      final_status = s;
+      break;
+    }
+    if (c->opt.verbose)
+      std::fprintf(stderr, "it %3d pobj %+.10e dobj %+.10e gap %.2e pinf %.2e mu %.2e ap %.3f ad %.3f\n",
+                   it, pobj, dobj, gap, pinf, mu, o.ap, o.ad);
+    launch_update(c->D, c->Xbar, c->dX, c->opt.gamma * o.ap, c->z, c->dz, c->opt.gamma * o.ad, c->stream);
+    KCHECK(c);
+  }
+  cudaEventRecord(t1, c->stream);
+  CUDA_TRY(c, cudaEventSynchronize(t1));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, t0, t1);
+  r.seconds = ms * 1e-3;
+  r.t_scm = tms[0] * 1e-3;
+  r.t_chol = tms[1] * 1e-3;
+  r.t_pmat = tms[2] * 1e-3;
+  r.t_other = r.seconds - r.t_scm - r.t_chol - r.t_pmat;
+  r.status = final_status;
+  if (res) *res = r;
+  return final_status;
+}
+
+mcsdp_status mcsdp_backward(mcsdp_ctx *c, const double *, const double *, double *, double *, double *) {
+  return fail(c, MCSDP_ERR_STATE, "mcsdp_backward (differentiation of the solution) is not implemented");
+}
+
+}  // extern "C"

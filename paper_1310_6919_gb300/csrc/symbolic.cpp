@@ -1,0 +1,427 @@
+// Host symbolic analysis (Sec. 2.1 "permute ... generate a chordal graph ... extract cliques",
+// Sec. 3.1 "row/column sets of CHOLMOD supernodes have the running intersection property").
+// Everything here is integer work done once before the main loop.
+#include "symbolic.h"
+
+#include <algorithm>
+#include <array>
+#include <map>
+#include <numeric>
+#include <set>
+#include <sstream>
+
+namespace mcsdp {
+namespace {
+
+// Exact minimum-degree ordering on the elimination graph (ties: smallest caller index).
+// Returns the elimination order and, for each step, the neighbours at elimination time
+// (= the row structure of that column of the Cholesky factor).
+void min_degree(int n, std::vector<std::vector<int>> adj, std::vector<int> &order,
+                std::vector<std::vector<int>> &elim_struct) {
+  std::set<std::pair<int, int>> pq;
+  std::vector<char> done(n, 0);
+  for (int v = 0; v < n; ++v) pq.insert({(int)adj[v].size(), v});
+  order.clear();
+  elim_struct.assign(n, {});
+  std::vector<int> tmp;
+  while (!pq.empty()) {
+    int v = pq.begin()->second;
+    pq.erase(pq.begin());
+    done[v] = 1;
+    std::vector<int> N = adj[v];  // all live
+    order.push_back(v);
+    elim_struct[v] = N;
+    for (int u : N) {
+      pq.erase({(int)adj[u].size(), u});
+      // adj[u] := (adj[u] ∪ N) \ {u, v}
+      tmp.clear();
+      const auto &a = adj[u];
+      size_t i = 0, j = 0;
+      while (i < a.size() || j < N.size()) {
+        int x;
+        if (j >= N.size() || (i < a.size() && a[i] < N[j])) x = a[i++];
+        else if (i >= a.size() || N[j] < a[i]) x = N[j++];
+        else { x = a[i]; ++i; ++j; }
+        if (x != u && x != v) tmp.push_back(x);
+      }
+      adj[u].swap(tmp);
+      pq.insert({(int)adj[u].size(), u});
+    }
+    adj[v].clear();
+  }
+}
+
+}  // namespace
+
+std::string analyze(const ProblemData &P, const SymbolicOptions &o, Symbolic &S) {
+  const int n = P.n, m = P.m;
+  S = Symbolic();
+  S.n = n;
+  S.m = m;
+  // ---- aggregate sparsity pattern (Sec. 1) ----
+  std::vector<std::vector<int>> adj(n);
+  {
+    std::vector<std::pair<int, int>> e;
+    e.reserve(P.row.size() * 2);
+    for (size_t t = 0; t < P.row.size(); ++t) {
+      int i = P.row[t], j = P.col[t];
+      if (i != j) { e.push_back({i, j}); e.push_back({j, i}); }
+    }
+    std::sort(e.begin(), e.end());
+    e.erase(std::unique(e.begin(), e.end()), e.end());
+    for (auto &p : e) adj[p.first].push_back(p.second);
+  }
+  // ---- ordering + filled structure ----
+  std::vector<int> order;
+  std::vector<std::vector<int>> est;
+  min_degree(n, adj, order, est);
+  std::vector<int> pos(n);
+  for (int p = 0; p < n; ++p) pos[order[p]] = p;
+  std::vector<std::vector<int>> st(n);  // struct in elimination positions
+  std::vector<int> parent(n, -1);
+  for (int p = 0; p < n; ++p) {
+    auto &s = st[p];
+    for (int u : est[order[p]]) s.push_back(pos[u]);
+    std::sort(s.begin(), s.end());
+    if (!s.empty()) parent[p] = s[0];
+  }
+  // ---- postorder of the elimination tree ----
+  std::vector<std::vector<int>> kids(n);
+  for (int p = 0; p < n; ++p)
+    if (parent[p] >= 0) kids[parent[p]].push_back(p);
+  std::vector<int> post(n, -1);
+  {
+    int cnt = 0;
+    std::vector<std::pair<int, size_t>> stack;
+    for (int r = 0; r < n; ++r) {
+      if (parent[r] >= 0) continue;
+      stack.push_back({r, 0});
+      while (!stack.empty()) {
+        auto &top = stack.back();
+        if (top.second < kids[top.first].size()) {
+          int c = kids[top.first][top.second++];
+          stack.push_back({c, 0});
+        } else {
+          post[top.first] = cnt++;
+          stack.pop_back();
+        }
+      }
+    }
+  }
+  S.perm.assign(n, 0);
+  S.iperm.assign(n, 0);
+  std::vector<std::vector<int>> sn_struct(n);  // struct in new indices
+  std::vector<int> par(n, -1);
+  for (int p = 0; p < n; ++p) {
+    int q = post[p];
+    S.perm[q] = order[p];
+    S.iperm[order[p]] = q;
+    auto &s = sn_struct[q];
+    for (int x : st[p]) s.push_back(post[x]);
+    std::sort(s.begin(), s.end());
+    par[q] = parent[p] >= 0 ? post[parent[p]] : -1;
+  }
+  // ---- fundamental supernodes ----
+  std::vector<int> nchild(n, 0);
+  for (int q = 0; q < n; ++q)
+    if (par[q] >= 0) nchild[par[q]]++;
+  S.sn_col.push_back(0);
+  for (int q = 0; q < n;) {
+    int v = q;
+    while (v + 1 < n && par[v] == v + 1 && nchild[v + 1] == 1 &&
+           sn_struct[v].size() == sn_struct[v + 1].size() + 1)
+      ++v;
+    S.sn_col.push_back(v + 1);
+    q = v + 1;
+  }
+  S.ns = (int)S.sn_col.size() - 1;
+  S.col2sn.assign(n, 0);
+  S.sn_rowptr.assign(S.ns + 1, 0);
+  S.sn_valptr.assign(S.ns + 1, 0);
+  for (int s = 0; s < S.ns; ++s) {
+    int c0 = S.sn_col[s], c1 = S.sn_col[s + 1];
+    for (int c = c0; c < c1; ++c) S.col2sn[c] = s;
+    for (int c = c0; c < c1; ++c) S.rows.push_back(c);
+    for (int x : sn_struct[c1 - 1]) S.rows.push_back(x);
+    int nrow = (c1 - c0) + (int)sn_struct[c1 - 1].size();
+    int ncol = c1 - c0;
+    S.sn_rowptr[s + 1] = S.sn_rowptr[s] + nrow;
+    S.sn_valptr[s + 1] = S.sn_valptr[s] + (int64_t)nrow * ncol;
+    S.max_nrow = std::max(S.max_nrow, nrow);
+    S.max_ncol = std::max(S.max_ncol, ncol);
+    S.nnz_lower_E += (int64_t)nrow * ncol - (int64_t)ncol * (ncol - 1) / 2;
+  }
+  S.sn_parent.assign(S.ns, -1);
+  for (int s = 0; s < S.ns; ++s) {
+    int nrow = (int)(S.sn_rowptr[s + 1] - S.sn_rowptr[s]);
+    int ncol = S.sn_col[s + 1] - S.sn_col[s];
+    if (nrow > ncol) S.sn_parent[s] = S.col2sn[S.rows[S.sn_rowptr[s] + ncol]];
+  }
+  // ---- height levels ----
+  {
+    std::vector<int> h(S.ns, 0);
+    for (int s = 0; s < S.ns; ++s)  // children precede parents
+      if (S.sn_parent[s] >= 0) h[S.sn_parent[s]] = std::max(h[S.sn_parent[s]], h[s] + 1);
+    S.height = S.ns ? *std::max_element(h.begin(), h.end()) + 1 : 0;
+    S.lvl_ptr.assign(S.height + 1, 0);
+    for (int s = 0; s < S.ns; ++s) S.lvl_ptr[h[s] + 1]++;
+    for (int l = 0; l < S.height; ++l) S.lvl_ptr[l + 1] += S.lvl_ptr[l];
+    S.lvl_sn.assign(S.ns, 0);
+    std::vector<int> fill(S.lvl_ptr.begin(), S.lvl_ptr.end() - 1);
+    for (int s = 0; s < S.ns; ++s) S.lvl_sn[fill[h[s]]++] = s;
+  }
+  // ---- left-looking update lists ----
+  {
+    std::vector<std::vector<std::array<int, 3>>> lists(S.ns);  // (src, p1, p2)
+    for (int s = 0; s < S.ns; ++s) {
+      int64_t r0 = S.sn_rowptr[s];
+      int nrow = (int)(S.sn_rowptr[s + 1] - r0);
+      int ncol = S.sn_col[s + 1] - S.sn_col[s];
+      int p = ncol;
+      while (p < nrow) {
+        int t = S.col2sn[S.rows[r0 + p]];
+        int q = p;
+        while (q < nrow && S.rows[r0 + q] < S.sn_col[t + 1]) ++q;
+        lists[t].push_back({s, p, q});
+        p = q;
+      }
+    }
+    S.upd_ptr.assign(S.ns + 1, 0);
+    S.upd_relptr.push_back(0);
+    for (int t = 0; t < S.ns; ++t) {
+      int64_t tr0 = S.sn_rowptr[t];
+      int tnrow = (int)(S.sn_rowptr[t + 1] - tr0);
+      for (auto &e : lists[t]) {
+        int s = e[0];
+        S.upd_src.push_back(s);
+        S.upd_p1.push_back(e[1]);
+        S.upd_p2.push_back(e[2]);
+        int64_t r0 = S.sn_rowptr[s];
+        int nrow = (int)(S.sn_rowptr[s + 1] - r0);
+        int k = 0;
+        for (int p = e[1]; p < nrow; ++p) {
+          int r = S.rows[r0 + p];
+          while (k < tnrow && S.rows[tr0 + k] < r) ++k;
+          if (k >= tnrow || S.rows[tr0 + k] != r) return "internal: update rows not in target clique";
+          S.upd_rel.push_back(k);
+        }
+        S.upd_relptr.push_back((int64_t)S.upd_rel.size());
+      }
+      S.upd_ptr[t + 1] = (int)S.upd_src.size();
+    }
+  }
+  // ---- layout offset of a lower position (new indices r >= c) ----
+  auto layout_off = [&](int r, int c) -> int64_t {
+    int s = S.col2sn[c];
+    int64_t r0 = S.sn_rowptr[s];
+    int nrow = (int)(S.sn_rowptr[s + 1] - r0);
+    const int *b = S.rows.data() + r0;
+    const int *it = std::lower_bound(b, b + nrow, r);
+    if (it == b + nrow || *it != r) return -1;
+    return S.sn_valptr[s] + (int64_t)(it - b) + (int64_t)(c - S.sn_col[s]) * nrow;
+  };
+  // ---- aggregate-pattern slots ----
+  {
+    size_t ne = P.row.size();
+    std::vector<int64_t> off(ne);
+    for (size_t t = 0; t < ne; ++t) {
+      int p = S.iperm[P.row[t]], q = S.iperm[P.col[t]];
+      int r = std::max(p, q), c = std::min(p, q);
+      off[t] = layout_off(r, c);
+      if (off[t] < 0) return "internal: aggregate entry not covered by E";
+    }
+    std::vector<size_t> idx(ne);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::sort(idx.begin(), idx.end(), [&](size_t a, size_t b) {
+      return off[a] != off[b] ? off[a] < off[b] : P.mat[a] < P.mat[b];
+    });
+    S.slot_ptr.push_back(0);
+    for (size_t u = 0; u < ne;) {
+      size_t v = u;
+      double a0 = 0.0;
+      while (v < ne && off[idx[v]] == off[idx[u]]) {
+        size_t t = idx[v];
+        S.slot_k.push_back(P.mat[t]);
+        S.slot_val.push_back(P.val[t]);
+        if (P.mat[t] == 0) a0 += P.val[t];
+        ++v;
+      }
+      size_t t = idx[u];
+      int p = S.iperm[P.row[t]], q = S.iperm[P.col[t]];
+      S.slot_i.push_back(std::max(p, q));
+      S.slot_j.push_back(std::min(p, q));
+      S.slot_off.push_back(off[t]);
+      S.slot_a0.push_back(a0);
+      S.slot_ptr.push_back((int)S.slot_k.size());
+      u = v;
+    }
+    S.nslot = (int64_t)S.slot_off.size();
+    // constraint lists
+    std::vector<std::vector<std::pair<int64_t, double>>> cl(m);
+    for (size_t t = 0; t < ne; ++t) {
+      if (P.mat[t] == 0) continue;
+      double w = P.row[t] == P.col[t] ? P.val[t] : 2.0 * P.val[t];
+      cl[P.mat[t] - 1].push_back({off[t], w});
+    }
+    S.con_ptr.assign(m + 1, 0);
+    for (int k = 0; k < m; ++k) {
+      std::sort(cl[k].begin(), cl[k].end());
+      for (auto &e : cl[k]) { S.con_off.push_back(e.first); S.con_w.push_back(e.second); }
+      S.con_ptr[k + 1] = (int)S.con_off.size();
+    }
+    // symmetric row lists over slots
+    std::vector<std::vector<std::pair<int, int64_t>>> rl(n);
+    for (int64_t s = 0; s < S.nslot; ++s) {
+      rl[S.slot_i[s]].push_back({S.slot_j[s], S.slot_off[s]});
+      if (S.slot_i[s] != S.slot_j[s]) rl[S.slot_j[s]].push_back({S.slot_i[s], S.slot_off[s]});
+    }
+    S.arow_ptr.assign(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+      std::sort(rl[i].begin(), rl[i].end());
+      for (auto &e : rl[i]) { S.arow_col.push_back(e.first); S.arow_off.push_back(e.second); }
+      S.arow_ptr[i + 1] = (int)S.arow_col.size();
+    }
+  }
+  // ---- strict-lower row structures ----
+  {
+    std::vector<int> cnt(n + 1, 0);
+    for (int s = 0; s < S.ns; ++s) {
+      int64_t r0 = S.sn_rowptr[s];
+      int nrow = (int)(S.sn_rowptr[s + 1] - r0), c0 = S.sn_col[s], ncol = S.sn_col[s + 1] - c0;
+      for (int lc = 0; lc < ncol; ++lc)
+        for (int p = lc + 1; p < nrow; ++p) cnt[S.rows[r0 + p] + 1]++;
+    }
+    for (int i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+    S.rs_ptr = cnt;
+    S.rs_col.assign(cnt[n], 0);
+    S.rs_off.assign(cnt[n], 0);
+    std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+    for (int s = 0; s < S.ns; ++s) {
+      int64_t r0 = S.sn_rowptr[s];
+      int nrow = (int)(S.sn_rowptr[s + 1] - r0), c0 = S.sn_col[s], ncol = S.sn_col[s + 1] - c0;
+      for (int lc = 0; lc < ncol; ++lc)
+        for (int p = lc + 1; p < nrow; ++p) {
+          int r = S.rows[r0 + p];
+          int at = fill[r]++;
+          S.rs_col[at] = c0 + lc;
+          S.rs_off[at] = S.sn_valptr[s] + p + (int64_t)lc * nrow;
+        }
+    }
+  }
+  // ---- SCM groups ----
+  {
+    std::vector<std::vector<int>> supp(m);
+    S.unit_diag_constraints = true;
+    for (size_t t = 0; t < P.row.size(); ++t) {
+      if (P.mat[t] == 0) continue;
+      int k = P.mat[t] - 1;
+      supp[k].push_back(S.iperm[P.row[t]]);
+      supp[k].push_back(S.iperm[P.col[t]]);
+    }
+    std::vector<int> cnt_entries(m, 0);
+    for (size_t t = 0; t < P.row.size(); ++t) {
+      if (P.mat[t] == 0) continue;
+      int k = P.mat[t] - 1;
+      cnt_entries[k]++;
+      if (P.row[t] != P.col[t] || P.row[t] != k || P.val[t] != 1.0) S.unit_diag_constraints = false;
+    }
+    for (int k = 0; k < m; ++k) {
+      if (cnt_entries[k] != 1) S.unit_diag_constraints = false;
+      auto &s = supp[k];
+      std::sort(s.begin(), s.end());
+      s.erase(std::unique(s.begin(), s.end()), s.end());
+      if (s.empty()) return "constraint matrix A_" + std::to_string(k + 1) + " is empty";
+      if ((int)s.size() > o.panel_max)
+        return "constraint A_" + std::to_string(k + 1) + " touches " + std::to_string(s.size()) +
+               " rows/columns; the SCM panel limit is " + std::to_string(o.panel_max);
+    }
+    std::vector<int> ord(m);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) {
+      if (supp[a][0] != supp[b][0]) return supp[a][0] < supp[b][0];
+      return a < b;
+    });
+    S.con_order = ord;
+    S.con_internal.assign(m, 0);
+    for (int i = 0; i < m; ++i) S.con_internal[ord[i]] = i;
+    S.grp_cptr.push_back(0);
+    S.grp_pptr.push_back(0);
+    std::vector<int> U, tmp;
+    int gstart = 0;
+    auto close_group = [&](int end) {
+      S.grp_cptr.push_back(end);
+      for (int x : U) S.grp_cols.push_back(x);
+      S.grp_pptr.push_back((int)S.grp_cols.size());
+      U.clear();
+      gstart = end;
+    };
+    for (int i = 0; i < m; ++i) {
+      const auto &s = supp[ord[i]];
+      tmp.clear();
+      std::set_union(U.begin(), U.end(), s.begin(), s.end(), std::back_inserter(tmp));
+      if (i > gstart && ((int)tmp.size() > o.panel_max || i - gstart >= o.group_max)) {
+        close_group(i);
+        U = s;
+      } else {
+        U.swap(tmp);
+      }
+    }
+    close_group(m);
+    S.ngroup = (int)S.grp_cptr.size() - 1;
+    S.grp_rowoff.assign(S.ngroup + 1, 0);
+    for (int g = 0; g < S.ngroup; ++g)
+      S.grp_rowoff[g + 1] = S.grp_rowoff[g] + (S.grp_pptr[g + 1] - S.grp_pptr[g]);
+    // local nonzero lists per internal constraint (both triangles)
+    std::vector<std::vector<std::array<double, 3>>> loc(m);
+    std::vector<int> grp_of(m);
+    for (int g = 0; g < S.ngroup; ++g)
+      for (int i = S.grp_cptr[g]; i < S.grp_cptr[g + 1]; ++i) grp_of[i] = g;
+    for (size_t t = 0; t < P.row.size(); ++t) {
+      if (P.mat[t] == 0) continue;
+      int i = S.con_internal[P.mat[t] - 1];
+      int g = grp_of[i];
+      const int *pb = S.grp_cols.data() + S.grp_pptr[g];
+      const int *pe = S.grp_cols.data() + S.grp_pptr[g + 1];
+      int a = (int)(std::lower_bound(pb, pe, S.iperm[P.row[t]]) - pb);
+      int b = (int)(std::lower_bound(pb, pe, S.iperm[P.col[t]]) - pb);
+      loc[i].push_back({(double)a, (double)b, P.val[t]});
+      if (a != b) loc[i].push_back({(double)b, (double)a, P.val[t]});
+    }
+    S.anz_ptr.assign(m + 1, 0);
+    for (int i = 0; i < m; ++i) {
+      for (auto &e : loc[i]) {
+        S.anz_a.push_back((int16_t)e[0]);
+        S.anz_b.push_back((int16_t)e[1]);
+        S.anz_v.push_back(e[2]);
+      }
+      S.anz_ptr[i + 1] = (int)S.anz_v.size();
+    }
+    // reach (forward) and need (backward) supernode lists per group
+    std::vector<char> mark(S.ns, 0);
+    S.reach_ptr.push_back(0);
+    for (int g = 0; g < S.ngroup; ++g) {
+      std::fill(mark.begin(), mark.end(), 0);
+      for (int p = S.grp_pptr[g]; p < S.grp_pptr[g + 1]; ++p)
+        for (int s = S.col2sn[S.grp_cols[p]]; s >= 0 && !mark[s]; s = S.sn_parent[s]) mark[s] = 1;
+      for (int s = 0; s < S.ns; ++s)
+        if (mark[s]) S.reach_sn.push_back(s);
+      S.reach_ptr.push_back((int64_t)S.reach_sn.size());
+    }
+    std::vector<std::vector<int>> need(S.ngroup);
+    std::fill(mark.begin(), mark.end(), 0);
+    for (int g = S.ngroup - 1; g >= 0; --g) {
+      for (int p = S.grp_pptr[g]; p < S.grp_pptr[g + 1]; ++p)
+        for (int s = S.col2sn[S.grp_cols[p]]; s >= 0 && !mark[s]; s = S.sn_parent[s]) mark[s] = 1;
+      for (int s = 0; s < S.ns; ++s)
+        if (mark[s]) need[g].push_back(s);
+    }
+    S.need_ptr.push_back(0);
+    for (int g = 0; g < S.ngroup; ++g) {
+      for (int s : need[g]) S.need_sn.push_back(s);
+      S.need_ptr.push_back((int64_t)S.need_sn.size());
+    }
+  }
+  return "";
+}
+
+}  // namespace mcsdp

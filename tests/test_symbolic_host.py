@@ -1,0 +1,99 @@
+"""Host-side tests of libmcsdp (no GPU): the library loads, exports every symbol of
+include/mcsdp.h, validates input, and its symbolic analysis yields a clique tree that the oracle's
+checks accept (PEO, E ⊇ aggregate pattern, running intersection property)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from instances import (lattice_maxcut, block_arrow, random_gnm_maxcut, small_random_sdp,
+                       cycle_maxcut)
+from oracle.chordal import (cliques_from_supernodes, check_structure, pattern_from_cliques,
+                            is_perfect_elimination, covers)
+from oracle.sdp import SparseSym
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1310_6919_gb300 import build_library, _lib
+    build_library()
+    return _lib.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    hdr = open(os.path.join(ROOT, "include", "mcsdp.h")).read()
+    declared = set(re.findall(r"\b(mcsdp_[a-z_]+)\s*\(", hdr))
+    assert len(declared) >= 14
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def _problem(inst, **kw):
+    from paper_1310_6919_gb300 import Problem
+    return Problem.from_instance(inst, device=-1, **kw)
+
+
+@pytest.mark.parametrize("inst", [lattice_maxcut(10, 10), lattice_maxcut(6, 5, seed=3),
+                                  block_arrow(6, 12, 4, 60, seed=5), random_gnm_maxcut(60, 150, 4),
+                                  small_random_sdp(9, 12, 2), cycle_maxcut(17)],
+                         ids=lambda i: i.name)
+def test_symbolic_structure_is_valid(inst):
+    P = _problem(inst)
+    s = P.sym_export()
+    n = inst.n
+    cl = cliques_from_supernodes(s["sn_col"], s["sn_rowptr"], s["sn_rows"])
+    check_structure(n, cl)
+    E = pattern_from_cliques(n, cl)
+    assert is_perfect_elimination(E)
+    A = SparseSym.from_instance(inst)
+    assert covers(E, s["perm"], A.aggregate_pattern())
+    assert sorted(s["perm"].tolist()) == list(range(n))
+    assert sorted(s["con_order"].tolist()) == list(range(inst.m))
+    info = P.info
+    assert info["nnz_layout"] == int(s["sn_valptr"][-1])
+    assert info["nnz_lower_E"] == int(np.tril(E).sum())
+
+
+def test_host_only_context_refuses_device_work():
+    from paper_1310_6919_gb300 import MCSDPError
+    P = _problem(lattice_maxcut(4, 4))
+    with pytest.raises(MCSDPError) as e:
+        P.solve()
+    assert "ERR_STATE" in str(e.value)
+
+
+def _raw_create(lib, n, m, b, mat, row, col, val):
+    from paper_1310_6919_gb300 import _lib
+    b = np.asarray(b, np.float64)
+    arrs = [np.asarray(a, np.int32) for a in (mat, row, col)]
+    v = np.asarray(val, np.float64)
+    prob = _lib.Problem_t(n, m, 1, b.ctypes.data_as(C.POINTER(C.c_double)), len(v),
+                          *[a.ctypes.data_as(C.POINTER(C.c_int32)) for a in arrs],
+                          v.ctypes.data_as(C.POINTER(C.c_double)))
+    opt = _lib.Options_t()
+    lib.mcsdp_default_options(C.byref(opt))
+    opt.device = -1
+    ctx = C.c_void_p()
+    st = lib.mcsdp_create(C.byref(prob), C.byref(opt), None, C.byref(ctx))
+    msg = lib.mcsdp_last_error(ctx).decode()
+    lib.mcsdp_destroy(ctx)
+    return st, msg
+
+
+def test_input_validation(lib):
+    ok = ([0, 1, 1], [0, 0, 1], [1, 0, 1], [1.0, 1.0, 1.0])
+    assert _raw_create(lib, 2, 1, [1.0], *ok)[0] == 0
+    st, msg = _raw_create(lib, 2, 1, [1.0], [0, 1, 1], [1, 0, 0], [0, 0, 0], [1.0, 1.0, 1.0])
+    assert st == 1 and "row > col" in msg
+    st, msg = _raw_create(lib, 2, 1, [1.0], [0, 1, 1], [0, 0, 0], [0, 0, 0], [1.0, 1.0, 2.0])
+    assert st == 1 and "duplicate" in msg
+    st, msg = _raw_create(lib, 2, 1, [1.0], [0, 3], [0, 0], [0, 0], [1.0, 1.0])
+    assert st == 1 and "out of range" in msg
+    st, msg = _raw_create(lib, 0, 1, [1.0], [0], [0], [0], [1.0])
+    assert st == 1
+    st, msg = _raw_create(lib, 2, 1, [np.nan], *ok)
+    assert st == 1
