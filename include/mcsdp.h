@@ -80,6 +80,7 @@ typedef struct {
   int32_t panel_max;     /* max columns per SCM panel group (<= 96); 0 = default 80 */
   int32_t group_max;     /* max constraints per SCM group (<= 64); 0 = default 64 */
   double panel_budget_mb;/* bound on the SCM panel buffers; 0 = default 1024 MB */
+  int32_t profile;       /* 1 = time every kernel class with CUDA events (mcsdp_stats_get) */
 } mcsdp_options;
 
 void mcsdp_default_options(mcsdp_options *opt);
@@ -106,6 +107,7 @@ typedef struct {
   int64_t nnz_layout;   /* stored values per layout array */
   int64_t nnz_lower_E;  /* entries of lower(E) including the diagonal */
   int64_t nslot;        /* distinct lower positions of the aggregate pattern */
+  int64_t table_bytes;  /* bytes of symbolic tables mcsdp_set_workspace copies host -> device */
 } mcsdp_sym_info;
 mcsdp_status mcsdp_sym_info_get(const mcsdp_ctx *ctx, mcsdp_sym_info *info);
 
@@ -158,6 +160,32 @@ mcsdp_status mcsdp_newton_step(mcsdp_ctx *ctx, const double *Xbar_layout_dev, co
 /* Factors at the iterate: L̂ (Algorithm 1) and N (Y = N N^T) in the layout (device). */
 mcsdp_status mcsdp_factors(mcsdp_ctx *ctx, const double *Xbar_layout_dev, const double *z_dev,
                            double *Lhat_layout_dev, double *N_layout_dev);
+
+/* Kernel statistics of the context since creation or the last reset: the number of kernel
+ * launches the library issued (always counted) and, when options.profile = 1, the device time of
+ * each kernel class measured with CUDA events recorded on the context's stream around the
+ * launches of that class.  Classes: 0 K2 Y=NN^T, 1 K1 Algorithm 1, 2 SCM panel solves,
+ * 3 SCM tile contraction, 4 SCM Cholesky (potrf/trsm/syrk), 5 SCE back substitution,
+ * 6 P-MATRIX, 7 primal step length, 8 dual step length (candidate factorisations),
+ * 9 other (pattern scatter, scalars, update). */
+#define MCSDP_NCLASS 10
+typedef struct {
+  int64_t launches;
+  int64_t count[16];   /* launches per class */
+  double ms[16];       /* device milliseconds per class (profile = 1 only) */
+} mcsdp_stats;
+mcsdp_status mcsdp_stats_get(const mcsdp_ctx *ctx, mcsdp_stats *st);
+
+/* Algorithmic work of one PDIPM iteration per kernel class (same class numbering as
+ * mcsdp_stats): FP64 flops (one multiply-add = 2) that the method needs for the context's
+ * structure, and the minimum DRAM bytes (each operand read once, each result written once).
+ * For class 8 (dual step) the figures are per candidate factorisation. */
+typedef struct {
+  double flops[16];
+  double bytes[16];
+} mcsdp_work;
+mcsdp_status mcsdp_work_model(const mcsdp_ctx *ctx, mcsdp_work *w);
+mcsdp_status mcsdp_stats_reset(mcsdp_ctx *ctx);
 
 /* Differentiation of the solution (implicit differentiation of the central-path KKT system).
  * Not implemented: returns MCSDP_ERR_STATE. */

@@ -18,14 +18,26 @@ class Options_t(C.Structure):
                 ("feas_tol", C.c_double), ("max_iter", C.c_int32), ("precision", C.c_int32),
                 ("timeout_cycles", C.c_int64), ("device", C.c_int32), ("verbose", C.c_int32),
                 ("panel_max", C.c_int32), ("group_max", C.c_int32),
-                ("panel_budget_mb", C.c_double)]
+                ("panel_budget_mb", C.c_double), ("profile", C.c_int32)]
+
+
+class Work_t(C.Structure):
+    _fields_ = [("flops", C.c_double * 16), ("bytes", C.c_double * 16)]
+
+
+class Stats_t(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("count", C.c_int64 * 16), ("ms", C.c_double * 16)]
+
+
+KCLASS = ["ychol", "alg1", "scm_panel", "scm_tile", "scm_chol", "sce_backsolve", "pmatrix",
+          "primal_step", "dual_step", "other"]
 
 
 class SymInfo_t(C.Structure):
     _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("nsuper", C.c_int32),
                 ("ngroup", C.c_int32), ("max_nrow", C.c_int32), ("max_ncol", C.c_int32),
                 ("tree_height", C.c_int32), ("nnz_layout", C.c_int64),
-                ("nnz_lower_E", C.c_int64), ("nslot", C.c_int64)]
+                ("nnz_lower_E", C.c_int64), ("nslot", C.c_int64), ("table_bytes", C.c_int64)]
 
 
 class Result_t(C.Structure):
@@ -42,7 +54,8 @@ STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_NOT_PD", 3: "ERR_MAXITER", 4: "ERR_STAL
 EXPORTED = ["mcsdp_default_options", "mcsdp_create", "mcsdp_destroy", "mcsdp_last_error",
             "mcsdp_workspace_size", "mcsdp_set_workspace", "mcsdp_sym_info_get",
             "mcsdp_sym_export", "mcsdp_solve", "mcsdp_set_iterate", "mcsdp_get_iterate",
-            "mcsdp_scm_assemble", "mcsdp_newton_step", "mcsdp_factors", "mcsdp_backward"]
+            "mcsdp_scm_assemble", "mcsdp_newton_step", "mcsdp_factors", "mcsdp_backward",
+            "mcsdp_stats_get", "mcsdp_stats_reset", "mcsdp_work_model"]
 
 _lib = None
 
@@ -77,6 +90,9 @@ def load():
     L.mcsdp_newton_step.argtypes = [P, V, V, V, V, V, dp, dp, dp]
     L.mcsdp_factors.argtypes = [P, V, V, V, V]
     L.mcsdp_backward.argtypes = [P, V, V, V, V, V]
+    L.mcsdp_stats_get.argtypes = [P, C.POINTER(Stats_t)]
+    L.mcsdp_stats_reset.argtypes = [P]
+    L.mcsdp_work_model.argtypes = [P, C.POINTER(Work_t)]
     for f in EXPORTED:
         if getattr(L, f).restype is C.c_int or f not in ("mcsdp_default_options", "mcsdp_destroy",
                                                            "mcsdp_last_error"):

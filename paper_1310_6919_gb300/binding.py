@@ -179,6 +179,27 @@ class Problem:
                                               _ptr(dY), C.byref(ap), C.byref(ad), C.byref(mu)))
         return dict(dz=dz, dX=dX, dY=dY, alpha_p=ap.value, alpha_d=ad.value, mu=mu.value)
 
+    def stats(self):
+        st = _lib.Stats_t()
+        self._check(self._L.mcsdp_stats_get(self._ctx, C.byref(st)))
+        return dict(launches=st.launches,
+                    count={k: st.count[i] for i, k in enumerate(_lib.KCLASS)},
+                    ms={k: st.ms[i] for i, k in enumerate(_lib.KCLASS)})
+
+    def work_model(self):
+        w = _lib.Work_t()
+        self._check(self._L.mcsdp_work_model(self._ctx, C.byref(w)))
+        return dict(flops={k: w.flops[i] for i, k in enumerate(_lib.KCLASS)},
+                    bytes={k: w.bytes[i] for i, k in enumerate(_lib.KCLASS)})
+
+    def identity_layout(self):
+        ro, co, valid, _ = self.layout_index()
+        v = np.where(valid & (ro == co), 1.0, 0.0)
+        return torch.tensor(v, dtype=torch.float64, device=self.torch_device)
+
+    def stats_reset(self):
+        self._check(self._L.mcsdp_stats_reset(self._ctx))
+
     def factors(self, Xbar_layout, z):
         X = self._dev(Xbar_layout, self.info["nnz_layout"])
         zz = self._dev(z, self.m)

@@ -87,7 +87,7 @@ void launch_scm_tiles(const DevSym &S, const int2 *tiles, int ntiles, int g0, co
 // B internal, (m+1) x m lower, column-major, ld = ldb; row m holds g^T on entry and
 // (L^{-1} g)^T on exit.
 int dense_chol_bordered(double *B, int64_t ldb, int m, int *status, cudaStream_t st);
-void dense_backsolve(const double *B, int64_t ldb, int m, double *x, cudaStream_t st);
+int dense_backsolve(const double *B, int64_t ldb, int m, double *x, cudaStream_t st);
 void launch_rhs_border(const DevSym &S, double *B, int64_t ldb, const double *hvec, double betamu,
                        cudaStream_t st);
 void launch_dz_to_user(const DevSym &S, const double *dz_int, double *dz_user, cudaStream_t st);

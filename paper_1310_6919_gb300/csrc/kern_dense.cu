@@ -159,9 +159,11 @@ int dense_chol_bordered(double *B, int64_t ldb, int m, int *status, cudaStream_t
     configured = true;
   }
   const int rows = m + 1;  // including the border row
+  int launches = 0;
   for (int k0 = 0; k0 < m; k0 += NB) {
     const int nb = (m - k0) < NB ? (m - k0) : NB;
     k_potrf_diag<<<1, 256, 0, st>>>(B, ldb, k0, nb, status);
+    ++launches;
     const int r0 = k0 + nb;
     const int nr = rows - r0;
     if (nr > 0) {
@@ -170,9 +172,10 @@ int dense_chol_bordered(double *B, int64_t ldb, int m, int *status, cudaStream_t
       const int nt = (nr + 63) / 64;
       const int ntiles = nt * (nt + 1) / 2;
       k_syrk_tiles<<<ntiles, 256, 2 * NB * 64 * sizeof(double), st>>>(B, ldb, k0, nb, r0, rows, m);
+      launches += 2;
     }
   }
-  return 0;
+  return launches;
 }
 
 // Backward substitution L^T x = y, y = row m of B, blocks of 64 from the bottom.
@@ -215,15 +218,21 @@ __global__ void k_copy_border(const double *B, int64_t ldb, int m, double *x) {
     x[j] = B[m + (int64_t)j * ldb];
 }
 
-void dense_backsolve(const double *B, int64_t ldb, int m, double *x, cudaStream_t st) {
+int dense_backsolve(const double *B, int64_t ldb, int m, double *x, cudaStream_t st) {
   k_copy_border<<<(m + 255) / 256, 256, 0, st>>>(B, ldb, m, x);
+  int launches = 1;
   const int nblk = (m + NB - 1) / NB;
   for (int bk = nblk - 1; bk >= 0; --bk) {
     const int b0 = bk * NB;
     const int nb = (m - b0) < NB ? (m - b0) : NB;
     k_bs_diag<<<1, 32, 0, st>>>(B, ldb, b0, nb, x);
-    if (b0 > 0) k_bs_update<<<(b0 + 127) / 128, 128, 0, st>>>(B, ldb, b0, nb, x);
+    ++launches;
+    if (b0 > 0) {
+      k_bs_update<<<(b0 + 127) / 128, 128, 0, st>>>(B, ldb, b0, nb, x);
+      ++launches;
+    }
   }
+  return launches;
 }
 
 // row m of B <- g_i = b_{user(i)} - beta mu h_i   (internal order)

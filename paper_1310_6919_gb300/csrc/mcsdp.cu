@@ -74,6 +74,12 @@ struct mcsdp_ctx {
   int *status = nullptr, *rhs_dev = nullptr;
   int2 *tiles_dev = nullptr;
   int64_t *panoff_dev = nullptr;
+  // kernel statistics
+  int64_t launches = 0;
+  int64_t kcount[16] = {};
+  double kms[16] = {};
+  std::vector<cudaEvent_t> evpool;
+  std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> pending;
 };
 
 namespace {
@@ -98,6 +104,56 @@ mcsdp_status fail(mcsdp_ctx *c, mcsdp_status s, const std::string &msg) {
   } while (0)
 
 size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
+
+enum KClass { KC_YCHOL = 0, KC_ALG1, KC_PANEL, KC_TILE, KC_CHOL, KC_BSOLVE, KC_PMAT, KC_PSTEP,
+              KC_DSTEP, KC_MISC };
+
+cudaEvent_t ev_get(mcsdp_ctx *c) {
+  if (c->evpool.empty()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  cudaEvent_t e = c->evpool.back();
+  c->evpool.pop_back();
+  return e;
+}
+
+// Brackets the launches of one kernel class: counts them and, with profiling on, records CUDA
+// events on the context's stream around them.
+struct KScope {
+  mcsdp_ctx *c;
+  int cls;
+  cudaEvent_t a = nullptr;
+  KScope(mcsdp_ctx *c_, int cls_) : c(c_), cls(cls_) {
+    if (c->opt.profile) {
+      a = ev_get(c);
+      cudaEventRecord(a, c->stream);
+    }
+  }
+  void done(int nlaunch) {
+    c->launches += nlaunch;
+    c->kcount[cls] += nlaunch;
+    if (a) {
+      cudaEvent_t b = ev_get(c);
+      cudaEventRecord(b, c->stream);
+      c->pending.emplace_back(cls, a, b);
+      a = nullptr;
+    }
+  }
+};
+
+// resolve recorded event pairs; call only after the stream has been synchronised
+void prof_flush(mcsdp_ctx *c) {
+  for (auto &p : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, std::get<1>(p), std::get<2>(p)) == cudaSuccess)
+      c->kms[std::get<0>(p)] += ms;
+    c->evpool.push_back(std::get<1>(p));
+    c->evpool.push_back(std::get<2>(p));
+  }
+  c->pending.clear();
+}
 
 template <class T>
 void plan_table(mcsdp_ctx *c, size_t &cur, const std::string &name, const std::vector<T> &v) {
@@ -322,6 +378,7 @@ mcsdp_status ready(mcsdp_ctx *c) {
 mcsdp_status read_status(mcsdp_ctx *c, int *h, int count) {
   CUDA_TRY(c, cudaMemcpyAsync(h, c->status, count * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  prof_flush(c);
   return MCSDP_OK;
 }
 
@@ -329,7 +386,9 @@ mcsdp_status read_status(mcsdp_ctx *c, int *h, int count) {
 
 mcsdp_status phase_Y(mcsdp_ctx *c, const double *z) {
   CUDA_TRY(c, cudaMemsetAsync(c->Ylay, 0, c->D.nnzL * 8, c->stream));
+  KScope ks(c, KC_MISC);
   launch_slot_combine(c->D, c->Ylay, z, 1.0, -1.0, c->stream);
+  ks.done(1);
   KCHECK(c);
   return MCSDP_OK;
 }
@@ -340,10 +399,12 @@ mcsdp_status phase_ychol(mcsdp_ctx *c, int ncand, const double *alpha, const dou
   const Symbolic &S = c->S;
   if (ychol_smem_bytes(c->D) > 220 * 1024)
     return fail(c, MCSDP_ERR_ARG, "supernode too large for the shared-memory Cholesky kernel");
+  KScope ks(c, ncand > 1 ? KC_DSTEP : KC_YCHOL);
   for (int l = 0; l < S.height; ++l) {
     launch_ychol_level(c->D, S.lvl_ptr[l], S.lvl_ptr[l + 1] - S.lvl_ptr[l], ncand, alpha, Yb, dY,
                        Nbuf, dinv, status, c->stream);
   }
+  ks.done(S.height);
   KCHECK(c);
   return MCSDP_OK;
 }
@@ -358,18 +419,24 @@ mcsdp_status factor_Y(mcsdp_ctx *c) {
 mcsdp_status factor_X(mcsdp_ctx *c, const double *Xbar) {
   if (alg1_smem_bytes(c->D) > 220 * 1024)
     return fail(c, MCSDP_ERR_ARG, "clique too large for the shared-memory Algorithm 1 kernel");
+  KScope ks(c, KC_ALG1);
   launch_alg1(c->D, Xbar, c->Lh, c->dinvL, c->status + 1, c->stream);
+  ks.done(1);
   KCHECK(c);
   return MCSDP_OK;
 }
 
 mcsdp_status phase_scm(mcsdp_ctx *c) {
   for (const Chunk &ch : c->chunks) {
+    KScope k1(c, KC_PANEL);
     launch_scm_panels(c->D, ch.g0, ch.g1, c->Lh, c->dinvL, c->N, c->dinvN, c->pan,
                       c->panoff_dev + ch.g0, c->rhs_dev + ch.rhs_begin, ch.nrhs, c->stream);
+    k1.done(1);
     KCHECK(c);
+    KScope k2(c, KC_TILE);
     launch_scm_tiles(c->D, c->tiles_dev + ch.tile_begin, ch.ntiles, ch.g0, c->pan,
                      c->panoff_dev + ch.g0, c->B, c->ldb, c->hvec, c->pmax, c->stream);
+    k2.done(1);
     KCHECK(c);
   }
   return MCSDP_OK;
@@ -388,27 +455,49 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
   mcsdp_status s = phase_scm(c);
   if (s) return s;
   cudaEventRecord(c->ev[1], c->stream);
-  launch_rhs_border(c->D, c->B, c->ldb, c->hvec, beta * mu, c->stream);
-  dense_chol_bordered(c->B, c->ldb, m, c->status + 2, c->stream);
-  dense_backsolve(c->B, c->ldb, m, c->xs, c->stream);
-  launch_dz_to_user(c->D, c->xs, c->dz, c->stream);
+  {
+    KScope k0(c, KC_MISC);
+    launch_rhs_border(c->D, c->B, c->ldb, c->hvec, beta * mu, c->stream);
+    k0.done(1);
+    KScope k1(c, KC_CHOL);
+    k1.done(dense_chol_bordered(c->B, c->ldb, m, c->status + 2, c->stream));
+    KScope k2(c, KC_BSOLVE);
+    int nl = dense_backsolve(c->B, c->ldb, m, c->xs, c->stream);
+    launch_dz_to_user(c->D, c->xs, c->dz, c->stream);
+    k2.done(nl + 1);
+  }
   KCHECK(c);
   cudaEventRecord(c->ev[2], c->stream);
   CUDA_TRY(c, cudaMemsetAsync(c->dY, 0, c->D.nnzL * 8, c->stream));
-  launch_slot_combine(c->D, c->dY, c->dz, 0.0, -1.0, c->stream);
-  launch_pmatrix(c->D, c->Lh, c->dinvL, c->N, c->dinvN, c->dY, c->YinvE, c->Mlow, c->Mup, c->stream);
-  launch_dx_combine(c->D, beta * mu, Xbar, c->YinvE, c->Mlow, c->Mup, c->dX, c->stream);
+  {
+    KScope k0(c, KC_MISC);
+    launch_slot_combine(c->D, c->dY, c->dz, 0.0, -1.0, c->stream);
+    k0.done(1);
+    KScope k1(c, KC_PMAT);
+    launch_pmatrix(c->D, c->Lh, c->dinvL, c->N, c->dinvN, c->dY, c->YinvE, c->Mlow, c->Mup, c->stream);
+    k1.done(1);
+    KScope k2(c, KC_MISC);
+    launch_dx_combine(c->D, beta * mu, Xbar, c->YinvE, c->Mlow, c->Mup, c->dX, c->stream);
+    k2.done(1);
+  }
   KCHECK(c);
   cudaEventRecord(c->ev[3], c->stream);
   // primal step (eq. primal_length2)
-  launch_primal_step(c->D, Xbar, c->dX, c->alpha_r, c->status + 3, c->stream);
-  launch_measures(c->D, Xbar, c->Ylay, c->z, c->alpha_r, c->scal, c->stream);
+  {
+    KScope k1(c, KC_PSTEP);
+    launch_primal_step(c->D, Xbar, c->dX, c->alpha_r, c->status + 3, c->stream);
+    k1.done(1);
+    KScope k2(c, KC_MISC);
+    launch_measures(c->D, Xbar, c->Ylay, c->z, c->alpha_r, c->scal, c->stream);
+    k2.done(1);
+  }
   KCHECK(c);
   double sc[8];
   int st[4];
   CUDA_TRY(c, cudaMemcpyAsync(sc, c->scal, 6 * 8, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(st, c->status, 4 * 4, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  prof_flush(c);
   if (st[2] & ST_NOT_PD) return fail(c, MCSDP_ERR_NOT_PD, "Schur complement matrix is not positive definite");
   o.ap = sc[5];
   // dual step: bisection on the success of Y + alpha dY = N N^T (K2 on candidates)
@@ -433,6 +522,7 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
     int cs[NCAND];
     CUDA_TRY(c, cudaMemcpyAsync(cs, c->status + 8, NCAND * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  prof_flush(c);
     for (int i = 0; i < NCAND; ++i) {
       if (cs[i] == 0) lo = std::max(lo, cand[i]);
       else hi = (hi < 0) ? cand[i] : std::min(hi, cand[i]);
@@ -466,12 +556,17 @@ mcsdp_status prepare(mcsdp_ctx *c, const double *Xbar, const double *z, double *
   if (s) return s;
   s = factor_X(c, Xbar);
   if (s) return s;
-  launch_measures(c->D, Xbar, c->Ylay, z, nullptr, c->scal, c->stream);
+  {
+    KScope k2(c, KC_MISC);
+    launch_measures(c->D, Xbar, c->Ylay, z, nullptr, c->scal, c->stream);
+    k2.done(1);
+  }
   KCHECK(c);
   int st[4];
   if (scal_host) CUDA_TRY(c, cudaMemcpyAsync(scal_host, c->scal, 6 * 8, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(st, c->status, 4 * 4, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  prof_flush(c);
   if (st[0] & ST_NOT_PD) return fail(c, MCSDP_ERR_NOT_PD, "Y = A_0 - sum z_k A_k is not positive definite");
   if (st[1] & ST_NOT_PD) return fail(c, MCSDP_ERR_NOT_PD, "a clique block of X̄ is not positive definite");
   return MCSDP_OK;
@@ -479,11 +574,14 @@ mcsdp_status prepare(mcsdp_ctx *c, const double *Xbar, const double *z, double *
 
 mcsdp_status set_default_start(mcsdp_ctx *c) {
   CUDA_TRY(c, cudaMemsetAsync(c->Xbar, 0, c->D.nnzL * 8, c->stream));
+  KScope ks(c, KC_MISC);
   launch_set_identity(c->D, c->Xbar, c->stream);
+  ks.done(1);
   KCHECK(c);
   CUDA_TRY(c, cudaMemcpyAsync(c->z, c->z0_default.data(), (size_t)c->S.m * 8, cudaMemcpyHostToDevice,
                               c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  prof_flush(c);
   return MCSDP_OK;
 }
 
@@ -590,6 +688,11 @@ void mcsdp_destroy(mcsdp_ctx *c) {
     cudaSetDevice(c->device);
     for (int i = 0; i < 8; ++i)
       if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    if (!c->pending.empty()) {
+      cudaStreamSynchronize(c->stream);
+      prof_flush(c);
+    }
+    for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
   }
   delete c;
 }
@@ -613,6 +716,7 @@ mcsdp_status mcsdp_set_workspace(mcsdp_ctx *c, void *ptr, size_t bytes) {
     CUDA_TRY(c, cudaMemcpyAsync(c->ws + u.off, u.src, u.bytes, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->B, 0, (size_t)c->ldb * c->S.m * 8, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  prof_flush(c);
   c->iterate_set = false;
   return MCSDP_OK;
 }
@@ -630,6 +734,8 @@ mcsdp_status mcsdp_sym_info_get(const mcsdp_ctx *c, mcsdp_sym_info *info) {
   info->nnz_layout = S.ns ? S.sn_valptr[S.ns] : 0;
   info->nnz_lower_E = S.nnz_lower_E;
   info->nslot = S.nslot;
+  info->table_bytes = 0;
+  for (const Upload &u : c->uploads) info->table_bytes += (int64_t)u.bytes;
   return MCSDP_OK;
 }
 
@@ -656,6 +762,7 @@ mcsdp_status mcsdp_set_iterate(mcsdp_ctx *c, const double *Xbar, const double *z
   if (Xbar) CUDA_TRY(c, cudaMemcpyAsync(c->Xbar, Xbar, c->D.nnzL * 8, cudaMemcpyDeviceToDevice, c->stream));
   if (z) CUDA_TRY(c, cudaMemcpyAsync(c->z, z, (size_t)c->S.m * 8, cudaMemcpyDeviceToDevice, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  prof_flush(c);
   c->iterate_set = true;
   return MCSDP_OK;
 }
@@ -668,6 +775,7 @@ mcsdp_status mcsdp_get_iterate(const mcsdp_ctx *cc, double *Xbar, double *z, dou
   if (z) CUDA_TRY(c, cudaMemcpyAsync(z, c->z, (size_t)c->S.m * 8, cudaMemcpyDeviceToDevice, c->stream));
   if (Y) CUDA_TRY(c, cudaMemcpyAsync(Y, c->Ylay, c->D.nnzL * 8, cudaMemcpyDeviceToDevice, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  prof_flush(c);
   return MCSDP_OK;
 }
 
@@ -679,6 +787,7 @@ mcsdp_status mcsdp_factors(mcsdp_ctx *c, const double *Xbar, const double *z, do
   if (Lh) CUDA_TRY(c, cudaMemcpyAsync(Lh, c->Lh, c->D.nnzL * 8, cudaMemcpyDeviceToDevice, c->stream));
   if (N) CUDA_TRY(c, cudaMemcpyAsync(N, c->N, c->D.nnzL * 8, cudaMemcpyDeviceToDevice, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  prof_flush(c);
   return MCSDP_OK;
 }
 
@@ -696,7 +805,9 @@ mcsdp_status mcsdp_scm_assemble(mcsdp_ctx *c, const double *Xbar, const double *
   if (s) return s;
   s = phase_scm(c);
   if (s) return s;
+  KScope ks(c, KC_MISC);
   launch_B_to_user(c->D, c->B, c->ldb, Bout, ldb, c->hvec, h, c->stream);
+  ks.done(1);
   KCHECK(c);
   int st[4];
   s = read_status(c, st, 4);
@@ -724,6 +835,7 @@ mcsdp_status mcsdp_newton_step(mcsdp_ctx *c, const double *Xbar, const double *z
   if (dX) CUDA_TRY(c, cudaMemcpyAsync(dX, c->dX, c->D.nnzL * 8, cudaMemcpyDeviceToDevice, c->stream));
   if (dY) CUDA_TRY(c, cudaMemcpyAsync(dY, c->dY, c->D.nnzL * 8, cudaMemcpyDeviceToDevice, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  prof_flush(c);
   if (ap) *ap = o.ap;
   if (ad) *ad = o.ad;
   if (mu) *mu = muv;
@@ -781,11 +893,14 @@ mcsdp_status mcsdp_solve(mcsdp_ctx *c, mcsdp_result *res) {
     if (c->opt.verbose)
       std::fprintf(stderr, "it %3d pobj %+.10e dobj %+.10e gap %.2e pinf %.2e mu %.2e ap %.3f ad %.3f\n",
                    it, pobj, dobj, gap, pinf, mu, o.ap, o.ad);
+    KScope ks(c, KC_MISC);
     launch_update(c->D, c->Xbar, c->dX, c->opt.gamma * o.ap, c->z, c->dz, c->opt.gamma * o.ad, c->stream);
+    ks.done(1);
     KCHECK(c);
   }
   cudaEventRecord(t1, c->stream);
   CUDA_TRY(c, cudaEventSynchronize(t1));
+  prof_flush(c);
   float ms = 0;
   cudaEventElapsedTime(&ms, t0, t1);
   r.seconds = ms * 1e-3;
@@ -796,6 +911,127 @@ mcsdp_status mcsdp_solve(mcsdp_ctx *c, mcsdp_result *res) {
   r.status = final_status;
   if (res) *res = r;
   return final_status;
+}
+
+mcsdp_status mcsdp_stats_get(const mcsdp_ctx *c, mcsdp_stats *st) {
+  if (!c || !st) return MCSDP_ERR_ARG;
+  std::memset(st, 0, sizeof(*st));
+  st->launches = c->launches;
+  for (int i = 0; i < 16; ++i) {
+    st->count[i] = c->kcount[i];
+    st->ms[i] = c->kms[i];
+  }
+  return MCSDP_OK;
+}
+
+mcsdp_status mcsdp_work_model(const mcsdp_ctx *c, mcsdp_work *w) {
+  if (!c || !w) return MCSDP_ERR_ARG;
+  std::memset(w, 0, sizeof(*w));
+  const Symbolic &S = c->S;
+  const int ns = S.ns;
+  auto nrow_of = [&](int s) { return (double)(S.sn_rowptr[s + 1] - S.sn_rowptr[s]); };
+  auto ncol_of = [&](int s) { return (double)(S.sn_col[s + 1] - S.sn_col[s]); };
+  // stored lower entries of a supernode = multiply-adds of one triangular pass, one RHS
+  std::vector<double> ent(ns);
+  double nnzE = 0;
+  for (int s = 0; s < ns; ++s) {
+    const double k = ncol_of(s), r = nrow_of(s);
+    ent[s] = k * (k + 1) / 2 + (r - k) * k;
+    nnzE += ent[s];
+  }
+  // path entries from column j upward (forward solve with e_j)
+  auto path_entries = [&](int j) {
+    int s = S.col2sn[j];
+    const double k = ncol_of(s), r = nrow_of(s);
+    const double lc = j - S.sn_col[s];
+    double e = 0;
+    for (double cc = lc; cc < k; cc += 1) e += r - cc;
+    for (s = S.sn_parent[s]; s >= 0; s = S.sn_parent[s]) e += ent[s];
+    return e;
+  };
+  // K2: supernodal Cholesky
+  double fy = 0;
+  for (int s = 0; s < ns; ++s) {
+    const double k = ncol_of(s), r = nrow_of(s);
+    fy += k * k * k / 3 + (r - k) * k * k;
+  }
+  for (int t = 0; t < ns; ++t)
+    for (int u = S.upd_ptr[t]; u < S.upd_ptr[t + 1]; ++u) {
+      const int src = S.upd_src[u];
+      const double na = nrow_of(src) - S.upd_p1[u], nb = S.upd_p2[u] - S.upd_p1[u];
+      fy += 2 * ncol_of(src) * (na * nb - nb * (nb - 1) / 2);
+    }
+  w->flops[0] = fy;
+  w->bytes[0] = 8 * (2 * nnzE);
+  // K1: per clique Cholesky (k^3/3) + triangular inverse (k^3/3)
+  double f1 = 0, b1 = 0;
+  for (int s = 0; s < ns; ++s) {
+    const double k = nrow_of(s);
+    f1 += 2 * k * k * k / 3;
+  }
+  b1 = 8 * 2 * nnzE;
+  w->flops[1] = f1;
+  w->bytes[1] = b1;
+  // K3 panels: 2 |P_g| right-hand sides per group, forward along each column's own path,
+  // backward over the supernodes needed by the rows of P_h, h >= g
+  double fp = 0, bp = 0;
+  const int R = S.grp_pptr[S.ngroup];
+  for (int g = 0; g < S.ngroup; ++g) {
+    double need = 0;
+    for (int64_t t = S.need_ptr[g]; t < S.need_ptr[g + 1]; ++t) need += ent[S.need_sn[t]];
+    for (int p = S.grp_pptr[g]; p < S.grp_pptr[g + 1]; ++p) fp += 2 * 2 * (path_entries(S.grp_cols[p]) + need);
+    bp += 8.0 * 2 * (R - S.grp_pptr[g]) * (S.grp_pptr[g + 1] - S.grp_pptr[g]);
+  }
+  w->flops[2] = fp;
+  w->bytes[2] = bp + 8 * 2 * nnzE;  // panels written once, both factors read once
+  // K3 tiles: one multiply-add per pair of nonzeros of (A_i, A_j), i >= j
+  double ft = 0;
+  std::vector<double> cnt(S.m);
+  for (int i = 0; i < S.m; ++i) cnt[i] = S.anz_ptr[i + 1] - S.anz_ptr[i];
+  std::vector<double> suffix(S.m + 1, 0.0);
+  for (int i = S.m - 1; i >= 0; --i) suffix[i] = suffix[i + 1] + cnt[i];
+  for (int j = 0; j < S.m; ++j) ft += 2 * cnt[j] * suffix[j];
+  w->flops[3] = ft;
+  w->bytes[3] = bp + 8.0 * S.m * (S.m + 1) / 2;  // panels read once, lower(B) written once
+  // K4: dense Cholesky with the bordered right-hand side, back substitution
+  const double m = S.m;
+  w->flops[4] = m * m * m / 3 + m * m;
+  w->bytes[4] = 8 * 2 * (m * (m + 1) / 2);
+  w->flops[5] = m * m;
+  w->bytes[5] = 8 * m * (m + 1) / 2;
+  // K6: per column: N forward along the path, N backward, dY product, L̂ forward and backward
+  double fpm = 0;
+  const double arow = (double)S.arow_col.size();
+  for (int j = 0; j < S.n; ++j) fpm += 2 * (path_entries(j) + 3 * nnzE);
+  fpm += 2 * arow * S.n;
+  w->flops[6] = fpm;
+  w->bytes[6] = 8 * (2 * nnzE + (double)S.nslot + 4 * nnzE);
+  // K7: per clique Cholesky (k^3/3), two triangular solves with k right-hand sides (k^3 each),
+  // Householder tridiagonalisation (4k^3/3)
+  double fps = 0;
+  for (int s = 0; s < ns; ++s) {
+    const double k = nrow_of(s);
+    fps += (1.0 / 3 + 2.0 + 4.0 / 3) * k * k * k;
+  }
+  w->flops[7] = fps;
+  w->bytes[7] = 8 * 2 * nnzE;
+  w->flops[8] = fy;
+  w->bytes[8] = 8 * 3 * nnzE;
+  return MCSDP_OK;
+}
+
+mcsdp_status mcsdp_stats_reset(mcsdp_ctx *c) {
+  if (!c) return MCSDP_ERR_ARG;
+  if (!c->pending.empty() && !c->host_only) {
+    cudaStreamSynchronize(c->stream);
+    prof_flush(c);
+  }
+  c->launches = 0;
+  for (int i = 0; i < 16; ++i) {
+    c->kcount[i] = 0;
+    c->kms[i] = 0.0;
+  }
+  return MCSDP_OK;
 }
 
 mcsdp_status mcsdp_backward(mcsdp_ctx *c, const double *, const double *, double *, double *, double *) {
