@@ -81,6 +81,9 @@ typedef struct {
   int32_t group_max;     /* max constraints per SCM group (<= 64); 0 = default 64 */
   double panel_budget_mb;/* bound on the SCM panel buffers; 0 = default 1024 MB */
   int32_t profile;       /* 1 = time every kernel class with CUDA events (mcsdp_stats_get) */
+  int32_t relax;         /* 1 = relaxed supernode amalgamation (default), 0 = fundamental
+                            supernodes only; amalgamation enlarges E with explicit zeros */
+  int32_t solve_warps;   /* warps per SM of the many-right-hand-side solve kernels; 0 = 2 */
 } mcsdp_options;
 
 void mcsdp_default_options(mcsdp_options *opt);

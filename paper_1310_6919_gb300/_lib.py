@@ -18,7 +18,8 @@ class Options_t(C.Structure):
                 ("feas_tol", C.c_double), ("max_iter", C.c_int32), ("precision", C.c_int32),
                 ("timeout_cycles", C.c_int64), ("device", C.c_int32), ("verbose", C.c_int32),
                 ("panel_max", C.c_int32), ("group_max", C.c_int32),
-                ("panel_budget_mb", C.c_double), ("profile", C.c_int32)]
+                ("panel_budget_mb", C.c_double), ("profile", C.c_int32), ("relax", C.c_int32),
+                ("solve_warps", C.c_int32)]
 
 
 class Work_t(C.Structure):

@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmcsdp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU = ["kern_sparse.cu", "kern_scm.cu", "kern_dense.cu", "mcsdp.cu"]
+CU = ["kern_sparse.cu", "kern_scm.cu", "kern_dense.cu", "kern_lsolve.cu", "mcsdp.cu"]
 CPP = ["symbolic.cpp"]
 
 

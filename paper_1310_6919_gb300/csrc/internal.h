@@ -8,8 +8,9 @@ namespace mcsdp {
 // Device copies of the symbolic tables (all pointers into the caller's workspace).
 struct DevSym {
   int n, m, ns, ngroup, max_nrow, max_ncol;
-  int64_t nnzL, nslot;
+  int64_t nnzL, nslot, nnzD;
   const int *sn_col;
+  const int64_t *sn_dptr;
   const int64_t *sn_rowptr;
   const int *rows;
   const int64_t *sn_valptr;
@@ -35,7 +36,37 @@ struct DevSym {
   const double *anz_v;
   const int64_t *reach_ptr, *need_ptr;
   const int *reach_sn, *need_sn;
+  const int *sn_fdesc;
+  // update lists split in chunks: chunk 0 of target t is upd_ptr[t] .. upd_c0end[t] (applied by
+  // t's own CTA); the extra chunks xch_beg[t] .. xch_end[t] of the xch_* tables are summed in
+  // parallel into slots (offset xch_slotw in rows of the solve buffer, xch_slotf in doubles of a
+  // frontal partial) and added by t's CTA in chunk order
+  const int *upd_c0end, *xch_beg, *xch_end;
+  const int *xch_t, *xch_ub, *xch_ue;
+  const int64_t *xch_slotw, *xch_slotf;
+  int64_t nslotw, nslotf;
+  // P-MATRIX items (nw consecutive columns): union of the columns' etree paths, ascending
+  const int64_t *pm_ptr;
+  const int *pm_sn;
   const double *b;
+};
+
+// Skip rule of the level-scheduled solves: (supernode t, tile) is processed only if bit t is set
+// in one of the bitmap rows tile_keys[tile].x .. tile_keys[tile].y (bits == nullptr: never skip).
+struct LsSkip {
+  const uint32_t *bits;
+  const int2 *tile_keys;
+  int words;  // 32-bit words per bitmap row
+};
+
+// Launch shape of the multi-right-hand-side supernodal solve kernels (one warp per right-hand
+// side, nw warps per CTA, factor blocks staged in shared memory).
+struct SolveCfg {
+  int nw;          // warps (right-hand sides) per CTA
+  int wsmem;       // 1: right-hand sides in shared memory, 0: in global scratch
+  int cap, cap_d, cap_r;  // stage capacities: L block, D block (doubles), rows (ints)
+  int grid;        // persistent CTAs
+  size_t smem;     // dynamic shared memory per CTA
 };
 
 // Status word bits written by kernels (never trap).
@@ -47,18 +78,33 @@ void launch_slot_combine(const DevSym &S, double *out_layout, const double *vec,
                          double c1, cudaStream_t st);
 // Left-looking supernodal Cholesky of Y_c = Ybase + alpha_c dY for ncand candidates, one level
 // of the supernodal tree per launch.  Nbuf holds ncand layouts, dinv ncand n-vectors.
+// Dbuf receives, per candidate, the inverses of the diagonal blocks N_SS^{-1} (sn_dptr layout).
 void launch_ychol_level(const DevSym &S, int lvl_begin, int lvl_count, int ncand,
                         const double *alpha, const double *Ybase, const double *dY, double *Nbuf,
-                        double *dinv, int *status, cudaStream_t st);
+                        double *Dbuf, int *status, const double *Pf, cudaStream_t st);
+// partial sums of the extra update chunks [x0, x0+nx) for ncand candidates into Pf
+void launch_ychol_partials(const DevSym &S, int x0, int nx, int ncand, const double *Nbuf,
+                           double *Pf, const int *status, cudaStream_t st);
 size_t ychol_smem_bytes(const DevSym &S);
 // Algorithm 1: L̂ from X̄ clique by clique.
-void launch_alg1(const DevSym &S, const double *Xbar, double *Lhat, double *dinvL, int *status,
+void launch_alg1(const DevSym &S, const double *Xbar, double *Lhat, double *DL, int *status,
                  cudaStream_t st);
 size_t alg1_smem_bytes(const DevSym &S);
-// P-MATRIX columns (eq. newdX2): Y^{-1} on E, M = X̂ dY Y^{-1} on E (lower and transposed)
-void launch_pmatrix(const DevSym &S, const double *Lhat, const double *dinvL, const double *N,
-                    const double *dinvN, const double *dY, double *YinvE, double *Mlow,
-                    double *Mup, cudaStream_t st);
+// Level-scheduled supernodal solves of the columns of W (row-major n x ldw, ncolsW columns):
+// forward (L^{-1}, levels bottom-up) or backward (L^{-T}, top-down).  Returns the launch count.
+// lvl_xptr_host: per level, range of extra update chunks; Pw: partial buffer (nslotw rows of ldw)
+int lsolve(const DevSym &S, const int *lvl_ptr_host, const int *lvl_xptr_host, int height, bool fwd,
+           const double *L, const double *D, double *W, int64_t ldw, int ncolsW, const LsSkip &sk,
+           double *Pw, cudaStream_t st);
+void launch_rhs_unit(double *W, int64_t ldw, const int *rowof, int nrhs, cudaStream_t st);
+// P-MATRIX pieces for the columns [k0, k0 + nc) held in W (row-major, ld = ldw):
+// Y^{-1} on lower(E) from Wy; Ww = dY Wy; M = X̂ dY Y^{-1} on E (lower and transposed) from Ww
+void launch_extract_lowerE(const DevSym &S, const double *W, int64_t ldw, int k0, int nc,
+                           double *outE, cudaStream_t st);
+void launch_extract_upperE(const DevSym &S, const double *W, int64_t ldw, int k0, int nc,
+                           double *outE, cudaStream_t st);
+void launch_dY_times(const DevSym &S, const double *dY, const double *Wy, double *Ww, int64_t ldw,
+                     int nc, cudaStream_t st);
 void launch_dx_combine(const DevSym &S, double betamu, const double *Xbar, const double *YinvE,
                        const double *Mlow, const double *Mup, double *dX, cudaStream_t st);
 // clique-wise primal step length (eq. primal_length2): alpha_r per clique
@@ -73,15 +119,12 @@ void launch_update(const DevSym &S, double *Xbar, const double *dX, double ap, d
 void launch_set_identity(const DevSym &S, double *Xbar, cudaStream_t st);
 
 // ---------------- SCM assembly (kern_scm.cu) ----------------
-// Panels X̂[P_h, P_g] and Y^{-1}[P_h, P_g] (h >= g) for groups [g0, g1) by warp-per-column
-// supernodal solves; panel (g, which) lives at pan + pan_off[g - g0] + which * pan_half[g - g0].
-void launch_scm_panels(const DevSym &S, int g0, int g1, const double *Lhat, const double *dinvL,
-                       const double *N, const double *dinvN, double *pan, const int64_t *pan_off_dev,
-                       const int *rhs_grp_dev, int nrhs, cudaStream_t st);
-// Tiles B[J_h, J_g] for g in [g0, g1), h >= g; h_i = A_i . Y^{-1} on the diagonal tiles.
-void launch_scm_tiles(const DevSym &S, const int2 *tiles, int ntiles, int g0, const double *pan,
-                      const int64_t *pan_off_dev, double *B, int64_t ldb, double *hvec, int pmax,
-                      cudaStream_t st);
+// Tiles B[J_h, J_g] for the listed (h, g), h >= g, from WX = X̂[:, P_g] and WY = Y^{-1}[:, P_g]
+// (row-major, ld = ldw, the columns of group g start at goff[g]); h_i = A_i . Y^{-1} on the
+// diagonal tiles.
+void launch_scm_tiles(const DevSym &S, const int2 *tiles, int ntiles, const double *WX,
+                      const double *WY, int64_t ldw, const int *goff, double *B, int64_t ldb,
+                      double *hvec, int pmax, cudaStream_t st);
 
 // ---------------- dense SCM factorisation (kern_dense.cu) ----------------
 // B internal, (m+1) x m lower, column-major, ld = ldb; row m holds g^T on entry and

@@ -67,25 +67,25 @@ __device__ void chol_panel_smem(double *F, int nrow, int ncol, int *status_word,
 
 // K2 for one level: CTA (supernode in level, candidate).  Frontal block F = (Ybase + a dY)
 // restricted to C_t x S_t, minus updates from the descendants listed for t, then factored.
-__global__ void k_ychol(DevSym S, int lvl_begin, const double *__restrict__ alpha,
-                        const double *__restrict__ Yb, const double *__restrict__ dY, double *Nbuf,
-                        double *dinv, int *status) {
-  extern __shared__ double F[];
-  const int t = S.lvl_sn[lvl_begin + blockIdx.x];
-  const int c = blockIdx.y;
-  if (*(volatile int *)&status[c] & ST_NOT_PD) return;
-  double *N = Nbuf + (int64_t)c * S.nnzL;
-  double *dv = dinv + (int64_t)c * S.n;
-  const double a = alpha ? alpha[c] : 0.0;
-  const int64_t r0 = S.sn_rowptr[t];
-  const int nrow = (int)(S.sn_rowptr[t + 1] - r0);
-  const int c0 = S.sn_col[t], ncol = S.sn_col[t + 1] - c0;
-  const int64_t v0 = S.sn_valptr[t];
-  const int sz = nrow * ncol;
+// inverse of the leading ncol x ncol lower block of F (ld = nrow) into D (ld = ncol), one thread
+// per column, forward substitution
+__device__ void tri_inverse_smem(const double *F, int ld, int ncol, double *D) {
+  for (int j = threadIdx.x; j < ncol; j += blockDim.x) {
+    for (int i = 0; i < j; ++i) D[i + (int64_t)j * ncol] = 0.0;
+    D[j + (int64_t)j * ncol] = 1.0 / F[j + (int64_t)j * ld];
+    for (int i = j + 1; i < ncol; ++i) {
+      double s = 0.0;
+      for (int l = j; l < i; ++l) s = fma(F[i + (int64_t)l * ld], D[l + (int64_t)j * ncol], s);
+      D[i + (int64_t)j * ncol] = -s / F[i + (int64_t)i * ld];
+    }
+  }
+}
+
+// F[rel rows, rel cols] += sgn * L_s[p1:, :] L_s[p1:p2, :]^T for the updates [ub, ue) of t
+__device__ void ychol_pull(const DevSym &S, int ub, int ue, const double *N, double *F, int nrow,
+                           double sgn) {
   const int tid = threadIdx.x, bd = blockDim.x;
-  for (int i = tid; i < sz; i += bd) F[i] = dY ? fma(a, dY[v0 + i], Yb[v0 + i]) : Yb[v0 + i];
-  __syncthreads();
-  for (int u = S.upd_ptr[t]; u < S.upd_ptr[t + 1]; ++u) {
+  for (int u = ub; u < ue; ++u) {
     const int s = S.upd_src[u], p1 = S.upd_p1[u], p2 = S.upd_p2[u];
     const int *rel = S.upd_rel + S.upd_relptr[u];
     const int snrow = (int)(S.sn_rowptr[s + 1] - S.sn_rowptr[s]);
@@ -98,20 +98,84 @@ __global__ void k_ychol(DevSym S, int lvl_begin, const double *__restrict__ alph
       double acc = 0.0;
       for (int k = 0; k < sncol; ++k)
         acc = fma(Ls[p1 + ia + (int64_t)k * snrow], Ls[p1 + ib + (int64_t)k * snrow], acc);
-      F[rel[ia] + (int64_t)rel[ib] * nrow] -= acc;
+      F[rel[ia] + (int64_t)rel[ib] * nrow] += sgn * acc;
     }
+    __syncthreads();
+  }
+}
+
+// extra update chunks of a level: Pf[cand][slot] = sum of the chunk's updates (nrow_t x ncol_t)
+__global__ void k_ychol_partial(DevSym S, int x0, const double *__restrict__ Nbuf, double *Pf,
+                                const int *status) {
+  extern __shared__ double F[];
+  const int x = x0 + blockIdx.x;
+  const int c = blockIdx.y;
+  if (*(volatile const int *)&status[c] & ST_NOT_PD) return;
+  const int t = S.xch_t[x];
+  const int nrow = (int)(S.sn_rowptr[t + 1] - S.sn_rowptr[t]);
+  const int ncol = S.sn_col[t + 1] - S.sn_col[t];
+  const int sz = nrow * ncol;
+  for (int i = threadIdx.x; i < sz; i += blockDim.x) F[i] = 0.0;
+  __syncthreads();
+  ychol_pull(S, S.xch_ub[x], S.xch_ue[x], Nbuf + (int64_t)c * S.nnzL, F, nrow, 1.0);
+  double *P = Pf + (int64_t)c * S.nslotf + S.xch_slotf[x];
+  for (int i = threadIdx.x; i < sz; i += blockDim.x) P[i] = F[i];
+}
+
+void launch_ychol_partials(const DevSym &S, int x0, int nx, int ncand, const double *Nbuf,
+                           double *Pf, const int *status, cudaStream_t st) {
+  if (nx <= 0) return;
+  const size_t smem = (size_t)S.max_nrow * S.max_ncol * 8;
+  static size_t configured = 0;
+  if (smem > 48 * 1024 && smem > configured) {
+    cudaFuncSetAttribute(k_ychol_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = smem;
+  }
+  dim3 grid(nx, ncand);
+  k_ychol_partial<<<grid, 256, smem, st>>>(S, x0, Nbuf, Pf, status);
+}
+
+__global__ void k_ychol(DevSym S, int lvl_begin, const double *__restrict__ alpha,
+                        const double *__restrict__ Yb, const double *__restrict__ dY, double *Nbuf,
+                        double *Dbuf, int *status, const double *__restrict__ Pf) {
+  extern __shared__ double F[];
+  const int t = S.lvl_sn[lvl_begin + blockIdx.x];
+  const int c = blockIdx.y;
+  if (*(volatile int *)&status[c] & ST_NOT_PD) return;
+  double *N = Nbuf + (int64_t)c * S.nnzL;
+  double *Dc = Dbuf + (int64_t)c * S.nnzD;
+  const double a = alpha ? alpha[c] : 0.0;
+  const int64_t r0 = S.sn_rowptr[t];
+  const int nrow = (int)(S.sn_rowptr[t + 1] - r0);
+  const int c0 = S.sn_col[t], ncol = S.sn_col[t + 1] - c0;
+  const int64_t v0 = S.sn_valptr[t];
+  const int sz = nrow * ncol;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  for (int i = tid; i < sz; i += bd) F[i] = dY ? fma(a, dY[v0 + i], Yb[v0 + i]) : Yb[v0 + i];
+  __syncthreads();
+  ychol_pull(S, S.upd_ptr[t], S.upd_c0end[t], N, F, nrow, -1.0);
+  for (int x = S.xch_beg[t]; x < S.xch_end[t]; ++x) {
+    const double *P = Pf + (int64_t)c * S.nslotf + S.xch_slotf[x];
+    for (int i = tid; i < sz; i += bd) F[i] -= P[i];
     __syncthreads();
   }
   chol_panel_smem(F, nrow, ncol, &status[c], ST_NOT_PD);
   for (int i = tid; i < sz; i += bd) N[v0 + i] = F[i];
-  for (int j = tid; j < ncol; j += bd) dv[c0 + j] = 1.0 / F[j + (int64_t)j * nrow];
+  double *Dsm = F + sz;
+  tri_inverse_smem(F, nrow, ncol, Dsm);
+  __syncthreads();
+  const int64_t d0 = S.sn_dptr[t];
+  for (int i = tid; i < ncol * ncol; i += bd) Dc[d0 + i] = Dsm[i];
+  (void)c0;
 }
 
-size_t ychol_smem_bytes(const DevSym &S) { return (size_t)S.max_nrow * S.max_ncol * 8; }
+size_t ychol_smem_bytes(const DevSym &S) {
+  return ((size_t)S.max_nrow * S.max_ncol + (size_t)S.max_ncol * S.max_ncol) * 8;
+}
 
 void launch_ychol_level(const DevSym &S, int lvl_begin, int lvl_count, int ncand,
                         const double *alpha, const double *Yb, const double *dY, double *Nbuf,
-                        double *dinv, int *status, cudaStream_t st) {
+                        double *Dbuf, int *status, const double *Pf, cudaStream_t st) {
   dim3 grid(lvl_count, ncand);
   const size_t smem = ychol_smem_bytes(S);
   static size_t configured = 0;
@@ -119,14 +183,14 @@ void launch_ychol_level(const DevSym &S, int lvl_begin, int lvl_count, int ncand
     cudaFuncSetAttribute(k_ychol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     configured = smem;
   }
-  k_ychol<<<grid, 256, smem, st>>>(S, lvl_begin, alpha, Yb, dY, Nbuf, dinv, status);
+  k_ychol<<<grid, 256, smem, st>>>(S, lvl_begin, alpha, Yb, dY, Nbuf, Dbuf, status, Pf);
 }
 
 // ---------------------------------------------------------------------------------------------
 // K1: Algorithm 1.  For clique r with k = |C_r|: the reversed block P X̄_CC P (Step 2-1) is
 // Cholesky-factored, M = chol(P X̄_CC P) (Step 2-2); L_r = P M^{-T} P (Step 2-3) and its first
 // |S_r| columns are stored as L̂_{C_r S_r} (Step 3).
-__global__ void k_alg1(DevSym S, const double *__restrict__ X, double *Lh, double *dinvL,
+__global__ void k_alg1(DevSym S, const double *__restrict__ X, double *Lh, double *DL,
                        int *status) {
   extern __shared__ double sm[];
   const int r = blockIdx.x;
@@ -164,14 +228,20 @@ __global__ void k_alg1(DevSym S, const double *__restrict__ X, double *Lh, doubl
     const int a = idx % k, b = idx / k;
     Lh[v0 + idx] = (a >= b) ? T[(k - 1 - b) + (int64_t)(k - 1 - a) * k] : 0.0;
   }
-  for (int b = tid; b < ns; b += bd) dinvL[c0 + b] = 1.0 / T[(k - 1 - b) + (int64_t)(k - 1 - b) * k];
+  // (L_r)_SS^{-1} is the leading block of L_r^{-1} = P M^T P: entry [a][b] = M[k-1-b][k-1-a]
+  const int64_t d0 = S.sn_dptr[r];
+  for (int idx = tid; idx < ns * ns; idx += bd) {
+    const int a = idx % ns, b = idx / ns;
+    DL[d0 + idx] = (a >= b) ? A[(k - 1 - b) + (int64_t)(k - 1 - a) * k] : 0.0;
+  }
+  (void)c0;
 }
 
 size_t alg1_smem_bytes(const DevSym &S) {
   return ((size_t)2 * S.max_nrow * S.max_nrow + S.max_nrow) * 8;
 }
 
-void launch_alg1(const DevSym &S, const double *X, double *Lh, double *dinvL, int *status,
+void launch_alg1(const DevSym &S, const double *X, double *Lh, double *DL, int *status,
                  cudaStream_t st) {
   const size_t smem = alg1_smem_bytes(S);
   static size_t configured = 0;
@@ -179,7 +249,7 @@ void launch_alg1(const DevSym &S, const double *X, double *Lh, double *dinvL, in
     cudaFuncSetAttribute(k_alg1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     configured = smem;
   }
-  k_alg1<<<S.ns, 256, smem, st>>>(S, X, Lh, dinvL, status);
+  k_alg1<<<S.ns, 256, smem, st>>>(S, X, Lh, DL, status);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -189,54 +259,63 @@ void launch_alg1(const DevSym &S, const double *X, double *Lh, double *dinvL, in
 // and the entries on E are stored: Y^{-1} on lower(E), M = X̂ dY Y^{-1} at (i, k) for rows i of
 // column k (Mlow) and at the transposed position for rows i < k (Mup).
 
-__global__ void k_pmatrix(DevSym S, const double *__restrict__ Lh, const double *__restrict__ dinvL,
-                          const double *__restrict__ N, const double *__restrict__ dinvN,
-                          const double *__restrict__ dY, double *YinvE, double *Mlow, double *Mup,
-                          int wpb) {
-  extern __shared__ double sm[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int k = blockIdx.x * wpb + warp;
-  if (k >= S.n) return;
-  const int n = S.n;
-  double *y = sm + (int64_t)warp * 2 * n;
-  double *w = y + n;
-  for (int i = lane; i < n; i += 32) y[i] = (i == k) ? 1.0 : 0.0;
-  __syncwarp();
-  for (int s = S.col2sn[k]; s >= 0; s = S.sn_parent[s]) warp_fwd_sn(S, N, dinvN, y, s, lane);
-  for (int s = S.ns - 1; s >= 0; --s) warp_bwd_sn(S, N, dinvN, y, s, lane);
+// K6 pieces.  For the columns k in [k0, k0 + nc) solved into W (row-major, ld = ldw):
+// lower(E) entries of column k: outE[(i, k)] = W[i][k - k0] for the rows i >= k of k's clique
+__global__ void k_extract_lowerE(DevSym S, const double *__restrict__ W, int64_t ldw, int k0, int nc,
+                                 double *outE) {
+  const int j = blockIdx.x * blockDim.y + threadIdx.y;
+  if (j >= nc) return;
+  const int k = k0 + j;
   const int t = S.col2sn[k];
   const int64_t r0 = S.sn_rowptr[t];
   const int nrow = (int)(S.sn_rowptr[t + 1] - r0);
   const int lc = k - S.sn_col[t];
   const int64_t cbase = S.sn_valptr[t] + (int64_t)lc * nrow;
-  for (int p = lc + lane; p < nrow; p += 32) YinvE[cbase + p] = y[S.rows[r0 + p]];
-  for (int i = lane; i < n; i += 32) {
-    double acc = 0.0;
-    for (int q = S.arow_ptr[i]; q < S.arow_ptr[i + 1]; ++q)
-      acc = fma(dY[S.arow_off[q]], y[S.arow_col[q]], acc);
-    w[i] = acc;
-  }
-  __syncwarp();
-  for (int s = 0; s < S.ns; ++s) warp_fwd_sn(S, Lh, dinvL, w, s, lane);
-  for (int s = S.ns - 1; s >= 0; --s) warp_bwd_sn(S, Lh, dinvL, w, s, lane);
-  for (int p = lc + lane; p < nrow; p += 32) Mlow[cbase + p] = w[S.rows[r0 + p]];
-  for (int q = S.rs_ptr[k] + lane; q < S.rs_ptr[k + 1]; q += 32) Mup[S.rs_off[q]] = w[S.rs_col[q]];
+  for (int p = lc + threadIdx.x; p < nrow; p += blockDim.x)
+    outE[cbase + p] = W[(int64_t)S.rows[r0 + p] * ldw + j];
 }
 
-void launch_pmatrix(const DevSym &S, const double *Lh, const double *dinvL, const double *N,
-                    const double *dinvN, const double *dY, double *YinvE, double *Mlow,
-                    double *Mup, cudaStream_t st) {
-  size_t per = (size_t)2 * S.n * 8;
-  int wpb = (int)((200 * 1024) / per);
-  if (wpb > 4) wpb = 4;
-  if (wpb < 1) wpb = 1;
-  int blocks = (S.n + wpb - 1) / wpb;
-  static size_t configured = 0;
-  if (per * wpb > configured) {
-    cudaFuncSetAttribute(k_pmatrix, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(per * wpb));
-    configured = per * wpb;
-  }
-  k_pmatrix<<<blocks, 32 * wpb, per * wpb, st>>>(S, Lh, dinvL, N, dinvN, dY, YinvE, Mlow, Mup, wpb);
+// transposed entries: for rows i < k with (k, i) in E, outE[(k, i)] = W[i][k - k0]
+__global__ void k_extract_upperE(DevSym S, const double *__restrict__ W, int64_t ldw, int k0, int nc,
+                                 double *outE) {
+  const int j = blockIdx.x * blockDim.y + threadIdx.y;
+  if (j >= nc) return;
+  const int k = k0 + j;
+  for (int q = S.rs_ptr[k] + threadIdx.x; q < S.rs_ptr[k + 1]; q += blockDim.x)
+    outE[S.rs_off[q]] = W[(int64_t)S.rs_col[q] * ldw + j];
+}
+
+void launch_extract_lowerE(const DevSym &S, const double *W, int64_t ldw, int k0, int nc,
+                           double *outE, cudaStream_t st) {
+  if (nc <= 0) return;
+  dim3 blk(32, 8);
+  k_extract_lowerE<<<(nc + 7) / 8, blk, 0, st>>>(S, W, ldw, k0, nc, outE);
+}
+
+void launch_extract_upperE(const DevSym &S, const double *W, int64_t ldw, int k0, int nc,
+                           double *outE, cudaStream_t st) {
+  if (nc <= 0) return;
+  dim3 blk(32, 8);
+  k_extract_upperE<<<(nc + 7) / 8, blk, 0, st>>>(S, W, ldw, k0, nc, outE);
+}
+
+// Ww = dY Wy on the aggregate pattern (full symmetric row lists), row i per CTA row
+__global__ void k_dY_times(DevSym S, const double *__restrict__ dY, const double *__restrict__ Wy,
+                          double *Ww, int64_t ldw, int nc) {
+  const int i = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nc) return;
+  double acc = 0.0;
+  for (int q = S.arow_ptr[i]; q < S.arow_ptr[i + 1]; ++q)
+    acc = fma(dY[S.arow_off[q]], Wy[(int64_t)S.arow_col[q] * ldw + j], acc);
+  Ww[(int64_t)i * ldw + j] = acc;
+}
+
+void launch_dY_times(const DevSym &S, const double *dY, const double *Wy, double *Ww, int64_t ldw,
+                     int nc, cudaStream_t st) {
+  if (nc <= 0) return;
+  dim3 grid((nc + 127) / 128, S.n);
+  k_dY_times<<<grid, 128, 0, st>>>(S, dY, Wy, Ww, ldw, nc);
 }
 
 // dX on lower(E): beta mu Y^{-1} - X̄ - (M + M^T)/2   (eq. dX with the symmetrisation)

@@ -17,6 +17,7 @@
 #include "../../include/mcsdp.h"
 #include "internal.h"
 #include "symbolic.h"
+#include "warp_solve.cuh"
 
 using namespace mcsdp;
 
@@ -29,10 +30,11 @@ struct Upload {
 };
 
 struct Chunk {
-  int g0, g1;
-  int64_t rhs_begin;
-  int nrhs;
-  int64_t tile_begin;
+  int g0, g1;        // groups of the chunk
+  int nrhs;          // right-hand sides (= columns of X̂ / Y^{-1}) of the chunk
+  int64_t rhs_begin; // into rowof_all / goff offsets
+  int64_t tkey_begin;
+  int64_t tile_begin;  // SCM tiles (h, g) of the chunk
   int ntiles;
 };
 
@@ -58,9 +60,23 @@ struct mcsdp_ctx {
   int64_t ldb = 0;
   int pmax = 0;
   std::vector<Chunk> chunks;
-  std::vector<int> rhs_all;
+  std::vector<int> rowof_all;       // SCM right-hand side -> row of its unit vector (per chunk)
+  std::vector<int> goff_all;        // per group: first right-hand side within its chunk
+  std::vector<int2> tkey_all;       // per SCM tile of 32 right-hand sides: group range
+  std::vector<uint32_t> reach_bits, need_bits;  // per group, one bit per supernode
+  std::vector<int2> pm_tkey;        // per P-MATRIX tile of 32 columns: (tile, tile)
+  std::vector<uint32_t> pm_bits;    // per P-MATRIX tile: supernodes on its columns' paths
+  std::vector<int> pm_rowof;        // P-MATRIX right-hand side j -> row j (identity)
+  // update-list chunks (see DevSym)
+  std::vector<int> upd_c0end, xch_beg, xch_end, xch_t, xch_ub, xch_ue, lvl_xptr;
+  std::vector<int64_t> xch_slotw, xch_slotf;
+  int64_t nslotw = 0, nslotf = 0;
+  int bit_words = 1;
+  int pm_cols = 0;                  // P-MATRIX columns per chunk (multiple of 32)
+  int64_t ldw = 0;                  // leading dimension of the solve buffers
+  SolveCfg scfg{};
+  int num_sms = 152;
   std::vector<int2> tiles_all;
-  std::vector<int64_t> panoff_all;  // per group, offset within its chunk buffer
   std::vector<double> z0_default;
   bool z0_ok = false;
   bool iterate_set = false;
@@ -69,11 +85,12 @@ struct mcsdp_ctx {
   double *Xbar = nullptr, *z = nullptr, *Ylay = nullptr, *N = nullptr, *dinvN = nullptr;
   double *Lh = nullptr, *dinvL = nullptr, *dY = nullptr, *dX = nullptr, *YinvE = nullptr;
   double *Mlow = nullptr, *Mup = nullptr, *B = nullptr, *hvec = nullptr, *xs = nullptr;
-  double *dz = nullptr, *pan = nullptr, *Ncand = nullptr, *dinvCand = nullptr;
+  double *dz = nullptr, *W1 = nullptr, *W2 = nullptr, *Ncand = nullptr, *dinvCand = nullptr;
+  double *Pw = nullptr, *Pf = nullptr;
   double *alpha_c = nullptr, *alpha_r = nullptr, *scal = nullptr;
-  int *status = nullptr, *rhs_dev = nullptr;
-  int2 *tiles_dev = nullptr;
-  int64_t *panoff_dev = nullptr;
+  int *status = nullptr, *rowof_dev = nullptr, *goff_dev = nullptr, *pm_rowof_dev = nullptr;
+  int2 *tiles_dev = nullptr, *tkey_dev = nullptr, *pm_tkey_dev = nullptr;
+  uint32_t *reach_bits_dev = nullptr, *need_bits_dev = nullptr, *pm_bits_dev = nullptr;
   // kernel statistics
   int64_t launches = 0;
   int64_t kcount[16] = {};
@@ -170,6 +187,7 @@ void plan_buf(mcsdp_ctx *c, size_t &cur, const std::string &name, size_t bytes) 
 void plan_workspace(mcsdp_ctx *c) {
   Symbolic &S = c->S;
   const int64_t nnzL = S.sn_valptr[S.ns];
+  const int64_t nnzD = S.sn_dptr[S.ns];
   const int n = S.n, m = S.m;
   size_t cur = 0;
   c->uploads.clear();
@@ -177,6 +195,7 @@ void plan_workspace(mcsdp_ctx *c) {
   plan_table(c, cur, "sn_rowptr", S.sn_rowptr);
   plan_table(c, cur, "rows", S.rows);
   plan_table(c, cur, "sn_valptr", S.sn_valptr);
+  plan_table(c, cur, "sn_dptr", S.sn_dptr);
   plan_table(c, cur, "sn_parent", S.sn_parent);
   plan_table(c, cur, "col2sn", S.col2sn);
   plan_table(c, cur, "lvl_sn", S.lvl_sn);
@@ -215,52 +234,156 @@ void plan_workspace(mcsdp_ctx *c) {
   plan_table(c, cur, "need_ptr", S.need_ptr);
   plan_table(c, cur, "reach_sn", S.reach_sn);
   plan_table(c, cur, "need_sn", S.need_sn);
+  plan_table(c, cur, "sn_fdesc", S.sn_fdesc);
   plan_table(c, cur, "b", c->P.b);
-  // SCM chunk plan
-  c->chunks.clear();
-  c->rhs_all.clear();
-  c->tiles_all.clear();
-  c->panoff_all.assign(S.ngroup, 0);
-  const int R = S.grp_pptr[S.ngroup];
+  // ---- update lists in chunks: a target with a long list (the root clique of a block-arrow
+  // pattern receives an update from nearly every clique) gets its extra chunks summed in
+  // parallel by partial kernels, then added in fixed order (deterministic) ----
+  {
+    const double chunk_work = 256.0;
+    c->upd_c0end.assign(S.ns, 0);
+    c->xch_beg.assign(S.ns, 0);
+    c->xch_end.assign(S.ns, 0);
+    c->xch_t.clear(); c->xch_ub.clear(); c->xch_ue.clear();
+    c->xch_slotw.clear(); c->xch_slotf.clear();
+    c->nslotw = c->nslotf = 0;
+    // levels of the targets: chunks are listed level by level
+    std::vector<int> lvl_of(S.ns, 0);
+    for (int l = 0; l < S.height; ++l)
+      for (int q = S.lvl_ptr[l]; q < S.lvl_ptr[l + 1]; ++q) lvl_of[S.lvl_sn[q]] = l;
+    c->lvl_xptr.assign(S.height + 1, 0);
+    for (int l = 0; l < S.height; ++l) {
+      c->lvl_xptr[l] = (int)c->xch_t.size();
+      for (int q = S.lvl_ptr[l]; q < S.lvl_ptr[l + 1]; ++q) {
+        const int t = S.lvl_sn[q];
+        const int tncol = S.sn_col[t + 1] - S.sn_col[t];
+        const int tnrow = (int)(S.sn_rowptr[t + 1] - S.sn_rowptr[t]);
+        std::vector<int> cuts{S.upd_ptr[t]};
+        double wsum = 0;
+        for (int u = S.upd_ptr[t]; u < S.upd_ptr[t + 1]; ++u) {
+          const int d = S.upd_src[u];
+          const double w = (double)(S.upd_p2[u] - S.upd_p1[u]) * (S.sn_col[d + 1] - S.sn_col[d]);
+          if (wsum > 0 && wsum + w > chunk_work) {
+            cuts.push_back(u);
+            wsum = 0;
+          }
+          wsum += w;
+        }
+        cuts.push_back(S.upd_ptr[t + 1]);
+        c->upd_c0end[t] = cuts[1];
+        c->xch_beg[t] = (int)c->xch_t.size();
+        for (size_t k = 1; k + 1 < cuts.size(); ++k) {
+          c->xch_t.push_back(t);
+          c->xch_ub.push_back(cuts[k]);
+          c->xch_ue.push_back(cuts[k + 1]);
+          c->xch_slotw.push_back(c->nslotw);
+          c->xch_slotf.push_back(c->nslotf);
+          c->nslotw += tncol;
+          c->nslotf += (int64_t)tnrow * tncol;
+        }
+        c->xch_end[t] = (int)c->xch_t.size();
+      }
+    }
+    c->lvl_xptr[S.height] = (int)c->xch_t.size();
+    (void)lvl_of;
+  }
+  plan_table(c, cur, "upd_c0end", c->upd_c0end);
+  plan_table(c, cur, "xch_beg", c->xch_beg);
+  plan_table(c, cur, "xch_end", c->xch_end);
+  plan_table(c, cur, "xch_t", c->xch_t);
+  plan_table(c, cur, "xch_ub", c->xch_ub);
+  plan_table(c, cur, "xch_ue", c->xch_ue);
+  plan_table(c, cur, "xch_slotw", c->xch_slotw);
+  plan_table(c, cur, "xch_slotf", c->xch_slotf);
+  // ---- many-right-hand-side solves (kern_lsolve.cu): skip bitmaps and chunk plan ----
   const double budget = (c->opt.panel_budget_mb > 0 ? c->opt.panel_budget_mb : 1024.0) * 1048576.0;
-  size_t pan_max = 0;
+  c->bit_words = (S.ns + 31) / 32;
+  const int words = c->bit_words;
+  c->reach_bits.assign((size_t)S.ngroup * words, 0u);
+  c->need_bits.assign((size_t)S.ngroup * words, 0u);
+  for (int g = 0; g < S.ngroup; ++g) {
+    for (int64_t t = S.reach_ptr[g]; t < S.reach_ptr[g + 1]; ++t)
+      c->reach_bits[(size_t)g * words + (S.reach_sn[t] >> 5)] |= 1u << (S.reach_sn[t] & 31);
+    for (int64_t t = S.need_ptr[g]; t < S.need_ptr[g + 1]; ++t)
+      c->need_bits[(size_t)g * words + (S.need_sn[t] >> 5)] |= 1u << (S.need_sn[t] & 31);
+  }
+  c->chunks.clear();
+  c->rowof_all.clear();
+  c->tkey_all.clear();
+  c->tiles_all.clear();
+  c->goff_all.assign(S.ngroup, 0);
   c->pmax = 0;
+  int max_rhs = 0;
   for (int g = 0; g < S.ngroup;) {
     Chunk ch{};
     ch.g0 = g;
-    ch.rhs_begin = (int64_t)c->rhs_all.size();
+    ch.rhs_begin = (int64_t)c->rowof_all.size();
+    ch.tkey_begin = (int64_t)c->tkey_all.size();
     ch.tile_begin = (int64_t)c->tiles_all.size();
-    size_t bytes = 0;
+    int nr = 0;
+    std::vector<int> grp_of_rhs;
     while (g < S.ngroup) {
       const int pg = S.grp_pptr[g + 1] - S.grp_pptr[g];
-      const size_t gb = (size_t)2 * (R - S.grp_pptr[g]) * pg * 8;
-      if (g > ch.g0 && bytes + gb > budget) break;
-      c->panoff_all[g] = (int64_t)(bytes / 8);
-      bytes += gb;
+      const double bytes = 2.0 * n * 8.0 * (((nr + pg) + 31) / 32 * 32);
+      if (g > ch.g0 && bytes > budget) break;
+      c->goff_all[g] = nr;
+      for (int q = 0; q < pg; ++q) {
+        c->rowof_all.push_back(S.grp_cols[S.grp_pptr[g] + q]);
+        grp_of_rhs.push_back(g);
+      }
+      nr += pg;
       c->pmax = std::max(c->pmax, pg);
-      for (int which = 0; which < 2; ++which)
-        for (int cc = 0; cc < pg; ++cc) c->rhs_all.push_back((g << 9) | (which << 8) | cc);
       for (int h = g; h < S.ngroup; ++h) c->tiles_all.push_back(make_int2(h, g));
       ++g;
     }
     ch.g1 = g;
-    ch.nrhs = (int)((int64_t)c->rhs_all.size() - ch.rhs_begin);
+    ch.nrhs = nr;
+    for (int t0 = 0; t0 < nr; t0 += 32)
+      c->tkey_all.push_back(make_int2(grp_of_rhs[t0], grp_of_rhs[std::min(nr, t0 + 32) - 1]));
     ch.ntiles = (int)((int64_t)c->tiles_all.size() - ch.tile_begin);
     c->chunks.push_back(ch);
-    pan_max = std::max(pan_max, bytes);
+    max_rhs = std::max(max_rhs, nr);
   }
-  plan_table(c, cur, "rhs", c->rhs_all);
+  // P-MATRIX: columns in chunks of pm_cols (multiple of 32); per 32-column tile the supernodes on
+  // the columns' etree paths (forward reach of the unit right-hand sides)
+  {
+    int pmc = (int)std::min<double>((double)n, budget / (2.0 * n * 8.0));
+    pmc = std::max(32, pmc / 32 * 32);
+    c->pm_cols = std::min(pmc, (n + 31) / 32 * 32);
+    const int ntile = (n + 31) / 32;
+    c->pm_bits.assign((size_t)ntile * words, 0u);
+    c->pm_tkey.resize(ntile);
+    for (int tl = 0; tl < ntile; ++tl) {
+      c->pm_tkey[tl] = make_int2(tl, tl);
+      for (int k = tl * 32; k < std::min(n, tl * 32 + 32); ++k)
+        for (int s2 = S.col2sn[k]; s2 >= 0; s2 = S.sn_parent[s2]) {
+          uint32_t &wd = c->pm_bits[(size_t)tl * words + (s2 >> 5)];
+          if (wd & (1u << (s2 & 31))) break;
+          wd |= 1u << (s2 & 31);
+        }
+    }
+    c->pm_rowof.resize(n);
+    for (int k = 0; k < n; ++k) c->pm_rowof[k] = k;
+  }
+  c->ldw = ((int64_t)std::max(max_rhs, c->pm_cols) + 31) / 32 * 32;
+  plan_table(c, cur, "rowof", c->rowof_all);
+  plan_table(c, cur, "goff", c->goff_all);
+  plan_table(c, cur, "tkey", c->tkey_all);
   plan_table(c, cur, "tiles", c->tiles_all);
-  plan_table(c, cur, "panoff", c->panoff_all);
+  plan_table(c, cur, "reach_bits", c->reach_bits);
+  plan_table(c, cur, "need_bits", c->need_bits);
+  plan_table(c, cur, "pm_bits", c->pm_bits);
+  plan_table(c, cur, "pm_tkey", c->pm_tkey);
+  plan_table(c, cur, "pm_rowof", c->pm_rowof);
   // iteration buffers
   c->ldb = ((int64_t)m + 1 + 31) / 32 * 32;
   plan_buf(c, cur, "Xbar", nnzL * 8);
   plan_buf(c, cur, "z", (size_t)m * 8);
   plan_buf(c, cur, "Ylay", nnzL * 8);
   plan_buf(c, cur, "N", nnzL * 8);
-  plan_buf(c, cur, "dinvN", (size_t)n * 8);
+  plan_buf(c, cur, "dinvN", (size_t)nnzD * 8);
   plan_buf(c, cur, "Lh", nnzL * 8);
-  plan_buf(c, cur, "dinvL", (size_t)n * 8);
+  plan_buf(c, cur, "dinvL", (size_t)nnzD * 8);
   plan_buf(c, cur, "dY", nnzL * 8);
   plan_buf(c, cur, "dX", nnzL * 8);
   plan_buf(c, cur, "YinvE", nnzL * 8);
@@ -270,9 +393,12 @@ void plan_workspace(mcsdp_ctx *c) {
   plan_buf(c, cur, "hvec", (size_t)m * 8);
   plan_buf(c, cur, "xs", (size_t)m * 8);
   plan_buf(c, cur, "dz", (size_t)m * 8);
-  plan_buf(c, cur, "pan", pan_max);
+  plan_buf(c, cur, "W1", (size_t)n * c->ldw * 8);
+  plan_buf(c, cur, "W2", (size_t)n * c->ldw * 8);
+  plan_buf(c, cur, "Pw", (size_t)std::max<int64_t>(1, c->nslotw) * c->ldw * 8);
+  plan_buf(c, cur, "Pf", (size_t)std::max<int64_t>(1, c->nslotf) * NCAND * 8);
   plan_buf(c, cur, "Ncand", (size_t)NCAND * nnzL * 8);
-  plan_buf(c, cur, "dinvCand", (size_t)NCAND * n * 8);
+  plan_buf(c, cur, "dinvCand", (size_t)NCAND * nnzD * 8);
   plan_buf(c, cur, "alpha_c", NCAND * 8);
   plan_buf(c, cur, "alpha_r", (size_t)S.ns * 8);
   plan_buf(c, cur, "scal", 16 * 8);
@@ -296,7 +422,9 @@ void bind_pointers(mcsdp_ctx *c) {
   D.max_ncol = S.max_ncol;
   D.nnzL = S.sn_valptr[S.ns];
   D.nslot = S.nslot;
+  D.nnzD = S.sn_dptr[S.ns];
   D.sn_col = wsp<int>(c, "sn_col");
+  D.sn_dptr = wsp<int64_t>(c, "sn_dptr");
   D.sn_rowptr = wsp<int64_t>(c, "sn_rowptr");
   D.rows = wsp<int>(c, "rows");
   D.sn_valptr = wsp<int64_t>(c, "sn_valptr");
@@ -338,6 +466,8 @@ void bind_pointers(mcsdp_ctx *c) {
   D.need_ptr = wsp<int64_t>(c, "need_ptr");
   D.reach_sn = wsp<int>(c, "reach_sn");
   D.need_sn = wsp<int>(c, "need_sn");
+  D.sn_fdesc = wsp<int>(c, "sn_fdesc");
+
   D.b = wsp<double>(c, "b");
   c->Xbar = wsp<double>(c, "Xbar");
   c->z = wsp<double>(c, "z");
@@ -355,16 +485,36 @@ void bind_pointers(mcsdp_ctx *c) {
   c->hvec = wsp<double>(c, "hvec");
   c->xs = wsp<double>(c, "xs");
   c->dz = wsp<double>(c, "dz");
-  c->pan = wsp<double>(c, "pan");
+  c->W1 = wsp<double>(c, "W1");
+  c->W2 = wsp<double>(c, "W2");
+  c->Pw = wsp<double>(c, "Pw");
+  c->Pf = wsp<double>(c, "Pf");
+  D.upd_c0end = wsp<int>(c, "upd_c0end");
+  D.xch_beg = wsp<int>(c, "xch_beg");
+  D.xch_end = wsp<int>(c, "xch_end");
+  D.xch_t = wsp<int>(c, "xch_t");
+  D.xch_ub = wsp<int>(c, "xch_ub");
+  D.xch_ue = wsp<int>(c, "xch_ue");
+  D.xch_slotw = wsp<int64_t>(c, "xch_slotw");
+  D.xch_slotf = wsp<int64_t>(c, "xch_slotf");
+  D.nslotw = c->nslotw;
+  D.nslotf = c->nslotf;
   c->Ncand = wsp<double>(c, "Ncand");
   c->dinvCand = wsp<double>(c, "dinvCand");
   c->alpha_c = wsp<double>(c, "alpha_c");
   c->alpha_r = wsp<double>(c, "alpha_r");
   c->scal = wsp<double>(c, "scal");
   c->status = wsp<int>(c, "status");
-  c->rhs_dev = wsp<int>(c, "rhs");
+
+  c->rowof_dev = wsp<int>(c, "rowof");
+  c->goff_dev = wsp<int>(c, "goff");
+  c->tkey_dev = wsp<int2>(c, "tkey");
   c->tiles_dev = wsp<int2>(c, "tiles");
-  c->panoff_dev = wsp<int64_t>(c, "panoff");
+  c->reach_bits_dev = wsp<uint32_t>(c, "reach_bits");
+  c->need_bits_dev = wsp<uint32_t>(c, "need_bits");
+  c->pm_bits_dev = wsp<uint32_t>(c, "pm_bits");
+  c->pm_tkey_dev = wsp<int2>(c, "pm_tkey");
+  c->pm_rowof_dev = wsp<int>(c, "pm_rowof");
 }
 
 mcsdp_status ready(mcsdp_ctx *c) {
@@ -400,11 +550,18 @@ mcsdp_status phase_ychol(mcsdp_ctx *c, int ncand, const double *alpha, const dou
   if (ychol_smem_bytes(c->D) > 220 * 1024)
     return fail(c, MCSDP_ERR_ARG, "supernode too large for the shared-memory Cholesky kernel");
   KScope ks(c, ncand > 1 ? KC_DSTEP : KC_YCHOL);
+  int nl = 0;
   for (int l = 0; l < S.height; ++l) {
+    const int xb = c->lvl_xptr[l], xc = c->lvl_xptr[l + 1] - xb;
+    if (xc > 0) {
+      launch_ychol_partials(c->D, xb, xc, ncand, Nbuf, c->Pf, status, c->stream);
+      ++nl;
+    }
     launch_ychol_level(c->D, S.lvl_ptr[l], S.lvl_ptr[l + 1] - S.lvl_ptr[l], ncand, alpha, Yb, dY,
-                       Nbuf, dinv, status, c->stream);
+                       Nbuf, dinv, status, c->Pf, c->stream);
+    ++nl;
   }
-  ks.done(S.height);
+  ks.done(nl);
   KCHECK(c);
   return MCSDP_OK;
 }
@@ -427,18 +584,60 @@ mcsdp_status factor_X(mcsdp_ctx *c, const double *Xbar) {
 }
 
 mcsdp_status phase_scm(mcsdp_ctx *c) {
+  const Symbolic &S = c->S;
+  const int n = S.n;
   for (const Chunk &ch : c->chunks) {
     KScope k1(c, KC_PANEL);
-    launch_scm_panels(c->D, ch.g0, ch.g1, c->Lh, c->dinvL, c->N, c->dinvN, c->pan,
-                      c->panoff_dev + ch.g0, c->rhs_dev + ch.rhs_begin, ch.nrhs, c->stream);
-    k1.done(1);
+    int nl = 0;
+    CUDA_TRY(c, cudaMemsetAsync(c->W1, 0, (size_t)n * c->ldw * 8, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->W2, 0, (size_t)n * c->ldw * 8, c->stream));
+    launch_rhs_unit(c->W1, c->ldw, c->rowof_dev + ch.rhs_begin, ch.nrhs, c->stream);
+    launch_rhs_unit(c->W2, c->ldw, c->rowof_dev + ch.rhs_begin, ch.nrhs, c->stream);
+    nl += 2;
+    LsSkip fw{c->reach_bits_dev, c->tkey_dev + ch.tkey_begin, c->bit_words};
+    LsSkip bw{c->need_bits_dev, c->tkey_dev + ch.tkey_begin, c->bit_words};
+    // X̂[:, P_g] = L̂^{-T} L̂^{-1} E and Y^{-1}[:, P_g] = N^{-T} N^{-1} E for the chunk's groups
+    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), S.height, true, c->Lh, c->dinvL, c->W1, c->ldw, ch.nrhs, fw, c->Pw, c->stream);
+    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), S.height, false, c->Lh, c->dinvL, c->W1, c->ldw, ch.nrhs, bw, c->Pw, c->stream);
+    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), S.height, true, c->N, c->dinvN, c->W2, c->ldw, ch.nrhs, fw, c->Pw, c->stream);
+    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), S.height, false, c->N, c->dinvN, c->W2, c->ldw, ch.nrhs, bw, c->Pw, c->stream);
+    k1.done(nl);
     KCHECK(c);
     KScope k2(c, KC_TILE);
-    launch_scm_tiles(c->D, c->tiles_dev + ch.tile_begin, ch.ntiles, ch.g0, c->pan,
-                     c->panoff_dev + ch.g0, c->B, c->ldb, c->hvec, c->pmax, c->stream);
+    launch_scm_tiles(c->D, c->tiles_dev + ch.tile_begin, ch.ntiles, c->W1, c->W2, c->ldw,
+                     c->goff_dev, c->B, c->ldb, c->hvec, c->pmax, c->stream);
     k2.done(1);
     KCHECK(c);
   }
+  return MCSDP_OK;
+}
+
+// P-MATRIX (eq. newdX2): for column blocks of the identity, Y^{-1} E (N solves), dY Y^{-1} E,
+// X̂ dY Y^{-1} E (L̂ solves), keeping the entries on E.
+mcsdp_status phase_pmatrix(mcsdp_ctx *c, int *nlaunch) {
+  const Symbolic &S = c->S;
+  const int n = S.n;
+  int nl = 0;
+  const LsSkip none{nullptr, nullptr, 0};
+  for (int k0 = 0; k0 < n; k0 += c->pm_cols) {
+    const int nc = std::min(c->pm_cols, n - k0);
+    CUDA_TRY(c, cudaMemsetAsync(c->W1, 0, (size_t)n * c->ldw * 8, c->stream));
+    launch_rhs_unit(c->W1 + 0, c->ldw, c->pm_rowof_dev + k0, nc, c->stream);
+    LsSkip fw{c->pm_bits_dev, c->pm_tkey_dev + k0 / 32, c->bit_words};
+    nl += 1;
+    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), S.height, true, c->N, c->dinvN, c->W1, c->ldw, nc, fw, c->Pw, c->stream);
+    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), S.height, false, c->N, c->dinvN, c->W1, c->ldw, nc, none, c->Pw, c->stream);
+    launch_extract_lowerE(c->D, c->W1, c->ldw, k0, nc, c->YinvE, c->stream);
+    launch_dY_times(c->D, c->dY, c->W1, c->W2, c->ldw, nc, c->stream);
+    nl += 2;
+    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), S.height, true, c->Lh, c->dinvL, c->W2, c->ldw, nc, none, c->Pw, c->stream);
+    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), S.height, false, c->Lh, c->dinvL, c->W2, c->ldw, nc, none, c->Pw, c->stream);
+    launch_extract_lowerE(c->D, c->W2, c->ldw, k0, nc, c->Mlow, c->stream);
+    launch_extract_upperE(c->D, c->W2, c->ldw, k0, nc, c->Mup, c->stream);
+    nl += 2;
+  }
+  KCHECK(c);
+  *nlaunch = nl;
   return MCSDP_OK;
 }
 
@@ -474,8 +673,10 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
     launch_slot_combine(c->D, c->dY, c->dz, 0.0, -1.0, c->stream);
     k0.done(1);
     KScope k1(c, KC_PMAT);
-    launch_pmatrix(c->D, c->Lh, c->dinvL, c->N, c->dinvN, c->dY, c->YinvE, c->Mlow, c->Mup, c->stream);
-    k1.done(1);
+    int nl = 0;
+    mcsdp_status ps = phase_pmatrix(c, &nl);
+    if (ps) return ps;
+    k1.done(nl);
     KScope k2(c, KC_MISC);
     launch_dx_combine(c->D, beta * mu, Xbar, c->YinvE, c->Mlow, c->Mup, c->dX, c->stream);
     k2.done(1);
@@ -605,6 +806,9 @@ void mcsdp_default_options(mcsdp_options *o) {
   o->panel_max = 80;
   o->group_max = 64;
   o->panel_budget_mb = 1024.0;
+  o->profile = 0;
+  o->relax = 1;
+  o->solve_warps = 0;
 }
 
 const char *mcsdp_last_error(const mcsdp_ctx *c) { return c ? c->err.c_str() : "null context"; }
@@ -656,8 +860,13 @@ mcsdp_status mcsdp_create(const mcsdp_problem *p, const mcsdp_options *opt, void
   SymbolicOptions so;
   so.panel_max = c->opt.panel_max;
   so.group_max = c->opt.group_max;
+  so.relax = c->opt.relax;
   std::string e = analyze(P, so, c->S);
   if (!e.empty()) return fail(c, MCSDP_ERR_ARG, e);
+  if (c->S.max_ncol > 96 || c->S.max_nrow > 160)
+    return fail(c, MCSDP_ERR_ARG, "a clique of " + std::to_string(c->S.max_nrow) + " rows / " +
+                                      std::to_string(c->S.max_ncol) +
+                                      " columns exceeds this build's shared-memory kernels (160 / 96)");
   // default dual start
   c->z0_default.assign(P.m, 0.0);
   if (c->S.unit_diag_constraints) {
@@ -670,8 +879,14 @@ mcsdp_status mcsdp_create(const mcsdp_problem *p, const mcsdp_options *opt, void
     for (size_t t = 0; t < P.row.size(); ++t)
       if (P.mat[t] > 0) c->z0_default[P.mat[t] - 1] = -rowabs[P.row[t]] - 1.0;
   }
-  plan_workspace(c);
   c->host_only = c->opt.device < 0;
+  if (!c->host_only) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->opt.device) == cudaSuccess &&
+        sms > 0)
+      c->num_sms = sms;
+  }
+  plan_workspace(c);
   c->stream = (cudaStream_t)stream;
   if (!c->host_only) {
     c->device = c->opt.device;

@@ -125,21 +125,64 @@ std::string analyze(const ProblemData &P, const SymbolicOptions &o, Symbolic &S)
   std::vector<int> nchild(n, 0);
   for (int q = 0; q < n; ++q)
     if (par[q] >= 0) nchild[par[q]]++;
-  S.sn_col.push_back(0);
+  struct SN {
+    int c0, c1;
+    double truenz;
+    bool alive;
+  };
+  std::vector<SN> F;
+  std::vector<int> col2f(n, 0);
   for (int q = 0; q < n;) {
     int v = q;
     while (v + 1 < n && par[v] == v + 1 && nchild[v + 1] == 1 &&
            sn_struct[v].size() == sn_struct[v + 1].size() + 1)
       ++v;
-    S.sn_col.push_back(v + 1);
+    double t = 0;
+    for (int c = q; c <= v; ++c) t += 1.0 + (double)sn_struct[c].size();
+    for (int c = q; c <= v; ++c) col2f[c] = (int)F.size();
+    F.push_back({q, v + 1, t, true});
     q = v + 1;
   }
-  S.ns = (int)S.sn_col.size() - 1;
+  // ---- relaxed amalgamation: merge a supernode into its parent when it is the parent's last
+  // child (columns contiguous) and the explicit zeros this adds stay small.  The merged clique is
+  // S_child ∪ S_parent ∪ U_parent (U_child \ S_parent ⊆ U_parent by the clique-tree property), so
+  // E grows by the zeros counted here and stays chordal with the same ordering.
+  if (o.relax) {
+    for (size_t f = 0; f + 1 < F.size(); ++f) {
+      SN &a = F[f];
+      const auto &Ua = sn_struct[a.c1 - 1];
+      if (Ua.empty()) continue;
+      const int pf = col2f[Ua[0]];
+      SN &p = F[pf];
+      if (p.c0 != a.c1) continue;  // not the contiguous (last) child
+      const double k = p.c1 - a.c0;
+      const double nu = (double)sn_struct[p.c1 - 1].size();
+      if (k + nu > o.max_clique) continue;
+      const double stored = k * (k + 1) / 2 + nu * k;
+      const double z = (stored - (a.truenz + p.truenz)) / stored;
+      const bool merge = k <= 4 || (k <= 16 && z < 0.8) || (k <= 48 && z < 0.1) || z < 0.05;
+      if (!merge) continue;
+      p.c0 = a.c0;
+      p.truenz += a.truenz;
+      a.alive = false;
+      for (int c = a.c0; c < a.c1; ++c) col2f[c] = pf;
+    }
+  }
+  S.sn_col.push_back(0);
+  std::vector<std::pair<int, int>> sns;  // (c0, c1) of the surviving supernodes
+  for (auto &f : F)
+    if (f.alive) sns.push_back({f.c0, f.c1});
+  std::sort(sns.begin(), sns.end());
+  for (auto &pr : sns) S.sn_col.push_back(pr.second);
+  S.ns = (int)sns.size();
   S.col2sn.assign(n, 0);
   S.sn_rowptr.assign(S.ns + 1, 0);
   S.sn_valptr.assign(S.ns + 1, 0);
+  S.sn_dptr.assign(S.ns + 1, 0);
   for (int s = 0; s < S.ns; ++s) {
     int c0 = S.sn_col[s], c1 = S.sn_col[s + 1];
+    S.sn_dptr[s + 1] = S.sn_dptr[s] + (int64_t)(c1 - c0) * (c1 - c0);
+    if (c0 != sns[s].first) return "internal: supernode partition not contiguous";
     for (int c = c0; c < c1; ++c) S.col2sn[c] = s;
     for (int c = c0; c < c1; ++c) S.rows.push_back(c);
     for (int x : sn_struct[c1 - 1]) S.rows.push_back(x);
@@ -157,6 +200,10 @@ std::string analyze(const ProblemData &P, const SymbolicOptions &o, Symbolic &S)
     int ncol = S.sn_col[s + 1] - S.sn_col[s];
     if (nrow > ncol) S.sn_parent[s] = S.col2sn[S.rows[S.sn_rowptr[s] + ncol]];
   }
+  S.sn_fdesc.resize(S.ns);
+  for (int s = 0; s < S.ns; ++s) S.sn_fdesc[s] = s;
+  for (int s = 0; s < S.ns; ++s)
+    if (S.sn_parent[s] >= 0) S.sn_fdesc[S.sn_parent[s]] = std::min(S.sn_fdesc[S.sn_parent[s]], S.sn_fdesc[s]);
   // ---- height levels ----
   {
     std::vector<int> h(S.ns, 0);

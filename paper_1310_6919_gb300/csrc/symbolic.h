@@ -26,7 +26,9 @@ struct Symbolic {
   std::vector<int64_t> sn_rowptr;           // ns+1
   std::vector<int> rows;                    // clique rows (new indices), S_r first, ascending
   std::vector<int64_t> sn_valptr;           // ns+1
+  std::vector<int64_t> sn_dptr;             // ns+1: offsets of the ncol x ncol inverse blocks
   std::vector<int> sn_parent;               // -1 for roots
+  std::vector<int> sn_fdesc;                // smallest supernode index in the subtree of s
   std::vector<int> col2sn;                  // n
   int max_nrow = 0, max_ncol = 0;
   int64_t nnz_lower_E = 0;
@@ -82,6 +84,8 @@ struct Symbolic {
 struct SymbolicOptions {
   int panel_max = 80;
   int group_max = 64;
+  int relax = 1;          // relaxed supernode amalgamation
+  int max_clique = 96;    // amalgamation never makes a clique larger than this
 };
 
 // Returns empty string on success, else an error message.
