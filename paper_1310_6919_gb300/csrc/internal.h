@@ -8,6 +8,7 @@ namespace mcsdp {
 // Device copies of the symbolic tables (all pointers into the caller's workspace).
 struct DevSym {
   int n, m, ns, ngroup, max_nrow, max_ncol;
+  int max_grp_nnz;  // largest number of stored nonzeros (both triangles) of one SCM group
   int64_t nnzL, nslot, nnzD;
   const int *sn_col;
   const int64_t *sn_dptr;
@@ -129,8 +130,11 @@ void launch_scm_tiles(const DevSym &S, const int2 *tiles, int ntiles, const doub
 // ---------------- dense SCM factorisation (kern_dense.cu) ----------------
 // B internal, (m+1) x m lower, column-major, ld = ldb; row m holds g^T on entry and
 // (L^{-1} g)^T on exit.
-int dense_chol_bordered(double *B, int64_t ldb, int m, int *status, cudaStream_t st);
-int dense_backsolve(const double *B, int64_t ldb, int m, double *x, cudaStream_t st);
+// Linv: ceil(m / 64) blocks of 64 x 64 doubles receiving the inverses of the diagonal blocks
+int dense_chol_bordered(double *B, int64_t ldb, int m, int *status, double *Linv,
+                        cudaStream_t st);
+int dense_backsolve(const double *B, int64_t ldb, int m, const double *Linv, double *x,
+                    cudaStream_t st);
 void launch_rhs_border(const DevSym &S, double *B, int64_t ldb, const double *hvec, double betamu,
                        cudaStream_t st);
 void launch_dz_to_user(const DevSym &S, const double *dz_int, double *dz_user, cudaStream_t st);

@@ -15,189 +15,201 @@ namespace mcsdp {
 
 constexpr int NB = 64;  // panel width
 
-// Cholesky of the nb x nb diagonal block at (k0, k0), one CTA.
-__global__ void k_potrf_diag(double *B, int64_t ldb, int k0, int nb, int *status) {
-  __shared__ double A[NB * NB];
-  __shared__ double s_inv;
-  const int tid = threadIdx.x, bd = blockDim.x;
-  for (int idx = tid; idx < nb * nb; idx += bd) {
-    int i = idx % nb, j = idx / nb;
-    A[idx] = (i >= j) ? B[(k0 + i) + (int64_t)(k0 + j) * ldb] : 0.0;
+// Cholesky of the nb x nb diagonal block at (k0, k0), one CTA of 256 threads, and the inverse
+// of the factor (stored in Linv, nb x nb column-major, ld NB).  Thread (r, q) = (tid / 4, tid % 4)
+// owns row r of the block and every 4th column of the trailing update.
+__global__ void k_potrf_diag(double *B, int64_t ldb, int k0, int nb, int *status, double *Linv) {
+  extern __shared__ double smp[];
+  double *A = smp;                  // row-major, padded: A[r * (NB+1) + c]
+  double *T = smp + NB * (NB + 1);  // inverse, column-major
+  __shared__ double rdg[NB];
+  __shared__ double piv[2];
+  const int tid = threadIdx.x;
+  const int r = tid & 63, q = tid >> 6;
+  constexpr int LD = NB + 1;
+  for (int idx = tid; idx < nb * nb; idx += 256) {
+    const int i = idx % nb, j = idx / nb;
+    A[i * LD + j] = (i >= j) ? B[(k0 + i) + (int64_t)(k0 + j) * ldb] : 0.0;
   }
   __syncthreads();
+  bool bad = false;
   for (int j = 0; j < nb; ++j) {
-    if (tid == 0) {
-      double d = A[j + j * nb];
+    if (tid == 0) {  // one thread: FP64 sqrt / division are long multi-instruction sequences
+      double d = A[j * LD + j];
       if (!(d > 0.0)) {
-        atomicOr(status, ST_NOT_PD);
+        bad = true;
         d = 1.0;
       }
-      d = sqrt(d);
-      A[j + j * nb] = d;
-      s_inv = 1.0 / d;
+      const double sd = sqrt(d);
+      piv[0] = sd;
+      piv[1] = 1.0 / sd;
     }
     __syncthreads();
-    for (int i = j + 1 + tid; i < nb; i += bd) A[i + j * nb] *= s_inv;
-    __syncthreads();
-    const int w = nb - j - 1;
-    for (int idx = tid; idx < w * w; idx += bd) {
-      int kk = j + 1 + idx / w, ii = j + 1 + idx % w;
-      if (ii >= kk) A[ii + kk * nb] -= A[ii + j * nb] * A[kk + j * nb];
+    if (q == 0 && r < nb) {
+      if (r == j) A[j * LD + j] = piv[0];
+      else if (r > j) A[r * LD + j] *= piv[1];
     }
     __syncthreads();
+    if (r > j && r < nb) {
+      const double arj = A[r * LD + j];
+      for (int kk = j + 1 + q; kk <= r; kk += 4) A[r * LD + kk] -= arj * A[kk * LD + j];
+    }
+    __syncthreads();  // the next pivot is final
   }
-  for (int idx = tid; idx < nb * nb; idx += bd) {
-    int i = idx % nb, j = idx / nb;
-    if (i >= j) B[(k0 + i) + (int64_t)(k0 + j) * ldb] = A[idx];
-  }
-}
-
-// Rows [r0, rend) of the panel columns [k0, k0+nb): X <- X L_kk^{-T}.  One warp per 8 rows,
-// lanes over columns; the dependency along the columns is resolved by shuffles.
-constexpr int TRSM_ROWS_PER_WARP = 8;
-constexpr int TRSM_WARPS = 4;
-
-__global__ void k_trsm_panel(double *B, int64_t ldb, int k0, int nb, int r0, int rend) {
-  __shared__ double L[NB * NB];
-  __shared__ double rdiag[NB];
-  const int tid = threadIdx.x, bd = blockDim.x;
-  for (int idx = tid; idx < nb * nb; idx += bd) {
-    int i = idx % nb, j = idx / nb;
-    L[idx] = (i >= j) ? B[(k0 + i) + (int64_t)(k0 + j) * ldb] : 0.0;
-  }
+  if (bad && tid == 0) atomicOr(status, ST_NOT_PD);
   __syncthreads();
-  for (int j = tid; j < nb; j += bd) rdiag[j] = 1.0 / L[j + j * nb];
+  if (tid < nb) rdg[tid] = 1.0 / A[tid * LD + tid];
   __syncthreads();
-  const int warp = tid >> 5, lane = tid & 31;
-  const int rbase = r0 + (blockIdx.x * TRSM_WARPS + warp) * TRSM_ROWS_PER_WARP;
-  double acc0[TRSM_ROWS_PER_WARP], acc1[TRSM_ROWS_PER_WARP];
-#pragma unroll
-  for (int q = 0; q < TRSM_ROWS_PER_WARP; ++q) {
-    const int row = rbase + q;
-    acc0[q] = (row < rend && lane < nb) ? B[row + (int64_t)(k0 + lane) * ldb] : 0.0;
-    acc1[q] = (row < rend && lane + 32 < nb) ? B[row + (int64_t)(k0 + lane + 32) * ldb] : 0.0;
-  }
-  for (int c = 0; c < nb; ++c) {
-    const int owner = c & 31;
-    const bool hi = c >= 32;
-#pragma unroll
-    for (int q = 0; q < TRSM_ROWS_PER_WARP; ++q) {
-      double mine = hi ? acc1[q] : acc0[q];
-      double xc = __shfl_sync(0xffffffffu, mine, owner) * rdiag[c];
-      if (lane == owner) {
-        if (hi) acc1[q] = xc;
-        else acc0[q] = xc;
+  // inverse of the lower-triangular factor: column j of T by forward substitution
+  if (tid < nb) {
+    const int j = tid;
+    T[j + j * NB] = rdg[j];
+    for (int i = j + 1; i < nb; ++i) {
+      double s0 = 0.0, s1 = 0.0;
+      int l = j;
+      for (; l + 1 < i; l += 2) {
+        s0 = fma(A[i * LD + l], T[l + j * NB], s0);
+        s1 = fma(A[i * LD + l + 1], T[l + 1 + j * NB], s1);
       }
-      // columns c' > c owned by this lane
-      if (lane > c && lane < nb) acc0[q] = fma(-xc, L[lane + c * nb], acc0[q]);
-      if (lane + 32 > c && lane + 32 < nb) acc1[q] = fma(-xc, L[(lane + 32) + c * nb], acc1[q]);
+      if (l < i) s0 = fma(A[i * LD + l], T[l + j * NB], s0);
+      T[i + j * NB] = -(s0 + s1) * rdg[i];
     }
+    for (int i = 0; i < j; ++i) T[i + j * NB] = 0.0;
   }
+  __syncthreads();
+  for (int idx = tid; idx < nb * nb; idx += 256) {
+    const int i = idx % nb, j = idx / nb;
+    if (i >= j) B[(k0 + i) + (int64_t)(k0 + j) * ldb] = A[i * LD + j];
+    Linv[i + j * NB] = T[i + j * NB];
+  }
+}
+
+// Rows [r0, rend) of the panel columns [k0, k0+nb): X <- X L_kk^{-T} = X Linv^T.  CTA = 16 rows
+// x nb columns (256 threads, 4 outputs each), so the panel solve spreads over many SMs.
+constexpr int TRSM_ROWS = 16;
+__global__ void k_trsm_panel(double *B, int64_t ldb, int k0, int nb, int r0, int rend,
+                             const double *__restrict__ Linv) {
+  extern __shared__ double smt[];
+  double *Xs = smt;                   // [l][row], TRSM_ROWS rows
+  double *Ts = smt + NB * TRSM_ROWS;  // [l][col] = Linv[col][l]
+  const int tid = threadIdx.x;
+  const int rb = r0 + blockIdx.x * TRSM_ROWS;
+  for (int idx = tid; idx < nb * TRSM_ROWS; idx += 256) {
+    const int rr = idx % TRSM_ROWS, l = idx / TRSM_ROWS;
+    const int gi = rb + rr;
+    Xs[l * TRSM_ROWS + rr] = (gi < rend) ? B[gi + (int64_t)(k0 + l) * ldb] : 0.0;
+  }
+  for (int idx = tid; idx < nb * 64; idx += 256) {
+    const int cc = idx % 64, l = idx / 64;
+    Ts[l * 64 + cc] = (cc < nb) ? Linv[cc + l * NB] : 0.0;
+  }
+  __syncthreads();
+  const int tx = tid & 15, ty = tid >> 4;  // row ty, columns tx*4 .. tx*4+3
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int l = 0; l < nb; ++l) {
+    const double a = Xs[l * TRSM_ROWS + ty];
 #pragma unroll
-  for (int q = 0; q < TRSM_ROWS_PER_WARP; ++q) {
-    const int row = rbase + q;
-    if (row < rend) {
-      if (lane < nb) B[row + (int64_t)(k0 + lane) * ldb] = acc0[q];
-      if (lane + 32 < nb) B[row + (int64_t)(k0 + lane + 32) * ldb] = acc1[q];
+    for (int t = 0; t < 4; ++t) acc[t] = fma(a, Ts[l * 64 + tx * 4 + t], acc[t]);
+  }
+  const int gi = rb + ty;
+  if (gi < rend) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int c = tx * 4 + t;
+      if (c < nb) B[gi + (int64_t)(k0 + c) * ldb] = acc[t];
     }
   }
 }
 
-// Trailing update C -= P P^T on the lower 64 x 64 tiles of rows [r0, rend), columns [r0, cend).
-// P = columns [k0, k0+nb) of the rows.  256 threads, 4 x 4 register blocking.
+// Trailing update C -= P P^T on the lower TS x TS tiles of rows [r0, rend), columns [r0, cend).
+// P = columns [k0, k0+nb) of the rows.  256 threads, 2 x 2 register blocking; small tiles keep
+// all SMs busy on the later panels (one FP64 tile of 64 x 64 x 64 would take ~60 us on one SM).
+constexpr int TS = 32;
 __global__ void k_syrk_tiles(double *B, int64_t ldb, int k0, int nb, int r0, int rend, int cend) {
   extern __shared__ double smd[];
-  double *Ai = smd;              // [nb][64] (k-major)
-  double *Aj = smd + NB * 64;    // [nb][64]
-  // tile index -> (ti, tj), ti >= tj
+  double *Ai = smd;             // [nb][TS] (k-major)
+  double *Aj = smd + NB * TS;   // [nb][TS]
   const int t = blockIdx.x;
   int ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
   while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
   while (ti * (ti + 1) / 2 > t) --ti;
   const int tj = t - ti * (ti + 1) / 2;
-  const int rb = r0 + ti * 64, cb = r0 + tj * 64;
+  const int rb = r0 + ti * TS, cb = r0 + tj * TS;
   if (cb >= cend) return;
   const int tid = threadIdx.x;
-  for (int idx = tid; idx < nb * 64; idx += 256) {
-    const int r = idx % 64, l = idx / 64;
-    const int gi = rb + r, gj = cb + r;
-    Ai[l * 64 + r] = (gi < rend) ? B[gi + (int64_t)(k0 + l) * ldb] : 0.0;
-    Aj[l * 64 + r] = (gj < rend) ? B[gj + (int64_t)(k0 + l) * ldb] : 0.0;
+  for (int idx = tid; idx < nb * TS; idx += 256) {
+    const int rr = idx % TS, l = idx / TS;
+    const int gi = rb + rr, gj = cb + rr;
+    Ai[l * TS + rr] = (gi < rend) ? B[gi + (int64_t)(k0 + l) * ldb] : 0.0;
+    Aj[l * TS + rr] = (gj < rend) ? B[gj + (int64_t)(k0 + l) * ldb] : 0.0;
   }
   __syncthreads();
   const int tx = tid & 15, ty = tid >> 4;
-  double acc[4][4] = {};
+  double acc[2][2] = {};
   for (int l = 0; l < nb; ++l) {
-    double a[4], b[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      a[q] = Ai[l * 64 + ty * 4 + q];
-      b[q] = Aj[l * 64 + tx * 4 + q];
-    }
-#pragma unroll
-    for (int p = 0; p < 4; ++p)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[p][q] = fma(a[p], b[q], acc[p][q]);
+    const double a0 = Ai[l * TS + ty * 2], a1 = Ai[l * TS + ty * 2 + 1];
+    const double b0 = Aj[l * TS + tx * 2], b1 = Aj[l * TS + tx * 2 + 1];
+    acc[0][0] = fma(a0, b0, acc[0][0]);
+    acc[0][1] = fma(a0, b1, acc[0][1]);
+    acc[1][0] = fma(a1, b0, acc[1][0]);
+    acc[1][1] = fma(a1, b1, acc[1][1]);
   }
 #pragma unroll
-  for (int p = 0; p < 4; ++p) {
-    const int gi = rb + ty * 4 + p;
+  for (int p = 0; p < 2; ++p) {
+    const int gi = rb + ty * 2 + p;
     if (gi >= rend) continue;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int gj = cb + tx * 4 + q;
+    for (int q = 0; q < 2; ++q) {
+      const int gj = cb + tx * 2 + q;
       if (gj < cend && gi >= gj) B[gi + (int64_t)gj * ldb] -= acc[p][q];
     }
   }
 }
 
-int dense_chol_bordered(double *B, int64_t ldb, int m, int *status, cudaStream_t st) {
+int dense_chol_bordered(double *B, int64_t ldb, int m, int *status, double *Linv_all,
+                        cudaStream_t st) {
+  const int smem_potrf = (NB * (NB + 1) + NB * NB) * (int)sizeof(double);
+  const int smem_trsm = (NB * TRSM_ROWS + NB * 64) * (int)sizeof(double);
+  const int smem_tile = 2 * NB * TS * (int)sizeof(double);
   static bool configured = false;
   if (!configured) {
-    cudaFuncSetAttribute(k_syrk_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(2 * NB * 64 * sizeof(double)));
+    cudaFuncSetAttribute(k_syrk_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_tile);
+    cudaFuncSetAttribute(k_trsm_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_trsm);
+    cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_potrf);
     configured = true;
   }
   const int rows = m + 1;  // including the border row
   int launches = 0;
   for (int k0 = 0; k0 < m; k0 += NB) {
     const int nb = (m - k0) < NB ? (m - k0) : NB;
-    k_potrf_diag<<<1, 256, 0, st>>>(B, ldb, k0, nb, status);
+    double *Linv = Linv_all + (int64_t)(k0 / NB) * NB * NB;
+    k_potrf_diag<<<1, 256, smem_potrf, st>>>(B, ldb, k0, nb, status, Linv);
     ++launches;
     const int r0 = k0 + nb;
     const int nr = rows - r0;
     if (nr > 0) {
-      const int per_cta = TRSM_WARPS * TRSM_ROWS_PER_WARP;
-      k_trsm_panel<<<(nr + per_cta - 1) / per_cta, 32 * TRSM_WARPS, 0, st>>>(B, ldb, k0, nb, r0, rows);
-      const int nt = (nr + 63) / 64;
+      k_trsm_panel<<<(nr + TRSM_ROWS - 1) / TRSM_ROWS, 256, smem_trsm, st>>>(B, ldb, k0, nb, r0, rows, Linv);
+      const int nt = (nr + TS - 1) / TS;
       const int ntiles = nt * (nt + 1) / 2;
-      k_syrk_tiles<<<ntiles, 256, 2 * NB * 64 * sizeof(double), st>>>(B, ldb, k0, nb, r0, rows, m);
+      k_syrk_tiles<<<ntiles, 256, smem_tile, st>>>(B, ldb, k0, nb, r0, rows, m);
       launches += 2;
     }
   }
   return launches;
 }
 
-// Backward substitution L^T x = y, y = row m of B, blocks of 64 from the bottom.
-__global__ void k_bs_diag(const double *B, int64_t ldb, int b0, int nb, double *x) {
-  // one warp: x[b0..b0+nb) <- L_bb^{-T} x[b0..b0+nb)
-  const int lane = threadIdx.x;
-  double x0 = (lane < nb) ? x[b0 + lane] : 0.0;
-  double x1 = (lane + 32 < nb) ? x[b0 + lane + 32] : 0.0;
-  for (int c = nb - 1; c >= 0; --c) {
-    const int owner = c & 31;
-    const bool hi = c >= 32;
-    double mine = hi ? x1 : x0;
-    double xc = __shfl_sync(0xffffffffu, mine, owner) / B[(b0 + c) + (int64_t)(b0 + c) * ldb];
-    if (lane == owner) {
-      if (hi) x1 = xc;
-      else x0 = xc;
-    }
-    if (lane < c) x0 = fma(-xc, B[(b0 + c) + (int64_t)(b0 + lane) * ldb], x0);
-    if (lane + 32 < c) x1 = fma(-xc, B[(b0 + c) + (int64_t)(b0 + lane + 32) * ldb], x1);
+// Backward substitution L^T x = y, y = row m of B, blocks of 64 from the bottom; the diagonal
+// block step is x_b <- Linv_b^T x_b with the inverses stored by the factorisation.
+__global__ void k_bs_diag(const double *__restrict__ Linv, int b0, int nb, double *x) {
+  __shared__ double xs[NB];
+  const int t = threadIdx.x;
+  if (t < nb) xs[t] = x[b0 + t];
+  __syncthreads();
+  if (t < nb) {
+    double acc = 0.0;
+    for (int i = t; i < nb; ++i) acc = fma(Linv[i + t * NB], xs[i], acc);  // Linv[i][t]
+    x[b0 + t] = acc;
   }
-  if (lane < nb) x[b0 + lane] = x0;
-  if (lane + 32 < nb) x[b0 + lane + 32] = x1;
 }
 
 // x[j] -= sum_{i in block} L[i][j] x[i] for j < b0
@@ -207,9 +219,14 @@ __global__ void k_bs_update(const double *B, int64_t ldb, int b0, int nb, double
   __syncthreads();
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < b0; j += gridDim.x * blockDim.x) {
     const double *col = B + (int64_t)j * ldb + b0;
-    double acc = 0.0;
-    for (int i = 0; i < nb; ++i) acc = fma(col[i], xb[i], acc);
-    x[j] -= acc;
+    double a0 = 0.0, a1 = 0.0;
+    int i = 0;
+    for (; i + 1 < nb; i += 2) {
+      a0 = fma(col[i], xb[i], a0);
+      a1 = fma(col[i + 1], xb[i + 1], a1);
+    }
+    if (i < nb) a0 = fma(col[i], xb[i], a0);
+    x[j] -= a0 + a1;
   }
 }
 
@@ -218,14 +235,15 @@ __global__ void k_copy_border(const double *B, int64_t ldb, int m, double *x) {
     x[j] = B[m + (int64_t)j * ldb];
 }
 
-int dense_backsolve(const double *B, int64_t ldb, int m, double *x, cudaStream_t st) {
+int dense_backsolve(const double *B, int64_t ldb, int m, const double *Linv_all, double *x,
+                    cudaStream_t st) {
   k_copy_border<<<(m + 255) / 256, 256, 0, st>>>(B, ldb, m, x);
   int launches = 1;
   const int nblk = (m + NB - 1) / NB;
   for (int bk = nblk - 1; bk >= 0; --bk) {
     const int b0 = bk * NB;
     const int nb = (m - b0) < NB ? (m - b0) : NB;
-    k_bs_diag<<<1, 32, 0, st>>>(B, ldb, b0, nb, x);
+    k_bs_diag<<<1, NB, 0, st>>>(Linv_all + (int64_t)bk * NB * NB, b0, nb, x);
     ++launches;
     if (b0 > 0) {
       k_bs_update<<<(b0 + 127) / 128, 128, 0, st>>>(B, ldb, b0, nb, x);

@@ -29,29 +29,58 @@ __device__ __forceinline__ bool ls_skip(const LsSkip &sk, int t, int tile) {
   return true;
 }
 
-// acc[c][lane] -= sum over updates [ub, ue) of target t of L_d[rows in S_t, :] W[S_d]
+// acc[c][lane] -= sum over updates [ub, ue) of target t of L_d[rows in S_t, :] W[S_d].
+// Each update block L_d[p1:p2, j0:j0+8] is loaded by the 32 lanes together into the warp's stage
+// (one memory round trip), the 8 source values per lane in parallel with it.
 __device__ __forceinline__ void lfwd_pull(const DevSym &S, int ub, int ue, const double *L,
                                           const double *Wc, int64_t ldw, bool act, double *acc,
-                                          int lane) {
-  for (int u = ub; u < ue; ++u) {
-    const int d = S.upd_src[u], p1 = S.upd_p1[u], p2 = S.upd_p2[u];
-    const int *rel = S.upd_rel + S.upd_relptr[u];
-    const int dc0 = S.sn_col[d];
-    const int dncol = S.sn_col[d + 1] - dc0;
-    const int dnrow = (int)(S.sn_rowptr[d + 1] - S.sn_rowptr[d]);
-    const double *Ld = L + S.sn_valptr[d];
-    for (int j0 = 0; j0 < dncol; j0 += LS_CH) {
-      const int cw = dncol - j0 < LS_CH ? dncol - j0 : LS_CH;
-      double x[LS_CH];
+                                          double *stg, int *srel, int lane) {
+  for (int u0 = ub; u0 < ue; u0 += 32) {
+    // metadata of up to 32 updates, one per lane, then broadcast by shuffles
+    int m_p1 = 0, m_np = 0, m_dc0 = 0, m_dncol = 0, m_dnrow = 0;
+    int64_t m_rel = 0, m_val = 0;
+    if (u0 + lane < ue) {
+      const int u = u0 + lane;
+      const int d = S.upd_src[u];
+      m_p1 = S.upd_p1[u];
+      m_np = S.upd_p2[u] - m_p1;
+      m_rel = S.upd_relptr[u];
+      m_dc0 = S.sn_col[d];
+      m_dncol = S.sn_col[d + 1] - m_dc0;
+      m_dnrow = (int)(S.sn_rowptr[d + 1] - S.sn_rowptr[d]);
+      m_val = S.sn_valptr[d];
+    }
+    const int cnt = ue - u0 < 32 ? ue - u0 : 32;
+    for (int k = 0; k < cnt; ++k) {
+      const int p1 = __shfl_sync(0xffffffffu, m_p1, k);
+      const int np = __shfl_sync(0xffffffffu, m_np, k);
+      const int dc0 = __shfl_sync(0xffffffffu, m_dc0, k);
+      const int dncol = __shfl_sync(0xffffffffu, m_dncol, k);
+      const int dnrow = __shfl_sync(0xffffffffu, m_dnrow, k);
+      const int64_t relp = __shfl_sync(0xffffffffu, m_rel, k);
+      const int64_t valp = __shfl_sync(0xffffffffu, m_val, k);
+      const int *rel = S.upd_rel + relp;
+      const double *Ld = L + valp;
+      for (int p = lane; p < np; p += 32) srel[p] = rel[p];
+      for (int j0 = 0; j0 < dncol; j0 += LS_CH) {
+        const int cw = dncol - j0 < LS_CH ? dncol - j0 : LS_CH;
+        double x[LS_CH];
 #pragma unroll
-      for (int q = 0; q < LS_CH; ++q) x[q] = (q < cw && act) ? Wc[(int64_t)(dc0 + j0 + q) * ldw] : 0.0;
-      const double *base = Ld + (int64_t)j0 * dnrow;
-      for (int p = p1; p < p2; ++p) {
-        double a = 0.0;
+        for (int q = 0; q < LS_CH; ++q) x[q] = (q < cw && act) ? Wc[(int64_t)(dc0 + j0 + q) * ldw] : 0.0;
+        const double *base = Ld + (int64_t)j0 * dnrow + p1;
+        for (int e = lane; e < np * cw; e += 32) {
+          const int p = e % np, q = e / np;
+          stg[q * np + p] = base[p + (int64_t)q * dnrow];
+        }
+        __syncwarp();
+        for (int p = 0; p < np; ++p) {
+          double a = 0.0;
 #pragma unroll
-        for (int q = 0; q < LS_CH; ++q)
-          if (q < cw) a = fma(base[p + (int64_t)q * dnrow], x[q], a);
-        acc[rel[p - p1] * 32 + lane] -= a;
+          for (int q = 0; q < LS_CH; ++q)
+            if (q < cw) a = fma(stg[q * np + p], x[q], a);
+          acc[srel[p] * 32 + lane] -= a;
+        }
+        __syncwarp();
       }
     }
   }
@@ -62,6 +91,8 @@ __global__ void k_lfwd_partial(DevSym S, int x0, int ntiles, const double *__res
                                const double *__restrict__ W, int64_t ldw, int ncolsW,
                                LsSkip sk, double *Pw) {
   extern __shared__ double acc[];
+  double *stg = acc + S.max_ncol * 32;
+  int *srel = reinterpret_cast<int *>(stg + LS_CH * S.max_nrow);
   const int lane = threadIdx.x;
   const int x = x0 + blockIdx.x / ntiles;
   const int tile = blockIdx.x % ntiles;
@@ -71,7 +102,7 @@ __global__ void k_lfwd_partial(DevSym S, int x0, int ntiles, const double *__res
   const bool act = col < ncolsW;
   const int ncol = S.sn_col[t + 1] - S.sn_col[t];
   for (int c = 0; c < ncol; ++c) acc[c * 32 + lane] = 0.0;
-  lfwd_pull(S, S.xch_ub[x], S.xch_ue[x], L, W + (act ? col : 0), ldw, act, acc, lane);
+  lfwd_pull(S, S.xch_ub[x], S.xch_ue[x], L, W + (act ? col : 0), ldw, act, acc, stg, srel, lane);
   double *P = Pw + S.xch_slotw[x] * ldw + (act ? col : 0);
   if (act)
     for (int c = 0; c < ncol; ++c) P[(int64_t)c * ldw] = acc[c * 32 + lane];
@@ -80,7 +111,9 @@ __global__ void k_lfwd_partial(DevSym S, int x0, int ntiles, const double *__res
 __global__ void k_lfwd(DevSym S, int lvl_begin, int ntiles, const double *__restrict__ L,
                        const double *__restrict__ Dall, double *W, int64_t ldw, int ncolsW,
                        LsSkip sk, const double *__restrict__ Pw) {
-  extern __shared__ double acc[];  // [ncol][32]
+  extern __shared__ double acc[];  // [ncol][32], then the update stage
+  double *stg = acc + S.max_ncol * 32;
+  int *srel = reinterpret_cast<int *>(stg + LS_CH * S.max_nrow);
   const int lane = threadIdx.x;
   const int t = S.lvl_sn[lvl_begin + blockIdx.x / ntiles];
   const int tile = blockIdx.x % ntiles;
@@ -91,10 +124,21 @@ __global__ void k_lfwd(DevSym S, int lvl_begin, int ntiles, const double *__rest
   const int ncol = S.sn_col[t + 1] - c0;
   double *Wc = W + (act ? col : 0);
   for (int c = 0; c < ncol; ++c) acc[c * 32 + lane] = act ? Wc[(int64_t)(c0 + c) * ldw] : 0.0;
-  lfwd_pull(S, S.upd_ptr[t], S.upd_c0end[t], L, Wc, ldw, act, acc, lane);
-  for (int x = S.xch_beg[t]; x < S.xch_end[t]; ++x) {
-    const double *P = Pw + S.xch_slotw[x] * ldw + (act ? col : 0);
-    for (int c = 0; c < ncol; ++c) acc[c * 32 + lane] += act ? P[(int64_t)c * ldw] : 0.0;
+  lfwd_pull(S, S.upd_ptr[t], S.upd_c0end[t], L, Wc, ldw, act, acc, stg, srel, lane);
+  const int xb = S.xch_beg[t], xe = S.xch_end[t];
+  if (act && xe > xb) {
+    for (int c = 0; c < ncol; ++c) {
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int x = xb;
+      for (; x + 3 < xe; x += 4) {
+        s0 += Pw[(S.xch_slotw[x] + c) * ldw + col];
+        s1 += Pw[(S.xch_slotw[x + 1] + c) * ldw + col];
+        s2 += Pw[(S.xch_slotw[x + 2] + c) * ldw + col];
+        s3 += Pw[(S.xch_slotw[x + 3] + c) * ldw + col];
+      }
+      for (; x < xe; ++x) s0 += Pw[(S.xch_slotw[x] + c) * ldw + col];
+      acc[c * 32 + lane] += (s0 + s1) + (s2 + s3);
+    }
   }
   const double *D = Dall + S.sn_dptr[t];
   for (int i = 0; i < ncol; ++i) {
@@ -133,14 +177,18 @@ __global__ void k_lbwd(DevSym S, int lvl_begin, int ntiles, const double *__rest
     for (int q = 0; q < LS_CH; ++q) a[q] = (q < cw && act) ? Wc[(int64_t)(c0 + j0 + q) * ldw] : 0.0;
     const double *base = Lt + (int64_t)j0 * nrow;
     int p = ncol;
-    for (; p + 1 < nrow; p += 2) {
+    for (; p + 3 < nrow; p += 4) {
       const double w0 = act ? Wc[(int64_t)rw[p] * ldw] : 0.0;
       const double w1 = act ? Wc[(int64_t)rw[p + 1] * ldw] : 0.0;
+      const double w2 = act ? Wc[(int64_t)rw[p + 2] * ldw] : 0.0;
+      const double w3 = act ? Wc[(int64_t)rw[p + 3] * ldw] : 0.0;
 #pragma unroll
       for (int q = 0; q < LS_CH; ++q)
         if (q < cw) {
           a[q] = fma(-base[p + (int64_t)q * nrow], w0, a[q]);
           a[q] = fma(-base[p + 1 + (int64_t)q * nrow], w1, a[q]);
+          a[q] = fma(-base[p + 2 + (int64_t)q * nrow], w2, a[q]);
+          a[q] = fma(-base[p + 3 + (int64_t)q * nrow], w3, a[q]);
         }
     }
     for (; p < nrow; ++p) {
@@ -172,7 +220,7 @@ int lsolve(const DevSym &S, const int *lvl_ptr_host, const int *lvl_xptr_host, i
            double *Pw, cudaStream_t st) {
   if (ncolsW <= 0) return 0;
   const int ntiles = (ncolsW + 31) / 32;
-  const size_t smem = (size_t)S.max_ncol * 32 * 8;
+  const size_t smem = (size_t)S.max_ncol * 32 * 8 + (size_t)LS_CH * S.max_nrow * 8 + (size_t)S.max_nrow * 4 + 16;
   static size_t configured = 0;
   if (smem > 48 * 1024 && smem > configured) {
     cudaFuncSetAttribute(k_lfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -41,21 +41,42 @@ __global__ void k_scm_tiles(DevSym S, const int2 *__restrict__ tiles,
   __syncthreads();
   const int i0 = S.grp_cptr[h], nh = S.grp_cptr[h + 1] - i0;
   const int j0 = S.grp_cptr[g], ng = S.grp_cptr[g + 1] - j0;
+  // nonzero lists of J_h and J_g in shared memory: (offset into Xs/Ys column, value)
+  const int hb = S.anz_ptr[i0], hn = S.anz_ptr[i0 + nh] - hb;
+  const int gb = S.anz_ptr[j0], gn = S.anz_ptr[j0 + ng] - gb;
+  double *hv = Ys + ph * pg;
+  double *gv = hv + hn;
+  int *ha = reinterpret_cast<int *>(gv + gn);  // a (row of Xs) | b << 16 (row of Ys)
+  int *ga = ha + hn;                           // c * ph | d * ph << 16 packed as two shorts
+  int *gd = ga + gn;
+  for (int e = tid; e < hn; e += bd) {
+    hv[e] = S.anz_v[hb + e];
+    ha[e] = S.anz_a[hb + e] | (S.anz_b[hb + e] << 16);
+  }
+  for (int e = tid; e < gn; e += bd) {
+    gv[e] = S.anz_v[gb + e];
+    ga[e] = S.anz_a[gb + e] * ph;
+    gd[e] = S.anz_b[gb + e] * ph;
+  }
+  __syncthreads();
   for (int idx = tid; idx < nh * ng; idx += bd) {
-    const int i = i0 + idx % nh, j = j0 + idx / nh;
+    const int ii = idx % nh, jj = idx / nh;
+    const int i = i0 + ii, j = j0 + jj;
     if (h == g && i < j) continue;
     double acc = 0.0;
-    const int ub = S.anz_ptr[j], ue = S.anz_ptr[j + 1];
-    for (int t = S.anz_ptr[i]; t < S.anz_ptr[i + 1]; ++t) {
-      const int a = S.anz_a[t], b = S.anz_b[t];
+    const int ub = S.anz_ptr[j] - gb, ue = S.anz_ptr[j + 1] - gb;
+    for (int t = S.anz_ptr[i] - hb; t < S.anz_ptr[i + 1] - hb; ++t) {
+      const int a = ha[t] & 0xffff, b = ha[t] >> 16;
       const double *xr = Xs + a;
       const double *yr = Ys + b;
-      double s = 0.0;
-      for (int u = ub; u < ue; ++u) {
-        const int c = S.anz_a[u], d = S.anz_b[u];
-        s = fma(S.anz_v[u] * xr[c * ph], yr[d * ph], s);
+      double s0 = 0.0, s1 = 0.0;
+      int u = ub;
+      for (; u + 1 < ue; u += 2) {
+        s0 = fma(gv[u] * xr[ga[u]], yr[gd[u]], s0);
+        s1 = fma(gv[u + 1] * xr[ga[u + 1]], yr[gd[u + 1]], s1);
       }
-      acc = fma(S.anz_v[t], s, acc);
+      if (u < ue) s0 = fma(gv[u] * xr[ga[u]], yr[gd[u]], s0);
+      acc = fma(hv[t], s0 + s1, acc);
     }
     B[i + (int64_t)j * ldb] = acc;
   }
@@ -74,8 +95,8 @@ void launch_scm_tiles(const DevSym &S, const int2 *tiles, int ntiles, const doub
                       const double *WY, int64_t ldw, const int *goff, double *B, int64_t ldb,
                       double *hvec, int pmax, cudaStream_t st) {
   if (ntiles <= 0) return;
-  // two |P_h| x |P_g| blocks in shared memory; pmax = widest panel (<= 96)
-  size_t smem = (size_t)2 * pmax * pmax * 8;
+  // two |P_h| x |P_g| blocks plus the nonzero lists of two groups in shared memory
+  size_t smem = (size_t)2 * pmax * pmax * 8 + (size_t)2 * S.max_grp_nnz * (8 + 8) + 64;
   static size_t configured = 0;
   if (smem > configured) {
     cudaFuncSetAttribute(k_scm_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -70,13 +70,20 @@ __device__ void chol_panel_smem(double *F, int nrow, int ncol, int *status_word,
 // inverse of the leading ncol x ncol lower block of F (ld = nrow) into D (ld = ncol), one thread
 // per column, forward substitution
 __device__ void tri_inverse_smem(const double *F, int ld, int ncol, double *D) {
+  // diagonal reciprocals first (one division per column), then column j by forward substitution
+  for (int j = threadIdx.x; j < ncol; j += blockDim.x) D[j + (int64_t)j * ncol] = 1.0 / F[j + (int64_t)j * ld];
+  __syncthreads();
   for (int j = threadIdx.x; j < ncol; j += blockDim.x) {
     for (int i = 0; i < j; ++i) D[i + (int64_t)j * ncol] = 0.0;
-    D[j + (int64_t)j * ncol] = 1.0 / F[j + (int64_t)j * ld];
     for (int i = j + 1; i < ncol; ++i) {
-      double s = 0.0;
-      for (int l = j; l < i; ++l) s = fma(F[i + (int64_t)l * ld], D[l + (int64_t)j * ncol], s);
-      D[i + (int64_t)j * ncol] = -s / F[i + (int64_t)i * ld];
+      double s0 = 0.0, s1 = 0.0;
+      int l = j;
+      for (; l + 1 < i; l += 2) {
+        s0 = fma(F[i + (int64_t)l * ld], D[l + (int64_t)j * ncol], s0);
+        s1 = fma(F[i + (int64_t)(l + 1) * ld], D[l + 1 + (int64_t)j * ncol], s1);
+      }
+      if (l < i) s0 = fma(F[i + (int64_t)l * ld], D[l + (int64_t)j * ncol], s0);
+      D[i + (int64_t)j * ncol] = -(s0 + s1) * D[i + (int64_t)i * ncol];
     }
   }
 }

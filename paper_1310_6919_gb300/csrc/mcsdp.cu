@@ -86,7 +86,7 @@ struct mcsdp_ctx {
   double *Lh = nullptr, *dinvL = nullptr, *dY = nullptr, *dX = nullptr, *YinvE = nullptr;
   double *Mlow = nullptr, *Mup = nullptr, *B = nullptr, *hvec = nullptr, *xs = nullptr;
   double *dz = nullptr, *W1 = nullptr, *W2 = nullptr, *Ncand = nullptr, *dinvCand = nullptr;
-  double *Pw = nullptr, *Pf = nullptr;
+  double *Pw = nullptr, *Pf = nullptr, *Binv = nullptr;
   double *alpha_c = nullptr, *alpha_r = nullptr, *scal = nullptr;
   int *status = nullptr, *rowof_dev = nullptr, *goff_dev = nullptr, *pm_rowof_dev = nullptr;
   int2 *tiles_dev = nullptr, *tkey_dev = nullptr, *pm_tkey_dev = nullptr;
@@ -240,7 +240,7 @@ void plan_workspace(mcsdp_ctx *c) {
   // pattern receives an update from nearly every clique) gets its extra chunks summed in
   // parallel by partial kernels, then added in fixed order (deterministic) ----
   {
-    const double chunk_work = 256.0;
+    const double chunk_work = 1024.0;
     c->upd_c0end.assign(S.ns, 0);
     c->xch_beg.assign(S.ns, 0);
     c->xch_end.assign(S.ns, 0);
@@ -391,6 +391,7 @@ void plan_workspace(mcsdp_ctx *c) {
   plan_buf(c, cur, "Mup", nnzL * 8);
   plan_buf(c, cur, "B", (size_t)c->ldb * m * 8);
   plan_buf(c, cur, "hvec", (size_t)m * 8);
+  plan_buf(c, cur, "Binv", (size_t)((m + 63) / 64) * 64 * 64 * 8);
   plan_buf(c, cur, "xs", (size_t)m * 8);
   plan_buf(c, cur, "dz", (size_t)m * 8);
   plan_buf(c, cur, "W1", (size_t)n * c->ldw * 8);
@@ -420,6 +421,9 @@ void bind_pointers(mcsdp_ctx *c) {
   D.ngroup = S.ngroup;
   D.max_nrow = S.max_nrow;
   D.max_ncol = S.max_ncol;
+  D.max_grp_nnz = 0;
+  for (int g = 0; g < S.ngroup; ++g)
+    D.max_grp_nnz = std::max(D.max_grp_nnz, S.anz_ptr[S.grp_cptr[g + 1]] - S.anz_ptr[S.grp_cptr[g]]);
   D.nnzL = S.sn_valptr[S.ns];
   D.nslot = S.nslot;
   D.nnzD = S.sn_dptr[S.ns];
@@ -483,6 +487,7 @@ void bind_pointers(mcsdp_ctx *c) {
   c->Mup = wsp<double>(c, "Mup");
   c->B = wsp<double>(c, "B");
   c->hvec = wsp<double>(c, "hvec");
+  c->Binv = wsp<double>(c, "Binv");
   c->xs = wsp<double>(c, "xs");
   c->dz = wsp<double>(c, "dz");
   c->W1 = wsp<double>(c, "W1");
@@ -659,9 +664,9 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
     launch_rhs_border(c->D, c->B, c->ldb, c->hvec, beta * mu, c->stream);
     k0.done(1);
     KScope k1(c, KC_CHOL);
-    k1.done(dense_chol_bordered(c->B, c->ldb, m, c->status + 2, c->stream));
+    k1.done(dense_chol_bordered(c->B, c->ldb, m, c->status + 2, c->Binv, c->stream));
     KScope k2(c, KC_BSOLVE);
-    int nl = dense_backsolve(c->B, c->ldb, m, c->xs, c->stream);
+    int nl = dense_backsolve(c->B, c->ldb, m, c->Binv, c->xs, c->stream);
     launch_dz_to_user(c->D, c->xs, c->dz, c->stream);
     k2.done(nl + 1);
   }
