@@ -190,6 +190,23 @@ typedef struct {
 mcsdp_status mcsdp_work_model(const mcsdp_ctx *ctx, mcsdp_work *w);
 mcsdp_status mcsdp_stats_reset(mcsdp_ctx *ctx);
 
+/* Schur complement equation solve that allocates nothing: x = B^{-1} g for a symmetric positive
+ * definite B (lower triangle read, column-major, leading dimension ldb >= m; device), g and x
+ * device vectors of length m.  The paper has no counterpart: this entry point exists for callers
+ * that cannot allocate device memory on their code path, e.g. code whose device memory is owned
+ * by another framework's caching allocator that has already reserved the device, or a loop that
+ * must not pay for a synchronising allocation.  Its working copy of B and the inverses of the
+ * diagonal blocks live in one file-scope device array of the library (about 8.9 MB per GPU that
+ * loads the library, held until the process exits), so m <= MCSDP_SCE_NOALLOC_MAX_M; larger m is
+ * rejected with MCSDP_ERR_ARG.  B and g are not modified.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) and must therefore come before any stream capture.
+ * Every call reuses the same array, so calls whose GPU work overlaps (different streams, different
+ * host threads) race; serialise them.  Returns MCSDP_ERR_NOT_PD if B is not positive definite.
+ * cuda_stream is a cudaStream_t; the call synchronises it before returning. */
+#define MCSDP_SCE_NOALLOC_MAX_M 1024
+mcsdp_status mcsdp_sce_solve_noalloc(const double *B_dev, int64_t ldb, const double *g_dev,
+                                     double *x_dev, int32_t m, void *cuda_stream);
+
 /* Differentiation of the solution (implicit differentiation of the central-path KKT system).
  * Not implemented: returns MCSDP_ERR_STATE. */
 mcsdp_status mcsdp_backward(mcsdp_ctx *ctx, const double *gX_layout_dev, const double *gz_dev,

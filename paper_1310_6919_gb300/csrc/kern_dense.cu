@@ -8,7 +8,9 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <mutex>
 
+#include "../../include/mcsdp.h"
 #include "internal.h"
 
 namespace mcsdp {
@@ -298,4 +300,69 @@ void launch_B_to_user(const DevSym &S, const double *Bi, int64_t ldi, double *Bo
   k_B_to_user<<<blocks, 256, 0, st>>>(S, Bi, ldi, Bo, ldo, hi, ho);
 }
 
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free Schur complement solve.  Working storage: the bordered copy of B
+// ((m+1) x m, leading dimension m+1), the inverses of the 64 x 64 diagonal blocks, and one
+// status word, all in one file-scope device array.
+constexpr int NA_MAX_M = MCSDP_SCE_NOALLOC_MAX_M;
+constexpr size_t NA_B = (size_t)(NA_MAX_M + 1) * NA_MAX_M;
+constexpr size_t NA_INV = (size_t)((NA_MAX_M + NB - 1) / NB) * NB * NB;
+constexpr size_t NA_TOTAL = NA_B + NA_INV + 32;
+
+static __device__ __align__(256) double g_sce_noalloc_scratch[NA_TOTAL];
+
+// copy lower(B) and g into the bordered working matrix; clear the status word
+__global__ void k_noalloc_setup(double *Bw, int64_t ldw, const double *__restrict__ B, int64_t ldb,
+                                const double *__restrict__ g, int m, int *status) {
+  const int64_t total = (int64_t)m * m;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % m), j = (int)(idx / m);
+    if (i >= j) Bw[i + j * ldw] = B[i + j * ldb];
+  }
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x)
+    Bw[m + j * ldw] = g[j];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *status = 0;
+}
+
 }  // namespace mcsdp
+
+namespace {
+std::mutex g_na_mu;
+double *g_na_ptr[64] = {};  // device address of the scratch array, per device ordinal
+}  // namespace
+
+extern "C" mcsdp_status mcsdp_sce_solve_noalloc(const double *B, int64_t ldb, const double *g,
+                                                double *x, int32_t m, void *stream) {
+  using namespace mcsdp;
+  if (m <= 0 || m > NA_MAX_M || ldb < m || !B || !g || !x) return MCSDP_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MCSDP_ERR_CUDA;
+  double *base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    if (!g_na_ptr[dev]) {
+      void *p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_sce_noalloc_scratch) != cudaSuccess || !p) return MCSDP_ERR_CUDA;
+      g_na_ptr[dev] = static_cast<double *>(p);
+    }
+    base = g_na_ptr[dev];
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t ldw = (int64_t)m + 1;
+  double *Bw = base;
+  double *Binv = base + NA_B;
+  int *status = reinterpret_cast<int *>(base + NA_B + NA_INV);
+  int blocks = (int)(((int64_t)m * m + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  k_noalloc_setup<<<blocks, 256, 0, st>>>(Bw, ldw, B, ldb, g, m, status);
+  dense_chol_bordered(Bw, ldw, m, status, Binv, st);
+  dense_backsolve(Bw, ldw, m, Binv, x, st);
+  if (cudaGetLastError() != cudaSuccess) return MCSDP_ERR_CUDA;
+  int hst = 0;
+  if (cudaMemcpyAsync(&hst, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return MCSDP_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return MCSDP_ERR_CUDA;
+  return (hst & ST_NOT_PD) ? MCSDP_ERR_NOT_PD : MCSDP_OK;
+}
