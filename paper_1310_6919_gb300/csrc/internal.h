@@ -131,8 +131,10 @@ void launch_scm_tiles(const DevSym &S, const int2 *tiles, int ntiles, const doub
 // B internal, (m+1) x m lower, column-major, ld = ldb; row m holds g^T on entry and
 // (L^{-1} g)^T on exit.
 // Linv: ceil(m / 64) blocks of 64 x 64 doubles receiving the inverses of the diagonal blocks
+// st2/ev_next/ev_rest (two events each): second stream for the lookahead; nullptr = one stream
 int dense_chol_bordered(double *B, int64_t ldb, int m, int *status, double *Linv,
-                        cudaStream_t st);
+                        cudaStream_t st, cudaStream_t st2, cudaEvent_t *ev_next,
+                        cudaEvent_t *ev_rest);
 int dense_backsolve(const double *B, int64_t ldb, int m, const double *Linv, double *x,
                     cudaStream_t st);
 void launch_rhs_border(const DevSym &S, double *B, int64_t ldb, const double *hvec, double betamu,

@@ -15,28 +15,30 @@
 
 namespace mcsdp {
 
-constexpr int NB = 64;  // panel width
+constexpr int NB = 32;  // panel width (FP64 on one SM is slow: a narrow panel keeps the
+                        // serial factor-and-invert step short)
 
 // Cholesky of the nb x nb diagonal block at (k0, k0), one CTA of 256 threads, and the inverse
-// of the factor (stored in Linv, nb x nb column-major, ld NB).  Thread (r, q) = (tid / 4, tid % 4)
-// owns row r of the block and every 4th column of the trailing update.
+// of the factor (stored in Linv, nb x nb column-major, ld NB).  Thread (r, q) = (tid % NB,
+// tid / NB) owns row r and every 8th column of the trailing update; the inverse is formed
+// row-step by row-step with all threads (T <- rows of L^{-1}), not one column per thread.
 __global__ void k_potrf_diag(double *B, int64_t ldb, int k0, int nb, int *status, double *Linv) {
-  extern __shared__ double smp[];
-  double *A = smp;                  // row-major, padded: A[r * (NB+1) + c]
-  double *T = smp + NB * (NB + 1);  // inverse, column-major
-  __shared__ double rdg[NB];
+  constexpr int LD = NB + 1;
+  constexpr int NQ = 256 / NB;
+  __shared__ double A[NB * LD];  // row-major, padded
+  __shared__ double T[NB * LD];  // inverse, row-major
   __shared__ double piv[2];
   const int tid = threadIdx.x;
-  const int r = tid & 63, q = tid >> 6;
-  constexpr int LD = NB + 1;
-  for (int idx = tid; idx < nb * nb; idx += 256) {
-    const int i = idx % nb, j = idx / nb;
-    A[i * LD + j] = (i >= j) ? B[(k0 + i) + (int64_t)(k0 + j) * ldb] : 0.0;
+  const int r = tid % NB, q = tid / NB;
+  for (int idx = tid; idx < NB * NB; idx += 256) {
+    const int i = idx % NB, j = idx / NB;
+    A[i * LD + j] = (i >= j && i < nb && j < nb) ? B[(k0 + i) + (int64_t)(k0 + j) * ldb] : 0.0;
+    T[i * LD + j] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
   bool bad = false;
   for (int j = 0; j < nb; ++j) {
-    if (tid == 0) {  // one thread: FP64 sqrt / division are long multi-instruction sequences
+    if (tid == 0) {
       double d = A[j * LD + j];
       if (!(d > 0.0)) {
         bad = true;
@@ -54,35 +56,29 @@ __global__ void k_potrf_diag(double *B, int64_t ldb, int k0, int nb, int *status
     __syncthreads();
     if (r > j && r < nb) {
       const double arj = A[r * LD + j];
-      for (int kk = j + 1 + q; kk <= r; kk += 4) A[r * LD + kk] -= arj * A[kk * LD + j];
+      for (int kk = j + 1 + q; kk <= r; kk += NQ) A[r * LD + kk] -= arj * A[kk * LD + j];
     }
-    __syncthreads();  // the next pivot is final
+    __syncthreads();
   }
   if (bad && tid == 0) atomicOr(status, ST_NOT_PD);
-  __syncthreads();
-  if (tid < nb) rdg[tid] = 1.0 / A[tid * LD + tid];
-  __syncthreads();
-  // inverse of the lower-triangular factor: column j of T by forward substitution
-  if (tid < nb) {
-    const int j = tid;
-    T[j + j * NB] = rdg[j];
-    for (int i = j + 1; i < nb; ++i) {
-      double s0 = 0.0, s1 = 0.0;
-      int l = j;
-      for (; l + 1 < i; l += 2) {
-        s0 = fma(A[i * LD + l], T[l + j * NB], s0);
-        s1 = fma(A[i * LD + l + 1], T[l + 1 + j * NB], s1);
-      }
-      if (l < i) s0 = fma(A[i * LD + l], T[l + j * NB], s0);
-      T[i + j * NB] = -(s0 + s1) * rdg[i];
+  // T = L^{-1}: forward elimination on the identity, one pivot row at a time; step k scales row
+  // k of T by 1/L[k][k] and removes L[i][k] times it from the rows i > k (all threads)
+  for (int k = 0; k < nb; ++k) {
+    const double rk = 1.0 / A[k * LD + k];
+    __syncthreads();
+    if (q == 0 && r <= k) T[k * LD + r] *= rk;
+    __syncthreads();
+    // rows i > k, columns c <= k
+    for (int e = tid; e < (nb - k - 1) * (k + 1); e += 256) {
+      const int i = k + 1 + e / (k + 1), c = e % (k + 1);
+      T[i * LD + c] -= A[i * LD + k] * T[k * LD + c];
     }
-    for (int i = 0; i < j; ++i) T[i + j * NB] = 0.0;
   }
   __syncthreads();
-  for (int idx = tid; idx < nb * nb; idx += 256) {
-    const int i = idx % nb, j = idx / nb;
-    if (i >= j) B[(k0 + i) + (int64_t)(k0 + j) * ldb] = A[i * LD + j];
-    Linv[i + j * NB] = T[i + j * NB];
+  for (int idx = tid; idx < NB * NB; idx += 256) {
+    const int i = idx % NB, j = idx / NB;
+    if (i < nb && j < nb && i >= j) B[(k0 + i) + (int64_t)(k0 + j) * ldb] = A[i * LD + j];
+    Linv[i + j * NB] = (i < nb && j < nb && i >= j) ? T[i * LD + j] : 0.0;
   }
 }
 
@@ -93,7 +89,7 @@ __global__ void k_trsm_panel(double *B, int64_t ldb, int k0, int nb, int r0, int
                              const double *__restrict__ Linv) {
   extern __shared__ double smt[];
   double *Xs = smt;                   // [l][row], TRSM_ROWS rows
-  double *Ts = smt + NB * TRSM_ROWS;  // [l][col] = Linv[col][l]
+  double *Ts = smt + NB * TRSM_ROWS;  // [l][col] = Linv[col][l], NB columns
   const int tid = threadIdx.x;
   const int rb = r0 + blockIdx.x * TRSM_ROWS;
   for (int idx = tid; idx < nb * TRSM_ROWS; idx += 256) {
@@ -101,49 +97,52 @@ __global__ void k_trsm_panel(double *B, int64_t ldb, int k0, int nb, int r0, int
     const int gi = rb + rr;
     Xs[l * TRSM_ROWS + rr] = (gi < rend) ? B[gi + (int64_t)(k0 + l) * ldb] : 0.0;
   }
-  for (int idx = tid; idx < nb * 64; idx += 256) {
-    const int cc = idx % 64, l = idx / 64;
-    Ts[l * 64 + cc] = (cc < nb) ? Linv[cc + l * NB] : 0.0;
+  for (int idx = tid; idx < nb * NB; idx += 256) {
+    const int cc = idx % NB, l = idx / NB;
+    Ts[l * NB + cc] = Linv[cc + l * NB];
   }
   __syncthreads();
-  const int tx = tid & 15, ty = tid >> 4;  // row ty, columns tx*4 .. tx*4+3
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  constexpr int CPT = NB * TRSM_ROWS / 256;  // columns per thread
+  const int tx = tid % (NB / CPT), ty = tid / (NB / CPT);
+  double acc[CPT];
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) acc[t] = 0.0;
   for (int l = 0; l < nb; ++l) {
     const double a = Xs[l * TRSM_ROWS + ty];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) acc[t] = fma(a, Ts[l * 64 + tx * 4 + t], acc[t]);
+    for (int t = 0; t < CPT; ++t) acc[t] = fma(a, Ts[l * NB + tx * CPT + t], acc[t]);
   }
   const int gi = rb + ty;
   if (gi < rend) {
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int c = tx * 4 + t;
+    for (int t = 0; t < CPT; ++t) {
+      const int c = tx * CPT + t;
       if (c < nb) B[gi + (int64_t)(k0 + c) * ldb] = acc[t];
     }
   }
 }
 
-// Trailing update C -= P P^T on the lower TS x TS tiles of rows [r0, rend), columns [r0, cend).
-// P = columns [k0, k0+nb) of the rows.  256 threads, 2 x 2 register blocking; small tiles keep
-// all SMs busy on the later panels (one FP64 tile of 64 x 64 x 64 would take ~60 us on one SM).
+// Trailing update C -= P P^T for the columns [c_lo, c_hi) of the rows [c_lo, rend), lower part
+// (gi >= gj), with P = columns [k0, k0+nb) of the same rows; CTA = one TS x TS tile
+// (blockIdx.x: row tile from c_lo, blockIdx.y: column tile from c_lo).  256 threads, 2 x 2
+// register blocking; small tiles keep all SMs busy (a 64 x 64 x 64 FP64 tile takes ~60 us on
+// one SM of this part).
 constexpr int TS = 32;
-__global__ void k_syrk_tiles(double *B, int64_t ldb, int k0, int nb, int r0, int rend, int cend) {
+__global__ void k_syrk_tiles(double *B, int64_t ldb, int k0, int nb, int c_lo, int c_hi,
+                             int rend) {
   extern __shared__ double smd[];
   double *Ai = smd;             // [nb][TS] (k-major)
   double *Aj = smd + NB * TS;   // [nb][TS]
-  const int t = blockIdx.x;
-  int ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-  while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
-  while (ti * (ti + 1) / 2 > t) --ti;
-  const int tj = t - ti * (ti + 1) / 2;
-  const int rb = r0 + ti * TS, cb = r0 + tj * TS;
-  if (cb >= cend) return;
+  const int ti = blockIdx.x, tj = blockIdx.y;
+  if (ti < tj) return;
+  const int rb = c_lo + ti * TS, cb = c_lo + tj * TS;
+  if (cb >= c_hi || rb >= rend) return;
   const int tid = threadIdx.x;
   for (int idx = tid; idx < nb * TS; idx += 256) {
     const int rr = idx % TS, l = idx / TS;
     const int gi = rb + rr, gj = cb + rr;
     Ai[l * TS + rr] = (gi < rend) ? B[gi + (int64_t)(k0 + l) * ldb] : 0.0;
-    Aj[l * TS + rr] = (gj < rend) ? B[gj + (int64_t)(k0 + l) * ldb] : 0.0;
+    Aj[l * TS + rr] = (gj < c_hi) ? B[gj + (int64_t)(k0 + l) * ldb] : 0.0;
   }
   __syncthreads();
   const int tx = tid & 15, ty = tid >> 4;
@@ -163,39 +162,68 @@ __global__ void k_syrk_tiles(double *B, int64_t ldb, int k0, int nb, int r0, int
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const int gj = cb + tx * 2 + q;
-      if (gj < cend && gi >= gj) B[gi + (int64_t)gj * ldb] -= acc[p][q];
+      if (gj < c_hi && gi >= gj) B[gi + (int64_t)gj * ldb] -= acc[p][q];
     }
   }
 }
 
+static void launch_syrk(double *B, int64_t ldb, int k0, int nb, int c_lo, int c_hi, int rend,
+                        int smem, cudaStream_t st) {
+  if (c_lo >= c_hi) return;
+  const int nti = (rend - c_lo + TS - 1) / TS, ntj = (c_hi - c_lo + TS - 1) / TS;
+  k_syrk_tiles<<<dim3(nti, ntj), 256, smem, st>>>(B, ldb, k0, nb, c_lo, c_hi, rend);
+}
+
+// Right-looking blocked Cholesky of the leading m columns of the bordered (m+1) x m matrix with
+// lookahead: on st (the critical path) panel k is factored (potrf), its rows below are solved
+// (trsm) and its update is applied to block column k+1; the rest of its update (block columns
+// >= k+2) runs on st2, overlapping the next panel's factor-and-solve.  ev_next[k%2] /
+// ev_rest[k%2] order the two streams so no block is updated by both at once; st waits for st2
+// at the end.  With st2 == nullptr everything runs on st.
 int dense_chol_bordered(double *B, int64_t ldb, int m, int *status, double *Linv_all,
-                        cudaStream_t st) {
-  const int smem_potrf = (NB * (NB + 1) + NB * NB) * (int)sizeof(double);
-  const int smem_trsm = (NB * TRSM_ROWS + NB * 64) * (int)sizeof(double);
+                        cudaStream_t st, cudaStream_t st2, cudaEvent_t *ev_next,
+                        cudaEvent_t *ev_rest) {
+  const int smem_trsm = (NB * TRSM_ROWS + NB * NB) * (int)sizeof(double);
   const int smem_tile = 2 * NB * TS * (int)sizeof(double);
   static bool configured = false;
   if (!configured) {
     cudaFuncSetAttribute(k_syrk_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_tile);
     cudaFuncSetAttribute(k_trsm_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_trsm);
-    cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_potrf);
     configured = true;
   }
   const int rows = m + 1;  // including the border row
   int launches = 0;
-  for (int k0 = 0; k0 < m; k0 += NB) {
+  const bool la = st2 != nullptr;
+  for (int k0 = 0, k = 0; k0 < m; k0 += NB, ++k) {
     const int nb = (m - k0) < NB ? (m - k0) : NB;
-    double *Linv = Linv_all + (int64_t)(k0 / NB) * NB * NB;
-    k_potrf_diag<<<1, 256, smem_potrf, st>>>(B, ldb, k0, nb, status, Linv);
+    double *Linv = Linv_all + (int64_t)k * NB * NB;
+    k_potrf_diag<<<1, 256, 0, st>>>(B, ldb, k0, nb, status, Linv);
     ++launches;
     const int r0 = k0 + nb;
     const int nr = rows - r0;
-    if (nr > 0) {
-      k_trsm_panel<<<(nr + TRSM_ROWS - 1) / TRSM_ROWS, 256, smem_trsm, st>>>(B, ldb, k0, nb, r0, rows, Linv);
-      const int nt = (nr + TS - 1) / TS;
-      const int ntiles = nt * (nt + 1) / 2;
-      k_syrk_tiles<<<ntiles, 256, smem_tile, st>>>(B, ldb, k0, nb, r0, rows, m);
-      launches += 2;
+    if (nr <= 0) continue;
+    k_trsm_panel<<<(nr + TRSM_ROWS - 1) / TRSM_ROWS, 256, smem_trsm, st>>>(B, ldb, k0, nb, r0, rows, Linv);
+    ++launches;
+    const int c_next = r0 + NB < m ? r0 + NB : m;  // block column k+1 = [r0, c_next)
+    if (!la) {
+      launch_syrk(B, ldb, k0, nb, r0, m, rows, smem_tile, st);
+      ++launches;
+      continue;
     }
+    if (k >= 1) cudaStreamWaitEvent(st, ev_rest[(k - 1) & 1], 0);  // st2 finished panel k-1
+    launch_syrk(B, ldb, k0, nb, r0, c_next, rows, smem_tile, st);
+    cudaEventRecord(ev_next[k & 1], st);
+    ++launches;
+    if (c_next < m) {
+      cudaStreamWaitEvent(st2, ev_next[k & 1], 0);
+      launch_syrk(B, ldb, k0, nb, c_next, m, rows, smem_tile, st2);
+      ++launches;
+    }
+    cudaEventRecord(ev_rest[k & 1], st2);
+  }
+  if (la) {
+    cudaEventRecord(ev_rest[0], st2);
+    cudaStreamWaitEvent(st, ev_rest[0], 0);
   }
   return launches;
 }
@@ -357,7 +385,7 @@ extern "C" mcsdp_status mcsdp_sce_solve_noalloc(const double *B, int64_t ldb, co
   int blocks = (int)(((int64_t)m * m + 255) / 256);
   if (blocks > 4096) blocks = 4096;
   k_noalloc_setup<<<blocks, 256, 0, st>>>(Bw, ldw, B, ldb, g, m, status);
-  dense_chol_bordered(Bw, ldw, m, status, Binv, st);
+  dense_chol_bordered(Bw, ldw, m, status, Binv, st, nullptr, nullptr, nullptr);
   dense_backsolve(Bw, ldw, m, Binv, x, st);
   if (cudaGetLastError() != cudaSuccess) return MCSDP_ERR_CUDA;
   int hst = 0;

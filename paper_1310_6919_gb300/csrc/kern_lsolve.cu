@@ -15,6 +15,8 @@
 // (forward reach of unit columns) or whose result is not needed (backward).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace mcsdp {
@@ -32,6 +34,29 @@ __device__ __forceinline__ bool ls_skip(const LsSkip &sk, int t, int tile) {
 // acc[c][lane] -= sum over updates [ub, ue) of target t of L_d[rows in S_t, :] W[S_d].
 // Each update block L_d[p1:p2, j0:j0+8] is loaded by the 32 lanes together into the warp's stage
 // (one memory round trip), the 8 source values per lane in parallel with it.
+// one chunk of CW source columns: acc[srel[p]] -= sum_q stg[q][p] x[q]  (exact width, so no
+// FP64 instruction slot is spent on a predicated-off column)
+template <int CW>
+__device__ __forceinline__ void lfwd_chunk(const double *Wc, int64_t ldw, bool act, int dc0j,
+                                           const double *base, int dnrow, int np, double *acc,
+                                           double *stg, const int *srel, int lane) {
+  double x[CW];
+#pragma unroll
+  for (int q = 0; q < CW; ++q) x[q] = act ? Wc[(int64_t)(dc0j + q) * ldw] : 0.0;
+  for (int e = lane; e < np * CW; e += 32) {
+    const int p = e % np, q = e / np;
+    stg[q * np + p] = base[p + (int64_t)q * dnrow];
+  }
+  __syncwarp();
+  for (int p = 0; p < np; ++p) {
+    double a = 0.0;
+#pragma unroll
+    for (int q = 0; q < CW; ++q) a = fma(stg[q * np + p], x[q], a);
+    acc[srel[p] * 32 + lane] -= a;
+  }
+  __syncwarp();
+}
+
 __device__ __forceinline__ void lfwd_pull(const DevSym &S, int ub, int ue, const double *L,
                                           const double *Wc, int64_t ldw, bool act, double *acc,
                                           double *stg, int *srel, int lane) {
@@ -64,23 +89,17 @@ __device__ __forceinline__ void lfwd_pull(const DevSym &S, int ub, int ue, const
       for (int p = lane; p < np; p += 32) srel[p] = rel[p];
       for (int j0 = 0; j0 < dncol; j0 += LS_CH) {
         const int cw = dncol - j0 < LS_CH ? dncol - j0 : LS_CH;
-        double x[LS_CH];
-#pragma unroll
-        for (int q = 0; q < LS_CH; ++q) x[q] = (q < cw && act) ? Wc[(int64_t)(dc0 + j0 + q) * ldw] : 0.0;
         const double *base = Ld + (int64_t)j0 * dnrow + p1;
-        for (int e = lane; e < np * cw; e += 32) {
-          const int p = e % np, q = e / np;
-          stg[q * np + p] = base[p + (int64_t)q * dnrow];
+        switch (cw) {
+          case 1: lfwd_chunk<1>(Wc, ldw, act, dc0 + j0, base, dnrow, np, acc, stg, srel, lane); break;
+          case 2: lfwd_chunk<2>(Wc, ldw, act, dc0 + j0, base, dnrow, np, acc, stg, srel, lane); break;
+          case 3: lfwd_chunk<3>(Wc, ldw, act, dc0 + j0, base, dnrow, np, acc, stg, srel, lane); break;
+          case 4: lfwd_chunk<4>(Wc, ldw, act, dc0 + j0, base, dnrow, np, acc, stg, srel, lane); break;
+          case 5: lfwd_chunk<5>(Wc, ldw, act, dc0 + j0, base, dnrow, np, acc, stg, srel, lane); break;
+          case 6: lfwd_chunk<6>(Wc, ldw, act, dc0 + j0, base, dnrow, np, acc, stg, srel, lane); break;
+          case 7: lfwd_chunk<7>(Wc, ldw, act, dc0 + j0, base, dnrow, np, acc, stg, srel, lane); break;
+          default: lfwd_chunk<8>(Wc, ldw, act, dc0 + j0, base, dnrow, np, acc, stg, srel, lane); break;
         }
-        __syncwarp();
-        for (int p = 0; p < np; ++p) {
-          double a = 0.0;
-#pragma unroll
-          for (int q = 0; q < LS_CH; ++q)
-            if (q < cw) a = fma(stg[q * np + p], x[q], a);
-          acc[srel[p] * 32 + lane] -= a;
-        }
-        __syncwarp();
       }
     }
   }
@@ -108,6 +127,29 @@ __global__ void k_lfwd_partial(DevSym S, int x0, int ntiles, const double *__res
     for (int c = 0; c < ncol; ++c) P[(int64_t)c * ldw] = acc[c * 32 + lane];
 }
 
+// W[S_t] += sum of the partial slots of t (in chunk order), one thread per (row of S_t, column),
+// for every target of the level that has extra update chunks (grid row y = chunk index; only
+// the first chunk of each target does the work)
+__global__ void k_lfwd_reduce(DevSym S, int x0, int nx, const double *__restrict__ Pw, double *W,
+                              int64_t ldw, int ncolsW, LsSkip sk) {
+  const int x = x0 + blockIdx.y;
+  if (x >= x0 + nx) return;
+  const int t = S.xch_t[x];
+  if (S.xch_beg[t] != x) return;
+  const int c0 = S.sn_col[t];
+  const int ncol = S.sn_col[t + 1] - c0;
+  const int xb = S.xch_beg[t], xe = S.xch_end[t];
+  const int64_t tot = (int64_t)ncol * ncolsW;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / ncolsW), col = (int)(e % ncolsW);
+    if (ls_skip(sk, t, col / 32)) continue;
+    double sacc = 0.0;
+    for (int xx = xb; xx < xe; ++xx) sacc += Pw[(S.xch_slotw[xx] + c) * ldw + col];
+    W[(int64_t)(c0 + c) * ldw + col] += sacc;
+  }
+}
+
 __global__ void k_lfwd(DevSym S, int lvl_begin, int ntiles, const double *__restrict__ L,
                        const double *__restrict__ Dall, double *W, int64_t ldw, int ncolsW,
                        LsSkip sk, const double *__restrict__ Pw) {
@@ -125,21 +167,7 @@ __global__ void k_lfwd(DevSym S, int lvl_begin, int ntiles, const double *__rest
   double *Wc = W + (act ? col : 0);
   for (int c = 0; c < ncol; ++c) acc[c * 32 + lane] = act ? Wc[(int64_t)(c0 + c) * ldw] : 0.0;
   lfwd_pull(S, S.upd_ptr[t], S.upd_c0end[t], L, Wc, ldw, act, acc, stg, srel, lane);
-  const int xb = S.xch_beg[t], xe = S.xch_end[t];
-  if (act && xe > xb) {
-    for (int c = 0; c < ncol; ++c) {
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-      int x = xb;
-      for (; x + 3 < xe; x += 4) {
-        s0 += Pw[(S.xch_slotw[x] + c) * ldw + col];
-        s1 += Pw[(S.xch_slotw[x + 1] + c) * ldw + col];
-        s2 += Pw[(S.xch_slotw[x + 2] + c) * ldw + col];
-        s3 += Pw[(S.xch_slotw[x + 3] + c) * ldw + col];
-      }
-      for (; x < xe; ++x) s0 += Pw[(S.xch_slotw[x] + c) * ldw + col];
-      acc[c * 32 + lane] += (s0 + s1) + (s2 + s3);
-    }
-  }
+  // the extra chunks of t were already added to W[S_t] by k_lfwd_reduce
   const double *D = Dall + S.sn_dptr[t];
   for (int i = 0; i < ncol; ++i) {
     double a0 = 0.0, a1 = 0.0;
@@ -151,6 +179,38 @@ __global__ void k_lfwd(DevSym S, int lvl_begin, int ntiles, const double *__rest
     if (j <= i) a0 = fma(D[i + j * ncol], acc[j * 32 + lane], a0);
     if (act) Wc[(int64_t)(c0 + i) * ldw] = a0 + a1;
   }
+}
+
+// a[q] = W[c0j + q] - sum_{p >= ncol} L[p][j0 + q] W[rw[p]] for the CW columns of one chunk,
+// stored in acc[q][lane]
+template <int CW>
+__device__ __forceinline__ void lbwd_chunk(const double *Wc, int64_t ldw, bool act, int c0j,
+                                           const double *base, int nrow, int ncol, const int *rw,
+                                           double *acc, int lane) {
+  double a[CW];
+#pragma unroll
+  for (int q = 0; q < CW; ++q) a[q] = act ? Wc[(int64_t)(c0j + q) * ldw] : 0.0;
+  int p = ncol;
+  for (; p + 3 < nrow; p += 4) {
+    const double w0 = act ? Wc[(int64_t)rw[p] * ldw] : 0.0;
+    const double w1 = act ? Wc[(int64_t)rw[p + 1] * ldw] : 0.0;
+    const double w2 = act ? Wc[(int64_t)rw[p + 2] * ldw] : 0.0;
+    const double w3 = act ? Wc[(int64_t)rw[p + 3] * ldw] : 0.0;
+#pragma unroll
+    for (int q = 0; q < CW; ++q) {
+      a[q] = fma(-base[p + (int64_t)q * nrow], w0, a[q]);
+      a[q] = fma(-base[p + 1 + (int64_t)q * nrow], w1, a[q]);
+      a[q] = fma(-base[p + 2 + (int64_t)q * nrow], w2, a[q]);
+      a[q] = fma(-base[p + 3 + (int64_t)q * nrow], w3, a[q]);
+    }
+  }
+  for (; p < nrow; ++p) {
+    const double w0 = act ? Wc[(int64_t)rw[p] * ldw] : 0.0;
+#pragma unroll
+    for (int q = 0; q < CW; ++q) a[q] = fma(-base[p + (int64_t)q * nrow], w0, a[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < CW; ++q) acc[q * 32 + lane] = a[q];
 }
 
 __global__ void k_lbwd(DevSym S, int lvl_begin, int ntiles, const double *__restrict__ L,
@@ -172,34 +232,17 @@ __global__ void k_lbwd(DevSym S, int lvl_begin, int ntiles, const double *__rest
   double *Wc = W + (act ? col : 0);
   for (int j0 = 0; j0 < ncol; j0 += LS_CH) {
     const int cw = ncol - j0 < LS_CH ? ncol - j0 : LS_CH;
-    double a[LS_CH];
-#pragma unroll
-    for (int q = 0; q < LS_CH; ++q) a[q] = (q < cw && act) ? Wc[(int64_t)(c0 + j0 + q) * ldw] : 0.0;
     const double *base = Lt + (int64_t)j0 * nrow;
-    int p = ncol;
-    for (; p + 3 < nrow; p += 4) {
-      const double w0 = act ? Wc[(int64_t)rw[p] * ldw] : 0.0;
-      const double w1 = act ? Wc[(int64_t)rw[p + 1] * ldw] : 0.0;
-      const double w2 = act ? Wc[(int64_t)rw[p + 2] * ldw] : 0.0;
-      const double w3 = act ? Wc[(int64_t)rw[p + 3] * ldw] : 0.0;
-#pragma unroll
-      for (int q = 0; q < LS_CH; ++q)
-        if (q < cw) {
-          a[q] = fma(-base[p + (int64_t)q * nrow], w0, a[q]);
-          a[q] = fma(-base[p + 1 + (int64_t)q * nrow], w1, a[q]);
-          a[q] = fma(-base[p + 2 + (int64_t)q * nrow], w2, a[q]);
-          a[q] = fma(-base[p + 3 + (int64_t)q * nrow], w3, a[q]);
-        }
+    switch (cw) {
+      case 1: lbwd_chunk<1>(Wc, ldw, act, c0 + j0, base, nrow, ncol, rw, acc + j0 * 32, lane); break;
+      case 2: lbwd_chunk<2>(Wc, ldw, act, c0 + j0, base, nrow, ncol, rw, acc + j0 * 32, lane); break;
+      case 3: lbwd_chunk<3>(Wc, ldw, act, c0 + j0, base, nrow, ncol, rw, acc + j0 * 32, lane); break;
+      case 4: lbwd_chunk<4>(Wc, ldw, act, c0 + j0, base, nrow, ncol, rw, acc + j0 * 32, lane); break;
+      case 5: lbwd_chunk<5>(Wc, ldw, act, c0 + j0, base, nrow, ncol, rw, acc + j0 * 32, lane); break;
+      case 6: lbwd_chunk<6>(Wc, ldw, act, c0 + j0, base, nrow, ncol, rw, acc + j0 * 32, lane); break;
+      case 7: lbwd_chunk<7>(Wc, ldw, act, c0 + j0, base, nrow, ncol, rw, acc + j0 * 32, lane); break;
+      default: lbwd_chunk<8>(Wc, ldw, act, c0 + j0, base, nrow, ncol, rw, acc + j0 * 32, lane); break;
     }
-    for (; p < nrow; ++p) {
-      const double w0 = act ? Wc[(int64_t)rw[p] * ldw] : 0.0;
-#pragma unroll
-      for (int q = 0; q < LS_CH; ++q)
-        if (q < cw) a[q] = fma(-base[p + (int64_t)q * nrow], w0, a[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < LS_CH; ++q)
-      if (q < cw) acc[(j0 + q) * 32 + lane] = a[q];
   }
   const double *D = Dall + S.sn_dptr[t];
   for (int i = 0; i < ncol; ++i) {
@@ -239,7 +282,9 @@ int lsolve(const DevSym &S, const int *lvl_ptr_host, const int *lvl_xptr_host, i
       if (xc > 0) {
         k_lfwd_partial<<<(unsigned)((int64_t)xc * ntiles), 32, smem, st>>>(S, xb, ntiles, L, W, ldw,
                                                                            ncolsW, sk, Pw);
-        ++launches;
+        const int rb = (int)std::min<int64_t>(1024, ((int64_t)S.max_ncol * ncolsW + 255) / 256);
+        k_lfwd_reduce<<<dim3(rb, xc), 256, 0, st>>>(S, xb, xc, Pw, W, ldw, ncolsW, sk);
+        launches += 2;
       }
       k_lfwd<<<(unsigned)blocks, 32, smem, st>>>(S, b, ntiles, L, D, W, ldw, ncolsW, sk, Pw);
     }

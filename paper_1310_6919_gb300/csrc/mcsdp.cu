@@ -81,6 +81,8 @@ struct mcsdp_ctx {
   bool z0_ok = false;
   bool iterate_set = false;
   cudaEvent_t ev[8] = {};
+  cudaStream_t st2 = nullptr;                  // lookahead stream of the SCM Cholesky
+  cudaEvent_t ev_next[2] = {}, ev_rest[2] = {};
   // device buffers
   double *Xbar = nullptr, *z = nullptr, *Ylay = nullptr, *N = nullptr, *dinvN = nullptr;
   double *Lh = nullptr, *dinvL = nullptr, *dY = nullptr, *dX = nullptr, *YinvE = nullptr;
@@ -240,7 +242,7 @@ void plan_workspace(mcsdp_ctx *c) {
   // pattern receives an update from nearly every clique) gets its extra chunks summed in
   // parallel by partial kernels, then added in fixed order (deterministic) ----
   {
-    const double chunk_work = 1024.0;
+    const double chunk_work = 256.0;
     c->upd_c0end.assign(S.ns, 0);
     c->xch_beg.assign(S.ns, 0);
     c->xch_end.assign(S.ns, 0);
@@ -664,7 +666,8 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
     launch_rhs_border(c->D, c->B, c->ldb, c->hvec, beta * mu, c->stream);
     k0.done(1);
     KScope k1(c, KC_CHOL);
-    k1.done(dense_chol_bordered(c->B, c->ldb, m, c->status + 2, c->Binv, c->stream));
+    k1.done(dense_chol_bordered(c->B, c->ldb, m, c->status + 2, c->Binv, c->stream, c->st2,
+                                c->ev_next, c->ev_rest));
     KScope k2(c, KC_BSOLVE);
     int nl = dense_backsolve(c->B, c->ldb, m, c->Binv, c->xs, c->stream);
     launch_dz_to_user(c->D, c->xs, c->dz, c->stream);
@@ -897,6 +900,11 @@ mcsdp_status mcsdp_create(const mcsdp_problem *p, const mcsdp_options *opt, void
     c->device = c->opt.device;
     CUDA_TRY(c, cudaSetDevice(c->device));
     for (int i = 0; i < 8; ++i) CUDA_TRY(c, cudaEventCreate(&c->ev[i]));
+    CUDA_TRY(c, cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+      CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_next[i], cudaEventDisableTiming));
+      CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_rest[i], cudaEventDisableTiming));
+    }
   }
   c->err.clear();
   return MCSDP_OK;
@@ -913,6 +921,11 @@ void mcsdp_destroy(mcsdp_ctx *c) {
       prof_flush(c);
     }
     for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
+    for (int i = 0; i < 2; ++i) {
+      if (c->ev_next[i]) cudaEventDestroy(c->ev_next[i]);
+      if (c->ev_rest[i]) cudaEventDestroy(c->ev_rest[i]);
+    }
+    if (c->st2) cudaStreamDestroy(c->st2);
   }
   delete c;
 }
