@@ -9,6 +9,7 @@ namespace mcsdp {
 struct DevSym {
   int n, m, ns, ngroup, max_nrow, max_ncol;
   int max_grp_nnz;  // largest number of stored nonzeros (both triangles) of one SCM group
+  int max_con_nnz;  // ... of one constraint
   int64_t nnzL, nslot, nnzD;
   const int *sn_col;
   const int64_t *sn_dptr;
@@ -123,6 +124,7 @@ void launch_set_identity(const DevSym &S, double *Xbar, cudaStream_t st);
 // Tiles B[J_h, J_g] for the listed (h, g), h >= g, from WX = X̂[:, P_g] and WY = Y^{-1}[:, P_g]
 // (row-major, ld = ldw, the columns of group g start at goff[g]); h_i = A_i . Y^{-1} on the
 // diagonal tiles.
+size_t scm_tiles_smem_bytes(const DevSym &S, int pmax);
 void launch_scm_tiles(const DevSym &S, const int2 *tiles, int ntiles, const double *WX,
                       const double *WY, int64_t ldw, const int *goff, double *B, int64_t ldb,
                       double *hvec, int pmax, cudaStream_t st);

@@ -48,11 +48,24 @@ __device__ __forceinline__ void lfwd_chunk(const double *Wc, int64_t ldw, bool a
     stg[q * np + p] = base[p + (int64_t)q * dnrow];
   }
   __syncwarp();
-  for (int p = 0; p < np; ++p) {
-    double a = 0.0;
+  int p = 0;
+  for (; p + 1 < np; p += 2) {  // two rows at a time: independent chains
+    double a0 = 0.0, a1 = 0.0;
 #pragma unroll
-    for (int q = 0; q < CW; ++q) a = fma(stg[q * np + p], x[q], a);
-    acc[srel[p] * 32 + lane] -= a;
+    for (int q = 0; q < CW; ++q) {
+      a0 = fma(stg[q * np + p], x[q], a0);
+      a1 = fma(stg[q * np + p + 1], x[q], a1);
+    }
+    const int r0 = srel[p] * 32 + lane, r1 = srel[p + 1] * 32 + lane;
+    const double v0 = acc[r0], v1 = acc[r1];
+    acc[r0] = v0 - a0;
+    acc[r1] = v1 - a1;
+  }
+  if (p < np) {
+    double a0 = 0.0;
+#pragma unroll
+    for (int q = 0; q < CW; ++q) a0 = fma(stg[q * np + p], x[q], a0);
+    acc[srel[p] * 32 + lane] -= a0;
   }
   __syncwarp();
 }
@@ -187,9 +200,12 @@ template <int CW>
 __device__ __forceinline__ void lbwd_chunk(const double *Wc, int64_t ldw, bool act, int c0j,
                                            const double *base, int nrow, int ncol, const int *rw,
                                            double *acc, int lane) {
-  double a[CW];
+  double a[CW], b[CW];  // two independent chains per column (even / odd rows)
 #pragma unroll
-  for (int q = 0; q < CW; ++q) a[q] = act ? Wc[(int64_t)(c0j + q) * ldw] : 0.0;
+  for (int q = 0; q < CW; ++q) {
+    a[q] = act ? Wc[(int64_t)(c0j + q) * ldw] : 0.0;
+    b[q] = 0.0;
+  }
   int p = ncol;
   for (; p + 3 < nrow; p += 4) {
     const double w0 = act ? Wc[(int64_t)rw[p] * ldw] : 0.0;
@@ -199,9 +215,9 @@ __device__ __forceinline__ void lbwd_chunk(const double *Wc, int64_t ldw, bool a
 #pragma unroll
     for (int q = 0; q < CW; ++q) {
       a[q] = fma(-base[p + (int64_t)q * nrow], w0, a[q]);
-      a[q] = fma(-base[p + 1 + (int64_t)q * nrow], w1, a[q]);
+      b[q] = fma(-base[p + 1 + (int64_t)q * nrow], w1, b[q]);
       a[q] = fma(-base[p + 2 + (int64_t)q * nrow], w2, a[q]);
-      a[q] = fma(-base[p + 3 + (int64_t)q * nrow], w3, a[q]);
+      b[q] = fma(-base[p + 3 + (int64_t)q * nrow], w3, b[q]);
     }
   }
   for (; p < nrow; ++p) {
@@ -210,7 +226,7 @@ __device__ __forceinline__ void lbwd_chunk(const double *Wc, int64_t ldw, bool a
     for (int q = 0; q < CW; ++q) a[q] = fma(-base[p + (int64_t)q * nrow], w0, a[q]);
   }
 #pragma unroll
-  for (int q = 0; q < CW; ++q) acc[q * 32 + lane] = a[q];
+  for (int q = 0; q < CW; ++q) acc[q * 32 + lane] = a[q] + b[q];
 }
 
 __global__ void k_lbwd(DevSym S, int lvl_begin, int ntiles, const double *__restrict__ L,

@@ -13,10 +13,14 @@
 // staged in shared memory.  Only the lower triangle (h >= g) is formed (B is symmetric).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.h"
 #include "warp_solve.cuh"
 
 namespace mcsdp {
+
+constexpr int XW_CAP = 6144;  // doubles of shared memory for the X̂-times-A_j products
 
 __global__ void k_scm_tiles(DevSym S, const int2 *__restrict__ tiles,
                             const double *__restrict__ WX, const double *__restrict__ WY,
@@ -59,26 +63,46 @@ __global__ void k_scm_tiles(DevSym S, const int2 *__restrict__ tiles,
     gd[e] = S.anz_b[gb + e] * ph;
   }
   __syncthreads();
-  for (int idx = tid; idx < nh * ng; idx += bd) {
-    const int ii = idx % nh, jj = idx / nh;
-    const int i = i0 + ii, j = j0 + jj;
-    if (h == g && i < j) continue;
-    double acc = 0.0;
-    const int ub = S.anz_ptr[j] - gb, ue = S.anz_ptr[j + 1] - gb;
-    for (int t = S.anz_ptr[i] - hb; t < S.anz_ptr[i + 1] - hb; ++t) {
-      const int a = ha[t] & 0xffff, b = ha[t] >> 16;
-      const double *xr = Xs + a;
-      const double *yr = Ys + b;
-      double s0 = 0.0, s1 = 0.0;
-      int u = ub;
-      for (; u + 1 < ue; u += 2) {
-        s0 = fma(gv[u] * xr[ga[u]], yr[gd[u]], s0);
-        s1 = fma(gv[u + 1] * xr[ga[u + 1]], yr[gd[u + 1]], s1);
-      }
-      if (u < ue) s0 = fma(gv[u] * xr[ga[u]], yr[gd[u]], s0);
-      acc = fma(hv[t], s0 + s1, acc);
+  // constraints j of J_g in batches of JB: XW[jb][u][a] = [A_j]_u * X̂[P_h[a], c_u] for the
+  // nonzeros u of A_j, then B_ij = sum_t v_t sum_u XW[jb][u][a_t] Y^{-1}[P_h[b_t], d_u]
+  // (one multiply-add per pair of nonzeros)
+  // the int lists (hn + 2 gn ints) start 8-byte aligned; round their end up to 8 bytes
+  double *XW = reinterpret_cast<double *>(ha + ((hn + 2 * gn + 1) & ~1));
+  const int cap_nnz = XW_CAP / (ph > 0 ? ph : 1);
+  for (int jb0 = 0, nj = 0; jb0 < ng; jb0 += nj) {
+    // batch: as many constraints as fit XW_CAP doubles (at least one)
+    nj = 1;
+    while (jb0 + nj < ng && S.anz_ptr[j0 + jb0 + nj + 1] - S.anz_ptr[j0 + jb0] <= cap_nnz) ++nj;
+    // the batch's nonzeros are contiguous: [S.anz_ptr[j0 + jb0], S.anz_ptr[j0 + jb0 + nj])
+    const int ub0 = S.anz_ptr[j0 + jb0] - gb, ub1 = S.anz_ptr[j0 + jb0 + nj] - gb;
+    for (int e = tid; e < (ub1 - ub0) * ph; e += bd) {
+      const int u = ub0 + e / ph, a = e % ph;
+      XW[(u - ub0) * ph + a] = gv[u] * Xs[a + ga[u]];
     }
-    B[i + (int64_t)j * ldb] = acc;
+    __syncthreads();
+    for (int idx = tid; idx < nh * nj; idx += bd) {
+      const int ii = idx % nh, jb = idx / nh;
+      const int i = i0 + ii, j = j0 + jb0 + jb;
+      if (h == g && i < j) continue;
+      const int ub = S.anz_ptr[j] - gb, ue = S.anz_ptr[j + 1] - gb;
+      double acc = 0.0;
+      for (int t = S.anz_ptr[i] - hb; t < S.anz_ptr[i + 1] - hb; ++t) {
+        const int a = ha[t] & 0xffff, b = ha[t] >> 16;
+        const double *xw = XW + (ub - ub0) * ph + a;
+        const double *yr = Ys + b;
+        double s0 = 0.0, s1 = 0.0;
+        int u = 0;
+        const int nu = ue - ub;
+        for (; u + 1 < nu; u += 2) {
+          s0 = fma(xw[u * ph], yr[gd[ub + u]], s0);
+          s1 = fma(xw[(u + 1) * ph], yr[gd[ub + u + 1]], s1);
+        }
+        if (u < nu) s0 = fma(xw[u * ph], yr[gd[ub + u]], s0);
+        acc = fma(hv[t], s0 + s1, acc);
+      }
+      B[i + (int64_t)j * ldb] = acc;
+    }
+    __syncthreads();
   }
   if (h == g) {
     for (int ii = tid; ii < nh; ii += bd) {
@@ -91,12 +115,18 @@ __global__ void k_scm_tiles(DevSym S, const int2 *__restrict__ tiles,
   }
 }
 
+size_t scm_tiles_smem_bytes(const DevSym &S, int pmax) {
+  const size_t xw = std::max<size_t>(XW_CAP, (size_t)S.max_con_nnz * pmax);
+  return (size_t)2 * pmax * pmax * 8 + (size_t)2 * S.max_grp_nnz * (8 + 8) + 64 + xw * 8;
+}
+
 void launch_scm_tiles(const DevSym &S, const int2 *tiles, int ntiles, const double *WX,
                       const double *WY, int64_t ldw, const int *goff, double *B, int64_t ldb,
                       double *hvec, int pmax, cudaStream_t st) {
   if (ntiles <= 0) return;
-  // two |P_h| x |P_g| blocks plus the nonzero lists of two groups in shared memory
-  size_t smem = (size_t)2 * pmax * pmax * 8 + (size_t)2 * S.max_grp_nnz * (8 + 8) + 64;
+  // two |P_h| x |P_g| blocks, the nonzero lists of two groups, and the X̂-times-A_j products of
+  // one batch of constraints (XW_CAP doubles, or one constraint's if larger) in shared memory
+  const size_t smem = scm_tiles_smem_bytes(S, pmax);
   static size_t configured = 0;
   if (smem > configured) {
     cudaFuncSetAttribute(k_scm_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -38,7 +38,7 @@ struct Chunk {
   int ntiles;
 };
 
-constexpr int NCAND = 8;  // candidates per dual step-length round
+constexpr int NCAND = 16;  // candidates per dual step-length round
 
 }  // namespace
 
@@ -405,7 +405,7 @@ void plan_workspace(mcsdp_ctx *c) {
   plan_buf(c, cur, "alpha_c", NCAND * 8);
   plan_buf(c, cur, "alpha_r", (size_t)S.ns * 8);
   plan_buf(c, cur, "scal", 16 * 8);
-  plan_buf(c, cur, "status", 16 * 4);
+  plan_buf(c, cur, "status", (8 + NCAND) * 4);  // [0..3] phases, [8..8+NCAND) dual candidates
   c->ws_bytes = cur;
 }
 
@@ -426,6 +426,8 @@ void bind_pointers(mcsdp_ctx *c) {
   D.max_grp_nnz = 0;
   for (int g = 0; g < S.ngroup; ++g)
     D.max_grp_nnz = std::max(D.max_grp_nnz, S.anz_ptr[S.grp_cptr[g + 1]] - S.anz_ptr[S.grp_cptr[g]]);
+  D.max_con_nnz = 0;
+  for (int i = 0; i < S.m; ++i) D.max_con_nnz = std::max(D.max_con_nnz, S.anz_ptr[i + 1] - S.anz_ptr[i]);
   D.nnzL = S.sn_valptr[S.ns];
   D.nslot = S.nslot;
   D.nnzD = S.sn_dptr[S.ns];
@@ -574,7 +576,7 @@ mcsdp_status phase_ychol(mcsdp_ctx *c, int ncand, const double *alpha, const dou
 }
 
 mcsdp_status factor_Y(mcsdp_ctx *c) {
-  CUDA_TRY(c, cudaMemsetAsync(c->status, 0, 16 * sizeof(int), c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->status, 0, 8 * sizeof(int), c->stream));
   mcsdp_status s = phase_ychol(c, 1, nullptr, c->Ylay, nullptr, c->N, c->dinvN, c->status);
   if (s) return s;
   return MCSDP_OK;
@@ -712,7 +714,8 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
   // dual step: bisection on the success of Y + alpha dY = N N^T (K2 on candidates)
   double lo = 0.0, hi = -1.0;  // largest passing, smallest failing
   double cand[NCAND];
-  const double first[NCAND] = {1.0, 0.9, 0.75, 0.5, 0.25, 0.1, 0.03, 0.01};
+  const double first[NCAND] = {1.0, 0.95, 0.9, 0.85, 0.8, 0.7, 0.6, 0.5,
+                               0.4, 0.3, 0.2, 0.1, 0.05, 0.02, 0.01, 0.003};
   for (int round = 0; round < 6; ++round) {
     if (round == 0) {
       for (int i = 0; i < NCAND; ++i) cand[i] = first[i];
@@ -945,6 +948,8 @@ mcsdp_status mcsdp_set_workspace(mcsdp_ctx *c, void *ptr, size_t bytes) {
   c->ws = (char *)ptr;
   c->ws_have = bytes;
   bind_pointers(c);
+  if (scm_tiles_smem_bytes(c->D, c->pmax) > 227 * 1024)
+    return fail(c, MCSDP_ERR_ARG, "SCM groups too large for the shared-memory tile kernel");
   for (const Upload &u : c->uploads)
     CUDA_TRY(c, cudaMemcpyAsync(c->ws + u.off, u.src, u.bytes, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->B, 0, (size_t)c->ldb * c->S.m * 8, c->stream));
