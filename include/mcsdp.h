@@ -73,7 +73,10 @@ typedef struct {
 typedef struct {
   double beta, gamma, gap_tol, feas_tol;
   int32_t max_iter;
-  int32_t precision;     /* 0 = FP64 (the only form implemented; others -> MCSDP_ERR_ARG) */
+  int32_t precision;     /* 0 = FP64; 1 = mixed: the SCE B dz = g is solved with an FP32 Cholesky
+                            factor of the FP64 B and FP64 iterative refinement, promoted to the
+                            FP64 factor for the rest of a solve when the refinement stalls or the
+                            FP32 factorisation breaks down (m <= 50000); everything else FP64 */
   int64_t timeout_cycles;/* bound on any device spin-wait; 0 = library default */
   int32_t device;        /* CUDA device ordinal, or -1 for host-only */
   int32_t verbose;       /* 1 = one log line per iteration on stderr */
@@ -136,6 +139,10 @@ typedef struct {
   double seconds;       /* wall time of the loop measured with CUDA events */
   double t_scm, t_chol, t_pmat, t_other; /* per-phase seconds (S-ELEMENTS, S-CHOLESKY, P-MATRIX,
                                             rest), CUDA events */
+  int32_t precision;     /* the option the solve ran with */
+  int32_t promoted_iter; /* mixed form: first iteration solved with the FP64 factor, -1 if none */
+  int32_t refine_steps;  /* mixed form: FP64 refinement steps over the solve */
+  int32_t reserved;
 } mcsdp_result;
 mcsdp_status mcsdp_solve(mcsdp_ctx *ctx, mcsdp_result *res);
 
@@ -149,7 +156,8 @@ mcsdp_status mcsdp_get_iterate(const mcsdp_ctx *ctx, double *Xbar_layout_dev, do
  * K2 (Y = N N^T), K1 (Algorithm 1: L̂ from X̄), K3 (B_ij = A_i . (X̂ A_j Y^{-1})).
  * Writes the lower triangle (i >= j, caller's constraint order) of B into B_dev, column-major
  * with leading dimension ldb >= m; the strict upper triangle is not touched.
- * h_dev (may be NULL) receives h_i = A_i . Y^{-1}.  precision must be 0 (FP64). */
+ * h_dev (may be NULL) receives h_i = A_i . Y^{-1}.  precision is 0 or 1: B is assembled in
+ * FP64 in both forms (the mixed form lowers only the precision of its factorisation). */
 mcsdp_status mcsdp_scm_assemble(mcsdp_ctx *ctx, const double *Xbar_layout_dev, const double *z_dev,
                                 double *B_dev, int64_t ldb, double *h_dev, int32_t precision);
 

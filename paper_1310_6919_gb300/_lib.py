@@ -46,7 +46,9 @@ class Result_t(C.Structure):
                 ("pinf", C.c_double), ("dinf", C.c_double), ("mu", C.c_double),
                 ("iters", C.c_int32), ("status", C.c_int32), ("seconds", C.c_double),
                 ("t_scm", C.c_double), ("t_chol", C.c_double), ("t_pmat", C.c_double),
-                ("t_other", C.c_double)]
+                ("t_other", C.c_double), ("precision", C.c_int32),
+                ("promoted_iter", C.c_int32), ("refine_steps", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_NOT_PD", 3: "ERR_MAXITER", 4: "ERR_STALL",

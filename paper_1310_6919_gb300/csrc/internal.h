@@ -139,6 +139,18 @@ int dense_chol_bordered(double *B, int64_t ldb, int m, int *status, double *Linv
                         cudaEvent_t *ev_rest);
 int dense_backsolve(const double *B, int64_t ldb, int m, const double *Linv, double *x,
                     cudaStream_t st);
+int dense_chol_f32(float *B, int64_t ldb, int m, int *status, float *Linv, cudaStream_t st,
+                   cudaStream_t st2, cudaEvent_t *ev_next, cudaEvent_t *ev_rest);
+// Mixed precision: B32 <- FP32 Cholesky factor of lower(B) (with L^T in the upper triangle)
+// and g <- row m of B (the right-hand side border), r <- g, x <- 0
+int mixed_factor(const double *B, int64_t ldb, int m, float *B32, float *Linv32, int *status,
+                 double *g, double *r, double *x, cudaStream_t st, cudaStream_t st2,
+                 cudaEvent_t *ev_next, cudaEvent_t *ev_rest);
+// one refinement step: x += (L32 L32^T)^{-1} r, y = B x and ay = |B||x| (FP64), r = g - y,
+// norms = (max|r|, max(ay + |g|))
+int mixed_refine_step(const double *B, int64_t ldb, int m, const float *L32, const float *Linv32,
+                      const double *g, double *x, double *r, double *y, double *ay, double *norms,
+                      cudaStream_t st);
 void launch_rhs_border(const DevSym &S, double *B, int64_t ldb, const double *hvec, double betamu,
                        cudaStream_t st);
 void launch_dz_to_user(const DevSym &S, const double *dz_int, double *dz_user, cudaStream_t st);

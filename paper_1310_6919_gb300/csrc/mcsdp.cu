@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <map>
 #include <set>
 #include <string>
@@ -89,6 +90,11 @@ struct mcsdp_ctx {
   double *Mlow = nullptr, *Mup = nullptr, *B = nullptr, *hvec = nullptr, *xs = nullptr;
   double *dz = nullptr, *W1 = nullptr, *W2 = nullptr, *Ncand = nullptr, *dinvCand = nullptr;
   double *Pw = nullptr, *Pf = nullptr, *Binv = nullptr;
+  // mixed form: FP32 factor of B, FP64 refinement vectors
+  float *B32 = nullptr, *Linv32 = nullptr;
+  double *gref = nullptr, *rref = nullptr, *yref = nullptr, *ayref = nullptr, *nref = nullptr;
+  bool promoted = false;        // the FP64 factor is used for the rest of the solve
+  int promoted_iter = -1, refine_steps = 0, cur_iter = 0;
   double *alpha_c = nullptr, *alpha_r = nullptr, *scal = nullptr;
   int *status = nullptr, *rowof_dev = nullptr, *goff_dev = nullptr, *pm_rowof_dev = nullptr;
   int2 *tiles_dev = nullptr, *tkey_dev = nullptr, *pm_tkey_dev = nullptr;
@@ -405,7 +411,18 @@ void plan_workspace(mcsdp_ctx *c) {
   plan_buf(c, cur, "alpha_c", NCAND * 8);
   plan_buf(c, cur, "alpha_r", (size_t)S.ns * 8);
   plan_buf(c, cur, "scal", 16 * 8);
-  plan_buf(c, cur, "status", (8 + NCAND) * 4);  // [0..3] phases, [8..8+NCAND) dual candidates
+  plan_buf(c, cur, "status", (8 + NCAND) * 4);  // [0..3] phases, [4] FP32 factor, [8..8+NCAND) dual candidates
+  {
+    const bool mx = c->opt.precision == 1;
+    const size_t nblk = (size_t)(m + 31) / 32;
+    plan_buf(c, cur, "B32", mx ? (size_t)m * m * 4 : 0);
+    plan_buf(c, cur, "Linv32", mx ? nblk * 32 * 32 * 4 : 0);
+    plan_buf(c, cur, "gref", mx ? (size_t)m * 8 : 0);
+    plan_buf(c, cur, "rref", mx ? (size_t)m * 8 : 0);
+    plan_buf(c, cur, "yref", mx ? (size_t)m * 8 : 0);
+    plan_buf(c, cur, "ayref", mx ? (size_t)m * 8 : 0);
+    plan_buf(c, cur, "nref", 4 * 8);
+  }  // [0..3] phases, [8..8+NCAND) dual candidates
   c->ws_bytes = cur;
 }
 
@@ -514,6 +531,13 @@ void bind_pointers(mcsdp_ctx *c) {
   c->alpha_r = wsp<double>(c, "alpha_r");
   c->scal = wsp<double>(c, "scal");
   c->status = wsp<int>(c, "status");
+  c->B32 = wsp<float>(c, "B32");
+  c->Linv32 = wsp<float>(c, "Linv32");
+  c->gref = wsp<double>(c, "gref");
+  c->rref = wsp<double>(c, "rref");
+  c->yref = wsp<double>(c, "yref");
+  c->ayref = wsp<double>(c, "ayref");
+  c->nref = wsp<double>(c, "nref");
 
   c->rowof_dev = wsp<int>(c, "rowof");
   c->goff_dev = wsp<int>(c, "goff");
@@ -654,6 +678,60 @@ struct IterOut {
   double mu, pobj, dobj, gap, pinf, ap, ad;
 };
 
+// Mixed form of the SCE solve B dz = g (eq. SCE): Cholesky factor of B rounded to FP32, then
+// iterative refinement with the residual g - B x formed in FP64 from the FP64 B (the scheme of
+// LAPACK's dsposv).  Measure of convergence: omega = max|r| / max(|B||x| + |g|).  Success when
+// omega <= sqrt(m) eps64; the refinement is abandoned (*solved = false, B untouched) when the
+// FP32 factorisation breaks down, when omega fails to halve in two consecutive steps while still
+// above m eps64 (the worst-case backward error of the FP64 factorisation itself), or after
+// MIXED_MAX_STEPS steps.  Leaves x in c->xs (internal order).
+constexpr int MIXED_MAX_STEPS = 10;
+mcsdp_status mixed_sce(mcsdp_ctx *c, bool *solved) {
+  const int m = c->S.m;
+  *solved = false;
+  CUDA_TRY(c, cudaMemsetAsync(c->status + 4, 0, sizeof(int), c->stream));
+  {
+    KScope k1(c, KC_CHOL);
+    k1.done(mixed_factor(c->B, c->ldb, m, c->B32, c->Linv32, c->status + 4, c->gref, c->rref,
+                         c->xs, c->stream, c->st2, c->ev_next, c->ev_rest));
+  }
+  KCHECK(c);
+  const double eps = std::ldexp(1.0, -53);
+  const double tol_ok = std::sqrt((double)m) * eps, tol_stall = (double)m * eps;
+  double prev = 1.0;
+  int slow = 0;
+  for (int k = 0; k < MIXED_MAX_STEPS; ++k) {
+    {
+      KScope k2(c, KC_BSOLVE);
+      k2.done(mixed_refine_step(c->B, c->ldb, m, c->B32, c->Linv32, c->gref, c->xs, c->rref,
+                                c->yref, c->ayref, c->nref, c->stream));
+    }
+    KCHECK(c);
+    double nr[2];
+    int fst = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(nr, c->nref, 2 * 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(&fst, c->status + 4, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    prof_flush(c);
+    ++c->refine_steps;
+    if (fst & ST_NOT_PD) return MCSDP_OK;  // FP32 factor broke down: promote
+    const double omega = nr[0] / std::max(nr[1], std::numeric_limits<double>::min());
+    if (!std::isfinite(omega)) return MCSDP_OK;
+    if (c->opt.verbose > 1) std::fprintf(stderr, "  refine %d omega %.3e\n", k, omega);
+    if (omega <= tol_ok) {
+      *solved = true;
+      return MCSDP_OK;
+    }
+    slow = (omega > 0.5 * prev) ? slow + 1 : 0;
+    if (slow >= 2) {
+      *solved = omega <= tol_stall;
+      return MCSDP_OK;
+    }
+    prev = omega;
+  }
+  return MCSDP_OK;
+}
+
 // Computes the Newton direction at (Xbar, z) into c->dz, c->dY, c->dX and the step lengths.
 // Requires Ylay/N/Lh already factored at the iterate.
 mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, float *tms) {
@@ -667,13 +745,25 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
     KScope k0(c, KC_MISC);
     launch_rhs_border(c->D, c->B, c->ldb, c->hvec, beta * mu, c->stream);
     k0.done(1);
-    KScope k1(c, KC_CHOL);
-    k1.done(dense_chol_bordered(c->B, c->ldb, m, c->status + 2, c->Binv, c->stream, c->st2,
-                                c->ev_next, c->ev_rest));
-    KScope k2(c, KC_BSOLVE);
-    int nl = dense_backsolve(c->B, c->ldb, m, c->Binv, c->xs, c->stream);
+    bool solved = false;
+    if (c->opt.precision == 1 && !c->promoted) {
+      s = mixed_sce(c, &solved);
+      if (s) return s;
+      if (!solved) {
+        c->promoted = true;
+        c->promoted_iter = c->cur_iter;
+      }
+    }
+    if (!solved) {
+      KScope k1(c, KC_CHOL);
+      k1.done(dense_chol_bordered(c->B, c->ldb, m, c->status + 2, c->Binv, c->stream, c->st2,
+                                  c->ev_next, c->ev_rest));
+      KScope k2(c, KC_BSOLVE);
+      k2.done(dense_backsolve(c->B, c->ldb, m, c->Binv, c->xs, c->stream));
+    }
+    KScope k3(c, KC_MISC);
     launch_dz_to_user(c->D, c->xs, c->dz, c->stream);
-    k2.done(nl + 1);
+    k3.done(1);
   }
   KCHECK(c);
   cudaEventRecord(c->ev[2], c->stream);
@@ -838,7 +928,10 @@ mcsdp_status mcsdp_create(const mcsdp_problem *p, const mcsdp_options *opt, void
     return fail(c, MCSDP_ERR_ARG, "entry arrays missing");
   if (!p->c) return fail(c, MCSDP_ERR_ARG, "c/b vector missing");
   if (p->form != 0 && p->form != 1) return fail(c, MCSDP_ERR_ARG, "form must be 0 (SDPA) or 1 (paper)");
-  if (c->opt.precision != 0) return fail(c, MCSDP_ERR_ARG, "only precision 0 (FP64) is implemented");
+  if (c->opt.precision != 0 && c->opt.precision != 1)
+    return fail(c, MCSDP_ERR_ARG, "precision must be 0 (FP64) or 1 (mixed)");
+  if (c->opt.precision == 1 && p->m > 50000)
+    return fail(c, MCSDP_ERR_ARG, "the mixed form supports m <= 50000");
   if (c->opt.panel_max <= 0) c->opt.panel_max = 80;
   if (c->opt.panel_max > 96) return fail(c, MCSDP_ERR_ARG, "panel_max must be <= 96");
   if (c->opt.group_max <= 0) c->opt.group_max = 64;
@@ -1033,7 +1126,7 @@ mcsdp_status mcsdp_scm_assemble(mcsdp_ctx *c, const double *Xbar, const double *
                                 int64_t ldb, double *h, int32_t precision) {
   mcsdp_status s = ready(c);
   if (s) return s;
-  if (precision != 0) return fail(c, MCSDP_ERR_ARG, "only precision 0 (FP64) is implemented");
+  if (precision != 0 && precision != 1) return fail(c, MCSDP_ERR_ARG, "precision must be 0 or 1");
   if (!Xbar || !z || !Bout || ldb < c->S.m) return fail(c, MCSDP_ERR_ARG, "bad arguments");
   s = phase_Y(c, z);
   if (s) return s;
@@ -1067,6 +1160,9 @@ mcsdp_status mcsdp_newton_step(mcsdp_ctx *c, const double *Xbar, const double *z
   if (s) return s;
   const double muv = sc[0] / c->S.n;
   IterOut o{};
+  c->promoted = false;  // each call decides on its own
+  c->promoted_iter = -1;
+  c->cur_iter = 0;
   s = direction(c, Xbar, muv, o, nullptr);
   if (s) return s;
   if (dz) CUDA_TRY(c, cudaMemcpyAsync(dz, c->dz, (size_t)c->S.m * 8, cudaMemcpyDeviceToDevice, c->stream));
@@ -1089,6 +1185,10 @@ mcsdp_status mcsdp_solve(mcsdp_ctx *c, mcsdp_result *res) {
     c->iterate_set = true;
   }
   mcsdp_result r{};
+  c->promoted = false;
+  c->promoted_iter = -1;
+  c->refine_steps = 0;
+  double prev_pinf = -1.0;
   float tms[4] = {0, 0, 0, 0};
   cudaEvent_t t0 = c->ev[6], t1 = c->ev[7];
   cudaEventRecord(t0, c->stream);
@@ -1105,6 +1205,15 @@ mcsdp_status mcsdp_solve(mcsdp_ctx *c, mcsdp_result *res) {
     const double mu = sc[0] / n, pobj = sc[1], dobj = sc[2];
     const double gap = std::fabs(pobj - dobj) / std::max(1.0, (std::fabs(pobj) + std::fabs(dobj)) / 2);
     const double pinf = sc[3] / std::max(1.0, sc[4]);
+    // mixed form: promote to the FP64 factor if the primal residual grows (it contracts by
+    // (1 - gamma alpha_p) per iteration in exact arithmetic)
+    if (c->opt.precision == 1 && !c->promoted && prev_pinf > 0 && pinf > 2.0 * prev_pinf &&
+        pinf > 1e-12) {
+      c->promoted = true;
+      c->promoted_iter = it;
+    }
+    prev_pinf = pinf;
+    c->cur_iter = it;
     r.pobj = pobj;
     r.dobj = dobj;
     r.gap = gap;
@@ -1147,6 +1256,9 @@ mcsdp_status mcsdp_solve(mcsdp_ctx *c, mcsdp_result *res) {
   r.t_pmat = tms[2] * 1e-3;
   r.t_other = r.seconds - r.t_scm - r.t_chol - r.t_pmat;
   r.status = final_status;
+  r.precision = c->opt.precision;
+  r.promoted_iter = c->opt.precision == 1 ? c->promoted_iter : -1;
+  r.refine_steps = c->refine_steps;
   if (res) *res = r;
   return final_status;
 }
