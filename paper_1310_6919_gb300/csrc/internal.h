@@ -5,6 +5,23 @@
 
 namespace mcsdp {
 
+// Per-update metadata of the left-looking update lists (one 32-byte record per update u):
+// source supernode d's first column, width and row count, the first row p1 of its block that
+// lands in the target, the block's row count np, and the offsets of the relative row indices
+// and of d's values
+struct alignas(16) UpdMeta {
+  int dc0, dncol, dnrow, p1;
+  int np, pad;
+  int64_t relptr, valp;
+};
+
+// Per level of the supernode tree, for sizing the staged solve kernels: largest ncol and nrow of
+// its supernodes, and for the updates its targets receive, the source chunk width (<= 8 columns)
+// and the largest row count of an update block
+struct LsLevel {
+  int nc, nr, cw, np;
+};
+
 // Device copies of the symbolic tables (all pointers into the caller's workspace).
 struct DevSym {
   int n, m, ns, ngroup, max_nrow, max_ncol;
@@ -47,6 +64,9 @@ struct DevSym {
   const int *xch_t, *xch_ub, *xch_ue;
   const int64_t *xch_slotw, *xch_slotf;
   int64_t nslotw, nslotf;
+  // first extra chunk of every target that has extra chunks, level by level
+  const int *xfst;
+  const UpdMeta *upd_meta;
   // P-MATRIX items (nw consecutive columns): union of the columns' etree paths, ascending
   const int64_t *pm_ptr;
   const int *pm_sn;
@@ -85,8 +105,9 @@ void launch_ychol_level(const DevSym &S, int lvl_begin, int lvl_count, int ncand
                         const double *alpha, const double *Ybase, const double *dY, double *Nbuf,
                         double *Dbuf, int *status, const double *Pf, cudaStream_t st);
 // partial sums of the extra update chunks [x0, x0+nx) for ncand candidates into Pf
-void launch_ychol_partials(const DevSym &S, int x0, int nx, int ncand, const double *Nbuf,
-                           double *Pf, const int *status, cudaStream_t st);
+// (then summed per target into the slot of its first extra chunk: xfst[f0 .. f0+nf))
+void launch_ychol_partials(const DevSym &S, int x0, int nx, int f0, int nf, int ncand,
+                           const double *Nbuf, double *Pf, const int *status, cudaStream_t st);
 size_t ychol_smem_bytes(const DevSym &S);
 // Algorithm 1: L̂ from X̄ clique by clique.
 void launch_alg1(const DevSym &S, const double *Xbar, double *Lhat, double *DL, int *status,
@@ -94,8 +115,10 @@ void launch_alg1(const DevSym &S, const double *Xbar, double *Lhat, double *DL, 
 size_t alg1_smem_bytes(const DevSym &S);
 // Level-scheduled supernodal solves of the columns of W (row-major n x ldw, ncolsW columns):
 // forward (L^{-1}, levels bottom-up) or backward (L^{-T}, top-down).  Returns the launch count.
-// lvl_xptr_host: per level, range of extra update chunks; Pw: partial buffer (nslotw rows of ldw)
-int lsolve(const DevSym &S, const int *lvl_ptr_host, const int *lvl_xptr_host, int height, bool fwd,
+// lvl_xptr_host: per level, range of extra update chunks; lvl_fptr_host: per level, range of
+// xfst (targets with extra chunks); Pw: partial buffer (nslotw rows of ldw)
+int lsolve(const DevSym &S, const int *lvl_ptr_host, const int *lvl_xptr_host,
+           const int *lvl_fptr_host, const LsLevel *lvl_info, int height, bool fwd,
            const double *L, const double *D, double *W, int64_t ldw, int ncolsW, const LsSkip &sk,
            double *Pw, cudaStream_t st);
 void launch_rhs_unit(double *W, int64_t ldw, const int *rowof, int nrhs, cudaStream_t st);
@@ -141,15 +164,18 @@ int dense_backsolve(const double *B, int64_t ldb, int m, const double *Linv, dou
                     cudaStream_t st);
 int dense_chol_f32(float *B, int64_t ldb, int m, int *status, float *Linv, cudaStream_t st,
                    cudaStream_t st2, cudaEvent_t *ev_next, cudaEvent_t *ev_rest);
-// Mixed precision: B32 <- FP32 Cholesky factor of lower(B) (with L^T in the upper triangle)
-// and g <- row m of B (the right-hand side border), r <- g, x <- 0
-int mixed_factor(const double *B, int64_t ldb, int m, float *B32, float *Linv32, int *status,
+// Mixed precision.  mixed_factor: B made fully symmetric (strict upper <- lower^T), B32 <- FP32
+// Cholesky factor of B (L^T in its strict upper triangle), g <- row m of B (the right-hand side
+// border), r <- g, x <- 0.
+int mixed_factor(double *B, int64_t ldb, int m, float *B32, float *Linv32, int *status,
                  double *g, double *r, double *x, cudaStream_t st, cudaStream_t st2,
                  cudaEvent_t *ev_next, cudaEvent_t *ev_rest);
-// one refinement step: x += (L32 L32^T)^{-1} r, y = B x and ay = |B||x| (FP64), r = g - y,
-// norms = (max|r|, max(ay + |g|))
+// number of column chunks of the refinement's matrix-vector product (P, A hold chunks x m)
+int mixed_chunks(int m);
+// one refinement step: x += (L32 L32^T)^{-1} r, then r = g - B x (FP64) and
+// norms = (max|r|, max(|B||x| + |g|))
 int mixed_refine_step(const double *B, int64_t ldb, int m, const float *L32, const float *Linv32,
-                      const double *g, double *x, double *r, double *y, double *ay, double *norms,
+                      const double *g, double *x, double *r, double *P, double *A, double *norms,
                       cudaStream_t st);
 void launch_rhs_border(const DevSym &S, double *B, int64_t ldb, const double *hvec, double betamu,
                        cudaStream_t st);

@@ -5,6 +5,7 @@
 // A right-looking blocked factorisation of the leading m columns carries that row through the
 // panel solves and trailing updates, so on exit row m holds (L^{-1} g)^T and only the backward
 // substitution L^T dz = L^{-1} g remains.  FP64 throughout.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -19,110 +20,132 @@ constexpr int NB = 32;  // panel width (FP64 on one SM is slow: a narrow panel k
                         // serial factor-and-invert step short)
 
 // Cholesky of the nb x nb diagonal block at (k0, k0), one CTA of 256 threads, and the inverse
-// of the factor (stored in Linv, nb x nb column-major, ld NB).  Thread (r, q) = (tid % NB,
-// tid / NB) owns row r and every 8th column of the trailing update; the inverse is formed
-// row-step by row-step with all threads (T <- rows of L^{-1}), not one column per thread.
+// of the factor (stored in Linv, nb x nb column-major, ld NB).  The serial column loop is the
+// critical path of the whole factorisation.  FP64 on this part issues one warp instruction per
+// 64 cycles per SM sub-partition whatever the number of active lanes, so the work of every step
+// is packed densely over the threads: step j updates the s(s+1)/2 entries of the trailing
+// triangle (s = nb-1-j) through a packed (row, column) table, and step k of the inverse the
+// (nb-1-k)(k+1) entries below row k.  The loop carries one reciprocal per column and no square
+// root: it forms A = U D U^T (U unit lower), then L = U D^{1/2} and L^{-1} = D^{-1/2} U^{-1},
+// the nb square roots taken in parallel after the loop and U^{-1} found by forward elimination.
 template <class T>
 __global__ void k_potrf_diag(T *B, int64_t ldb, int k0, int nb, int *status, T *Linv) {
   constexpr int LD = NB + 1;
-  constexpr int NQ = 256 / NB;
-  __shared__ T A[NB * LD];  // row-major, padded
-  __shared__ T Ti[NB * LD];  // inverse, row-major
-  __shared__ T piv[2];
+  constexpr int NP = NB * (NB - 1) / 2;  // packed trailing-triangle size for s = NB - 1
+  __shared__ T A[NB * LD];   // working copy, row-major; the trailing part is updated in place
+  __shared__ T U[NB * LD];   // unit lower factor, row-major
+  __shared__ T V[NB * LD];   // U^{-1}, row-major
+  __shared__ T rd[NB], dd[NB];
+  __shared__ unsigned char pr[NP], pc[NP];  // packed index e -> (row, column), column <= row
   const int tid = threadIdx.x;
-  const int r = tid % NB, q = tid / NB;
   for (int idx = tid; idx < NB * NB; idx += 256) {
     const int i = idx % NB, j = idx / NB;
     A[i * LD + j] = (i >= j && i < nb && j < nb) ? B[(k0 + i) + (int64_t)(k0 + j) * ldb] : T(0);
-    Ti[i * LD + j] = (i == j) ? T(1) : T(0);
+    V[i * LD + j] = (i == j) ? T(1) : T(0);
+    U[i * LD + j] = (i == j) ? T(1) : T(0);
   }
+  if (tid < NB - 1)
+    for (int c = 0; c <= tid; ++c) {
+      pr[tid * (tid + 1) / 2 + c] = (unsigned char)tid;
+      pc[tid * (tid + 1) / 2 + c] = (unsigned char)c;
+    }
   __syncthreads();
   bool bad = false;
   for (int j = 0; j < nb; ++j) {
-    if (tid == 0) {
-      T d = A[j * LD + j];
-      if (!(d > T(0))) {
-        bad = true;
-        d = T(1);
+    if (tid < 32) {  // warp 0: pivot, its reciprocal and the scaled column j
+      T rj = T(0);
+      if (tid == 0) {
+        T d = A[j * LD + j];
+        if (!(d > T(0))) {
+          bad = true;
+          d = T(1);
+        }
+        dd[j] = d;
+        rj = T(1) / d;
+        rd[j] = rj;
       }
-      const T sd = sqrt(d);
-      piv[0] = sd;
-      piv[1] = T(1) / sd;
+      rj = __shfl_sync(0xffffffffu, rj, 0);
+      const int r = j + 1 + tid;
+      if (r < nb) U[r * LD + j] = A[r * LD + j] * rj;
     }
     __syncthreads();
-    if (q == 0 && r < nb) {
-      if (r == j) A[j * LD + j] = piv[0];
-      else if (r > j) A[r * LD + j] *= piv[1];
-    }
-    __syncthreads();
-    if (r > j && r < nb) {
-      const T arj = A[r * LD + j];
-      for (int kk = j + 1 + q; kk <= r; kk += NQ) A[r * LD + kk] -= arj * A[kk * LD + j];
+    // trailing triangle rows/columns j+1 .. nb-1; column j is only read
+    const int s = nb - 1 - j, np = s * (s + 1) / 2;
+    for (int e = tid; e < np; e += 256) {
+      const int r = j + 1 + pr[e], kk = j + 1 + pc[e];
+      A[r * LD + kk] -= U[r * LD + j] * A[kk * LD + j];
     }
     __syncthreads();
   }
   if (bad && tid == 0) atomicOr(status, ST_NOT_PD);
-  // T = L^{-1}: forward elimination on the identity, one pivot row at a time; step k scales row
-  // k of T by 1/L[k][k] and removes L[i][k] times it from the rows i > k (all threads)
-  for (int k = 0; k < nb; ++k) {
-    const T rk = T(1) / A[k * LD + k];
-    __syncthreads();
-    if (q == 0 && r <= k) Ti[k * LD + r] *= rk;
-    __syncthreads();
-    // rows i > k, columns c <= k
-    for (int e = tid; e < (nb - k - 1) * (k + 1); e += 256) {
-      const int i = k + 1 + e / (k + 1), c = e % (k + 1);
-      Ti[i * LD + c] -= A[i * LD + k] * Ti[k * LD + c];
+  if (tid < nb) {
+    const T sq = sqrt(dd[tid]);
+    dd[tid] = sq;
+    rd[tid] = T(1) / sq;
+  }
+  // V = U^{-1}: step k removes U[r][k] times row k (final) from the rows r > k
+  for (int k = 0; k < nb - 1; ++k) {
+    const int w = k + 1, cnt = (nb - 1 - k) * w;
+    for (int e = tid; e < cnt; e += 256) {
+      const int r = k + 1 + e / w, c = e - (e / w) * w;
+      V[r * LD + c] -= U[r * LD + k] * V[k * LD + c];
     }
+    __syncthreads();
   }
   __syncthreads();
   for (int idx = tid; idx < NB * NB; idx += 256) {
     const int i = idx % NB, j = idx / NB;
-    if (i < nb && j < nb && i >= j) B[(k0 + i) + (int64_t)(k0 + j) * ldb] = A[i * LD + j];
-    Linv[i + j * NB] = (i < nb && j < nb && i >= j) ? Ti[i * LD + j] : T(0);
+    const bool in = i < nb && j < nb && i >= j;
+    if (in) B[(k0 + i) + (int64_t)(k0 + j) * ldb] = (i == j) ? dd[j] : U[i * LD + j] * dd[j];
+    Linv[i + j * NB] = in ? V[i * LD + j] * rd[i] : T(0);
   }
 }
 
-// Rows [r0, rend) of the panel columns [k0, k0+nb): X <- X L_kk^{-T} = X Linv^T.  CTA = 16 rows
-// x nb columns (256 threads, 4 outputs each), so the panel solve spreads over many SMs.
-constexpr int TRSM_ROWS = 16;
+// Rows [r0, rend) of the panel columns [k0, k0+nb): X <- X L_kk^{-T} = X Linv^T.  CTA = 4 rows
+// x 32 columns (128 threads, one output each: thread = (row, column = lane)); a CTA owns whole
+// rows, so it solves them in place.  Small CTAs spread the panel solve over all SMs (FP64 runs
+// at two lanes per cycle per SM here).
+constexpr int TRSM_ROWS = 4;
 template <class T>
 __global__ void k_trsm_panel(T *B, int64_t ldb, int k0, int nb, int r0, int rend,
                              const T *__restrict__ Linv) {
-  extern __shared__ __align__(16) unsigned char smt_raw[];
-  T *smt = reinterpret_cast<T *>(smt_raw);
-  T *Xs = smt;                   // [l][row], TRSM_ROWS rows
-  T *Ts = smt + NB * TRSM_ROWS;  // [l][col] = Linv[col][l], NB columns
-  const int tid = threadIdx.x;
-  const int rb = r0 + blockIdx.x * TRSM_ROWS;
-  for (int idx = tid; idx < nb * TRSM_ROWS; idx += 256) {
-    const int rr = idx % TRSM_ROWS, l = idx / TRSM_ROWS;
-    const int gi = rb + rr;
-    Xs[l * TRSM_ROWS + rr] = (gi < rend) ? B[gi + (int64_t)(k0 + l) * ldb] : T(0);
-  }
-  for (int idx = tid; idx < nb * NB; idx += 256) {
-    const int cc = idx % NB, l = idx / NB;
-    Ts[l * NB + cc] = Linv[cc + l * NB];
+  __shared__ T Xs[TRSM_ROWS][NB + 1];
+  __shared__ T Ts[NB][NB + 1];  // Ts[l][c] = Linv[c][l]
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int gi = r0 + blockIdx.x * TRSM_ROWS + w;
+  Xs[w][lane] = (gi < rend && lane < nb) ? B[gi + (int64_t)(k0 + lane) * ldb] : T(0);
+  for (int idx = tid; idx < NB * NB; idx += TRSM_ROWS * 32) {
+    const int c = idx % NB, l = idx / NB;
+    Ts[l][c] = Linv[c + l * NB];
   }
   __syncthreads();
-  constexpr int CPT = NB * TRSM_ROWS / 256;  // columns per thread
-  const int tx = tid % (NB / CPT), ty = tid / (NB / CPT);
-  T acc[CPT];
-#pragma unroll
-  for (int t = 0; t < CPT; ++t) acc[t] = T(0);
-  for (int l = 0; l < nb; ++l) {
-    const T a = Xs[l * TRSM_ROWS + ty];
-#pragma unroll
-    for (int t = 0; t < CPT; ++t) acc[t] = fma(a, Ts[l * NB + tx * CPT + t], acc[t]);
+  T acc = T(0);
+#pragma unroll 8
+  for (int l = 0; l < NB; ++l) acc = fma(Xs[w][l], Ts[l][lane], acc);
+  if (gi < rend && lane < nb) B[gi + (int64_t)(k0 + lane) * ldb] = acc;
+}
+
+// Update of block column k+1 (columns [c0, c1), c1 - c0 <= 32) by panel k (columns [k0, k0+nb))
+// for the rows [c0, rend), lower part: C[i][c] -= sum_l P[i][l] P[c][l].  CTA = 4 rows x 32
+// columns (128 threads, thread = (row, column = lane)); on the critical path, so the work is
+// spread over many small CTAs.
+template <class T>
+__global__ void k_syrk_next(T *B, int64_t ldb, int k0, int nb, int c0, int c1, int rend) {
+  __shared__ T Pi[TRSM_ROWS][NB + 1];
+  __shared__ T Pc[NB][NB + 1];  // Pc[l][c] = P[c0 + c][l]
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int gi = c0 + blockIdx.x * TRSM_ROWS + w;
+  Pi[w][lane] = (gi < rend && lane < nb) ? B[gi + (int64_t)(k0 + lane) * ldb] : T(0);
+  for (int idx = tid; idx < NB * NB; idx += TRSM_ROWS * 32) {
+    const int c = idx % NB, l = idx / NB;
+    Pc[l][c] = (c0 + c < c1 && l < nb) ? B[(c0 + c) + (int64_t)(k0 + l) * ldb] : T(0);
   }
-  const int gi = rb + ty;
-  if (gi < rend) {
-#pragma unroll
-    for (int t = 0; t < CPT; ++t) {
-      const int c = tx * CPT + t;
-      if (c < nb) B[gi + (int64_t)(k0 + c) * ldb] = acc[t];
-    }
-  }
+  __syncthreads();
+  T acc = T(0);
+#pragma unroll 8
+  for (int l = 0; l < NB; ++l) acc = fma(Pi[w][l], Pc[l][lane], acc);
+  const int gc = c0 + lane;
+  if (gi < rend && gc < c1 && gi >= gc) B[gi + (int64_t)gc * ldb] -= acc;
 }
 
 // Trailing update C -= P P^T for the columns [c_lo, c_hi) of the rows [c_lo, rend), lower part
@@ -189,12 +212,10 @@ static void launch_syrk(T *B, int64_t ldb, int k0, int nb, int c_lo, int c_hi, i
 template <class T>
 static int dense_chol(T *B, int64_t ldb, int m, int rows, int *status, T *Linv_all, cudaStream_t st,
                       cudaStream_t st2, cudaEvent_t *ev_next, cudaEvent_t *ev_rest) {
-  const int smem_trsm = (NB * TRSM_ROWS + NB * NB) * (int)sizeof(T);
   const int smem_tile = 2 * NB * TS * (int)sizeof(T);
   static bool configured = false;
   if (!configured) {
     cudaFuncSetAttribute(k_syrk_tiles<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_tile);
-    cudaFuncSetAttribute(k_trsm_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_trsm);
     configured = true;
   }
   int launches = 0;
@@ -207,7 +228,7 @@ static int dense_chol(T *B, int64_t ldb, int m, int rows, int *status, T *Linv_a
     const int r0 = k0 + nb;
     const int nr = rows - r0;
     if (nr <= 0) continue;
-    k_trsm_panel<T><<<(nr + TRSM_ROWS - 1) / TRSM_ROWS, 256, smem_trsm, st>>>(B, ldb, k0, nb, r0, rows, Linv);
+    k_trsm_panel<T><<<(nr + TRSM_ROWS - 1) / TRSM_ROWS, TRSM_ROWS * 32, 0, st>>>(B, ldb, k0, nb, r0, rows, Linv);
     ++launches;
     const int c_next = r0 + NB < m ? r0 + NB : m;  // block column k+1 = [r0, c_next)
     if (!la) {
@@ -216,7 +237,7 @@ static int dense_chol(T *B, int64_t ldb, int m, int rows, int *status, T *Linv_a
       continue;
     }
     if (k >= 1) cudaStreamWaitEvent(st, ev_rest[(k - 1) & 1], 0);  // st2 finished panel k-1
-    launch_syrk<T>(B, ldb, k0, nb, r0, c_next, rows, smem_tile, st);
+    k_syrk_next<T><<<(nr + TRSM_ROWS - 1) / TRSM_ROWS, TRSM_ROWS * 32, 0, st>>>(B, ldb, k0, nb, r0, c_next, rows);
     cudaEventRecord(ev_next[k & 1], st);
     ++launches;
     if (c_next < m) {
@@ -348,136 +369,229 @@ void launch_B_to_user(const DevSym &S, const double *Bi, int64_t ldi, double *Bo
 // ---------------------------------------------------------------------------------------------
 // Mixed precision: FP32 factor of B, FP64 iterative refinement against the FP64 B.
 //
-// B32 <- lower(B) in FP32 (ld m)
-__global__ void k_lower_to_f32(const double *__restrict__ B, int64_t ldb, float *B32, int m) {
-  const int64_t tot = (int64_t)m * m;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(idx % m), j = (int)(idx / m);
-    if (i >= j) B32[idx] = (float)B[i + (int64_t)j * ldb];
+// Preparation, 32 x 32 tiles of the lower triangle (tile row ti >= tile column tj): B32 <- the
+// tile rounded to FP32 (ld m), and the FP64 B made fully symmetric (the tile's transpose written
+// into the strict upper triangle, staged through shared memory so both sides are coalesced), so
+// the refinement's matrix-vector product is a plain column-major product.
+__global__ void k_mixed_prep(double *B, int64_t ldb, float *B32, int m) {
+  __shared__ double t[32][33];
+  const int ti = blockIdx.x, tj = blockIdx.y;
+  if (ti < tj) return;
+  const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;  // 256 threads: 32 x 8
+  const int i0 = ti * 32, j0 = tj * 32;
+  for (int c = ly; c < 32; c += 8) {
+    const int i = i0 + lx, j = j0 + c;
+    double v = 0.0;
+    if (i < m && j < m && i >= j) {
+      v = B[i + (int64_t)j * ldb];
+      B32[i + (int64_t)j * m] = (float)v;
+    }
+    t[lx][c] = v;
+  }
+  __syncthreads();
+  // transposed write: B[j][i] for i > j, i.e. row j0+lx... column i0+c
+  for (int c = ly; c < 32; c += 8) {
+    const int j = j0 + lx, i = i0 + c;
+    if (i < m && j < m && i > j) B[j + (int64_t)i * ldb] = t[c][lx];
   }
 }
 
-// after the FP32 factorisation: copy L into the unused upper triangle as L^T (coalesced backward
-// substitution)
+// after the FP32 factorisation: L^T into the unused strict upper triangle of B32 (tiled
+// transpose), so the backward substitution reads it coalesced
 __global__ void k_lower_to_upper_f32(float *L, int m) {
-  const int64_t tot = (int64_t)m * m;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(idx % m), j = (int)(idx / m);
-    if (i > j) L[j + (int64_t)i * m] = L[idx];
+  __shared__ float t[32][33];
+  const int ti = blockIdx.x, tj = blockIdx.y;
+  if (ti < tj) return;
+  const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+  const int i0 = ti * 32, j0 = tj * 32;
+  for (int c = ly; c < 32; c += 8) {
+    const int i = i0 + lx, j = j0 + c;
+    t[lx][c] = (i < m && j < m && i > j) ? L[i + (int64_t)j * m] : 0.f;
+  }
+  __syncthreads();
+  for (int c = ly; c < 32; c += 8) {
+    const int j = j0 + lx, i = i0 + c;
+    if (i < m && j < m && i > j) L[j + (int64_t)i * m] = t[c][lx];
   }
 }
 
-// x += L^{-T} L^{-1} r with the FP32 factor (ld m; L^T in the upper triangle) and the inverses of
-// its NB x NB diagonal blocks; one CTA of 1024 threads, the vector in shared memory (m floats).
-__global__ void k_refine_solve_f32(const float *__restrict__ L, int m, const float *__restrict__ Linv,
-                                   const double *__restrict__ r, double *x) {
-  extern __shared__ float ys[];
+// x += L^{-T} L^{-1} r with the FP32 factor (ld m; L^T in the strict upper triangle) and the
+// inverses of its NB x NB diagonal blocks.  One cluster of RCL CTAs: row block kb belongs to CTA
+// kb % RCL, which keeps those rows of the vector in its shared memory.  Step kb of the forward
+// substitution: the owner forms y_kb = Linv_kb (rows kb) and writes it into every CTA's shared
+// memory (distributed shared memory), one cluster barrier, then every CTA removes L_{i,kb} y_kb
+// from its own rows i below the block.  The backward substitution runs the same way from the
+// last block with L^T.  Each thread loads the factor entries of its next update before the
+// barrier, so their latency overlaps the owner's step.  Per step: one hardware cluster barrier
+// (no spin loop).
+constexpr int RCL = 8;
+constexpr int RTH = 256;
+__global__ void __cluster_dims__(RCL, 1, 1) __launch_bounds__(RTH)
+    k_refine_solve_f32(const float *__restrict__ L, int m, const float *__restrict__ Linv,
+                       const double *__restrict__ r, double *x) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ float ys[];  // m floats; the CTA's own rows are used
+  __shared__ float yb[2][NB];
   __shared__ float tb[NB];
-  const int tid = threadIdx.x, bd = blockDim.x;
-  for (int i = tid; i < m; i += bd) ys[i] = (float)r[i];
-  __syncthreads();
+  const int rank = (int)cl.block_rank();
+  const int tid = threadIdx.x;
   const int nblk = (m + NB - 1) / NB;
-  // forward: y = L^{-1} r, right-looking by blocks
-  for (int kb = 0; kb < nblk; ++kb) {
-    const int b0 = kb * NB, nb = m - b0 < NB ? m - b0 : NB;
-    const float *Li = Linv + (int64_t)kb * NB * NB;
-    if (tid < nb) {
-      float a = 0.f;
-      for (int l = 0; l <= tid; ++l) a = fmaf(Li[tid + l * NB], ys[b0 + l], a);
-      tb[tid] = a;
-    }
-    __syncthreads();
-    if (tid < nb) ys[b0 + tid] = tb[tid];
-    __syncthreads();
-    for (int i = b0 + nb + tid; i < m; i += bd) {
-      float a = 0.f;
-      for (int l = 0; l < nb; ++l) a = fmaf(L[i + (int64_t)(b0 + l) * m], tb[l], a);
-      ys[i] -= a;
-    }
-    __syncthreads();
-  }
-  // backward: x = L^{-T} y, by blocks from the last; L^T read from the upper triangle
-  for (int kb = nblk - 1; kb >= 0; --kb) {
-    const int b0 = kb * NB, nb = m - b0 < NB ? m - b0 : NB;
-    const float *Li = Linv + (int64_t)kb * NB * NB;
-    if (tid < nb) {
-      float a = 0.f;
-      for (int l = tid; l < nb; ++l) a = fmaf(Li[l + tid * NB], ys[b0 + l], a);  // Linv[l][tid]
-      tb[tid] = a;
-    }
-    __syncthreads();
-    if (tid < nb) ys[b0 + tid] = tb[tid];
-    __syncthreads();
-    for (int i = tid; i < b0; i += bd) {
-      float a = 0.f;
-      for (int l = 0; l < nb; ++l) a = fmaf(L[i + (int64_t)(b0 + l) * m], tb[l], a);  // L^T[i][b0+l]
-      ys[i] -= a;
-    }
-    __syncthreads();
-  }
-  for (int i = tid; i < m; i += bd) x[i] += (double)ys[i];
-}
-
-// y = B x and ay_i = sum_j |B_ij x_j| for the symmetric B stored in its lower triangle (FP64).
-// CTA = 32 rows (256 threads): the part j <= i is read along rows (lane = row, 8 column phases),
-// the part j > i along the columns of the block (warp = column, lanes over j), both coalesced.
-__global__ void k_symv_f64(const double *__restrict__ B, int64_t ldb, int m,
-                           const double *__restrict__ x, double *y, double *ay) {
-  __shared__ double p1[8][33], a1[8][33];
-  __shared__ double p2[32], a2[32];
-  const int il = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int ib = blockIdx.x * 32, i = ib + il;
-  double s = 0.0, sa = 0.0;
-  if (i < m)
-    for (int j = w; j <= i; j += 8) {
-      const double v = B[i + (int64_t)j * ldb] * x[j];
-      s += v;
-      sa += fabs(v);
-    }
-  p1[w][il] = s;
-  a1[w][il] = sa;
-  for (int cc = w; cc < 32; cc += 8) {
-    const int ii = ib + cc;
-    double t = 0.0, ta = 0.0;
-    if (ii < m)
-      for (int j = ii + 1 + il; j < m; j += 32) {
-        const double v = B[j + (int64_t)ii * ldb] * x[j];
-        t += v;
-        ta += fabs(v);
-      }
-    for (int o = 16; o > 0; o >>= 1) {
-      t += __shfl_xor_sync(0xffffffffu, t, o);
-      ta += __shfl_xor_sync(0xffffffffu, ta, o);
-    }
-    if (il == 0) {
-      p2[cc] = t;
-      a2[cc] = ta;
-    }
-  }
+  for (int i = tid; i < m; i += RTH)
+    if ((i / NB) % RCL == rank) ys[i] = (float)r[i];
   __syncthreads();
-  if (w == 0 && i < m) {
-    double r = p2[il], ra = a2[il];
-    for (int q = 0; q < 8; ++q) {
-      r += p1[q][il];
-      ra += a1[q][il];
+  int step = 0;
+  // ---- forward: y = L^{-1} r
+  for (int kb = 0; kb < nblk; ++kb, ++step) {
+    const int b0 = kb * NB, nb = min(NB, m - b0), buf = step & 1;
+    // own row blocks after kb: kb' = first + q * RCL
+    const int first = kb + 1 + ((rank - (kb + 1)) % RCL + RCL) % RCL;
+    const int nown = first < nblk ? (nblk - 1 - first) / RCL + 1 : 0;
+    // prefetch the first slot's factor entries
+    const int slot0 = tid;
+    float lv[NB];
+    int i0 = -1;
+    if (slot0 < nown * NB) {
+      i0 = (first + (slot0 / NB) * RCL) * NB + slot0 % NB;
+      if (i0 < m) {
+#pragma unroll
+        for (int l = 0; l < NB; ++l) lv[l] = (l < nb) ? L[i0 + (int64_t)(b0 + l) * m] : 0.f;
+      } else {
+        i0 = -1;
+      }
     }
-    y[i] = r;
-    ay[i] = ra;
+    if (kb % RCL == rank) {
+      if (tid < nb) {
+        const float *Li = Linv + (int64_t)kb * NB * NB;
+        float a = 0.f;
+        for (int l = 0; l <= tid; ++l) a = fmaf(Li[tid + l * NB], ys[b0 + l], a);
+        tb[tid] = a;
+      }
+      __syncthreads();
+      if (tid < NB) {  // the whole block, zero past nb, so the unrolled updates read no stale values
+        const float v = tid < nb ? tb[tid] : 0.f;
+        if (tid < nb) ys[b0 + tid] = v;
+        for (int q = 0; q < RCL; ++q) cl.map_shared_rank(&yb[buf][0], q)[tid] = v;
+      }
+    }
+    cl.sync();
+    if (i0 >= 0) {
+      float a = 0.f;
+#pragma unroll
+      for (int l = 0; l < NB; ++l) a = fmaf(lv[l], yb[buf][l], a);
+      ys[i0] -= a;
+    }
+    for (int slot = tid + RTH; slot < nown * NB; slot += RTH) {
+      const int i = (first + (slot / NB) * RCL) * NB + slot % NB;
+      if (i >= m) continue;
+      float a = 0.f;
+      for (int l = 0; l < nb; ++l) a = fmaf(L[i + (int64_t)(b0 + l) * m], yb[buf][l], a);
+      ys[i] -= a;
+    }
+    __syncthreads();
+  }
+  // ---- backward: x = L^{-T} y
+  for (int kb = nblk - 1; kb >= 0; --kb, ++step) {
+    const int b0 = kb * NB, nb = min(NB, m - b0), buf = step & 1;
+    // own row blocks before kb: kb' = q * RCL + rank < kb
+    const int nown = rank < kb ? (kb - 1 - rank) / RCL + 1 : 0;
+    float lv[NB];
+    int i0 = -1;
+    if (tid < nown * NB) {
+      i0 = (rank + (tid / NB) * RCL) * NB + tid % NB;
+#pragma unroll
+      for (int l = 0; l < NB; ++l) lv[l] = (l < nb) ? L[i0 + (int64_t)(b0 + l) * m] : 0.f;
+    }
+    if (kb % RCL == rank) {
+      if (tid < nb) {
+        const float *Li = Linv + (int64_t)kb * NB * NB;
+        float a = 0.f;
+        for (int l = tid; l < nb; ++l) a = fmaf(Li[l + tid * NB], ys[b0 + l], a);
+        tb[tid] = a;
+      }
+      __syncthreads();
+      if (tid < NB) {  // the whole block, zero past nb, so the unrolled updates read no stale values
+        const float v = tid < nb ? tb[tid] : 0.f;
+        if (tid < nb) ys[b0 + tid] = v;
+        for (int q = 0; q < RCL; ++q) cl.map_shared_rank(&yb[buf][0], q)[tid] = v;
+      }
+    }
+    cl.sync();
+    if (i0 >= 0) {
+      float a = 0.f;
+#pragma unroll
+      for (int l = 0; l < NB; ++l) a = fmaf(lv[l], yb[buf][l], a);
+      ys[i0] -= a;
+    }
+    for (int slot = tid + RTH; slot < nown * NB; slot += RTH) {
+      const int i = (rank + (slot / NB) * RCL) * NB + slot % NB;
+      float a = 0.f;
+      for (int l = 0; l < nb; ++l) a = fmaf(L[i + (int64_t)(b0 + l) * m], yb[buf][l], a);
+      ys[i] -= a;
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < m; i += RTH)
+    if ((i / NB) % RCL == rank) x[i] += (double)ys[i];
+  cl.sync();  // no CTA leaves while another may still write into its shared memory
+}
+
+// Partial products of y = B x with the full symmetric FP64 B (column-major): CTA (row block of
+// 32, column chunk J of MV_CHUNK columns), 256 threads = 32 rows x 8 column phases; writes
+// P[J][i] = sum_{j in J} B_ij x_j and A[J][i] = sum_{j in J} |B_ij x_j|.
+constexpr int MV_CHUNK = 256;
+__global__ void k_gemv_part(const double *__restrict__ B, int64_t ldb, int m,
+                            const double *__restrict__ x, double *P, double *A) {
+  __shared__ double ps[8][33], as[8][33];
+  const int il = threadIdx.x & 31, ph = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + il;
+  const int j0 = blockIdx.y * MV_CHUNK, j1 = min(m, j0 + MV_CHUNK);
+  double s0 = 0.0, s1 = 0.0, a0 = 0.0, a1 = 0.0;
+  if (i < m) {
+    int j = j0 + ph;
+    for (; j + 8 < j1; j += 16) {
+      const double v0 = B[i + (int64_t)j * ldb] * x[j];
+      const double v1 = B[i + (int64_t)(j + 8) * ldb] * x[j + 8];
+      s0 += v0;
+      s1 += v1;
+      a0 += fabs(v0);
+      a1 += fabs(v1);
+    }
+    for (; j < j1; j += 8) {
+      const double v0 = B[i + (int64_t)j * ldb] * x[j];
+      s0 += v0;
+      a0 += fabs(v0);
+    }
+  }
+  ps[ph][il] = s0 + s1;
+  as[ph][il] = a0 + a1;
+  __syncthreads();
+  if (ph == 0 && i < m) {
+    double u = 0.0, v = 0.0;
+    for (int q = 0; q < 8; ++q) {
+      u += ps[q][il];
+      v += as[q][il];
+    }
+    P[(int64_t)blockIdx.y * m + i] = u;
+    A[(int64_t)blockIdx.y * m + i] = v;
   }
 }
 
-// r = g - y; out[0] = max_i |r_i|, out[1] = max_i (ay_i + |g_i|)  (one CTA)
-__global__ void k_resid(const double *__restrict__ g, const double *__restrict__ y,
-                        const double *__restrict__ ay, double *r, int m, double *out) {
+// r = g - sum_J P[J]; out[0] = max_i |r_i|, out[1] = max_i (sum_J A[J][i] + |g_i|)  (one CTA)
+__global__ void k_resid(const double *__restrict__ g, const double *__restrict__ P,
+                        const double *__restrict__ A, int nchunk, double *r, int m, double *out) {
   __shared__ double mr[32], mg[32];
   double ar = 0.0, ag = 0.0;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    const double v = g[i] - y[i];
+    double y = 0.0, ay = 0.0;
+    for (int q = 0; q < nchunk; ++q) {
+      y += P[(int64_t)q * m + i];
+      ay += A[(int64_t)q * m + i];
+    }
+    const double v = g[i] - y;
     r[i] = v;
     ar = fmax(ar, fabs(v));
-    ag = fmax(ag, ay[i] + fabs(g[i]));
+    ag = fmax(ag, ay + fabs(g[i]));
   }
   for (int o = 16; o > 0; o >>= 1) {
     ar = fmax(ar, __shfl_down_sync(0xffffffffu, ar, o));
@@ -510,27 +624,29 @@ __global__ void k_mixed_init(const double *__restrict__ B, int64_t ldb, int m, d
   }
 }
 
-int mixed_factor(const double *B, int64_t ldb, int m, float *B32, float *Linv32, int *status,
+int mixed_chunks(int m) { return (m + MV_CHUNK - 1) / MV_CHUNK; }
+
+int mixed_factor(double *B, int64_t ldb, int m, float *B32, float *Linv32, int *status,
                  double *g, double *r, double *x, cudaStream_t st, cudaStream_t st2,
                  cudaEvent_t *ev_next, cudaEvent_t *ev_rest) {
   k_mixed_init<<<(m + 255) / 256, 256, 0, st>>>(B, ldb, m, g, r, x);
-  int blocks = (int)(((int64_t)m * m + 255) / 256);
-  if (blocks > 8192) blocks = 8192;
-  k_lower_to_f32<<<blocks, 256, 0, st>>>(B, ldb, B32, m);
-  int nl = 1 + dense_chol_f32(B32, m, m, status, Linv32, st, st2, ev_next, ev_rest);
-  k_lower_to_upper_f32<<<blocks, 256, 0, st>>>(B32, m);
-  return nl + 2;
+  const int nt = (m + 31) / 32;
+  k_mixed_prep<<<dim3(nt, nt), 256, 0, st>>>(B, ldb, B32, m);
+  int nl = 2 + dense_chol_f32(B32, m, m, status, Linv32, st, st2, ev_next, ev_rest);
+  k_lower_to_upper_f32<<<dim3(nt, nt), 256, 0, st>>>(B32, m);
+  return nl + 1;
 }
 
 int mixed_refine_step(const double *B, int64_t ldb, int m, const float *L32, const float *Linv32,
-                      const double *g, double *x, double *r, double *y, double *ay, double *norms,
+                      const double *g, double *x, double *r, double *P, double *A, double *norms,
                       cudaStream_t st) {
   const size_t smem = (size_t)m * sizeof(float);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_refine_solve_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_refine_solve_f32<<<1, 1024, smem, st>>>(L32, m, Linv32, r, x);
-  k_symv_f64<<<(m + 31) / 32, 256, 0, st>>>(B, ldb, m, x, y, ay);
-  k_resid<<<1, 1024, 0, st>>>(g, y, ay, r, m, norms);
+  k_refine_solve_f32<<<RCL, RTH, smem, st>>>(L32, m, Linv32, r, x);
+  const int nch = mixed_chunks(m);
+  k_gemv_part<<<dim3((m + 31) / 32, nch), 256, 0, st>>>(B, ldb, m, x, P, A);
+  k_resid<<<1, 1024, 0, st>>>(g, P, A, nch, r, m, norms);
   return 3;
 }
 

@@ -140,26 +140,32 @@ __global__ void k_lfwd_partial(DevSym S, int x0, int ntiles, const double *__res
     for (int c = 0; c < ncol; ++c) P[(int64_t)c * ldw] = acc[c * 32 + lane];
 }
 
-// W[S_t] += sum of the partial slots of t (in chunk order), one thread per (row of S_t, column),
-// for every target of the level that has extra update chunks (grid row y = chunk index; only
-// the first chunk of each target does the work)
-__global__ void k_lfwd_reduce(DevSym S, int x0, int nx, const double *__restrict__ Pw, double *W,
+// W[S_t] += sum of the partial slots of t, for every target of the level with extra update
+// chunks.  CTA = (32 columns, row c of S_t, target) x 8 chunk phases: phase p sums the chunks
+// xb + p, xb + p + 8, ..., then the 8 phase sums are added in order (deterministic).
+__global__ void k_lfwd_reduce(DevSym S, int f0, const double *__restrict__ Pw, double *W,
                               int64_t ldw, int ncolsW, LsSkip sk) {
-  const int x = x0 + blockIdx.y;
-  if (x >= x0 + nx) return;
-  const int t = S.xch_t[x];
-  if (S.xch_beg[t] != x) return;
+  __shared__ double part[8][33];
+  const int xb = S.xfst[f0 + blockIdx.z];
+  const int t = S.xch_t[xb];
   const int c0 = S.sn_col[t];
   const int ncol = S.sn_col[t + 1] - c0;
-  const int xb = S.xch_beg[t], xe = S.xch_end[t];
-  const int64_t tot = (int64_t)ncol * ncolsW;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e / ncolsW), col = (int)(e % ncolsW);
-    if (ls_skip(sk, t, col / 32)) continue;
-    double sacc = 0.0;
-    for (int xx = xb; xx < xe; ++xx) sacc += Pw[(S.xch_slotw[xx] + c) * ldw + col];
-    W[(int64_t)(c0 + c) * ldw + col] += sacc;
+  const int c = blockIdx.y;
+  if (c >= ncol) return;
+  const int tile = blockIdx.x;
+  if (ls_skip(sk, t, tile)) return;
+  const int lane = threadIdx.x & 31, ph = threadIdx.x >> 5;
+  const int col = tile * 32 + lane;
+  const int xe = S.xch_end[t];
+  double a = 0.0;
+  if (col < ncolsW)
+    for (int xx = xb + ph; xx < xe; xx += 8) a += Pw[(S.xch_slotw[xx] + c) * ldw + col];
+  part[ph][lane] = a;
+  __syncthreads();
+  if (ph == 0 && col < ncolsW) {
+    double s = part[0][lane];
+    for (int q = 1; q < 8; ++q) s += part[q][lane];
+    W[(int64_t)(c0 + c) * ldw + col] += s;
   }
 }
 
@@ -274,7 +280,302 @@ __global__ void k_lbwd(DevSym S, int lvl_begin, int ntiles, const double *__rest
   }
 }
 
-int lsolve(const DevSym &S, const int *lvl_ptr_host, const int *lvl_xptr_host, int height, bool fwd,
+// ---------------------------------------------------------------------------------------------
+// Staged forms.  Every operand a CTA needs (its D block, its acc rows of W, the update blocks and
+// source values, the gathered ancestor rows of W) is copied into shared memory with cp.async, so
+// a CTA waits for memory about once instead of once per dependent load; the update blocks go
+// through a ring of LS_R buffers, LS_R - 1 chunks in flight while one is applied.  Each CTA is
+// one warp; shared memory is sized per level (small supernodes at the bottom of the tree keep
+// many CTAs per SM).
+constexpr int LS_R = 4;
+
+__device__ __forceinline__ void cpa8(void *s, const void *g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(s)),
+               "l"(g)
+               : "memory");
+}
+__device__ __forceinline__ void cpa4(void *s, const void *g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(s)),
+               "l"(g)
+               : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__host__ __device__ inline int al16(int b) { return (b + 15) & ~15; }
+
+struct FwdLayout {
+  int acc, ds, meta, buf, bufsz, total;
+};
+// nc: ncol bound, cw/np: update chunk width / rows bound (cw = 0: no updates), with_d: D block
+__host__ __device__ inline FwdLayout fwd_layout(int nc, int cw, int np, bool with_d) {
+  FwdLayout L;
+  int o = 0;
+  L.acc = o;
+  o += al16(nc * 32 * 8);
+  L.ds = o;
+  o += with_d ? al16(nc * nc * 8) : 0;
+  L.meta = o;
+  o += cw > 0 ? 64 * (int)sizeof(UpdMeta) : 0;
+  L.buf = o;
+  L.bufsz = cw > 0 ? al16(cw * 32 * 8) + al16(cw * np * 8) + al16(np * 4) : 0;
+  o += LS_R * L.bufsz;
+  L.total = o;
+  return L;
+}
+
+struct BwdLayout {
+  int ls, ds, acc, wv, rws, total;
+};
+__host__ __device__ inline BwdLayout bwd_layout(int nr, int nc) {
+  BwdLayout L;
+  int o = 0;
+  L.ls = o;
+  o += al16(nr * nc * 8);
+  L.ds = o;
+  o += al16(nc * nc * 8);
+  L.acc = o;
+  o += al16(nc * 32 * 8);
+  L.wv = o;
+  o += al16(nr * 32 * 8);
+  L.rws = o;
+  o += al16(nr * 4);
+  L.total = o;
+  return L;
+}
+
+// acc[srel[p]][lane] -= sum over the updates [ub, ue) of L_d[p1 + p, :] W[S_d], the update
+// blocks taken in chunks of <= cw source columns through the ring
+__device__ __forceinline__ void pull_staged(const DevSym &S, int ub, int ue, const double *L,
+                                            const double *Wc, int64_t ldw, double *acc,
+                                            unsigned char *sm, const FwdLayout &lay, int cw, int npb,
+                                            int lane) {
+  UpdMeta *ms = reinterpret_cast<UpdMeta *>(sm + lay.meta);
+  int meta_end = ub;
+  int iu = ub, ij = 0, issued = 0;
+  const int xs_off = 0, lb_off = al16(cw * 32 * 8), sr_off = lb_off + al16(cw * npb * 8);
+  auto issue = [&]() {
+    if (iu < ue) {
+      while (iu >= meta_end) {  // next 32 records into the metadata ring (64 entries)
+        const int v = meta_end + lane;
+        if (v < ue) ms[v & 63] = S.upd_meta[v];
+        meta_end += 32;
+        __syncwarp();
+      }
+      const UpdMeta m = ms[iu & 63];
+      unsigned char *b = sm + lay.buf + (issued % LS_R) * lay.bufsz;
+      double *xs = reinterpret_cast<double *>(b + xs_off);
+      double *Lb = reinterpret_cast<double *>(b + lb_off);
+      int *sr = reinterpret_cast<int *>(b + sr_off);
+      const int w = min(cw, m.dncol - ij);
+      for (int q = 0; q < w; ++q) cpa8(xs + q * 32 + lane, Wc + (int64_t)(m.dc0 + ij + q) * ldw);
+      const double *Lsrc = L + m.valp + (int64_t)ij * m.dnrow + m.p1;
+      for (int e = lane; e < m.np * w; e += 32) {
+        const int q = e / m.np, p = e - q * m.np;
+        cpa8(Lb + e, Lsrc + (int64_t)q * m.dnrow + p);
+      }
+      for (int p = lane; p < m.np; p += 32) cpa4(sr + p, S.upd_rel + m.relptr + p);
+      ij += w;
+      if (ij >= m.dncol) {
+        ++iu;
+        ij = 0;
+      }
+    }
+    cpa_commit();
+    ++issued;
+  };
+  for (int k = 0; k < LS_R - 1; ++k) issue();
+  int cu = ub, cj = 0, done = 0;
+  while (cu < ue) {
+    issue();
+    cpa_wait<LS_R - 1>();
+    __syncwarp();
+    const UpdMeta m = ms[cu & 63];
+    const unsigned char *b = sm + lay.buf + (done % LS_R) * lay.bufsz;
+    const double *xs = reinterpret_cast<const double *>(b + xs_off);
+    const double *Lb = reinterpret_cast<const double *>(b + lb_off);
+    const int *sr = reinterpret_cast<const int *>(b + sr_off);
+    const int w = min(cw, m.dncol - cj), np = m.np;
+    int p = 0;
+    for (; p + 3 < np; p += 4) {
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      for (int q = 0; q < w; ++q) {
+        const double x = xs[q * 32 + lane];
+        const double *lq = Lb + q * np + p;
+        a0 = fma(lq[0], x, a0);
+        a1 = fma(lq[1], x, a1);
+        a2 = fma(lq[2], x, a2);
+        a3 = fma(lq[3], x, a3);
+      }
+      acc[sr[p] * 32 + lane] -= a0;
+      acc[sr[p + 1] * 32 + lane] -= a1;
+      acc[sr[p + 2] * 32 + lane] -= a2;
+      acc[sr[p + 3] * 32 + lane] -= a3;
+    }
+    for (; p < np; ++p) {
+      double a0 = 0.0;
+      for (int q = 0; q < w; ++q) a0 = fma(Lb[q * np + p], xs[q * 32 + lane], a0);
+      acc[sr[p] * 32 + lane] -= a0;
+    }
+    __syncwarp();
+    cj += w;
+    if (cj >= m.dncol) {
+      ++cu;
+      cj = 0;
+    }
+    ++done;
+  }
+}
+
+// NW warps per CTA: NW = 1 for wide levels (many CTAs per SM already use every SM
+// sub-partition); NW = 4 for narrow levels near the root, where one CTA per SM would leave three
+// of the four FP64 sub-partitions idle: warp 0 applies the updates, then the product with D is
+// split by rows over the warps.
+template <int NW>
+__global__ void __launch_bounds__(32 * NW)
+    k_lfwd2(DevSym S, int lvl_begin, int ntiles, const double *__restrict__ L,
+            const double *__restrict__ Dall, double *W, int64_t ldw, int ncolsW, LsSkip sk, int nc,
+            int cw, int npb) {
+  extern __shared__ __align__(16) unsigned char smf[];
+  const FwdLayout lay = fwd_layout(nc, cw, npb, true);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int t = S.lvl_sn[lvl_begin + blockIdx.x / ntiles];
+  const int tile = blockIdx.x % ntiles;
+  if (ls_skip(sk, t, tile)) return;
+  const int col = tile * 32 + lane;
+  const bool act = col < ncolsW;
+  const int c0 = S.sn_col[t];
+  const int ncol = S.sn_col[t + 1] - c0;
+  double *acc = reinterpret_cast<double *>(smf + lay.acc);
+  double *Ds = reinterpret_cast<double *>(smf + lay.ds);
+  double *Wc = W + (act ? col : 0);
+  for (int j = warp; j < ncol; j += NW) cpa8(acc + j * 32 + lane, Wc + (int64_t)(c0 + j) * ldw);
+  const double *D = Dall + S.sn_dptr[t];
+  for (int e = tid; e < ncol * ncol; e += 32 * NW) cpa8(Ds + e, D + e);
+  cpa_commit();
+  if (NW > 1) {
+    cpa_wait<0>();
+    __syncthreads();
+  }
+  if (warp == 0) {
+    pull_staged(S, S.upd_ptr[t], S.upd_c0end[t], L, Wc, ldw, acc, smf, lay, cw, npb, lane);
+    cpa_wait<0>();
+  }
+  __syncthreads();
+  // W[S_t] <- D acc  (D lower: D[i][j] = Ds[i + j ncol], zero above the diagonal), 4 rows at once
+  for (int i0 = 4 * warp; i0 < ncol; i0 += 4 * NW) {
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    const int jend = min(i0 + 4, ncol);
+    for (int j = 0; j < jend; ++j) {
+      const double x = acc[j * 32 + lane];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (i0 + r < ncol) a[r] = fma(Ds[(i0 + r) + j * ncol], x, a[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (act && i0 + r < ncol) Wc[(int64_t)(c0 + i0 + r) * ldw] = a[r];
+  }
+}
+
+__global__ void k_lfwd_partial2(DevSym S, int x0, int ntiles, const double *__restrict__ L,
+                                const double *__restrict__ W, int64_t ldw, int ncolsW, LsSkip sk,
+                                double *Pw, int nc, int cw, int npb) {
+  extern __shared__ __align__(16) unsigned char smp[];
+  const FwdLayout lay = fwd_layout(nc, cw, npb, false);
+  const int lane = threadIdx.x;
+  const int x = x0 + blockIdx.x / ntiles;
+  const int tile = blockIdx.x % ntiles;
+  const int t = S.xch_t[x];
+  if (ls_skip(sk, t, tile)) return;
+  const int col = tile * 32 + lane;
+  const bool act = col < ncolsW;
+  const int ncol = S.sn_col[t + 1] - S.sn_col[t];
+  double *acc = reinterpret_cast<double *>(smp + lay.acc);
+  for (int c = 0; c < ncol; ++c) acc[c * 32 + lane] = 0.0;
+  pull_staged(S, S.xch_ub[x], S.xch_ue[x], L, W + (act ? col : 0), ldw, acc, smp, lay, cw, npb,
+              lane);
+  cpa_wait<0>();
+  __syncwarp();
+  double *P = Pw + S.xch_slotw[x] * ldw + (act ? col : 0);
+  if (act)
+    for (int c = 0; c < ncol; ++c) P[(int64_t)c * ldw] = acc[c * 32 + lane];
+}
+
+template <int NW>
+__global__ void __launch_bounds__(32 * NW)
+    k_lbwd2(DevSym S, int lvl_begin, int ntiles, const double *__restrict__ L,
+            const double *__restrict__ Dall, double *W, int64_t ldw, int ncolsW, LsSkip sk,
+            int nr_b, int nc_b) {
+  extern __shared__ __align__(16) unsigned char smb[];
+  const BwdLayout lay = bwd_layout(nr_b, nc_b);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int t = S.lvl_sn[lvl_begin + blockIdx.x / ntiles];
+  const int tile = blockIdx.x % ntiles;
+  if (ls_skip(sk, t, tile)) return;
+  const int col = tile * 32 + lane;
+  const bool act = col < ncolsW;
+  const int c0 = S.sn_col[t];
+  const int ncol = S.sn_col[t + 1] - c0;
+  const int64_t r0 = S.sn_rowptr[t];
+  const int nrow = (int)(S.sn_rowptr[t + 1] - r0);
+  double *Ls = reinterpret_cast<double *>(smb + lay.ls);
+  double *Ds = reinterpret_cast<double *>(smb + lay.ds);
+  double *acc = reinterpret_cast<double *>(smb + lay.acc);
+  double *wv = reinterpret_cast<double *>(smb + lay.wv);
+  int *rws = reinterpret_cast<int *>(smb + lay.rws);
+  const double *Lt = L + S.sn_valptr[t];
+  const double *D = Dall + S.sn_dptr[t];
+  double *Wc = W + (act ? col : 0);
+  for (int p = ncol + tid; p < nrow; p += 32 * NW) rws[p] = S.rows[r0 + p];
+  for (int e = tid; e < nrow * ncol; e += 32 * NW) cpa8(Ls + e, Lt + e);
+  for (int e = tid; e < ncol * ncol; e += 32 * NW) cpa8(Ds + e, D + e);
+  for (int j = warp; j < ncol; j += NW) cpa8(acc + j * 32 + lane, Wc + (int64_t)(c0 + j) * ldw);
+  __syncthreads();
+  for (int p = ncol + warp; p < nrow; p += NW)
+    cpa8(wv + (p - ncol) * 32 + lane, Wc + (int64_t)rws[p] * ldw);
+  cpa_commit();
+  cpa_wait<0>();
+  __syncthreads();
+  // acc[j] -= sum_{p >= ncol} L[p][j] W[rows[p]], 4 columns j at once (column blocks over warps)
+  for (int j0 = 4 * warp; j0 < ncol; j0 += 4 * NW) {
+    double a[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) a[r] = (j0 + r < ncol) ? acc[(j0 + r) * 32 + lane] : 0.0;
+    for (int p = ncol; p < nrow; ++p) {
+      const double w = wv[(p - ncol) * 32 + lane];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (j0 + r < ncol) a[r] = fma(-Ls[p + (j0 + r) * nrow], w, a[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (j0 + r < ncol) acc[(j0 + r) * 32 + lane] = a[r];
+  }
+  __syncthreads();
+  // W[S_t] <- D^T acc: out[i] = sum_{j >= i} D[j][i] acc[j], 4 rows at once (row blocks over warps)
+  for (int i0 = 4 * warp; i0 < ncol; i0 += 4 * NW) {
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int j = i0; j < ncol; ++j) {
+      const double x = acc[j * 32 + lane];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (i0 + r < ncol) a[r] = fma(Ds[j + (i0 + r) * ncol], x, a[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (act && i0 + r < ncol) Wc[(int64_t)(c0 + i0 + r) * ldw] = a[r];
+  }
+}
+
+constexpr int LS_SMEM_CAP = 200 * 1024;
+constexpr int LS_NARROW_PER_SM = 8;  // CTAs per SM of a level below which a CTA gets four warps
+
+int lsolve(const DevSym &S, const int *lvl_ptr_host, const int *lvl_xptr_host,
+           const int *lvl_fptr_host, const LsLevel *lvl_info, int height, bool fwd,
            const double *L, const double *D, double *W, int64_t ldw, int ncolsW, const LsSkip &sk,
            double *Pw, cudaStream_t st) {
   if (ncolsW <= 0) return 0;
@@ -287,19 +588,62 @@ int lsolve(const DevSym &S, const int *lvl_ptr_host, const int *lvl_xptr_host, i
     cudaFuncSetAttribute(k_lfwd_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     configured = smem;
   }
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+  }
+  static bool configured2 = false;
+  if (!configured2) {
+    cudaFuncSetAttribute(k_lfwd2<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, LS_SMEM_CAP);
+    cudaFuncSetAttribute(k_lbwd2<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, LS_SMEM_CAP);
+    cudaFuncSetAttribute(k_lfwd2<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, LS_SMEM_CAP);
+    cudaFuncSetAttribute(k_lbwd2<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, LS_SMEM_CAP);
+    cudaFuncSetAttribute(k_lfwd_partial2, cudaFuncAttributeMaxDynamicSharedMemorySize, LS_SMEM_CAP);
+    configured2 = true;
+  }
   int launches = 0;
   for (int li = 0; li < height; ++li) {
     const int l = fwd ? li : height - 1 - li;
     const int b = lvl_ptr_host[l], cnt = lvl_ptr_host[l + 1] - b;
     const int64_t blocks = (int64_t)cnt * ntiles;
     if (blocks <= 0) continue;
-    if (fwd) {
+    const LsLevel &lv = lvl_info[l];
+    const int sf = fwd_layout(lv.nc, lv.cw, lv.np, true).total;
+    const int sp = fwd_layout(lv.nc, lv.cw, lv.np, false).total;
+    const int sb = bwd_layout(lv.nr, lv.nc).total;
+    const bool narrow = blocks <= (int64_t)LS_NARROW_PER_SM * nsm;
+    if (fwd && sf <= LS_SMEM_CAP) {
+      const int xb = lvl_xptr_host[l], xc = lvl_xptr_host[l + 1] - xb;
+      if (xc > 0) {
+        k_lfwd_partial2<<<(unsigned)((int64_t)xc * ntiles), 32, sp, st>>>(
+            S, xb, ntiles, L, W, ldw, ncolsW, sk, Pw, lv.nc, lv.cw, lv.np);
+        const int f0 = lvl_fptr_host[l], nf = lvl_fptr_host[l + 1] - f0;
+        if (nf > 0) k_lfwd_reduce<<<dim3(ntiles, lv.nc, nf), 256, 0, st>>>(S, f0, Pw, W, ldw, ncolsW, sk);
+        launches += 2;
+      }
+      if (narrow)
+        k_lfwd2<4><<<(unsigned)blocks, 128, sf, st>>>(S, b, ntiles, L, D, W, ldw, ncolsW, sk, lv.nc,
+                                                      lv.cw, lv.np);
+      else
+        k_lfwd2<1><<<(unsigned)blocks, 32, sf, st>>>(S, b, ntiles, L, D, W, ldw, ncolsW, sk, lv.nc,
+                                                     lv.cw, lv.np);
+    } else if (!fwd && sb <= LS_SMEM_CAP) {
+      if (narrow)
+        k_lbwd2<4><<<(unsigned)blocks, 128, sb, st>>>(S, b, ntiles, L, D, W, ldw, ncolsW, sk, lv.nr,
+                                                      lv.nc);
+      else
+        k_lbwd2<1><<<(unsigned)blocks, 32, sb, st>>>(S, b, ntiles, L, D, W, ldw, ncolsW, sk, lv.nr,
+                                                     lv.nc);
+    } else if (fwd) {
       const int xb = lvl_xptr_host[l], xc = lvl_xptr_host[l + 1] - xb;
       if (xc > 0) {
         k_lfwd_partial<<<(unsigned)((int64_t)xc * ntiles), 32, smem, st>>>(S, xb, ntiles, L, W, ldw,
                                                                            ncolsW, sk, Pw);
-        const int rb = (int)std::min<int64_t>(1024, ((int64_t)S.max_ncol * ncolsW + 255) / 256);
-        k_lfwd_reduce<<<dim3(rb, xc), 256, 0, st>>>(S, xb, xc, Pw, W, ldw, ncolsW, sk);
+        const int f0 = lvl_fptr_host[l], nf = lvl_fptr_host[l + 1] - f0;
+        if (nf > 0) k_lfwd_reduce<<<dim3(ntiles, S.max_ncol, nf), 256, 0, st>>>(S, f0, Pw, W, ldw, ncolsW, sk);
         launches += 2;
       }
       k_lfwd<<<(unsigned)blocks, 32, smem, st>>>(S, b, ntiles, L, D, W, ldw, ncolsW, sk, Pw);

@@ -37,55 +37,79 @@ void launch_slot_combine(const DevSym &S, double *out, const double *vec, double
 
 // ---------------------------------------------------------------------------------------------
 // dense Cholesky of an nrow x ncol column-major panel in shared memory (lower, in place):
-// the leading ncol x ncol block is factored, the rows below are solved against it.
-__device__ void chol_panel_smem(double *F, int nrow, int ncol, int *status_word, int flag) {
-  __shared__ double s_inv;
+// the leading ncol x ncol block is factored, the rows below are solved against it.  The serial
+// column loop carries one reciprocal per column and two barriers: warp 0 takes the pivot d_j,
+// its reciprocal and the scaled column u = F[:, j] / d_j (kept aside, so column j stays
+// unscaled while the trailing update reads it) and writes the previous column's u back; all
+// threads then update the trailing part.  This is F = U D U^T with U unit lower; the square
+// roots of D are taken in parallel at the end (L = U D^{1/2}).  scr: 2 * nrow + ncol doubles.
+__device__ void chol_panel_smem(double *F, int nrow, int ncol, int *status_word, int flag,
+                                double *scr) {
+  double *uc = scr, *dv = scr + 2 * nrow;
   const int tid = threadIdx.x, bd = blockDim.x;
   for (int j = 0; j < ncol; ++j) {
-    if (tid == 0) {
-      double d = F[j + (int64_t)j * nrow];
-      if (!(d > 0.0)) {
-        atomicOr(status_word, flag);
-        d = 1.0;
+    double *u = uc + (j & 1) * nrow;
+    if (tid < 32) {
+      double rj = 0.0;
+      if (tid == 0) {
+        double d = F[j + (int64_t)j * nrow];
+        if (!(d > 0.0)) {
+          atomicOr(status_word, flag);
+          d = 1.0;
+        }
+        dv[j] = d;
+        rj = 1.0 / d;
       }
-      d = sqrt(d);
-      F[j + (int64_t)j * nrow] = d;
-      s_inv = 1.0 / d;
+      rj = __shfl_sync(0xffffffffu, rj, 0);
+      for (int i = j + 1 + tid; i < nrow; i += 32) u[i] = F[i + (int64_t)j * nrow] * rj;
+      if (j > 0) {
+        const double *up = uc + ((j - 1) & 1) * nrow;
+        for (int i = j + tid; i < nrow; i += 32) F[i + (int64_t)(j - 1) * nrow] = up[i];
+      }
     }
-    __syncthreads();
-    const double iv = s_inv;
-    for (int i = j + 1 + tid; i < nrow; i += bd) F[i + (int64_t)j * nrow] *= iv;
     __syncthreads();
     const int w = ncol - j - 1, hgt = nrow - j - 1;
     for (int idx = tid; idx < w * hgt; idx += bd) {
-      int kk = j + 1 + idx / hgt, ii = j + 1 + idx % hgt;
-      if (ii >= kk) F[ii + (int64_t)kk * nrow] -= F[ii + (int64_t)j * nrow] * F[kk + (int64_t)j * nrow];
+      const int kk = j + 1 + idx / hgt, ii = j + 1 + idx % hgt;
+      if (ii >= kk) F[ii + (int64_t)kk * nrow] -= u[ii] * F[kk + (int64_t)j * nrow];
     }
     __syncthreads();
   }
+  if (ncol > 0) {
+    const double *up = uc + ((ncol - 1) & 1) * nrow;
+    for (int i = ncol + tid; i < nrow; i += bd) F[i + (int64_t)(ncol - 1) * nrow] = up[i];
+  }
+  for (int j = tid; j < ncol; j += bd) dv[j] = sqrt(dv[j]);
+  __syncthreads();
+  for (int idx = tid; idx < nrow * ncol; idx += bd) {
+    const int i = idx % nrow, j = idx / nrow;
+    if (i > j) F[i + (int64_t)j * nrow] *= dv[j];
+    else if (i == j) F[i + (int64_t)j * nrow] = dv[j];
+  }
+  __syncthreads();
 }
 
-// K2 for one level: CTA (supernode in level, candidate).  Frontal block F = (Ybase + a dY)
-// restricted to C_t x S_t, minus updates from the descendants listed for t, then factored.
-// inverse of the leading ncol x ncol lower block of F (ld = nrow) into D (ld = ncol), one thread
-// per column, forward substitution
-__device__ void tri_inverse_smem(const double *F, int ld, int ncol, double *D) {
-  // diagonal reciprocals first (one division per column), then column j by forward substitution
-  for (int j = threadIdx.x; j < ncol; j += blockDim.x) D[j + (int64_t)j * ncol] = 1.0 / F[j + (int64_t)j * ld];
+// D = L^{-1} for the leading ncol x ncol lower block L of F (ld = ld), D column-major (ld ncol).
+// With U = L diag(L)^{-1} (unit lower), L^{-1} = diag(L)^{-1} U^{-1}; U^{-1} is found by forward
+// elimination on the identity, one barrier per step, the (ncol-1-k)(k+1) entries of step k
+// spread over all threads.  rdv: ncol doubles of scratch.
+__device__ void tri_inverse_smem(const double *F, int ld, int ncol, double *D, double *rdv) {
+  const int tid = threadIdx.x, bd = blockDim.x;
+  for (int j = tid; j < ncol; j += bd) rdv[j] = 1.0 / F[j + (int64_t)j * ld];
+  for (int idx = tid; idx < ncol * ncol; idx += bd) D[idx] = (idx % ncol == idx / ncol) ? 1.0 : 0.0;
   __syncthreads();
-  for (int j = threadIdx.x; j < ncol; j += blockDim.x) {
-    for (int i = 0; i < j; ++i) D[i + (int64_t)j * ncol] = 0.0;
-    for (int i = j + 1; i < ncol; ++i) {
-      double s0 = 0.0, s1 = 0.0;
-      int l = j;
-      for (; l + 1 < i; l += 2) {
-        s0 = fma(F[i + (int64_t)l * ld], D[l + (int64_t)j * ncol], s0);
-        s1 = fma(F[i + (int64_t)(l + 1) * ld], D[l + 1 + (int64_t)j * ncol], s1);
-      }
-      if (l < i) s0 = fma(F[i + (int64_t)l * ld], D[l + (int64_t)j * ncol], s0);
-      D[i + (int64_t)j * ncol] = -(s0 + s1) * D[i + (int64_t)i * ncol];
+  for (int k = 0; k + 1 < ncol; ++k) {
+    const int w = k + 1, cnt = (ncol - 1 - k) * w;
+    const double rk = rdv[k];
+    for (int e = tid; e < cnt; e += bd) {
+      const int q = e / w;
+      const int i = k + 1 + q, c = e - q * w;
+      D[i + (int64_t)c * ncol] -= F[i + (int64_t)k * ld] * rk * D[k + (int64_t)c * ncol];
     }
+    __syncthreads();
   }
+  for (int idx = tid; idx < ncol * ncol; idx += bd) D[idx] *= rdv[idx % ncol];
+  __syncthreads();
 }
 
 // F[rel rows, rel cols] += sgn * L_s[p1:, :] L_s[p1:p2, :]^T for the updates [ub, ue) of t
@@ -129,8 +153,35 @@ __global__ void k_ychol_partial(DevSym S, int x0, const double *__restrict__ Nbu
   for (int i = threadIdx.x; i < sz; i += blockDim.x) P[i] = F[i];
 }
 
-void launch_ychol_partials(const DevSym &S, int x0, int nx, int ncand, const double *Nbuf,
-                           double *Pf, const int *status, cudaStream_t st) {
+// the extra chunks of a target summed into the slot of its first chunk.  CTA = 32 entries x 8
+// chunk phases (phase p sums the chunks x + p, x + p + 8, ...), then the 8 phase sums are added
+// in order (deterministic); grid (entry blocks, target, candidate)
+__global__ void k_ychol_reduce(DevSym S, int f0, double *Pf, const int *status) {
+  __shared__ double part[8][33];
+  const int x = S.xfst[f0 + blockIdx.y];
+  const int c = blockIdx.z;
+  if (*(volatile const int *)&status[c] & ST_NOT_PD) return;
+  const int t = S.xch_t[x];
+  const int xe = S.xch_end[t];
+  const int sz = (int)(S.sn_rowptr[t + 1] - S.sn_rowptr[t]) * (S.sn_col[t + 1] - S.sn_col[t]);
+  if ((int)blockIdx.x * 32 >= sz) return;
+  const int lane = threadIdx.x & 31, ph = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
+  double *P = Pf + (int64_t)c * S.nslotf;
+  double a = 0.0;
+  if (i < sz)
+    for (int xx = x + ph; xx < xe; xx += 8) a += P[S.xch_slotf[xx] + i];
+  part[ph][lane] = a;
+  __syncthreads();
+  if (ph == 0 && i < sz) {
+    double s = part[0][lane];
+    for (int q = 1; q < 8; ++q) s += part[q][lane];
+    P[S.xch_slotf[x] + i] = s;
+  }
+}
+
+void launch_ychol_partials(const DevSym &S, int x0, int nx, int f0, int nf, int ncand,
+                           const double *Nbuf, double *Pf, const int *status, cudaStream_t st) {
   if (nx <= 0) return;
   const size_t smem = (size_t)S.max_nrow * S.max_ncol * 8;
   static size_t configured = 0;
@@ -140,6 +191,10 @@ void launch_ychol_partials(const DevSym &S, int x0, int nx, int ncand, const dou
   }
   dim3 grid(nx, ncand);
   k_ychol_partial<<<grid, 256, smem, st>>>(S, x0, Nbuf, Pf, status);
+  if (nf > 0) {
+    const int gx = (S.max_nrow * S.max_ncol + 31) / 32;
+    k_ychol_reduce<<<dim3(gx, nf, ncand), 256, 0, st>>>(S, f0, Pf, status);
+  }
 }
 
 __global__ void k_ychol(DevSym S, int lvl_begin, const double *__restrict__ alpha,
@@ -161,23 +216,24 @@ __global__ void k_ychol(DevSym S, int lvl_begin, const double *__restrict__ alph
   for (int i = tid; i < sz; i += bd) F[i] = dY ? fma(a, dY[v0 + i], Yb[v0 + i]) : Yb[v0 + i];
   __syncthreads();
   ychol_pull(S, S.upd_ptr[t], S.upd_c0end[t], N, F, nrow, -1.0);
-  for (int x = S.xch_beg[t]; x < S.xch_end[t]; ++x) {
-    const double *P = Pf + (int64_t)c * S.nslotf + S.xch_slotf[x];
+  if (S.xch_end[t] > S.xch_beg[t]) {  // the extra chunks, already summed into the first slot
+    const double *P = Pf + (int64_t)c * S.nslotf + S.xch_slotf[S.xch_beg[t]];
     for (int i = tid; i < sz; i += bd) F[i] -= P[i];
     __syncthreads();
   }
-  chol_panel_smem(F, nrow, ncol, &status[c], ST_NOT_PD);
-  for (int i = tid; i < sz; i += bd) N[v0 + i] = F[i];
   double *Dsm = F + sz;
-  tri_inverse_smem(F, nrow, ncol, Dsm);
-  __syncthreads();
+  double *scr = Dsm + ncol * ncol;
+  chol_panel_smem(F, nrow, ncol, &status[c], ST_NOT_PD, scr);
+  for (int i = tid; i < sz; i += bd) N[v0 + i] = F[i];
+  tri_inverse_smem(F, nrow, ncol, Dsm, scr);
   const int64_t d0 = S.sn_dptr[t];
   for (int i = tid; i < ncol * ncol; i += bd) Dc[d0 + i] = Dsm[i];
   (void)c0;
 }
 
 size_t ychol_smem_bytes(const DevSym &S) {
-  return ((size_t)S.max_nrow * S.max_ncol + (size_t)S.max_ncol * S.max_ncol) * 8;
+  return ((size_t)S.max_nrow * S.max_ncol + (size_t)S.max_ncol * S.max_ncol + 2 * (size_t)S.max_nrow +
+          S.max_ncol) * 8;
 }
 
 void launch_ychol_level(const DevSym &S, int lvl_begin, int lvl_count, int ncand,
@@ -207,7 +263,7 @@ __global__ void k_alg1(DevSym S, const double *__restrict__ X, double *Lh, doubl
   const int64_t v0 = S.sn_valptr[r];
   double *A = sm;                      // k x k
   double *T = sm + (int64_t)k * k;     // k x k, inverse of M
-  double *rd = T + (int64_t)k * k;     // k reciprocals of the diagonal of M
+  double *rd = T + (int64_t)k * k;     // 3k doubles of scratch
   const int tid = threadIdx.x, bd = blockDim.x;
   for (int idx = tid; idx < k * k; idx += bd) {
     const int a = idx % k, b = idx / k;
@@ -217,19 +273,8 @@ __global__ void k_alg1(DevSym S, const double *__restrict__ X, double *Lh, doubl
     A[(k - 1 - b) + (int64_t)(k - 1 - a) * k] = v;
   }
   __syncthreads();
-  chol_panel_smem(A, k, k, status, ST_NOT_PD);
-  for (int j = tid; j < k; j += bd) rd[j] = 1.0 / A[j + (int64_t)j * k];
-  __syncthreads();
-  // T = M^{-1}, lower triangular, one thread per column
-  for (int j = tid; j < k; j += bd) {
-    T[j + (int64_t)j * k] = rd[j];
-    for (int i = j + 1; i < k; ++i) {
-      double s = 0.0;
-      for (int l = j; l < i; ++l) s = fma(A[i + (int64_t)l * k], T[l + (int64_t)j * k], s);
-      T[i + (int64_t)j * k] = -s * rd[i];
-    }
-  }
-  __syncthreads();
+  chol_panel_smem(A, k, k, status, ST_NOT_PD, rd);
+  tri_inverse_smem(A, k, k, T, rd);  // T = M^{-1}
   // L_r[a][b] = (P M^{-T} P)[a][b] = T[k-1-b][k-1-a]
   for (int idx = tid; idx < k * ns; idx += bd) {
     const int a = idx % k, b = idx / k;
@@ -245,7 +290,7 @@ __global__ void k_alg1(DevSym S, const double *__restrict__ X, double *Lh, doubl
 }
 
 size_t alg1_smem_bytes(const DevSym &S) {
-  return ((size_t)2 * S.max_nrow * S.max_nrow + S.max_nrow) * 8;
+  return ((size_t)2 * S.max_nrow * S.max_nrow + 3 * (size_t)S.max_nrow) * 8;
 }
 
 void launch_alg1(const DevSym &S, const double *X, double *Lh, double *DL, int *status,
@@ -392,7 +437,7 @@ __global__ void k_primal_step(DevSym S, const double *__restrict__ X, const doub
     W[b + (int64_t)a * k] = dv;
   }
   __syncthreads();
-  chol_panel_smem(Xs, k, k, status, ST_NOT_PD);
+  chol_panel_smem(Xs, k, k, status, ST_NOT_PD, q + k);
   for (int j = tid; j < k; j += bd) rd[j] = 1.0 / Xs[j + (int64_t)j * k];
   __syncthreads();
   for (int pass = 0; pass < 2; ++pass) {
@@ -506,7 +551,7 @@ __global__ void k_primal_step(DevSym S, const double *__restrict__ X, const doub
 }
 
 size_t primal_step_smem_bytes(const DevSym &S) {
-  return ((size_t)2 * S.max_nrow * S.max_nrow + 5 * (size_t)S.max_nrow) * 8;
+  return ((size_t)2 * S.max_nrow * S.max_nrow + 8 * (size_t)S.max_nrow) * 8;
 }
 
 void launch_primal_step(const DevSym &S, const double *X, const double *D, double *alpha_r,

@@ -69,7 +69,9 @@ struct mcsdp_ctx {
   std::vector<uint32_t> pm_bits;    // per P-MATRIX tile: supernodes on its columns' paths
   std::vector<int> pm_rowof;        // P-MATRIX right-hand side j -> row j (identity)
   // update-list chunks (see DevSym)
-  std::vector<int> upd_c0end, xch_beg, xch_end, xch_t, xch_ub, xch_ue, lvl_xptr;
+  std::vector<int> upd_c0end, xch_beg, xch_end, xch_t, xch_ub, xch_ue, lvl_xptr, xfst, lvl_fptr;
+  std::vector<UpdMeta> upd_meta;
+  std::vector<LsLevel> lvl_info;
   std::vector<int64_t> xch_slotw, xch_slotf;
   int64_t nslotw = 0, nslotf = 0;
   int bit_words = 1;
@@ -260,8 +262,11 @@ void plan_workspace(mcsdp_ctx *c) {
     for (int l = 0; l < S.height; ++l)
       for (int q = S.lvl_ptr[l]; q < S.lvl_ptr[l + 1]; ++q) lvl_of[S.lvl_sn[q]] = l;
     c->lvl_xptr.assign(S.height + 1, 0);
+    c->lvl_fptr.assign(S.height + 1, 0);
+    c->xfst.clear();
     for (int l = 0; l < S.height; ++l) {
       c->lvl_xptr[l] = (int)c->xch_t.size();
+      c->lvl_fptr[l] = (int)c->xfst.size();
       for (int q = S.lvl_ptr[l]; q < S.lvl_ptr[l + 1]; ++q) {
         const int t = S.lvl_sn[q];
         const int tncol = S.sn_col[t + 1] - S.sn_col[t];
@@ -280,6 +285,7 @@ void plan_workspace(mcsdp_ctx *c) {
         cuts.push_back(S.upd_ptr[t + 1]);
         c->upd_c0end[t] = cuts[1];
         c->xch_beg[t] = (int)c->xch_t.size();
+        if (cuts.size() > 2) c->xfst.push_back((int)c->xch_t.size());
         for (size_t k = 1; k + 1 < cuts.size(); ++k) {
           c->xch_t.push_back(t);
           c->xch_ub.push_back(cuts[k]);
@@ -293,6 +299,34 @@ void plan_workspace(mcsdp_ctx *c) {
       }
     }
     c->lvl_xptr[S.height] = (int)c->xch_t.size();
+    c->lvl_fptr[S.height] = (int)c->xfst.size();
+    // per-update records and per-level bounds of the staged solve kernels
+    c->upd_meta.assign(S.upd_src.size(), UpdMeta{});
+    for (size_t u = 0; u < S.upd_src.size(); ++u) {
+      const int d = S.upd_src[u];
+      UpdMeta &q = c->upd_meta[u];
+      q.dc0 = S.sn_col[d];
+      q.dncol = S.sn_col[d + 1] - S.sn_col[d];
+      q.dnrow = (int)(S.sn_rowptr[d + 1] - S.sn_rowptr[d]);
+      q.p1 = S.upd_p1[u];
+      q.np = S.upd_p2[u] - S.upd_p1[u];
+      q.pad = 0;
+      q.relptr = S.upd_relptr[u];
+      q.valp = S.sn_valptr[d];
+    }
+    c->lvl_info.assign(S.height, LsLevel{0, 0, 0, 0});
+    for (int l = 0; l < S.height; ++l) {
+      LsLevel &lv = c->lvl_info[l];
+      for (int q = S.lvl_ptr[l]; q < S.lvl_ptr[l + 1]; ++q) {
+        const int t = S.lvl_sn[q];
+        lv.nc = std::max(lv.nc, S.sn_col[t + 1] - S.sn_col[t]);
+        lv.nr = std::max(lv.nr, (int)(S.sn_rowptr[t + 1] - S.sn_rowptr[t]));
+        for (int u = S.upd_ptr[t]; u < S.upd_ptr[t + 1]; ++u) {
+          lv.cw = std::max(lv.cw, std::min(8, c->upd_meta[u].dncol));
+          lv.np = std::max(lv.np, c->upd_meta[u].np);
+        }
+      }
+    }
     (void)lvl_of;
   }
   plan_table(c, cur, "upd_c0end", c->upd_c0end);
@@ -303,6 +337,8 @@ void plan_workspace(mcsdp_ctx *c) {
   plan_table(c, cur, "xch_ue", c->xch_ue);
   plan_table(c, cur, "xch_slotw", c->xch_slotw);
   plan_table(c, cur, "xch_slotf", c->xch_slotf);
+  plan_table(c, cur, "xfst", c->xfst);
+  plan_table(c, cur, "upd_meta", c->upd_meta);
   // ---- many-right-hand-side solves (kern_lsolve.cu): skip bitmaps and chunk plan ----
   const double budget = (c->opt.panel_budget_mb > 0 ? c->opt.panel_budget_mb : 1024.0) * 1048576.0;
   c->bit_words = (S.ns + 31) / 32;
@@ -355,8 +391,10 @@ void plan_workspace(mcsdp_ctx *c) {
   // P-MATRIX: columns in chunks of pm_cols (multiple of 32); per 32-column tile the supernodes on
   // the columns' etree paths (forward reach of the unit right-hand sides)
   {
+    // all n columns at once when the budget allows (a ragged last chunk would pay the latency of
+    // every level again for a few columns)
     int pmc = (int)std::min<double>((double)n, budget / (2.0 * n * 8.0));
-    pmc = std::max(32, pmc / 32 * 32);
+    pmc = pmc >= n ? (n + 31) / 32 * 32 : std::max(32, pmc / 32 * 32);
     c->pm_cols = std::min(pmc, (n + 31) / 32 * 32);
     const int ntile = (n + 31) / 32;
     c->pm_bits.assign((size_t)ntile * words, 0u);
@@ -419,8 +457,8 @@ void plan_workspace(mcsdp_ctx *c) {
     plan_buf(c, cur, "Linv32", mx ? nblk * 32 * 32 * 4 : 0);
     plan_buf(c, cur, "gref", mx ? (size_t)m * 8 : 0);
     plan_buf(c, cur, "rref", mx ? (size_t)m * 8 : 0);
-    plan_buf(c, cur, "yref", mx ? (size_t)m * 8 : 0);
-    plan_buf(c, cur, "ayref", mx ? (size_t)m * 8 : 0);
+    plan_buf(c, cur, "yref", mx ? (size_t)mixed_chunks(m) * m * 8 : 0);
+    plan_buf(c, cur, "ayref", mx ? (size_t)mixed_chunks(m) * m * 8 : 0);
     plan_buf(c, cur, "nref", 4 * 8);
   }  // [0..3] phases, [8..8+NCAND) dual candidates
   c->ws_bytes = cur;
@@ -523,6 +561,8 @@ void bind_pointers(mcsdp_ctx *c) {
   D.xch_ue = wsp<int>(c, "xch_ue");
   D.xch_slotw = wsp<int64_t>(c, "xch_slotw");
   D.xch_slotf = wsp<int64_t>(c, "xch_slotf");
+  D.xfst = wsp<int>(c, "xfst");
+  D.upd_meta = wsp<UpdMeta>(c, "upd_meta");
   D.nslotw = c->nslotw;
   D.nslotf = c->nslotf;
   c->Ncand = wsp<double>(c, "Ncand");
@@ -587,7 +627,8 @@ mcsdp_status phase_ychol(mcsdp_ctx *c, int ncand, const double *alpha, const dou
   for (int l = 0; l < S.height; ++l) {
     const int xb = c->lvl_xptr[l], xc = c->lvl_xptr[l + 1] - xb;
     if (xc > 0) {
-      launch_ychol_partials(c->D, xb, xc, ncand, Nbuf, c->Pf, status, c->stream);
+      launch_ychol_partials(c->D, xb, xc, c->lvl_fptr[l], c->lvl_fptr[l + 1] - c->lvl_fptr[l], ncand,
+                            Nbuf, c->Pf, status, c->stream);
       ++nl;
     }
     launch_ychol_level(c->D, S.lvl_ptr[l], S.lvl_ptr[l + 1] - S.lvl_ptr[l], ncand, alpha, Yb, dY,
@@ -630,10 +671,10 @@ mcsdp_status phase_scm(mcsdp_ctx *c) {
     LsSkip fw{c->reach_bits_dev, c->tkey_dev + ch.tkey_begin, c->bit_words};
     LsSkip bw{c->need_bits_dev, c->tkey_dev + ch.tkey_begin, c->bit_words};
     // X̂[:, P_g] = L̂^{-T} L̂^{-1} E and Y^{-1}[:, P_g] = N^{-T} N^{-1} E for the chunk's groups
-    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), S.height, true, c->Lh, c->dinvL, c->W1, c->ldw, ch.nrhs, fw, c->Pw, c->stream);
-    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), S.height, false, c->Lh, c->dinvL, c->W1, c->ldw, ch.nrhs, bw, c->Pw, c->stream);
-    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), S.height, true, c->N, c->dinvN, c->W2, c->ldw, ch.nrhs, fw, c->Pw, c->stream);
-    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), S.height, false, c->N, c->dinvN, c->W2, c->ldw, ch.nrhs, bw, c->Pw, c->stream);
+    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), c->lvl_fptr.data(), c->lvl_info.data(), S.height, true, c->Lh, c->dinvL, c->W1, c->ldw, ch.nrhs, fw, c->Pw, c->stream);
+    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), c->lvl_fptr.data(), c->lvl_info.data(), S.height, false, c->Lh, c->dinvL, c->W1, c->ldw, ch.nrhs, bw, c->Pw, c->stream);
+    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), c->lvl_fptr.data(), c->lvl_info.data(), S.height, true, c->N, c->dinvN, c->W2, c->ldw, ch.nrhs, fw, c->Pw, c->stream);
+    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), c->lvl_fptr.data(), c->lvl_info.data(), S.height, false, c->N, c->dinvN, c->W2, c->ldw, ch.nrhs, bw, c->Pw, c->stream);
     k1.done(nl);
     KCHECK(c);
     KScope k2(c, KC_TILE);
@@ -658,13 +699,13 @@ mcsdp_status phase_pmatrix(mcsdp_ctx *c, int *nlaunch) {
     launch_rhs_unit(c->W1 + 0, c->ldw, c->pm_rowof_dev + k0, nc, c->stream);
     LsSkip fw{c->pm_bits_dev, c->pm_tkey_dev + k0 / 32, c->bit_words};
     nl += 1;
-    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), S.height, true, c->N, c->dinvN, c->W1, c->ldw, nc, fw, c->Pw, c->stream);
-    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), S.height, false, c->N, c->dinvN, c->W1, c->ldw, nc, none, c->Pw, c->stream);
+    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), c->lvl_fptr.data(), c->lvl_info.data(), S.height, true, c->N, c->dinvN, c->W1, c->ldw, nc, fw, c->Pw, c->stream);
+    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), c->lvl_fptr.data(), c->lvl_info.data(), S.height, false, c->N, c->dinvN, c->W1, c->ldw, nc, none, c->Pw, c->stream);
     launch_extract_lowerE(c->D, c->W1, c->ldw, k0, nc, c->YinvE, c->stream);
     launch_dY_times(c->D, c->dY, c->W1, c->W2, c->ldw, nc, c->stream);
     nl += 2;
-    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), S.height, true, c->Lh, c->dinvL, c->W2, c->ldw, nc, none, c->Pw, c->stream);
-    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), S.height, false, c->Lh, c->dinvL, c->W2, c->ldw, nc, none, c->Pw, c->stream);
+    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), c->lvl_fptr.data(), c->lvl_info.data(), S.height, true, c->Lh, c->dinvL, c->W2, c->ldw, nc, none, c->Pw, c->stream);
+    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), c->lvl_fptr.data(), c->lvl_info.data(), S.height, false, c->Lh, c->dinvL, c->W2, c->ldw, nc, none, c->Pw, c->stream);
     launch_extract_lowerE(c->D, c->W2, c->ldw, k0, nc, c->Mlow, c->stream);
     launch_extract_upperE(c->D, c->W2, c->ldw, k0, nc, c->Mup, c->stream);
     nl += 2;
