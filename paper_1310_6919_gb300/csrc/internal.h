@@ -67,6 +67,9 @@ struct DevSym {
   // first extra chunk of every target that has extra chunks, level by level
   const int *xfst;
   const UpdMeta *upd_meta;
+  // clique r's entries outside its own columns: layout offsets of the packed lower triangle of
+  // the (nrow - ncol)^2 block, cmap_off[cmap_ptr[r] + i (i + 1) / 2 + j] for local rows i >= j
+  const int64_t *cmap_ptr, *cmap_off;
   // P-MATRIX items (nw consecutive columns): union of the columns' etree paths, ascending
   const int64_t *pm_ptr;
   const int *pm_sn;

@@ -96,7 +96,11 @@ __global__ void k_potrf_diag(T *B, int64_t ldb, int k0, int nb, int *status, T *
   for (int idx = tid; idx < NB * NB; idx += 256) {
     const int i = idx % NB, j = idx / NB;
     const bool in = i < nb && j < nb && i >= j;
-    if (in) B[(k0 + i) + (int64_t)(k0 + j) * ldb] = (i == j) ? dd[j] : U[i * LD + j] * dd[j];
+    if (in) {
+      const T v = (i == j) ? dd[j] : U[i * LD + j] * dd[j];
+      B[(k0 + i) + (int64_t)(k0 + j) * ldb] = v;
+      if (i > j) B[(k0 + j) + (int64_t)(k0 + i) * ldb] = v;  // L^T in the strict upper triangle
+    }
     Linv[i + j * NB] = in ? V[i * LD + j] * rd[i] : T(0);
   }
 }
@@ -104,10 +108,12 @@ __global__ void k_potrf_diag(T *B, int64_t ldb, int k0, int nb, int *status, T *
 // Rows [r0, rend) of the panel columns [k0, k0+nb): X <- X L_kk^{-T} = X Linv^T.  CTA = 4 rows
 // x 32 columns (128 threads, one output each: thread = (row, column = lane)); a CTA owns whole
 // rows, so it solves them in place.  Small CTAs spread the panel solve over all SMs (FP64 runs
-// at two lanes per cycle per SM here).
+// at two lanes per cycle per SM here).  Rows below ncl (the matrix proper, not the border row)
+// are also stored transposed into the strict upper triangle, so the factor's rows can later be
+// read as contiguous columns.
 constexpr int TRSM_ROWS = 4;
 template <class T>
-__global__ void k_trsm_panel(T *B, int64_t ldb, int k0, int nb, int r0, int rend,
+__global__ void k_trsm_panel(T *B, int64_t ldb, int k0, int nb, int r0, int rend, int ncl,
                              const T *__restrict__ Linv) {
   __shared__ T Xs[TRSM_ROWS][NB + 1];
   __shared__ T Ts[NB][NB + 1];  // Ts[l][c] = Linv[c][l]
@@ -122,7 +128,10 @@ __global__ void k_trsm_panel(T *B, int64_t ldb, int k0, int nb, int r0, int rend
   T acc = T(0);
 #pragma unroll 8
   for (int l = 0; l < NB; ++l) acc = fma(Xs[w][l], Ts[l][lane], acc);
-  if (gi < rend && lane < nb) B[gi + (int64_t)(k0 + lane) * ldb] = acc;
+  if (gi < rend && lane < nb) {
+    B[gi + (int64_t)(k0 + lane) * ldb] = acc;
+    if (gi < ncl) B[(k0 + lane) + (int64_t)gi * ldb] = acc;
+  }
 }
 
 // Update of block column k+1 (columns [c0, c1), c1 - c0 <= 32) by panel k (columns [k0, k0+nb))
@@ -228,7 +237,7 @@ static int dense_chol(T *B, int64_t ldb, int m, int rows, int *status, T *Linv_a
     const int r0 = k0 + nb;
     const int nr = rows - r0;
     if (nr <= 0) continue;
-    k_trsm_panel<T><<<(nr + TRSM_ROWS - 1) / TRSM_ROWS, TRSM_ROWS * 32, 0, st>>>(B, ldb, k0, nb, r0, rows, Linv);
+    k_trsm_panel<T><<<(nr + TRSM_ROWS - 1) / TRSM_ROWS, TRSM_ROWS * 32, 0, st>>>(B, ldb, k0, nb, r0, rows, m, Linv);
     ++launches;
     const int c_next = r0 + NB < m ? r0 + NB : m;  // block column k+1 = [r0, c_next)
     if (!la) {
@@ -302,8 +311,89 @@ __global__ void k_copy_border(const double *B, int64_t ldb, int m, double *x) {
     x[j] = B[m + (int64_t)j * ldb];
 }
 
+// Backward substitution L^T x = y (y = row m of B) by one cluster of BCL CTAs: row block kb
+// belongs to CTA kb % BCL, which keeps those entries of the vector in shared memory.  Step kb
+// (from the last block): the owner forms x_kb = Linv_kb^T y_kb and writes it into every CTA's
+// shared memory, one cluster barrier, then each CTA removes L_{kb,i} x_kb from its own rows i
+// above the block, reading L^T from the strict upper triangle, where the factorisation stored
+// it (coalesced).  The factor entries of a step are loaded before its barrier.  Per step: one
+// hardware cluster barrier.
+constexpr int BCL = 8;
+constexpr int BTH = 256;
+__global__ void __cluster_dims__(BCL, 1, 1) __launch_bounds__(BTH)
+    k_backsolve_cluster(const double *__restrict__ B, int64_t ldb, int m,
+                        const double *__restrict__ Linv, double *x) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ double yv[];  // m doubles; the CTA's own rows are used
+  __shared__ double xb[2][NB];
+  __shared__ double tb[NB];
+  const int rank = (int)cl.block_rank();
+  const int tid = threadIdx.x;
+  const int nblk = (m + NB - 1) / NB;
+  for (int i = tid; i < m; i += BTH)
+    if ((i / NB) % BCL == rank) yv[i] = B[m + (int64_t)i * ldb];
+  __syncthreads();
+  int step = 0;
+  for (int kb = nblk - 1; kb >= 0; --kb, ++step) {
+    const int b0 = kb * NB, nb = min(NB, m - b0), buf = step & 1;
+    const int nown = rank < kb ? (kb - 1 - rank) / BCL + 1 : 0;
+    double lv[NB];
+    int i0 = -1;
+    if (tid < nown * NB) {
+      i0 = (rank + (tid / NB) * BCL) * NB + tid % NB;
+#pragma unroll
+      for (int l = 0; l < NB; ++l) lv[l] = (l < nb) ? B[i0 + (int64_t)(b0 + l) * ldb] : 0.0;
+    }
+    if (kb % BCL == rank) {
+      if (tid < nb) {
+        const double *Li = Linv + (int64_t)kb * NB * NB;
+        double a = 0.0;
+        for (int l = tid; l < nb; ++l) a = fma(Li[l + tid * NB], yv[b0 + l], a);
+        tb[tid] = a;
+      }
+      __syncthreads();
+      if (tid < NB) {
+        const double v = tid < nb ? tb[tid] : 0.0;
+        if (tid < nb) yv[b0 + tid] = v;
+        for (int q = 0; q < BCL; ++q) cl.map_shared_rank(&xb[buf][0], q)[tid] = v;
+      }
+    }
+    cl.sync();
+    if (i0 >= 0) {
+      double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+      for (int l = 0; l < NB; l += 2) {
+        a0 = fma(lv[l], xb[buf][l], a0);
+        a1 = fma(lv[l + 1], xb[buf][l + 1], a1);
+      }
+      yv[i0] -= a0 + a1;
+    }
+    for (int slot = tid + BTH; slot < nown * NB; slot += BTH) {
+      const int i = (rank + (slot / NB) * BCL) * NB + slot % NB;
+      double a = 0.0;
+      for (int l = 0; l < nb; ++l) a = fma(B[i + (int64_t)(b0 + l) * ldb], xb[buf][l], a);
+      yv[i] -= a;
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < m; i += BTH)
+    if ((i / NB) % BCL == rank) x[i] = yv[i];
+  cl.sync();  // no CTA leaves while another may still write into its shared memory
+}
+
+constexpr int BS_CLUSTER_MAX_M = 24 * 1024;  // the vector must fit the shared memory of a CTA
+
 int dense_backsolve(const double *B, int64_t ldb, int m, const double *Linv_all, double *x,
                     cudaStream_t st) {
+  if (m <= BS_CLUSTER_MAX_M) {
+    const size_t smem = (size_t)m * sizeof(double);
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_backsolve_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+    k_backsolve_cluster<<<BCL, BTH, smem, st>>>(B, ldb, m, Linv_all, x);
+    return 1;
+  }
   k_copy_border<<<(m + 255) / 256, 256, 0, st>>>(B, ldb, m, x);
   int launches = 1;
   const int nblk = (m + NB - 1) / NB;
@@ -393,25 +483,6 @@ __global__ void k_mixed_prep(double *B, int64_t ldb, float *B32, int m) {
   for (int c = ly; c < 32; c += 8) {
     const int j = j0 + lx, i = i0 + c;
     if (i < m && j < m && i > j) B[j + (int64_t)i * ldb] = t[c][lx];
-  }
-}
-
-// after the FP32 factorisation: L^T into the unused strict upper triangle of B32 (tiled
-// transpose), so the backward substitution reads it coalesced
-__global__ void k_lower_to_upper_f32(float *L, int m) {
-  __shared__ float t[32][33];
-  const int ti = blockIdx.x, tj = blockIdx.y;
-  if (ti < tj) return;
-  const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
-  const int i0 = ti * 32, j0 = tj * 32;
-  for (int c = ly; c < 32; c += 8) {
-    const int i = i0 + lx, j = j0 + c;
-    t[lx][c] = (i < m && j < m && i > j) ? L[i + (int64_t)j * m] : 0.f;
-  }
-  __syncthreads();
-  for (int c = ly; c < 32; c += 8) {
-    const int j = j0 + lx, i = i0 + c;
-    if (i < m && j < m && i > j) L[j + (int64_t)i * m] = t[c][lx];
   }
 }
 
@@ -632,9 +703,8 @@ int mixed_factor(double *B, int64_t ldb, int m, float *B32, float *Linv32, int *
   k_mixed_init<<<(m + 255) / 256, 256, 0, st>>>(B, ldb, m, g, r, x);
   const int nt = (m + 31) / 32;
   k_mixed_prep<<<dim3(nt, nt), 256, 0, st>>>(B, ldb, B32, m);
-  int nl = 2 + dense_chol_f32(B32, m, m, status, Linv32, st, st2, ev_next, ev_rest);
-  k_lower_to_upper_f32<<<dim3(nt, nt), 256, 0, st>>>(B32, m);
-  return nl + 1;
+  // the factorisation leaves L^T in the strict upper triangle of B32 as well
+  return 2 + dense_chol_f32(B32, m, m, status, Linv32, st, st2, ev_next, ev_rest);
 }
 
 int mixed_refine_step(const double *B, int64_t ldb, int m, const float *L32, const float *Linv32,

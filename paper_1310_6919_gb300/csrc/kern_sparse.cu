@@ -12,6 +12,17 @@
 
 namespace mcsdp {
 
+// A CTA-wide early exit on a flag that other CTAs may set while this one runs: thread 0 reads
+// it once and the whole CTA follows that reading (every thread then reaches the same barriers).
+__device__ __forceinline__ bool cta_flag_set(const int *flag, int mask) {
+  __shared__ int v;
+  if (threadIdx.x == 0) v = (*(volatile const int *)flag) & mask;
+  __syncthreads();
+  const bool r = v != 0;
+  __syncthreads();
+  return r;
+}
+
 // ---------------------------------------------------------------------------------------------
 // K5: out[slot] = c0 * A_0[slot] + c1 * sum_k vec[k] A_k[slot]
 __global__ void k_slot_combine(DevSym S, double *out, const double *__restrict__ vec, double c0,
@@ -141,7 +152,7 @@ __global__ void k_ychol_partial(DevSym S, int x0, const double *__restrict__ Nbu
   extern __shared__ double F[];
   const int x = x0 + blockIdx.x;
   const int c = blockIdx.y;
-  if (*(volatile const int *)&status[c] & ST_NOT_PD) return;
+  if (cta_flag_set(&status[c], ST_NOT_PD)) return;
   const int t = S.xch_t[x];
   const int nrow = (int)(S.sn_rowptr[t + 1] - S.sn_rowptr[t]);
   const int ncol = S.sn_col[t + 1] - S.sn_col[t];
@@ -160,7 +171,7 @@ __global__ void k_ychol_reduce(DevSym S, int f0, double *Pf, const int *status) 
   __shared__ double part[8][33];
   const int x = S.xfst[f0 + blockIdx.y];
   const int c = blockIdx.z;
-  if (*(volatile const int *)&status[c] & ST_NOT_PD) return;
+  if (cta_flag_set(&status[c], ST_NOT_PD)) return;
   const int t = S.xch_t[x];
   const int xe = S.xch_end[t];
   const int sz = (int)(S.sn_rowptr[t + 1] - S.sn_rowptr[t]) * (S.sn_col[t + 1] - S.sn_col[t]);
@@ -203,7 +214,7 @@ __global__ void k_ychol(DevSym S, int lvl_begin, const double *__restrict__ alph
   extern __shared__ double F[];
   const int t = S.lvl_sn[lvl_begin + blockIdx.x];
   const int c = blockIdx.y;
-  if (*(volatile int *)&status[c] & ST_NOT_PD) return;
+  if (cta_flag_set(&status[c], ST_NOT_PD)) return;
   double *N = Nbuf + (int64_t)c * S.nnzL;
   double *Dc = Dbuf + (int64_t)c * S.nnzD;
   const double a = alpha ? alpha[c] : 0.0;
@@ -398,14 +409,33 @@ void launch_dx_combine(const DevSym &S, double betamu, const double *X, const do
 // K7: alpha_r = max{alpha in (0,1] : X̄_CC + alpha dX_CC psd} (eq. primal_length2):
 // X̄_CC = L L^T, W = L^{-1} dX_CC L^{-T}, Householder tridiagonalisation of W, smallest
 // eigenvalue by Sturm-count multisection; alpha_r = min(1, -1/lambda_min).
-__device__ int sturm_count(const double *d, const double *e, int k, double sig) {
-  int cnt = 0;
-  double q = d[0] - sig;
-  if (q < 0) ++cnt;
+// Number of eigenvalues below sig of the symmetric tridiagonal matrix T (diagonal d, squared
+// off-diagonal e2, entries scaled to magnitude <= 1): the sign changes of the leading principal
+// minors p_i = det(T_i - sig I), p_0 = 1, from the three-term recurrence
+// p_i = (d_{i-1} - sig) p_{i-1} - e2_{i-2} p_{i-2} (Sturm sequence; a zero minor takes the sign
+// opposite to its predecessor).  No division, one dependent multiply-add per step; the pair
+// (p_i, p_{i-1}) is rescaled by a power of two (exact) every eighth step.
+__device__ int sturm_count_p(const double *d, const double *e2, int k, double sig) {
+  double pm = 1.0, p = d[0] - sig;
+  bool sp = (p < 0.0) || (p == 0.0);
+  int cnt = sp ? 1 : 0;
   for (int i = 1; i < k; ++i) {
-    if (q == 0.0) q = 1e-300;
-    q = (d[i] - sig) - e[i - 1] * e[i - 1] / q;
-    if (q < 0) ++cnt;
+    const double pn = fma(d[i] - sig, p, -e2[i - 1] * pm);
+    pm = p;
+    p = pn;
+    const bool s = (p < 0.0) || (p == 0.0 && !sp);
+    cnt += (s != sp) ? 1 : 0;
+    sp = s;
+    if ((i & 7) == 0) {
+      const double a = fmax(fabs(p), fabs(pm));
+      if (a > 0x1p+400) {
+        p *= 0x1p-400;
+        pm *= 0x1p-400;
+      } else if (a < 0x1p-400 && a > 0.0) {
+        p *= 0x1p+400;
+        pm *= 0x1p+400;
+      }
+    }
   }
   return cnt;
 }
@@ -515,39 +545,65 @@ __global__ void k_primal_step(DevSym S, const double *__restrict__ X, const doub
     dd[k - 1] = W[(k - 1) + (int64_t)(k - 1) * k];
   }
   __syncthreads();
-  if (tid < 32) {
-    const int lane = tid;
-    double lo = 1e300, hi = -1e300;
-    for (int i = 0; i < k; ++i) {
-      double rad = (i > 0 ? fabs(ee[i - 1]) : 0.0) + (i + 1 < k ? fabs(ee[i]) : 0.0);
-      lo = fmin(lo, dd[i] - rad);
-      hi = fmax(hi, dd[i] + rad);
-    }
-    lo -= 1e-12 * (fabs(lo) + 1.0);
-    hi += 1e-12 * (fabs(hi) + 1.0);
-    for (int it = 0; it < 64; ++it) {
-      const double sig = lo + (hi - lo) * (double)(lane + 1) / 33.0;
-      const int c = sturm_count(dd, ee, k, sig);
-      const unsigned ball = __ballot_sync(0xffffffffu, c >= 1);
-      const double s31 = __shfl_sync(0xffffffffu, sig, 31);
-      if (ball == 0u) {
-        lo = s31;
-      } else {
-        const int f = __ffs(ball) - 1;
-        const double sf = __shfl_sync(0xffffffffu, sig, f);
-        const double sp = __shfl_sync(0xffffffffu, sig, f > 0 ? f - 1 : 0);
-        hi = sf;
-        if (f > 0) lo = sp;
-      }
-      if (hi - lo <= 4e-16 * fmax(fabs(lo), fabs(hi)) + 1e-300) break;
-    }
-    if (lane == 0) {
-      const double lam = 0.5 * (lo + hi);
-      sh[0] = lam < -1.0 ? -1.0 / lam : 1.0;
-    }
+  // scale T by a power of two (exact) so its entries are at most 1 in magnitude
+  if (tid == 0) {
+    double amax = 0.0;
+    for (int i = 0; i < k; ++i) amax = fmax(amax, fabs(dd[i]));
+    for (int i = 0; i + 1 < k; ++i) amax = fmax(amax, fabs(ee[i]));
+    sh[1] = amax > 0.0 ? ldexp(1.0, ilogb(amax) + 1) : 1.0;
   }
   __syncthreads();
-  if (tid == 0) alpha_r[r] = sh[0];
+  const double sc = sh[1], isc = 1.0 / sc;
+  for (int i = tid; i < k; i += bd) {
+    dd[i] *= isc;
+    if (i + 1 < k) v[i] = (ee[i] * isc) * (ee[i] * isc);
+  }
+  __syncthreads();
+  // alpha_r = 1 unless lambda_min(W) < -1
+  if (tid == 0) sh[2] = (double)sturm_count_p(dd, v, k, -isc);
+  __syncthreads();
+  if (sh[2] == 0.0) {
+    if (tid == 0) alpha_r[r] = 1.0;
+    return;
+  }
+  // lambda_min in [Gershgorin lower bound, -1): multisection, one shift per thread per round
+  __shared__ double bnd[2];
+  __shared__ int wfirst[32];
+  if (tid == 0) {
+    double lo = 1e300;
+    for (int i = 0; i < k; ++i) {
+      const double rad = (i > 0 ? fabs(ee[i - 1]) : 0.0) + (i + 1 < k ? fabs(ee[i]) : 0.0);
+      lo = fmin(lo, dd[i] - rad * isc);
+    }
+    bnd[0] = lo - 1e-12 * (fabs(lo) + 1.0);
+    bnd[1] = -isc;
+  }
+  __syncthreads();
+  const int lane = tid & 31, warp = tid >> 5, nw = bd >> 5;
+  for (int it = 0; it < 16; ++it) {
+    const double lo = bnd[0], hi = bnd[1];
+    if (hi - lo <= 4e-16 * fmax(fabs(lo), fabs(hi))) break;
+    const double sig = lo + ((hi - lo) / (double)(bd + 1)) * (double)(tid + 1);
+    const unsigned ball = __ballot_sync(0xffffffffu, sturm_count_p(dd, v, k, sig) >= 1);
+    if (lane == 0) wfirst[warp] = ball ? warp * 32 + __ffs(ball) - 1 : (1 << 30);
+    __syncthreads();
+    if (tid == 0) {
+      int f = 1 << 30;
+      for (int w = 0; w < nw; ++w) f = min(f, wfirst[w]);
+      const double step = (hi - lo) / (double)(bd + 1);
+      if (f == (1 << 30)) {
+        bnd[0] = lo + step * (double)bd;
+      } else {
+        bnd[1] = lo + step * (double)(f + 1);
+        if (f > 0) bnd[0] = lo + step * (double)f;
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const double lam = 0.5 * (bnd[0] + bnd[1]) * sc;
+    alpha_r[r] = lam < -1.0 ? -1.0 / lam : 1.0;
+  }
 }
 
 size_t primal_step_smem_bytes(const DevSym &S) {

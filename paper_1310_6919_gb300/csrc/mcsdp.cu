@@ -71,6 +71,7 @@ struct mcsdp_ctx {
   // update-list chunks (see DevSym)
   std::vector<int> upd_c0end, xch_beg, xch_end, xch_t, xch_ub, xch_ue, lvl_xptr, xfst, lvl_fptr;
   std::vector<UpdMeta> upd_meta;
+  std::vector<int64_t> cmap_ptr, cmap_off;
   std::vector<LsLevel> lvl_info;
   std::vector<int64_t> xch_slotw, xch_slotf;
   int64_t nslotw = 0, nslotf = 0;
@@ -151,11 +152,12 @@ cudaEvent_t ev_get(mcsdp_ctx *c) {
 struct KScope {
   mcsdp_ctx *c;
   int cls;
+  cudaStream_t s;
   cudaEvent_t a = nullptr;
-  KScope(mcsdp_ctx *c_, int cls_) : c(c_), cls(cls_) {
+  KScope(mcsdp_ctx *c_, int cls_, cudaStream_t s_ = nullptr) : c(c_), cls(cls_), s(s_ ? s_ : c_->stream) {
     if (c->opt.profile) {
       a = ev_get(c);
-      cudaEventRecord(a, c->stream);
+      cudaEventRecord(a, s);
     }
   }
   void done(int nlaunch) {
@@ -163,7 +165,7 @@ struct KScope {
     c->kcount[cls] += nlaunch;
     if (a) {
       cudaEvent_t b = ev_get(c);
-      cudaEventRecord(b, c->stream);
+      cudaEventRecord(b, s);
       c->pending.emplace_back(cls, a, b);
       a = nullptr;
     }
@@ -171,15 +173,22 @@ struct KScope {
 };
 
 // resolve recorded event pairs; call only after the stream has been synchronised
+// (pairs recorded on the second stream may still be running: they stay pending)
 void prof_flush(mcsdp_ctx *c) {
+  std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> keep;
   for (auto &p : c->pending) {
+    if (cudaEventQuery(std::get<2>(p)) == cudaErrorNotReady) {
+      if (cudaPeekAtLastError() == cudaErrorNotReady) (void)cudaGetLastError();
+      keep.push_back(p);
+      continue;
+    }
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, std::get<1>(p), std::get<2>(p)) == cudaSuccess)
       c->kms[std::get<0>(p)] += ms;
     c->evpool.push_back(std::get<1>(p));
     c->evpool.push_back(std::get<2>(p));
   }
-  c->pending.clear();
+  c->pending.swap(keep);
 }
 
 template <class T>
@@ -339,6 +348,31 @@ void plan_workspace(mcsdp_ctx *c) {
   plan_table(c, cur, "xch_slotf", c->xch_slotf);
   plan_table(c, cur, "xfst", c->xfst);
   plan_table(c, cur, "upd_meta", c->upd_meta);
+  // clique entries outside the own columns of each clique: layout offsets (binary search in the
+  // owning supernode's rows, done once here instead of per entry on the device)
+  {
+    c->cmap_ptr.assign(S.ns + 1, 0);
+    c->cmap_off.clear();
+    for (int r = 0; r < S.ns; ++r) {
+      const int64_t r0 = S.sn_rowptr[r];
+      const int k = (int)(S.sn_rowptr[r + 1] - r0);
+      const int nsr = S.sn_col[r + 1] - S.sn_col[r];
+      for (int i = 0; i < k - nsr; ++i)
+        for (int j = 0; j <= i; ++j) {
+          const int rr = S.rows[r0 + nsr + i], cc = S.rows[r0 + nsr + j];
+          const int t = S.col2sn[cc];
+          const int64_t t0 = S.sn_rowptr[t];
+          const int tn = (int)(S.sn_rowptr[t + 1] - t0);
+          const int lc = cc - S.sn_col[t];
+          const int *b = S.rows.data() + t0;
+          const int pos = (int)(std::lower_bound(b + lc, b + tn, rr) - b);
+          c->cmap_off.push_back(S.sn_valptr[t] + pos + (int64_t)lc * tn);
+        }
+      c->cmap_ptr[r + 1] = (int64_t)c->cmap_off.size();
+    }
+  }
+  plan_table(c, cur, "cmap_ptr", c->cmap_ptr);
+  plan_table(c, cur, "cmap_off", c->cmap_off);
   // ---- many-right-hand-side solves (kern_lsolve.cu): skip bitmaps and chunk plan ----
   const double budget = (c->opt.panel_budget_mb > 0 ? c->opt.panel_budget_mb : 1024.0) * 1048576.0;
   c->bit_words = (S.ns + 31) / 32;
@@ -563,6 +597,8 @@ void bind_pointers(mcsdp_ctx *c) {
   D.xch_slotf = wsp<int64_t>(c, "xch_slotf");
   D.xfst = wsp<int>(c, "xfst");
   D.upd_meta = wsp<UpdMeta>(c, "upd_meta");
+  D.cmap_ptr = wsp<int64_t>(c, "cmap_ptr");
+  D.cmap_off = wsp<int64_t>(c, "cmap_off");
   D.nslotw = c->nslotw;
   D.nslotf = c->nslotf;
   c->Ncand = wsp<double>(c, "Ncand");
@@ -824,24 +860,16 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
   }
   KCHECK(c);
   cudaEventRecord(c->ev[3], c->stream);
-  // primal step (eq. primal_length2)
+  // primal step (eq. primal_length2) on the second stream: it needs only X̄ and dX, so it runs
+  // while the dual step's candidate factorisations run on the main stream
+  CUDA_TRY(c, cudaStreamWaitEvent(c->st2, c->ev[3], 0));
   {
-    KScope k1(c, KC_PSTEP);
-    launch_primal_step(c->D, Xbar, c->dX, c->alpha_r, c->status + 3, c->stream);
+    KScope k1(c, KC_PSTEP, c->st2);
+    launch_primal_step(c->D, Xbar, c->dX, c->alpha_r, c->status + 3, c->st2);
     k1.done(1);
-    KScope k2(c, KC_MISC);
-    launch_measures(c->D, Xbar, c->Ylay, c->z, c->alpha_r, c->scal, c->stream);
-    k2.done(1);
   }
+  CUDA_TRY(c, cudaEventRecord(c->ev[5], c->st2));
   KCHECK(c);
-  double sc[8];
-  int st[4];
-  CUDA_TRY(c, cudaMemcpyAsync(sc, c->scal, 6 * 8, cudaMemcpyDeviceToHost, c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(st, c->status, 4 * 4, cudaMemcpyDeviceToHost, c->stream));
-  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  prof_flush(c);
-  if (st[2] & ST_NOT_PD) return fail(c, MCSDP_ERR_NOT_PD, "Schur complement matrix is not positive definite");
-  o.ap = sc[5];
   // dual step: bisection on the success of Y + alpha dY = N N^T (K2 on candidates)
   double lo = 0.0, hi = -1.0;  // largest passing, smallest failing
   double cand[NCAND];
@@ -873,6 +901,21 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
     if (lo >= 1.0) break;
     if (lo > 0 && hi > 0 && (hi - lo) <= 1e-3 * lo) break;
   }
+  CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->ev[5], 0));
+  {
+    KScope k2(c, KC_MISC);
+    launch_measures(c->D, Xbar, c->Ylay, c->z, c->alpha_r, c->scal, c->stream);
+    k2.done(1);
+  }
+  KCHECK(c);
+  double sc[8];
+  int st[4];
+  CUDA_TRY(c, cudaMemcpyAsync(sc, c->scal, 6 * 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(st, c->status, 4 * 4, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  prof_flush(c);
+  if (st[2] & ST_NOT_PD) return fail(c, MCSDP_ERR_NOT_PD, "Schur complement matrix is not positive definite");
+  o.ap = sc[5];
   if (lo <= 0.0) return fail(c, MCSDP_ERR_STALL, "dual step length collapsed");
   o.ad = std::min(lo, 1.0);
   cudaEventRecord(c->ev[4], c->stream);

@@ -258,7 +258,9 @@ __device__ __forceinline__ double clique_entry(const DevSym &S, const double *X,
   const int ns = S.sn_col[r + 1] - S.sn_col[r];
   const int hi = a > b ? a : b, lo = a > b ? b : a;
   if (lo < ns) return X[S.sn_valptr[r] + hi + (int64_t)lo * k];
-  return X[layout_offset(S, S.rows[r0 + hi], S.rows[r0 + lo])];
+  const int i = hi - ns, j = lo - ns;
+  (void)r0;
+  return X[S.cmap_off[S.cmap_ptr[r] + (int64_t)i * (i + 1) / 2 + j]];
 }
 
 __device__ __forceinline__ double block_reduce_sum(double v, double *red) {
