@@ -159,20 +159,25 @@ void launch_scm_tiles(const DevSym &S, const int2 *tiles, int ntiles, const doub
 // B internal, (m+1) x m lower, column-major, ld = ldb; row m holds g^T on entry and
 // (L^{-1} g)^T on exit.
 // Linv: ceil(m / 64) blocks of 64 x 64 doubles receiving the inverses of the diagonal blocks
-// st2/ev_next/ev_rest (two events each): second stream for the lookahead; nullptr = one stream
+// Streams of the blocked Cholesky with lookahead: the critical path (diagonal block, panel solve,
+// update of the next block column) on a high-priority stream, the rest of every trailing update
+// on a low-priority one, forked from and joined back into the caller's stream.
+struct CholStreams {
+  cudaStream_t chain = nullptr, rest = nullptr;
+  cudaEvent_t next[2] = {}, rest_ev[2] = {}, fork = nullptr, chain_done = nullptr;
+};
+// cs == nullptr: everything on st, no lookahead
 int dense_chol_bordered(double *B, int64_t ldb, int m, int *status, double *Linv,
-                        cudaStream_t st, cudaStream_t st2, cudaEvent_t *ev_next,
-                        cudaEvent_t *ev_rest);
+                        cudaStream_t st, const CholStreams *cs);
 int dense_backsolve(const double *B, int64_t ldb, int m, const double *Linv, double *x,
                     cudaStream_t st);
 int dense_chol_f32(float *B, int64_t ldb, int m, int *status, float *Linv, cudaStream_t st,
-                   cudaStream_t st2, cudaEvent_t *ev_next, cudaEvent_t *ev_rest);
+                   const CholStreams *cs);
 // Mixed precision.  mixed_factor: B made fully symmetric (strict upper <- lower^T), B32 <- FP32
 // Cholesky factor of B (L^T in its strict upper triangle), g <- row m of B (the right-hand side
 // border), r <- g, x <- 0.
 int mixed_factor(double *B, int64_t ldb, int m, float *B32, float *Linv32, int *status,
-                 double *g, double *r, double *x, cudaStream_t st, cudaStream_t st2,
-                 cudaEvent_t *ev_next, cudaEvent_t *ev_rest);
+                 double *g, double *r, double *x, cudaStream_t st, const CholStreams *cs);
 // number of column chunks of the refinement's matrix-vector product (P, A hold chunks x m)
 int mixed_chunks(int m);
 // one refinement step: x += (L32 L32^T)^{-1} r, then r = g - B x (FP64) and

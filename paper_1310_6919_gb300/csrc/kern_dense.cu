@@ -19,25 +19,46 @@ namespace mcsdp {
 constexpr int NB = 32;  // panel width (FP64 on one SM is slow: a narrow panel keeps the
                         // serial factor-and-invert step short)
 
+// Reciprocal for the pivots of the serial column loops: an FP32 reciprocal of the rounded value
+// refined by two Newton-Raphson steps r <- r + r (1 - d r) in FP64 (each squares the relative
+// error: 2^-23 -> 2^-46 -> below half an ulp before the final rounding), four dependent FP64
+// operations instead of a full division.  Outside the FP32 range the plain division is used.
+template <class T>
+__device__ __forceinline__ T pivot_rcp(T d);
+template <>
+__device__ __forceinline__ double pivot_rcp<double>(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / d;
+  double r = (double)__frcp_rn((float)d);
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
+template <>
+__device__ __forceinline__ float pivot_rcp<float>(float d) {
+  return __frcp_rn(d);
+}
+
 // Cholesky of the nb x nb diagonal block at (k0, k0), one CTA of 256 threads, and the inverse
 // of the factor (stored in Linv, nb x nb column-major, ld NB).  The serial column loop is the
-// critical path of the whole factorisation.  FP64 on this part issues one warp instruction per
-// 64 cycles per SM sub-partition whatever the number of active lanes, so the work of every step
-// is packed densely over the threads: step j updates the s(s+1)/2 entries of the trailing
-// triangle (s = nb-1-j) through a packed (row, column) table, and step k of the inverse the
-// (nb-1-k)(k+1) entries below row k.  The loop carries one reciprocal per column and no square
-// root: it forms A = U D U^T (U unit lower), then L = U D^{1/2} and L^{-1} = D^{-1/2} U^{-1},
-// the nb square roots taken in parallel after the loop and U^{-1} found by forward elimination.
+// critical path of the whole factorisation, so it is warp-specialised with one barrier per
+// column: at step j, warp 0 brings column j+1 up to date, takes its pivot d_{j+1}, the
+// reciprocal and the scaled column U[:, j+1]; warps 1-7 meanwhile apply step j to the columns
+// >= j+2 and step j of the inverse U^{-1} (forward elimination, row j final).  This is
+// A = U D U^T with U unit lower; L = U D^{1/2} and L^{-1} = D^{-1/2} U^{-1} follow with the nb
+// square roots taken in parallel.  FP64 on this part issues one warp instruction per 64 cycles
+// per SM sub-partition whatever the number of active lanes, so the trailing and inverse work of
+// a step is packed densely over the 224 threads of warps 1-7.
 template <class T>
 __global__ void k_potrf_diag(T *B, int64_t ldb, int k0, int nb, int *status, T *Linv) {
   constexpr int LD = NB + 1;
-  constexpr int NP = NB * (NB - 1) / 2;  // packed trailing-triangle size for s = NB - 1
+  constexpr int NP = NB * (NB - 1) / 2;  // packed triangle size for side NB - 1
   __shared__ T A[NB * LD];   // working copy, row-major; the trailing part is updated in place
   __shared__ T U[NB * LD];   // unit lower factor, row-major
   __shared__ T V[NB * LD];   // U^{-1}, row-major
   __shared__ T rd[NB], dd[NB];
   __shared__ unsigned char pr[NP], pc[NP];  // packed index e -> (row, column), column <= row
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int idx = tid; idx < NB * NB; idx += 256) {
     const int i = idx % NB, j = idx / NB;
     A[i * LD + j] = (i >= j && i < nb && j < nb) ? B[(k0 + i) + (int64_t)(k0 + j) * ldb] : T(0);
@@ -51,46 +72,68 @@ __global__ void k_potrf_diag(T *B, int64_t ldb, int k0, int nb, int *status, T *
     }
   __syncthreads();
   bool bad = false;
-  for (int j = 0; j < nb; ++j) {
-    if (tid < 32) {  // warp 0: pivot, its reciprocal and the scaled column j
-      T rj = T(0);
-      if (tid == 0) {
-        T d = A[j * LD + j];
-        if (!(d > T(0))) {
-          bad = true;
-          d = T(1);
-        }
-        dd[j] = d;
-        rj = T(1) / d;
-        rd[j] = rj;
+  if (warp == 0) {  // column 0: pivot, reciprocal, scaled column
+    T r0 = T(0);
+    if (lane == 0) {
+      T d = A[0];
+      if (!(d > T(0))) {
+        bad = true;
+        d = T(1);
       }
-      rj = __shfl_sync(0xffffffffu, rj, 0);
-      const int r = j + 1 + tid;
-      if (r < nb) U[r * LD + j] = A[r * LD + j] * rj;
+      dd[0] = d;
+      r0 = pivot_rcp<T>(d);
+      rd[0] = r0;
     }
-    __syncthreads();
-    // trailing triangle rows/columns j+1 .. nb-1; column j is only read
-    const int s = nb - 1 - j, np = s * (s + 1) / 2;
-    for (int e = tid; e < np; e += 256) {
-      const int r = j + 1 + pr[e], kk = j + 1 + pc[e];
-      A[r * LD + kk] -= U[r * LD + j] * A[kk * LD + j];
+    r0 = __shfl_sync(0xffffffffu, r0, 0);
+    if (lane >= 1 && lane < nb) U[lane * LD] = A[lane * LD] * r0;
+  }
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    if (warp == 0) {
+      if (j + 1 < nb) {
+        // column j+1 (rows >= j+1) receives step j, then its pivot and scaled column
+        const int r = j + 1 + lane;
+        T a = T(0);
+        if (r < nb) {
+          a = A[r * LD + j + 1] - U[r * LD + j] * A[(j + 1) * LD + j];
+          A[r * LD + j + 1] = a;
+        }
+        T d = __shfl_sync(0xffffffffu, a, 0), rj = T(0);
+        if (lane == 0) {
+          if (!(d > T(0))) {
+            bad = true;
+            d = T(1);
+          }
+          dd[j + 1] = d;
+          rj = pivot_rcp<T>(d);
+          rd[j + 1] = rj;
+        }
+        rj = __shfl_sync(0xffffffffu, rj, 0);
+        if (r < nb && lane >= 1) U[r * LD + j + 1] = a * rj;
+      }
+    } else {
+      // step j on columns >= j+2 (rows >= column), and step j of the inverse
+      const int s = nb - 2 - j;
+      const int ntr = s > 0 ? s * (s + 1) / 2 : 0;
+      const int w = j + 1, ninv = (nb - 1 - j) * w;
+      for (int e = tid - 32; e < ntr + ninv; e += 224) {
+        if (e < ntr) {
+          const int ii = j + 2 + pr[e], kk = j + 2 + pc[e];
+          A[ii * LD + kk] -= U[ii * LD + j] * A[kk * LD + j];
+        } else {
+          const int f = e - ntr, q = f / w;
+          const int i = j + 1 + q, c = f - q * w;
+          V[i * LD + c] -= U[i * LD + j] * V[j * LD + c];
+        }
+      }
     }
     __syncthreads();
   }
-  if (bad && tid == 0) atomicOr(status, ST_NOT_PD);
+  if (bad) atomicOr(status, ST_NOT_PD);
   if (tid < nb) {
     const T sq = sqrt(dd[tid]);
     dd[tid] = sq;
     rd[tid] = T(1) / sq;
-  }
-  // V = U^{-1}: step k removes U[r][k] times row k (final) from the rows r > k
-  for (int k = 0; k < nb - 1; ++k) {
-    const int w = k + 1, cnt = (nb - 1 - k) * w;
-    for (int e = tid; e < cnt; e += 256) {
-      const int r = k + 1 + e / w, c = e - (e / w) * w;
-      V[r * LD + c] -= U[r * LD + k] * V[k * LD + c];
-    }
-    __syncthreads();
   }
   __syncthreads();
   for (int idx = tid; idx < NB * NB; idx += 256) {
@@ -219,8 +262,17 @@ static void launch_syrk(T *B, int64_t ldb, int k0, int nb, int c_lo, int c_hi, i
 // ev_rest[k%2] order the two streams so no block is updated by both at once; st waits for st2
 // at the end.  With st2 == nullptr everything runs on st.
 template <class T>
-static int dense_chol(T *B, int64_t ldb, int m, int rows, int *status, T *Linv_all, cudaStream_t st,
-                      cudaStream_t st2, cudaEvent_t *ev_next, cudaEvent_t *ev_rest) {
+static int dense_chol(T *B, int64_t ldb, int m, int rows, int *status, T *Linv_all,
+                      cudaStream_t st_caller, const CholStreams *cs) {
+  // critical path on st (high priority), trailing updates on st2 (low priority)
+  const bool la = cs != nullptr;
+  cudaStream_t st = la ? cs->chain : st_caller, st2 = la ? cs->rest : nullptr;
+  const cudaEvent_t *ev_next = la ? cs->next : nullptr, *ev_rest = la ? cs->rest_ev : nullptr;
+  if (la) {
+    cudaEventRecord(cs->fork, st_caller);
+    cudaStreamWaitEvent(st, cs->fork, 0);
+    cudaStreamWaitEvent(st2, cs->fork, 0);
+  }
   const int smem_tile = 2 * NB * TS * (int)sizeof(T);
   static bool configured = false;
   if (!configured) {
@@ -228,7 +280,6 @@ static int dense_chol(T *B, int64_t ldb, int m, int rows, int *status, T *Linv_a
     configured = true;
   }
   int launches = 0;
-  const bool la = st2 != nullptr;
   for (int k0 = 0, k = 0; k0 < m; k0 += NB, ++k) {
     const int nb = (m - k0) < NB ? (m - k0) : NB;
     T *Linv = Linv_all + (int64_t)k * NB * NB;
@@ -257,21 +308,22 @@ static int dense_chol(T *B, int64_t ldb, int m, int rows, int *status, T *Linv_a
     cudaEventRecord(ev_rest[k & 1], st2);
   }
   if (la) {
-    cudaEventRecord(ev_rest[0], st2);
-    cudaStreamWaitEvent(st, ev_rest[0], 0);
+    cudaEventRecord(cs->rest_ev[0], st2);
+    cudaEventRecord(cs->chain_done, st);
+    cudaStreamWaitEvent(st_caller, cs->rest_ev[0], 0);
+    cudaStreamWaitEvent(st_caller, cs->chain_done, 0);
   }
   return launches;
 }
 
 int dense_chol_bordered(double *B, int64_t ldb, int m, int *status, double *Linv_all,
-                        cudaStream_t st, cudaStream_t st2, cudaEvent_t *ev_next,
-                        cudaEvent_t *ev_rest) {
-  return dense_chol<double>(B, ldb, m, m + 1, status, Linv_all, st, st2, ev_next, ev_rest);
+                        cudaStream_t st, const CholStreams *cs) {
+  return dense_chol<double>(B, ldb, m, m + 1, status, Linv_all, st, cs);
 }
 
 int dense_chol_f32(float *B, int64_t ldb, int m, int *status, float *Linv_all, cudaStream_t st,
-                   cudaStream_t st2, cudaEvent_t *ev_next, cudaEvent_t *ev_rest) {
-  return dense_chol<float>(B, ldb, m, m, status, Linv_all, st, st2, ev_next, ev_rest);
+                   const CholStreams *cs) {
+  return dense_chol<float>(B, ldb, m, m, status, Linv_all, st, cs);
 }
 
 // Backward substitution L^T x = y, y = row m of B, blocks of 64 from the bottom; the diagonal
@@ -698,13 +750,12 @@ __global__ void k_mixed_init(const double *__restrict__ B, int64_t ldb, int m, d
 int mixed_chunks(int m) { return (m + MV_CHUNK - 1) / MV_CHUNK; }
 
 int mixed_factor(double *B, int64_t ldb, int m, float *B32, float *Linv32, int *status,
-                 double *g, double *r, double *x, cudaStream_t st, cudaStream_t st2,
-                 cudaEvent_t *ev_next, cudaEvent_t *ev_rest) {
+                 double *g, double *r, double *x, cudaStream_t st, const CholStreams *cs) {
   k_mixed_init<<<(m + 255) / 256, 256, 0, st>>>(B, ldb, m, g, r, x);
   const int nt = (m + 31) / 32;
   k_mixed_prep<<<dim3(nt, nt), 256, 0, st>>>(B, ldb, B32, m);
   // the factorisation leaves L^T in the strict upper triangle of B32 as well
-  return 2 + dense_chol_f32(B32, m, m, status, Linv32, st, st2, ev_next, ev_rest);
+  return 2 + dense_chol_f32(B32, m, m, status, Linv32, st, cs);
 }
 
 int mixed_refine_step(const double *B, int64_t ldb, int m, const float *L32, const float *Linv32,
@@ -776,7 +827,7 @@ extern "C" mcsdp_status mcsdp_sce_solve_noalloc(const double *B, int64_t ldb, co
   int blocks = (int)(((int64_t)m * m + 255) / 256);
   if (blocks > 4096) blocks = 4096;
   k_noalloc_setup<<<blocks, 256, 0, st>>>(Bw, ldw, B, ldb, g, m, status);
-  dense_chol_bordered(Bw, ldw, m, status, Binv, st, nullptr, nullptr, nullptr);
+  dense_chol_bordered(Bw, ldw, m, status, Binv, st, nullptr);
   dense_backsolve(Bw, ldw, m, Binv, x, st);
   if (cudaGetLastError() != cudaSuccess) return MCSDP_ERR_CUDA;
   int hst = 0;

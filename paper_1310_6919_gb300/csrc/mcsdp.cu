@@ -85,7 +85,9 @@ struct mcsdp_ctx {
   bool z0_ok = false;
   bool iterate_set = false;
   cudaEvent_t ev[8] = {};
-  cudaStream_t st2 = nullptr;                  // lookahead stream of the SCM Cholesky
+  cudaStream_t st2 = nullptr;                  // low priority: trailing updates, primal step
+  cudaStream_t st1 = nullptr;                  // high priority: the Cholesky's critical path
+  CholStreams cs;
   cudaEvent_t ev_next[2] = {}, ev_rest[2] = {};
   // device buffers
   double *Xbar = nullptr, *z = nullptr, *Ylay = nullptr, *N = nullptr, *dinvN = nullptr;
@@ -770,7 +772,7 @@ mcsdp_status mixed_sce(mcsdp_ctx *c, bool *solved) {
   {
     KScope k1(c, KC_CHOL);
     k1.done(mixed_factor(c->B, c->ldb, m, c->B32, c->Linv32, c->status + 4, c->gref, c->rref,
-                         c->xs, c->stream, c->st2, c->ev_next, c->ev_rest));
+                         c->xs, c->stream, &c->cs));
   }
   KCHECK(c);
   const double eps = std::ldexp(1.0, -53);
@@ -833,8 +835,7 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
     }
     if (!solved) {
       KScope k1(c, KC_CHOL);
-      k1.done(dense_chol_bordered(c->B, c->ldb, m, c->status + 2, c->Binv, c->stream, c->st2,
-                                  c->ev_next, c->ev_rest));
+      k1.done(dense_chol_bordered(c->B, c->ldb, m, c->status + 2, c->Binv, c->stream, &c->cs));
       KScope k2(c, KC_BSOLVE);
       k2.done(dense_backsolve(c->B, c->ldb, m, c->Binv, c->xs, c->stream));
     }
@@ -1080,11 +1081,20 @@ mcsdp_status mcsdp_create(const mcsdp_problem *p, const mcsdp_options *opt, void
     c->device = c->opt.device;
     CUDA_TRY(c, cudaSetDevice(c->device));
     for (int i = 0; i < 8; ++i) CUDA_TRY(c, cudaEventCreate(&c->ev[i]));
-    CUDA_TRY(c, cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking));
+    int prio_lo = 0, prio_hi = 0;
+    CUDA_TRY(c, cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+    CUDA_TRY(c, cudaStreamCreateWithPriority(&c->st2, cudaStreamNonBlocking, prio_lo));
+    CUDA_TRY(c, cudaStreamCreateWithPriority(&c->st1, cudaStreamNonBlocking, prio_hi));
     for (int i = 0; i < 2; ++i) {
       CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_next[i], cudaEventDisableTiming));
       CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_rest[i], cudaEventDisableTiming));
+      c->cs.next[i] = c->ev_next[i];
+      c->cs.rest_ev[i] = c->ev_rest[i];
     }
+    CUDA_TRY(c, cudaEventCreateWithFlags(&c->cs.fork, cudaEventDisableTiming));
+    CUDA_TRY(c, cudaEventCreateWithFlags(&c->cs.chain_done, cudaEventDisableTiming));
+    c->cs.chain = c->st1;
+    c->cs.rest = c->st2;
   }
   c->err.clear();
   return MCSDP_OK;
@@ -1106,6 +1116,9 @@ void mcsdp_destroy(mcsdp_ctx *c) {
       if (c->ev_rest[i]) cudaEventDestroy(c->ev_rest[i]);
     }
     if (c->st2) cudaStreamDestroy(c->st2);
+    if (c->st1) cudaStreamDestroy(c->st1);
+    if (c->cs.fork) cudaEventDestroy(c->cs.fork);
+    if (c->cs.chain_done) cudaEventDestroy(c->cs.chain_done);
   }
   delete c;
 }
