@@ -73,10 +73,14 @@ typedef struct {
 typedef struct {
   double beta, gamma, gap_tol, feas_tol;
   int32_t max_iter;
-  int32_t precision;     /* 0 = FP64; 1 = mixed: the SCE B dz = g is solved with an FP32 Cholesky
-                            factor of the FP64 B and FP64 iterative refinement, promoted to the
-                            FP64 factor for the rest of a solve when the refinement stalls or the
-                            FP32 factorisation breaks down (m <= 50000); everything else FP64 */
+  int32_t precision;     /* 0 = FP64.  1 = mixed: the SCM solves and contraction (K3) and the
+                            P-MATRIX solves (K6) run in FP32 from FP32 copies of L̂ and N; the
+                            SCE B dz = g is solved with an FP32 Cholesky factor of B and FP64
+                            iterative refinement against the stored B; Y's factor, Algorithm 1,
+                            the step lengths and the update stay FP64.  The solve promotes to
+                            FP64 throughout once the relative gap falls below mixed_gap, the
+                            refinement stalls, the FP32 factorisation breaks down or the primal
+                            residual grows (m <= 50000). */
   int64_t timeout_cycles;/* bound on any device spin-wait; 0 = library default */
   int32_t device;        /* CUDA device ordinal, or -1 for host-only */
   int32_t verbose;       /* 1 = one log line per iteration on stderr */
@@ -86,7 +90,9 @@ typedef struct {
   int32_t profile;       /* 1 = time every kernel class with CUDA events (mcsdp_stats_get) */
   int32_t relax;         /* 1 = relaxed supernode amalgamation (default), 0 = fundamental
                             supernodes only; amalgamation enlarges E with explicit zeros */
-  int32_t solve_warps;   /* warps per SM of the many-right-hand-side solve kernels; 0 = 2 */
+  int32_t solve_warps;   /* unused (kept for layout compatibility) */
+  double mixed_gap;      /* mixed form: relative gap below which every stage runs in FP64
+                            (default 1e-5) */
 } mcsdp_options;
 
 void mcsdp_default_options(mcsdp_options *opt);

@@ -154,7 +154,7 @@ class Problem:
             self._check(st)
         return out
 
-    def scm_assemble(self, Xbar_layout, z, out=None):
+    def scm_assemble(self, Xbar_layout, z, out=None, precision=0):
         X = self._dev(Xbar_layout, self.info["nnz_layout"])
         zz = self._dev(z, self.m)
         B = out if out is not None else torch.zeros(self.m, self.m, dtype=torch.float64,
@@ -165,7 +165,7 @@ class Problem:
         Bt = B.t()
         assert Bt.stride(0) == 1
         self._check(self._L.mcsdp_scm_assemble(self._ctx, _ptr(X), _ptr(zz), _ptr(B), self.m,
-                                               _ptr(h), 0))
+                                               _ptr(h), int(precision)))
         return Bt, h
 
     def newton_step(self, Xbar_layout, z):

@@ -120,19 +120,29 @@ size_t alg1_smem_bytes(const DevSym &S);
 // forward (L^{-1}, levels bottom-up) or backward (L^{-T}, top-down).  Returns the launch count.
 // lvl_xptr_host: per level, range of extra update chunks; lvl_fptr_host: per level, range of
 // xfst (targets with extra chunks); Pw: partial buffer (nslotw rows of ldw)
+template <class T>
 int lsolve(const DevSym &S, const int *lvl_ptr_host, const int *lvl_xptr_host,
            const int *lvl_fptr_host, const LsLevel *lvl_info, int height, bool fwd,
-           const double *L, const double *D, double *W, int64_t ldw, int ncolsW, const LsSkip &sk,
-           double *Pw, cudaStream_t st);
-void launch_rhs_unit(double *W, int64_t ldw, const int *rowof, int nrhs, cudaStream_t st);
+           const T *L, const T *D, T *W, int64_t ldw, int ncolsW, const LsSkip &sk, T *Pw,
+           cudaStream_t st);
+template <class T>
+void launch_rhs_unit(T *W, int64_t ldw, const int *rowof, int nrhs, cudaStream_t st);
+// every level fits the shared-memory staged kernels for this element size
+bool lsolve_staged_fits(const LsLevel *lvl_info, int height, int elem_size);
 // P-MATRIX pieces for the columns [k0, k0 + nc) held in W (row-major, ld = ldw):
-// Y^{-1} on lower(E) from Wy; Ww = dY Wy; M = X̂ dY Y^{-1} on E (lower and transposed) from Ww
-void launch_extract_lowerE(const DevSym &S, const double *W, int64_t ldw, int k0, int nc,
+// Y^{-1} on lower(E) from Wy; Ww = dY Wy; M = X̂ dY Y^{-1} on E (lower and transposed) from Ww.
+// T = double (FP64 form) or float (the mixed form's solves); the outputs on E are FP64.
+template <class T>
+void launch_extract_lowerE(const DevSym &S, const T *W, int64_t ldw, int k0, int nc,
                            double *outE, cudaStream_t st);
-void launch_extract_upperE(const DevSym &S, const double *W, int64_t ldw, int k0, int nc,
+template <class T>
+void launch_extract_upperE(const DevSym &S, const T *W, int64_t ldw, int k0, int nc,
                            double *outE, cudaStream_t st);
-void launch_dY_times(const DevSym &S, const double *dY, const double *Wy, double *Ww, int64_t ldw,
-                     int nc, cudaStream_t st);
+template <class T>
+void launch_dY_times(const DevSym &S, const double *dY, const T *Wy, T *Ww, int64_t ldw, int nc,
+                     cudaStream_t st);
+// out = (float) in, n entries (FP32 copies of the factors for the mixed form's solves)
+void launch_cast_f32(const double *in, float *out, int64_t n, cudaStream_t st);
 void launch_dx_combine(const DevSym &S, double betamu, const double *Xbar, const double *YinvE,
                        const double *Mlow, const double *Mup, double *dX, cudaStream_t st);
 // clique-wise primal step length (eq. primal_length2): alpha_r per clique
@@ -151,9 +161,11 @@ void launch_set_identity(const DevSym &S, double *Xbar, cudaStream_t st);
 // (row-major, ld = ldw, the columns of group g start at goff[g]); h_i = A_i . Y^{-1} on the
 // diagonal tiles.
 size_t scm_tiles_smem_bytes(const DevSym &S, int pmax);
-void launch_scm_tiles(const DevSym &S, const int2 *tiles, int ntiles, const double *WX,
-                      const double *WY, int64_t ldw, const int *goff, double *B, int64_t ldb,
-                      double *hvec, int pmax, cudaStream_t st);
+// T = double: FP64 form; T = float: mixed form (FP32 operands and sums, entries stored in FP64)
+template <class T>
+void launch_scm_tiles(const DevSym &S, const int2 *tiles, int ntiles, const T *WX, const T *WY,
+                      int64_t ldw, const int *goff, double *B, int64_t ldb, double *hvec,
+                      int pmax, cudaStream_t st);
 
 // ---------------- dense SCM factorisation (kern_dense.cu) ----------------
 // B internal, (m+1) x m lower, column-major, ld = ldb; row m holds g^T on entry and
@@ -162,22 +174,35 @@ void launch_scm_tiles(const DevSym &S, const int2 *tiles, int ntiles, const doub
 // Streams of the blocked Cholesky with lookahead: the critical path (diagonal block, panel solve,
 // update of the next block column) on a high-priority stream, the rest of every trailing update
 // on a low-priority one, forked from and joined back into the caller's stream.
+// The launch sequence (about four kernels per 32-column panel plus the stream dependencies) is
+// the same at every iteration, so after one eager run it is captured once into a CUDA graph per
+// (element type, matrix, size) and replayed.
+struct CholGraph {
+  const void *B = nullptr, *Linv = nullptr;
+  const int *status = nullptr;
+  int64_t ldb = 0;
+  int m = 0, rows = 0, esize = 0, runs = 0, kernels = 0;
+  cudaGraphExec_t exec = nullptr;
+};
 struct CholStreams {
   cudaStream_t chain = nullptr, rest = nullptr;
   cudaEvent_t next[2] = {}, rest_ev[2] = {}, fork = nullptr, chain_done = nullptr;
+  cudaEvent_t entry = nullptr, exit = nullptr;  // caller's stream -> chain stream -> caller's
+  CholGraph graphs[4];
 };
-// cs == nullptr: everything on st, no lookahead
+void chol_graphs_destroy(CholStreams *cs);
+// cs == nullptr: everything on st, no lookahead, no graph
 int dense_chol_bordered(double *B, int64_t ldb, int m, int *status, double *Linv,
-                        cudaStream_t st, const CholStreams *cs);
+                        cudaStream_t st, CholStreams *cs);
 int dense_backsolve(const double *B, int64_t ldb, int m, const double *Linv, double *x,
                     cudaStream_t st);
 int dense_chol_f32(float *B, int64_t ldb, int m, int *status, float *Linv, cudaStream_t st,
-                   const CholStreams *cs);
+                   CholStreams *cs);
 // Mixed precision.  mixed_factor: B made fully symmetric (strict upper <- lower^T), B32 <- FP32
 // Cholesky factor of B (L^T in its strict upper triangle), g <- row m of B (the right-hand side
 // border), r <- g, x <- 0.
 int mixed_factor(double *B, int64_t ldb, int m, float *B32, float *Linv32, int *status,
-                 double *g, double *r, double *x, cudaStream_t st, const CholStreams *cs);
+                 double *g, double *r, double *x, cudaStream_t st, CholStreams *cs);
 // number of column chunks of the refinement's matrix-vector product (P, A hold chunks x m)
 int mixed_chunks(int m);
 // one refinement step: x += (L32 L32^T)^{-1} r, then r = g - B x (FP64) and

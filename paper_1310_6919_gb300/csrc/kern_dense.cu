@@ -316,14 +316,95 @@ static int dense_chol(T *B, int64_t ldb, int m, int rows, int *status, T *Linv_a
   return launches;
 }
 
+// the factorisation through the graph cache of cs: the first call for a (type, matrix, size)
+// runs eagerly (it also sets the kernels' shared-memory attributes), the second captures the
+// sequence into a graph, every later one replays it
+template <class T>
+static int dense_chol_graph(T *B, int64_t ldb, int m, int rows, int *status, T *Linv,
+                            cudaStream_t st, CholStreams *cs);
+
+// runs on the chain stream (created by the library, so capturable whatever the caller's stream
+// is), ordered after and joined back into the caller's stream
+template <class T>
+static int dense_chol_cached(T *B, int64_t ldb, int m, int rows, int *status, T *Linv,
+                             cudaStream_t st_caller, CholStreams *cs) {
+  if (!cs) return dense_chol<T>(B, ldb, m, rows, status, Linv, st_caller, nullptr);
+  cudaEventRecord(cs->entry, st_caller);
+  cudaStreamWaitEvent(cs->chain, cs->entry, 0);
+  const int nl = dense_chol_graph<T>(B, ldb, m, rows, status, Linv, cs->chain, cs);
+  cudaEventRecord(cs->exit, cs->chain);
+  cudaStreamWaitEvent(st_caller, cs->exit, 0);
+  return nl;
+}
+
+template <class T>
+static int dense_chol_graph(T *B, int64_t ldb, int m, int rows, int *status, T *Linv,
+                            cudaStream_t st, CholStreams *cs) {
+  CholGraph *g = nullptr, *freeg = nullptr;
+  for (CholGraph &x : cs->graphs) {
+    if (x.B == B && x.Linv == Linv && x.status == status && x.ldb == ldb && x.m == m &&
+        x.rows == rows && x.esize == (int)sizeof(T))
+      g = &x;
+    else if (!x.B && !freeg)
+      freeg = &x;
+  }
+  if (!g && freeg) {
+    g = freeg;
+    g->B = B;
+    g->Linv = Linv;
+    g->status = status;
+    g->ldb = ldb;
+    g->m = m;
+    g->rows = rows;
+    g->esize = (int)sizeof(T);
+  }
+  if (!g || g->runs <= 0) {  // no slot left, first use, or capture unavailable: eager
+    if (g && g->runs == 0) g->runs = 1;
+    return dense_chol<T>(B, ldb, m, rows, status, Linv, st, cs);
+  }
+  if (!g->exec) {
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      (void)cudaGetLastError();
+      g->runs = -1;
+      return dense_chol<T>(B, ldb, m, rows, status, Linv, st, cs);
+    }
+    const int nl = dense_chol<T>(B, ldb, m, rows, status, Linv, st, cs);
+    if (cudaStreamEndCapture(st, &graph) != cudaSuccess || !graph) {
+      (void)cudaGetLastError();
+      g->runs = -1;
+      return dense_chol<T>(B, ldb, m, rows, status, Linv, st, cs);
+    }
+    if (cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) {
+      (void)cudaGetLastError();
+      g->exec = nullptr;
+    }
+    cudaGraphDestroy(graph);
+    if (!g->exec) {
+      g->runs = -1;
+      return dense_chol<T>(B, ldb, m, rows, status, Linv, st, cs);
+    }
+    g->kernels = nl;
+  }
+  cudaGraphLaunch(g->exec, st);
+  return g->kernels;  // kernels launched (as graph nodes)
+}
+
+void chol_graphs_destroy(CholStreams *cs) {
+  for (CholGraph &x : cs->graphs) {
+    if (x.exec) cudaGraphExecDestroy(x.exec);
+    x = CholGraph{};
+  }
+}
+
 int dense_chol_bordered(double *B, int64_t ldb, int m, int *status, double *Linv_all,
-                        cudaStream_t st, const CholStreams *cs) {
-  return dense_chol<double>(B, ldb, m, m + 1, status, Linv_all, st, cs);
+                        cudaStream_t st, CholStreams *cs) {
+  return dense_chol_cached<double>(B, ldb, m, m + 1, status, Linv_all, st, cs);
 }
 
 int dense_chol_f32(float *B, int64_t ldb, int m, int *status, float *Linv_all, cudaStream_t st,
-                   const CholStreams *cs) {
-  return dense_chol<float>(B, ldb, m, m, status, Linv_all, st, cs);
+                   CholStreams *cs) {
+  return dense_chol_cached<float>(B, ldb, m, m, status, Linv_all, st, cs);
 }
 
 // Backward substitution L^T x = y, y = row m of B, blocks of 64 from the bottom; the diagonal
@@ -750,7 +831,7 @@ __global__ void k_mixed_init(const double *__restrict__ B, int64_t ldb, int m, d
 int mixed_chunks(int m) { return (m + MV_CHUNK - 1) / MV_CHUNK; }
 
 int mixed_factor(double *B, int64_t ldb, int m, float *B32, float *Linv32, int *status,
-                 double *g, double *r, double *x, cudaStream_t st, const CholStreams *cs) {
+                 double *g, double *r, double *x, cudaStream_t st, CholStreams *cs) {
   k_mixed_init<<<(m + 255) / 256, 256, 0, st>>>(B, ldb, m, g, r, x);
   const int nt = (m + 31) / 32;
   k_mixed_prep<<<dim3(nt, nt), 256, 0, st>>>(B, ldb, B32, m);

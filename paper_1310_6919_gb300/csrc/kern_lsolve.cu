@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -143,9 +144,10 @@ __global__ void k_lfwd_partial(DevSym S, int x0, int ntiles, const double *__res
 // W[S_t] += sum of the partial slots of t, for every target of the level with extra update
 // chunks.  CTA = (32 columns, row c of S_t, target) x 8 chunk phases: phase p sums the chunks
 // xb + p, xb + p + 8, ..., then the 8 phase sums are added in order (deterministic).
-__global__ void k_lfwd_reduce(DevSym S, int f0, const double *__restrict__ Pw, double *W,
+template <class T>
+__global__ void k_lfwd_reduce(DevSym S, int f0, const T *__restrict__ Pw, T *W,
                               int64_t ldw, int ncolsW, LsSkip sk) {
-  __shared__ double part[8][33];
+  __shared__ T part[8][33];
   const int xb = S.xfst[f0 + blockIdx.z];
   const int t = S.xch_t[xb];
   const int c0 = S.sn_col[t];
@@ -157,13 +159,13 @@ __global__ void k_lfwd_reduce(DevSym S, int f0, const double *__restrict__ Pw, d
   const int lane = threadIdx.x & 31, ph = threadIdx.x >> 5;
   const int col = tile * 32 + lane;
   const int xe = S.xch_end[t];
-  double a = 0.0;
+  T a = T(0);
   if (col < ncolsW)
     for (int xx = xb + ph; xx < xe; xx += 8) a += Pw[(S.xch_slotw[xx] + c) * ldw + col];
   part[ph][lane] = a;
   __syncthreads();
   if (ph == 0 && col < ncolsW) {
-    double s = part[0][lane];
+    T s = part[0][lane];
     for (int q = 1; q < 8; ++q) s += part[q][lane];
     W[(int64_t)(c0 + c) * ldw + col] += s;
   }
@@ -299,6 +301,11 @@ __device__ __forceinline__ void cpa4(void *s, const void *g) {
                "l"(g)
                : "memory");
 }
+template <class T>
+__device__ __forceinline__ void cpaT(void *s, const void *g) {
+  if constexpr (sizeof(T) == 8) cpa8(s, g);
+  else cpa4(s, g);
+}
 __device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cpa_wait() {
@@ -311,17 +318,17 @@ struct FwdLayout {
   int acc, ds, meta, buf, bufsz, total;
 };
 // nc: ncol bound, cw/np: update chunk width / rows bound (cw = 0: no updates), with_d: D block
-__host__ __device__ inline FwdLayout fwd_layout(int nc, int cw, int np, bool with_d) {
+__host__ __device__ inline FwdLayout fwd_layout(int nc, int cw, int np, bool with_d, int es) {
   FwdLayout L;
   int o = 0;
   L.acc = o;
-  o += al16(nc * 32 * 8);
+  o += al16(nc * 32 * es);
   L.ds = o;
-  o += with_d ? al16(nc * nc * 8) : 0;
+  o += with_d ? al16(nc * nc * es) : 0;
   L.meta = o;
   o += cw > 0 ? 64 * (int)sizeof(UpdMeta) : 0;
   L.buf = o;
-  L.bufsz = cw > 0 ? al16(cw * 32 * 8) + al16(cw * np * 8) + al16(np * 4) : 0;
+  L.bufsz = cw > 0 ? al16(cw * 32 * es) + al16(cw * np * es) + al16(np * 4) : 0;
   o += LS_R * L.bufsz;
   L.total = o;
   return L;
@@ -330,17 +337,17 @@ __host__ __device__ inline FwdLayout fwd_layout(int nc, int cw, int np, bool wit
 struct BwdLayout {
   int ls, ds, acc, wv, rws, total;
 };
-__host__ __device__ inline BwdLayout bwd_layout(int nr, int nc) {
+__host__ __device__ inline BwdLayout bwd_layout(int nr, int nc, int es) {
   BwdLayout L;
   int o = 0;
   L.ls = o;
-  o += al16(nr * nc * 8);
+  o += al16(nr * nc * es);
   L.ds = o;
-  o += al16(nc * nc * 8);
+  o += al16(nc * nc * es);
   L.acc = o;
-  o += al16(nc * 32 * 8);
+  o += al16(nc * 32 * es);
   L.wv = o;
-  o += al16(nr * 32 * 8);
+  o += al16(nr * 32 * es);
   L.rws = o;
   o += al16(nr * 4);
   L.total = o;
@@ -349,14 +356,16 @@ __host__ __device__ inline BwdLayout bwd_layout(int nr, int nc) {
 
 // acc[srel[p]][lane] -= sum over the updates [ub, ue) of L_d[p1 + p, :] W[S_d], the update
 // blocks taken in chunks of <= cw source columns through the ring
-__device__ __forceinline__ void pull_staged(const DevSym &S, int ub, int ue, const double *L,
-                                            const double *Wc, int64_t ldw, double *acc,
+template <class T>
+__device__ __forceinline__ void pull_staged(const DevSym &S, int ub, int ue, const T *L,
+                                            const T *Wc, int64_t ldw, T *acc,
                                             unsigned char *sm, const FwdLayout &lay, int cw, int npb,
                                             int lane) {
   UpdMeta *ms = reinterpret_cast<UpdMeta *>(sm + lay.meta);
   int meta_end = ub;
   int iu = ub, ij = 0, issued = 0;
-  const int xs_off = 0, lb_off = al16(cw * 32 * 8), sr_off = lb_off + al16(cw * npb * 8);
+  const int es = (int)sizeof(T);
+  const int xs_off = 0, lb_off = al16(cw * 32 * es), sr_off = lb_off + al16(cw * npb * es);
   auto issue = [&]() {
     if (iu < ue) {
       while (iu >= meta_end) {  // next 32 records into the metadata ring (64 entries)
@@ -367,15 +376,15 @@ __device__ __forceinline__ void pull_staged(const DevSym &S, int ub, int ue, con
       }
       const UpdMeta m = ms[iu & 63];
       unsigned char *b = sm + lay.buf + (issued % LS_R) * lay.bufsz;
-      double *xs = reinterpret_cast<double *>(b + xs_off);
-      double *Lb = reinterpret_cast<double *>(b + lb_off);
+      T *xs = reinterpret_cast<T *>(b + xs_off);
+      T *Lb = reinterpret_cast<T *>(b + lb_off);
       int *sr = reinterpret_cast<int *>(b + sr_off);
       const int w = min(cw, m.dncol - ij);
-      for (int q = 0; q < w; ++q) cpa8(xs + q * 32 + lane, Wc + (int64_t)(m.dc0 + ij + q) * ldw);
-      const double *Lsrc = L + m.valp + (int64_t)ij * m.dnrow + m.p1;
+      for (int q = 0; q < w; ++q) cpaT<T>(xs + q * 32 + lane, Wc + (int64_t)(m.dc0 + ij + q) * ldw);
+      const T *Lsrc = L + m.valp + (int64_t)ij * m.dnrow + m.p1;
       for (int e = lane; e < m.np * w; e += 32) {
         const int q = e / m.np, p = e - q * m.np;
-        cpa8(Lb + e, Lsrc + (int64_t)q * m.dnrow + p);
+        cpaT<T>(Lb + e, Lsrc + (int64_t)q * m.dnrow + p);
       }
       for (int p = lane; p < m.np; p += 32) cpa4(sr + p, S.upd_rel + m.relptr + p);
       ij += w;
@@ -395,16 +404,16 @@ __device__ __forceinline__ void pull_staged(const DevSym &S, int ub, int ue, con
     __syncwarp();
     const UpdMeta m = ms[cu & 63];
     const unsigned char *b = sm + lay.buf + (done % LS_R) * lay.bufsz;
-    const double *xs = reinterpret_cast<const double *>(b + xs_off);
-    const double *Lb = reinterpret_cast<const double *>(b + lb_off);
+    const T *xs = reinterpret_cast<const T *>(b + xs_off);
+    const T *Lb = reinterpret_cast<const T *>(b + lb_off);
     const int *sr = reinterpret_cast<const int *>(b + sr_off);
     const int w = min(cw, m.dncol - cj), np = m.np;
     int p = 0;
     for (; p + 3 < np; p += 4) {
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
       for (int q = 0; q < w; ++q) {
-        const double x = xs[q * 32 + lane];
-        const double *lq = Lb + q * np + p;
+        const T x = xs[q * 32 + lane];
+        const T *lq = Lb + q * np + p;
         a0 = fma(lq[0], x, a0);
         a1 = fma(lq[1], x, a1);
         a2 = fma(lq[2], x, a2);
@@ -416,7 +425,7 @@ __device__ __forceinline__ void pull_staged(const DevSym &S, int ub, int ue, con
       acc[sr[p + 3] * 32 + lane] -= a3;
     }
     for (; p < np; ++p) {
-      double a0 = 0.0;
+      T a0 = T(0);
       for (int q = 0; q < w; ++q) a0 = fma(Lb[q * np + p], xs[q * 32 + lane], a0);
       acc[sr[p] * 32 + lane] -= a0;
     }
@@ -434,13 +443,13 @@ __device__ __forceinline__ void pull_staged(const DevSym &S, int ub, int ue, con
 // sub-partition); NW = 4 for narrow levels near the root, where one CTA per SM would leave three
 // of the four FP64 sub-partitions idle: warp 0 applies the updates, then the product with D is
 // split by rows over the warps.
-template <int NW>
+template <class T, int NW>
 __global__ void __launch_bounds__(32 * NW)
-    k_lfwd2(DevSym S, int lvl_begin, int ntiles, const double *__restrict__ L,
-            const double *__restrict__ Dall, double *W, int64_t ldw, int ncolsW, LsSkip sk, int nc,
+    k_lfwd2(DevSym S, int lvl_begin, int ntiles, const T *__restrict__ L,
+            const T *__restrict__ Dall, T *W, int64_t ldw, int ncolsW, LsSkip sk, int nc,
             int cw, int npb) {
   extern __shared__ __align__(16) unsigned char smf[];
-  const FwdLayout lay = fwd_layout(nc, cw, npb, true);
+  const FwdLayout lay = fwd_layout(nc, cw, npb, true, (int)sizeof(T));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int t = S.lvl_sn[lvl_begin + blockIdx.x / ntiles];
   const int tile = blockIdx.x % ntiles;
@@ -449,12 +458,12 @@ __global__ void __launch_bounds__(32 * NW)
   const bool act = col < ncolsW;
   const int c0 = S.sn_col[t];
   const int ncol = S.sn_col[t + 1] - c0;
-  double *acc = reinterpret_cast<double *>(smf + lay.acc);
-  double *Ds = reinterpret_cast<double *>(smf + lay.ds);
-  double *Wc = W + (act ? col : 0);
-  for (int j = warp; j < ncol; j += NW) cpa8(acc + j * 32 + lane, Wc + (int64_t)(c0 + j) * ldw);
-  const double *D = Dall + S.sn_dptr[t];
-  for (int e = tid; e < ncol * ncol; e += 32 * NW) cpa8(Ds + e, D + e);
+  T *acc = reinterpret_cast<T *>(smf + lay.acc);
+  T *Ds = reinterpret_cast<T *>(smf + lay.ds);
+  T *Wc = W + (act ? col : 0);
+  for (int j = warp; j < ncol; j += NW) cpaT<T>(acc + j * 32 + lane, Wc + (int64_t)(c0 + j) * ldw);
+  const T *D = Dall + S.sn_dptr[t];
+  for (int e = tid; e < ncol * ncol; e += 32 * NW) cpaT<T>(Ds + e, D + e);
   cpa_commit();
   if (NW > 1) {
     cpa_wait<0>();
@@ -467,10 +476,10 @@ __global__ void __launch_bounds__(32 * NW)
   __syncthreads();
   // W[S_t] <- D acc  (D lower: D[i][j] = Ds[i + j ncol], zero above the diagonal), 4 rows at once
   for (int i0 = 4 * warp; i0 < ncol; i0 += 4 * NW) {
-    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    T a[4] = {T(0), T(0), T(0), T(0)};
     const int jend = min(i0 + 4, ncol);
     for (int j = 0; j < jend; ++j) {
-      const double x = acc[j * 32 + lane];
+      const T x = acc[j * 32 + lane];
 #pragma unroll
       for (int r = 0; r < 4; ++r)
         if (i0 + r < ncol) a[r] = fma(Ds[(i0 + r) + j * ncol], x, a[r]);
@@ -481,11 +490,12 @@ __global__ void __launch_bounds__(32 * NW)
   }
 }
 
-__global__ void k_lfwd_partial2(DevSym S, int x0, int ntiles, const double *__restrict__ L,
-                                const double *__restrict__ W, int64_t ldw, int ncolsW, LsSkip sk,
-                                double *Pw, int nc, int cw, int npb) {
+template <class T>
+__global__ void k_lfwd_partial2(DevSym S, int x0, int ntiles, const T *__restrict__ L,
+                                const T *__restrict__ W, int64_t ldw, int ncolsW, LsSkip sk,
+                                T *Pw, int nc, int cw, int npb) {
   extern __shared__ __align__(16) unsigned char smp[];
-  const FwdLayout lay = fwd_layout(nc, cw, npb, false);
+  const FwdLayout lay = fwd_layout(nc, cw, npb, false, (int)sizeof(T));
   const int lane = threadIdx.x;
   const int x = x0 + blockIdx.x / ntiles;
   const int tile = blockIdx.x % ntiles;
@@ -494,24 +504,24 @@ __global__ void k_lfwd_partial2(DevSym S, int x0, int ntiles, const double *__re
   const int col = tile * 32 + lane;
   const bool act = col < ncolsW;
   const int ncol = S.sn_col[t + 1] - S.sn_col[t];
-  double *acc = reinterpret_cast<double *>(smp + lay.acc);
-  for (int c = 0; c < ncol; ++c) acc[c * 32 + lane] = 0.0;
+  T *acc = reinterpret_cast<T *>(smp + lay.acc);
+  for (int c = 0; c < ncol; ++c) acc[c * 32 + lane] = T(0);
   pull_staged(S, S.xch_ub[x], S.xch_ue[x], L, W + (act ? col : 0), ldw, acc, smp, lay, cw, npb,
               lane);
   cpa_wait<0>();
   __syncwarp();
-  double *P = Pw + S.xch_slotw[x] * ldw + (act ? col : 0);
+  T *P = Pw + S.xch_slotw[x] * ldw + (act ? col : 0);
   if (act)
     for (int c = 0; c < ncol; ++c) P[(int64_t)c * ldw] = acc[c * 32 + lane];
 }
 
-template <int NW>
+template <class T, int NW>
 __global__ void __launch_bounds__(32 * NW)
-    k_lbwd2(DevSym S, int lvl_begin, int ntiles, const double *__restrict__ L,
-            const double *__restrict__ Dall, double *W, int64_t ldw, int ncolsW, LsSkip sk,
+    k_lbwd2(DevSym S, int lvl_begin, int ntiles, const T *__restrict__ L,
+            const T *__restrict__ Dall, T *W, int64_t ldw, int ncolsW, LsSkip sk,
             int nr_b, int nc_b) {
   extern __shared__ __align__(16) unsigned char smb[];
-  const BwdLayout lay = bwd_layout(nr_b, nc_b);
+  const BwdLayout lay = bwd_layout(nr_b, nc_b, (int)sizeof(T));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int t = S.lvl_sn[lvl_begin + blockIdx.x / ntiles];
   const int tile = blockIdx.x % ntiles;
@@ -522,31 +532,31 @@ __global__ void __launch_bounds__(32 * NW)
   const int ncol = S.sn_col[t + 1] - c0;
   const int64_t r0 = S.sn_rowptr[t];
   const int nrow = (int)(S.sn_rowptr[t + 1] - r0);
-  double *Ls = reinterpret_cast<double *>(smb + lay.ls);
-  double *Ds = reinterpret_cast<double *>(smb + lay.ds);
-  double *acc = reinterpret_cast<double *>(smb + lay.acc);
-  double *wv = reinterpret_cast<double *>(smb + lay.wv);
+  T *Ls = reinterpret_cast<T *>(smb + lay.ls);
+  T *Ds = reinterpret_cast<T *>(smb + lay.ds);
+  T *acc = reinterpret_cast<T *>(smb + lay.acc);
+  T *wv = reinterpret_cast<T *>(smb + lay.wv);
   int *rws = reinterpret_cast<int *>(smb + lay.rws);
-  const double *Lt = L + S.sn_valptr[t];
-  const double *D = Dall + S.sn_dptr[t];
-  double *Wc = W + (act ? col : 0);
+  const T *Lt = L + S.sn_valptr[t];
+  const T *D = Dall + S.sn_dptr[t];
+  T *Wc = W + (act ? col : 0);
   for (int p = ncol + tid; p < nrow; p += 32 * NW) rws[p] = S.rows[r0 + p];
-  for (int e = tid; e < nrow * ncol; e += 32 * NW) cpa8(Ls + e, Lt + e);
-  for (int e = tid; e < ncol * ncol; e += 32 * NW) cpa8(Ds + e, D + e);
-  for (int j = warp; j < ncol; j += NW) cpa8(acc + j * 32 + lane, Wc + (int64_t)(c0 + j) * ldw);
+  for (int e = tid; e < nrow * ncol; e += 32 * NW) cpaT<T>(Ls + e, Lt + e);
+  for (int e = tid; e < ncol * ncol; e += 32 * NW) cpaT<T>(Ds + e, D + e);
+  for (int j = warp; j < ncol; j += NW) cpaT<T>(acc + j * 32 + lane, Wc + (int64_t)(c0 + j) * ldw);
   __syncthreads();
   for (int p = ncol + warp; p < nrow; p += NW)
-    cpa8(wv + (p - ncol) * 32 + lane, Wc + (int64_t)rws[p] * ldw);
+    cpaT<T>(wv + (p - ncol) * 32 + lane, Wc + (int64_t)rws[p] * ldw);
   cpa_commit();
   cpa_wait<0>();
   __syncthreads();
   // acc[j] -= sum_{p >= ncol} L[p][j] W[rows[p]], 4 columns j at once (column blocks over warps)
   for (int j0 = 4 * warp; j0 < ncol; j0 += 4 * NW) {
-    double a[4];
+    T a[4];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) a[r] = (j0 + r < ncol) ? acc[(j0 + r) * 32 + lane] : 0.0;
+    for (int r = 0; r < 4; ++r) a[r] = (j0 + r < ncol) ? acc[(j0 + r) * 32 + lane] : T(0);
     for (int p = ncol; p < nrow; ++p) {
-      const double w = wv[(p - ncol) * 32 + lane];
+      const T w = wv[(p - ncol) * 32 + lane];
 #pragma unroll
       for (int r = 0; r < 4; ++r)
         if (j0 + r < ncol) a[r] = fma(-Ls[p + (j0 + r) * nrow], w, a[r]);
@@ -558,9 +568,9 @@ __global__ void __launch_bounds__(32 * NW)
   __syncthreads();
   // W[S_t] <- D^T acc: out[i] = sum_{j >= i} D[j][i] acc[j], 4 rows at once (row blocks over warps)
   for (int i0 = 4 * warp; i0 < ncol; i0 += 4 * NW) {
-    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    T a[4] = {T(0), T(0), T(0), T(0)};
     for (int j = i0; j < ncol; ++j) {
-      const double x = acc[j * 32 + lane];
+      const T x = acc[j * 32 + lane];
 #pragma unroll
       for (int r = 0; r < 4; ++r)
         if (i0 + r < ncol) a[r] = fma(Ds[j + (i0 + r) * ncol], x, a[r]);
@@ -572,12 +582,22 @@ __global__ void __launch_bounds__(32 * NW)
 }
 
 constexpr int LS_SMEM_CAP = 200 * 1024;
+
+bool lsolve_staged_fits(const LsLevel *lvl_info, int height, int elem_size) {
+  for (int l = 0; l < height; ++l) {
+    const LsLevel &lv = lvl_info[l];
+    if (fwd_layout(lv.nc, lv.cw, lv.np, true, elem_size).total > LS_SMEM_CAP) return false;
+    if (bwd_layout(lv.nr, lv.nc, elem_size).total > LS_SMEM_CAP) return false;
+  }
+  return true;
+}
 constexpr int LS_NARROW_PER_SM = 8;  // CTAs per SM of a level below which a CTA gets four warps
 
+template <class T>
 int lsolve(const DevSym &S, const int *lvl_ptr_host, const int *lvl_xptr_host,
            const int *lvl_fptr_host, const LsLevel *lvl_info, int height, bool fwd,
-           const double *L, const double *D, double *W, int64_t ldw, int ncolsW, const LsSkip &sk,
-           double *Pw, cudaStream_t st) {
+           const T *L, const T *D, T *W, int64_t ldw, int ncolsW, const LsSkip &sk,
+           T *Pw, cudaStream_t st) {
   if (ncolsW <= 0) return 0;
   const int ntiles = (ncolsW + 31) / 32;
   const size_t smem = (size_t)S.max_ncol * 32 * 8 + (size_t)LS_CH * S.max_nrow * 8 + (size_t)S.max_nrow * 4 + 16;
@@ -597,11 +617,11 @@ int lsolve(const DevSym &S, const int *lvl_ptr_host, const int *lvl_xptr_host,
   }
   static bool configured2 = false;
   if (!configured2) {
-    cudaFuncSetAttribute(k_lfwd2<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, LS_SMEM_CAP);
-    cudaFuncSetAttribute(k_lbwd2<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, LS_SMEM_CAP);
-    cudaFuncSetAttribute(k_lfwd2<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, LS_SMEM_CAP);
-    cudaFuncSetAttribute(k_lbwd2<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, LS_SMEM_CAP);
-    cudaFuncSetAttribute(k_lfwd_partial2, cudaFuncAttributeMaxDynamicSharedMemorySize, LS_SMEM_CAP);
+    cudaFuncSetAttribute(k_lfwd2<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, LS_SMEM_CAP);
+    cudaFuncSetAttribute(k_lbwd2<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, LS_SMEM_CAP);
+    cudaFuncSetAttribute(k_lfwd2<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, LS_SMEM_CAP);
+    cudaFuncSetAttribute(k_lbwd2<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, LS_SMEM_CAP);
+    cudaFuncSetAttribute(k_lfwd_partial2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, LS_SMEM_CAP);
     configured2 = true;
   }
   int launches = 0;
@@ -611,39 +631,42 @@ int lsolve(const DevSym &S, const int *lvl_ptr_host, const int *lvl_xptr_host,
     const int64_t blocks = (int64_t)cnt * ntiles;
     if (blocks <= 0) continue;
     const LsLevel &lv = lvl_info[l];
-    const int sf = fwd_layout(lv.nc, lv.cw, lv.np, true).total;
-    const int sp = fwd_layout(lv.nc, lv.cw, lv.np, false).total;
-    const int sb = bwd_layout(lv.nr, lv.nc).total;
+    const int es = (int)sizeof(T);
+    const int sf = fwd_layout(lv.nc, lv.cw, lv.np, true, es).total;
+    const int sp = fwd_layout(lv.nc, lv.cw, lv.np, false, es).total;
+    const int sb = bwd_layout(lv.nr, lv.nc, es).total;
     const bool narrow = blocks <= (int64_t)LS_NARROW_PER_SM * nsm;
     if (fwd && sf <= LS_SMEM_CAP) {
       const int xb = lvl_xptr_host[l], xc = lvl_xptr_host[l + 1] - xb;
       if (xc > 0) {
-        k_lfwd_partial2<<<(unsigned)((int64_t)xc * ntiles), 32, sp, st>>>(
+        k_lfwd_partial2<T><<<(unsigned)((int64_t)xc * ntiles), 32, sp, st>>>(
             S, xb, ntiles, L, W, ldw, ncolsW, sk, Pw, lv.nc, lv.cw, lv.np);
         const int f0 = lvl_fptr_host[l], nf = lvl_fptr_host[l + 1] - f0;
-        if (nf > 0) k_lfwd_reduce<<<dim3(ntiles, lv.nc, nf), 256, 0, st>>>(S, f0, Pw, W, ldw, ncolsW, sk);
+        if (nf > 0) k_lfwd_reduce<T><<<dim3(ntiles, lv.nc, nf), 256, 0, st>>>(S, f0, Pw, W, ldw, ncolsW, sk);
         launches += 2;
       }
       if (narrow)
-        k_lfwd2<4><<<(unsigned)blocks, 128, sf, st>>>(S, b, ntiles, L, D, W, ldw, ncolsW, sk, lv.nc,
+        k_lfwd2<T, 4><<<(unsigned)blocks, 128, sf, st>>>(S, b, ntiles, L, D, W, ldw, ncolsW, sk, lv.nc,
                                                       lv.cw, lv.np);
       else
-        k_lfwd2<1><<<(unsigned)blocks, 32, sf, st>>>(S, b, ntiles, L, D, W, ldw, ncolsW, sk, lv.nc,
+        k_lfwd2<T, 1><<<(unsigned)blocks, 32, sf, st>>>(S, b, ntiles, L, D, W, ldw, ncolsW, sk, lv.nc,
                                                      lv.cw, lv.np);
     } else if (!fwd && sb <= LS_SMEM_CAP) {
       if (narrow)
-        k_lbwd2<4><<<(unsigned)blocks, 128, sb, st>>>(S, b, ntiles, L, D, W, ldw, ncolsW, sk, lv.nr,
+        k_lbwd2<T, 4><<<(unsigned)blocks, 128, sb, st>>>(S, b, ntiles, L, D, W, ldw, ncolsW, sk, lv.nr,
                                                       lv.nc);
       else
-        k_lbwd2<1><<<(unsigned)blocks, 32, sb, st>>>(S, b, ntiles, L, D, W, ldw, ncolsW, sk, lv.nr,
+        k_lbwd2<T, 1><<<(unsigned)blocks, 32, sb, st>>>(S, b, ntiles, L, D, W, ldw, ncolsW, sk, lv.nr,
                                                      lv.nc);
+    } else if constexpr (!std::is_same<T, double>::value) {
+      return -1;  // FP32 solves only through the staged kernels
     } else if (fwd) {
       const int xb = lvl_xptr_host[l], xc = lvl_xptr_host[l + 1] - xb;
       if (xc > 0) {
         k_lfwd_partial<<<(unsigned)((int64_t)xc * ntiles), 32, smem, st>>>(S, xb, ntiles, L, W, ldw,
                                                                            ncolsW, sk, Pw);
         const int f0 = lvl_fptr_host[l], nf = lvl_fptr_host[l + 1] - f0;
-        if (nf > 0) k_lfwd_reduce<<<dim3(ntiles, S.max_ncol, nf), 256, 0, st>>>(S, f0, Pw, W, ldw, ncolsW, sk);
+        if (nf > 0) k_lfwd_reduce<double><<<dim3(ntiles, S.max_ncol, nf), 256, 0, st>>>(S, f0, Pw, W, ldw, ncolsW, sk);
         launches += 2;
       }
       k_lfwd<<<(unsigned)blocks, 32, smem, st>>>(S, b, ntiles, L, D, W, ldw, ncolsW, sk, Pw);
@@ -654,14 +677,25 @@ int lsolve(const DevSym &S, const int *lvl_ptr_host, const int *lvl_xptr_host,
   return launches;
 }
 
+template int lsolve<double>(const DevSym &, const int *, const int *, const int *, const LsLevel *,
+                            int, bool, const double *, const double *, double *, int64_t, int,
+                            const LsSkip &, double *, cudaStream_t);
+template int lsolve<float>(const DevSym &, const int *, const int *, const int *, const LsLevel *,
+                           int, bool, const float *, const float *, float *, int64_t, int,
+                           const LsSkip &, float *, cudaStream_t);
+
 // W[rowof[j] * ldw + j] = 1 for the unit right-hand sides (W zeroed before)
-__global__ void k_rhs_unit(double *W, int64_t ldw, const int *rowof, int nrhs) {
+template <class T>
+__global__ void k_rhs_unit(T *W, int64_t ldw, const int *rowof, int nrhs) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < nrhs) W[(int64_t)rowof[j] * ldw + j] = 1.0;
+  if (j < nrhs) W[(int64_t)rowof[j] * ldw + j] = T(1);
 }
 
-void launch_rhs_unit(double *W, int64_t ldw, const int *rowof, int nrhs, cudaStream_t st) {
-  if (nrhs > 0) k_rhs_unit<<<(nrhs + 255) / 256, 256, 0, st>>>(W, ldw, rowof, nrhs);
+template <class T>
+void launch_rhs_unit(T *W, int64_t ldw, const int *rowof, int nrhs, cudaStream_t st) {
+  if (nrhs > 0) k_rhs_unit<T><<<(nrhs + 255) / 256, 256, 0, st>>>(W, ldw, rowof, nrhs);
 }
+template void launch_rhs_unit<double>(double *, int64_t, const int *, int, cudaStream_t);
+template void launch_rhs_unit<float>(float *, int64_t, const int *, int, cudaStream_t);
 
 }  // namespace mcsdp

@@ -22,18 +22,22 @@ namespace mcsdp {
 
 constexpr int XW_CAP = 6144;  // doubles of shared memory for the X̂-times-A_j products
 
+// T = double: the FP64 form; T = float: the mixed form's assembly (FP32 operands and sums, the
+// entries stored into the FP64 B)
+template <class T>
 __global__ void k_scm_tiles(DevSym S, const int2 *__restrict__ tiles,
-                            const double *__restrict__ WX, const double *__restrict__ WY,
+                            const T *__restrict__ WX, const T *__restrict__ WY,
                             int64_t ldw, const int *__restrict__ goff, double *B, int64_t ldb,
                             double *hvec) {
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) unsigned char smr[];
+  T *sm = reinterpret_cast<T *>(smr);
   const int2 tl = tiles[blockIdx.x];
   const int h = tl.x, g = tl.y;
   const int pbg = S.grp_pptr[g], pg = S.grp_pptr[g + 1] - pbg;
   const int pbh = S.grp_pptr[h], ph = S.grp_pptr[h + 1] - pbh;
   const int cg = goff[g];
-  double *Xs = sm;
-  double *Ys = sm + ph * pg;
+  T *Xs = sm;
+  T *Ys = sm + ph * pg;
   const int tid = threadIdx.x, bd = blockDim.x;
   // X̂[P_h, P_g], Y^{-1}[P_h, P_g]: rows P_h of the group's solved columns
   for (int idx = tid; idx < ph * pg; idx += bd) {
@@ -48,17 +52,17 @@ __global__ void k_scm_tiles(DevSym S, const int2 *__restrict__ tiles,
   // nonzero lists of J_h and J_g in shared memory: (offset into Xs/Ys column, value)
   const int hb = S.anz_ptr[i0], hn = S.anz_ptr[i0 + nh] - hb;
   const int gb = S.anz_ptr[j0], gn = S.anz_ptr[j0 + ng] - gb;
-  double *hv = Ys + ph * pg;
-  double *gv = hv + hn;
+  T *hv = Ys + ph * pg;
+  T *gv = hv + hn;
   int *ha = reinterpret_cast<int *>(gv + gn);  // a (row of Xs) | b << 16 (row of Ys)
   int *ga = ha + hn;                           // c * ph | d * ph << 16 packed as two shorts
   int *gd = ga + gn;
   for (int e = tid; e < hn; e += bd) {
-    hv[e] = S.anz_v[hb + e];
+    hv[e] = (T)S.anz_v[hb + e];
     ha[e] = S.anz_a[hb + e] | (S.anz_b[hb + e] << 16);
   }
   for (int e = tid; e < gn; e += bd) {
-    gv[e] = S.anz_v[gb + e];
+    gv[e] = (T)S.anz_v[gb + e];
     ga[e] = S.anz_a[gb + e] * ph;
     gd[e] = S.anz_b[gb + e] * ph;
   }
@@ -67,7 +71,7 @@ __global__ void k_scm_tiles(DevSym S, const int2 *__restrict__ tiles,
   // nonzeros u of A_j, then B_ij = sum_t v_t sum_u XW[jb][u][a_t] Y^{-1}[P_h[b_t], d_u]
   // (one multiply-add per pair of nonzeros)
   // the int lists (hn + 2 gn ints) start 8-byte aligned; round their end up to 8 bytes
-  double *XW = reinterpret_cast<double *>(ha + ((hn + 2 * gn + 1) & ~1));
+  T *XW = reinterpret_cast<T *>(ha + ((hn + 2 * gn + 1) & ~1));
   const int cap_nnz = XW_CAP / (ph > 0 ? ph : 1);
   for (int jb0 = 0, nj = 0; jb0 < ng; jb0 += nj) {
     // batch: as many constraints as fit XW_CAP doubles (at least one)
@@ -85,12 +89,12 @@ __global__ void k_scm_tiles(DevSym S, const int2 *__restrict__ tiles,
       const int i = i0 + ii, j = j0 + jb0 + jb;
       if (h == g && i < j) continue;
       const int ub = S.anz_ptr[j] - gb, ue = S.anz_ptr[j + 1] - gb;
-      double acc = 0.0;
+      T acc = T(0);
       for (int t = S.anz_ptr[i] - hb; t < S.anz_ptr[i + 1] - hb; ++t) {
         const int a = ha[t] & 0xffff, b = ha[t] >> 16;
-        const double *xw = XW + (ub - ub0) * ph + a;
-        const double *yr = Ys + b;
-        double s0 = 0.0, s1 = 0.0;
+        const T *xw = XW + (ub - ub0) * ph + a;
+        const T *yr = Ys + b;
+        T s0 = T(0), s1 = T(0);
         int u = 0;
         const int nu = ue - ub;
         for (; u + 1 < nu; u += 2) {
@@ -100,17 +104,17 @@ __global__ void k_scm_tiles(DevSym S, const int2 *__restrict__ tiles,
         if (u < nu) s0 = fma(xw[u * ph], yr[gd[ub + u]], s0);
         acc = fma(hv[t], s0 + s1, acc);
       }
-      B[i + (int64_t)j * ldb] = acc;
+      B[i + (int64_t)j * ldb] = (double)acc;
     }
     __syncthreads();
   }
   if (h == g) {
     for (int ii = tid; ii < nh; ii += bd) {
       const int i = i0 + ii;
-      double hv = 0.0;
+      T hsum = T(0);
       for (int t = S.anz_ptr[i]; t < S.anz_ptr[i + 1]; ++t)
-        hv = fma(S.anz_v[t], Ys[S.anz_a[t] + S.anz_b[t] * ph], hv);
-      hvec[i] = hv;
+        hsum = fma((T)S.anz_v[t], Ys[S.anz_a[t] + S.anz_b[t] * ph], hsum);
+      hvec[i] = (double)hsum;
     }
   }
 }
@@ -120,8 +124,9 @@ size_t scm_tiles_smem_bytes(const DevSym &S, int pmax) {
   return (size_t)2 * pmax * pmax * 8 + (size_t)2 * S.max_grp_nnz * (8 + 8) + 64 + xw * 8;
 }
 
-void launch_scm_tiles(const DevSym &S, const int2 *tiles, int ntiles, const double *WX,
-                      const double *WY, int64_t ldw, const int *goff, double *B, int64_t ldb,
+template <class T>
+void launch_scm_tiles(const DevSym &S, const int2 *tiles, int ntiles, const T *WX,
+                      const T *WY, int64_t ldw, const int *goff, double *B, int64_t ldb,
                       double *hvec, int pmax, cudaStream_t st) {
   if (ntiles <= 0) return;
   // two |P_h| x |P_g| blocks, the nonzero lists of two groups, and the X̂-times-A_j products of
@@ -129,10 +134,16 @@ void launch_scm_tiles(const DevSym &S, const int2 *tiles, int ntiles, const doub
   const size_t smem = scm_tiles_smem_bytes(S, pmax);
   static size_t configured = 0;
   if (smem > configured) {
-    cudaFuncSetAttribute(k_scm_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_scm_tiles<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     configured = smem;
   }
-  k_scm_tiles<<<ntiles, 256, smem, st>>>(S, tiles, WX, WY, ldw, goff, B, ldb, hvec);
+  k_scm_tiles<T><<<ntiles, 256, smem, st>>>(S, tiles, WX, WY, ldw, goff, B, ldb, hvec);
 }
+template void launch_scm_tiles<double>(const DevSym &, const int2 *, int, const double *,
+                                       const double *, int64_t, const int *, double *, int64_t,
+                                       double *, int, cudaStream_t);
+template void launch_scm_tiles<float>(const DevSym &, const int2 *, int, const float *,
+                                      const float *, int64_t, const int *, double *, int64_t,
+                                      double *, int, cudaStream_t);
 
 }  // namespace mcsdp

@@ -324,7 +324,8 @@ void launch_alg1(const DevSym &S, const double *X, double *Lh, double *DL, int *
 
 // K6 pieces.  For the columns k in [k0, k0 + nc) solved into W (row-major, ld = ldw):
 // lower(E) entries of column k: outE[(i, k)] = W[i][k - k0] for the rows i >= k of k's clique
-__global__ void k_extract_lowerE(DevSym S, const double *__restrict__ W, int64_t ldw, int k0, int nc,
+template <class T>
+__global__ void k_extract_lowerE(DevSym S, const T *__restrict__ W, int64_t ldw, int k0, int nc,
                                  double *outE) {
   const int j = blockIdx.x * blockDim.y + threadIdx.y;
   if (j >= nc) return;
@@ -335,50 +336,80 @@ __global__ void k_extract_lowerE(DevSym S, const double *__restrict__ W, int64_t
   const int lc = k - S.sn_col[t];
   const int64_t cbase = S.sn_valptr[t] + (int64_t)lc * nrow;
   for (int p = lc + threadIdx.x; p < nrow; p += blockDim.x)
-    outE[cbase + p] = W[(int64_t)S.rows[r0 + p] * ldw + j];
+    outE[cbase + p] = (double)W[(int64_t)S.rows[r0 + p] * ldw + j];
 }
 
 // transposed entries: for rows i < k with (k, i) in E, outE[(k, i)] = W[i][k - k0]
-__global__ void k_extract_upperE(DevSym S, const double *__restrict__ W, int64_t ldw, int k0, int nc,
+template <class T>
+__global__ void k_extract_upperE(DevSym S, const T *__restrict__ W, int64_t ldw, int k0, int nc,
                                  double *outE) {
   const int j = blockIdx.x * blockDim.y + threadIdx.y;
   if (j >= nc) return;
   const int k = k0 + j;
   for (int q = S.rs_ptr[k] + threadIdx.x; q < S.rs_ptr[k + 1]; q += blockDim.x)
-    outE[S.rs_off[q]] = W[(int64_t)S.rs_col[q] * ldw + j];
+    outE[S.rs_off[q]] = (double)W[(int64_t)S.rs_col[q] * ldw + j];
 }
 
-void launch_extract_lowerE(const DevSym &S, const double *W, int64_t ldw, int k0, int nc,
+template <class T>
+void launch_extract_lowerE(const DevSym &S, const T *W, int64_t ldw, int k0, int nc,
                            double *outE, cudaStream_t st) {
   if (nc <= 0) return;
   dim3 blk(32, 8);
-  k_extract_lowerE<<<(nc + 7) / 8, blk, 0, st>>>(S, W, ldw, k0, nc, outE);
+  k_extract_lowerE<T><<<(nc + 7) / 8, blk, 0, st>>>(S, W, ldw, k0, nc, outE);
 }
 
-void launch_extract_upperE(const DevSym &S, const double *W, int64_t ldw, int k0, int nc,
+template <class T>
+void launch_extract_upperE(const DevSym &S, const T *W, int64_t ldw, int k0, int nc,
                            double *outE, cudaStream_t st) {
   if (nc <= 0) return;
   dim3 blk(32, 8);
-  k_extract_upperE<<<(nc + 7) / 8, blk, 0, st>>>(S, W, ldw, k0, nc, outE);
+  k_extract_upperE<T><<<(nc + 7) / 8, blk, 0, st>>>(S, W, ldw, k0, nc, outE);
 }
 
 // Ww = dY Wy on the aggregate pattern (full symmetric row lists), row i per CTA row
-__global__ void k_dY_times(DevSym S, const double *__restrict__ dY, const double *__restrict__ Wy,
-                          double *Ww, int64_t ldw, int nc) {
+template <class T>
+__global__ void k_dY_times(DevSym S, const double *__restrict__ dY, const T *__restrict__ Wy,
+                          T *Ww, int64_t ldw, int nc) {
   const int i = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nc) return;
-  double acc = 0.0;
+  T acc = T(0);
   for (int q = S.arow_ptr[i]; q < S.arow_ptr[i + 1]; ++q)
-    acc = fma(dY[S.arow_off[q]], Wy[(int64_t)S.arow_col[q] * ldw + j], acc);
+    acc = fma((T)dY[S.arow_off[q]], Wy[(int64_t)S.arow_col[q] * ldw + j], acc);
   Ww[(int64_t)i * ldw + j] = acc;
 }
 
-void launch_dY_times(const DevSym &S, const double *dY, const double *Wy, double *Ww, int64_t ldw,
+template <class T>
+void launch_dY_times(const DevSym &S, const double *dY, const T *Wy, T *Ww, int64_t ldw,
                      int nc, cudaStream_t st) {
   if (nc <= 0) return;
   dim3 grid((nc + 127) / 128, S.n);
-  k_dY_times<<<grid, 128, 0, st>>>(S, dY, Wy, Ww, ldw, nc);
+  k_dY_times<T><<<grid, 128, 0, st>>>(S, dY, Wy, Ww, ldw, nc);
+}
+
+#define MCSDP_PM_INST(T)                                                                        \
+  template void launch_extract_lowerE<T>(const DevSym &, const T *, int64_t, int, int, double *, \
+                                         cudaStream_t);                                         \
+  template void launch_extract_upperE<T>(const DevSym &, const T *, int64_t, int, int, double *, \
+                                         cudaStream_t);                                         \
+  template void launch_dY_times<T>(const DevSym &, const double *, const T *, T *, int64_t, int, \
+                                   cudaStream_t);
+MCSDP_PM_INST(double)
+MCSDP_PM_INST(float)
+#undef MCSDP_PM_INST
+
+// out[i] = (float) in[i]
+__global__ void k_cast_f32(const double *__restrict__ in, float *out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+void launch_cast_f32(const double *in, float *out, int64_t n, cudaStream_t st) {
+  if (n <= 0) return;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  k_cast_f32<<<blocks, 256, 0, st>>>(in, out, n);
 }
 
 // dX on lower(E): beta mu Y^{-1} - X̄ - (M + M^T)/2   (eq. dX with the symmetrisation)

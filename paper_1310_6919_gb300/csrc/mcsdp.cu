@@ -97,6 +97,8 @@ struct mcsdp_ctx {
   double *Pw = nullptr, *Pf = nullptr, *Binv = nullptr;
   // mixed form: FP32 factor of B, FP64 refinement vectors
   float *B32 = nullptr, *Linv32 = nullptr;
+  float *L32 = nullptr, *N32 = nullptr, *dL32 = nullptr, *dN32 = nullptr;  // FP32 factor copies
+  bool f32_solves = false;      // the FP32 SCM / P-MATRIX solves fit the staged kernels
   double *gref = nullptr, *rref = nullptr, *yref = nullptr, *ayref = nullptr, *nref = nullptr;
   bool promoted = false;        // the FP64 factor is used for the rest of the solve
   int promoted_iter = -1, refine_steps = 0, cur_iter = 0;
@@ -496,6 +498,11 @@ void plan_workspace(mcsdp_ctx *c) {
     plan_buf(c, cur, "yref", mx ? (size_t)mixed_chunks(m) * m * 8 : 0);
     plan_buf(c, cur, "ayref", mx ? (size_t)mixed_chunks(m) * m * 8 : 0);
     plan_buf(c, cur, "nref", 4 * 8);
+    plan_buf(c, cur, "L32", mx ? (size_t)nnzL * 4 : 0);
+    plan_buf(c, cur, "N32", mx ? (size_t)nnzL * 4 : 0);
+    plan_buf(c, cur, "dL32", mx ? (size_t)nnzD * 4 : 0);
+    plan_buf(c, cur, "dN32", mx ? (size_t)nnzD * 4 : 0);
+    c->f32_solves = mx && lsolve_staged_fits(c->lvl_info.data(), S.height, 4);
   }  // [0..3] phases, [8..8+NCAND) dual candidates
   c->ws_bytes = cur;
 }
@@ -616,6 +623,10 @@ void bind_pointers(mcsdp_ctx *c) {
   c->yref = wsp<double>(c, "yref");
   c->ayref = wsp<double>(c, "ayref");
   c->nref = wsp<double>(c, "nref");
+  c->L32 = wsp<float>(c, "L32");
+  c->N32 = wsp<float>(c, "N32");
+  c->dL32 = wsp<float>(c, "dL32");
+  c->dN32 = wsp<float>(c, "dN32");
 
   c->rowof_dev = wsp<int>(c, "rowof");
   c->goff_dev = wsp<int>(c, "goff");
@@ -695,29 +706,67 @@ mcsdp_status factor_X(mcsdp_ctx *c, const double *Xbar) {
   return MCSDP_OK;
 }
 
+// factors in the element type of the solves: FP64 originals, or the FP32 copies of the mixed form
+template <class T>
+struct SolveFactors {
+  const T *Lh, *dinvL, *N, *dinvN;
+};
+SolveFactors<double> factors_of(const mcsdp_ctx *c, double) {
+  return {c->Lh, c->dinvL, c->N, c->dinvN};
+}
+SolveFactors<float> factors_of(const mcsdp_ctx *c, float) {
+  return {c->L32, c->dL32, c->N32, c->dN32};
+}
+
+// FP32 copies of L̂, N and their diagonal-block inverses (mixed form)
+void cast_factors(mcsdp_ctx *c) {
+  KScope ks(c, KC_MISC);
+  launch_cast_f32(c->Lh, c->L32, c->D.nnzL, c->stream);
+  launch_cast_f32(c->N, c->N32, c->D.nnzL, c->stream);
+  launch_cast_f32(c->dinvL, c->dL32, c->D.nnzD, c->stream);
+  launch_cast_f32(c->dinvN, c->dN32, c->D.nnzD, c->stream);
+  ks.done(4);
+}
+
+template <class T>
+int lsolve_c(mcsdp_ctx *c, bool fwd, const T *L, const T *Dinv, T *W, int ncols, const LsSkip &sk) {
+  const Symbolic &S = c->S;
+  return lsolve<T>(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), c->lvl_fptr.data(),
+                   c->lvl_info.data(), S.height, fwd, L, Dinv, W, c->ldw, ncols, sk,
+                   reinterpret_cast<T *>(c->Pw), c->stream);
+}
+
+// K3 with solves in T (the W buffers and partial slots hold T; as FP32 they use half their size)
+template <class T>
 mcsdp_status phase_scm(mcsdp_ctx *c) {
   const Symbolic &S = c->S;
   const int n = S.n;
+  const SolveFactors<T> f = factors_of(c, T());
+  T *W1 = reinterpret_cast<T *>(c->W1), *W2 = reinterpret_cast<T *>(c->W2);
   for (const Chunk &ch : c->chunks) {
     KScope k1(c, KC_PANEL);
     int nl = 0;
-    CUDA_TRY(c, cudaMemsetAsync(c->W1, 0, (size_t)n * c->ldw * 8, c->stream));
-    CUDA_TRY(c, cudaMemsetAsync(c->W2, 0, (size_t)n * c->ldw * 8, c->stream));
-    launch_rhs_unit(c->W1, c->ldw, c->rowof_dev + ch.rhs_begin, ch.nrhs, c->stream);
-    launch_rhs_unit(c->W2, c->ldw, c->rowof_dev + ch.rhs_begin, ch.nrhs, c->stream);
+    CUDA_TRY(c, cudaMemsetAsync(W1, 0, (size_t)n * c->ldw * sizeof(T), c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(W2, 0, (size_t)n * c->ldw * sizeof(T), c->stream));
+    launch_rhs_unit(W1, c->ldw, c->rowof_dev + ch.rhs_begin, ch.nrhs, c->stream);
+    launch_rhs_unit(W2, c->ldw, c->rowof_dev + ch.rhs_begin, ch.nrhs, c->stream);
     nl += 2;
     LsSkip fw{c->reach_bits_dev, c->tkey_dev + ch.tkey_begin, c->bit_words};
     LsSkip bw{c->need_bits_dev, c->tkey_dev + ch.tkey_begin, c->bit_words};
     // X̂[:, P_g] = L̂^{-T} L̂^{-1} E and Y^{-1}[:, P_g] = N^{-T} N^{-1} E for the chunk's groups
-    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), c->lvl_fptr.data(), c->lvl_info.data(), S.height, true, c->Lh, c->dinvL, c->W1, c->ldw, ch.nrhs, fw, c->Pw, c->stream);
-    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), c->lvl_fptr.data(), c->lvl_info.data(), S.height, false, c->Lh, c->dinvL, c->W1, c->ldw, ch.nrhs, bw, c->Pw, c->stream);
-    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), c->lvl_fptr.data(), c->lvl_info.data(), S.height, true, c->N, c->dinvN, c->W2, c->ldw, ch.nrhs, fw, c->Pw, c->stream);
-    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), c->lvl_fptr.data(), c->lvl_info.data(), S.height, false, c->N, c->dinvN, c->W2, c->ldw, ch.nrhs, bw, c->Pw, c->stream);
+    int r[4] = {lsolve_c<T>(c, true, f.Lh, f.dinvL, W1, ch.nrhs, fw),
+                lsolve_c<T>(c, false, f.Lh, f.dinvL, W1, ch.nrhs, bw),
+                lsolve_c<T>(c, true, f.N, f.dinvN, W2, ch.nrhs, fw),
+                lsolve_c<T>(c, false, f.N, f.dinvN, W2, ch.nrhs, bw)};
+    for (int q = 0; q < 4; ++q) {
+      if (r[q] < 0) return fail(c, MCSDP_ERR_ARG, "solve shape not supported in this precision");
+      nl += r[q];
+    }
     k1.done(nl);
     KCHECK(c);
     KScope k2(c, KC_TILE);
-    launch_scm_tiles(c->D, c->tiles_dev + ch.tile_begin, ch.ntiles, c->W1, c->W2, c->ldw,
-                     c->goff_dev, c->B, c->ldb, c->hvec, c->pmax, c->stream);
+    launch_scm_tiles(c->D, c->tiles_dev + ch.tile_begin, ch.ntiles, (const T *)W1, (const T *)W2,
+                     c->ldw, c->goff_dev, c->B, c->ldb, c->hvec, c->pmax, c->stream);
     k2.done(1);
     KCHECK(c);
   }
@@ -726,27 +775,35 @@ mcsdp_status phase_scm(mcsdp_ctx *c) {
 
 // P-MATRIX (eq. newdX2): for column blocks of the identity, Y^{-1} E (N solves), dY Y^{-1} E,
 // X̂ dY Y^{-1} E (L̂ solves), keeping the entries on E.
+template <class T>
 mcsdp_status phase_pmatrix(mcsdp_ctx *c, int *nlaunch) {
   const Symbolic &S = c->S;
   const int n = S.n;
   int nl = 0;
   const LsSkip none{nullptr, nullptr, 0};
+  const SolveFactors<T> f = factors_of(c, T());
+  T *W1 = reinterpret_cast<T *>(c->W1), *W2 = reinterpret_cast<T *>(c->W2);
   for (int k0 = 0; k0 < n; k0 += c->pm_cols) {
     const int nc = std::min(c->pm_cols, n - k0);
-    CUDA_TRY(c, cudaMemsetAsync(c->W1, 0, (size_t)n * c->ldw * 8, c->stream));
-    launch_rhs_unit(c->W1 + 0, c->ldw, c->pm_rowof_dev + k0, nc, c->stream);
+    CUDA_TRY(c, cudaMemsetAsync(W1, 0, (size_t)n * c->ldw * sizeof(T), c->stream));
+    launch_rhs_unit(W1, c->ldw, c->pm_rowof_dev + k0, nc, c->stream);
     LsSkip fw{c->pm_bits_dev, c->pm_tkey_dev + k0 / 32, c->bit_words};
     nl += 1;
-    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), c->lvl_fptr.data(), c->lvl_info.data(), S.height, true, c->N, c->dinvN, c->W1, c->ldw, nc, fw, c->Pw, c->stream);
-    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), c->lvl_fptr.data(), c->lvl_info.data(), S.height, false, c->N, c->dinvN, c->W1, c->ldw, nc, none, c->Pw, c->stream);
-    launch_extract_lowerE(c->D, c->W1, c->ldw, k0, nc, c->YinvE, c->stream);
-    launch_dY_times(c->D, c->dY, c->W1, c->W2, c->ldw, nc, c->stream);
+    int r[4];
+    r[0] = lsolve_c<T>(c, true, f.N, f.dinvN, W1, nc, fw);
+    r[1] = lsolve_c<T>(c, false, f.N, f.dinvN, W1, nc, none);
+    launch_extract_lowerE(c->D, (const T *)W1, c->ldw, k0, nc, c->YinvE, c->stream);
+    launch_dY_times(c->D, c->dY, (const T *)W1, W2, c->ldw, nc, c->stream);
     nl += 2;
-    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), c->lvl_fptr.data(), c->lvl_info.data(), S.height, true, c->Lh, c->dinvL, c->W2, c->ldw, nc, none, c->Pw, c->stream);
-    nl += lsolve(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), c->lvl_fptr.data(), c->lvl_info.data(), S.height, false, c->Lh, c->dinvL, c->W2, c->ldw, nc, none, c->Pw, c->stream);
-    launch_extract_lowerE(c->D, c->W2, c->ldw, k0, nc, c->Mlow, c->stream);
-    launch_extract_upperE(c->D, c->W2, c->ldw, k0, nc, c->Mup, c->stream);
+    r[2] = lsolve_c<T>(c, true, f.Lh, f.dinvL, W2, nc, none);
+    r[3] = lsolve_c<T>(c, false, f.Lh, f.dinvL, W2, nc, none);
+    launch_extract_lowerE(c->D, (const T *)W2, c->ldw, k0, nc, c->Mlow, c->stream);
+    launch_extract_upperE(c->D, (const T *)W2, c->ldw, k0, nc, c->Mup, c->stream);
     nl += 2;
+    for (int q = 0; q < 4; ++q) {
+      if (r[q] < 0) return fail(c, MCSDP_ERR_ARG, "solve shape not supported in this precision");
+      nl += r[q];
+    }
   }
   KCHECK(c);
   *nlaunch = nl;
@@ -760,12 +817,14 @@ struct IterOut {
 // Mixed form of the SCE solve B dz = g (eq. SCE): Cholesky factor of B rounded to FP32, then
 // iterative refinement with the residual g - B x formed in FP64 from the FP64 B (the scheme of
 // LAPACK's dsposv).  Measure of convergence: omega = max|r| / max(|B||x| + |g|).  Success when
-// omega <= sqrt(m) eps64; the refinement is abandoned (*solved = false, B untouched) when the
-// FP32 factorisation breaks down, when omega fails to halve in two consecutive steps while still
-// above m eps64 (the worst-case backward error of the FP64 factorisation itself), or after
-// MIXED_MAX_STEPS steps.  Leaves x in c->xs (internal order).
+// omega <= sqrt(m) eps64 (FP64-assembled B); the refinement is abandoned (*solved = false, B
+// untouched) when the FP32 factorisation breaks down, when omega fails to halve in two
+// consecutive steps while still above m eps64 (the worst-case backward error of the FP64
+// factorisation itself), or after MIXED_MAX_STEPS steps.  Leaves x in c->xs (internal order).
 constexpr int MIXED_MAX_STEPS = 10;
-mcsdp_status mixed_sce(mcsdp_ctx *c, bool *solved) {
+// b32: B was assembled in FP32 (entries accurate to about 1e-6 relative): the refinement then
+// stops at omega <= 1e-10, which already puts the solve error far below the assembly error
+mcsdp_status mixed_sce(mcsdp_ctx *c, bool b32, bool *solved) {
   const int m = c->S.m;
   *solved = false;
   CUDA_TRY(c, cudaMemsetAsync(c->status + 4, 0, sizeof(int), c->stream));
@@ -776,7 +835,8 @@ mcsdp_status mixed_sce(mcsdp_ctx *c, bool *solved) {
   }
   KCHECK(c);
   const double eps = std::ldexp(1.0, -53);
-  const double tol_ok = std::sqrt((double)m) * eps, tol_stall = (double)m * eps;
+  const double tol_ok = b32 ? 1e-10 : std::sqrt((double)m) * eps;
+  const double tol_stall = b32 ? 1e-10 : (double)m * eps;
   double prev = 1.0;
   int slow = 0;
   for (int k = 0; k < MIXED_MAX_STEPS; ++k) {
@@ -817,7 +877,10 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
   const double beta = c->opt.beta;
   const int m = c->S.m;
   cudaEventRecord(c->ev[0], c->stream);
-  mcsdp_status s = phase_scm(c);
+  // mixed form before promotion: FP32 solves and contraction from FP32 copies of the factors
+  bool f32 = c->opt.precision == 1 && !c->promoted && c->f32_solves;
+  if (f32) cast_factors(c);
+  mcsdp_status s = f32 ? phase_scm<float>(c) : phase_scm<double>(c);
   if (s) return s;
   cudaEventRecord(c->ev[1], c->stream);
   {
@@ -826,11 +889,21 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
     k0.done(1);
     bool solved = false;
     if (c->opt.precision == 1 && !c->promoted) {
-      s = mixed_sce(c, &solved);
+      s = mixed_sce(c, f32, &solved);
       if (s) return s;
       if (!solved) {
+        // promotion: from here on everything in FP64, starting with this iteration's SCM (an
+        // FP32-assembled B can be singular where the FP64 one is not)
         c->promoted = true;
         c->promoted_iter = c->cur_iter;
+        if (f32) {
+          f32 = false;
+          s = phase_scm<double>(c);
+          if (s) return s;
+          KScope k4(c, KC_MISC);
+          launch_rhs_border(c->D, c->B, c->ldb, c->hvec, beta * mu, c->stream);
+          k4.done(1);
+        }
       }
     }
     if (!solved) {
@@ -852,7 +925,7 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
     k0.done(1);
     KScope k1(c, KC_PMAT);
     int nl = 0;
-    mcsdp_status ps = phase_pmatrix(c, &nl);
+    mcsdp_status ps = f32 ? phase_pmatrix<float>(c, &nl) : phase_pmatrix<double>(c, &nl);
     if (ps) return ps;
     k1.done(nl);
     KScope k2(c, KC_MISC);
@@ -995,6 +1068,7 @@ void mcsdp_default_options(mcsdp_options *o) {
   o->profile = 0;
   o->relax = 1;
   o->solve_warps = 0;
+  o->mixed_gap = 1e-5;
 }
 
 const char *mcsdp_last_error(const mcsdp_ctx *c) { return c ? c->err.c_str() : "null context"; }
@@ -1093,6 +1167,8 @@ mcsdp_status mcsdp_create(const mcsdp_problem *p, const mcsdp_options *opt, void
     }
     CUDA_TRY(c, cudaEventCreateWithFlags(&c->cs.fork, cudaEventDisableTiming));
     CUDA_TRY(c, cudaEventCreateWithFlags(&c->cs.chain_done, cudaEventDisableTiming));
+    CUDA_TRY(c, cudaEventCreateWithFlags(&c->cs.entry, cudaEventDisableTiming));
+    CUDA_TRY(c, cudaEventCreateWithFlags(&c->cs.exit, cudaEventDisableTiming));
     c->cs.chain = c->st1;
     c->cs.rest = c->st2;
   }
@@ -1117,8 +1193,11 @@ void mcsdp_destroy(mcsdp_ctx *c) {
     }
     if (c->st2) cudaStreamDestroy(c->st2);
     if (c->st1) cudaStreamDestroy(c->st1);
+    chol_graphs_destroy(&c->cs);
     if (c->cs.fork) cudaEventDestroy(c->cs.fork);
     if (c->cs.chain_done) cudaEventDestroy(c->cs.chain_done);
+    if (c->cs.entry) cudaEventDestroy(c->cs.entry);
+    if (c->cs.exit) cudaEventDestroy(c->cs.exit);
   }
   delete c;
 }
@@ -1231,7 +1310,14 @@ mcsdp_status mcsdp_scm_assemble(mcsdp_ctx *c, const double *Xbar, const double *
   if (s) return s;
   s = factor_X(c, Xbar);
   if (s) return s;
-  s = phase_scm(c);
+  if (precision == 1 && !(c->opt.precision == 1 && c->f32_solves))
+    return fail(c, MCSDP_ERR_ARG, "precision 1 needs a context created with precision 1");
+  if (precision == 1) {
+    cast_factors(c);
+    s = phase_scm<float>(c);
+  } else {
+    s = phase_scm<double>(c);
+  }
   if (s) return s;
   KScope ks(c, KC_MISC);
   launch_B_to_user(c->D, c->B, c->ldb, Bout, ldb, c->hvec, h, c->stream);
@@ -1302,10 +1388,12 @@ mcsdp_status mcsdp_solve(mcsdp_ctx *c, mcsdp_result *res) {
     const double mu = sc[0] / n, pobj = sc[1], dobj = sc[2];
     const double gap = std::fabs(pobj - dobj) / std::max(1.0, (std::fabs(pobj) + std::fabs(dobj)) / 2);
     const double pinf = sc[3] / std::max(1.0, sc[4]);
-    // mixed form: promote to the FP64 factor if the primal residual grows (it contracts by
+    // mixed form: FP64 throughout once the gap is small, or if the primal residual grows well
+    // above the level the FP32 solves leave (about 1e-6 relative; it contracts by
     // (1 - gamma alpha_p) per iteration in exact arithmetic)
-    if (c->opt.precision == 1 && !c->promoted && prev_pinf > 0 && pinf > 2.0 * prev_pinf &&
-        pinf > 1e-12) {
+    if (c->opt.precision == 1 && !c->promoted &&
+        ((prev_pinf > 0 && pinf > 2.0 * prev_pinf && pinf > 1e-4) ||
+         gap < (c->opt.mixed_gap > 0 ? c->opt.mixed_gap : 1e-5))) {
       c->promoted = true;
       c->promoted_iter = it;
     }
