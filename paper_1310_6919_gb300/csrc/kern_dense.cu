@@ -480,10 +480,14 @@ __global__ void __cluster_dims__(BCL, 1, 1) __launch_bounds__(BTH)
     }
     if (kb % BCL == rank) {
       if (tid < nb) {
-        const double *Li = Linv + (int64_t)kb * NB * NB;
-        double a = 0.0;
-        for (int l = tid; l < nb; ++l) a = fma(Li[l + tid * NB], yv[b0 + l], a);
-        tb[tid] = a;
+        const double *Li = Linv + (int64_t)kb * NB * NB;  // zero above the diagonal
+        double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+        for (int l = 0; l < NB; l += 2) {
+          a0 = fma(Li[l + tid * NB], l < nb ? yv[b0 + l] : 0.0, a0);
+          a1 = fma(Li[l + 1 + tid * NB], l + 1 < nb ? yv[b0 + l + 1] : 0.0, a1);
+        }
+        tb[tid] = a0 + a1;
       }
       __syncthreads();
       if (tid < NB) {
@@ -666,9 +670,10 @@ __global__ void __cluster_dims__(RCL, 1, 1) __launch_bounds__(RTH)
     }
     if (kb % RCL == rank) {
       if (tid < nb) {
-        const float *Li = Linv + (int64_t)kb * NB * NB;
+        const float *Li = Linv + (int64_t)kb * NB * NB;  // zero above the diagonal
         float a = 0.f;
-        for (int l = 0; l <= tid; ++l) a = fmaf(Li[tid + l * NB], ys[b0 + l], a);
+#pragma unroll
+        for (int l = 0; l < NB; ++l) a = fmaf(Li[tid + l * NB], l < nb ? ys[b0 + l] : 0.f, a);
         tb[tid] = a;
       }
       __syncthreads();
@@ -708,9 +713,10 @@ __global__ void __cluster_dims__(RCL, 1, 1) __launch_bounds__(RTH)
     }
     if (kb % RCL == rank) {
       if (tid < nb) {
-        const float *Li = Linv + (int64_t)kb * NB * NB;
+        const float *Li = Linv + (int64_t)kb * NB * NB;  // zero above the diagonal
         float a = 0.f;
-        for (int l = tid; l < nb; ++l) a = fmaf(Li[l + tid * NB], ys[b0 + l], a);
+#pragma unroll
+        for (int l = 0; l < NB; ++l) a = fmaf(Li[l + tid * NB], l < nb ? ys[b0 + l] : 0.f, a);
         tb[tid] = a;
       }
       __syncthreads();

@@ -216,7 +216,7 @@ __global__ void k_ychol(DevSym S, int lvl_begin, const double *__restrict__ alph
   const int c = blockIdx.y;
   if (cta_flag_set(&status[c], ST_NOT_PD)) return;
   double *N = Nbuf + (int64_t)c * S.nnzL;
-  double *Dc = Dbuf + (int64_t)c * S.nnzD;
+  double *Dc = Dbuf ? Dbuf + (int64_t)c * S.nnzD : nullptr;
   const double a = alpha ? alpha[c] : 0.0;
   const int64_t r0 = S.sn_rowptr[t];
   const int nrow = (int)(S.sn_rowptr[t + 1] - r0);
@@ -236,6 +236,7 @@ __global__ void k_ychol(DevSym S, int lvl_begin, const double *__restrict__ alph
   double *scr = Dsm + ncol * ncol;
   chol_panel_smem(F, nrow, ncol, &status[c], ST_NOT_PD, scr);
   for (int i = tid; i < sz; i += bd) N[v0 + i] = F[i];
+  if (!Dbuf) return;  // step-length candidates: only the success of the factorisation matters
   tri_inverse_smem(F, nrow, ncol, Dsm, scr);
   const int64_t d0 = S.sn_dptr[t];
   for (int i = tid; i < ncol * ncol; i += bd) Dc[d0 + i] = Dsm[i];

@@ -93,7 +93,7 @@ struct mcsdp_ctx {
   double *Xbar = nullptr, *z = nullptr, *Ylay = nullptr, *N = nullptr, *dinvN = nullptr;
   double *Lh = nullptr, *dinvL = nullptr, *dY = nullptr, *dX = nullptr, *YinvE = nullptr;
   double *Mlow = nullptr, *Mup = nullptr, *B = nullptr, *hvec = nullptr, *xs = nullptr;
-  double *dz = nullptr, *W1 = nullptr, *W2 = nullptr, *Ncand = nullptr, *dinvCand = nullptr;
+  double *dz = nullptr, *W1 = nullptr, *W2 = nullptr, *Ncand = nullptr;
   double *Pw = nullptr, *Pf = nullptr, *Binv = nullptr;
   // mixed form: FP32 factor of B, FP64 refinement vectors
   float *B32 = nullptr, *Linv32 = nullptr;
@@ -483,7 +483,6 @@ void plan_workspace(mcsdp_ctx *c) {
   plan_buf(c, cur, "Pw", (size_t)std::max<int64_t>(1, c->nslotw) * c->ldw * 8);
   plan_buf(c, cur, "Pf", (size_t)std::max<int64_t>(1, c->nslotf) * NCAND * 8);
   plan_buf(c, cur, "Ncand", (size_t)NCAND * nnzL * 8);
-  plan_buf(c, cur, "dinvCand", (size_t)NCAND * nnzD * 8);
   plan_buf(c, cur, "alpha_c", NCAND * 8);
   plan_buf(c, cur, "alpha_r", (size_t)S.ns * 8);
   plan_buf(c, cur, "scal", 16 * 8);
@@ -611,7 +610,6 @@ void bind_pointers(mcsdp_ctx *c) {
   D.nslotw = c->nslotw;
   D.nslotf = c->nslotf;
   c->Ncand = wsp<double>(c, "Ncand");
-  c->dinvCand = wsp<double>(c, "dinvCand");
   c->alpha_c = wsp<double>(c, "alpha_c");
   c->alpha_r = wsp<double>(c, "alpha_r");
   c->scal = wsp<double>(c, "scal");
@@ -962,7 +960,7 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
     }
     CUDA_TRY(c, cudaMemcpyAsync(c->alpha_c, cand, NCAND * 8, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->status + 8, 0, NCAND * sizeof(int), c->stream));
-    s = phase_ychol(c, NCAND, c->alpha_c, c->Ylay, c->dY, c->Ncand, c->dinvCand, c->status + 8);
+    s = phase_ychol(c, NCAND, c->alpha_c, c->Ylay, c->dY, c->Ncand, nullptr, c->status + 8);
     if (s) return s;
     int cs[NCAND];
     CUDA_TRY(c, cudaMemcpyAsync(cs, c->status + 8, NCAND * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
