@@ -119,10 +119,12 @@ __global__ void k_scm_tiles(DevSym S, const int2 *__restrict__ tiles,
   }
 }
 
-size_t scm_tiles_smem_bytes(const DevSym &S, int pmax) {
+// es: element size (8 for the FP64 form; the FP32 form needs about half, so two CTAs fit an SM)
+size_t scm_tiles_smem_bytes(const DevSym &S, int pmax, int es) {
   const size_t xw = std::max<size_t>(XW_CAP, (size_t)S.max_con_nnz * pmax);
-  return (size_t)2 * pmax * pmax * 8 + (size_t)2 * S.max_grp_nnz * (8 + 8) + 64 + xw * 8;
+  return (size_t)2 * pmax * pmax * es + (size_t)2 * S.max_grp_nnz * (es + 8) + 64 + xw * es;
 }
+size_t scm_tiles_smem_bytes(const DevSym &S, int pmax) { return scm_tiles_smem_bytes(S, pmax, 8); }
 
 template <class T>
 void launch_scm_tiles(const DevSym &S, const int2 *tiles, int ntiles, const T *WX,
@@ -131,7 +133,7 @@ void launch_scm_tiles(const DevSym &S, const int2 *tiles, int ntiles, const T *W
   if (ntiles <= 0) return;
   // two |P_h| x |P_g| blocks, the nonzero lists of two groups, and the X̂-times-A_j products of
   // one batch of constraints (XW_CAP doubles, or one constraint's if larger) in shared memory
-  const size_t smem = scm_tiles_smem_bytes(S, pmax);
+  const size_t smem = scm_tiles_smem_bytes(S, pmax, (int)sizeof(T));
   static size_t configured = 0;
   if (smem > configured) {
     cudaFuncSetAttribute(k_scm_tiles<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -67,6 +67,7 @@ struct mcsdp_ctx {
   std::vector<uint32_t> reach_bits, need_bits;  // per group, one bit per supernode
   std::vector<int2> pm_tkey;        // per P-MATRIX tile of 32 columns: (tile, tile)
   std::vector<uint32_t> pm_bits;    // per P-MATRIX tile: supernodes on its columns' paths
+  std::vector<uint32_t> pm_need;    // per P-MATRIX tile: supernodes the backward L̂ solve needs
   std::vector<int> pm_rowof;        // P-MATRIX right-hand side j -> row j (identity)
   // update-list chunks (see DevSym)
   std::vector<int> upd_c0end, xch_beg, xch_end, xch_t, xch_ub, xch_ue, lvl_xptr, xfst, lvl_fptr;
@@ -106,6 +107,7 @@ struct mcsdp_ctx {
   int *status = nullptr, *rowof_dev = nullptr, *goff_dev = nullptr, *pm_rowof_dev = nullptr;
   int2 *tiles_dev = nullptr, *tkey_dev = nullptr, *pm_tkey_dev = nullptr;
   uint32_t *reach_bits_dev = nullptr, *need_bits_dev = nullptr, *pm_bits_dev = nullptr;
+  uint32_t *pm_need_dev = nullptr;
   // kernel statistics
   int64_t launches = 0;
   int64_t kcount[16] = {};
@@ -436,6 +438,24 @@ void plan_workspace(mcsdp_ctx *c) {
     c->pm_cols = std::min(pmc, (n + 31) / 32 * 32);
     const int ntile = (n + 31) / 32;
     c->pm_bits.assign((size_t)ntile * words, 0u);
+    // M = X̂ dY Y^{-1} is kept only on E: column k needs the rows i >= k of k's clique and the
+    // rows i < k with (k, i) in E; the backward substitution for a row needs its supernode and
+    // all that supernode's ancestors
+    c->pm_need.assign((size_t)ntile * words, 0u);
+    auto mark_path = [&](int tl, int s2) {
+      for (; s2 >= 0; s2 = S.sn_parent[s2]) {
+        uint32_t &wd = c->pm_need[(size_t)tl * words + (s2 >> 5)];
+        if (wd & (1u << (s2 & 31))) break;
+        wd |= 1u << (s2 & 31);
+      }
+    };
+    for (int tl = 0; tl < ntile; ++tl)
+      for (int k = tl * 32; k < std::min(n, tl * 32 + 32); ++k) {
+        const int t = S.col2sn[k];
+        for (int64_t p = S.sn_rowptr[t]; p < S.sn_rowptr[t + 1]; ++p)
+          mark_path(tl, S.col2sn[S.rows[p]]);
+        for (int q = S.rs_ptr[k]; q < S.rs_ptr[k + 1]; ++q) mark_path(tl, S.col2sn[S.rs_col[q]]);
+      }
     c->pm_tkey.resize(ntile);
     for (int tl = 0; tl < ntile; ++tl) {
       c->pm_tkey[tl] = make_int2(tl, tl);
@@ -457,6 +477,7 @@ void plan_workspace(mcsdp_ctx *c) {
   plan_table(c, cur, "reach_bits", c->reach_bits);
   plan_table(c, cur, "need_bits", c->need_bits);
   plan_table(c, cur, "pm_bits", c->pm_bits);
+  plan_table(c, cur, "pm_need", c->pm_need);
   plan_table(c, cur, "pm_tkey", c->pm_tkey);
   plan_table(c, cur, "pm_rowof", c->pm_rowof);
   // iteration buffers
@@ -633,6 +654,7 @@ void bind_pointers(mcsdp_ctx *c) {
   c->reach_bits_dev = wsp<uint32_t>(c, "reach_bits");
   c->need_bits_dev = wsp<uint32_t>(c, "need_bits");
   c->pm_bits_dev = wsp<uint32_t>(c, "pm_bits");
+  c->pm_need_dev = wsp<uint32_t>(c, "pm_need");
   c->pm_tkey_dev = wsp<int2>(c, "pm_tkey");
   c->pm_rowof_dev = wsp<int>(c, "pm_rowof");
 }
@@ -786,6 +808,7 @@ mcsdp_status phase_pmatrix(mcsdp_ctx *c, int *nlaunch) {
     CUDA_TRY(c, cudaMemsetAsync(W1, 0, (size_t)n * c->ldw * sizeof(T), c->stream));
     launch_rhs_unit(W1, c->ldw, c->pm_rowof_dev + k0, nc, c->stream);
     LsSkip fw{c->pm_bits_dev, c->pm_tkey_dev + k0 / 32, c->bit_words};
+    LsSkip bwL{c->pm_need_dev, c->pm_tkey_dev + k0 / 32, c->bit_words};
     nl += 1;
     int r[4];
     r[0] = lsolve_c<T>(c, true, f.N, f.dinvN, W1, nc, fw);
@@ -794,7 +817,7 @@ mcsdp_status phase_pmatrix(mcsdp_ctx *c, int *nlaunch) {
     launch_dY_times(c->D, c->dY, (const T *)W1, W2, c->ldw, nc, c->stream);
     nl += 2;
     r[2] = lsolve_c<T>(c, true, f.Lh, f.dinvL, W2, nc, none);
-    r[3] = lsolve_c<T>(c, false, f.Lh, f.dinvL, W2, nc, none);
+    r[3] = lsolve_c<T>(c, false, f.Lh, f.dinvL, W2, nc, bwL);
     launch_extract_lowerE(c->D, (const T *)W2, c->ldw, k0, nc, c->Mlow, c->stream);
     launch_extract_upperE(c->D, (const T *)W2, c->ldw, k0, nc, c->Mup, c->stream);
     nl += 2;
