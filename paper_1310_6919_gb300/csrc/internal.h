@@ -22,6 +22,26 @@ struct LsLevel {
   int nc, nr, cw, np;
 };
 
+// Reciprocal for the pivots of the serial column loops: an FP32 reciprocal of the rounded value
+// refined by two Newton-Raphson steps r <- r + r (1 - d r) in FP64 (each squares the relative
+// error: 2^-23 -> 2^-46 -> below half an ulp before the final rounding), four dependent FP64
+// operations instead of a full division.  Outside the FP32 range the plain division is used.
+template <class T>
+__device__ __forceinline__ T pivot_rcp(T d);
+template <>
+__device__ __forceinline__ double pivot_rcp<double>(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / d;
+  double r = (double)__frcp_rn((float)d);
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
+template <>
+__device__ __forceinline__ float pivot_rcp<float>(float d) {
+  return __frcp_rn(d);
+}
+
 // Device copies of the symbolic tables (all pointers into the caller's workspace).
 struct DevSym {
   int n, m, ns, ngroup, max_nrow, max_ncol;

@@ -19,26 +19,6 @@ namespace mcsdp {
 constexpr int NB = 32;  // panel width (FP64 on one SM is slow: a narrow panel keeps the
                         // serial factor-and-invert step short)
 
-// Reciprocal for the pivots of the serial column loops: an FP32 reciprocal of the rounded value
-// refined by two Newton-Raphson steps r <- r + r (1 - d r) in FP64 (each squares the relative
-// error: 2^-23 -> 2^-46 -> below half an ulp before the final rounding), four dependent FP64
-// operations instead of a full division.  Outside the FP32 range the plain division is used.
-template <class T>
-__device__ __forceinline__ T pivot_rcp(T d);
-template <>
-__device__ __forceinline__ double pivot_rcp<double>(double d) {
-  if (!(d > 1e-30 && d < 1e30)) return 1.0 / d;
-  double r = (double)__frcp_rn((float)d);
-  double e = fma(-d, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-d, r, 1.0);
-  return fma(r, e, r);
-}
-template <>
-__device__ __forceinline__ float pivot_rcp<float>(float d) {
-  return __frcp_rn(d);
-}
-
 // Cholesky of the nb x nb diagonal block at (k0, k0), one CTA of 256 threads, and the inverse
 // of the factor (stored in Linv, nb x nb column-major, ld NB).  The serial column loop is the
 // critical path of the whole factorisation, so it is warp-specialised with one barrier per

@@ -49,50 +49,83 @@ void launch_slot_combine(const DevSym &S, double *out, const double *vec, double
 // ---------------------------------------------------------------------------------------------
 // dense Cholesky of an nrow x ncol column-major panel in shared memory (lower, in place):
 // the leading ncol x ncol block is factored, the rows below are solved against it.  The serial
-// column loop carries one reciprocal per column and two barriers: warp 0 takes the pivot d_j,
-// its reciprocal and the scaled column u = F[:, j] / d_j (kept aside, so column j stays
-// unscaled while the trailing update reads it) and writes the previous column's u back; all
-// threads then update the trailing part.  This is F = U D U^T with U unit lower; the square
-// roots of D are taken in parallel at the end (L = U D^{1/2}).  scr: 2 * nrow + ncol doubles.
+// column loop is warp-specialised with one barrier per column: at step j, warp 0 writes the
+// finished column j-1 back, brings column j+1 up to date, takes its pivot d_{j+1}, the
+// reciprocal (FP32 seed and two Newton steps) and the scaled column u_{j+1} = F[:, j+1] / d_{j+1}
+// (kept aside, so the column stays unscaled while the others read it); the other warps apply
+// step j to the columns >= j+2.  This is F = U D U^T with U unit lower; the square roots of D
+// are taken in parallel at the end (L = U D^{1/2}).  Needs >= 2 warps.
+// scr: 2 * nrow + ncol doubles.
 __device__ void chol_panel_smem(double *F, int nrow, int ncol, int *status_word, int flag,
                                 double *scr) {
   double *uc = scr, *dv = scr + 2 * nrow;
-  const int tid = threadIdx.x, bd = blockDim.x;
-  for (int j = 0; j < ncol; ++j) {
-    double *u = uc + (j & 1) * nrow;
-    if (tid < 32) {
-      double rj = 0.0;
-      if (tid == 0) {
-        double d = F[j + (int64_t)j * nrow];
-        if (!(d > 0.0)) {
-          atomicOr(status_word, flag);
-          d = 1.0;
-        }
-        dv[j] = d;
-        rj = 1.0 / d;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nth = blockDim.x - 32;
+  bool bad = false;
+  if (warp == 0 && ncol > 0) {  // column 0: pivot, reciprocal, scaled column
+    double r0 = 0.0;
+    if (lane == 0) {
+      double d = F[0];
+      if (!(d > 0.0)) {
+        bad = true;
+        d = 1.0;
       }
-      rj = __shfl_sync(0xffffffffu, rj, 0);
-      for (int i = j + 1 + tid; i < nrow; i += 32) u[i] = F[i + (int64_t)j * nrow] * rj;
-      if (j > 0) {
-        const double *up = uc + ((j - 1) & 1) * nrow;
-        for (int i = j + tid; i < nrow; i += 32) F[i + (int64_t)(j - 1) * nrow] = up[i];
-      }
+      dv[0] = d;
+      r0 = pivot_rcp<double>(d);
     }
-    __syncthreads();
-    const int w = ncol - j - 1, hgt = nrow - j - 1;
-    for (int idx = tid; idx < w * hgt; idx += bd) {
-      const int kk = j + 1 + idx / hgt, ii = j + 1 + idx % hgt;
-      if (ii >= kk) F[ii + (int64_t)kk * nrow] -= u[ii] * F[kk + (int64_t)j * nrow];
-    }
-    __syncthreads();
+    r0 = __shfl_sync(0xffffffffu, r0, 0);
+    for (int i = 1 + lane; i < nrow; i += 32) uc[i] = F[i] * r0;
   }
-  if (ncol > 0) {
-    const double *up = uc + ((ncol - 1) & 1) * nrow;
-    for (int i = ncol + tid; i < nrow; i += bd) F[i + (int64_t)(ncol - 1) * nrow] = up[i];
-  }
-  for (int j = tid; j < ncol; j += bd) dv[j] = sqrt(dv[j]);
   __syncthreads();
-  for (int idx = tid; idx < nrow * ncol; idx += bd) {
+  for (int j = 0; j < ncol; ++j) {
+    const double *u = uc + (j & 1) * nrow;  // u_j
+    if (warp == 0) {
+      if (j >= 1) {  // column j-1 is no longer read: store u_{j-1} (rows > j-1)
+        const double *up = uc + ((j - 1) & 1) * nrow;
+        for (int i = j + lane; i < nrow; i += 32) F[i + (int64_t)(j - 1) * nrow] = up[i];
+      }
+      __syncwarp();
+      if (j + 1 < ncol) {
+        double *un = uc + ((j + 1) & 1) * nrow;
+        const double fj = F[(j + 1) + (int64_t)j * nrow];
+        double a0 = 0.0;
+        for (int i = j + 1 + lane; i < nrow; i += 32) {
+          const double a = F[i + (int64_t)(j + 1) * nrow] - u[i] * fj;
+          F[i + (int64_t)(j + 1) * nrow] = a;
+          if (i == j + 1) a0 = a;
+        }
+        double rj = 0.0;
+        if (lane == 0) {
+          double d = a0;
+          if (!(d > 0.0)) {
+            bad = true;
+            d = 1.0;
+          }
+          dv[j + 1] = d;
+          rj = pivot_rcp<double>(d);
+        }
+        rj = __shfl_sync(0xffffffffu, rj, 0);
+        __syncwarp();
+        for (int i = j + 2 + lane; i < nrow; i += 32) un[i] = F[i + (int64_t)(j + 1) * nrow] * rj;
+      }
+    } else {
+      // step j on the columns >= j+2 (rows >= column); column j is only read
+      const int w = ncol - j - 2, hgt = nrow - j - 2;
+      const int nwork = (w > 0 && hgt > 0) ? w * hgt : 0;
+      for (int idx = tid - 32; idx < nwork; idx += nth) {
+        const int kk = j + 2 + idx / hgt, ii = j + 2 + idx % hgt;
+        if (ii >= kk) F[ii + (int64_t)kk * nrow] -= u[ii] * F[kk + (int64_t)j * nrow];
+      }
+    }
+    __syncthreads();
+  }
+  if (bad) atomicOr(status_word, flag);
+  if (ncol > 0 && warp == 0) {
+    const double *up = uc + ((ncol - 1) & 1) * nrow;
+    for (int i = ncol + lane; i < nrow; i += 32) F[i + (int64_t)(ncol - 1) * nrow] = up[i];
+  }
+  for (int j = tid; j < ncol; j += blockDim.x) dv[j] = sqrt(dv[j]);
+  __syncthreads();
+  for (int idx = tid; idx < nrow * ncol; idx += blockDim.x) {
     const int i = idx % nrow, j = idx / nrow;
     if (i > j) F[i + (int64_t)j * nrow] *= dv[j];
     else if (i == j) F[i + (int64_t)j * nrow] = dv[j];
