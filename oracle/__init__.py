@@ -14,6 +14,8 @@ Modules
   pdipm       dense HKM primal-dual interior-point method (Sec. 2.2, Steps 0-4) and the
               matrix-completion Newton step at a given iterate
   maxcut      closed forms and brute force used as pins
+  diff        central-path point at fixed mu (Newton centring) and its implicit derivatives
+              with respect to b, A_0 and A_k (the differentiation row; not in the paper)
 
 Parity status: every function above is pinned by tests in tests/test_oracle_*.py against closed
 forms, invariants or brute force (see each function's docstring for its pin).

@@ -1,0 +1,82 @@
+"""Test infrastructure (oracle): implicit differentiation of the central-path point.
+
+Not in the paper (the differentiation row of the build plan).  The point differentiated is the
+central-path point for a fixed mu > 0 of (P)/(D) (Sec. 1, Sec. 2.2):
+
+    A(X) = b,   Y = A_0 - sum_k z_k A_k,   X Y = mu I,
+
+i.e. X = mu Y^{-1} with z the root of F(z) = A(mu Y(z)^{-1}) - b.  F'(z) is the Schur complement
+matrix at X = mu Y^{-1} (B_pq = A_p . (X A_q Y^{-1}), eq. newSCM), so Newton's method on z is the
+centring step of the method.  For a loss  l = <G, X> + g_z^T z  (G symmetric) the adjoint is
+
+    R   = sym(X G Y^{-1}),   v = B^{-1} (A(R) + g_z),
+    g_b = v,   g_{A_0} = sym(X (A^*(v) - G) Y^{-1}),   g_{A_k} = -z_k g_{A_0} - v_k X,
+
+(sym(M) = (M + M^T)/2, A^*(v) = sum_k v_k A_k), obtained by differentiating F(z; b, A_0, A_k) = 0
+and X = mu Y^{-1}.  Plain dense FP64, slow, for small instances.
+"""
+import numpy as np
+
+from .scm import scm_dense
+from .sdp import dual_slack
+
+
+def _sym(M):
+    return 0.5 * (M + M.T)
+
+
+def central_point(A, b, mu, z0, tol=1e-13, max_newton=60):
+    """Newton on F(z) = A(mu Y(z)^{-1}) - b from a dual-feasible z0, halving the step until
+    Y stays positive definite.  Returns z, Y, X = mu Y^{-1}."""
+    z = np.array(z0, dtype=np.float64)
+    scale = max(1.0, float(np.max(np.abs(b))))
+    for _ in range(max_newton):
+        Y = dual_slack(A, z)
+        Yinv = np.linalg.inv(Y)
+        Yinv = _sym(Yinv)
+        X = mu * Yinv
+        F = A.op(X) - b
+        if np.max(np.abs(F)) <= tol * scale:
+            return z, Y, X
+        Bm = scm_dense(A, X, Yinv)
+        dz = np.linalg.solve(Bm, -F)
+        t = 1.0
+        while True:
+            try:
+                np.linalg.cholesky(dual_slack(A, z + t * dz))
+                break
+            except np.linalg.LinAlgError:
+                t *= 0.5
+                if t < 1e-12:
+                    raise RuntimeError("centring step collapsed")
+        z = z + t * dz
+    raise RuntimeError("centring did not converge")
+
+
+def backward(A, z, Y, X, G, gz):
+    """Gradients of l = <G, X> + gz^T z at the central point (z, Y, X): returns (g_b, g_{A_0},
+    g_A) with g_A[k-1] the dense gradient with respect to A_k (symmetric matrices; the gradient
+    with respect to a stored off-diagonal entry that also sets its mirror is twice the entry)."""
+    Yinv = _sym(np.linalg.inv(Y))
+    R = _sym(X @ G @ Yinv)
+    Bm = scm_dense(A, X, Yinv)
+    v = np.linalg.solve(Bm, A.op(R) + gz)
+    gA0 = _sym(X @ (A.adjoint(v) - G) @ Yinv)
+    gA = [-z[k] * gA0 - v[k] * X for k in range(A.m)]
+    return v, gA0, gA
+
+
+def entry_gradients(A_inst, z, v, gA0, X):
+    """Per stored entry (mat, row, col) of the input (row <= col): d l / d val."""
+    out = np.empty(len(A_inst.val))
+    for e, (k, i, j) in enumerate(zip(A_inst.mat, A_inst.row, A_inst.col)):
+        f = 1.0 if i == j else 2.0
+        g = gA0[i, j] if k == 0 else (-z[k - 1] * gA0[i, j] - v[k - 1] * X[i, j])
+        out[e] = f * g
+    return out
+
+
+def loss(A, b, mu, z0, G, gz):
+    """l at the central point for (A, b, mu), started from z0."""
+    z, Y, X = central_point(A, b, mu, z0)
+    return float(np.sum(G * X) + gz @ z)
