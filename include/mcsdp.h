@@ -221,8 +221,20 @@ mcsdp_status mcsdp_stats_reset(mcsdp_ctx *ctx);
 mcsdp_status mcsdp_sce_solve_noalloc(const double *B_dev, int64_t ldb, const double *g_dev,
                                      double *x_dev, int32_t m, void *cuda_stream);
 
-/* Differentiation of the solution (implicit differentiation of the central-path KKT system).
- * Not implemented: returns MCSDP_ERR_STATE. */
+/* Differentiation of the solution (not in the paper).  The point differentiated is the
+ * central-path point for mu = X̄.Y/n of the context's iterate: the iterate is first re-centred
+ * (Newton on z for A(mu Y(z)^{-1}) = b with Y(z) = A_0 - sum z_k A_k, to a residual of 1e-13
+ * relative; the context's iterate becomes that point, X̄ = mu Y^{-1} on E).  For the loss
+ * l = sum over layout entries gX . X̄ + gz^T z, implicit differentiation of A(X) = b,
+ * X = mu Y^{-1} gives, with R = sym(X̂ G Y^{-1}) (G the symmetric matrix of the weights gX),
+ * v = B^{-1}(A(R) + gz) (B the SCM at the point), g_{A_0} = sym(X̂ (A^*(v) - G) Y^{-1}):
+ *   gb[m]   dl/db (the c vector of the input), = v
+ *   gC[n0]  dl/d value of every input entry of matrix 0, in input order
+ *   gA[n1]  dl/d value of every input entry of matrices 1..m, in input order (-z_k g_{A_0} -
+ *           v_k X̄ at the entry)
+ * (an off-diagonal entry stands for both triangles, so its gradient counts twice; form 0 flips
+ * the sign for matrix 0).  gX (nnz_layout) and gz (m) may be NULL (zero weights); any output may
+ * be NULL.  Device pointers, FP64.  Status MCSDP_ERR_STALL if the centring fails. */
 mcsdp_status mcsdp_backward(mcsdp_ctx *ctx, const double *gX_layout_dev, const double *gz_dev,
                             double *gC_dev, double *gb_dev, double *gA_dev);
 

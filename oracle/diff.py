@@ -25,19 +25,24 @@ def _sym(M):
     return 0.5 * (M + M.T)
 
 
-def central_point(A, b, mu, z0, tol=1e-13, max_newton=60):
+def central_point(A, b, mu, z0, tol=1e-13, floor=1e-9, max_newton=60):
     """Newton on F(z) = A(mu Y(z)^{-1}) - b from a dual-feasible z0, halving the step until
-    Y stays positive definite.  Returns z, Y, X = mu Y^{-1}."""
+    Y stays positive definite, until max|F| <= tol max(1, max|b|), or until a step no longer
+    halves the residual once it is below floor (the rounding level of evaluating F).
+    Returns z, Y, X = mu Y^{-1}."""
     z = np.array(z0, dtype=np.float64)
     scale = max(1.0, float(np.max(np.abs(b))))
+    prev = None
     for _ in range(max_newton):
         Y = dual_slack(A, z)
         Yinv = np.linalg.inv(Y)
         Yinv = _sym(Yinv)
         X = mu * Yinv
         F = A.op(X) - b
-        if np.max(np.abs(F)) <= tol * scale:
+        res = np.max(np.abs(F)) / scale
+        if res <= tol or (prev is not None and res > 0.5 * prev and res <= floor):
             return z, Y, X
+        prev = res
         Bm = scm_dense(A, X, Yinv)
         dz = np.linalg.solve(Bm, -F)
         t = 1.0

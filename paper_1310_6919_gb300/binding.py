@@ -154,6 +154,28 @@ class Problem:
             self._check(st)
         return out
 
+    def backward(self, gX_layout=None, gz=None):
+        """Gradients of l = gX . X̄ (layout) + gz . z at the re-centred central-path point for the
+        iterate's mu (mcsdp_backward).  Returns gb (m), gC (entries of matrix 0, input order),
+        gA (entries of matrices 1..m, input order) and g_entries (all input entries, input
+        order)."""
+        n0 = int(np.count_nonzero(self._mat == 0))
+        n1 = len(self._mat) - n0
+        gX = None if gX_layout is None else self._dev(gX_layout, self.info["nnz_layout"])
+        gzz = None if gz is None else self._dev(gz, self.m)
+        gb = torch.zeros(self.m, dtype=torch.float64, device=self.torch_device)
+        gC = torch.zeros(max(n0, 1), dtype=torch.float64, device=self.torch_device)
+        gA = torch.zeros(max(n1, 1), dtype=torch.float64, device=self.torch_device)
+        self._check(self._L.mcsdp_backward(self._ctx, _ptr(gX), _ptr(gzz), _ptr(gC), _ptr(gb),
+                                           _ptr(gA)))
+        gC, gA = gC[:n0], gA[:n1]
+        ge = torch.zeros(len(self._mat), dtype=torch.float64, device=self.torch_device)
+        sel0 = torch.from_numpy(np.nonzero(self._mat == 0)[0]).to(self.torch_device)
+        sel1 = torch.from_numpy(np.nonzero(self._mat != 0)[0]).to(self.torch_device)
+        ge[sel0] = gC
+        ge[sel1] = gA
+        return {"gb": gb, "gC": gC, "gA": gA, "g_entries": ge}
+
     def scm_assemble(self, Xbar_layout, z, out=None, precision=0):
         X = self._dev(Xbar_layout, self.info["nnz_layout"])
         zz = self._dev(z, self.m)

@@ -161,6 +161,22 @@ void launch_extract_upperE(const DevSym &S, const T *W, int64_t ldw, int k0, int
 template <class T>
 void launch_dY_times(const DevSym &S, const double *dY, const T *Wy, T *Ww, int64_t ldw, int nc,
                      cudaStream_t st);
+// differentiation (mcsdp_backward): Wout = D Win for D symmetric on lower(E) (layout);
+// the symmetric matrix standing for layout weights; axpy; sym(M) on E; A(M) (+ add); the SCE border
+// from a caller-order vector; per-entry gradients
+void launch_E_times(const DevSym &S, const double *D, const double *Win, double *Wout, int64_t ldw,
+                    int nc, cudaStream_t st);
+void launch_layout_sym(const DevSym &S, const double *g, double *out, cudaStream_t st);
+void launch_axpy(int64_t n, double a, const double *x, double *y, cudaStream_t st);
+void launch_sym_combine(const DevSym &S, const double *Mlow, const double *Mup, double *out,
+                        cudaStream_t st);
+void launch_con_apply(const DevSym &S, const double *M, const double *add, double *out,
+                      cudaStream_t st);
+void launch_border_from_user(const DevSym &S, double *B, int64_t ldb, const double *rhs,
+                             cudaStream_t st);
+void launch_entry_grads(int64_t nnz, const int64_t *off, const int *k, const int *pos,
+                        const double *f, const double *gA0, const double *X, const double *z,
+                        const double *v, double *gC, double *gA, cudaStream_t st);
 // out = (float) in, n entries (FP32 copies of the factors for the mixed form's solves)
 void launch_cast_f32(const double *in, float *out, int64_t n, cudaStream_t st);
 void launch_dx_combine(const DevSym &S, double betamu, const double *Xbar, const double *YinvE,

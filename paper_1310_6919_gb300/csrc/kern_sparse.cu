@@ -7,6 +7,8 @@
 //   K8  scalars and update
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.h"
 #include "warp_solve.cuh"
 
@@ -768,6 +770,135 @@ __global__ void k_set_identity(DevSym S, double *X) {
 
 void launch_set_identity(const DevSym &S, double *X, cudaStream_t st) {
   k_set_identity<<<(S.n + 255) / 256, 256, 0, st>>>(S, X);
+}
+
+}  // namespace mcsdp
+
+namespace mcsdp {
+
+// ---------------------------------------------------------------------------------------------
+// Differentiation of the central-path point (mcsdp_backward)
+
+// Wout[i][j] = sum_l D_il Win[l][j] for the symmetric D stored on lower(E) in the layout:
+// row i's strict-lower entries (rs_* lists) and column i's entries on and below the diagonal
+__global__ void k_E_times(DevSym S, const double *__restrict__ D, const double *__restrict__ Win,
+                          double *Wout, int64_t ldw, int nc) {
+  const int i = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nc) return;
+  double acc = 0.0;
+  for (int q = S.rs_ptr[i]; q < S.rs_ptr[i + 1]; ++q)
+    acc = fma(D[S.rs_off[q]], Win[(int64_t)S.rs_col[q] * ldw + j], acc);
+  const int t = S.col2sn[i];
+  const int64_t r0 = S.sn_rowptr[t];
+  const int nrow = (int)(S.sn_rowptr[t + 1] - r0);
+  const int lc = i - S.sn_col[t];
+  const int64_t base = S.sn_valptr[t] + (int64_t)lc * nrow;
+  for (int p = lc; p < nrow; ++p) acc = fma(D[base + p], Win[(int64_t)S.rows[r0 + p] * ldw + j], acc);
+  Wout[(int64_t)i * ldw + j] = acc;
+}
+
+void launch_E_times(const DevSym &S, const double *D, const double *Win, double *Wout, int64_t ldw,
+                    int nc, cudaStream_t st) {
+  if (nc <= 0) return;
+  dim3 grid((nc + 127) / 128, S.n);
+  k_E_times<<<grid, 128, 0, st>>>(S, D, Win, Wout, ldw, nc);
+}
+
+// out = the symmetric matrix whose entries on lower(E) dotted with a symmetric X give the layout
+// dot product sum g . X: off-diagonal layout values halved (they stand for both triangles), the
+// diagonal kept; positions of the layout above a supernode's diagonal set to zero
+__global__ void k_layout_sym(DevSym S, const double *__restrict__ g, double *out) {
+  const int t = blockIdx.x;
+  const int64_t v0 = S.sn_valptr[t];
+  const int nrow = (int)(S.sn_rowptr[t + 1] - S.sn_rowptr[t]);
+  const int ncol = S.sn_col[t + 1] - S.sn_col[t];
+  for (int e = threadIdx.x; e < nrow * ncol; e += blockDim.x) {
+    const int p = e % nrow, lc = e / nrow;
+    out[v0 + e] = p == lc ? g[v0 + e] : (p > lc ? 0.5 * g[v0 + e] : 0.0);
+  }
+}
+
+void launch_layout_sym(const DevSym &S, const double *g, double *out, cudaStream_t st) {
+  k_layout_sym<<<S.ns, 128, 0, st>>>(S, g, out);
+}
+
+// out = sym(M) on lower(E) from M's lower (Mlow) and transposed (Mup) entries on E
+__global__ void k_sym_combine(DevSym S, const double *__restrict__ Mlow,
+                              const double *__restrict__ Mup, double *out) {
+  const int t = blockIdx.x;
+  const int64_t v0 = S.sn_valptr[t];
+  const int nrow = (int)(S.sn_rowptr[t + 1] - S.sn_rowptr[t]);
+  const int ncol = S.sn_col[t + 1] - S.sn_col[t];
+  for (int e = threadIdx.x; e < nrow * ncol; e += blockDim.x) {
+    const int p = e % nrow, lc = e / nrow;
+    out[v0 + e] = p == lc ? Mlow[v0 + e] : (p > lc ? 0.5 * (Mlow[v0 + e] + Mup[v0 + e]) : 0.0);
+  }
+}
+
+void launch_sym_combine(const DevSym &S, const double *Mlow, const double *Mup, double *out,
+                        cudaStream_t st) {
+  k_sym_combine<<<S.ns, 128, 0, st>>>(S, Mlow, Mup, out);
+}
+
+// y = a x + y on n entries
+__global__ void k_axpy(int64_t n, double a, const double *__restrict__ x, double *y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = fma(a, x[i], y[i]);
+}
+void launch_axpy(int64_t n, double a, const double *x, double *y, cudaStream_t st) {
+  int blocks = (int)std::min<int64_t>(4096, (n + 255) / 256);
+  if (blocks > 0) k_axpy<<<blocks, 256, 0, st>>>(n, a, x, y);
+}
+
+// out[k] = A_k . M + add[k] (caller order) for M on the layout
+__global__ void k_con_apply(DevSym S, const double *__restrict__ M, const double *__restrict__ add,
+                            double *out) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < S.m; k += gridDim.x * blockDim.x) {
+    double a = 0.0;
+    for (int q = S.con_ptr[k]; q < S.con_ptr[k + 1]; ++q) a = fma(S.con_w[q], M[S.con_off[q]], a);
+    out[k] = add ? a + add[k] : a;
+  }
+}
+void launch_con_apply(const DevSym &S, const double *M, const double *add, double *out,
+                      cudaStream_t st) {
+  k_con_apply<<<(S.m + 255) / 256, 256, 0, st>>>(S, M, add, out);
+}
+
+// row m of B <- rhs (caller order) in the internal constraint order
+__global__ void k_border_from_user(DevSym S, double *B, int64_t ldb, const double *__restrict__ rhs) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.m; i += gridDim.x * blockDim.x)
+    B[S.m + (int64_t)i * ldb] = rhs[S.con_order[i]];
+}
+void launch_border_from_user(const DevSym &S, double *B, int64_t ldb, const double *rhs,
+                             cudaStream_t st) {
+  k_border_from_user<<<(S.m + 255) / 256, 256, 0, st>>>(S, B, ldb, rhs);
+}
+
+// per stored input entry e: gradient f_e g_{A_k}[off_e] with g_{A_0} = gA0 and
+// g_{A_k} = -z_k gA0 - v_k X (k >= 1); f_e = 2 for an off-diagonal entry (it sets both
+// triangles), with the sign of the input form for matrix 0
+__global__ void k_entry_grads(int64_t nnz, const int64_t *__restrict__ off, const int *__restrict__ kk,
+                              const int *__restrict__ pos, const double *__restrict__ f,
+                              const double *__restrict__ gA0, const double *__restrict__ X,
+                              const double *__restrict__ z, const double *__restrict__ v,
+                              double *gC, double *gA) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int k = kk[e];
+    const double g0 = gA0[off[e]];
+    if (k == 0) {
+      if (gC) gC[pos[e]] = f[e] * g0;
+    } else if (gA) {
+      gA[pos[e]] = f[e] * (-z[k - 1] * g0 - v[k - 1] * X[off[e]]);
+    }
+  }
+}
+void launch_entry_grads(int64_t nnz, const int64_t *off, const int *k, const int *pos,
+                        const double *f, const double *gA0, const double *X, const double *z,
+                        const double *v, double *gC, double *gA, cudaStream_t st) {
+  int blocks = (int)std::min<int64_t>(4096, (nnz + 255) / 256);
+  if (blocks > 0) k_entry_grads<<<blocks, 256, 0, st>>>(nnz, off, k, pos, f, gA0, X, z, v, gC, gA);
 }
 
 }  // namespace mcsdp

@@ -13,6 +13,7 @@
 #include <set>
 #include <string>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/mcsdp.h"
@@ -84,6 +85,15 @@ struct mcsdp_ctx {
   std::vector<int2> tiles_all;
   std::vector<double> z0_default;
   bool z0_ok = false;
+  // the input entries as given (caller order), for per-entry gradients
+  int form = 1;
+  std::vector<int> ue_k, ue_i, ue_j;
+  std::vector<int64_t> ent_off;
+  std::vector<int> ent_k, ent_pos;
+  std::vector<double> ent_f;
+  int64_t *ent_off_dev = nullptr;
+  int *ent_k_dev = nullptr, *ent_pos_dev = nullptr;
+  double *ent_f_dev = nullptr, *zsave = nullptr, *bwd_g = nullptr, *vrhs = nullptr;
   bool iterate_set = false;
   cudaEvent_t ev[8] = {};
   cudaStream_t st2 = nullptr;                  // low priority: trailing updates, primal step
@@ -377,6 +387,35 @@ void plan_workspace(mcsdp_ctx *c) {
       c->cmap_ptr[r + 1] = (int64_t)c->cmap_off.size();
     }
   }
+  // per input entry: layout offset of its lower position, matrix, index within the gradient
+  // output of its kind (matrix 0 / matrices 1..m) and the factor (2 off the diagonal, the sign of
+  // the input form for matrix 0)
+  {
+    const size_t ne = c->ue_k.size();
+    c->ent_off.assign(ne, 0);
+    c->ent_k.assign(ne, 0);
+    c->ent_pos.assign(ne, 0);
+    c->ent_f.assign(ne, 0.0);
+    int n0 = 0, n1 = 0;
+    for (size_t e = 0; e < ne; ++e) {
+      const int a = S.iperm[c->ue_i[e]], b2 = S.iperm[c->ue_j[e]];
+      const int rr = std::max(a, b2), cc = std::min(a, b2);
+      const int t = S.col2sn[cc];
+      const int64_t t0 = S.sn_rowptr[t];
+      const int tn = (int)(S.sn_rowptr[t + 1] - t0);
+      const int lc = cc - S.sn_col[t];
+      const int *rb = S.rows.data() + t0;
+      const int pos = (int)(std::lower_bound(rb + lc, rb + tn, rr) - rb);
+      c->ent_off[e] = S.sn_valptr[t] + pos + (int64_t)lc * tn;
+      c->ent_k[e] = c->ue_k[e];
+      c->ent_pos[e] = c->ue_k[e] == 0 ? n0++ : n1++;
+      c->ent_f[e] = (c->ue_i[e] != c->ue_j[e] ? 2.0 : 1.0) * (c->ue_k[e] == 0 && c->form == 0 ? -1.0 : 1.0);
+    }
+  }
+  plan_table(c, cur, "ent_off", c->ent_off);
+  plan_table(c, cur, "ent_k", c->ent_k);
+  plan_table(c, cur, "ent_pos", c->ent_pos);
+  plan_table(c, cur, "ent_f", c->ent_f);
   plan_table(c, cur, "cmap_ptr", c->cmap_ptr);
   plan_table(c, cur, "cmap_off", c->cmap_off);
   // ---- many-right-hand-side solves (kern_lsolve.cu): skip bitmaps and chunk plan ----
@@ -483,6 +522,9 @@ void plan_workspace(mcsdp_ctx *c) {
   // iteration buffers
   c->ldb = ((int64_t)m + 1 + 31) / 32 * 32;
   plan_buf(c, cur, "Xbar", nnzL * 8);
+  plan_buf(c, cur, "zsave", (size_t)m * 8);
+  plan_buf(c, cur, "bwd_g", nnzL * 8);
+  plan_buf(c, cur, "vrhs", (size_t)m * 8);
   plan_buf(c, cur, "z", (size_t)m * 8);
   plan_buf(c, cur, "Ylay", nnzL * 8);
   plan_buf(c, cur, "N", nnzL * 8);
@@ -596,6 +638,13 @@ void bind_pointers(mcsdp_ctx *c) {
 
   D.b = wsp<double>(c, "b");
   c->Xbar = wsp<double>(c, "Xbar");
+  c->zsave = wsp<double>(c, "zsave");
+  c->bwd_g = wsp<double>(c, "bwd_g");
+  c->vrhs = wsp<double>(c, "vrhs");
+  c->ent_off_dev = wsp<int64_t>(c, "ent_off");
+  c->ent_k_dev = wsp<int>(c, "ent_k");
+  c->ent_pos_dev = wsp<int>(c, "ent_pos");
+  c->ent_f_dev = wsp<double>(c, "ent_f");
   c->z = wsp<double>(c, "z");
   c->Ylay = wsp<double>(c, "Ylay");
   c->N = wsp<double>(c, "N");
@@ -795,8 +844,11 @@ mcsdp_status phase_scm(mcsdp_ctx *c) {
 
 // P-MATRIX (eq. newdX2): for column blocks of the identity, Y^{-1} E (N solves), dY Y^{-1} E,
 // X̂ dY Y^{-1} E (L̂ solves), keeping the entries on E.
+// Dlay == nullptr: dY (on the aggregate pattern); else a symmetric D on lower(E).  yinv_only:
+// only Y^{-1} on E (into YinvE).
 template <class T>
-mcsdp_status phase_pmatrix(mcsdp_ctx *c, int *nlaunch) {
+mcsdp_status phase_pmatrix(mcsdp_ctx *c, int *nlaunch, const double *Dlay = nullptr,
+                           bool yinv_only = false) {
   const Symbolic &S = c->S;
   const int n = S.n;
   int nl = 0;
@@ -814,8 +866,21 @@ mcsdp_status phase_pmatrix(mcsdp_ctx *c, int *nlaunch) {
     r[0] = lsolve_c<T>(c, true, f.N, f.dinvN, W1, nc, fw);
     r[1] = lsolve_c<T>(c, false, f.N, f.dinvN, W1, nc, none);
     launch_extract_lowerE(c->D, (const T *)W1, c->ldw, k0, nc, c->YinvE, c->stream);
-    launch_dY_times(c->D, c->dY, (const T *)W1, W2, c->ldw, nc, c->stream);
-    nl += 2;
+    nl += 1;
+    if (yinv_only) {
+      for (int q = 0; q < 2; ++q) {
+        if (r[q] < 0) return fail(c, MCSDP_ERR_ARG, "solve shape not supported in this precision");
+        nl += r[q];
+      }
+      continue;
+    }
+    if constexpr (std::is_same<T, double>::value) {
+      if (Dlay) launch_E_times(c->D, Dlay, (const double *)W1, (double *)W2, c->ldw, nc, c->stream);
+      else launch_dY_times(c->D, c->dY, (const T *)W1, W2, c->ldw, nc, c->stream);
+    } else {
+      launch_dY_times(c->D, c->dY, (const T *)W1, W2, c->ldw, nc, c->stream);
+    }
+    nl += 1;
     r[2] = lsolve_c<T>(c, true, f.Lh, f.dinvL, W2, nc, none);
     r[3] = lsolve_c<T>(c, false, f.Lh, f.dinvL, W2, nc, bwL);
     launch_extract_lowerE(c->D, (const T *)W2, c->ldw, k0, nc, c->Mlow, c->stream);
@@ -1119,6 +1184,10 @@ mcsdp_status mcsdp_create(const mcsdp_problem *p, const mcsdp_options *opt, void
   if (!(c->opt.beta > 0 && c->opt.beta < 1) || !(c->opt.gamma > 0 && c->opt.gamma < 1))
     return fail(c, MCSDP_ERR_ARG, "beta and gamma must lie in (0, 1)");
   ProblemData &P = c->P;
+  c->form = p->form;
+  c->ue_k.clear();
+  c->ue_i.clear();
+  c->ue_j.clear();
   P.n = p->n;
   P.m = p->m;
   P.b.assign(p->c, p->c + p->m);
@@ -1132,7 +1201,9 @@ mcsdp_status mcsdp_create(const mcsdp_problem *p, const mcsdp_options *opt, void
     if (!std::isfinite(v)) return fail(c, MCSDP_ERR_ARG, "entry " + std::to_string(t) + ": not finite");
     if (!seen.insert({k, i, j}).second)
       return fail(c, MCSDP_ERR_ARG, "entry " + std::to_string(t) + ": duplicate (mat,row,col)");
-    if (v == 0.0) continue;
+    c->ue_k.push_back(k);
+    c->ue_i.push_back(i);
+    c->ue_j.push_back(j);
     if (k == 0 && p->form == 0) v = -v;  // A_0 = -F_0
     P.mat.push_back(k);
     P.row.push_back(i);
@@ -1590,8 +1661,106 @@ mcsdp_status mcsdp_stats_reset(mcsdp_ctx *c) {
   return MCSDP_OK;
 }
 
-mcsdp_status mcsdp_backward(mcsdp_ctx *c, const double *, const double *, double *, double *, double *) {
-  return fail(c, MCSDP_ERR_STATE, "mcsdp_backward (differentiation of the solution) is not implemented");
+mcsdp_status mcsdp_backward(mcsdp_ctx *c, const double *gX, const double *gz, double *gC,
+                            double *gb, double *gA) {
+  mcsdp_status s = ready(c);
+  if (s) return s;
+  if (!c->iterate_set) return fail(c, MCSDP_ERR_STATE, "no iterate: solve (or set an iterate) first");
+  const Symbolic &S = c->S;
+  const int n = S.n, m = S.m;
+  const int64_t nnzL = c->D.nnzL;
+  double sc[8];
+  // mu of the current iterate
+  s = prepare(c, c->Xbar, c->z, sc);
+  if (s) return s;
+  const double mu = sc[0] / n;
+  if (!(mu > 0)) return fail(c, MCSDP_ERR_NUMERIC, "mu is not positive at the iterate");
+  // centring: Newton on F(z) = A(mu Y(z)^{-1}) - b, X̄ = mu Y^{-1} on E (the max-det completion of
+  // which is mu Y^{-1}); the Jacobian is the SCM at that X̄ and -F = b - mu h
+  bool centred = false;
+  double prev_res = -1.0;
+  for (int it = 0; it < 40 && !centred; ++it) {
+    int nl = 0;
+    s = phase_pmatrix<double>(c, &nl, nullptr, true);
+    if (s) return s;
+    CUDA_TRY(c, cudaMemsetAsync(c->Xbar, 0, nnzL * 8, c->stream));
+    launch_axpy(nnzL, mu, c->YinvE, c->Xbar, c->stream);
+    launch_measures(c->D, c->Xbar, c->Ylay, c->z, nullptr, c->scal, c->stream);
+    KCHECK(c);
+    CUDA_TRY(c, cudaMemcpyAsync(sc, c->scal, 6 * 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    prof_flush(c);
+    // done at 1e-13 relative, or once Newton stops gaining at the rounding level of the
+    // residual evaluation (below 1e-9 relative)
+    const double res = sc[3] / std::max(1.0, sc[4]);
+    if (res <= 1e-13 || (prev_res >= 0 && res > 0.5 * prev_res && res <= 1e-9)) {
+      centred = true;
+      break;
+    }
+    prev_res = res;
+    s = factor_X(c, c->Xbar);
+    if (s) return s;
+    s = phase_scm<double>(c);
+    if (s) return s;
+    launch_rhs_border(c->D, c->B, c->ldb, c->hvec, mu, c->stream);
+    dense_chol_bordered(c->B, c->ldb, m, c->status + 2, c->Binv, c->stream, &c->cs);
+    dense_backsolve(c->B, c->ldb, m, c->Binv, c->xs, c->stream);
+    launch_dz_to_user(c->D, c->xs, c->dz, c->stream);
+    CUDA_TRY(c, cudaMemcpyAsync(c->zsave, c->z, (size_t)m * 8, cudaMemcpyDeviceToDevice, c->stream));
+    double t = 1.0;
+    for (int h = 0;; ++h) {
+      CUDA_TRY(c, cudaMemcpyAsync(c->z, c->zsave, (size_t)m * 8, cudaMemcpyDeviceToDevice, c->stream));
+      launch_axpy(m, t, c->dz, c->z, c->stream);
+      CUDA_TRY(c, cudaMemsetAsync(c->status, 0, 4 * sizeof(int), c->stream));
+      s = phase_Y(c, c->z);
+      if (s) return s;
+      s = phase_ychol(c, 1, nullptr, c->Ylay, nullptr, c->N, c->dinvN, c->status);
+      if (s) return s;
+      int st[4];
+      s = read_status(c, st, 4);
+      if (s) return s;
+      if (st[2] & ST_NOT_PD) return fail(c, MCSDP_ERR_NOT_PD, "Schur complement matrix is not positive definite");
+      if (!(st[0] & ST_NOT_PD)) break;
+      t *= 0.5;
+      if (h > 40) return fail(c, MCSDP_ERR_STALL, "centring step collapsed");
+    }
+  }
+  if (!centred) return fail(c, MCSDP_ERR_STALL, "centring did not converge");
+  // at the central point: L̂ (Algorithm 1 on X̄ = mu Y^{-1} on E) and the SCM
+  s = factor_X(c, c->Xbar);
+  if (s) return s;
+  s = phase_scm<double>(c);
+  if (s) return s;
+  // G (symmetric) from the layout weights of the loss on X̄; R = sym(X̂ G Y^{-1}) on E
+  double *G = c->dX;
+  if (gX) launch_layout_sym(c->D, gX, G, c->stream);
+  else CUDA_TRY(c, cudaMemsetAsync(G, 0, nnzL * 8, c->stream));
+  int nl = 0;
+  s = phase_pmatrix<double>(c, &nl, G);
+  if (s) return s;
+  launch_sym_combine(c->D, c->Mlow, c->Mup, c->bwd_g, c->stream);  // R
+  // v = B^{-1} (A(R) + g_z)
+  launch_con_apply(c->D, c->bwd_g, gz, c->vrhs, c->stream);
+  launch_border_from_user(c->D, c->B, c->ldb, c->vrhs, c->stream);
+  dense_chol_bordered(c->B, c->ldb, m, c->status + 2, c->Binv, c->stream, &c->cs);
+  dense_backsolve(c->B, c->ldb, m, c->Binv, c->xs, c->stream);
+  launch_dz_to_user(c->D, c->xs, c->dz, c->stream);  // v, caller order
+  // g_{A_0} = sym(X̂ (A^*(v) - G) Y^{-1}) on E
+  CUDA_TRY(c, cudaMemsetAsync(c->dY, 0, nnzL * 8, c->stream));
+  launch_slot_combine(c->D, c->dY, c->dz, 0.0, 1.0, c->stream);
+  launch_axpy(nnzL, -1.0, G, c->dY, c->stream);
+  s = phase_pmatrix<double>(c, &nl, c->dY);
+  if (s) return s;
+  launch_sym_combine(c->D, c->Mlow, c->Mup, c->bwd_g, c->stream);
+  if (gb) CUDA_TRY(c, cudaMemcpyAsync(gb, c->dz, (size_t)m * 8, cudaMemcpyDeviceToDevice, c->stream));
+  launch_entry_grads((int64_t)c->ent_k.size(), c->ent_off_dev, c->ent_k_dev, c->ent_pos_dev,
+                     c->ent_f_dev, c->bwd_g, c->Xbar, c->z, c->dz, gC, gA, c->stream);
+  KCHECK(c);
+  int st[4];
+  s = read_status(c, st, 4);
+  if (s) return s;
+  if (st[2] & ST_NOT_PD) return fail(c, MCSDP_ERR_NOT_PD, "Schur complement matrix is not positive definite");
+  return MCSDP_OK;
 }
 
 }  // extern "C"
