@@ -152,6 +152,15 @@ typedef struct {
 } mcsdp_result;
 mcsdp_status mcsdp_solve(mcsdp_ctx *ctx, mcsdp_result *res);
 
+/* Batched form (not in the paper; small SDPs keep one GPU busy only together): solves count
+ * independent problems concurrently, nthreads host threads (0 = min(count, 16)) each taking the
+ * next unsolved context; every context runs on its own stream (create each with a distinct
+ * stream for the solves to overlap on the device).  The context with the largest workspace is
+ * solved first, alone.  results[i] (may be NULL) receives context i's result.  Returns MCSDP_OK
+ * when every solve returned MCSDP_OK, else the status of the first (lowest index) that did not. */
+mcsdp_status mcsdp_solve_batch(mcsdp_ctx *const *ctxs, int32_t count, int32_t nthreads,
+                               mcsdp_result *results);
+
 /* Iterate in device memory: Xbar_layout[nnz_layout] (X̄ on E), z[m]; Y is derived as
  * A_0 - sum z_k A_k.  Any pointer may be NULL (then not copied). */
 mcsdp_status mcsdp_set_iterate(mcsdp_ctx *ctx, const double *Xbar_layout_dev, const double *z_dev);

@@ -253,6 +253,24 @@ def diagonal_lp_sdp(n, m, seed):
     return _pack(f"diag_lp_{n}_{m}", n, m, b, ent, z0=y0, meta={"kind": "lp"})
 
 
+def batch_mix(n_maxcut, n_arrow, seed=SEED_BASE + 4):
+    """Many small SDPs (the batched configuration): max-cut on G(n, floor(5n/2)) with
+    n ~ U{50..400}, weights U[0,1); block-arrow with n ~ U{100..600}, border 20, ceil((n-20)/50)
+    blocks of sizes split evenly, m = n.  Problem p draws from seed + p."""
+    rng = Xoshiro256ss(seed)
+    out = []
+    for p in range(n_maxcut):
+        n = 50 + rng.below(351)
+        out.append(random_gnm_maxcut(n, (5 * n) // 2, seed + 1000 + p))
+    for p in range(n_arrow):
+        n = 100 + rng.below(501)
+        nb = -(-(n - 20) // 50)
+        base, extra = divmod(n - 20, nb)
+        sizes = [base + (1 if q < extra else 0) for q in range(nb)]
+        out.append(block_arrow(nb, sizes[0], 20, n, seed=seed + 5000 + p, block_sizes=sizes))
+    return out
+
+
 def workload(name, seed=None):
     """Named workloads: 'grid_maxcut_100' (10x10 lattice), 'block_arrow_2020' (40 x 50 + 20,
     m = 2000), 'block_arrow_1020' (20 x 50 + 20, m = 1000), 'ring_maxcut_20000'."""

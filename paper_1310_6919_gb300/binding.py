@@ -26,7 +26,7 @@ class Problem:
     mat/row/col/val list the upper triangle (row <= col) of A_0..A_m (mat 0 = A_0) when
     form=1, or of SDPA's F_0..F_m with c = b when form=0."""
 
-    def __init__(self, n, m, b, mat, row, col, val, form=1, device=0, **options):
+    def __init__(self, n, m, b, mat, row, col, val, form=1, device=0, stream=None, **options):
         self._L = _lib.load()
         self._ctx = C.c_void_p()
         self.n, self.m = int(n), int(m)
@@ -47,11 +47,13 @@ class Problem:
             setattr(opt, k, v)
         opt.device = int(device)
         self.device = int(device)
-        stream = None
+        cs = None
         if self.device >= 0:
             self.torch_device = torch.device("cuda", self.device)
-            stream = C.c_void_p(torch.cuda.current_stream(self.torch_device).cuda_stream)
-        st = self._L.mcsdp_create(C.byref(prob), C.byref(opt), stream, C.byref(self._ctx))
+            s = stream if stream is not None else torch.cuda.current_stream(self.torch_device)
+            self.stream = s
+            cs = C.c_void_p(s.cuda_stream)
+        st = self._L.mcsdp_create(C.byref(prob), C.byref(opt), cs, C.byref(self._ctx))
         self._check(st)
         self.info = self.sym_info()
         if self.device >= 0:
@@ -229,3 +231,23 @@ class Problem:
         N = self.zeros_layout()
         self._check(self._L.mcsdp_factors(self._ctx, _ptr(X), _ptr(zz), _ptr(Lh), _ptr(N)))
         return Lh, N
+
+
+def solve_batch(problems, nthreads=0):
+    """Solves the problems concurrently (mcsdp_solve_batch): host threads each take the next
+    unsolved problem; create each Problem with its own stream (stream=torch.cuda.Stream()) for
+    the solves to overlap on the device.  Returns the result dicts in order."""
+    if not problems:
+        return []
+    L = problems[0]._L
+    arr = (C.c_void_p * len(problems))(*[p._ctx.value for p in problems])
+    res = (_lib.Result_t * len(problems))()
+    torch.cuda.synchronize()
+    L.mcsdp_solve_batch(arr, len(problems), int(nthreads), res)
+    out = []
+    for r in res:
+        d = {f: getattr(r, f) for f, _ in r._fields_}
+        d["status_name"] = _lib.STATUS.get(d["status"], d["status"])
+        out.append(d)
+    return out
+

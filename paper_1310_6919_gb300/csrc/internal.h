@@ -42,6 +42,11 @@ __device__ __forceinline__ float pivot_rcp<float>(float d) {
   return __frcp_rn(d);
 }
 
+// Raises a kernel's dynamic shared-memory limit to the device's opt-in maximum (less its static
+// shared memory), once per (device, kernel); thread-safe, so contexts may run on several host
+// threads.  The limit does not change what a launch uses (its own request does).
+void smem_optin(const void *kernel);
+
 // Device copies of the symbolic tables (all pointers into the caller's workspace).
 struct DevSym {
   int n, m, ns, ngroup, max_nrow, max_ncol;

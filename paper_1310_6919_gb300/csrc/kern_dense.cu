@@ -254,11 +254,7 @@ static int dense_chol(T *B, int64_t ldb, int m, int rows, int *status, T *Linv_a
     cudaStreamWaitEvent(st2, cs->fork, 0);
   }
   const int smem_tile = 2 * NB * TS * (int)sizeof(T);
-  static bool configured = false;
-  if (!configured) {
-    cudaFuncSetAttribute(k_syrk_tiles<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_tile);
-    configured = true;
-  }
+  smem_optin((const void *)k_syrk_tiles<T>);
   int launches = 0;
   for (int k0 = 0, k = 0; k0 < m; k0 += NB, ++k) {
     const int nb = (m - k0) < NB ? (m - k0) : NB;
@@ -505,9 +501,7 @@ int dense_backsolve(const double *B, int64_t ldb, int m, const double *Linv_all,
                     cudaStream_t st) {
   if (m <= BS_CLUSTER_MAX_M) {
     const size_t smem = (size_t)m * sizeof(double);
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(k_backsolve_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
+    if (smem > 48 * 1024) smem_optin((const void *)k_backsolve_cluster);
     k_backsolve_cluster<<<BCL, BTH, smem, st>>>(B, ldb, m, Linv_all, x);
     return 1;
   }
@@ -829,8 +823,7 @@ int mixed_refine_step(const double *B, int64_t ldb, int m, const float *L32, con
                       const double *g, double *x, double *r, double *P, double *A, double *norms,
                       cudaStream_t st) {
   const size_t smem = (size_t)m * sizeof(float);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_refine_solve_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 48 * 1024) smem_optin((const void *)k_refine_solve_f32);
   k_refine_solve_f32<<<RCL, RTH, smem, st>>>(L32, m, Linv32, r, x);
   const int nch = mixed_chunks(m);
   k_gemv_part<<<dim3((m + 31) / 32, nch), 256, 0, st>>>(B, ldb, m, x, P, A);

@@ -601,12 +601,10 @@ int lsolve(const DevSym &S, const int *lvl_ptr_host, const int *lvl_xptr_host,
   if (ncolsW <= 0) return 0;
   const int ntiles = (ncolsW + 31) / 32;
   const size_t smem = (size_t)S.max_ncol * 32 * 8 + (size_t)LS_CH * S.max_nrow * 8 + (size_t)S.max_nrow * 4 + 16;
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaFuncSetAttribute(k_lfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_lbwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_lfwd_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured = smem;
+  if (smem > 48 * 1024) {
+    smem_optin((const void *)k_lfwd);
+    smem_optin((const void *)k_lbwd);
+    smem_optin((const void *)k_lfwd_partial);
   }
   static int nsm = 0;
   if (nsm == 0) {
@@ -615,15 +613,11 @@ int lsolve(const DevSym &S, const int *lvl_ptr_host, const int *lvl_xptr_host,
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (nsm <= 0) nsm = 1;
   }
-  static bool configured2 = false;
-  if (!configured2) {
-    cudaFuncSetAttribute(k_lfwd2<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, LS_SMEM_CAP);
-    cudaFuncSetAttribute(k_lbwd2<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, LS_SMEM_CAP);
-    cudaFuncSetAttribute(k_lfwd2<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, LS_SMEM_CAP);
-    cudaFuncSetAttribute(k_lbwd2<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, LS_SMEM_CAP);
-    cudaFuncSetAttribute(k_lfwd_partial2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, LS_SMEM_CAP);
-    configured2 = true;
-  }
+  smem_optin((const void *)k_lfwd2<T, 1>);
+  smem_optin((const void *)k_lbwd2<T, 1>);
+  smem_optin((const void *)k_lfwd2<T, 4>);
+  smem_optin((const void *)k_lbwd2<T, 4>);
+  smem_optin((const void *)k_lfwd_partial2<T>);
   int launches = 0;
   for (int li = 0; li < height; ++li) {
     const int l = fwd ? li : height - 1 - li;

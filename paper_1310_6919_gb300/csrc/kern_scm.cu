@@ -134,11 +134,7 @@ void launch_scm_tiles(const DevSym &S, const int2 *tiles, int ntiles, const T *W
   // two |P_h| x |P_g| blocks, the nonzero lists of two groups, and the X̂-times-A_j products of
   // one batch of constraints (XW_CAP doubles, or one constraint's if larger) in shared memory
   const size_t smem = scm_tiles_smem_bytes(S, pmax, (int)sizeof(T));
-  static size_t configured = 0;
-  if (smem > configured) {
-    cudaFuncSetAttribute(k_scm_tiles<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured = smem;
-  }
+  smem_optin((const void *)k_scm_tiles<T>);
   k_scm_tiles<T><<<ntiles, 256, smem, st>>>(S, tiles, WX, WY, ldw, goff, B, ldb, hvec);
 }
 template void launch_scm_tiles<double>(const DevSym &, const int2 *, int, const double *,

@@ -230,11 +230,7 @@ void launch_ychol_partials(const DevSym &S, int x0, int nx, int f0, int nf, int 
                            const double *Nbuf, double *Pf, const int *status, cudaStream_t st) {
   if (nx <= 0) return;
   const size_t smem = (size_t)S.max_nrow * S.max_ncol * 8;
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaFuncSetAttribute(k_ychol_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured = smem;
-  }
+  smem_optin((const void *)k_ychol_partial);
   dim3 grid(nx, ncand);
   k_ychol_partial<<<grid, 256, smem, st>>>(S, x0, Nbuf, Pf, status);
   if (nf > 0) {
@@ -288,11 +284,7 @@ void launch_ychol_level(const DevSym &S, int lvl_begin, int lvl_count, int ncand
                         double *Dbuf, int *status, const double *Pf, cudaStream_t st) {
   dim3 grid(lvl_count, ncand);
   const size_t smem = ychol_smem_bytes(S);
-  static size_t configured = 0;
-  if (smem > configured) {
-    cudaFuncSetAttribute(k_ychol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured = smem;
-  }
+  smem_optin((const void *)k_ychol);
   k_ychol<<<grid, 256, smem, st>>>(S, lvl_begin, alpha, Yb, dY, Nbuf, Dbuf, status, Pf);
 }
 
@@ -343,11 +335,7 @@ size_t alg1_smem_bytes(const DevSym &S) {
 void launch_alg1(const DevSym &S, const double *X, double *Lh, double *DL, int *status,
                  cudaStream_t st) {
   const size_t smem = alg1_smem_bytes(S);
-  static size_t configured = 0;
-  if (smem > configured) {
-    cudaFuncSetAttribute(k_alg1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured = smem;
-  }
+  smem_optin((const void *)k_alg1);
   k_alg1<<<S.ns, 256, smem, st>>>(S, X, Lh, DL, status);
 }
 
@@ -680,11 +668,7 @@ size_t primal_step_smem_bytes(const DevSym &S) {
 void launch_primal_step(const DevSym &S, const double *X, const double *D, double *alpha_r,
                         int *status, cudaStream_t st) {
   const size_t smem = primal_step_smem_bytes(S);
-  static size_t configured = 0;
-  if (smem > configured) {
-    cudaFuncSetAttribute(k_primal_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured = smem;
-  }
+  smem_optin((const void *)k_primal_step);
   k_primal_step<<<S.ns, 256, smem, st>>>(S, X, D, alpha_r, status);
 }
 

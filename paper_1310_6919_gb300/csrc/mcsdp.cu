@@ -4,14 +4,17 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <limits>
 #include <map>
+#include <mutex>
 #include <set>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <type_traits>
 #include <vector>
@@ -125,6 +128,21 @@ struct mcsdp_ctx {
   std::vector<cudaEvent_t> evpool;
   std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> pending;
 };
+
+void mcsdp::smem_optin(const void *kernel) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void *>> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  if (!done.insert({dev, kernel}).second) return;
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa{};
+  cudaFuncGetAttributes(&fa, kernel);
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       optin - (int)fa.sharedSizeBytes);
+}
 
 namespace {
 
@@ -1538,6 +1556,49 @@ mcsdp_status mcsdp_solve(mcsdp_ctx *c, mcsdp_result *res) {
   r.refine_steps = c->refine_steps;
   if (res) *res = r;
   return final_status;
+}
+
+mcsdp_status mcsdp_solve_batch(mcsdp_ctx *const *ctxs, int32_t count, int32_t nthreads,
+                               mcsdp_result *results) {
+  if (count < 0 || (count > 0 && !ctxs)) return MCSDP_ERR_ARG;
+  if (count == 0) return MCSDP_OK;
+  std::vector<mcsdp_status> st(count, MCSDP_OK);
+  auto run = [&](int i) {
+    mcsdp_ctx *c = ctxs[i];
+    mcsdp_result r{};
+    if (!c) {
+      st[i] = MCSDP_ERR_ARG;
+    } else {
+      if (!c->host_only) cudaSetDevice(c->device);
+      st[i] = mcsdp_solve(c, &r);
+    }
+    if (results) results[i] = r;
+  };
+  // the largest problem first, alone: it sets every kernel's shared-memory attribute to the
+  // largest value any of the others needs
+  int big = 0;
+  size_t bigsz = 0;
+  for (int i = 0; i < count; ++i)
+    if (ctxs[i] && ctxs[i]->ws_bytes >= bigsz) {
+      bigsz = ctxs[i]->ws_bytes;
+      big = i;
+    }
+  run(big);
+  std::atomic<int> next{0};
+  const int nt = nthreads > 0 ? nthreads : std::min(count, 16);
+  auto worker = [&]() {
+    for (;;) {
+      const int i = next.fetch_add(1);
+      if (i >= count) break;
+      if (i != big) run(i);
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nt; ++t) pool.emplace_back(worker);
+  for (auto &t : pool) t.join();
+  for (int i = 0; i < count; ++i)
+    if (st[i] != MCSDP_OK) return st[i];
+  return MCSDP_OK;
 }
 
 mcsdp_status mcsdp_stats_get(const mcsdp_ctx *c, mcsdp_stats *st) {
