@@ -50,6 +50,24 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value, device):
+    """The largest value of a per-rank number over all ranks (a MAX all-reduce; identity when
+    the run is not distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(total_ms_max, steps, world_size):
+    """Seconds per solve of the whole job: every rank solved `steps` problems in at most
+    total_ms_max milliseconds (replicas, weak scaling)."""
+    return total_ms_max * 1e-3 / (steps * world_size)
+
+
 def golden_iters():
     try:
         with open(os.path.join(ROOT, "tests", "golden", WORKLOAD + ".json")) as f:
@@ -213,13 +231,9 @@ def run_gb300(args):
         dist.barrier()
     clk = clocks.stop()
     stats = P.stats()
-    total_ms = float(np.sum(step_ms))
-    if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(np.sum(step_ms)), f"cuda:{dev}")
     n_solves = args.steps * ws
-    value = total_ms * 1e-3 / n_solves
+    value = job_throughput(total_ms, args.steps, ws)
     r = results[-1]
     iters = int(r["iters"])
     ok = all(x["status"] == 0 for x in results)
@@ -276,11 +290,7 @@ def run_gb300(args):
         mixed_ms.append(e0.elapsed_time(e1))
         mixed_res.append(rm)
     mstats = Pm.stats()
-    mixed_total = float(np.sum(mixed_ms))
-    if ws > 1:
-        t = torch.tensor([mixed_total], dtype=torch.float64, device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        mixed_total = float(t.item())
+    mixed_total = max_over_ranks(float(np.sum(mixed_ms)), f"cuda:{dev}")
     rm = mixed_res[-1]
     mixed = {"value": mixed_total * 1e-3 / n_solves, "unit": "s/solve",
              "speedup_vs_fp64": value / (mixed_total * 1e-3 / n_solves),
