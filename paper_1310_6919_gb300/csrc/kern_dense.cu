@@ -10,6 +10,7 @@
 
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 
 #include "../../include/mcsdp.h"
 #include "internal.h"
@@ -126,6 +127,70 @@ __global__ void k_potrf_diag(T *B, int64_t ldb, int k0, int nb, int *status, T *
     }
     Linv[i + j * NB] = in ? V[i * LD + j] * rd[i] : T(0);
   }
+}
+
+// FP32 diagonal block (the mixed form's factor): one warp, lane r holds row r of the block in
+// registers.  Column j: every lane takes the pivot by a shuffle, the column is scaled, and row r
+// receives - L[r][j] L[kk][j] for every kk <= r, L[kk][j] shuffled from lane kk; the inverse is
+// formed the same way (row k of L^{-1} final after step k, then broadcast).  No barriers and no
+// shared memory: FP32 arithmetic is cheap here, the serial chain is shuffles.
+__global__ void __launch_bounds__(32)
+    k_potrf_warp_f32(float *B, int64_t ldb, int k0, int nb, int *status, float *Linv) {
+  const int lane = threadIdx.x;
+  float a[NB], t[NB];
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    a[j] = (lane < nb && j < nb && lane >= j) ? B[(k0 + lane) + (int64_t)(k0 + j) * ldb] : 0.f;
+    t[j] = (j == lane) ? 1.f : 0.f;
+  }
+  bool bad = false;
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    if (j < nb) {
+      float d = __shfl_sync(0xffffffffu, a[j], j);
+      if (!(d > 0.f)) {
+        bad = true;
+        d = 1.f;
+      }
+      const float sq = __fsqrt_rn(d), rs = __frcp_rn(sq);
+      if (lane == j) a[j] = sq;
+      else if (lane > j) a[j] *= rs;
+#pragma unroll
+      for (int kk = j + 1; kk < NB; ++kk) {
+        const float lkj = __shfl_sync(0xffffffffu, a[j], kk);
+        if (lane >= kk) a[kk] = fmaf(-a[j], lkj, a[kk]);
+      }
+    }
+  }
+  // L^{-1}: step k scales row k (lane k) by 1 / L[k][k] and removes L[r][k] times it from rows r > k
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    if (k < nb) {
+      const float rk = __frcp_rn(__shfl_sync(0xffffffffu, a[k], k));
+      if (lane == k) {
+#pragma unroll
+        for (int c = 0; c <= k; ++c) t[c] *= rk;
+      }
+#pragma unroll
+      for (int c = 0; c <= k; ++c) {
+        const float tkc = __shfl_sync(0xffffffffu, t[c], k);
+        if (lane > k) t[c] = fmaf(-a[k], tkc, t[c]);
+      }
+    }
+  }
+  if (lane < nb) {
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      if (j <= lane && j < nb) {
+        B[(k0 + lane) + (int64_t)(k0 + j) * ldb] = a[j];
+        if (j < lane) B[(k0 + j) + (int64_t)(k0 + lane) * ldb] = a[j];  // L^T, upper triangle
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NB; ++c)
+    Linv[lane + c * NB] = (lane < nb && c <= lane && c < nb) ? t[c] : 0.f;
+  if (bad && lane == 0) atomicOr(status, ST_NOT_PD);  // every lane saw the same pivots
 }
 
 // Rows [r0, rend) of the panel columns [k0, k0+nb): X <- X L_kk^{-T} = X Linv^T.  CTA = 4 rows
@@ -259,7 +324,10 @@ static int dense_chol(T *B, int64_t ldb, int m, int rows, int *status, T *Linv_a
   for (int k0 = 0, k = 0; k0 < m; k0 += NB, ++k) {
     const int nb = (m - k0) < NB ? (m - k0) : NB;
     T *Linv = Linv_all + (int64_t)k * NB * NB;
-    k_potrf_diag<T><<<1, 256, 0, st>>>(B, ldb, k0, nb, status, Linv);
+    if constexpr (std::is_same<T, float>::value)
+      k_potrf_warp_f32<<<1, 32, 0, st>>>(B, ldb, k0, nb, status, Linv);
+    else
+      k_potrf_diag<T><<<1, 256, 0, st>>>(B, ldb, k0, nb, status, Linv);
     ++launches;
     const int r0 = k0 + nb;
     const int nr = rows - r0;
