@@ -230,6 +230,16 @@ mcsdp_status mcsdp_stats_reset(mcsdp_ctx *ctx);
 mcsdp_status mcsdp_sce_solve_noalloc(const double *B_dev, int64_t ldb, const double *g_dev,
                                      double *x_dev, int32_t m, void *cuda_stream);
 
+/* The reciprocal that the factorisations' serial pivot loops use instead of a division (the
+ * diagonal-block Cholesky of the SCM, Sec. 3.1 type (i), and the supernodal Cholesky of Y, type
+ * (ii)): r[i] = 1/d[i] from an FP32 seed and one third-order series step in FP64, faithfully
+ * rounded (error below 0.52 ulp) for positive normal d; outside [2^-120, 2^121) and for
+ * non-positive or non-finite d it is the IEEE division.  Exposed so its accuracy can be checked
+ * against division.  d and r are device arrays of n doubles; asynchronous on cuda_stream
+ * (a cudaStream_t).  MCSDP_ERR_ARG for n < 0 or a NULL array with n > 0. */
+mcsdp_status mcsdp_pivot_reciprocal(const double *d_dev, double *r_dev, int64_t n,
+                                    void *cuda_stream);
+
 /* Differentiation of the solution (not in the paper).  The point differentiated is the
  * central-path point for mu = X̄.Y/n of the context's iterate: the iterate is first re-centred
  * (Newton on z for A(mu Y(z)^{-1}) = b with Y(z) = A_0 - sum z_k A_k, to a residual of 1e-13

@@ -22,25 +22,36 @@ struct LsLevel {
   int nc, nr, cw, np;
 };
 
-// Reciprocal for the pivots of the serial column loops: an FP32 reciprocal of the rounded value
-// refined by two Newton-Raphson steps r <- r + r (1 - d r) in FP64 (each squares the relative
-// error: 2^-23 -> 2^-46 -> below half an ulp before the final rounding), four dependent FP64
-// operations instead of a full division.  Outside the FP32 range the plain division is used.
+// Reciprocal for the pivots of the serial column loops (FP64 issues one warp instruction per 64
+// cycles per sub-partition here, so the chain is kept to three dependent FP64 operations).  Seed:
+// the PTX approximate FP64 reciprocal (special-function unit; relative error delta about 2^-20),
+// then one third-order step of the series 1/d = s / (1 - e) with e = 1 - d s:
+// r = s + s (e + e^2), whose truncation error e^3 (about 2^-60 relative) is below the final
+// rounding.  Outside 2^-1000 .. 2^1000, and for negative or non-finite d, the plain division.
 template <class T>
 __device__ __forceinline__ T pivot_rcp(T d);
 template <>
 __device__ __forceinline__ double pivot_rcp<double>(double d) {
-  if (!(d > 1e-30 && d < 1e30)) return 1.0 / d;
-  double r = (double)__frcp_rn((float)d);
-  double e = fma(-d, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-d, r, 1.0);
-  return fma(r, e, r);
+  const int hi = __double2hiint(d);
+  const int ex = (hi >> 20) & 0x7ff;  // biased exponent (sign bit tested separately)
+  if (hi < 0 || ex < 1023 - 1000 || ex > 1023 + 1000) return 1.0 / d;
+  double s;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(s) : "d"(d));
+  const double e = fma(-d, s, 1.0);
+  return fma(s, fma(e, e, e), s);
 }
 template <>
 __device__ __forceinline__ float pivot_rcp<float>(float d) {
   return __frcp_rn(d);
 }
+
+// d > 0 and finite, decided on the high word with integer operations (an FP64 comparison costs
+// a full FP64 issue slot); positive numbers below 2^-1042 count as zero.
+__device__ __forceinline__ bool pivot_positive(double d) {
+  const int hi = __double2hiint(d);
+  return hi > 0 && ((hi >> 20) & 0x7ff) != 0x7ff;
+}
+__device__ __forceinline__ bool pivot_positive(float d) { return d > 0.f && d < __int_as_float(0x7f800000); }
 
 // Raises a kernel's dynamic shared-memory limit to the device's opt-in maximum (less its static
 // shared memory), once per (device, kernel); thread-safe, so contexts may run on several host

@@ -24,16 +24,21 @@ constexpr int NB = 32;  // panel width (FP64 on one SM is slow: a narrow panel k
 // of the factor (stored in Linv, nb x nb column-major, ld NB).  The serial column loop is the
 // critical path of the whole factorisation, so it is warp-specialised with one barrier per
 // column: at step j, warp 0 brings column j+1 up to date, takes its pivot d_{j+1}, the
-// reciprocal and the scaled column U[:, j+1]; warps 1-7 meanwhile apply step j to the columns
-// >= j+2 and step j of the inverse U^{-1} (forward elimination, row j final).  This is
+// reciprocal and the scaled column U[:, j+1] (five dependent FP64 operations: the update, three
+// for the reciprocal, the scaling; the pivot test is integer); warps 1-7 meanwhile apply step j
+// to the columns >= j+2 and step j of the inverse U^{-1} (forward elimination, row j final).
+// FP64 on this part issues one warp instruction per 64 cycles per warp and about one per 16
+// cycles per SM, so the bulk work of a step is packed densely (at most three elements per
+// thread) and each thread loads all its operands before its independent FMAs.  This is
 // A = U D U^T with U unit lower; L = U D^{1/2} and L^{-1} = D^{-1/2} U^{-1} follow with the nb
-// square roots taken in parallel.  FP64 on this part issues one warp instruction per 64 cycles
-// per SM sub-partition whatever the number of active lanes, so the trailing and inverse work of
-// a step is packed densely over the 224 threads of warps 1-7.
+// square roots taken in parallel.
 template <class T>
-__global__ void k_potrf_diag(T *B, int64_t ldb, int k0, int nb, int *status, T *Linv) {
+__global__ void __launch_bounds__(256)
+    k_potrf_diag(T *B, int64_t ldb, int k0, int nb, int *status, T *Linv) {
   constexpr int LD = NB + 1;
   constexpr int NP = NB * (NB - 1) / 2;  // packed triangle size for side NB - 1
+  constexpr int NBULK = 224;             // warps 1-7
+  constexpr int SLOTS = 3;  // elements per bulk thread and step: NB(NB-1)/2 + ... <= 496 <= 672
   __shared__ T A[NB * LD];   // working copy, row-major; the trailing part is updated in place
   __shared__ T U[NB * LD];   // unit lower factor, row-major
   __shared__ T V[NB * LD];   // U^{-1}, row-major
@@ -54,67 +59,76 @@ __global__ void k_potrf_diag(T *B, int64_t ldb, int k0, int nb, int *status, T *
   __syncthreads();
   bool bad = false;
   if (warp == 0) {  // column 0: pivot, reciprocal, scaled column
-    T r0 = T(0);
-    if (lane == 0) {
-      T d = A[0];
-      if (!(d > T(0))) {
-        bad = true;
-        d = T(1);
-      }
-      dd[0] = d;
-      r0 = pivot_rcp<T>(d);
-      rd[0] = r0;
+    T d = A[0];
+    if (!pivot_positive(d)) {
+      bad = true;
+      d = T(1);
     }
-    r0 = __shfl_sync(0xffffffffu, r0, 0);
+    const T r0 = pivot_rcp<T>(d);
+    if (lane == 0) dd[0] = d;
     if (lane >= 1 && lane < nb) U[lane * LD] = A[lane * LD] * r0;
   }
   __syncthreads();
+  const int bt = tid - 32;  // bulk thread index (warps 1-7)
   for (int j = 0; j < nb; ++j) {
     if (warp == 0) {
       if (j + 1 < nb) {
-        // column j+1 (rows >= j+1) receives step j, then its pivot and scaled column
+        // column j+1 (rows >= j+1) receives step j, then its pivot and scaled column; every
+        // lane takes the pivot and its reciprocal (no second shuffle)
         const int r = j + 1 + lane;
         T a = T(0);
         if (r < nb) {
-          a = A[r * LD + j + 1] - U[r * LD + j] * A[(j + 1) * LD + j];
+          a = fma(-U[r * LD + j], A[(j + 1) * LD + j], A[r * LD + j + 1]);
           A[r * LD + j + 1] = a;
         }
-        T d = __shfl_sync(0xffffffffu, a, 0), rj = T(0);
-        if (lane == 0) {
-          if (!(d > T(0))) {
-            bad = true;
-            d = T(1);
-          }
-          dd[j + 1] = d;
-          rj = pivot_rcp<T>(d);
-          rd[j + 1] = rj;
+        T d = __shfl_sync(0xffffffffu, a, 0);
+        if (!pivot_positive(d)) {
+          bad = true;
+          d = T(1);
         }
-        rj = __shfl_sync(0xffffffffu, rj, 0);
+        const T rj = pivot_rcp<T>(d);
+        if (lane == 0) dd[j + 1] = d;
         if (r < nb && lane >= 1) U[r * LD + j + 1] = a * rj;
       }
     } else {
-      // step j on columns >= j+2 (rows >= column), and step j of the inverse
+      // step j on columns >= j+2 (rows >= column): A[ii][kk] -= U[ii][j] A[kk][j]; and step j
+      // of the inverse: V[i][c] -= U[i][j] V[j][c] for i > j, c <= j (element f of the
+      // (nb-1-j) x (j+1) block: i = j+1 + f div (j+1), by an FP32 product exact for f < 1024)
       const int s = nb - 2 - j;
       const int ntr = s > 0 ? s * (s + 1) / 2 : 0;
-      const int w = j + 1, ninv = (nb - 1 - j) * w;
-      for (int e = tid - 32; e < ntr + ninv; e += 224) {
+      const int w = j + 1, ntot = ntr + (nb - 1 - j) * w;
+      const float rw = 1.0f / (float)w;
+      T x[SLOTS], u[SLOTS], v[SLOTS];
+      T *dst[SLOTS];
+#pragma unroll
+      for (int q = 0; q < SLOTS; ++q) {
+        const int e = bt + q * NBULK;
+        dst[q] = nullptr;
         if (e < ntr) {
           const int ii = j + 2 + pr[e], kk = j + 2 + pc[e];
-          A[ii * LD + kk] -= U[ii * LD + j] * A[kk * LD + j];
-        } else {
-          const int f = e - ntr, q = f / w;
-          const int i = j + 1 + q, c = f - q * w;
-          V[i * LD + c] -= U[i * LD + j] * V[j * LD + c];
+          dst[q] = &A[ii * LD + kk];
+          u[q] = U[ii * LD + j];
+          v[q] = A[kk * LD + j];
+        } else if (e < ntot) {
+          const int f = e - ntr, qq = (int)(((float)f + 0.5f) * rw);
+          const int i = j + 1 + qq, c = f - qq * w;
+          dst[q] = &V[i * LD + c];
+          u[q] = U[i * LD + j];
+          v[q] = V[j * LD + c];
         }
+        if (dst[q]) x[q] = *dst[q];
       }
+#pragma unroll
+      for (int q = 0; q < SLOTS; ++q)
+        if (dst[q]) *dst[q] = fma(-u[q], v[q], x[q]);
     }
     __syncthreads();
   }
-  if (bad) atomicOr(status, ST_NOT_PD);
+  if (bad && lane == 0) atomicOr(status, ST_NOT_PD);  // warp 0's lanes saw the same pivots
   if (tid < nb) {
     const T sq = sqrt(dd[tid]);
     dd[tid] = sq;
-    rd[tid] = T(1) / sq;
+    rd[tid] = pivot_rcp<T>(sq);
   }
   __syncthreads();
   for (int idx = tid; idx < NB * NB; idx += 256) {
@@ -963,4 +977,22 @@ extern "C" mcsdp_status mcsdp_sce_solve_noalloc(const double *B, int64_t ldb, co
     return MCSDP_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return MCSDP_ERR_CUDA;
   return (hst & ST_NOT_PD) ? MCSDP_ERR_NOT_PD : MCSDP_OK;
+}
+
+namespace mcsdp {
+__global__ void k_pivot_rcp(const double *__restrict__ d, double *__restrict__ r, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    r[i] = pivot_rcp<double>(d[i]);
+}
+}  // namespace mcsdp
+
+extern "C" mcsdp_status mcsdp_pivot_reciprocal(const double *d, double *r, int64_t n,
+                                               void *stream) {
+  if (n < 0 || (n > 0 && (!d || !r))) return MCSDP_ERR_ARG;
+  if (n == 0) return MCSDP_OK;
+  const int64_t want = (n + 255) / 256;
+  const int blocks = want > 4096 ? 4096 : (int)want;
+  mcsdp::k_pivot_rcp<<<blocks, 256, 0, (cudaStream_t)stream>>>(d, r, n);
+  return cudaGetLastError() == cudaSuccess ? MCSDP_OK : MCSDP_ERR_CUDA;
 }
