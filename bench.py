@@ -265,6 +265,47 @@ def run_gb300(args):
            (scm_ms * 1e-3) / 1e12 if scm_ms > 0 else None}
     phases = {k: ms[k] / args.steps for k in ms}
 
+    mixed = batched = e2e = None
+    if args.legs == "all":
+        mixed, e2e, batched = other_legs(args, inst, dev, stream, flush, X0, z0, r, value, n_solves)
+
+    line = None
+    if rank == 0:
+        # oracle timed on the host cores, bounded sample (rank 0, N = 1 only)
+        cpu = None
+        if ws == 1 and not args.no_cpu_baseline:
+            from oracle.sdp import SparseSym
+            A = SparseSym.from_instance(inst)
+            oi = golden_iters() or iters
+            tcpu = oracle_sample_step(inst, A)
+            cpu = {"value": tcpu * oi, "unit": "s/solve", "cores": os.cpu_count(),
+                   "kind": "oracle",
+                   "sample": (f"one dense-oracle PDIPM iteration on {WORKLOAD} (SCM on 1/32 of the "
+                              f"rows, scaled x32) = {tcpu:.2f} s, times the oracle's {oi} "
+                              "iterations; numpy/BLAS default threading")}
+        line = {"metric": METRIC, "value": value, "unit": "s/solve", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC, "precision": "fp64",
+                           "iterations": iters, "pobj": r["pobj"], "gap": r["gap"],
+                           "all_optimal": ok, "l2": "flushed between solves (512 MiB write)",
+                           "parallelism": f"replicas x{ws}"},
+                "roofline": roof, "scm_assembly": scm, "phases_ms_per_solve": phases,
+                "mixed": mixed, "batched": batched,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(stats["launches"]),
+                "gpu_launches_per_solve": stats["launches"] / args.steps, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def other_legs(args, inst, dev, stream, flush, X0, z0, r, value, n_solves):
+    """The mixed-form leg, the end-to-end leg and the batched leg of the JSON line."""
+    import torch
+    from paper_1310_6919_gb300 import Problem
     # the mixed form on the same workload: FP32 factor of the SCM + FP64 refinement, promoted to
     # the FP64 factor when the refinement stalls (same L2 flush, same event timing)
     Pm = Problem(inst.n, inst.m, inst.b, inst.mat, inst.row, inst.col, inst.val, form=1,
@@ -299,9 +340,11 @@ def run_gb300(args):
              "promoted_iter": int(rm["promoted_iter"]), "refine_steps": int(rm["refine_steps"]),
              "all_optimal": all(x["status"] == 0 for x in mixed_res),
              "phases_ms_per_solve": {k: mstats["ms"][k] / args.steps for k in mstats["ms"]},
-             "desc": ("SCM assembled in FP64; Cholesky factor of the SCM in FP32; SCE solved by "
-                      "FP64 iterative refinement against the FP64 SCM (backward error <= "
-                      "sqrt(m) 2^-53); everything else FP64")}
+             "desc": ("SCM solves and tile contraction in FP32 from FP32 copies of the factors "
+                      "(B entries are FP64 numbers of FP32 sums); SCE by an FP32 Cholesky factor "
+                      "of B and FP64 iterative refinement against the stored B (backward error "
+                      "1e-10); FP64 throughout once the relative gap is below 1e-5 or the "
+                      "refinement stalls; everything else FP64")}
 
     # end to end through the public API with host buffers: create (symbolic analysis + upload),
     # solve, copy the solution (X̄ on E, z) back to pinned host memory
@@ -370,38 +413,7 @@ def run_gb300(args):
                "desc": ("48 max-cut G(n, 5n/2), n ~ U{50..400}, w ~ U[0,1) and 16 block-arrow "
                         "SDPs, n ~ U{100..600}, border 20, m = n (seeded); host wall time, "
                         "inputs resident")}
-
-    line = None
-    if rank == 0:
-        # oracle timed on the host cores, bounded sample (rank 0, N = 1 only)
-        cpu = None
-        if ws == 1 and not args.no_cpu_baseline:
-            from oracle.sdp import SparseSym
-            A = SparseSym.from_instance(inst)
-            oi = golden_iters() or iters
-            tcpu = oracle_sample_step(inst, A)
-            cpu = {"value": tcpu * oi, "unit": "s/solve", "cores": os.cpu_count(),
-                   "kind": "oracle",
-                   "sample": (f"one dense-oracle PDIPM iteration on {WORKLOAD} (SCM on 1/32 of the "
-                              f"rows, scaled x32) = {tcpu:.2f} s, times the oracle's {oi} "
-                              "iterations; numpy/BLAS default threading")}
-        line = {"metric": METRIC, "value": value, "unit": "s/solve", "n_gpus": ws,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-                "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic",
-                "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC, "precision": "fp64",
-                           "iterations": iters, "pobj": r["pobj"], "gap": r["gap"],
-                           "all_optimal": ok, "l2": "flushed between solves (512 MiB write)",
-                           "parallelism": f"replicas x{ws}"},
-                "roofline": roof, "scm_assembly": scm, "phases_ms_per_solve": phases,
-                "mixed": mixed, "batched": batched,
-                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(stats["launches"]),
-                "gpu_launches_per_solve": stats["launches"] / args.steps, "clocks": clk}
-        print(json.dumps(line), flush=True)
-    if ws > 1:
-        dist.barrier()
-        dist.destroy_process_group()
-    return 0
+    return mixed, e2e, batched
 
 
 def main():
@@ -411,6 +423,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--legs", default="all", choices=["all", "fp64"],
+                    help="fp64: only the headline FP64 leg (for profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

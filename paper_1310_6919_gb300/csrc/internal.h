@@ -7,11 +7,11 @@ namespace mcsdp {
 
 // Per-update metadata of the left-looking update lists (one 32-byte record per update u):
 // source supernode d's first column, width and row count, the first row p1 of its block that
-// lands in the target, the block's row count np, and the offsets of the relative row indices
-// and of d's values
+// lands in the target, the block's row count np, d itself, and the offsets of the relative row
+// indices and of d's values
 struct alignas(16) UpdMeta {
   int dc0, dncol, dnrow, p1;
-  int np, pad;
+  int np, src;
   int64_t relptr, valp;
 };
 
@@ -155,12 +155,13 @@ size_t alg1_smem_bytes(const DevSym &S);
 // Level-scheduled supernodal solves of the columns of W (row-major n x ldw, ncolsW columns):
 // forward (L^{-1}, levels bottom-up) or backward (L^{-T}, top-down).  Returns the launch count.
 // lvl_xptr_host: per level, range of extra update chunks; lvl_fptr_host: per level, range of
-// xfst (targets with extra chunks); Pw: partial buffer (nslotw rows of ldw)
+// xfst (targets with extra chunks); Pw: partial buffer (nslotw rows of ldw); active (host, per
+// level, or nullptr): the (supernode, tile) pairs the skip rule keeps, which sets the launch shape
 template <class T>
 int lsolve(const DevSym &S, const int *lvl_ptr_host, const int *lvl_xptr_host,
            const int *lvl_fptr_host, const LsLevel *lvl_info, int height, bool fwd,
            const T *L, const T *D, T *W, int64_t ldw, int ncolsW, const LsSkip &sk, T *Pw,
-           cudaStream_t st);
+           const int64_t *active, cudaStream_t st);
 template <class T>
 void launch_rhs_unit(T *W, int64_t ldw, const int *rowof, int nrhs, cudaStream_t st);
 // every level fits the shared-memory staged kernels for this element size

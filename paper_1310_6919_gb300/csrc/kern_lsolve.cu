@@ -315,7 +315,7 @@ __device__ __forceinline__ void cpa_wait() {
 __host__ __device__ inline int al16(int b) { return (b + 15) & ~15; }
 
 struct FwdLayout {
-  int acc, ds, meta, buf, bufsz, total;
+  int acc, ds, meta, hdr, buf, bufsz, total;
 };
 // nc: ncol bound, cw/np: update chunk width / rows bound (cw = 0: no updates), with_d: D block
 __host__ __device__ inline FwdLayout fwd_layout(int nc, int cw, int np, bool with_d, int es) {
@@ -327,6 +327,8 @@ __host__ __device__ inline FwdLayout fwd_layout(int nc, int cw, int np, bool wit
   o += with_d ? al16(nc * nc * es) : 0;
   L.meta = o;
   o += cw > 0 ? 64 * (int)sizeof(UpdMeta) : 0;
+  L.hdr = o;  // per ring slot: (row count, source column count) of the chunk it holds
+  o += cw > 0 ? al16(LS_R * 8) : 0;
   L.buf = o;
   L.bufsz = cw > 0 ? al16(cw * 32 * es) + al16(cw * np * es) + al16(np * 4) : 0;
   o += LS_R * L.bufsz;
@@ -355,27 +357,44 @@ __host__ __device__ inline BwdLayout bwd_layout(int nr, int nc, int es) {
 }
 
 // acc[srel[p]][lane] -= sum over the updates [ub, ue) of L_d[p1 + p, :] W[S_d], the update
-// blocks taken in chunks of <= cw source columns through the ring
+// blocks taken in chunks of <= cw source columns through the ring.  An update whose source
+// supernode d the skip rule drops for this tile is passed over: W[S_d] of the tile's right-hand
+// sides is zero there (d's own solve was skipped), so the result is the same bit for bit.  The
+// producer writes each chunk's (rows, columns) into its slot header, so the consumer needs no
+// update index of its own.
 template <class T>
 __device__ __forceinline__ void pull_staged(const DevSym &S, int ub, int ue, const T *L,
                                             const T *Wc, int64_t ldw, T *acc,
                                             unsigned char *sm, const FwdLayout &lay, int cw, int npb,
-                                            int lane) {
+                                            int lane, const LsSkip &sk, int tile) {
   UpdMeta *ms = reinterpret_cast<UpdMeta *>(sm + lay.meta);
+  int2 *hdr = reinterpret_cast<int2 *>(sm + lay.hdr);
   int meta_end = ub;
-  int iu = ub, ij = 0, issued = 0;
+  int iu = ub, ij = 0, issued = 0, chunks = 0;
   const int es = (int)sizeof(T);
   const int xs_off = 0, lb_off = al16(cw * 32 * es), sr_off = lb_off + al16(cw * npb * es);
+  const int2 kr = sk.bits ? sk.tile_keys[tile] : make_int2(0, -1);
+  auto dropped = [&](int d) {
+    if (!sk.bits) return false;
+    for (int key = kr.x; key <= kr.y; ++key)
+      if (sk.bits[(int64_t)key * sk.words + (d >> 5)] & (1u << (d & 31))) return false;
+    return true;
+  };
   auto issue = [&]() {
-    if (iu < ue) {
+    while (iu < ue) {
       while (iu >= meta_end) {  // next 32 records into the metadata ring (64 entries)
         const int v = meta_end + lane;
         if (v < ue) ms[v & 63] = S.upd_meta[v];
         meta_end += 32;
         __syncwarp();
       }
+      if (ij > 0 || !dropped(ms[iu & 63].src)) break;
+      ++iu;
+    }
+    if (iu < ue) {
       const UpdMeta m = ms[iu & 63];
-      unsigned char *b = sm + lay.buf + (issued % LS_R) * lay.bufsz;
+      const int slot = issued % LS_R;
+      unsigned char *b = sm + lay.buf + slot * lay.bufsz;
       T *xs = reinterpret_cast<T *>(b + xs_off);
       T *Lb = reinterpret_cast<T *>(b + lb_off);
       int *sr = reinterpret_cast<int *>(b + sr_off);
@@ -387,6 +406,8 @@ __device__ __forceinline__ void pull_staged(const DevSym &S, int ub, int ue, con
         cpaT<T>(Lb + e, Lsrc + (int64_t)q * m.dnrow + p);
       }
       for (int p = lane; p < m.np; p += 32) cpa4(sr + p, S.upd_rel + m.relptr + p);
+      if (lane == 0) hdr[slot] = make_int2(m.np, w);
+      ++chunks;
       ij += w;
       if (ij >= m.dncol) {
         ++iu;
@@ -397,17 +418,17 @@ __device__ __forceinline__ void pull_staged(const DevSym &S, int ub, int ue, con
     ++issued;
   };
   for (int k = 0; k < LS_R - 1; ++k) issue();
-  int cu = ub, cj = 0, done = 0;
-  while (cu < ue) {
+  int done = 0;
+  while (done < chunks) {  // chunks == done here only once the producer has reached ue
     issue();
     cpa_wait<LS_R - 1>();
     __syncwarp();
-    const UpdMeta m = ms[cu & 63];
+    const int2 h = hdr[done % LS_R];
     const unsigned char *b = sm + lay.buf + (done % LS_R) * lay.bufsz;
     const T *xs = reinterpret_cast<const T *>(b + xs_off);
     const T *Lb = reinterpret_cast<const T *>(b + lb_off);
     const int *sr = reinterpret_cast<const int *>(b + sr_off);
-    const int w = min(cw, m.dncol - cj), np = m.np;
+    const int np = h.x, w = h.y;
     int p = 0;
     for (; p + 3 < np; p += 4) {
       T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
@@ -430,11 +451,6 @@ __device__ __forceinline__ void pull_staged(const DevSym &S, int ub, int ue, con
       acc[sr[p] * 32 + lane] -= a0;
     }
     __syncwarp();
-    cj += w;
-    if (cj >= m.dncol) {
-      ++cu;
-      cj = 0;
-    }
     ++done;
   }
 }
@@ -470,7 +486,8 @@ __global__ void __launch_bounds__(32 * NW)
     __syncthreads();
   }
   if (warp == 0) {
-    pull_staged(S, S.upd_ptr[t], S.upd_c0end[t], L, Wc, ldw, acc, smf, lay, cw, npb, lane);
+    pull_staged(S, S.upd_ptr[t], S.upd_c0end[t], L, Wc, ldw, acc, smf, lay, cw, npb, lane, sk,
+                tile);
     cpa_wait<0>();
   }
   __syncthreads();
@@ -507,7 +524,7 @@ __global__ void k_lfwd_partial2(DevSym S, int x0, int ntiles, const T *__restric
   T *acc = reinterpret_cast<T *>(smp + lay.acc);
   for (int c = 0; c < ncol; ++c) acc[c * 32 + lane] = T(0);
   pull_staged(S, S.xch_ub[x], S.xch_ue[x], L, W + (act ? col : 0), ldw, acc, smp, lay, cw, npb,
-              lane);
+              lane, sk, tile);
   cpa_wait<0>();
   __syncwarp();
   T *P = Pw + S.xch_slotw[x] * ldw + (act ? col : 0);
@@ -597,7 +614,7 @@ template <class T>
 int lsolve(const DevSym &S, const int *lvl_ptr_host, const int *lvl_xptr_host,
            const int *lvl_fptr_host, const LsLevel *lvl_info, int height, bool fwd,
            const T *L, const T *D, T *W, int64_t ldw, int ncolsW, const LsSkip &sk,
-           T *Pw, cudaStream_t st) {
+           T *Pw, const int64_t *active, cudaStream_t st) {
   if (ncolsW <= 0) return 0;
   const int ntiles = (ncolsW + 31) / 32;
   const size_t smem = (size_t)S.max_ncol * 32 * 8 + (size_t)LS_CH * S.max_nrow * 8 + (size_t)S.max_nrow * 4 + 16;
@@ -629,7 +646,8 @@ int lsolve(const DevSym &S, const int *lvl_ptr_host, const int *lvl_xptr_host,
     const int sf = fwd_layout(lv.nc, lv.cw, lv.np, true, es).total;
     const int sp = fwd_layout(lv.nc, lv.cw, lv.np, false, es).total;
     const int sb = bwd_layout(lv.nr, lv.nc, es).total;
-    const bool narrow = blocks <= (int64_t)LS_NARROW_PER_SM * nsm;
+    // CTAs the skip rule drops return at once: the shape follows the pairs that do work
+    const bool narrow = (active ? active[l] : blocks) <= (int64_t)LS_NARROW_PER_SM * nsm;
     if (fwd && sf <= LS_SMEM_CAP) {
       const int xb = lvl_xptr_host[l], xc = lvl_xptr_host[l + 1] - xb;
       if (xc > 0) {
@@ -673,10 +691,10 @@ int lsolve(const DevSym &S, const int *lvl_ptr_host, const int *lvl_xptr_host,
 
 template int lsolve<double>(const DevSym &, const int *, const int *, const int *, const LsLevel *,
                             int, bool, const double *, const double *, double *, int64_t, int,
-                            const LsSkip &, double *, cudaStream_t);
+                            const LsSkip &, double *, const int64_t *, cudaStream_t);
 template int lsolve<float>(const DevSym &, const int *, const int *, const int *, const LsLevel *,
                            int, bool, const float *, const float *, float *, int64_t, int,
-                           const LsSkip &, float *, cudaStream_t);
+                           const LsSkip &, float *, const int64_t *, cudaStream_t);
 
 // W[rowof[j] * ldw + j] = 1 for the unit right-hand sides (W zeroed before)
 template <class T>

@@ -76,6 +76,7 @@ struct mcsdp_ctx {
   // update-list chunks (see DevSym)
   std::vector<int> upd_c0end, xch_beg, xch_end, xch_t, xch_ub, xch_ue, lvl_xptr, xfst, lvl_fptr;
   std::vector<UpdMeta> upd_meta;
+  std::vector<int64_t> lvl_active;  // scratch: per level, pairs a solve's skip rule keeps
   std::vector<int64_t> cmap_ptr, cmap_off;
   std::vector<LsLevel> lvl_info;
   std::vector<int64_t> xch_slotw, xch_slotf;
@@ -353,7 +354,7 @@ void plan_workspace(mcsdp_ctx *c) {
       q.dnrow = (int)(S.sn_rowptr[d + 1] - S.sn_rowptr[d]);
       q.p1 = S.upd_p1[u];
       q.np = S.upd_p2[u] - S.upd_p1[u];
-      q.pad = 0;
+      q.src = d;
       q.relptr = S.upd_relptr[u];
       q.valp = S.sn_valptr[d];
     }
@@ -815,12 +816,39 @@ void cast_factors(mcsdp_ctx *c) {
   ks.done(4);
 }
 
+// Host copy of a skip rule (the bit rows and the key range of each tile of 32 right-hand sides);
+// bits == nullptr keeps every (supernode, tile) pair.
+struct SkipHost {
+  const uint32_t *bits;
+  const int2 *tile_keys;
+};
+
 template <class T>
-int lsolve_c(mcsdp_ctx *c, bool fwd, const T *L, const T *Dinv, T *W, int ncols, const LsSkip &sk) {
+int lsolve_c(mcsdp_ctx *c, bool fwd, const T *L, const T *Dinv, T *W, int ncols, const LsSkip &sk,
+             const SkipHost &hk) {
   const Symbolic &S = c->S;
+  // per level, the (supernode, tile) pairs the skip rule keeps: the launch shape depends on them
+  int64_t *active = nullptr;
+  if (hk.bits) {
+    const int ntiles = (ncols + 31) / 32;
+    c->lvl_active.assign(S.height, 0);
+    for (int l = 0; l < S.height; ++l)
+      for (int q = S.lvl_ptr[l]; q < S.lvl_ptr[l + 1]; ++q) {
+        const int t = S.lvl_sn[q];
+        for (int tl = 0; tl < ntiles; ++tl) {
+          const int2 kr = hk.tile_keys[tl];
+          for (int key = kr.x; key <= kr.y; ++key)
+            if (hk.bits[(size_t)key * c->bit_words + (t >> 5)] & (1u << (t & 31))) {
+              ++c->lvl_active[l];
+              break;
+            }
+        }
+      }
+    active = c->lvl_active.data();
+  }
   return lsolve<T>(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), c->lvl_fptr.data(),
                    c->lvl_info.data(), S.height, fwd, L, Dinv, W, c->ldw, ncols, sk,
-                   reinterpret_cast<T *>(c->Pw), c->stream);
+                   reinterpret_cast<T *>(c->Pw), active, c->stream);
 }
 
 // K3 with solves in T (the W buffers and partial slots hold T; as FP32 they use half their size)
@@ -840,11 +868,13 @@ mcsdp_status phase_scm(mcsdp_ctx *c) {
     nl += 2;
     LsSkip fw{c->reach_bits_dev, c->tkey_dev + ch.tkey_begin, c->bit_words};
     LsSkip bw{c->need_bits_dev, c->tkey_dev + ch.tkey_begin, c->bit_words};
+    const SkipHost hfw{c->reach_bits.data(), c->tkey_all.data() + ch.tkey_begin};
+    const SkipHost hbw{c->need_bits.data(), c->tkey_all.data() + ch.tkey_begin};
     // X̂[:, P_g] = L̂^{-T} L̂^{-1} E and Y^{-1}[:, P_g] = N^{-T} N^{-1} E for the chunk's groups
-    int r[4] = {lsolve_c<T>(c, true, f.Lh, f.dinvL, W1, ch.nrhs, fw),
-                lsolve_c<T>(c, false, f.Lh, f.dinvL, W1, ch.nrhs, bw),
-                lsolve_c<T>(c, true, f.N, f.dinvN, W2, ch.nrhs, fw),
-                lsolve_c<T>(c, false, f.N, f.dinvN, W2, ch.nrhs, bw)};
+    int r[4] = {lsolve_c<T>(c, true, f.Lh, f.dinvL, W1, ch.nrhs, fw, hfw),
+                lsolve_c<T>(c, false, f.Lh, f.dinvL, W1, ch.nrhs, bw, hbw),
+                lsolve_c<T>(c, true, f.N, f.dinvN, W2, ch.nrhs, fw, hfw),
+                lsolve_c<T>(c, false, f.N, f.dinvN, W2, ch.nrhs, bw, hbw)};
     for (int q = 0; q < 4; ++q) {
       if (r[q] < 0) return fail(c, MCSDP_ERR_ARG, "solve shape not supported in this precision");
       nl += r[q];
@@ -879,10 +909,13 @@ mcsdp_status phase_pmatrix(mcsdp_ctx *c, int *nlaunch, const double *Dlay = null
     launch_rhs_unit(W1, c->ldw, c->pm_rowof_dev + k0, nc, c->stream);
     LsSkip fw{c->pm_bits_dev, c->pm_tkey_dev + k0 / 32, c->bit_words};
     LsSkip bwL{c->pm_need_dev, c->pm_tkey_dev + k0 / 32, c->bit_words};
+    const SkipHost hfw{c->pm_bits.data(), c->pm_tkey.data() + k0 / 32};
+    const SkipHost hbwL{c->pm_need.data(), c->pm_tkey.data() + k0 / 32};
+    const SkipHost hnone{nullptr, nullptr};
     nl += 1;
     int r[4];
-    r[0] = lsolve_c<T>(c, true, f.N, f.dinvN, W1, nc, fw);
-    r[1] = lsolve_c<T>(c, false, f.N, f.dinvN, W1, nc, none);
+    r[0] = lsolve_c<T>(c, true, f.N, f.dinvN, W1, nc, fw, hfw);
+    r[1] = lsolve_c<T>(c, false, f.N, f.dinvN, W1, nc, none, hnone);
     launch_extract_lowerE(c->D, (const T *)W1, c->ldw, k0, nc, c->YinvE, c->stream);
     nl += 1;
     if (yinv_only) {
@@ -899,8 +932,8 @@ mcsdp_status phase_pmatrix(mcsdp_ctx *c, int *nlaunch, const double *Dlay = null
       launch_dY_times(c->D, c->dY, (const T *)W1, W2, c->ldw, nc, c->stream);
     }
     nl += 1;
-    r[2] = lsolve_c<T>(c, true, f.Lh, f.dinvL, W2, nc, none);
-    r[3] = lsolve_c<T>(c, false, f.Lh, f.dinvL, W2, nc, bwL);
+    r[2] = lsolve_c<T>(c, true, f.Lh, f.dinvL, W2, nc, none, hnone);
+    r[3] = lsolve_c<T>(c, false, f.Lh, f.dinvL, W2, nc, bwL, hbwL);
     launch_extract_lowerE(c->D, (const T *)W2, c->ldw, k0, nc, c->Mlow, c->stream);
     launch_extract_upperE(c->D, (const T *)W2, c->ldw, k0, nc, c->Mup, c->stream);
     nl += 2;
