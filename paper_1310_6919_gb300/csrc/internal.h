@@ -238,12 +238,17 @@ struct CholGraph {
   cudaGraphExec_t exec = nullptr;
 };
 struct CholStreams {
+  // synchronisation words of the FP64 task-queue factorisation (nullptr: launch per panel)
+  int *dag_sync = nullptr;
+  size_t dag_words = 0;
   cudaStream_t chain = nullptr, rest = nullptr;
   cudaEvent_t next[2] = {}, rest_ev[2] = {}, fork = nullptr, chain_done = nullptr;
   cudaEvent_t entry = nullptr, exit = nullptr;  // caller's stream -> chain stream -> caller's
   CholGraph graphs[4];
 };
 void chol_graphs_destroy(CholStreams *cs);
+// words of the task-queue factorisation's synchronisation buffer (m columns, rows rows)
+size_t chol_dag_words(int m, int rows);
 // cs == nullptr: everything on st, no lookahead, no graph
 int dense_chol_bordered(double *B, int64_t ldb, int m, int *status, double *Linv,
                         cudaStream_t st, CholStreams *cs);

@@ -8,6 +8,7 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <type_traits>
@@ -33,21 +34,56 @@ constexpr int NB = 32;  // panel width (FP64 on one SM is slow: a narrow panel k
 // A = U D U^T with U unit lower; L = U D^{1/2} and L^{-1} = D^{-1/2} U^{-1} follow with the nb
 // square roots taken in parallel.
 template <class T>
-__global__ void __launch_bounds__(256)
-    k_potrf_diag(T *B, int64_t ldb, int k0, int nb, int *status, T *Linv) {
+struct PotrfSmem {
+  T A[NB * (NB + 1)];  // working copy, row-major; the trailing part is updated in place
+  T U[NB * (NB + 1)];  // unit lower factor, row-major
+  T V[NB * (NB + 1)];  // U^{-1}, row-major
+  T rd[NB], dd[NB];
+  unsigned char pr[NB * (NB - 1) / 2], pc[NB * (NB - 1) / 2];  // packed e -> (row, column)
+};
+
+// CG: read B through L2 only (the task-queue factorisation, whose tiles other SMs write).
+// hp > 0: first apply the previous panel's update to the tile row, A(k0.., k0..) -=
+// P P^T with P = B[k0 .. k0 + hp, k0 - NB .. k0) (the already solved tile left of it); rows
+// nb .. hp-1 of the tile row (the right-hand-side row) are updated in B.
+template <class T, bool CG>
+__device__ __forceinline__ void potrf_block(T *B, int64_t ldb, int k0, int nb, int *status,
+                                            T *Linv, PotrfSmem<T> &sm, int hp = 0) {
   constexpr int LD = NB + 1;
-  constexpr int NP = NB * (NB - 1) / 2;  // packed triangle size for side NB - 1
-  constexpr int NBULK = 224;             // warps 1-7
-  constexpr int SLOTS = 3;  // elements per bulk thread and step: NB(NB-1)/2 + ... <= 496 <= 672
-  __shared__ T A[NB * LD];   // working copy, row-major; the trailing part is updated in place
-  __shared__ T U[NB * LD];   // unit lower factor, row-major
-  __shared__ T V[NB * LD];   // U^{-1}, row-major
-  __shared__ T rd[NB], dd[NB];
-  __shared__ unsigned char pr[NP], pc[NP];  // packed index e -> (row, column), column <= row
+  constexpr int NBULK = 224;  // warps 1-7
+  constexpr int SLOTS = 3;    // elements per bulk thread and step: at most 496 <= 3 x 224
+  T *A = sm.A, *U = sm.U, *V = sm.V, *rd = sm.rd, *dd = sm.dd;
+  unsigned char *pr = sm.pr, *pc = sm.pc;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (hp > 0) {
+    T *P = V;  // P[i][l], staged in the inverse's array before that is set up
+    for (int idx = tid; idx < NB * NB; idx += 256) {
+      const int i = idx % NB, l = idx / NB;
+      P[i * LD + l] = i < hp ? __ldcg(B + (k0 + i) + (int64_t)(k0 - NB + l) * ldb) : T(0);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < NB * NB; idx += 256) {
+      const int i = idx % NB, j = idx / NB;
+      if (i >= j && i < hp && j < nb) {
+        T *src = B + (k0 + i) + (int64_t)(k0 + j) * ldb;
+        T s0 = T(0), s1 = T(0);
+#pragma unroll 8
+        for (int l = 0; l < NB; l += 2) {
+          s0 = fma(P[i * LD + l], P[j * LD + l], s0);
+          s1 = fma(P[i * LD + l + 1], P[j * LD + l + 1], s1);
+        }
+        const T v = __ldcg(src) - (s0 + s1);
+        if (i < nb) A[i * LD + j] = v;
+        else *src = v;  // the right-hand-side row
+      }
+    }
+    __syncthreads();
+  }
   for (int idx = tid; idx < NB * NB; idx += 256) {
     const int i = idx % NB, j = idx / NB;
-    A[i * LD + j] = (i >= j && i < nb && j < nb) ? B[(k0 + i) + (int64_t)(k0 + j) * ldb] : T(0);
+    const T *src = B + (k0 + i) + (int64_t)(k0 + j) * ldb;
+    if (hp == 0 || !(i >= j && i < nb && j < nb))
+      A[i * LD + j] = (i >= j && i < nb && j < nb) ? (CG ? __ldcg(src) : *src) : T(0);
     V[i * LD + j] = (i == j) ? T(1) : T(0);
     U[i * LD + j] = (i == j) ? T(1) : T(0);
   }
@@ -141,6 +177,13 @@ __global__ void __launch_bounds__(256)
     }
     Linv[i + j * NB] = in ? V[i * LD + j] * rd[i] : T(0);
   }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256)
+    k_potrf_diag(T *B, int64_t ldb, int k0, int nb, int *status, T *Linv) {
+  __shared__ PotrfSmem<T> sm;
+  potrf_block<T, false>(B, ldb, k0, nb, status, Linv, sm);
 }
 
 // FP32 diagonal block (the mixed form's factor): one warp, lane r holds row r of the block in
@@ -314,6 +357,335 @@ static void launch_syrk(T *B, int64_t ldb, int k0, int nb, int c_lo, int c_hi, i
   k_syrk_tiles<T><<<dim3(nti, ntj), 256, smem, st>>>(B, ldb, k0, nb, c_lo, c_hi, rend);
 }
 
+// ---- Task-queue factorisation (FP64): one persistent launch ----
+// The right-looking blocked Cholesky as tasks on 32 x 32 tiles (R row tiles of the rows x m
+// matrix, C column tiles):
+//   POTRF(k)      diagonal tile k: factor and inverse (potrf_block)
+//   TRSM(i, k)    tile (i, k), i > k: L(i, k) = A(i, k) L(k, k)^{-T}
+//   UPD(i, j, k)  tile (i, j), i >= j > k: A(i, j) -= L(i, k) L(j, k)^T (lower part if i == j)
+// The chain from one diagonal tile to the next is shortened: TRSM(p, p-1) is split over eight
+// tasks TS(p, s) of four rows each, and NEXT(p) = UPD(p, p, p-1) folded into the loading of
+// POTRF(p) (the right-hand-side row of the tile row updated with it).
+// CTAs take tickets from one counter; ticket order puts every dependency before its dependants:
+//   POTRF(0), TRSM(2..R-1, 0), then for k = 0 .. C-2:
+//     TS(k+1, 0..7), NEXT(k+1),
+//     UPD(k+2.., k+1, k)             the rest of the next column,
+//     UPD(i, j, k) for j >= k+2     the rest of panel k's update, with the block
+//     TRSM(k+3.., k+1)              placed DAG_DEFER tickets into it, so that NEXT(k+1) has
+//                                   normally finished before a CTA takes one of them.
+// A CTA holding the smallest unfinished ticket finds all its dependencies done, so the queue
+// always progresses whatever the residency (no co-scheduling needed).  Per tile (i, j) the host
+// zeroes upd[i][j] (updates applied; UPD(i, j, k) waits for k of them, which also serialises
+// the updates of one tile) and fin[i][j] (1 once L(i, j) is final).  The tiles are written and
+// read through L2 (ld.global.cg; release = fence + atomic add, acquire = ld.acquire.gpu).  Every
+// wait is bounded: on timeout the CTA sets the abort word and ST_TIMEOUT and every CTA leaves.
+// Against the launch-per-panel form this keeps the trailing tiles flowing across panels (no
+// launch gaps, no half-empty last waves per panel) while the next column's chain runs ahead.
+constexpr int DAG_THREADS = 256;
+constexpr int64_t DAG_SPIN_LIMIT = 1 << 22;  // polls per wait (about four seconds with backoff)
+constexpr int64_t DAG_DEFER = 512;           // tickets of panel k's rest before TRSM(., k+1)
+
+struct DagSync {
+  int *ticket, *abort, *upd, *fin;
+  int C;
+};
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// thread 0: wait until *flag >= target; false on abort or timeout (which it raises)
+__device__ bool dag_wait(const int *flag, int target, const DagSync &q, int *status) {
+  unsigned ns = 32;
+  for (int64_t it = 0; it < DAG_SPIN_LIMIT; ++it) {
+    if (ld_acquire(flag) >= target) return true;
+    if (ld_acquire(q.abort)) return false;
+    __nanosleep(ns);
+    if (ns < 1024) ns <<= 1;
+  }
+  atomicExch(q.abort, 1);
+  atomicOr(status, ST_TIMEOUT);
+  return false;
+}
+
+// sum_{j = a}^{C-1} (R - j)
+__device__ __forceinline__ int64_t dag_tail(int64_t a, int64_t R, int64_t C) {
+  if (a >= C) return 0;
+  const int64_t u = C - a;
+  return u * R - (u * (a + C - 1)) / 2;
+}
+// first row tile of the TRSM block of iteration k (tile (k+2, k+1) belongs to NEXT(k+2))
+__device__ __host__ __forceinline__ int64_t dag_trsm_lo(int64_t k, int64_t C) {
+  return k + 2 < C ? k + 3 : k + 2;
+}
+constexpr int DAG_TS = NB / 4;  // TS tasks per chain step
+// tickets of iteration k (k = 0 .. C-2): TS, NEXT, the next column's rest, panel k's rest, TRSMs
+__device__ __forceinline__ int64_t dag_iter_size(int64_t k, int64_t R, int64_t C) {
+  const int64_t lo = dag_trsm_lo(k, C);
+  return DAG_TS + 1 + (R - k - 2) + dag_tail(k + 2, R, C) + (R > lo ? R - lo : 0);
+}
+// completions that make tile (i, k) final: eight TS tasks for a tile left of a diagonal tile
+__device__ __forceinline__ int dag_fin_target(int i, int k, int C) {
+  return (i == k + 1 && i < C) ? DAG_TS : 1;
+}
+
+// TRSM(i, k): rows [i0, i0 + h) of columns [k0, k0 + nb).  Thread = (row r = tid / 8, columns
+// c = tid % 8 + 8 q, q < 4): four independent 32-term dot products with the inverse's rows.
+template <class T>
+__device__ void dag_trsm(T *B, int64_t ldb, int i0, int h, int k0, int nb, int ncl,
+                         const T *Linv, T *sm) {
+  constexpr int LD = NB + 1;
+  T *Xs = sm, *Ls = sm + NB * LD;  // Xs[r][l]; Ls[l][c] = Linv[c][l]
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < NB * NB; idx += DAG_THREADS) {
+    const int r = idx & (NB - 1), l = idx / NB;
+    Xs[r * LD + l] = (r < h && l < nb) ? __ldcg(B + (i0 + r) + (int64_t)(k0 + l) * ldb) : T(0);
+    Ls[l * LD + r] = __ldcg(Linv + r + l * NB);  // here r plays the column c
+  }
+  __syncthreads();
+  const int r = tid >> 3, c0 = tid & 7;
+  T acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll 8
+  for (int l = 0; l < NB; ++l) {
+    const T x = Xs[r * LD + l];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = fma(x, Ls[l * LD + c0 + 8 * q], acc[q]);
+  }
+  if (r < h) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = c0 + 8 * q;
+      if (c < nb) {
+        B[(i0 + r) + (int64_t)(k0 + c) * ldb] = acc[q];
+        if (i0 + r < ncl) B[(k0 + c) + (int64_t)(i0 + r) * ldb] = acc[q];  // L^T, upper part
+      }
+    }
+  }
+}
+
+// TS(p, s): rows i0 .. i0 + h (h <= 4) of the tile left of diagonal tile p, L = X Linv^T with
+// the full-width previous panel (nb = NB); two threads per output split the 32 terms.
+template <class T>
+__device__ void dag_trsm4(T *B, int64_t ldb, int i0, int h, int k0, int ncl, const T *Linv,
+                          T *sm) {
+  constexpr int LD = NB + 1;
+  T *Xs = sm, *Ls = sm + 4 * LD;  // Xs[r][l]; Ls[l][c] = Linv[c][l]
+  const int tid = threadIdx.x;
+  if (tid < 4 * NB) {
+    const int r = tid & 3, l = tid >> 2;
+    Xs[r * LD + l] = r < h ? __ldcg(B + (i0 + r) + (int64_t)(k0 + l) * ldb) : T(0);
+  }
+  for (int idx = tid; idx < NB * NB; idx += DAG_THREADS) {
+    const int c = idx & (NB - 1), l = idx / NB;
+    Ls[l * LD + c] = __ldcg(Linv + c + l * NB);
+  }
+  __syncthreads();
+  const int o = tid >> 1, half = tid & 1, r = o >> 5, c = o & (NB - 1);
+  T a0 = T(0), a1 = T(0);
+#pragma unroll
+  for (int l = half * 16; l < half * 16 + 16; l += 2) {
+    a0 = fma(Xs[r * LD + l], Ls[l * LD + c], a0);
+    a1 = fma(Xs[r * LD + l + 1], Ls[(l + 1) * LD + c], a1);
+  }
+  T acc = a0 + a1;
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  if (half == 0 && r < h) {
+    B[(i0 + r) + (int64_t)(k0 + c) * ldb] = acc;
+    if (i0 + r < ncl) B[(k0 + c) + (int64_t)(i0 + r) * ldb] = acc;  // L^T, upper part
+  }
+}
+
+// UPD(i, j, k): C rows [i0, i0 + h) x columns [j0, j0 + w) -= L(i, k) L(j, k)^T, the lower part
+// only on a diagonal tile (diag).  2 x 2 outputs per thread, K = nb.
+template <class T>
+__device__ void dag_upd(T *B, int64_t ldb, int i0, int h, int j0, int w, int k0, int nb, bool diag,
+                        T *sm) {
+  T *Ai = sm, *Aj = sm + NB * NB;  // [l][row]
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < NB * NB; idx += DAG_THREADS) {
+    const int rr = idx & (NB - 1), l = idx / NB;
+    const bool lk = l < nb;
+    Ai[l * NB + rr] = (lk && rr < h) ? __ldcg(B + (i0 + rr) + (int64_t)(k0 + l) * ldb) : T(0);
+    Aj[l * NB + rr] = (lk && rr < w) ? __ldcg(B + (j0 + rr) + (int64_t)(k0 + l) * ldb) : T(0);
+  }
+  __syncthreads();
+  const int tx = tid & 15, ty = tid >> 4;
+  T acc[2][2] = {};
+#pragma unroll 8
+  for (int l = 0; l < NB; ++l) {
+    const T a0 = Ai[l * NB + ty * 2], a1 = Ai[l * NB + ty * 2 + 1];
+    const T b0 = Aj[l * NB + tx * 2], b1 = Aj[l * NB + tx * 2 + 1];
+    acc[0][0] = fma(a0, b0, acc[0][0]);
+    acc[0][1] = fma(a0, b1, acc[0][1]);
+    acc[1][0] = fma(a1, b0, acc[1][0]);
+    acc[1][1] = fma(a1, b1, acc[1][1]);
+  }
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const int r = ty * 2 + p;
+    if (r >= h) continue;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int c = tx * 2 + q;
+      if (c < w && (!diag || r >= c)) {
+        T *dst = B + (i0 + r) + (int64_t)(j0 + c) * ldb;
+        *dst = __ldcg(dst) - acc[p][q];
+      }
+    }
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(DAG_THREADS, 2)
+    k_chol_dag(T *B, int64_t ldb, int m, int rows, int *status, T *Linv_all, DagSync q,
+               int64_t total) {
+  extern __shared__ __align__(16) unsigned char smd_raw[];
+  T *sm = reinterpret_cast<T *>(smd_raw);
+  __shared__ int s_task[3];  // [0] first ticket, [1] next ticket, [2] dependencies met
+  const int tid = threadIdx.x;
+  const int R = (rows + NB - 1) / NB, C = q.C;
+  const int lo0 = C > 1 ? 2 : 1;  // first TRSM(., 0) row tile (tile (1, 0) belongs to NEXT(1))
+  const int64_t pre = 1 + (R > lo0 ? R - lo0 : 0);
+  int kcur = 0;
+  int64_t kstart = pre;  // first ticket of iteration kcur
+  if (tid == 0) s_task[0] = atomicAdd(q.ticket, 1);
+  __syncthreads();
+  int t = s_task[0];
+  while (t < total) {
+    if (tid == 0) s_task[1] = atomicAdd(q.ticket, 1);  // the next ticket, fetched early
+    // decode t into (type, i, j, k): 0 POTRF(0), 1 TRSM(i, k), 2 UPD(i, j, k), 3 NEXT(k),
+    // 4 TS(k, s = tj)
+    int type, ti, tj, tk;
+    if (t == 0) {
+      type = 0; ti = tj = tk = 0;
+    } else if (t < pre) {
+      type = 1; ti = lo0 + t - 1; tj = tk = 0;
+    } else {
+      while (kcur + 1 < C && t >= kstart + dag_iter_size(kcur, R, C)) {
+        kstart += dag_iter_size(kcur, R, C);
+        ++kcur;
+      }
+      int64_t e = t - kstart;
+      const int k = kcur, n1 = R - k - 2;
+      if (e < DAG_TS) {
+        type = 4; ti = tk = k + 1; tj = (int)e;
+      } else if ((e -= DAG_TS) == 0) {
+        type = 3; ti = tj = tk = k + 1;
+      } else if ((e -= 1) < n1) {
+        type = 2; ti = k + 2 + (int)e; tj = k + 1; tk = k;
+      } else {
+        e -= n1;
+        const int64_t rest = dag_tail(k + 2, R, C), lo = dag_trsm_lo(k, C);
+        const int64_t ntr = R > lo ? R - lo : 0, defer = rest < DAG_DEFER ? rest : DAG_DEFER;
+        if (e >= defer && e < defer + ntr) {
+          type = 1; ti = (int)(lo + e - defer); tj = tk = k + 1;
+        } else {
+          if (e >= defer + ntr) e -= ntr;
+          int j = k + 2;
+          while (j < C && e >= R - j) {
+            e -= R - j;
+            ++j;
+          }
+          type = 2; ti = j + (int)e; tj = j; tk = k;  // j < C for every ticket below total
+        }
+      }
+    }
+    // dependencies (thread 0 waits, the CTA follows)
+    bool ok = true;
+    if (tid == 0) {
+      const int C_ = q.C;
+      if (type == 0) {
+        ok = true;  // POTRF(0): nothing before it
+      } else if (type == 4) {  // TS(p, s): rows of L(p, p-1)
+        ok = dag_wait(q.fin + (tk - 1) * C_ + (tk - 1), 1, q, status) &&
+             dag_wait(q.upd + tk * C_ + (tk - 1), tk - 1, q, status);
+      } else if (type == 3) {  // NEXT(p): UPD(p, p, p-1) and POTRF(p)
+        ok = dag_wait(q.fin + tk * C_ + (tk - 1), DAG_TS, q, status) &&
+             dag_wait(q.upd + tk * C_ + tk, tk - 1, q, status);
+      } else if (type == 1) {
+        ok = dag_wait(q.fin + tk * C_ + tk, 1, q, status) &&
+             dag_wait(q.upd + ti * C_ + tk, tk, q, status);
+      } else {
+        ok = dag_wait(q.fin + ti * C_ + tk, dag_fin_target(ti, tk, C_), q, status) &&
+             dag_wait(q.fin + tj * C_ + tk, dag_fin_target(tj, tk, C_), q, status) &&
+             dag_wait(q.upd + ti * C_ + tj, tk, q, status);
+      }
+      s_task[2] = ok ? 1 : 0;
+    }
+    __syncthreads();
+    if (!s_task[2]) break;
+    const int k0 = tk * NB, nb = min(NB, m - k0);
+    if (type == 4) {
+      const int i0 = k0 + 4 * tj, h = max(0, min(4, min(rows, k0 + NB) - i0));
+      dag_trsm4<T>(B, ldb, i0, h, k0 - NB, m, Linv_all + (int64_t)(tk - 1) * NB * NB, sm);
+    } else if (type == 0 || type == 3) {
+      T *Lk = Linv_all + (int64_t)tk * NB * NB;
+      // NEXT: the previous panel's update of this tile row is folded into the loading
+      potrf_block<T, true>(B, ldb, k0, nb, status, Lk, *reinterpret_cast<PotrfSmem<T> *>(sm),
+                           type == 3 ? min(NB, rows - k0) : 0);
+      // when m is not a multiple of NB the last diagonal tile's row block also holds the
+      // right-hand-side row m: solve it here (no TRSM task covers rows of a diagonal tile)
+      const int r0 = k0 + nb, r1 = min(rows, k0 + NB);
+      if (r0 < r1) {
+        __syncthreads();  // Lk stored by this CTA
+        dag_trsm<T>(B, ldb, r0, r1 - r0, k0, nb, m, Lk, sm);
+      }
+    } else if (type == 1) {
+      const int i0 = ti * NB;
+      dag_trsm<T>(B, ldb, i0, min(NB, rows - i0), k0, nb, m, Linv_all + (int64_t)tk * NB * NB,
+                  sm);
+    } else {
+      const int i0 = ti * NB, j0 = tj * NB;
+      dag_upd<T>(B, ldb, i0, min(NB, rows - i0), j0, min(NB, m - j0), k0, nb, ti == tj, sm);
+    }
+    __syncthreads();  // every store of the task issued; the next ticket visible
+    if (tid == 0) {
+      __threadfence();
+      if (type == 2) atomicAdd(q.upd + ti * q.C + tj, 1);
+      else if (type == 4) atomicAdd(q.fin + tk * q.C + (tk - 1), 1);  // one of DAG_TS
+      else atomicAdd(q.fin + ti * q.C + tk, 1);  // POTRF / NEXT: fin[p][p]; TRSM: fin[i][k]
+    }
+    t = s_task[1];
+    __syncthreads();  // s_task reused by the next iteration
+  }
+}
+
+// words of the task queue's synchronisation buffer for an m-column factorisation of rows rows
+size_t chol_dag_words(int m, int rows) {
+  const size_t R = (size_t)(rows + NB - 1) / NB, C = (size_t)(m + NB - 1) / NB;
+  return 8 + 2 * R * C;
+}
+
+template <class T>
+static int dense_chol_dag(T *B, int64_t ldb, int m, int rows, int *status, T *Linv_all,
+                          cudaStream_t st, int *sync) {
+  const int R = (rows + NB - 1) / NB, C = (m + NB - 1) / NB;
+  // tickets: POTRF(0), TRSM(2.., 0), then the iterations k = 0 .. C-2
+  const int lo0 = C > 1 ? 2 : 1;
+  int64_t total = 1 + (R > lo0 ? R - lo0 : 0);
+  for (int64_t k = 0; k + 1 < C; ++k) {
+    const int64_t a = k + 2, u = C - a, lo = dag_trsm_lo(k, C);
+    total += DAG_TS + 1 + (R - k - 2) + (a < C ? u * R - (u * (a + C - 1)) / 2 : 0) +
+             (R > lo ? R - lo : 0);
+  }
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+  }
+  const size_t smem = std::max(sizeof(PotrfSmem<T>), (size_t)2 * NB * (NB + 1) * sizeof(T));
+  cudaMemsetAsync(sync, 0, chol_dag_words(m, rows) * sizeof(int), st);
+  DagSync q{sync, sync + 1, sync + 8, sync + 8 + (size_t)R * C, C};
+  // two CTAs per SM: one loads or waits while the other computes
+  const int grid = (int)std::min<int64_t>(2 * (int64_t)nsm, total);
+  k_chol_dag<T><<<grid, DAG_THREADS, smem, st>>>(B, ldb, m, rows, status, Linv_all, q, total);
+  return 2;
+}
+
 // Right-looking blocked Cholesky of the leading m columns of a rows x m matrix (rows = m + 1 for
 // the bordered right-hand side, m otherwise) with lookahead: on st (the critical path) panel k is factored (potrf), its rows below are solved
 // (trsm) and its update is applied to block column k+1; the rest of its update (block columns
@@ -387,6 +759,10 @@ template <class T>
 static int dense_chol_cached(T *B, int64_t ldb, int m, int rows, int *status, T *Linv,
                              cudaStream_t st_caller, CholStreams *cs) {
   if (!cs) return dense_chol<T>(B, ldb, m, rows, status, Linv, st_caller, nullptr);
+  if constexpr (std::is_same<T, double>::value) {
+    if (cs->dag_sync && cs->dag_words >= chol_dag_words(m, rows))
+      return dense_chol_dag<T>(B, ldb, m, rows, status, Linv, st_caller, cs->dag_sync);
+  }
   cudaEventRecord(cs->entry, st_caller);
   cudaStreamWaitEvent(cs->chain, cs->entry, 0);
   const int nl = dense_chol_graph<T>(B, ldb, m, rows, status, Linv, cs->chain, cs);

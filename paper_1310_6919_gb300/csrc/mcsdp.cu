@@ -568,6 +568,7 @@ void plan_workspace(mcsdp_ctx *c) {
   plan_buf(c, cur, "alpha_c", NCAND * 8);
   plan_buf(c, cur, "alpha_r", (size_t)S.ns * 8);
   plan_buf(c, cur, "scal", 16 * 8);
+  plan_buf(c, cur, "chol_sync", chol_dag_words(m, m + 1) * 4);
   plan_buf(c, cur, "status", (8 + NCAND) * 4);  // [0..3] phases, [4] FP32 factor, [8..8+NCAND) dual candidates
   {
     const bool mx = c->opt.precision == 1;
@@ -703,6 +704,8 @@ void bind_pointers(mcsdp_ctx *c) {
   c->alpha_r = wsp<double>(c, "alpha_r");
   c->scal = wsp<double>(c, "scal");
   c->status = wsp<int>(c, "status");
+  c->cs.dag_sync = wsp<int>(c, "chol_sync");
+  c->cs.dag_words = chol_dag_words(c->S.m, c->S.m + 1);
   c->B32 = wsp<float>(c, "B32");
   c->Linv32 = wsp<float>(c, "Linv32");
   c->gref = wsp<double>(c, "gref");
@@ -1125,6 +1128,7 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
   CUDA_TRY(c, cudaMemcpyAsync(st, c->status, 4 * 4, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   prof_flush(c);
+  if (st[2] & ST_TIMEOUT) return fail(c, MCSDP_ERR_TIMEOUT, "SCM factorisation: a bounded wait gave up");
   if (st[2] & ST_NOT_PD) return fail(c, MCSDP_ERR_NOT_PD, "Schur complement matrix is not positive definite");
   o.ap = sc[5];
   if (lo <= 0.0) return fail(c, MCSDP_ERR_STALL, "dual step length collapsed");
@@ -1813,7 +1817,8 @@ mcsdp_status mcsdp_backward(mcsdp_ctx *c, const double *gX, const double *gz, do
       int st[4];
       s = read_status(c, st, 4);
       if (s) return s;
-      if (st[2] & ST_NOT_PD) return fail(c, MCSDP_ERR_NOT_PD, "Schur complement matrix is not positive definite");
+      if (st[2] & ST_TIMEOUT) return fail(c, MCSDP_ERR_TIMEOUT, "SCM factorisation: a bounded wait gave up");
+  if (st[2] & ST_NOT_PD) return fail(c, MCSDP_ERR_NOT_PD, "Schur complement matrix is not positive definite");
       if (!(st[0] & ST_NOT_PD)) break;
       t *= 0.5;
       if (h > 40) return fail(c, MCSDP_ERR_STALL, "centring step collapsed");
@@ -1853,6 +1858,7 @@ mcsdp_status mcsdp_backward(mcsdp_ctx *c, const double *gX, const double *gz, do
   int st[4];
   s = read_status(c, st, 4);
   if (s) return s;
+  if (st[2] & ST_TIMEOUT) return fail(c, MCSDP_ERR_TIMEOUT, "SCM factorisation: a bounded wait gave up");
   if (st[2] & ST_NOT_PD) return fail(c, MCSDP_ERR_NOT_PD, "Schur complement matrix is not positive definite");
   return MCSDP_OK;
 }

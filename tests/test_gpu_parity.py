@@ -95,6 +95,20 @@ def test_newton_step_matches_oracle(mk):
     assert st["alpha_d"] >= ref["alpha_d"] * (1 - 2e-3)
 
 
+@pytest.mark.parametrize("shape", [(8, 8), (16, 16), (11, 9), (7, 5)],
+                         ids=["m64", "m256", "m99", "m35"])
+def test_newton_step_scm_factor_tile_edges(shape):
+    """The SCM factorisation runs on 32 x 32 tiles of the (m + 1) x m bordered matrix: m a
+    multiple of 32 puts the right-hand-side row in a tile row of its own (m = 64, 256; eight
+    column tiles for 256), m = 99 and 35 leave ragged last tiles."""
+    from tests.gpu_helpers import Case, rel_err
+    c = Case(lattice_maxcut(*shape, seed=2))
+    Xbar, z = c.random_iterate(3)
+    st = c.P.newton_step(c.to_layout(Xbar), torch.tensor(z, device="cuda:0"))
+    ref = pdipm.mc_newton_step(c.A, c.inst.b, c.perm, c.cliques, Xbar, z)
+    assert rel_err(st["dz"].cpu().numpy(), ref["dz"]) < 1e-8
+
+
 def _solve(inst, **opts):
     from paper_1310_6919_gb300 import Problem
     P = Problem.from_instance(inst, device=0, **opts)
