@@ -42,48 +42,20 @@ struct PotrfSmem {
   unsigned char pr[NB * (NB - 1) / 2], pc[NB * (NB - 1) / 2];  // packed e -> (row, column)
 };
 
-// CG: read B through L2 only (the task-queue factorisation, whose tiles other SMs write).
-// hp > 0: first apply the previous panel's update to the tile row, A(k0.., k0..) -=
-// P P^T with P = B[k0 .. k0 + hp, k0 - NB .. k0) (the already solved tile left of it); rows
-// nb .. hp-1 of the tile row (the right-hand-side row) are updated in B.
+// CG: read B through L2 only (the task-queue factorisation, whose tiles other SMs write)
 template <class T, bool CG>
 __device__ __forceinline__ void potrf_block(T *B, int64_t ldb, int k0, int nb, int *status,
-                                            T *Linv, PotrfSmem<T> &sm, int hp = 0) {
+                                            T *Linv, PotrfSmem<T> &sm) {
   constexpr int LD = NB + 1;
   constexpr int NBULK = 224;  // warps 1-7
   constexpr int SLOTS = 3;    // elements per bulk thread and step: at most 496 <= 3 x 224
   T *A = sm.A, *U = sm.U, *V = sm.V, *rd = sm.rd, *dd = sm.dd;
   unsigned char *pr = sm.pr, *pc = sm.pc;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (hp > 0) {
-    T *P = V;  // P[i][l], staged in the inverse's array before that is set up
-    for (int idx = tid; idx < NB * NB; idx += 256) {
-      const int i = idx % NB, l = idx / NB;
-      P[i * LD + l] = i < hp ? __ldcg(B + (k0 + i) + (int64_t)(k0 - NB + l) * ldb) : T(0);
-    }
-    __syncthreads();
-    for (int idx = tid; idx < NB * NB; idx += 256) {
-      const int i = idx % NB, j = idx / NB;
-      if (i >= j && i < hp && j < nb) {
-        T *src = B + (k0 + i) + (int64_t)(k0 + j) * ldb;
-        T s0 = T(0), s1 = T(0);
-#pragma unroll 8
-        for (int l = 0; l < NB; l += 2) {
-          s0 = fma(P[i * LD + l], P[j * LD + l], s0);
-          s1 = fma(P[i * LD + l + 1], P[j * LD + l + 1], s1);
-        }
-        const T v = __ldcg(src) - (s0 + s1);
-        if (i < nb) A[i * LD + j] = v;
-        else *src = v;  // the right-hand-side row
-      }
-    }
-    __syncthreads();
-  }
   for (int idx = tid; idx < NB * NB; idx += 256) {
     const int i = idx % NB, j = idx / NB;
     const T *src = B + (k0 + i) + (int64_t)(k0 + j) * ldb;
-    if (hp == 0 || !(i >= j && i < nb && j < nb))
-      A[i * LD + j] = (i >= j && i < nb && j < nb) ? (CG ? __ldcg(src) : *src) : T(0);
+    A[i * LD + j] = (i >= j && i < nb && j < nb) ? (CG ? __ldcg(src) : *src) : T(0);
     V[i * LD + j] = (i == j) ? T(1) : T(0);
     U[i * LD + j] = (i == j) ? T(1) : T(0);
   }
@@ -363,16 +335,16 @@ static void launch_syrk(T *B, int64_t ldb, int k0, int nb, int c_lo, int c_hi, i
 //   POTRF(k)      diagonal tile k: factor and inverse (potrf_block)
 //   TRSM(i, k)    tile (i, k), i > k: L(i, k) = A(i, k) L(k, k)^{-T}
 //   UPD(i, j, k)  tile (i, j), i >= j > k: A(i, j) -= L(i, k) L(j, k)^T (lower part if i == j)
-// The chain from one diagonal tile to the next is shortened: TRSM(p, p-1) is split over eight
-// tasks TS(p, s) of four rows each, and NEXT(p) = UPD(p, p, p-1) folded into the loading of
-// POTRF(p) (the right-hand-side row of the tile row updated with it).
+// The chain from one diagonal tile to the next is what bounds the last panels, so its tiles are
+// split over several CTAs: TRSM(p, p-1) over eight tasks TS(p, s) of four rows, UPD(p, p, p-1)
+// over eight tasks UD(p, s) of four rows, then NEXT(p) = POTRF(p).
 // CTAs take tickets from one counter; ticket order puts every dependency before its dependants:
 //   POTRF(0), TRSM(2..R-1, 0), then for k = 0 .. C-2:
-//     TS(k+1, 0..7), NEXT(k+1),
-//     UPD(k+2.., k+1, k)             the rest of the next column,
-//     UPD(i, j, k) for j >= k+2     the rest of panel k's update, with the block
-//     TRSM(k+3.., k+1)              placed DAG_DEFER tickets into it, so that NEXT(k+1) has
-//                                   normally finished before a CTA takes one of them.
+//     TS(k+1, 0..7), UD(k+1, 0..7), NEXT(k+1),
+//     UPD(i, j, k) for j >= k+2     the rest of panel k's update, with the blocks
+//     UPD(k+2.., k+1, k)            (the rest of the next column) placed DAG_DEFER_COL and
+//     TRSM(k+3.., k+1)              DAG_DEFER_TRSM tickets into it, so that what they wait for
+//                                   (TS(k+1, .), NEXT(k+1)) has normally finished by then.
 // A CTA holding the smallest unfinished ticket finds all its dependencies done, so the queue
 // always progresses whatever the residency (no co-scheduling needed).  Per tile (i, j) the host
 // zeroes upd[i][j] (updates applied; UPD(i, j, k) waits for k of them, which also serialises
@@ -383,7 +355,8 @@ static void launch_syrk(T *B, int64_t ldb, int k0, int nb, int c_lo, int c_hi, i
 // launch gaps, no half-empty last waves per panel) while the next column's chain runs ahead.
 constexpr int DAG_THREADS = 256;
 constexpr int64_t DAG_SPIN_LIMIT = 1 << 22;  // polls per wait (about four seconds with backoff)
-constexpr int64_t DAG_DEFER = 512;           // tickets of panel k's rest before TRSM(., k+1)
+constexpr int64_t DAG_DEFER_COL = 128;   // tickets of panel k's rest before UPD(., k+1, k)
+constexpr int64_t DAG_DEFER_TRSM = 512;  // and before TRSM(., k+1)
 
 struct DagSync {
   int *ticket, *abort, *upd, *fin;
@@ -396,11 +369,17 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
   return v;
 }
 
-// thread 0: wait until *flag >= target; false on abort or timeout (which it raises)
-__device__ bool dag_wait(const int *flag, int target, const DagSync &q, int *status) {
+// thread 0: wait until every *f[x] >= tg[x] (x < n), the flags polled together; false on abort
+// or timeout (which it raises)
+__device__ bool dag_wait_all(const int *const *f, const int *tg, int n, const DagSync &q,
+                             int *status) {
   unsigned ns = 32;
   for (int64_t it = 0; it < DAG_SPIN_LIMIT; ++it) {
-    if (ld_acquire(flag) >= target) return true;
+    int v[3];
+    for (int x = 0; x < n; ++x) v[x] = ld_acquire(f[x]);
+    bool ready = true;
+    for (int x = 0; x < n; ++x) ready = ready && v[x] >= tg[x];
+    if (ready) return true;
     if (ld_acquire(q.abort)) return false;
     __nanosleep(ns);
     if (ns < 1024) ns <<= 1;
@@ -421,10 +400,11 @@ __device__ __host__ __forceinline__ int64_t dag_trsm_lo(int64_t k, int64_t C) {
   return k + 2 < C ? k + 3 : k + 2;
 }
 constexpr int DAG_TS = NB / 4;  // TS tasks per chain step
-// tickets of iteration k (k = 0 .. C-2): TS, NEXT, the next column's rest, panel k's rest, TRSMs
+// tickets of iteration k (k = 0 .. C-2): TS, UD, NEXT, the next column's rest, panel k's rest,
+// TRSMs
 __device__ __forceinline__ int64_t dag_iter_size(int64_t k, int64_t R, int64_t C) {
   const int64_t lo = dag_trsm_lo(k, C);
-  return DAG_TS + 1 + (R - k - 2) + dag_tail(k + 2, R, C) + (R > lo ? R - lo : 0);
+  return 2 * DAG_TS + 1 + (R - k - 2) + dag_tail(k + 2, R, C) + (R > lo ? R - lo : 0);
 }
 // completions that make tile (i, k) final: eight TS tasks for a tile left of a diagonal tile
 __device__ __forceinline__ int dag_fin_target(int i, int k, int C) {
@@ -497,6 +477,39 @@ __device__ void dag_trsm4(T *B, int64_t ldb, int i0, int h, int k0, int ncl, con
   }
 }
 
+// UD(p, s): rows r0 .. r0 + h (h <= 4) of the diagonal tile at (k0, k0) (with the
+// right-hand-side row when it lies in that tile row), columns c <= r, c < nb, minus
+// L(p, p-1)[r] . L(p, p-1)[c] (the previous panel, full width); two threads per output.
+template <class T>
+__device__ void dag_upd4(T *B, int64_t ldb, int k0, int r0, int h, int nb, T *sm) {
+  constexpr int LD = NB + 1;
+  T *Lr = sm, *Lc = sm + 4 * LD;  // Lr[r][l] rows r0.., Lc[c][l] rows k0..
+  const int tid = threadIdx.x;
+  const int q0 = k0 - NB;
+  if (tid < 4 * NB) {
+    const int r = tid & 3, l = tid >> 2;
+    Lr[r * LD + l] = r < h ? __ldcg(B + (k0 + r0 + r) + (int64_t)(q0 + l) * ldb) : T(0);
+  }
+  for (int idx = tid; idx < NB * NB; idx += DAG_THREADS) {
+    const int c = idx & (NB - 1), l = idx / NB;
+    Lc[c * LD + l] = c < nb ? __ldcg(B + (k0 + c) + (int64_t)(q0 + l) * ldb) : T(0);
+  }
+  __syncthreads();
+  const int o = tid >> 1, half = tid & 1, r = o >> 5, c = o & (NB - 1);
+  T a0 = T(0), a1 = T(0);
+#pragma unroll
+  for (int l = half * 16; l < half * 16 + 16; l += 2) {
+    a0 = fma(Lr[r * LD + l], Lc[c * LD + l], a0);
+    a1 = fma(Lr[r * LD + l + 1], Lc[c * LD + l + 1], a1);
+  }
+  T acc = a0 + a1;
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  if (half == 0 && r < h && c < nb && c <= r0 + r) {
+    T *dst = B + (k0 + r0 + r) + (int64_t)(k0 + c) * ldb;
+    *dst = __ldcg(dst) - acc;
+  }
+}
+
 // UPD(i, j, k): C rows [i0, i0 + h) x columns [j0, j0 + w) -= L(i, k) L(j, k)^T, the lower part
 // only on a diagonal tile (diag).  2 x 2 outputs per thread, K = nb.
 template <class T>
@@ -556,7 +569,7 @@ __global__ void __launch_bounds__(DAG_THREADS, 2)
   while (t < total) {
     if (tid == 0) s_task[1] = atomicAdd(q.ticket, 1);  // the next ticket, fetched early
     // decode t into (type, i, j, k): 0 POTRF(0), 1 TRSM(i, k), 2 UPD(i, j, k), 3 NEXT(k),
-    // 4 TS(k, s = tj)
+    // 4 TS(k, s = tj), 5 UD(k, s = tj)
     int type, ti, tj, tk;
     if (t == 0) {
       type = 0; ti = tj = tk = 0;
@@ -571,24 +584,36 @@ __global__ void __launch_bounds__(DAG_THREADS, 2)
       const int k = kcur, n1 = R - k - 2;
       if (e < DAG_TS) {
         type = 4; ti = tk = k + 1; tj = (int)e;
+      } else if ((e -= DAG_TS) < DAG_TS) {
+        type = 5; ti = tk = k + 1; tj = (int)e;
       } else if ((e -= DAG_TS) == 0) {
         type = 3; ti = tj = tk = k + 1;
-      } else if ((e -= 1) < n1) {
-        type = 2; ti = k + 2 + (int)e; tj = k + 1; tk = k;
       } else {
-        e -= n1;
+        e -= 1;
+        // body: rest[0, dc) | next column (n1) | rest[dc, dt) | TRSM block (ntr) | rest[dt, ..)
         const int64_t rest = dag_tail(k + 2, R, C), lo = dag_trsm_lo(k, C);
-        const int64_t ntr = R > lo ? R - lo : 0, defer = rest < DAG_DEFER ? rest : DAG_DEFER;
-        if (e >= defer && e < defer + ntr) {
-          type = 1; ti = (int)(lo + e - defer); tj = tk = k + 1;
+        const int64_t ntr = R > lo ? R - lo : 0;
+        const int64_t dc = rest < DAG_DEFER_COL ? rest : DAG_DEFER_COL;
+        const int64_t dt = rest < DAG_DEFER_TRSM ? rest : DAG_DEFER_TRSM;
+        int64_t ri = -1;
+        if (e < dc) {
+          ri = e;
+        } else if (e < dc + n1) {
+          type = 2; ti = k + 2 + (int)(e - dc); tj = k + 1; tk = k;
+        } else if (e < dt + n1) {
+          ri = e - n1;
+        } else if (e < dt + n1 + ntr) {
+          type = 1; ti = (int)(lo + e - dt - n1); tj = tk = k + 1;
         } else {
-          if (e >= defer + ntr) e -= ntr;
+          ri = e - n1 - ntr;
+        }
+        if (ri >= 0) {
           int j = k + 2;
-          while (j < C && e >= R - j) {
-            e -= R - j;
+          while (j < C && ri >= R - j) {
+            ri -= R - j;
             ++j;
           }
-          type = 2; ti = j + (int)e; tj = j; tk = k;  // j < C for every ticket below total
+          type = 2; ti = j + (int)ri; tj = j; tk = k;  // j < C for every ticket below total
         }
       }
     }
@@ -596,22 +621,30 @@ __global__ void __launch_bounds__(DAG_THREADS, 2)
     bool ok = true;
     if (tid == 0) {
       const int C_ = q.C;
-      if (type == 0) {
-        ok = true;  // POTRF(0): nothing before it
-      } else if (type == 4) {  // TS(p, s): rows of L(p, p-1)
-        ok = dag_wait(q.fin + (tk - 1) * C_ + (tk - 1), 1, q, status) &&
-             dag_wait(q.upd + tk * C_ + (tk - 1), tk - 1, q, status);
-      } else if (type == 3) {  // NEXT(p): UPD(p, p, p-1) and POTRF(p)
-        ok = dag_wait(q.fin + tk * C_ + (tk - 1), DAG_TS, q, status) &&
-             dag_wait(q.upd + tk * C_ + tk, tk - 1, q, status);
+      const int *f[3];
+      int tg[3], n = 0;
+      if (type == 4) {  // TS(p, s): rows of L(p, p-1)
+        f[0] = q.fin + (tk - 1) * C_ + (tk - 1); tg[0] = 1;
+        f[1] = q.upd + tk * C_ + (tk - 1); tg[1] = tk - 1;
+        n = 2;
+      } else if (type == 5) {  // UD(p, s): rows of the diagonal tile's update by panel p-1
+        f[0] = q.fin + tk * C_ + (tk - 1); tg[0] = DAG_TS;
+        f[1] = q.upd + tk * C_ + tk; tg[1] = tk - 1;
+        n = 2;
+      } else if (type == 3) {  // NEXT(p) = POTRF(p): every UD(p, .) done
+        f[0] = q.upd + tk * C_ + tk; tg[0] = tk - 1 + DAG_TS;
+        n = 1;
       } else if (type == 1) {
-        ok = dag_wait(q.fin + tk * C_ + tk, 1, q, status) &&
-             dag_wait(q.upd + ti * C_ + tk, tk, q, status);
-      } else {
-        ok = dag_wait(q.fin + ti * C_ + tk, dag_fin_target(ti, tk, C_), q, status) &&
-             dag_wait(q.fin + tj * C_ + tk, dag_fin_target(tj, tk, C_), q, status) &&
-             dag_wait(q.upd + ti * C_ + tj, tk, q, status);
-      }
+        f[0] = q.fin + tk * C_ + tk; tg[0] = 1;
+        f[1] = q.upd + ti * C_ + tk; tg[1] = tk;
+        n = 2;
+      } else if (type == 2) {
+        f[0] = q.fin + ti * C_ + tk; tg[0] = dag_fin_target(ti, tk, C_);
+        f[1] = q.fin + tj * C_ + tk; tg[1] = dag_fin_target(tj, tk, C_);
+        f[2] = q.upd + ti * C_ + tj; tg[2] = tk;
+        n = 3;
+      }  // type 0, POTRF(0): nothing before it
+      ok = n == 0 || dag_wait_all(f, tg, n, q, status);
       s_task[2] = ok ? 1 : 0;
     }
     __syncthreads();
@@ -620,11 +653,12 @@ __global__ void __launch_bounds__(DAG_THREADS, 2)
     if (type == 4) {
       const int i0 = k0 + 4 * tj, h = max(0, min(4, min(rows, k0 + NB) - i0));
       dag_trsm4<T>(B, ldb, i0, h, k0 - NB, m, Linv_all + (int64_t)(tk - 1) * NB * NB, sm);
+    } else if (type == 5) {
+      const int r0 = 4 * tj, h = max(0, min(4, min(rows, k0 + NB) - k0 - r0));
+      dag_upd4<T>(B, ldb, k0, r0, h, nb, sm);
     } else if (type == 0 || type == 3) {
       T *Lk = Linv_all + (int64_t)tk * NB * NB;
-      // NEXT: the previous panel's update of this tile row is folded into the loading
-      potrf_block<T, true>(B, ldb, k0, nb, status, Lk, *reinterpret_cast<PotrfSmem<T> *>(sm),
-                           type == 3 ? min(NB, rows - k0) : 0);
+      potrf_block<T, true>(B, ldb, k0, nb, status, Lk, *reinterpret_cast<PotrfSmem<T> *>(sm));
       // when m is not a multiple of NB the last diagonal tile's row block also holds the
       // right-hand-side row m: solve it here (no TRSM task covers rows of a diagonal tile)
       const int r0 = k0 + nb, r1 = min(rows, k0 + NB);
@@ -644,6 +678,7 @@ __global__ void __launch_bounds__(DAG_THREADS, 2)
     if (tid == 0) {
       __threadfence();
       if (type == 2) atomicAdd(q.upd + ti * q.C + tj, 1);
+      else if (type == 5) atomicAdd(q.upd + tk * q.C + tk, 1);        // one of DAG_TS on (p, p)
       else if (type == 4) atomicAdd(q.fin + tk * q.C + (tk - 1), 1);  // one of DAG_TS
       else atomicAdd(q.fin + ti * q.C + tk, 1);  // POTRF / NEXT: fin[p][p]; TRSM: fin[i][k]
     }
@@ -667,7 +702,7 @@ static int dense_chol_dag(T *B, int64_t ldb, int m, int rows, int *status, T *Li
   int64_t total = 1 + (R > lo0 ? R - lo0 : 0);
   for (int64_t k = 0; k + 1 < C; ++k) {
     const int64_t a = k + 2, u = C - a, lo = dag_trsm_lo(k, C);
-    total += DAG_TS + 1 + (R - k - 2) + (a < C ? u * R - (u * (a + C - 1)) / 2 : 0) +
+    total += 2 * DAG_TS + 1 + (R - k - 2) + (a < C ? u * R - (u * (a + C - 1)) / 2 : 0) +
              (R > lo ? R - lo : 0);
   }
   static int nsm = 0;
