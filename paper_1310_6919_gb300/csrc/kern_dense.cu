@@ -355,8 +355,8 @@ static void launch_syrk(T *B, int64_t ldb, int k0, int nb, int c_lo, int c_hi, i
 // launch gaps, no half-empty last waves per panel) while the next column's chain runs ahead.
 constexpr int DAG_THREADS = 256;
 constexpr int64_t DAG_SPIN_LIMIT = 1 << 22;  // polls per wait (about four seconds with backoff)
-constexpr int64_t DAG_DEFER_COL = 128;   // tickets of panel k's rest before UPD(., k+1, k)
-constexpr int64_t DAG_DEFER_TRSM = 512;  // and before TRSM(., k+1)
+constexpr int64_t DAG_DEFER_COL = 256;   // tickets of panel k's rest before UPD(., k+1, k)
+constexpr int64_t DAG_DEFER_TRSM = 768;  // and before TRSM(., k+1)
 
 struct DagSync {
   int *ticket, *abort, *upd, *fin;
