@@ -81,7 +81,10 @@ typedef struct {
                             FP64 throughout once the relative gap falls below mixed_gap, the
                             refinement stalls, the FP32 factorisation breaks down or the primal
                             residual grows (m <= 50000). */
-  int64_t timeout_cycles;/* bound on any device spin-wait; 0 = library default */
+  int64_t timeout_cycles;/* bound on any device spin-wait, in SM clock cycles (the SCM
+                          * factorisation's task dependencies); <= 0 = library default (2^32).
+                          * A wait that runs out aborts the factorisation: the call returns
+                          * MCSDP_ERR_TIMEOUT and the context stays usable */
   int32_t device;        /* CUDA device ordinal, or -1 for host-only */
   int32_t verbose;       /* 1 = one log line per iteration on stderr */
   int32_t panel_max;     /* max columns per SCM panel group (<= 96); 0 = default 80 */

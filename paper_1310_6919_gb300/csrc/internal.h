@@ -241,6 +241,7 @@ struct CholStreams {
   // synchronisation words of the FP64 task-queue factorisation (nullptr: launch per panel)
   int *dag_sync = nullptr;
   size_t dag_words = 0;
+  long long dag_budget = 0;  // cycles per device wait (options.timeout_cycles; 0 = default)
   cudaStream_t chain = nullptr, rest = nullptr;
   cudaEvent_t next[2] = {}, rest_ev[2] = {}, fork = nullptr, chain_done = nullptr;
   cudaEvent_t entry = nullptr, exit = nullptr;  // caller's stream -> chain stream -> caller's

@@ -354,14 +354,16 @@ static void launch_syrk(T *B, int64_t ldb, int k0, int nb, int c_lo, int c_hi, i
 // Against the launch-per-panel form this keeps the trailing tiles flowing across panels (no
 // launch gaps, no half-empty last waves per panel) while the next column's chain runs ahead.
 constexpr int DAG_THREADS = 256;
-constexpr int64_t DAG_SPIN_LIMIT = 1 << 22;  // polls per wait (about four seconds with backoff)
+constexpr int64_t DAG_SPIN_LIMIT = 1 << 23;  // polls per wait (a few seconds with backoff)
 constexpr int64_t DAG_DEFER_COL = 256;   // tickets of panel k's rest before UPD(., k+1, k)
 constexpr int64_t DAG_DEFER_TRSM = 768;  // and before TRSM(., k+1)
 
 struct DagSync {
   int *ticket, *abort, *upd, *fin;
   int C;
+  long long budget;  // SM clock cycles one wait may take before it gives up
 };
+constexpr long long DAG_DEFAULT_BUDGET = 1ll << 32;  // about two seconds at 2 GHz
 
 __device__ __forceinline__ int ld_acquire(const int *p) {
   int v;
@@ -370,19 +372,22 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
 }
 
 // thread 0: wait until every *f[x] >= tg[x] (x < n), the flags polled together; false on abort
-// or timeout (which it raises)
+// or once the wait has taken q.budget cycles (or DAG_SPIN_LIMIT polls), which raises the abort
+// word and ST_TIMEOUT
 __device__ bool dag_wait_all(const int *const *f, const int *tg, int n, const DagSync &q,
                              int *status) {
   unsigned ns = 32;
-  for (int64_t it = 0; it < DAG_SPIN_LIMIT; ++it) {
+  const long long t0 = clock64();
+  for (int64_t it = 0;; ++it) {
     int v[3];
     for (int x = 0; x < n; ++x) v[x] = ld_acquire(f[x]);
     bool ready = true;
     for (int x = 0; x < n; ++x) ready = ready && v[x] >= tg[x];
     if (ready) return true;
     if (ld_acquire(q.abort)) return false;
+    if (it >= DAG_SPIN_LIMIT || clock64() - t0 > q.budget) break;
     __nanosleep(ns);
-    if (ns < 1024) ns <<= 1;
+    if (ns < 256) ns <<= 1;
   }
   atomicExch(q.abort, 1);
   atomicOr(status, ST_TIMEOUT);
@@ -695,7 +700,7 @@ size_t chol_dag_words(int m, int rows) {
 
 template <class T>
 static int dense_chol_dag(T *B, int64_t ldb, int m, int rows, int *status, T *Linv_all,
-                          cudaStream_t st, int *sync) {
+                          cudaStream_t st, int *sync, long long budget) {
   const int R = (rows + NB - 1) / NB, C = (m + NB - 1) / NB;
   // tickets: POTRF(0), TRSM(2.., 0), then the iterations k = 0 .. C-2
   const int lo0 = C > 1 ? 2 : 1;
@@ -714,7 +719,8 @@ static int dense_chol_dag(T *B, int64_t ldb, int m, int rows, int *status, T *Li
   }
   const size_t smem = std::max(sizeof(PotrfSmem<T>), (size_t)2 * NB * (NB + 1) * sizeof(T));
   cudaMemsetAsync(sync, 0, chol_dag_words(m, rows) * sizeof(int), st);
-  DagSync q{sync, sync + 1, sync + 8, sync + 8 + (size_t)R * C, C};
+  DagSync q{sync, sync + 1, sync + 8, sync + 8 + (size_t)R * C, C,
+            budget > 0 ? budget : DAG_DEFAULT_BUDGET};
   // two CTAs per SM: one loads or waits while the other computes
   const int grid = (int)std::min<int64_t>(2 * (int64_t)nsm, total);
   k_chol_dag<T><<<grid, DAG_THREADS, smem, st>>>(B, ldb, m, rows, status, Linv_all, q, total);
@@ -796,7 +802,8 @@ static int dense_chol_cached(T *B, int64_t ldb, int m, int rows, int *status, T 
   if (!cs) return dense_chol<T>(B, ldb, m, rows, status, Linv, st_caller, nullptr);
   if constexpr (std::is_same<T, double>::value) {
     if (cs->dag_sync && cs->dag_words >= chol_dag_words(m, rows))
-      return dense_chol_dag<T>(B, ldb, m, rows, status, Linv, st_caller, cs->dag_sync);
+      return dense_chol_dag<T>(B, ldb, m, rows, status, Linv, st_caller, cs->dag_sync,
+                               cs->dag_budget);
   }
   cudaEventRecord(cs->entry, st_caller);
   cudaStreamWaitEvent(cs->chain, cs->entry, 0);

@@ -706,6 +706,7 @@ void bind_pointers(mcsdp_ctx *c) {
   c->status = wsp<int>(c, "status");
   c->cs.dag_sync = wsp<int>(c, "chol_sync");
   c->cs.dag_words = chol_dag_words(c->S.m, c->S.m + 1);
+  c->cs.dag_budget = c->opt.timeout_cycles;
   c->B32 = wsp<float>(c, "B32");
   c->Linv32 = wsp<float>(c, "Linv32");
   c->gref = wsp<double>(c, "gref");
