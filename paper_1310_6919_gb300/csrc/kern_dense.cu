@@ -800,6 +800,8 @@ template <class T>
 static int dense_chol_cached(T *B, int64_t ldb, int m, int rows, int *status, T *Linv,
                              cudaStream_t st_caller, CholStreams *cs) {
   if (!cs) return dense_chol<T>(B, ldb, m, rows, status, Linv, st_caller, nullptr);
+  // FP64: the task queue.  FP32 keeps the launch per panel (graph-captured): its tiles take a
+  // fraction of a microsecond, so the queue's per-task overheads dominate (measured slower).
   if constexpr (std::is_same<T, double>::value) {
     if (cs->dag_sync && cs->dag_words >= chol_dag_words(m, rows))
       return dense_chol_dag<T>(B, ldb, m, rows, status, Linv, st_caller, cs->dag_sync,
