@@ -339,12 +339,14 @@ static void launch_syrk(T *B, int64_t ldb, int k0, int nb, int c_lo, int c_hi, i
 // split over several CTAs: TRSM(p, p-1) over eight tasks TS(p, s) of four rows, UPD(p, p, p-1)
 // over eight tasks UD(p, s) of four rows, then NEXT(p) = POTRF(p).
 // CTAs take tickets from one counter; ticket order puts every dependency before its dependants:
-//   POTRF(0), TRSM(2..R-1, 0), then for k = 0 .. C-2:
-//     TS(k+1, 0..7), UD(k+1, 0..7), NEXT(k+1),
-//     UPD(i, j, k) for j >= k+2     the rest of panel k's update, with the blocks
-//     UPD(k+2.., k+1, k)            (the rest of the next column) placed DAG_DEFER_COL and
-//     TRSM(k+3.., k+1)              DAG_DEFER_TRSM tickets into it, so that what they wait for
-//                                   (TS(k+1, .), NEXT(k+1)) has normally finished by then.
+//   POTRF(0), TRSM(2..R-1, 0), TS(1, 0..7), UD(1, 0..7), NEXT(1), then for k = 0 .. C-2:
+//     UPD(i, j, k) for j >= k+2      the rest of panel k's update (column k+2 first), with
+//     UPD(k+2.., k+1, k)             the rest of the next column placed DAG_DEFER_COL tickets
+//                                    into it, right after it the chain step to tile k+2,
+//     TS(k+2, .), UD(k+2, .), NEXT(k+2)  which needs only UPD(k+2, k+2, k) and UPD(k+2, k+1, k)
+//                                    of this panel (so it runs one panel ahead), and
+//     TRSM(k+3.., k+1)               DAG_DEFER_TRSM tickets in, when NEXT(k+1) has normally
+//                                    finished.
 // A CTA holding the smallest unfinished ticket finds all its dependencies done, so the queue
 // always progresses whatever the residency (no co-scheduling needed).  Per tile (i, j) the host
 // zeroes upd[i][j] (updates applied; UPD(i, j, k) waits for k of them, which also serialises
@@ -355,8 +357,8 @@ static void launch_syrk(T *B, int64_t ldb, int k0, int nb, int c_lo, int c_hi, i
 // launch gaps, no half-empty last waves per panel) while the next column's chain runs ahead.
 constexpr int DAG_THREADS = 256;
 constexpr int64_t DAG_SPIN_LIMIT = 1 << 23;  // polls per wait (a few seconds with backoff)
-constexpr int64_t DAG_DEFER_COL = 256;   // tickets of panel k's rest before UPD(., k+1, k)
-constexpr int64_t DAG_DEFER_TRSM = 768;  // and before TRSM(., k+1)
+constexpr int64_t DAG_DEFER_COL = 64;    // tickets of panel k's rest before UPD(., k+1, k)
+constexpr int64_t DAG_DEFER_TRSM = 256;  // and before TRSM(., k+1)
 
 struct DagSync {
   int *ticket, *abort, *upd, *fin;
@@ -405,11 +407,15 @@ __device__ __host__ __forceinline__ int64_t dag_trsm_lo(int64_t k, int64_t C) {
   return k + 2 < C ? k + 3 : k + 2;
 }
 constexpr int DAG_TS = NB / 4;  // TS tasks per chain step
-// tickets of iteration k (k = 0 .. C-2): TS, UD, NEXT, the next column's rest, panel k's rest,
-// TRSMs
+// tickets of the chain step to diagonal tile p (TS, UD, NEXT); none past the last tile
+__device__ __host__ __forceinline__ int64_t dag_head(int64_t p, int64_t C) {
+  return p <= C - 1 ? 2 * DAG_TS + 1 : 0;
+}
+// tickets of iteration k (k = 0 .. C-2): panel k's rest, the next column's rest, the chain step
+// to tile k+2, the panel solves of column k+1
 __device__ __forceinline__ int64_t dag_iter_size(int64_t k, int64_t R, int64_t C) {
   const int64_t lo = dag_trsm_lo(k, C);
-  return 2 * DAG_TS + 1 + (R - k - 2) + dag_tail(k + 2, R, C) + (R > lo ? R - lo : 0);
+  return dag_tail(k + 2, R, C) + (R - k - 2) + dag_head(k + 2, C) + (R > lo ? R - lo : 0);
 }
 // completions that make tile (i, k) final: eight TS tasks for a tile left of a diagonal tile
 __device__ __forceinline__ int dag_fin_target(int i, int k, int C) {
@@ -565,7 +571,7 @@ __global__ void __launch_bounds__(DAG_THREADS, 2)
   const int tid = threadIdx.x;
   const int R = (rows + NB - 1) / NB, C = q.C;
   const int lo0 = C > 1 ? 2 : 1;  // first TRSM(., 0) row tile (tile (1, 0) belongs to NEXT(1))
-  const int64_t pre = 1 + (R > lo0 ? R - lo0 : 0);
+  const int64_t npre = 1 + (R > lo0 ? R - lo0 : 0), pre = npre + dag_head(1, C);
   int kcur = 0;
   int64_t kstart = pre;  // first ticket of iteration kcur
   if (tid == 0) s_task[0] = atomicAdd(q.ticket, 1);
@@ -576,10 +582,14 @@ __global__ void __launch_bounds__(DAG_THREADS, 2)
     // decode t into (type, i, j, k): 0 POTRF(0), 1 TRSM(i, k), 2 UPD(i, j, k), 3 NEXT(k),
     // 4 TS(k, s = tj), 5 UD(k, s = tj)
     int type, ti, tj, tk;
+    int hp = -1;  // chain step to tile hp, element he of its header
+    int64_t he = 0;
     if (t == 0) {
       type = 0; ti = tj = tk = 0;
-    } else if (t < pre) {
+    } else if (t < npre) {
       type = 1; ti = lo0 + t - 1; tj = tk = 0;
+    } else if (t < pre) {
+      hp = 1; he = t - npre;
     } else {
       while (kcur + 1 < C && t >= kstart + dag_iter_size(kcur, R, C)) {
         kstart += dag_iter_size(kcur, R, C);
@@ -587,39 +597,46 @@ __global__ void __launch_bounds__(DAG_THREADS, 2)
       }
       int64_t e = t - kstart;
       const int k = kcur, n1 = R - k - 2;
-      if (e < DAG_TS) {
-        type = 4; ti = tk = k + 1; tj = (int)e;
-      } else if ((e -= DAG_TS) < DAG_TS) {
-        type = 5; ti = tk = k + 1; tj = (int)e;
-      } else if ((e -= DAG_TS) == 0) {
-        type = 3; ti = tj = tk = k + 1;
+      // rest[0, dc) | next column (n1) | chain step to k+2 (nh) | rest[dc, dt) | TRSM block |
+      // rest[dt, ..): the chain step needs rest[0] = UPD(k+2, k+2, k) and the next column's
+      // UPD(k+2, k+1, k) before it, so it runs one panel ahead of the trailing work
+      const int64_t rest = dag_tail(k + 2, R, C), lo = dag_trsm_lo(k, C);
+      const int64_t ntr = R > lo ? R - lo : 0, nh = dag_head(k + 2, C);
+      int64_t dc = rest < DAG_DEFER_COL ? rest : DAG_DEFER_COL;
+      if (dc < 1 && rest > 0) dc = 1;
+      int64_t dt = rest < DAG_DEFER_TRSM ? rest : DAG_DEFER_TRSM;
+      if (dt < dc) dt = dc;
+      int64_t ri = -1;
+      if (e < dc) {
+        ri = e;
+      } else if (e < dc + n1) {
+        type = 2; ti = k + 2 + (int)(e - dc); tj = k + 1; tk = k;
+      } else if (e < dc + n1 + nh) {
+        hp = k + 2; he = e - dc - n1;
+      } else if (e < dt + n1 + nh) {
+        ri = e - n1 - nh;
+      } else if (e < dt + n1 + nh + ntr) {
+        type = 1; ti = (int)(lo + e - dt - n1 - nh); tj = tk = k + 1;
       } else {
-        e -= 1;
-        // body: rest[0, dc) | next column (n1) | rest[dc, dt) | TRSM block (ntr) | rest[dt, ..)
-        const int64_t rest = dag_tail(k + 2, R, C), lo = dag_trsm_lo(k, C);
-        const int64_t ntr = R > lo ? R - lo : 0;
-        const int64_t dc = rest < DAG_DEFER_COL ? rest : DAG_DEFER_COL;
-        const int64_t dt = rest < DAG_DEFER_TRSM ? rest : DAG_DEFER_TRSM;
-        int64_t ri = -1;
-        if (e < dc) {
-          ri = e;
-        } else if (e < dc + n1) {
-          type = 2; ti = k + 2 + (int)(e - dc); tj = k + 1; tk = k;
-        } else if (e < dt + n1) {
-          ri = e - n1;
-        } else if (e < dt + n1 + ntr) {
-          type = 1; ti = (int)(lo + e - dt - n1); tj = tk = k + 1;
-        } else {
-          ri = e - n1 - ntr;
+        ri = e - n1 - nh - ntr;
+      }
+      if (ri >= 0) {
+        int j = k + 2;
+        while (j < C && ri >= R - j) {
+          ri -= R - j;
+          ++j;
         }
-        if (ri >= 0) {
-          int j = k + 2;
-          while (j < C && ri >= R - j) {
-            ri -= R - j;
-            ++j;
-          }
-          type = 2; ti = j + (int)ri; tj = j; tk = k;  // j < C for every ticket below total
-        }
+        type = 2; ti = j + (int)ri; tj = j; tk = k;  // j < C for every ticket below total
+      }
+    }
+    if (hp >= 0) {  // TS(hp, s), UD(hp, s), NEXT(hp)
+      ti = tk = hp;
+      if (he < DAG_TS) {
+        type = 4; tj = (int)he;
+      } else if (he < 2 * DAG_TS) {
+        type = 5; tj = (int)(he - DAG_TS);
+      } else {
+        type = 3; tj = hp;
       }
     }
     // dependencies (thread 0 waits, the CTA follows)
@@ -702,12 +719,12 @@ template <class T>
 static int dense_chol_dag(T *B, int64_t ldb, int m, int rows, int *status, T *Linv_all,
                           cudaStream_t st, int *sync, long long budget) {
   const int R = (rows + NB - 1) / NB, C = (m + NB - 1) / NB;
-  // tickets: POTRF(0), TRSM(2.., 0), then the iterations k = 0 .. C-2
+  // tickets: POTRF(0), TRSM(2.., 0), the chain step to tile 1, then the iterations 0 .. C-2
   const int lo0 = C > 1 ? 2 : 1;
-  int64_t total = 1 + (R > lo0 ? R - lo0 : 0);
+  int64_t total = 1 + (R > lo0 ? R - lo0 : 0) + dag_head(1, C);
   for (int64_t k = 0; k + 1 < C; ++k) {
     const int64_t a = k + 2, u = C - a, lo = dag_trsm_lo(k, C);
-    total += 2 * DAG_TS + 1 + (R - k - 2) + (a < C ? u * R - (u * (a + C - 1)) / 2 : 0) +
+    total += (a < C ? u * R - (u * (a + C - 1)) / 2 : 0) + (R - k - 2) + dag_head(k + 2, C) +
              (R > lo ? R - lo : 0);
   }
   static int nsm = 0;
