@@ -362,10 +362,22 @@ constexpr int64_t DAG_DEFER_TRSM = 256;  // and before TRSM(., k+1)
 
 struct DagSync {
   int *ticket, *abort, *upd, *fin;
+  int *smbusy;  // per SM: 1 while a diagonal factor runs there
   int C;
   long long budget;  // SM clock cycles one wait may take before it gives up
 };
 constexpr long long DAG_DEFAULT_BUDGET = 1ll << 32;  // about two seconds at 2 GHz
+constexpr int DAG_MAX_SM = 1024;                     // words of the per-SM flags
+// The diagonal factor is the chain's longest task and FP64 issue is shared by the SM: while it
+// runs, the other CTA on its SM holds back its next panel solve or update (at most this many
+// cycles, a scheduling hint only: it then goes ahead, so it never deadlocks)
+constexpr long long DAG_YIELD_CYCLES = 100000;
+
+__device__ __forceinline__ unsigned sm_id() {
+  unsigned v;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(v));
+  return v;
+}
 
 __device__ __forceinline__ int ld_acquire(const int *p) {
   int v;
@@ -667,6 +679,14 @@ __global__ void __launch_bounds__(DAG_THREADS, 2)
         n = 3;
       }  // type 0, POTRF(0): nothing before it
       ok = n == 0 || dag_wait_all(f, tg, n, q, status);
+      const unsigned sid = sm_id() % DAG_MAX_SM;
+      if (ok && (type == 0 || type == 3)) {
+        atomicExch(q.smbusy + sid, 1);
+      } else if (ok && (type == 1 || type == 2)) {
+        const long long y0 = clock64();
+        while (ld_acquire(q.smbusy + sid) != 0 && clock64() - y0 < DAG_YIELD_CYCLES)
+          __nanosleep(128);
+      }
       s_task[2] = ok ? 1 : 0;
     }
     __syncthreads();
@@ -698,6 +718,7 @@ __global__ void __launch_bounds__(DAG_THREADS, 2)
     }
     __syncthreads();  // every store of the task issued; the next ticket visible
     if (tid == 0) {
+      if (type == 0 || type == 3) atomicExch(q.smbusy + sm_id() % DAG_MAX_SM, 0);
       __threadfence();
       if (type == 2) atomicAdd(q.upd + ti * q.C + tj, 1);
       else if (type == 5) atomicAdd(q.upd + tk * q.C + tk, 1);        // one of DAG_TS on (p, p)
@@ -712,7 +733,7 @@ __global__ void __launch_bounds__(DAG_THREADS, 2)
 // words of the task queue's synchronisation buffer for an m-column factorisation of rows rows
 size_t chol_dag_words(int m, int rows) {
   const size_t R = (size_t)(rows + NB - 1) / NB, C = (size_t)(m + NB - 1) / NB;
-  return 8 + 2 * R * C;
+  return 8 + 2 * R * C + DAG_MAX_SM;
 }
 
 template <class T>
@@ -736,7 +757,7 @@ static int dense_chol_dag(T *B, int64_t ldb, int m, int rows, int *status, T *Li
   }
   const size_t smem = std::max(sizeof(PotrfSmem<T>), (size_t)2 * NB * (NB + 1) * sizeof(T));
   cudaMemsetAsync(sync, 0, chol_dag_words(m, rows) * sizeof(int), st);
-  DagSync q{sync, sync + 1, sync + 8, sync + 8 + (size_t)R * C, C,
+  DagSync q{sync, sync + 1, sync + 8, sync + 8 + (size_t)R * C, sync + 8 + 2 * (size_t)R * C, C,
             budget > 0 ? budget : DAG_DEFAULT_BUDGET};
   // two CTAs per SM: one loads or waits while the other computes
   const int grid = (int)std::min<int64_t>(2 * (int64_t)nsm, total);
