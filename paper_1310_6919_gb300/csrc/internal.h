@@ -100,6 +100,10 @@ struct DevSym {
   const int *xch_t, *xch_ub, *xch_ue;
   const int64_t *xch_slotw, *xch_slotf;
   int64_t nslotw, nslotf;
+  // per (extra chunk x, tile of 32 right-hand sides): 1 if the partial slot holds a sum, 0 if
+  // every update of the chunk was passed over (the slot is then neither written nor read)
+  unsigned char *xvalid;
+  int xv_stride;  // tiles per chunk row of xvalid
   // first extra chunk of every target that has extra chunks, level by level
   const int *xfst;
   const UpdMeta *upd_meta;

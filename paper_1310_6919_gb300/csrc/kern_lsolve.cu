@@ -136,13 +136,14 @@ __global__ void k_lfwd_partial(DevSym S, int x0, int ntiles, const double *__res
   const int ncol = S.sn_col[t + 1] - S.sn_col[t];
   for (int c = 0; c < ncol; ++c) acc[c * 32 + lane] = 0.0;
   lfwd_pull(S, S.xch_ub[x], S.xch_ue[x], L, W + (act ? col : 0), ldw, act, acc, stg, srel, lane);
+  if (lane == 0) S.xvalid[(int64_t)x * S.xv_stride + tile] = 1;
   double *P = Pw + S.xch_slotw[x] * ldw + (act ? col : 0);
   if (act)
     for (int c = 0; c < ncol; ++c) P[(int64_t)c * ldw] = acc[c * 32 + lane];
 }
 
-// W[S_t] += sum of the partial slots of t, for every target of the level with extra update
-// chunks.  CTA = (32 columns, row c of S_t, target) x 8 chunk phases: phase p sums the chunks
+// W[S_t] += sum of the partial slots of t (those marked valid), for every target of the level
+// with extra update chunks.  CTA = (32 columns, row c of S_t, target) x 8 chunk phases: phase p sums the chunks
 // xb + p, xb + p + 8, ..., then the 8 phase sums are added in order (deterministic).
 template <class T>
 __global__ void k_lfwd_reduce(DevSym S, int f0, const T *__restrict__ Pw, T *W,
@@ -161,7 +162,8 @@ __global__ void k_lfwd_reduce(DevSym S, int f0, const T *__restrict__ Pw, T *W,
   const int xe = S.xch_end[t];
   T a = T(0);
   if (col < ncolsW)
-    for (int xx = xb + ph; xx < xe; xx += 8) a += Pw[(S.xch_slotw[xx] + c) * ldw + col];
+    for (int xx = xb + ph; xx < xe; xx += 8)
+      if (S.xvalid[(int64_t)xx * S.xv_stride + tile]) a += Pw[(S.xch_slotw[xx] + c) * ldw + col];
   part[ph][lane] = a;
   __syncthreads();
   if (ph == 0 && col < ncolsW) {
@@ -363,7 +365,7 @@ __host__ __device__ inline BwdLayout bwd_layout(int nr, int nc, int es) {
 // producer writes each chunk's (rows, columns) into its slot header, so the consumer needs no
 // update index of its own.
 template <class T>
-__device__ __forceinline__ void pull_staged(const DevSym &S, int ub, int ue, const T *L,
+__device__ __forceinline__ int pull_staged(const DevSym &S, int ub, int ue, const T *L,
                                             const T *Wc, int64_t ldw, T *acc,
                                             unsigned char *sm, const FwdLayout &lay, int cw, int npb,
                                             int lane, const LsSkip &sk, int tile) {
@@ -453,6 +455,7 @@ __device__ __forceinline__ void pull_staged(const DevSym &S, int ub, int ue, con
     __syncwarp();
     ++done;
   }
+  return chunks;  // update chunks pulled (0: every update was passed over)
 }
 
 // NW warps per CTA: NW = 1 for wide levels (many CTAs per SM already use every SM
@@ -523,10 +526,12 @@ __global__ void k_lfwd_partial2(DevSym S, int x0, int ntiles, const T *__restric
   const int ncol = S.sn_col[t + 1] - S.sn_col[t];
   T *acc = reinterpret_cast<T *>(smp + lay.acc);
   for (int c = 0; c < ncol; ++c) acc[c * 32 + lane] = T(0);
-  pull_staged(S, S.xch_ub[x], S.xch_ue[x], L, W + (act ? col : 0), ldw, acc, smp, lay, cw, npb,
-              lane, sk, tile);
+  const int pulled = pull_staged(S, S.xch_ub[x], S.xch_ue[x], L, W + (act ? col : 0), ldw, acc,
+                                 smp, lay, cw, npb, lane, sk, tile);
   cpa_wait<0>();
   __syncwarp();
+  if (lane == 0) S.xvalid[(int64_t)x * S.xv_stride + tile] = pulled > 0;
+  if (pulled == 0) return;  // nothing reached this chunk: the reduce passes the slot over
   T *P = Pw + S.xch_slotw[x] * ldw + (act ? col : 0);
   if (act)
     for (int c = 0; c < ncol; ++c) P[(int64_t)c * ldw] = acc[c * 32 + lane];

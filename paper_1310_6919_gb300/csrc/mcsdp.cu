@@ -564,6 +564,7 @@ void plan_workspace(mcsdp_ctx *c) {
   plan_buf(c, cur, "W2", (size_t)n * c->ldw * 8);
   plan_buf(c, cur, "Pw", (size_t)std::max<int64_t>(1, c->nslotw) * c->ldw * 8);
   plan_buf(c, cur, "Pf", (size_t)std::max<int64_t>(1, c->nslotf) * NCAND * 8);
+  plan_buf(c, cur, "xvalid", std::max<size_t>(1, c->xch_t.size()) * (size_t)(c->ldw / 32));
   plan_buf(c, cur, "Ncand", (size_t)NCAND * nnzL * 8);
   plan_buf(c, cur, "alpha_c", NCAND * 8);
   plan_buf(c, cur, "alpha_r", (size_t)S.ns * 8);
@@ -694,6 +695,8 @@ void bind_pointers(mcsdp_ctx *c) {
   D.xch_slotw = wsp<int64_t>(c, "xch_slotw");
   D.xch_slotf = wsp<int64_t>(c, "xch_slotf");
   D.xfst = wsp<int>(c, "xfst");
+  D.xvalid = wsp<unsigned char>(c, "xvalid");
+  D.xv_stride = (int)(c->ldw / 32);
   D.upd_meta = wsp<UpdMeta>(c, "upd_meta");
   D.cmap_ptr = wsp<int64_t>(c, "cmap_ptr");
   D.cmap_off = wsp<int64_t>(c, "cmap_off");
