@@ -362,15 +362,15 @@ constexpr int64_t DAG_DEFER_TRSM = 256;  // and before TRSM(., k+1)
 
 struct DagSync {
   int *ticket, *abort, *upd, *fin;
-  int *smbusy;  // per SM: 1 while a diagonal factor runs there
+  int *smbusy;  // per SM: 1 while a task of the diagonal chain runs there
   int C;
   long long budget;  // SM clock cycles one wait may take before it gives up
 };
 constexpr long long DAG_DEFAULT_BUDGET = 1ll << 32;  // about two seconds at 2 GHz
 constexpr int DAG_MAX_SM = 1024;                     // words of the per-SM flags
-// The diagonal factor is the chain's longest task and FP64 issue is shared by the SM: while it
-// runs, the other CTA on its SM holds back its next panel solve or update (at most this many
-// cycles, a scheduling hint only: it then goes ahead, so it never deadlocks)
+// The chain's tasks (TS, UD, the diagonal factor) bound the last panels and FP64 issue is shared
+// by the SM: while one runs, the other CTA on its SM holds back its next panel solve or update
+// (at most this many cycles, a scheduling hint only: it then goes ahead, so it never deadlocks)
 constexpr long long DAG_YIELD_CYCLES = 100000;
 
 __device__ __forceinline__ unsigned sm_id() {
@@ -680,7 +680,7 @@ __global__ void __launch_bounds__(DAG_THREADS, 2)
       }  // type 0, POTRF(0): nothing before it
       ok = n == 0 || dag_wait_all(f, tg, n, q, status);
       const unsigned sid = sm_id() % DAG_MAX_SM;
-      if (ok && (type == 0 || type == 3)) {
+      if (ok && (type == 0 || type == 3 || type == 4 || type == 5)) {  // the chain's tasks
         atomicExch(q.smbusy + sid, 1);
       } else if (ok && (type == 1 || type == 2)) {
         const long long y0 = clock64();
@@ -718,7 +718,7 @@ __global__ void __launch_bounds__(DAG_THREADS, 2)
     }
     __syncthreads();  // every store of the task issued; the next ticket visible
     if (tid == 0) {
-      if (type == 0 || type == 3) atomicExch(q.smbusy + sm_id() % DAG_MAX_SM, 0);
+      if (type == 0 || type >= 3) atomicExch(q.smbusy + sm_id() % DAG_MAX_SM, 0);
       __threadfence();
       if (type == 2) atomicAdd(q.upd + ti * q.C + tj, 1);
       else if (type == 5) atomicAdd(q.upd + tk * q.C + tk, 1);        // one of DAG_TS on (p, p)
