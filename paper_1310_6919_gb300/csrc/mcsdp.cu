@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -1250,7 +1251,17 @@ mcsdp_status mcsdp_create(const mcsdp_problem *p, const mcsdp_options *opt, void
   P.n = p->n;
   P.m = p->m;
   P.b.assign(p->c, p->c + p->m);
-  std::set<std::tuple<int, int, int>> seen;
+  // duplicates: sort (mat, row, col, input index); the first repeat in input order is reported
+  int64_t dup = -1;
+  {
+    std::vector<std::array<int64_t, 4>> keys((size_t)p->nnz);
+    for (int64_t t = 0; t < p->nnz; ++t) keys[t] = {p->mat[t], p->row[t], p->col[t], t};
+    std::sort(keys.begin(), keys.end());
+    for (size_t u = 1; u < keys.size(); ++u)
+      if (keys[u][0] == keys[u - 1][0] && keys[u][1] == keys[u - 1][1] &&
+          keys[u][2] == keys[u - 1][2] && (dup < 0 || keys[u][3] < dup))
+        dup = keys[u][3];
+  }
   for (int64_t t = 0; t < p->nnz; ++t) {
     int k = p->mat[t], i = p->row[t], j = p->col[t];
     double v = p->val[t];
@@ -1258,7 +1269,7 @@ mcsdp_status mcsdp_create(const mcsdp_problem *p, const mcsdp_options *opt, void
       return fail(c, MCSDP_ERR_ARG, "entry " + std::to_string(t) + ": index out of range");
     if (i > j) return fail(c, MCSDP_ERR_ARG, "entry " + std::to_string(t) + ": row > col (give the upper triangle)");
     if (!std::isfinite(v)) return fail(c, MCSDP_ERR_ARG, "entry " + std::to_string(t) + ": not finite");
-    if (!seen.insert({k, i, j}).second)
+    if (t == dup)
       return fail(c, MCSDP_ERR_ARG, "entry " + std::to_string(t) + ": duplicate (mat,row,col)");
     c->ue_k.push_back(k);
     c->ue_i.push_back(i);

@@ -4,9 +4,11 @@
 #include "symbolic.h"
 
 #include <algorithm>
+#include <cstdint>
 #include <array>
 #include <map>
 #include <numeric>
+#include <queue>
 #include <set>
 #include <sstream>
 
@@ -15,24 +17,91 @@ namespace {
 
 // Exact minimum-degree ordering on the elimination graph (ties: smallest caller index).
 // Returns the elimination order and, for each step, the neighbours at elimination time
-// (= the row structure of that column of the Cholesky factor).
+// (= the row structure of that column of the Cholesky factor).  The candidates sit in a binary
+// min-heap of (degree, vertex) with lazy deletion: a degree change pushes a new entry and stale
+// entries are skipped when they surface, which picks the same vertex as an ordered set would.
+// Up to MD_BITSET_N vertices the elimination graph is held as adjacency bitsets: a step is then
+// one word-wise OR per neighbour plus a popcount, instead of a merge of two sorted lists (the
+// same graph, so the same order).
+constexpr int MD_BITSET_N = 8192;
+
+void min_degree_bits(int n, const std::vector<std::vector<int>> &adj, std::vector<int> &order,
+                     std::vector<std::vector<int>> &elim_struct) {
+  using Key = std::pair<int, int>;  // (degree, vertex)
+  const int W = (n + 63) / 64;
+  std::vector<uint64_t> bits((size_t)n * W, 0);
+  std::vector<int> deg(n);
+  std::priority_queue<Key, std::vector<Key>, std::greater<Key>> pq;
+  for (int v = 0; v < n; ++v) {
+    uint64_t *b = bits.data() + (size_t)v * W;
+    for (int u : adj[v]) b[u >> 6] |= 1ull << (u & 63);
+    deg[v] = (int)adj[v].size();
+    pq.push({deg[v], v});
+  }
+  std::vector<char> done(n, 0);
+  order.clear();
+  order.reserve(n);
+  elim_struct.assign(n, {});
+  std::vector<uint64_t> nb(W);
+  while (!pq.empty()) {
+    const Key top = pq.top();
+    pq.pop();
+    const int v = top.second;
+    if (done[v] || top.first != deg[v]) continue;  // stale entry
+    done[v] = 1;
+    order.push_back(v);
+    uint64_t *bv = bits.data() + (size_t)v * W;
+    std::copy(bv, bv + W, nb.begin());
+    std::vector<int> &N = elim_struct[v];  // ascending
+    for (int w = 0; w < W; ++w)
+      for (uint64_t x = nb[w]; x; x &= x - 1) N.push_back(w * 64 + __builtin_ctzll(x));
+    std::fill(bv, bv + W, 0ull);
+    for (int u : N) {
+      // adj[u] := (adj[u] ∪ N) \ {u, v}
+      uint64_t *bu = bits.data() + (size_t)u * W;
+      int d = 0;
+      for (int w = 0; w < W; ++w) {
+        bu[w] |= nb[w];
+        if (w == (u >> 6)) bu[w] &= ~(1ull << (u & 63));
+        if (w == (v >> 6)) bu[w] &= ~(1ull << (v & 63));
+        d += __builtin_popcountll(bu[w]);
+      }
+      if (d != deg[u]) {
+        deg[u] = d;
+        pq.push({d, u});
+      }
+    }
+  }
+}
+
 void min_degree(int n, std::vector<std::vector<int>> adj, std::vector<int> &order,
                 std::vector<std::vector<int>> &elim_struct) {
-  std::set<std::pair<int, int>> pq;
+  if (n <= MD_BITSET_N) {
+    min_degree_bits(n, adj, order, elim_struct);
+    return;
+  }
+  using Key = std::pair<int, int>;  // (degree, vertex)
+  std::priority_queue<Key, std::vector<Key>, std::greater<Key>> pq;
+  std::vector<int> deg(n);
   std::vector<char> done(n, 0);
-  for (int v = 0; v < n; ++v) pq.insert({(int)adj[v].size(), v});
+  for (int v = 0; v < n; ++v) {
+    deg[v] = (int)adj[v].size();
+    pq.push({deg[v], v});
+  }
   order.clear();
+  order.reserve(n);
   elim_struct.assign(n, {});
   std::vector<int> tmp;
   while (!pq.empty()) {
-    int v = pq.begin()->second;
-    pq.erase(pq.begin());
+    const Key top = pq.top();
+    pq.pop();
+    const int v = top.second;
+    if (done[v] || top.first != deg[v]) continue;  // stale entry
     done[v] = 1;
-    std::vector<int> N = adj[v];  // all live
+    std::vector<int> N;
+    N.swap(adj[v]);  // all live
     order.push_back(v);
-    elim_struct[v] = N;
     for (int u : N) {
-      pq.erase({(int)adj[u].size(), u});
       // adj[u] := (adj[u] ∪ N) \ {u, v}
       tmp.clear();
       const auto &a = adj[u];
@@ -45,9 +114,12 @@ void min_degree(int n, std::vector<std::vector<int>> adj, std::vector<int> &orde
         if (x != u && x != v) tmp.push_back(x);
       }
       adj[u].swap(tmp);
-      pq.insert({(int)adj[u].size(), u});
+      if ((int)adj[u].size() != deg[u]) {
+        deg[u] = (int)adj[u].size();
+        pq.push({deg[u], u});
+      }
     }
-    adj[v].clear();
+    elim_struct[v] = std::move(N);
   }
 }
 
@@ -74,7 +146,7 @@ std::string analyze(const ProblemData &P, const SymbolicOptions &o, Symbolic &S)
   // ---- ordering + filled structure ----
   std::vector<int> order;
   std::vector<std::vector<int>> est;
-  min_degree(n, adj, order, est);
+  min_degree(n, std::move(adj), order, est);
   std::vector<int> pos(n);
   for (int p = 0; p < n; ++p) pos[order[p]] = p;
   std::vector<std::vector<int>> st(n);  // struct in elimination positions
