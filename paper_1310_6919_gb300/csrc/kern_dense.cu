@@ -995,16 +995,18 @@ __global__ void __cluster_dims__(BCL, 1, 1) __launch_bounds__(BTH)
       for (int l = 0; l < NB; ++l) lv[l] = (l < nb) ? B[i0 + (int64_t)(b0 + l) * ldb] : 0.0;
     }
     if (kb % BCL == rank) {
-      if (tid < nb) {
-        const double *Li = Linv + (int64_t)kb * NB * NB;  // zero above the diagonal
-        double a0 = 0.0, a1 = 0.0;
+      // x_kb = Linv_kb^T y_kb: eight threads per output, four terms each, summed by shuffles
+      // (Linv is zero above the diagonal and past nb)
+      const double *Li = Linv + (int64_t)kb * NB * NB;
+      const int o = tid >> 3, l0 = (tid & 7) * 4;
+      double a = 0.0;
 #pragma unroll
-        for (int l = 0; l < NB; l += 2) {
-          a0 = fma(Li[l + tid * NB], l < nb ? yv[b0 + l] : 0.0, a0);
-          a1 = fma(Li[l + 1 + tid * NB], l + 1 < nb ? yv[b0 + l + 1] : 0.0, a1);
-        }
-        tb[tid] = a0 + a1;
-      }
+      for (int q = 0; q < 4; ++q)
+        a = fma(Li[l0 + q + o * NB], l0 + q < nb ? yv[b0 + l0 + q] : 0.0, a);
+      a += __shfl_xor_sync(0xffffffffu, a, 1);
+      a += __shfl_xor_sync(0xffffffffu, a, 2);
+      a += __shfl_xor_sync(0xffffffffu, a, 4);
+      if ((tid & 7) == 0) tb[o] = a;
       __syncthreads();
       if (tid < NB) {
         const double v = tid < nb ? tb[tid] : 0.0;
