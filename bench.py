@@ -32,8 +32,8 @@ WORKLOAD_DESC = ("block-arrow SDP: 40 diagonal blocks of 50 + 20-wide border (n=
                  "A_0=I+sum y0_p A_p, seed 20131103")
 FP64_PEAK_GFLOPS = 1250.0   # GB300 nominal dense FP64 (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)
 # DRAM bytes (read + write) of one k_chol_dag launch (the whole m = 2000 factorisation) in an ncu
-# capture of this kernel (16.47 MB read + 3.27 MB written; the 32 MB SCM stays mostly in L2)
-CHOL_TRAFFIC = 19.74e6
+# capture of this kernel (16.47 MB read + 3.10 MB written; the 32 MB SCM stays mostly in L2)
+CHOL_TRAFFIC = 19.57e6
 KCLASS_DESC = {"ychol": "k_ychol (Y = N N^T)", "alg1": "k_alg1 (Algorithm 1)",
                "scm_panel": "k_lfwd2/k_lbwd2 (SCM panel solves)",
                "scm_tile": "k_scm_tiles (SCM tile contraction)",
