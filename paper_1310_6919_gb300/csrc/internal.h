@@ -207,6 +207,7 @@ void launch_primal_step(const DevSym &S, const double *Xbar, const double *dX, d
                         int *status, cudaStream_t st);
 size_t primal_step_smem_bytes(const DevSym &S);
 // scalars: [0] X̄.Y, [1] A_0.X̄, [2] b.z, [3] max|A(X̄)-b|, [4] max|b|, [5] min alpha_r
+// (scal holds 16 + 6 x 64 doubles: the partials of the first stage follow the 16 scalars)
 void launch_measures(const DevSym &S, const double *Xbar, const double *Ylay, const double *z,
                      const double *alpha_r, double *scal, cudaStream_t st);
 void launch_update(const DevSym &S, double *Xbar, const double *dX, double ap, double *z,

@@ -674,20 +674,36 @@ void launch_primal_step(const DevSym &S, const double *X, const double *D, doubl
 
 // ---------------------------------------------------------------------------------------------
 // K8: scalars, single CTA, fixed-order reductions (bitwise reproducible)
-__global__ void k_measures(DevSym S, const double *__restrict__ X, const double *__restrict__ Y,
-                           const double *__restrict__ z, const double *__restrict__ alpha_r,
-                           double *scal) {
+// The scalars of the stopping test and the step lengths, in two deterministic stages: MS_PARTS
+// CTAs each reduce a fixed contiguous share of the slots, constraints and cliques into six
+// partials (sums X.Y, A_0.X, b.z; maxima |A(X)-b|, |b|; minimum alpha_r), then one CTA combines
+// the partials in a fixed order.
+constexpr int MS_PARTS = 64;
+constexpr int MS_THREADS = 256;
+
+__global__ void __launch_bounds__(MS_THREADS)
+    k_measures_part(DevSym S, const double *__restrict__ X, const double *__restrict__ Y,
+                    const double *__restrict__ z, const double *__restrict__ alpha_r,
+                    double *part) {
   __shared__ double red[32];
-  const int tid = threadIdx.x, bd = blockDim.x;
+  const int tid = threadIdx.x, b = blockIdx.x;
+  auto share = [&](int64_t n, int64_t &lo, int64_t &hi) {
+    const int64_t per = (n + MS_PARTS - 1) / MS_PARTS;
+    lo = b * per;
+    hi = lo + per < n ? lo + per : n;
+  };
+  int64_t lo, hi;
   double xy = 0.0, pobj = 0.0;
-  for (int64_t s = tid; s < S.nslot; s += bd) {
+  share(S.nslot, lo, hi);
+  for (int64_t s = lo + tid; s < hi; s += MS_THREADS) {
     const int64_t o = S.slot_off[s];
     const double mult = (S.slot_i[s] == S.slot_j[s]) ? 1.0 : 2.0;
     xy += mult * X[o] * Y[o];
     pobj += mult * S.slot_a0[s] * X[o];
   }
   double pinf = 0.0, dobj = 0.0, maxb = 0.0;
-  for (int k = tid; k < S.m; k += bd) {
+  share(S.m, lo, hi);
+  for (int64_t k = lo + tid; k < hi; k += MS_THREADS) {
     double ax = 0.0;
     for (int q = S.con_ptr[k]; q < S.con_ptr[k + 1]; ++q) ax = fma(S.con_w[q], X[S.con_off[q]], ax);
     pinf = fmax(pinf, fabs(ax - S.b[k]));
@@ -695,12 +711,13 @@ __global__ void k_measures(DevSym S, const double *__restrict__ X, const double 
     maxb = fmax(maxb, fabs(S.b[k]));
   }
   double amin = 1.0;
-  if (alpha_r)
-    for (int r = tid; r < S.ns; r += bd) amin = fmin(amin, alpha_r[r]);
+  if (alpha_r) {
+    share(S.ns, lo, hi);
+    for (int64_t r = lo + tid; r < hi; r += MS_THREADS) amin = fmin(amin, alpha_r[r]);
+  }
   xy = block_reduce_sum(xy, red);
   pobj = block_reduce_sum(pobj, red);
   dobj = block_reduce_sum(dobj, red);
-  // max / min reductions
   __shared__ double mx[3][32];
   for (int o = 16; o > 0; o >>= 1) {
     pinf = fmax(pinf, __shfl_down_sync(0xffffffffu, pinf, o));
@@ -711,19 +728,27 @@ __global__ void k_measures(DevSym S, const double *__restrict__ X, const double 
   __syncthreads();
   if (tid == 0) {
     double a = 0.0, b2 = 0.0, c = 1.0;
-    for (int i = 0; i < (bd + 31) / 32; ++i) { a = fmax(a, mx[0][i]); b2 = fmax(b2, mx[1][i]); c = fmin(c, mx[2][i]); }
-    scal[0] = xy;
-    scal[1] = pobj;
-    scal[2] = dobj;
-    scal[3] = a;
-    scal[4] = b2;
-    scal[5] = c;
+    for (int i = 0; i < MS_THREADS / 32; ++i) { a = fmax(a, mx[0][i]); b2 = fmax(b2, mx[1][i]); c = fmin(c, mx[2][i]); }
+    double *pb = part + 6 * b;
+    pb[0] = xy; pb[1] = pobj; pb[2] = dobj; pb[3] = a; pb[4] = b2; pb[5] = c;
   }
+}
+
+__global__ void k_measures_fin(const double *__restrict__ part, double *scal) {
+  if (threadIdx.x != 0) return;
+  double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 1.0};
+  for (int b = 0; b < MS_PARTS; ++b) {  // fixed order
+    const double *pb = part + 6 * b;
+    v[0] += pb[0]; v[1] += pb[1]; v[2] += pb[2];
+    v[3] = fmax(v[3], pb[3]); v[4] = fmax(v[4], pb[4]); v[5] = fmin(v[5], pb[5]);
+  }
+  for (int q = 0; q < 6; ++q) scal[q] = v[q];
 }
 
 void launch_measures(const DevSym &S, const double *X, const double *Y, const double *z,
                      const double *alpha_r, double *scal, cudaStream_t st) {
-  k_measures<<<1, 1024, 0, st>>>(S, X, Y, z, alpha_r, scal);
+  k_measures_part<<<MS_PARTS, MS_THREADS, 0, st>>>(S, X, Y, z, alpha_r, scal + 16);
+  k_measures_fin<<<1, 32, 0, st>>>(scal + 16, scal);
 }
 
 __global__ void k_update(int64_t nnz, double *X, const double *__restrict__ dX, double ap, int m,

@@ -569,7 +569,7 @@ void plan_workspace(mcsdp_ctx *c) {
   plan_buf(c, cur, "Ncand", (size_t)NCAND * nnzL * 8);
   plan_buf(c, cur, "alpha_c", NCAND * 8);
   plan_buf(c, cur, "alpha_r", (size_t)S.ns * 8);
-  plan_buf(c, cur, "scal", 16 * 8);
+  plan_buf(c, cur, "scal", (16 + 6 * 64) * 8);  // scalars, then the measures' partials
   plan_buf(c, cur, "chol_sync", chol_dag_words(m, m + 1) * 4);
   plan_buf(c, cur, "status", (8 + NCAND) * 4);  // [0..3] phases, [4] FP32 factor, [8..8+NCAND) dual candidates
   {
@@ -1124,7 +1124,7 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
   {
     KScope k2(c, KC_MISC);
     launch_measures(c->D, Xbar, c->Ylay, c->z, c->alpha_r, c->scal, c->stream);
-    k2.done(1);
+    k2.done(2);
   }
   KCHECK(c);
   double sc[8];
@@ -1165,7 +1165,7 @@ mcsdp_status prepare(mcsdp_ctx *c, const double *Xbar, const double *z, double *
   {
     KScope k2(c, KC_MISC);
     launch_measures(c->D, Xbar, c->Ylay, z, nullptr, c->scal, c->stream);
-    k2.done(1);
+    k2.done(2);
   }
   KCHECK(c);
   int st[4];
