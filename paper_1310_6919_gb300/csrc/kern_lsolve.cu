@@ -459,9 +459,9 @@ __device__ __forceinline__ int pull_staged(const DevSym &S, int ub, int ue, cons
 }
 
 // NW warps per CTA: NW = 1 for wide levels (many CTAs per SM already use every SM
-// sub-partition); NW = 4 for narrow levels near the root, where one CTA per SM would leave three
-// of the four FP64 sub-partitions idle: warp 0 applies the updates, then the product with D is
-// split by rows over the warps.
+// sub-partition); NW = 2 for middling levels and NW = 4 for narrow levels near the root, where
+// one CTA per SM would leave FP64 sub-partitions idle: warp 0 applies the updates, then the
+// product with D is split by rows over the warps.
 template <class T, int NW>
 __global__ void __launch_bounds__(32 * NW)
     k_lfwd2(DevSym S, int lvl_begin, int ntiles, const T *__restrict__ L,
@@ -614,6 +614,7 @@ bool lsolve_staged_fits(const LsLevel *lvl_info, int height, int elem_size) {
   return true;
 }
 constexpr int LS_NARROW_PER_SM = 8;  // CTAs per SM of a level below which a CTA gets four warps
+constexpr int LS_MEDIUM_PER_SM = 48;  // ... and below which a CTA gets two
 
 template <class T>
 int lsolve(const DevSym &S, const int *lvl_ptr_host, const int *lvl_xptr_host,
@@ -639,6 +640,8 @@ int lsolve(const DevSym &S, const int *lvl_ptr_host, const int *lvl_xptr_host,
   smem_optin((const void *)k_lbwd2<T, 1>);
   smem_optin((const void *)k_lfwd2<T, 4>);
   smem_optin((const void *)k_lbwd2<T, 4>);
+  smem_optin((const void *)k_lbwd2<T, 2>);
+  smem_optin((const void *)k_lfwd2<T, 2>);
   smem_optin((const void *)k_lfwd_partial2<T>);
   int launches = 0;
   for (int li = 0; li < height; ++li) {
@@ -652,7 +655,9 @@ int lsolve(const DevSym &S, const int *lvl_ptr_host, const int *lvl_xptr_host,
     const int sp = fwd_layout(lv.nc, lv.cw, lv.np, false, es).total;
     const int sb = bwd_layout(lv.nr, lv.nc, es).total;
     // CTAs the skip rule drops return at once: the shape follows the pairs that do work
-    const bool narrow = (active ? active[l] : blocks) <= (int64_t)LS_NARROW_PER_SM * nsm;
+    const int64_t work = active ? active[l] : blocks;
+    const bool narrow = work <= (int64_t)LS_NARROW_PER_SM * nsm;
+    const bool medium = work <= (int64_t)LS_MEDIUM_PER_SM * nsm;
     if (fwd && sf <= LS_SMEM_CAP) {
       const int xb = lvl_xptr_host[l], xc = lvl_xptr_host[l + 1] - xb;
       if (xc > 0) {
@@ -665,6 +670,9 @@ int lsolve(const DevSym &S, const int *lvl_ptr_host, const int *lvl_xptr_host,
       if (narrow)
         k_lfwd2<T, 4><<<(unsigned)blocks, 128, sf, st>>>(S, b, ntiles, L, D, W, ldw, ncolsW, sk, lv.nc,
                                                       lv.cw, lv.np);
+      else if (medium)
+        k_lfwd2<T, 2><<<(unsigned)blocks, 64, sf, st>>>(S, b, ntiles, L, D, W, ldw, ncolsW, sk, lv.nc,
+                                                     lv.cw, lv.np);
       else
         k_lfwd2<T, 1><<<(unsigned)blocks, 32, sf, st>>>(S, b, ntiles, L, D, W, ldw, ncolsW, sk, lv.nc,
                                                      lv.cw, lv.np);
@@ -672,6 +680,9 @@ int lsolve(const DevSym &S, const int *lvl_ptr_host, const int *lvl_xptr_host,
       if (narrow)
         k_lbwd2<T, 4><<<(unsigned)blocks, 128, sb, st>>>(S, b, ntiles, L, D, W, ldw, ncolsW, sk, lv.nr,
                                                       lv.nc);
+      else if (medium)
+        k_lbwd2<T, 2><<<(unsigned)blocks, 64, sb, st>>>(S, b, ntiles, L, D, W, ldw, ncolsW, sk, lv.nr,
+                                                     lv.nc);
       else
         k_lbwd2<T, 1><<<(unsigned)blocks, 32, sb, st>>>(S, b, ntiles, L, D, W, ldw, ncolsW, sk, lv.nr,
                                                      lv.nc);
