@@ -194,10 +194,12 @@ mcsdp_status mcsdp_factors(mcsdp_ctx *ctx, const double *Xbar_layout_dev, const 
  * launches the library issued (always counted) and, when options.profile = 1, the device time of
  * each kernel class measured with CUDA events recorded on the context's stream around the
  * launches of that class.  Classes: 0 K2 Y=NN^T, 1 K1 Algorithm 1, 2 SCM panel solves,
- * 3 SCM tile contraction, 4 SCM Cholesky (potrf/trsm/syrk), 5 SCE back substitution,
- * 6 P-MATRIX, 7 primal step length, 8 dual step length (candidate factorisations),
- * 9 other (pattern scatter, scalars, update). */
-#define MCSDP_NCLASS 10
+ * 3 SCM tile contraction, 4 SCM Cholesky (task queue; FP32: potrf/trsm/syrk), 5 SCE back
+ * substitution, 6 P-MATRIX, 7 primal step length, 8 dual step length (candidate
+ * factorisations), 9 other (pattern scatter, scalars, update), 10 P-MATRIX Y^{-1} columns on
+ * the side stream (single column block: they run beside the SCE solve; their flops are counted
+ * in class 6).  Classes 7 and 10 run on side streams, so their times overlap the others'. */
+#define MCSDP_NCLASS 11
 typedef struct {
   int64_t launches;
   int64_t count[16];   /* launches per class */

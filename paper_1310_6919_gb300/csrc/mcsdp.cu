@@ -103,11 +103,16 @@ struct mcsdp_ctx {
   cudaEvent_t ev[8] = {};
   cudaStream_t st2 = nullptr;                  // low priority: trailing updates, primal step
   cudaStream_t st1 = nullptr;                  // high priority: the Cholesky's critical path
+  cudaStream_t st3 = nullptr;                  // low priority: the P-MATRIX's Y^{-1} columns
+  cudaEvent_t ev_yinv = nullptr;               // st3 done with them
   CholStreams cs;
   cudaEvent_t ev_next[2] = {}, ev_rest[2] = {};
   // device buffers
   double *Xbar = nullptr, *z = nullptr, *Ylay = nullptr, *N = nullptr, *dinvN = nullptr;
   double *Lh = nullptr, *dinvL = nullptr, *dY = nullptr, *dX = nullptr, *YinvE = nullptr;
+  double *W3 = nullptr;  // Y^{-1} columns of the single P-MATRIX block (nullptr: several blocks)
+  double *Pw2 = nullptr;          // partial slots and marks of the side stream's solves
+  unsigned char *xvalid2 = nullptr;
   double *Mlow = nullptr, *Mup = nullptr, *B = nullptr, *hvec = nullptr, *xs = nullptr;
   double *dz = nullptr, *W1 = nullptr, *W2 = nullptr, *Ncand = nullptr;
   double *Pw = nullptr, *Pf = nullptr, *Binv = nullptr;
@@ -170,7 +175,7 @@ mcsdp_status fail(mcsdp_ctx *c, mcsdp_status s, const std::string &msg) {
 size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
 
 enum KClass { KC_YCHOL = 0, KC_ALG1, KC_PANEL, KC_TILE, KC_CHOL, KC_BSOLVE, KC_PMAT, KC_PSTEP,
-              KC_DSTEP, KC_MISC };
+              KC_DSTEP, KC_MISC, KC_PMAT_SIDE };
 
 cudaEvent_t ev_get(mcsdp_ctx *c) {
   if (c->evpool.empty()) {
@@ -563,9 +568,17 @@ void plan_workspace(mcsdp_ctx *c) {
   plan_buf(c, cur, "dz", (size_t)m * 8);
   plan_buf(c, cur, "W1", (size_t)n * c->ldw * 8);
   plan_buf(c, cur, "W2", (size_t)n * c->ldw * 8);
+  // one P-MATRIX block: its Y^{-1} columns get a buffer of their own, so they can be formed
+  // while the SCE is solved
+  plan_buf(c, cur, "W3", c->pm_cols >= n ? (size_t)n * c->ldw * 8 : 0);
   plan_buf(c, cur, "Pw", (size_t)std::max<int64_t>(1, c->nslotw) * c->ldw * 8);
   plan_buf(c, cur, "Pf", (size_t)std::max<int64_t>(1, c->nslotf) * NCAND * 8);
   plan_buf(c, cur, "xvalid", std::max<size_t>(1, c->xch_t.size()) * (size_t)(c->ldw / 32));
+  // the side stream's own partial slots and marks (single P-MATRIX block: its Y^{-1} columns
+  // are solved beside the SCM solves)
+  const bool side = c->pm_cols >= n;
+  plan_buf(c, cur, "Pw2", side ? (size_t)std::max<int64_t>(1, c->nslotw) * c->ldw * 8 : 0);
+  plan_buf(c, cur, "xvalid2", side ? std::max<size_t>(1, c->xch_t.size()) * (size_t)(c->ldw / 32) : 0);
   plan_buf(c, cur, "Ncand", (size_t)NCAND * nnzL * 8);
   plan_buf(c, cur, "alpha_c", NCAND * 8);
   plan_buf(c, cur, "alpha_r", (size_t)S.ns * 8);
@@ -685,7 +698,10 @@ void bind_pointers(mcsdp_ctx *c) {
   c->dz = wsp<double>(c, "dz");
   c->W1 = wsp<double>(c, "W1");
   c->W2 = wsp<double>(c, "W2");
+  c->W3 = c->pm_cols >= c->S.n ? wsp<double>(c, "W3") : nullptr;
   c->Pw = wsp<double>(c, "Pw");
+  c->Pw2 = c->pm_cols >= c->S.n ? wsp<double>(c, "Pw2") : nullptr;
+  c->xvalid2 = c->pm_cols >= c->S.n ? wsp<unsigned char>(c, "xvalid2") : nullptr;
   c->Pf = wsp<double>(c, "Pf");
   D.upd_c0end = wsp<int>(c, "upd_c0end");
   D.xch_beg = wsp<int>(c, "xch_beg");
@@ -903,8 +919,10 @@ mcsdp_status phase_scm(mcsdp_ctx *c) {
 // Dlay == nullptr: dY (on the aggregate pattern); else a symmetric D on lower(E).  yinv_only:
 // only Y^{-1} on E (into YinvE).
 template <class T>
+// Wy (single block only): the block's Y^{-1} columns and Y^{-1} on E were already formed by
+// phase_pmatrix_yinv into Wy; only the dY product and the L̂ solves remain.
 mcsdp_status phase_pmatrix(mcsdp_ctx *c, int *nlaunch, const double *Dlay = nullptr,
-                           bool yinv_only = false) {
+                           bool yinv_only = false, const T *Wy = nullptr) {
   const Symbolic &S = c->S;
   const int n = S.n;
   int nl = 0;
@@ -913,19 +931,23 @@ mcsdp_status phase_pmatrix(mcsdp_ctx *c, int *nlaunch, const double *Dlay = null
   T *W1 = reinterpret_cast<T *>(c->W1), *W2 = reinterpret_cast<T *>(c->W2);
   for (int k0 = 0; k0 < n; k0 += c->pm_cols) {
     const int nc = std::min(c->pm_cols, n - k0);
-    CUDA_TRY(c, cudaMemsetAsync(W1, 0, (size_t)n * c->ldw * sizeof(T), c->stream));
-    launch_rhs_unit(W1, c->ldw, c->pm_rowof_dev + k0, nc, c->stream);
     LsSkip fw{c->pm_bits_dev, c->pm_tkey_dev + k0 / 32, c->bit_words};
     LsSkip bwL{c->pm_need_dev, c->pm_tkey_dev + k0 / 32, c->bit_words};
     const SkipHost hfw{c->pm_bits.data(), c->pm_tkey.data() + k0 / 32};
     const SkipHost hbwL{c->pm_need.data(), c->pm_tkey.data() + k0 / 32};
     const SkipHost hnone{nullptr, nullptr};
-    nl += 1;
-    int r[4];
-    r[0] = lsolve_c<T>(c, true, f.N, f.dinvN, W1, nc, fw, hfw);
-    r[1] = lsolve_c<T>(c, false, f.N, f.dinvN, W1, nc, none, hnone);
-    launch_extract_lowerE(c->D, (const T *)W1, c->ldw, k0, nc, c->YinvE, c->stream);
-    nl += 1;
+    int r[4] = {0, 0, 0, 0};
+    if (Wy) {
+      W1 = const_cast<T *>(Wy);
+    } else {
+      CUDA_TRY(c, cudaMemsetAsync(W1, 0, (size_t)n * c->ldw * sizeof(T), c->stream));
+      launch_rhs_unit(W1, c->ldw, c->pm_rowof_dev + k0, nc, c->stream);
+      nl += 1;
+      r[0] = lsolve_c<T>(c, true, f.N, f.dinvN, W1, nc, fw, hfw);
+      r[1] = lsolve_c<T>(c, false, f.N, f.dinvN, W1, nc, none, hnone);
+      launch_extract_lowerE(c->D, (const T *)W1, c->ldw, k0, nc, c->YinvE, c->stream);
+      nl += 1;
+    }
     if (yinv_only) {
       for (int q = 0; q < 2; ++q) {
         if (r[q] < 0) return fail(c, MCSDP_ERR_ARG, "solve shape not supported in this precision");
@@ -952,6 +974,29 @@ mcsdp_status phase_pmatrix(mcsdp_ctx *c, int *nlaunch, const double *Dlay = null
   }
   KCHECK(c);
   *nlaunch = nl;
+  return MCSDP_OK;
+}
+
+// The first half of the single P-MATRIX block, Y^{-1} E and Y^{-1} on E, into W3 (needs only
+// N, so it can run beside the SCE solve; it uses the solves' partial slots, so not beside the
+// SCM solves).  All on c->stream, which the caller points at the side stream.
+template <class T>
+mcsdp_status phase_pmatrix_yinv(mcsdp_ctx *c, int *nlaunch) {
+  const Symbolic &S = c->S;
+  const int n = S.n;
+  const LsSkip none{nullptr, nullptr, 0};
+  const SolveFactors<T> f = factors_of(c, T());
+  T *W = reinterpret_cast<T *>(c->W3);
+  LsSkip fw{c->pm_bits_dev, c->pm_tkey_dev, c->bit_words};
+  const SkipHost hfw{c->pm_bits.data(), c->pm_tkey.data()};
+  const SkipHost hnone{nullptr, nullptr};
+  CUDA_TRY(c, cudaMemsetAsync(W, 0, (size_t)n * c->ldw * sizeof(T), c->stream));
+  launch_rhs_unit(W, c->ldw, c->pm_rowof_dev, n, c->stream);
+  const int r0 = lsolve_c<T>(c, true, f.N, f.dinvN, W, n, fw, hfw);
+  const int r1 = lsolve_c<T>(c, false, f.N, f.dinvN, W, n, none, hnone);
+  if (r0 < 0 || r1 < 0) return fail(c, MCSDP_ERR_ARG, "solve shape not supported in this precision");
+  launch_extract_lowerE(c->D, (const T *)W, c->ldw, 0, n, c->YinvE, c->stream);
+  *nlaunch = 2 + r0 + r1;
   return MCSDP_OK;
 }
 
@@ -1025,7 +1070,32 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
   // mixed form before promotion: FP32 solves and contraction from FP32 copies of the factors
   bool f32 = c->opt.precision == 1 && !c->promoted && c->f32_solves;
   if (f32) cast_factors(c);
-  mcsdp_status s = f32 ? phase_scm<float>(c) : phase_scm<double>(c);
+  // the P-MATRIX's Y^{-1} columns need only N: with a single block they are formed on the side
+  // stream st3 (own solve buffer, partial slots and marks) beside the SCM solves, which are
+  // latency-bound and leave most SMs idle
+  const bool yinv_early = c->W3 != nullptr;
+  const bool yinv_f32 = f32;
+  mcsdp_status s = MCSDP_OK;
+  if (yinv_early) {
+    CUDA_TRY(c, cudaEventRecord(c->ev_yinv, c->stream));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->st3, c->ev_yinv, 0));
+    cudaStream_t main_st = c->stream;
+    double *pw = c->Pw;
+    unsigned char *xv = c->D.xvalid;
+    c->stream = c->st3;
+    c->Pw = c->Pw2;
+    c->D.xvalid = c->xvalid2;
+    KScope ky(c, KC_PMAT_SIDE, c->st3);
+    int nly = 0;
+    s = f32 ? phase_pmatrix_yinv<float>(c, &nly) : phase_pmatrix_yinv<double>(c, &nly);
+    ky.done(nly);
+    c->stream = main_st;
+    c->Pw = pw;
+    c->D.xvalid = xv;
+    if (s) return s;
+    CUDA_TRY(c, cudaEventRecord(c->ev_yinv, c->st3));
+  }
+  s = f32 ? phase_scm<float>(c) : phase_scm<double>(c);
   if (s) return s;
   cudaEventRecord(c->ev[1], c->stream);
   {
@@ -1043,7 +1113,7 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
         c->promoted_iter = c->cur_iter;
         if (f32) {
           f32 = false;
-          s = phase_scm<double>(c);
+          s = phase_scm<double>(c);  // (the side stream's FP32 Y^{-1} is redone below)
           if (s) return s;
           KScope k4(c, KC_MISC);
           launch_rhs_border(c->D, c->B, c->ldb, c->hvec, beta * mu, c->stream);
@@ -1070,7 +1140,13 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
     k0.done(1);
     KScope k1(c, KC_PMAT);
     int nl = 0;
-    mcsdp_status ps = f32 ? phase_pmatrix<float>(c, &nl) : phase_pmatrix<double>(c, &nl);
+    mcsdp_status ps;
+    if (yinv_early) CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->ev_yinv, 0));
+    if (yinv_early && yinv_f32 == f32)
+      ps = f32 ? phase_pmatrix<float>(c, &nl, nullptr, false, reinterpret_cast<const float *>(c->W3))
+               : phase_pmatrix<double>(c, &nl, nullptr, false, c->W3);
+    else
+      ps = f32 ? phase_pmatrix<float>(c, &nl) : phase_pmatrix<double>(c, &nl);
     if (ps) return ps;
     k1.done(nl);
     KScope k2(c, KC_MISC);
@@ -1321,6 +1397,8 @@ mcsdp_status mcsdp_create(const mcsdp_problem *p, const mcsdp_options *opt, void
     CUDA_TRY(c, cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
     CUDA_TRY(c, cudaStreamCreateWithPriority(&c->st2, cudaStreamNonBlocking, prio_lo));
     CUDA_TRY(c, cudaStreamCreateWithPriority(&c->st1, cudaStreamNonBlocking, prio_hi));
+    CUDA_TRY(c, cudaStreamCreateWithPriority(&c->st3, cudaStreamNonBlocking, prio_lo));
+    CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_yinv, cudaEventDisableTiming));
     for (int i = 0; i < 2; ++i) {
       CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_next[i], cudaEventDisableTiming));
       CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_rest[i], cudaEventDisableTiming));
@@ -1355,6 +1433,8 @@ void mcsdp_destroy(mcsdp_ctx *c) {
     }
     if (c->st2) cudaStreamDestroy(c->st2);
     if (c->st1) cudaStreamDestroy(c->st1);
+    if (c->st3) cudaStreamDestroy(c->st3);
+    if (c->ev_yinv) cudaEventDestroy(c->ev_yinv);
     chol_graphs_destroy(&c->cs);
     if (c->cs.fork) cudaEventDestroy(c->cs.fork);
     if (c->cs.chain_done) cudaEventDestroy(c->cs.chain_done);
