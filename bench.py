@@ -41,6 +41,7 @@ KCLASS_DESC = {"ychol": "k_ychol (Y = N N^T)", "alg1": "k_alg1 (Algorithm 1)",
                "sce_backsolve": "k_backsolve_cluster (SCE back substitution)",
                "pmatrix": "k_lfwd2/k_lbwd2/k_dY_times (P-MATRIX)", "primal_step": "k_primal_step",
                "pmatrix_side": "k_lfwd2/k_lbwd2 (P-MATRIX Y^-1 columns, side stream)",
+               "scm_panel_side": "k_lfwd2/k_lbwd2 (SCM N solves, side stream)",
                "dual_step": "k_ychol candidates (dual step)", "other": "scatter/scalars/update"}
 
 
@@ -242,10 +243,10 @@ def run_gb300(args):
     # roofline of the dominant kernel class (FP64 ALU bound)
     work = P.work_model()
     ms = stats["ms"]
-    # the dominant class among those on the main stream (primal_step and pmatrix_side run on
-    # side streams beside other phases, so their times overlap)
-    dom = max((k for k in ms if k not in ("other", "primal_step", "pmatrix_side")),
-              key=lambda k: ms[k])
+    # the dominant class among those on the main stream (primal_step, pmatrix_side and
+    # scm_panel_side run on side streams beside other phases, so their times overlap)
+    dom = max((k for k in ms if k not in ("other", "primal_step", "pmatrix_side",
+                                          "scm_panel_side")), key=lambda k: ms[k])
     tot_iters = sum(int(x["iters"]) for x in results)
     launches_dom = stats["count"][dom]
     flops_dom = work["flops"][dom] * tot_iters

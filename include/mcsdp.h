@@ -197,9 +197,11 @@ mcsdp_status mcsdp_factors(mcsdp_ctx *ctx, const double *Xbar_layout_dev, const 
  * 3 SCM tile contraction, 4 SCM Cholesky (task queue; FP32: potrf/trsm/syrk), 5 SCE back
  * substitution, 6 P-MATRIX, 7 primal step length, 8 dual step length (candidate
  * factorisations), 9 other (pattern scatter, scalars, update), 10 P-MATRIX Y^{-1} columns on
- * the side stream (single column block: they run beside the SCE solve; their flops are counted
- * in class 6).  Classes 7 and 10 run on side streams, so their times overlap the others'. */
-#define MCSDP_NCLASS 11
+ * a side stream (single column block: they run beside the SCM solves; their flops are counted
+ * in class 6), 11 the SCM's N solves on a side stream (beside the L̂ solves of class 2; their
+ * flops are counted in class 2).  Classes 7, 10 and 11 run on side streams, so their times
+ * overlap the others'. */
+#define MCSDP_NCLASS 12
 typedef struct {
   int64_t launches;
   int64_t count[16];   /* launches per class */

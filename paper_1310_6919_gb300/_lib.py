@@ -31,7 +31,7 @@ class Stats_t(C.Structure):
 
 
 KCLASS = ["ychol", "alg1", "scm_panel", "scm_tile", "scm_chol", "sce_backsolve", "pmatrix",
-          "primal_step", "dual_step", "other", "pmatrix_side"]
+          "primal_step", "dual_step", "other", "pmatrix_side", "scm_panel_side"]
 
 
 class SymInfo_t(C.Structure):

@@ -105,14 +105,18 @@ struct mcsdp_ctx {
   cudaStream_t st1 = nullptr;                  // high priority: the Cholesky's critical path
   cudaStream_t st3 = nullptr;                  // low priority: the P-MATRIX's Y^{-1} columns
   cudaEvent_t ev_yinv = nullptr;               // st3 done with them
+  cudaStream_t st4 = nullptr;                  // low priority: the SCM's N solves
+  cudaEvent_t ev_n0 = nullptr, ev_n1 = nullptr;  // chunk's right-hand sides set / N solves done
   CholStreams cs;
   cudaEvent_t ev_next[2] = {}, ev_rest[2] = {};
   // device buffers
   double *Xbar = nullptr, *z = nullptr, *Ylay = nullptr, *N = nullptr, *dinvN = nullptr;
   double *Lh = nullptr, *dinvL = nullptr, *dY = nullptr, *dX = nullptr, *YinvE = nullptr;
   double *W3 = nullptr;  // Y^{-1} columns of the single P-MATRIX block (nullptr: several blocks)
-  double *Pw2 = nullptr;          // partial slots and marks of the side stream's solves
+  double *Pw2 = nullptr;          // partial slots and marks of the side streams' solves
   unsigned char *xvalid2 = nullptr;
+  double *Pw3 = nullptr;
+  unsigned char *xvalid3 = nullptr;
   double *Mlow = nullptr, *Mup = nullptr, *B = nullptr, *hvec = nullptr, *xs = nullptr;
   double *dz = nullptr, *W1 = nullptr, *W2 = nullptr, *Ncand = nullptr;
   double *Pw = nullptr, *Pf = nullptr, *Binv = nullptr;
@@ -175,7 +179,7 @@ mcsdp_status fail(mcsdp_ctx *c, mcsdp_status s, const std::string &msg) {
 size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
 
 enum KClass { KC_YCHOL = 0, KC_ALG1, KC_PANEL, KC_TILE, KC_CHOL, KC_BSOLVE, KC_PMAT, KC_PSTEP,
-              KC_DSTEP, KC_MISC, KC_PMAT_SIDE };
+              KC_DSTEP, KC_MISC, KC_PMAT_SIDE, KC_PANEL_SIDE };
 
 cudaEvent_t ev_get(mcsdp_ctx *c) {
   if (c->evpool.empty()) {
@@ -579,6 +583,8 @@ void plan_workspace(mcsdp_ctx *c) {
   const bool side = c->pm_cols >= n;
   plan_buf(c, cur, "Pw2", side ? (size_t)std::max<int64_t>(1, c->nslotw) * c->ldw * 8 : 0);
   plan_buf(c, cur, "xvalid2", side ? std::max<size_t>(1, c->xch_t.size()) * (size_t)(c->ldw / 32) : 0);
+  plan_buf(c, cur, "Pw3", (size_t)std::max<int64_t>(1, c->nslotw) * c->ldw * 8);
+  plan_buf(c, cur, "xvalid3", std::max<size_t>(1, c->xch_t.size()) * (size_t)(c->ldw / 32));
   plan_buf(c, cur, "Ncand", (size_t)NCAND * nnzL * 8);
   plan_buf(c, cur, "alpha_c", NCAND * 8);
   plan_buf(c, cur, "alpha_r", (size_t)S.ns * 8);
@@ -702,6 +708,8 @@ void bind_pointers(mcsdp_ctx *c) {
   c->Pw = wsp<double>(c, "Pw");
   c->Pw2 = c->pm_cols >= c->S.n ? wsp<double>(c, "Pw2") : nullptr;
   c->xvalid2 = c->pm_cols >= c->S.n ? wsp<unsigned char>(c, "xvalid2") : nullptr;
+  c->Pw3 = wsp<double>(c, "Pw3");
+  c->xvalid3 = wsp<unsigned char>(c, "xvalid3");
   c->Pf = wsp<double>(c, "Pf");
   D.upd_c0end = wsp<int>(c, "upd_c0end");
   D.xch_beg = wsp<int>(c, "xch_beg");
@@ -894,16 +902,35 @@ mcsdp_status phase_scm(mcsdp_ctx *c) {
     LsSkip bw{c->need_bits_dev, c->tkey_dev + ch.tkey_begin, c->bit_words};
     const SkipHost hfw{c->reach_bits.data(), c->tkey_all.data() + ch.tkey_begin};
     const SkipHost hbw{c->need_bits.data(), c->tkey_all.data() + ch.tkey_begin};
-    // X̂[:, P_g] = L̂^{-T} L̂^{-1} E and Y^{-1}[:, P_g] = N^{-T} N^{-1} E for the chunk's groups
-    int r[4] = {lsolve_c<T>(c, true, f.Lh, f.dinvL, W1, ch.nrhs, fw, hfw),
-                lsolve_c<T>(c, false, f.Lh, f.dinvL, W1, ch.nrhs, bw, hbw),
-                lsolve_c<T>(c, true, f.N, f.dinvN, W2, ch.nrhs, fw, hfw),
-                lsolve_c<T>(c, false, f.N, f.dinvN, W2, ch.nrhs, bw, hbw)};
-    for (int q = 0; q < 4; ++q) {
-      if (r[q] < 0) return fail(c, MCSDP_ERR_ARG, "solve shape not supported in this precision");
-      nl += r[q];
+    // X̂[:, P_g] = L̂^{-T} L̂^{-1} E (here) and Y^{-1}[:, P_g] = N^{-T} N^{-1} E (on the side
+    // stream st4, with its own partial slots and marks: the two pairs of level-scheduled solves
+    // are independent and latency-bound, so they share the SMs)
+    CUDA_TRY(c, cudaEventRecord(c->ev_n0, c->stream));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->st4, c->ev_n0, 0));
+    int r[4];
+    {
+      cudaStream_t main_st = c->stream;
+      double *pw = c->Pw;
+      unsigned char *xv = c->D.xvalid;
+      c->stream = c->st4;
+      c->Pw = c->Pw3;
+      c->D.xvalid = c->xvalid3;
+      KScope kn(c, KC_PANEL_SIDE, c->st4);
+      r[2] = lsolve_c<T>(c, true, f.N, f.dinvN, W2, ch.nrhs, fw, hfw);
+      r[3] = lsolve_c<T>(c, false, f.N, f.dinvN, W2, ch.nrhs, bw, hbw);
+      kn.done(std::max(0, r[2]) + std::max(0, r[3]));
+      c->stream = main_st;
+      c->Pw = pw;
+      c->D.xvalid = xv;
+      CUDA_TRY(c, cudaEventRecord(c->ev_n1, c->st4));
     }
+    r[0] = lsolve_c<T>(c, true, f.Lh, f.dinvL, W1, ch.nrhs, fw, hfw);
+    r[1] = lsolve_c<T>(c, false, f.Lh, f.dinvL, W1, ch.nrhs, bw, hbw);
+    for (int q = 0; q < 2; ++q) nl += std::max(0, r[q]);
     k1.done(nl);
+    CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->ev_n1, 0));
+    for (int q = 0; q < 4; ++q)
+      if (r[q] < 0) return fail(c, MCSDP_ERR_ARG, "solve shape not supported in this precision");
     KCHECK(c);
     KScope k2(c, KC_TILE);
     launch_scm_tiles(c->D, c->tiles_dev + ch.tile_begin, ch.ntiles, (const T *)W1, (const T *)W2,
@@ -1399,6 +1426,9 @@ mcsdp_status mcsdp_create(const mcsdp_problem *p, const mcsdp_options *opt, void
     CUDA_TRY(c, cudaStreamCreateWithPriority(&c->st1, cudaStreamNonBlocking, prio_hi));
     CUDA_TRY(c, cudaStreamCreateWithPriority(&c->st3, cudaStreamNonBlocking, prio_lo));
     CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_yinv, cudaEventDisableTiming));
+    CUDA_TRY(c, cudaStreamCreateWithPriority(&c->st4, cudaStreamNonBlocking, prio_lo));
+    CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_n0, cudaEventDisableTiming));
+    CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_n1, cudaEventDisableTiming));
     for (int i = 0; i < 2; ++i) {
       CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_next[i], cudaEventDisableTiming));
       CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_rest[i], cudaEventDisableTiming));
@@ -1435,6 +1465,9 @@ void mcsdp_destroy(mcsdp_ctx *c) {
     if (c->st1) cudaStreamDestroy(c->st1);
     if (c->st3) cudaStreamDestroy(c->st3);
     if (c->ev_yinv) cudaEventDestroy(c->ev_yinv);
+    if (c->st4) cudaStreamDestroy(c->st4);
+    if (c->ev_n0) cudaEventDestroy(c->ev_n0);
+    if (c->ev_n1) cudaEventDestroy(c->ev_n1);
     chol_graphs_destroy(&c->cs);
     if (c->cs.fork) cudaEventDestroy(c->cs.fork);
     if (c->cs.chain_done) cudaEventDestroy(c->cs.chain_done);
