@@ -199,8 +199,8 @@ mcsdp_status mcsdp_factors(mcsdp_ctx *ctx, const double *Xbar_layout_dev, const 
  * factorisations), 9 other (pattern scatter, scalars, update), 10 P-MATRIX Y^{-1} columns on
  * a side stream (single column block: they run beside the SCM solves; their flops are counted
  * in class 6), 11 the SCM's N solves on a side stream (beside the L̂ solves of class 2; their
- * flops are counted in class 2).  Classes 7, 10 and 11 run on side streams, so their times
- * overlap the others'. */
+ * flops are counted in class 2).  Classes 1, 7, 10 and 11 run on side streams (class 1
+ * beside class 0), so their times overlap the others'. */
 #define MCSDP_NCLASS 12
 typedef struct {
   int64_t launches;

@@ -107,6 +107,7 @@ struct mcsdp_ctx {
   cudaEvent_t ev_yinv = nullptr;               // st3 done with them
   cudaStream_t st4 = nullptr;                  // low priority: the SCM's N solves
   cudaEvent_t ev_n0 = nullptr, ev_n1 = nullptr;  // chunk's right-hand sides set / N solves done
+  cudaEvent_t ev_f0 = nullptr, ev_f1 = nullptr;  // Algorithm 1 on st3: may start / done
   CholStreams cs;
   cudaEvent_t ev_next[2] = {}, ev_rest[2] = {};
   // device buffers
@@ -809,19 +810,33 @@ mcsdp_status phase_ychol(mcsdp_ctx *c, int ncand, const double *alpha, const dou
   return MCSDP_OK;
 }
 
-mcsdp_status factor_Y(mcsdp_ctx *c) {
-  CUDA_TRY(c, cudaMemsetAsync(c->status, 0, 8 * sizeof(int), c->stream));
-  mcsdp_status s = phase_ychol(c, 1, nullptr, c->Ylay, nullptr, c->N, c->dinvN, c->status);
-  if (s) return s;
-  return MCSDP_OK;
-}
-
 mcsdp_status factor_X(mcsdp_ctx *c, const double *Xbar) {
   if (alg1_smem_bytes(c->D) > 220 * 1024)
     return fail(c, MCSDP_ERR_ARG, "clique too large for the shared-memory Algorithm 1 kernel");
   KScope ks(c, KC_ALG1);
   launch_alg1(c->D, Xbar, c->Lh, c->dinvL, c->status + 1, c->stream);
   ks.done(1);
+  KCHECK(c);
+  return MCSDP_OK;
+}
+
+// Y = N N^T and Algorithm 1 (L̂ from X̄) share nothing: Algorithm 1 runs on the side stream st3
+// beside the Y factorisation (the status words are cleared before either starts)
+mcsdp_status factor_YX(mcsdp_ctx *c, const double *Xbar) {
+  if (alg1_smem_bytes(c->D) > 220 * 1024)
+    return fail(c, MCSDP_ERR_ARG, "clique too large for the shared-memory Algorithm 1 kernel");
+  CUDA_TRY(c, cudaMemsetAsync(c->status, 0, 8 * sizeof(int), c->stream));
+  CUDA_TRY(c, cudaEventRecord(c->ev_f0, c->stream));
+  CUDA_TRY(c, cudaStreamWaitEvent(c->st3, c->ev_f0, 0));
+  {
+    KScope ks(c, KC_ALG1, c->st3);
+    launch_alg1(c->D, Xbar, c->Lh, c->dinvL, c->status + 1, c->st3);
+    ks.done(1);
+  }
+  CUDA_TRY(c, cudaEventRecord(c->ev_f1, c->st3));
+  mcsdp_status s = phase_ychol(c, 1, nullptr, c->Ylay, nullptr, c->N, c->dinvN, c->status);
+  CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->ev_f1, 0));
+  if (s) return s;
   KCHECK(c);
   return MCSDP_OK;
 }
@@ -1261,9 +1276,7 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
 mcsdp_status prepare(mcsdp_ctx *c, const double *Xbar, const double *z, double *scal_host) {
   mcsdp_status s = phase_Y(c, z);
   if (s) return s;
-  s = factor_Y(c);
-  if (s) return s;
-  s = factor_X(c, Xbar);
+  s = factor_YX(c, Xbar);
   if (s) return s;
   {
     KScope k2(c, KC_MISC);
@@ -1429,6 +1442,8 @@ mcsdp_status mcsdp_create(const mcsdp_problem *p, const mcsdp_options *opt, void
     CUDA_TRY(c, cudaStreamCreateWithPriority(&c->st4, cudaStreamNonBlocking, prio_lo));
     CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_n0, cudaEventDisableTiming));
     CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_n1, cudaEventDisableTiming));
+    CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_f0, cudaEventDisableTiming));
+    CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_f1, cudaEventDisableTiming));
     for (int i = 0; i < 2; ++i) {
       CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_next[i], cudaEventDisableTiming));
       CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_rest[i], cudaEventDisableTiming));
@@ -1468,6 +1483,8 @@ void mcsdp_destroy(mcsdp_ctx *c) {
     if (c->st4) cudaStreamDestroy(c->st4);
     if (c->ev_n0) cudaEventDestroy(c->ev_n0);
     if (c->ev_n1) cudaEventDestroy(c->ev_n1);
+    if (c->ev_f0) cudaEventDestroy(c->ev_f0);
+    if (c->ev_f1) cudaEventDestroy(c->ev_f1);
     chol_graphs_destroy(&c->cs);
     if (c->cs.fork) cudaEventDestroy(c->cs.fork);
     if (c->cs.chain_done) cudaEventDestroy(c->cs.chain_done);
@@ -1581,9 +1598,7 @@ mcsdp_status mcsdp_scm_assemble(mcsdp_ctx *c, const double *Xbar, const double *
   if (!Xbar || !z || !Bout || ldb < c->S.m) return fail(c, MCSDP_ERR_ARG, "bad arguments");
   s = phase_Y(c, z);
   if (s) return s;
-  s = factor_Y(c);
-  if (s) return s;
-  s = factor_X(c, Xbar);
+  s = factor_YX(c, Xbar);
   if (s) return s;
   if (precision == 1 && !(c->opt.precision == 1 && c->f32_solves))
     return fail(c, MCSDP_ERR_ARG, "precision 1 needs a context created with precision 1");
