@@ -762,7 +762,7 @@ static int dense_chol_dag(T *B, int64_t ldb, int m, int rows, int *status, T *Li
   // two CTAs per SM: one loads or waits while the other computes
   const int grid = (int)std::min<int64_t>(2 * (int64_t)nsm, total);
   k_chol_dag<T><<<grid, DAG_THREADS, smem, st>>>(B, ldb, m, rows, status, Linv_all, q, total);
-  return 2;
+  return 1;  // kernel launches (the memset is not one of ours)
 }
 
 // Right-looking blocked Cholesky of the leading m columns of a rows x m matrix (rows = m + 1 for

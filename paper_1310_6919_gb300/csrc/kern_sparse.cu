@@ -735,10 +735,13 @@ __global__ void __launch_bounds__(MS_THREADS)
 }
 
 __global__ void k_measures_fin(const double *__restrict__ part, double *scal) {
+  __shared__ double ps[6 * MS_PARTS];
+  for (int e = threadIdx.x; e < 6 * MS_PARTS; e += blockDim.x) ps[e] = part[e];  // loads in parallel
+  __syncthreads();
   if (threadIdx.x != 0) return;
   double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 1.0};
   for (int b = 0; b < MS_PARTS; ++b) {  // fixed order
-    const double *pb = part + 6 * b;
+    const double *pb = ps + 6 * b;
     v[0] += pb[0]; v[1] += pb[1]; v[2] += pb[2];
     v[3] = fmax(v[3], pb[3]); v[4] = fmax(v[4], pb[4]); v[5] = fmin(v[5], pb[5]);
   }
@@ -748,7 +751,7 @@ __global__ void k_measures_fin(const double *__restrict__ part, double *scal) {
 void launch_measures(const DevSym &S, const double *X, const double *Y, const double *z,
                      const double *alpha_r, double *scal, cudaStream_t st) {
   k_measures_part<<<MS_PARTS, MS_THREADS, 0, st>>>(S, X, Y, z, alpha_r, scal + 16);
-  k_measures_fin<<<1, 32, 0, st>>>(scal + 16, scal);
+  k_measures_fin<<<1, 128, 0, st>>>(scal + 16, scal);
 }
 
 __global__ void k_update(int64_t nnz, double *X, const double *__restrict__ dX, double ap, int m,
