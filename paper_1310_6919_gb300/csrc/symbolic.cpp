@@ -133,15 +133,19 @@ std::string analyze(const ProblemData &P, const SymbolicOptions &o, Symbolic &S)
   // ---- aggregate sparsity pattern (Sec. 1) ----
   std::vector<std::vector<int>> adj(n);
   {
-    std::vector<std::pair<int, int>> e;
-    e.reserve(P.row.size() * 2);
+    // neighbour lists by counting, each sorted and deduplicated on its own
+    std::vector<int> deg(n, 0);
+    for (size_t t = 0; t < P.row.size(); ++t)
+      if (P.row[t] != P.col[t]) { ++deg[P.row[t]]; ++deg[P.col[t]]; }
+    for (int v = 0; v < n; ++v) adj[v].reserve(deg[v]);
     for (size_t t = 0; t < P.row.size(); ++t) {
-      int i = P.row[t], j = P.col[t];
-      if (i != j) { e.push_back({i, j}); e.push_back({j, i}); }
+      const int i = P.row[t], j = P.col[t];
+      if (i != j) { adj[i].push_back(j); adj[j].push_back(i); }
     }
-    std::sort(e.begin(), e.end());
-    e.erase(std::unique(e.begin(), e.end()), e.end());
-    for (auto &p : e) adj[p.first].push_back(p.second);
+    for (int v = 0; v < n; ++v) {
+      std::sort(adj[v].begin(), adj[v].end());
+      adj[v].erase(std::unique(adj[v].begin(), adj[v].end()), adj[v].end());
+    }
   }
   // ---- ordering + filled structure ----
   std::vector<int> order;
@@ -349,11 +353,12 @@ std::string analyze(const ProblemData &P, const SymbolicOptions &o, Symbolic &S)
       off[t] = layout_off(r, c);
       if (off[t] < 0) return "internal: aggregate entry not covered by E";
     }
+    // entries in (layout offset, matrix) order; the keys are sorted in one contiguous array
+    std::vector<std::array<int64_t, 3>> key(ne);
+    for (size_t t = 0; t < ne; ++t) key[t] = {off[t], P.mat[t], (int64_t)t};
+    std::sort(key.begin(), key.end());
     std::vector<size_t> idx(ne);
-    std::iota(idx.begin(), idx.end(), 0);
-    std::sort(idx.begin(), idx.end(), [&](size_t a, size_t b) {
-      return off[a] != off[b] ? off[a] < off[b] : P.mat[a] < P.mat[b];
-    });
+    for (size_t u = 0; u < ne; ++u) idx[u] = (size_t)key[u][2];
     S.slot_ptr.push_back(0);
     for (size_t u = 0; u < ne;) {
       size_t v = u;
