@@ -4,7 +4,10 @@
 // B (internal constraint order) is stored column-major with one extra row: row m holds g^T.
 // A right-looking blocked factorisation of the leading m columns carries that row through the
 // panel solves and trailing updates, so on exit row m holds (L^{-1} g)^T and only the backward
-// substitution L^T dz = L^{-1} g remains.  FP64 throughout.
+// substitution L^T dz = L^{-1} g remains.  In FP64 the factorisation is one persistent
+// task-queue launch (k_chol_dag); the launch-per-panel form serves the mixed form's FP32 factor
+// (graph-captured, lookahead streams) and the allocation-free solve (one stream).  The mixed
+// form's FP32 factor and FP64 refinement are at the end of the file.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
