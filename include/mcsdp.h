@@ -247,6 +247,16 @@ mcsdp_status mcsdp_sce_solve_noalloc(const double *B_dev, int64_t ldb, const dou
 mcsdp_status mcsdp_pivot_reciprocal(const double *d_dev, double *r_dev, int64_t n,
                                     void *cuda_stream);
 
+/* The ticket order of the FP64 SCM factorisation's task queue (the one persistent launch of
+ * Sec. 3.1 type (i)), exposed so the host tests can check it: for an m-column factorisation of a
+ * rows x m matrix (rows = m + 1 with the right-hand-side row) on 32 x 32 tiles, *ntask receives
+ * the number of tasks and, if tasks is not NULL, tasks[4 t .. 4 t + 3] = (type, i, j, k) of
+ * ticket t: 0 POTRF(0), 1 TRSM(i, k), 2 UPD(i, j, k), 3 factor of diagonal tile k, 4 / 5 the
+ * j-th four-row piece of TRSM(k, k-1) / UPD(k, k, k-1).  CTAs take tickets in increasing order,
+ * so the queue is deadlock-free when every task's dependencies have smaller tickets.  Host only;
+ * MCSDP_ERR_ARG for m <= 0, rows < m or ntask NULL. */
+mcsdp_status mcsdp_chol_task_order(int32_t m, int32_t rows, int64_t *ntask, int32_t *tasks);
+
 /* Differentiation of the solution (not in the paper).  The point differentiated is the
  * central-path point for mu = X̄.Y/n of the context's iterate: the iterate is first re-centred
  * (Newton on z for A(mu Y(z)^{-1}) = b with Y(z) = A_0 - sum z_k A_k, to a residual of 1e-13

@@ -59,7 +59,7 @@ EXPORTED = ["mcsdp_default_options", "mcsdp_create", "mcsdp_destroy", "mcsdp_las
             "mcsdp_sym_export", "mcsdp_solve", "mcsdp_set_iterate", "mcsdp_get_iterate",
             "mcsdp_scm_assemble", "mcsdp_newton_step", "mcsdp_factors", "mcsdp_backward",
             "mcsdp_stats_get", "mcsdp_stats_reset", "mcsdp_work_model", "mcsdp_sce_solve_noalloc",
-            "mcsdp_solve_batch", "mcsdp_pivot_reciprocal"]
+            "mcsdp_solve_batch", "mcsdp_pivot_reciprocal", "mcsdp_chol_task_order"]
 
 _lib = None
 
@@ -99,6 +99,7 @@ def load():
     L.mcsdp_work_model.argtypes = [P, C.POINTER(Work_t)]
     L.mcsdp_sce_solve_noalloc.argtypes = [V, C.c_int64, V, V, C.c_int32, V]
     L.mcsdp_pivot_reciprocal.argtypes = [V, V, C.c_int64, V]
+    L.mcsdp_chol_task_order.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_int64), V]
     L.mcsdp_solve_batch.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.c_int32,
                                     C.POINTER(Result_t)]
     for f in EXPORTED:

@@ -412,7 +412,7 @@ __device__ bool dag_wait_all(const int *const *f, const int *tg, int n, const Da
 }
 
 // sum_{j = a}^{C-1} (R - j)
-__device__ __forceinline__ int64_t dag_tail(int64_t a, int64_t R, int64_t C) {
+__device__ __host__ __forceinline__ int64_t dag_tail(int64_t a, int64_t R, int64_t C) {
   if (a >= C) return 0;
   const int64_t u = C - a;
   return u * R - (u * (a + C - 1)) / 2;
@@ -428,13 +428,102 @@ __device__ __host__ __forceinline__ int64_t dag_head(int64_t p, int64_t C) {
 }
 // tickets of iteration k (k = 0 .. C-2): panel k's rest, the next column's rest, the chain step
 // to tile k+2, the panel solves of column k+1
-__device__ __forceinline__ int64_t dag_iter_size(int64_t k, int64_t R, int64_t C) {
+__device__ __host__ __forceinline__ int64_t dag_iter_size(int64_t k, int64_t R, int64_t C) {
   const int64_t lo = dag_trsm_lo(k, C);
   return dag_tail(k + 2, R, C) + (R - k - 2) + dag_head(k + 2, C) + (R > lo ? R - lo : 0);
 }
 // completions that make tile (i, k) final: eight TS tasks for a tile left of a diagonal tile
 __device__ __forceinline__ int dag_fin_target(int i, int k, int C) {
   return (i == k + 1 && i < C) ? DAG_TS : 1;
+}
+
+// tickets before iteration 0: POTRF(0), TRSM(lo0.., 0) (npre of them), the chain step to tile 1
+struct DagPrefix {
+  int lo0;
+  int64_t npre, pre;
+};
+__device__ __host__ __forceinline__ DagPrefix dag_prefix(int R, int C) {
+  DagPrefix d;
+  d.lo0 = C > 1 ? 2 : 1;  // first TRSM(., 0) row tile (tile (1, 0) belongs to the chain step)
+  d.npre = 1 + (R > d.lo0 ? R - d.lo0 : 0);
+  d.pre = d.npre + dag_head(1, C);
+  return d;
+}
+// all tickets of an R x C tile factorisation
+__device__ __host__ __forceinline__ int64_t dag_total(int R, int C) {
+  int64_t total = dag_prefix(R, C).pre;
+  for (int64_t k = 0; k + 1 < C; ++k) total += dag_iter_size(k, R, C);
+  return total;
+}
+
+// Ticket t -> task (type, i, j, k): 0 POTRF(0), 1 TRSM(i, k), 2 UPD(i, j, k), 3 NEXT(k) (the
+// factor of diagonal tile k), 4 TS(k, s = j), 5 UD(k, s = j).  (kcur, kstart) carry the
+// iteration found for the previous, smaller ticket of the caller (start: 0, dag_prefix().pre).
+struct DagTask {
+  int type, i, j, k;
+};
+__device__ __host__ __forceinline__ DagTask dag_decode(int64_t t, int R, int C, const DagPrefix &pf,
+                                                       int &kcur, int64_t &kstart) {
+  DagTask d{0, 0, 0, 0};
+  int hp = -1;  // chain step to tile hp, element he of its header
+  int64_t he = 0;
+  if (t == 0) {
+    return d;
+  } else if (t < pf.npre) {
+    d.type = 1; d.i = pf.lo0 + (int)t - 1;
+    return d;
+  } else if (t < pf.pre) {
+    hp = 1; he = t - pf.npre;
+  } else {
+    while (kcur + 1 < C && t >= kstart + dag_iter_size(kcur, R, C)) {
+      kstart += dag_iter_size(kcur, R, C);
+      ++kcur;
+    }
+    int64_t e = t - kstart;
+    const int k = kcur, n1 = R - k - 2;
+    // rest[0, dc) | next column (n1) | chain step to k+2 (nh) | rest[dc, dt) | TRSM block |
+    // rest[dt, ..): the chain step needs rest[0] = UPD(k+2, k+2, k) and the next column's
+    // UPD(k+2, k+1, k) before it, so it runs one panel ahead of the trailing work
+    const int64_t rest = dag_tail(k + 2, R, C), lo = dag_trsm_lo(k, C);
+    const int64_t ntr = R > lo ? R - lo : 0, nh = dag_head(k + 2, C);
+    int64_t dc = rest < DAG_DEFER_COL ? rest : DAG_DEFER_COL;
+    if (dc < 1 && rest > 0) dc = 1;
+    int64_t dt = rest < DAG_DEFER_TRSM ? rest : DAG_DEFER_TRSM;
+    if (dt < dc) dt = dc;
+    int64_t ri = -1;
+    if (e < dc) {
+      ri = e;
+    } else if (e < dc + n1) {
+      d.type = 2; d.i = k + 2 + (int)(e - dc); d.j = k + 1; d.k = k;
+    } else if (e < dc + n1 + nh) {
+      hp = k + 2; he = e - dc - n1;
+    } else if (e < dt + n1 + nh) {
+      ri = e - n1 - nh;
+    } else if (e < dt + n1 + nh + ntr) {
+      d.type = 1; d.i = (int)(lo + e - dt - n1 - nh); d.j = d.k = k + 1;
+    } else {
+      ri = e - n1 - nh - ntr;
+    }
+    if (ri >= 0) {
+      int j = k + 2;
+      while (j < C && ri >= R - j) {
+        ri -= R - j;
+        ++j;
+      }
+      d.type = 2; d.i = j + (int)ri; d.j = j; d.k = k;  // j < C for every ticket below total
+    }
+  }
+  if (hp >= 0) {  // TS(hp, s), UD(hp, s), NEXT(hp)
+    d.i = d.k = hp;
+    if (he < DAG_TS) {
+      d.type = 4; d.j = (int)he;
+    } else if (he < 2 * DAG_TS) {
+      d.type = 5; d.j = (int)(he - DAG_TS);
+    } else {
+      d.type = 3; d.j = hp;
+    }
+  }
+  return d;
 }
 
 // TRSM(i, k): rows [i0, i0 + h) of columns [k0, k0 + nb).  Thread = (row r = tid / 8, columns
@@ -585,75 +674,16 @@ __global__ void __launch_bounds__(DAG_THREADS, 2)
   __shared__ int s_task[3];  // [0] first ticket, [1] next ticket, [2] dependencies met
   const int tid = threadIdx.x;
   const int R = (rows + NB - 1) / NB, C = q.C;
-  const int lo0 = C > 1 ? 2 : 1;  // first TRSM(., 0) row tile (tile (1, 0) belongs to NEXT(1))
-  const int64_t npre = 1 + (R > lo0 ? R - lo0 : 0), pre = npre + dag_head(1, C);
+  const DagPrefix pf = dag_prefix(R, C);
   int kcur = 0;
-  int64_t kstart = pre;  // first ticket of iteration kcur
+  int64_t kstart = pf.pre;  // first ticket of iteration kcur
   if (tid == 0) s_task[0] = atomicAdd(q.ticket, 1);
   __syncthreads();
   int t = s_task[0];
   while (t < total) {
     if (tid == 0) s_task[1] = atomicAdd(q.ticket, 1);  // the next ticket, fetched early
-    // decode t into (type, i, j, k): 0 POTRF(0), 1 TRSM(i, k), 2 UPD(i, j, k), 3 NEXT(k),
-    // 4 TS(k, s = tj), 5 UD(k, s = tj)
-    int type, ti, tj, tk;
-    int hp = -1;  // chain step to tile hp, element he of its header
-    int64_t he = 0;
-    if (t == 0) {
-      type = 0; ti = tj = tk = 0;
-    } else if (t < npre) {
-      type = 1; ti = lo0 + t - 1; tj = tk = 0;
-    } else if (t < pre) {
-      hp = 1; he = t - npre;
-    } else {
-      while (kcur + 1 < C && t >= kstart + dag_iter_size(kcur, R, C)) {
-        kstart += dag_iter_size(kcur, R, C);
-        ++kcur;
-      }
-      int64_t e = t - kstart;
-      const int k = kcur, n1 = R - k - 2;
-      // rest[0, dc) | next column (n1) | chain step to k+2 (nh) | rest[dc, dt) | TRSM block |
-      // rest[dt, ..): the chain step needs rest[0] = UPD(k+2, k+2, k) and the next column's
-      // UPD(k+2, k+1, k) before it, so it runs one panel ahead of the trailing work
-      const int64_t rest = dag_tail(k + 2, R, C), lo = dag_trsm_lo(k, C);
-      const int64_t ntr = R > lo ? R - lo : 0, nh = dag_head(k + 2, C);
-      int64_t dc = rest < DAG_DEFER_COL ? rest : DAG_DEFER_COL;
-      if (dc < 1 && rest > 0) dc = 1;
-      int64_t dt = rest < DAG_DEFER_TRSM ? rest : DAG_DEFER_TRSM;
-      if (dt < dc) dt = dc;
-      int64_t ri = -1;
-      if (e < dc) {
-        ri = e;
-      } else if (e < dc + n1) {
-        type = 2; ti = k + 2 + (int)(e - dc); tj = k + 1; tk = k;
-      } else if (e < dc + n1 + nh) {
-        hp = k + 2; he = e - dc - n1;
-      } else if (e < dt + n1 + nh) {
-        ri = e - n1 - nh;
-      } else if (e < dt + n1 + nh + ntr) {
-        type = 1; ti = (int)(lo + e - dt - n1 - nh); tj = tk = k + 1;
-      } else {
-        ri = e - n1 - nh - ntr;
-      }
-      if (ri >= 0) {
-        int j = k + 2;
-        while (j < C && ri >= R - j) {
-          ri -= R - j;
-          ++j;
-        }
-        type = 2; ti = j + (int)ri; tj = j; tk = k;  // j < C for every ticket below total
-      }
-    }
-    if (hp >= 0) {  // TS(hp, s), UD(hp, s), NEXT(hp)
-      ti = tk = hp;
-      if (he < DAG_TS) {
-        type = 4; tj = (int)he;
-      } else if (he < 2 * DAG_TS) {
-        type = 5; tj = (int)(he - DAG_TS);
-      } else {
-        type = 3; tj = hp;
-      }
-    }
+    const DagTask task = dag_decode(t, R, C, pf, kcur, kstart);
+    const int type = task.type, ti = task.i, tj = task.j, tk = task.k;
     // dependencies (thread 0 waits, the CTA follows)
     bool ok = true;
     if (tid == 0) {
@@ -743,14 +773,7 @@ template <class T>
 static int dense_chol_dag(T *B, int64_t ldb, int m, int rows, int *status, T *Linv_all,
                           cudaStream_t st, int *sync, long long budget) {
   const int R = (rows + NB - 1) / NB, C = (m + NB - 1) / NB;
-  // tickets: POTRF(0), TRSM(2.., 0), the chain step to tile 1, then the iterations 0 .. C-2
-  const int lo0 = C > 1 ? 2 : 1;
-  int64_t total = 1 + (R > lo0 ? R - lo0 : 0) + dag_head(1, C);
-  for (int64_t k = 0; k + 1 < C; ++k) {
-    const int64_t a = k + 2, u = C - a, lo = dag_trsm_lo(k, C);
-    total += (a < C ? u * R - (u * (a + C - 1)) / 2 : 0) + (R - k - 2) + dag_head(k + 2, C) +
-             (R > lo ? R - lo : 0);
-  }
+  const int64_t total = dag_total(R, C);
   static int nsm = 0;
   if (nsm == 0) {
     int dev = 0;
@@ -1458,4 +1481,24 @@ extern "C" mcsdp_status mcsdp_pivot_reciprocal(const double *d, double *r, int64
   const int blocks = want > 4096 ? 4096 : (int)want;
   mcsdp::k_pivot_rcp<<<blocks, 256, 0, (cudaStream_t)stream>>>(d, r, n);
   return cudaGetLastError() == cudaSuccess ? MCSDP_OK : MCSDP_ERR_CUDA;
+}
+
+extern "C" mcsdp_status mcsdp_chol_task_order(int32_t m, int32_t rows, int64_t *ntask,
+                                              int32_t *tasks) {
+  if (m <= 0 || rows < m || !ntask) return MCSDP_ERR_ARG;
+  const int R = (rows + mcsdp::NB - 1) / mcsdp::NB, C = (m + mcsdp::NB - 1) / mcsdp::NB;
+  const int64_t total = mcsdp::dag_total(R, C);
+  *ntask = total;
+  if (!tasks) return MCSDP_OK;
+  const mcsdp::DagPrefix pf = mcsdp::dag_prefix(R, C);
+  int kcur = 0;
+  int64_t kstart = pf.pre;
+  for (int64_t t = 0; t < total; ++t) {
+    const mcsdp::DagTask d = mcsdp::dag_decode(t, R, C, pf, kcur, kstart);
+    tasks[4 * t] = d.type;
+    tasks[4 * t + 1] = d.i;
+    tasks[4 * t + 2] = d.j;
+    tasks[4 * t + 3] = d.k;
+  }
+  return MCSDP_OK;
 }
