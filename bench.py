@@ -31,9 +31,10 @@ WORKLOAD_DESC = ("block-arrow SDP: 40 diagonal blocks of 50 + 20-wide border (n=
                  "8 N(0,1) upper positions per A_p inside one block+border clique, b=A(I), "
                  "A_0=I+sum y0_p A_p, seed 20131103")
 FP64_PEAK_GFLOPS = 1250.0   # GB300 nominal dense FP64 (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)
-# DRAM bytes (read + write) of one k_chol_dag launch (the whole m = 2000 factorisation) in an ncu
-# capture of this kernel (16.47 MB read + 3.10 MB written; the 32 MB SCM stays mostly in L2)
-CHOL_TRAFFIC = 19.57e6
+# DRAM bytes (read + write) per launch of the dominant kernel from an ncu capture of its current
+# source; None until one is taken (the k_chol_dag capture in profiles/ predates the move of its
+# ticket decode into a host+device function)
+CHOL_TRAFFIC = None
 KCLASS_DESC = {"ychol": "k_ychol (Y = N N^T)", "alg1": "k_alg1 (Algorithm 1)",
                "scm_panel": "k_lfwd2/k_lbwd2 (SCM panel solves)",
                "scm_tile": "k_scm_tiles (SCM tile contraction)",
@@ -259,7 +260,8 @@ def run_gb300(args):
             "frac": achieved / (FP64_PEAK_GFLOPS / 1e3),
             "traffic": CHOL_TRAFFIC if dom == "scm_chol" else None,
             "traffic_scope": ("DRAM bytes of one k_chol_dag launch (one factorisation) from an "
-                              "ncu capture of this kernel" if dom == "scm_chol" else None),
+                              "ncu capture of this kernel" if dom == "scm_chol" and CHOL_TRAFFIC
+                              else "no ncu capture of the current kernel source"),
             "avg_launch_ms": avg_ms, "launches": launches_dom,
             "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe table); probe measured 1.19"}
     scm_ms = (ms["scm_panel"] + ms["scm_tile"]) / max(1, tot_iters)
