@@ -20,10 +20,13 @@ namespace {
 // (= the row structure of that column of the Cholesky factor).  The candidates sit in a binary
 // min-heap of (degree, vertex) with lazy deletion: a degree change pushes a new entry and stale
 // entries are skipped when they surface, which picks the same vertex as an ordered set would.
-// Up to MD_BITSET_N vertices the elimination graph is held as adjacency bitsets: a step is then
-// one word-wise OR per neighbour plus a popcount, instead of a merge of two sorted lists (the
-// same graph, so the same order).
-constexpr int MD_BITSET_N = 8192;
+// Up to MD_BITSET_N vertices the elimination graph is held as adjacency bitsets (n^2/8 bytes:
+// 128 MiB at the bound): a step is then one word-wise OR per neighbour plus a popcount, instead
+// of a merge of two sorted lists (the same graph, so the same order).  Once fill makes the
+// neighbour sets dense (separator cliques of thousands of vertices in random sparse graphs) the
+// merge costs O(|adj u| + |N|) per neighbour and step against O(n/64) for the OR, so the bitsets
+// win by the clique size over 64.
+constexpr int MD_BITSET_N = 32768;
 
 void min_degree_bits(int n, const std::vector<std::vector<int>> &adj, std::vector<int> &order,
                      std::vector<std::vector<int>> &elim_struct) {
@@ -43,6 +46,8 @@ void min_degree_bits(int n, const std::vector<std::vector<int>> &adj, std::vecto
   order.reserve(n);
   elim_struct.assign(n, {});
   std::vector<uint64_t> nb(W);
+  std::vector<int> nzw;  // words of nb that hold a neighbour
+  nzw.reserve(W);
   while (!pq.empty()) {
     const Key top = pq.top();
     pq.pop();
@@ -53,19 +58,29 @@ void min_degree_bits(int n, const std::vector<std::vector<int>> &adj, std::vecto
     uint64_t *bv = bits.data() + (size_t)v * W;
     std::copy(bv, bv + W, nb.begin());
     std::vector<int> &N = elim_struct[v];  // ascending
-    for (int w = 0; w < W; ++w)
+    nzw.clear();
+    for (int w = 0; w < W; ++w) {
+      if (nb[w]) nzw.push_back(w);
       for (uint64_t x = nb[w]; x; x &= x - 1) N.push_back(w * 64 + __builtin_ctzll(x));
+    }
     std::fill(bv, bv + W, 0ull);
     for (int u : N) {
-      // adj[u] := (adj[u] ∪ N) \ {u, v}
+      // adj[u] := (adj[u] ∪ N) \ {u, v}; deg[u] is the popcount of row u, so only the bits
+      // that N adds are counted (v ∈ adj[u] drops out; u's own bit is held set meanwhile so
+      // that it is never counted as new)
       uint64_t *bu = bits.data() + (size_t)u * W;
-      int d = 0;
-      for (int w = 0; w < W; ++w) {
-        bu[w] |= nb[w];
-        if (w == (u >> 6)) bu[w] &= ~(1ull << (u & 63));
-        if (w == (v >> 6)) bu[w] &= ~(1ull << (v & 63));
-        d += __builtin_popcountll(bu[w]);
+      const uint64_t ubit = 1ull << (u & 63);
+      bu[v >> 6] &= ~(1ull << (v & 63));
+      bu[u >> 6] |= ubit;
+      int d = deg[u] - 1;
+      for (int w : nzw) {
+        const uint64_t add = nb[w] & ~bu[w];
+        if (add) {
+          bu[w] |= add;
+          d += __builtin_popcountll(add);
+        }
       }
+      bu[u >> 6] &= ~ubit;
       if (d != deg[u]) {
         deg[u] = d;
         pq.push({d, u});

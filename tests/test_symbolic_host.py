@@ -39,7 +39,9 @@ def _problem(inst, **kw):
 
 @pytest.mark.parametrize("inst", [lattice_maxcut(10, 10), lattice_maxcut(6, 5, seed=3),
                                   block_arrow(6, 12, 4, 60, seed=5), random_gnm_maxcut(60, 150, 4),
-                                  small_random_sdp(9, 12, 2), cycle_maxcut(17)],
+                                  small_random_sdp(9, 12, 2), cycle_maxcut(17),
+                                  # n = 8400: above 8192 vertices (the ordering's larger-n range)
+                                  lattice_maxcut(4, 2100, seed=9)],
                          ids=lambda i: i.name)
 def test_symbolic_structure_is_valid(inst):
     P = _problem(inst)
