@@ -60,6 +60,47 @@ def test_symbolic_structure_is_valid(inst):
     assert info["nnz_lower_E"] == int(np.tril(E).sum())
 
 
+def _min_degree_fill(P):
+    """Filled pattern (original indices) of exact minimum-degree elimination on the elimination
+    graph, ties broken by the smallest index: at each step the vertex of least current degree is
+    eliminated and its neighbours become a clique."""
+    n = P.shape[0]
+    adj = [set(np.nonzero(P[v])[0].tolist()) - {v} for v in range(n)]
+    alive = set(range(n))
+    F = P | P.T | np.eye(n, dtype=bool)
+    while alive:
+        v = min(alive, key=lambda u: (len(adj[u]), u))
+        N = adj[v]
+        for u in N:
+            adj[u] |= N
+            adj[u].discard(u)
+            adj[u].discard(v)
+        K = sorted(N | {v})
+        F[np.ix_(K, K)] = True
+        alive.remove(v)
+        adj[v] = set()
+    return F
+
+
+@pytest.mark.parametrize("inst", [lattice_maxcut(6, 5, seed=3), random_gnm_maxcut(60, 150, 4),
+                                  random_gnm_maxcut(150, 400, 7), block_arrow(6, 12, 4, 60, seed=5),
+                                  small_random_sdp(9, 12, 2), cycle_maxcut(17)],
+                         ids=lambda i: i.name)
+def test_pattern_is_the_minimum_degree_fill(inst):
+    # without amalgamation the cliques are the fundamental supernodes, so E is exactly the
+    # filled graph of the ordering: it must be that of exact minimum degree with smallest-index
+    # ties (the etree postorder the library applies afterwards does not change the filled graph)
+    P = _problem(inst, relax=0)
+    s = P.sym_export()
+    cl = cliques_from_supernodes(s["sn_col"], s["sn_rowptr"], s["sn_rows"])
+    E_new = pattern_from_cliques(inst.n, cl)
+    iperm = np.empty(inst.n, dtype=np.int64)
+    iperm[s["perm"]] = np.arange(inst.n)
+    E_orig = E_new[np.ix_(iperm, iperm)]
+    A = SparseSym.from_instance(inst)
+    assert np.array_equal(E_orig, _min_degree_fill(A.aggregate_pattern()))
+
+
 def test_host_only_context_refuses_device_work():
     from paper_1310_6919_gb300 import MCSDPError
     P = _problem(lattice_maxcut(4, 4))
