@@ -8,18 +8,76 @@
 #include <array>
 #include <map>
 #include <numeric>
-#include <queue>
 #include <set>
 #include <sstream>
 
 namespace mcsdp {
 namespace {
 
+// Binary min-heap of the live vertices keyed by (degree, vertex), with each vertex's position
+// in the heap kept so that a degree change moves the vertex in place.  The key order is total,
+// so the minimum is unique: the vertex of least degree, ties going to the smallest index.
+class DegreeHeap {
+ public:
+  explicit DegreeHeap(const std::vector<int> &deg) : deg_(deg), h_(deg.size()), pos_(deg.size()) {
+    const int n = (int)deg.size();
+    for (int v = 0; v < n; ++v) h_[v] = pos_[v] = v;
+    for (int i = n / 2 - 1; i >= 0; --i) down(i);
+  }
+  bool empty() const { return h_.empty(); }
+  int pop() {
+    const int v = h_[0];
+    pos_[v] = -1;
+    const int last = h_.back();
+    h_.pop_back();
+    if (!h_.empty()) {
+      h_[0] = last;
+      pos_[last] = 0;
+      down(0);
+    }
+    return v;
+  }
+  void changed(int v) {  // deg[v] changed; v is still in the heap
+    up(pos_[v]);
+    down(pos_[v]);
+  }
+
+ private:
+  bool less(int a, int b) const { return deg_[a] != deg_[b] ? deg_[a] < deg_[b] : a < b; }
+  void up(int i) {
+    const int v = h_[i];
+    while (i > 0) {
+      const int p = (i - 1) / 2;
+      if (!less(v, h_[p])) break;
+      h_[i] = h_[p];
+      pos_[h_[i]] = i;
+      i = p;
+    }
+    h_[i] = v;
+    pos_[v] = i;
+  }
+  void down(int i) {
+    const int v = h_[i], n = (int)h_.size();
+    for (;;) {
+      int c = 2 * i + 1;
+      if (c >= n) break;
+      if (c + 1 < n && less(h_[c + 1], h_[c])) ++c;
+      if (!less(h_[c], v)) break;
+      h_[i] = h_[c];
+      pos_[h_[i]] = i;
+      i = c;
+    }
+    h_[i] = v;
+    pos_[v] = i;
+  }
+  const std::vector<int> &deg_;
+  std::vector<int> h_, pos_;
+};
+
 // Exact minimum-degree ordering on the elimination graph (ties: smallest caller index).
 // Returns the elimination order and, for each step, the neighbours at elimination time
-// (= the row structure of that column of the Cholesky factor).  The candidates sit in a binary
-// min-heap of (degree, vertex) with lazy deletion: a degree change pushes a new entry and stale
-// entries are skipped when they surface, which picks the same vertex as an ordered set would.
+// (= the row structure of that column of the Cholesky factor).  The candidates sit in a
+// DegreeHeap, updated in place when an elimination changes a neighbour's degree.
 // Up to MD_BITSET_N vertices the elimination graph is held as adjacency bitsets (n^2/8 bytes:
 // 128 MiB at the bound): a step is then one word-wise OR per neighbour plus a popcount, instead
 // of a merge of two sorted lists (the same graph, so the same order).  Once fill makes the
@@ -30,30 +88,23 @@ constexpr int MD_BITSET_N = 32768;
 
 void min_degree_bits(int n, const std::vector<std::vector<int>> &adj, std::vector<int> &order,
                      std::vector<std::vector<int>> &elim_struct) {
-  using Key = std::pair<int, int>;  // (degree, vertex)
   const int W = (n + 63) / 64;
   std::vector<uint64_t> bits((size_t)n * W, 0);
   std::vector<int> deg(n);
-  std::priority_queue<Key, std::vector<Key>, std::greater<Key>> pq;
   for (int v = 0; v < n; ++v) {
     uint64_t *b = bits.data() + (size_t)v * W;
     for (int u : adj[v]) b[u >> 6] |= 1ull << (u & 63);
     deg[v] = (int)adj[v].size();
-    pq.push({deg[v], v});
   }
-  std::vector<char> done(n, 0);
+  DegreeHeap heap(deg);
   order.clear();
   order.reserve(n);
   elim_struct.assign(n, {});
   std::vector<uint64_t> nb(W);
   std::vector<int> nzw;  // words of nb that hold a neighbour
   nzw.reserve(W);
-  while (!pq.empty()) {
-    const Key top = pq.top();
-    pq.pop();
-    const int v = top.second;
-    if (done[v] || top.first != deg[v]) continue;  // stale entry
-    done[v] = 1;
+  while (!heap.empty()) {
+    const int v = heap.pop();
     order.push_back(v);
     uint64_t *bv = bits.data() + (size_t)v * W;
     std::copy(bv, bv + W, nb.begin());
@@ -83,7 +134,7 @@ void min_degree_bits(int n, const std::vector<std::vector<int>> &adj, std::vecto
       bu[u >> 6] &= ~ubit;
       if (d != deg[u]) {
         deg[u] = d;
-        pq.push({d, u});
+        heap.changed(u);
       }
     }
   }
@@ -95,24 +146,15 @@ void min_degree(int n, std::vector<std::vector<int>> adj, std::vector<int> &orde
     min_degree_bits(n, adj, order, elim_struct);
     return;
   }
-  using Key = std::pair<int, int>;  // (degree, vertex)
-  std::priority_queue<Key, std::vector<Key>, std::greater<Key>> pq;
   std::vector<int> deg(n);
-  std::vector<char> done(n, 0);
-  for (int v = 0; v < n; ++v) {
-    deg[v] = (int)adj[v].size();
-    pq.push({deg[v], v});
-  }
+  for (int v = 0; v < n; ++v) deg[v] = (int)adj[v].size();
+  DegreeHeap heap(deg);
   order.clear();
   order.reserve(n);
   elim_struct.assign(n, {});
   std::vector<int> tmp;
-  while (!pq.empty()) {
-    const Key top = pq.top();
-    pq.pop();
-    const int v = top.second;
-    if (done[v] || top.first != deg[v]) continue;  // stale entry
-    done[v] = 1;
+  while (!heap.empty()) {
+    const int v = heap.pop();
     std::vector<int> N;
     N.swap(adj[v]);  // all live
     order.push_back(v);
@@ -131,7 +173,7 @@ void min_degree(int n, std::vector<std::vector<int>> adj, std::vector<int> &orde
       adj[u].swap(tmp);
       if ((int)adj[u].size() != deg[u]) {
         deg[u] = (int)adj[u].size();
-        pq.push({deg[u], u});
+        heap.changed(u);
       }
     }
     elim_struct[v] = std::move(N);
@@ -368,12 +410,28 @@ std::string analyze(const ProblemData &P, const SymbolicOptions &o, Symbolic &S)
       off[t] = layout_off(r, c);
       if (off[t] < 0) return "internal: aggregate entry not covered by E";
     }
-    // entries in (layout offset, matrix) order; the keys are sorted in one contiguous array
-    std::vector<std::array<int64_t, 3>> key(ne);
-    for (size_t t = 0; t < ne; ++t) key[t] = {off[t], P.mat[t], (int64_t)t};
-    std::sort(key.begin(), key.end());
+    // entries in (layout offset, matrix, input index) order.  Layout offsets increase with the
+    // column of the lower position (supernodes are contiguous column ranges in order, each block
+    // column-major), so a counting sort on that column followed by a sort of each column's
+    // entries gives the full order without one sort over every entry.
     std::vector<size_t> idx(ne);
-    for (size_t u = 0; u < ne; ++u) idx[u] = (size_t)key[u][2];
+    {
+      std::vector<int64_t> colptr(n + 1, 0);
+      std::vector<int> colof(ne);
+      for (size_t t = 0; t < ne; ++t) {
+        colof[t] = std::min(S.iperm[P.row[t]], S.iperm[P.col[t]]);
+        colptr[colof[t] + 1]++;
+      }
+      for (int c = 0; c < n; ++c) colptr[c + 1] += colptr[c];
+      std::vector<int64_t> at(colptr.begin(), colptr.end() - 1);
+      for (size_t t = 0; t < ne; ++t) idx[at[colof[t]]++] = t;
+      for (int c = 0; c < n; ++c)
+        std::sort(idx.begin() + colptr[c], idx.begin() + colptr[c + 1], [&](size_t a, size_t b) {
+          if (off[a] != off[b]) return off[a] < off[b];
+          if (P.mat[a] != P.mat[b]) return P.mat[a] < P.mat[b];
+          return a < b;
+        });
+    }
     S.slot_ptr.push_back(0);
     for (size_t u = 0; u < ne;) {
       size_t v = u;
@@ -510,30 +568,38 @@ std::string analyze(const ProblemData &P, const SymbolicOptions &o, Symbolic &S)
     S.grp_rowoff.assign(S.ngroup + 1, 0);
     for (int g = 0; g < S.ngroup; ++g)
       S.grp_rowoff[g + 1] = S.grp_rowoff[g] + (S.grp_pptr[g + 1] - S.grp_pptr[g]);
-    // local nonzero lists per internal constraint (both triangles)
-    std::vector<std::vector<std::array<double, 3>>> loc(m);
+    // local nonzero lists per internal constraint (both triangles: an off-diagonal entry is
+    // followed by its mirror), each in input order; counted first, then filled in place
     std::vector<int> grp_of(m);
     for (int g = 0; g < S.ngroup; ++g)
       for (int i = S.grp_cptr[g]; i < S.grp_cptr[g + 1]; ++i) grp_of[i] = g;
-    for (size_t t = 0; t < P.row.size(); ++t) {
-      if (P.mat[t] == 0) continue;
-      int i = S.con_internal[P.mat[t] - 1];
-      int g = grp_of[i];
-      const int *pb = S.grp_cols.data() + S.grp_pptr[g];
-      const int *pe = S.grp_cols.data() + S.grp_pptr[g + 1];
-      int a = (int)(std::lower_bound(pb, pe, S.iperm[P.row[t]]) - pb);
-      int b = (int)(std::lower_bound(pb, pe, S.iperm[P.col[t]]) - pb);
-      loc[i].push_back({(double)a, (double)b, P.val[t]});
-      if (a != b) loc[i].push_back({(double)b, (double)a, P.val[t]});
-    }
     S.anz_ptr.assign(m + 1, 0);
-    for (int i = 0; i < m; ++i) {
-      for (auto &e : loc[i]) {
-        S.anz_a.push_back((int16_t)e[0]);
-        S.anz_b.push_back((int16_t)e[1]);
-        S.anz_v.push_back(e[2]);
+    for (size_t t = 0; t < P.row.size(); ++t)
+      if (P.mat[t] != 0) S.anz_ptr[S.con_internal[P.mat[t] - 1] + 1] += P.row[t] != P.col[t] ? 2 : 1;
+    for (int i = 0; i < m; ++i) S.anz_ptr[i + 1] += S.anz_ptr[i];
+    S.anz_a.assign(S.anz_ptr[m], 0);
+    S.anz_b.assign(S.anz_ptr[m], 0);
+    S.anz_v.assign(S.anz_ptr[m], 0.0);
+    {
+      std::vector<int> at(S.anz_ptr.begin(), S.anz_ptr.end() - 1);
+      for (size_t t = 0; t < P.row.size(); ++t) {
+        if (P.mat[t] == 0) continue;
+        int i = S.con_internal[P.mat[t] - 1];
+        int g = grp_of[i];
+        const int *pb = S.grp_cols.data() + S.grp_pptr[g];
+        const int *pe = S.grp_cols.data() + S.grp_pptr[g + 1];
+        int a = (int)(std::lower_bound(pb, pe, S.iperm[P.row[t]]) - pb);
+        int b = (int)(std::lower_bound(pb, pe, S.iperm[P.col[t]]) - pb);
+        if ((a != b) != (P.row[t] != P.col[t])) return "internal: constraint entry outside its panel";
+        S.anz_a[at[i]] = (int16_t)a;
+        S.anz_b[at[i]] = (int16_t)b;
+        S.anz_v[at[i]++] = P.val[t];
+        if (a != b) {
+          S.anz_a[at[i]] = (int16_t)b;
+          S.anz_b[at[i]] = (int16_t)a;
+          S.anz_v[at[i]++] = P.val[t];
+        }
       }
-      S.anz_ptr[i + 1] = (int)S.anz_v.size();
     }
     // reach (forward) and need (backward) supernode lists per group
     std::vector<char> mark(S.ns, 0);
