@@ -18,5 +18,7 @@ Modules
               with respect to b, A_0 and A_k (the differentiation row; not in the paper)
 
 Parity status: every function above is pinned by tests in tests/test_oracle_*.py against closed
-forms, invariants or brute force (see each function's docstring for its pin).
+forms, invariants or brute force (see each function's docstring for its pin);
+tests/test_oracle_mutants.py plants single-expression mistakes in this package's source and
+checks that a pin fails for each.
 """
