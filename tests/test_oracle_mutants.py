@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 import scipy.linalg as sla
 
+import oracle.certificate
 import oracle.completion
 import oracle.diff
 import oracle.pdipm
@@ -242,6 +243,24 @@ def pins_diff(ns):
         assert abs(fd - ge[t]) <= 1e-6 * scale
 
 
+def pins_certificate(ns):
+    inst = lattice_maxcut(4, 3, seed=2)
+    A = SparseSym.from_instance(inst)
+    perm = np.arange(12)
+    F = eliminate(A.aggregate_pattern())
+    cl = supernodes(F)
+    mc = oracle.pdipm.solve_mc(A, inst.b, inst.z0, perm, cl, F)
+    c = ns["certify"](A, inst.b, perm, cl, mc["Xbar"], mc["z"])
+    W = float(sum(inst.meta["weights"]))
+    assert c["y_pd"] and c["cliques_pd"]
+    assert c["lower"] <= -W + 1e-9 * W and -W <= c["upper"] + 1e-7 * W
+    rows, _ = max(cl, key=lambda q: len(q[0]))
+    X = mc["Xbar"].copy()
+    i, j = int(rows[0]), int(rows[1])
+    X[i, j] = X[j, i] = 2.0 * np.sqrt(X[i, i] * X[j, j])
+    assert not ns["certify"](A, inst.b, perm, cl, X, mc["z"])["cliques_pd"]
+
+
 # (module, pin set, planted mistake: original text -> changed text)
 MUTANTS = [
     # eq. (SCM): dropped Y^{-1}, wrong operand, wrong sign
@@ -289,13 +308,19 @@ MUTANTS = [
      "else (-z[k - 1] * gA0[i, j] + v[k - 1] * X[i, j])"),
     (oracle.diff, pins_diff, "R = _sym(X @ G @ Yinv)", "R = _sym(G @ Yinv)"),
     (oracle.diff, pins_diff, "f = 1.0 if i == j else 2.0", "f = 1.0"),
+    # certificate: largest instead of smallest clique eigenvalue, wrong sign of the lower end
+    (oracle.certificate, pins_certificate, "(Xn[np.ix_(rows, rows)])[0]",
+     "(Xn[np.ix_(rows, rows)])[-1]"),
+    (oracle.certificate, pins_certificate, "lower=float(np.dot(b, z))",
+     "lower=-float(np.dot(b, z))"),
 ]
 
 UNCHANGED = [(oracle.scm, pins_scm), (oracle.scm, pins_rhs),
              (oracle.completion, pins_completion), (oracle.completion, pins_algorithm1),
              (oracle.pdipm, pins_max_step), (oracle.pdipm, pins_measures),
              (oracle.pdipm, pins_solve_dense), (oracle.pdipm, pins_mc_step),
-             (oracle.sdp, pins_sdp), (oracle.diff, pins_diff)]
+             (oracle.sdp, pins_sdp), (oracle.diff, pins_diff),
+             (oracle.certificate, pins_certificate)]
 
 
 @pytest.mark.parametrize("module,pins", UNCHANGED,
