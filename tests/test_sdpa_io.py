@@ -155,5 +155,5 @@ def test_named_workload_hashes():
             h, name = line.split()
             want[name[:-len(".dat-s")]] = h
     assert set(want) == set(sdpa.NAMED)
-    for name in ("grid_maxcut_100", "block_arrow_1020", "block_arrow_2020"):
+    for name in sdpa.NAMED:
         assert sdpa.content_hash(sdpa.to_text(workload(name))) == want[name], name
