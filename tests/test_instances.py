@@ -53,6 +53,12 @@ def test_grid_maxcut_recipe():
         r, c, v = inst.matrix_entries(k)
         assert r.tolist() == [k - 1] and c.tolist() == [k - 1] and v.tolist() == [1.0]
     assert np.all(inst.b == 1.0)
+    # aggregate pattern: the diagonal plus both triangles of the 180 edges = 460 entries
+    pat = np.zeros((100, 100), bool)
+    for k in range(101):
+        r, c, _ = inst.matrix_entries(k)
+        pat[r, c] = pat[c, r] = True
+    assert int(pat.sum()) == 100 + 2 * 180
     # the default start Y(z0) is strictly diagonally dominant, hence positive definite
     Y = dual_slack_dense(inst, inst.z0)
     off = np.abs(Y).sum(axis=1) - np.abs(np.diag(Y))

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 from instances import (lattice_maxcut, block_arrow, random_gnm_maxcut, small_random_sdp,
-                       cycle_maxcut)
+                       cycle_maxcut, workload)
 from oracle.chordal import (cliques_from_supernodes, check_structure, pattern_from_cliques,
                             is_perfect_elimination, covers)
 from oracle.sdp import SparseSym
@@ -99,6 +99,27 @@ def test_pattern_is_the_minimum_degree_fill(inst):
     E_orig = E_new[np.ix_(iperm, iperm)]
     A = SparseSym.from_instance(inst)
     assert np.array_equal(E_orig, _min_degree_fill(A.aggregate_pattern()))
+
+
+def test_block_arrow_pattern_stays_block_arrow():
+    # the n = 2020 block-arrow SDP (40 blocks of 50, border 20): its aggregate pattern is chordal
+    # in any order that eliminates each block before the border, and minimum degree does so
+    # (block vertices have degree < 70, border vertices about 2000), so E adds no entry between
+    # two blocks, no clique exceeds block + border (70), and nnz(lower E) stays under the
+    # block-arrow bound 40 (50 * 20 + 50 * 51 / 2) + 20 * 21 / 2 = 91210
+    inst = workload("block_arrow_2020")
+    P = _problem(inst)
+    s = P.sym_export()
+    cl = cliques_from_supernodes(s["sn_col"], s["sn_rowptr"], s["sn_rows"])
+    assert max(len(r) for r, _ in cl) <= 70
+    E_new = pattern_from_cliques(inst.n, cl)
+    iperm = np.empty(inst.n, dtype=np.int64)
+    iperm[s["perm"]] = np.arange(inst.n)
+    E = E_new[np.ix_(iperm, iperm)]
+    blk = np.minimum(np.arange(inst.n) // 50, 40)      # border vertices -> 40
+    I, J = np.nonzero(E)
+    assert np.all((blk[I] == blk[J]) | (blk[I] == 40) | (blk[J] == 40))
+    assert P.info["nnz_lower_E"] <= 40 * (50 * 20 + 50 * 51 // 2) + 20 * 21 // 2
 
 
 def test_host_only_context_refuses_device_work():
