@@ -122,6 +122,29 @@ def test_block_arrow_pattern_stays_block_arrow():
     assert P.info["nnz_lower_E"] <= 40 * (50 * 20 + 50 * 51 // 2) + 20 * 21 // 2
 
 
+def test_sorted_list_ordering_range():
+    # n = 34000 > 32768: the ordering keeps its elimination graph as sorted lists instead of
+    # bitsets.  Dense E would not fit a test, so the checks are sparse: the cliques form a clique
+    # tree with the running intersection property, and every aggregate entry lies in the clique
+    # of its smaller (elimination-order) index.
+    inst = lattice_maxcut(4, 8500, seed=3)
+    P = _problem(inst)
+    s = P.sym_export()
+    n = inst.n
+    cl = cliques_from_supernodes(s["sn_col"], s["sn_rowptr"], s["sn_rows"])
+    check_structure(n, cl)
+    assert sorted(s["perm"].tolist()) == list(range(n))
+    iperm = np.empty(n, dtype=np.int64)
+    iperm[s["perm"]] = np.arange(n)
+    col2c = np.empty(n, dtype=np.int64)
+    for r, (rows, ns) in enumerate(cl):
+        col2c[rows[:ns]] = r
+    rowsets = [set(rows.tolist()) for rows, _ in cl]
+    for i, j in zip(inst.row, inst.col):
+        p, q = sorted((int(iperm[i]), int(iperm[j])))
+        assert q in rowsets[col2c[p]]
+
+
 def test_host_only_context_refuses_device_work():
     from paper_1310_6919_gb300 import MCSDPError
     P = _problem(lattice_maxcut(4, 4))
