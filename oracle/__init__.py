@@ -15,7 +15,7 @@ Modules
               matrix-completion Newton step at a given iterate
   maxcut      closed forms and brute force used as pins
   diff        central-path point at fixed mu (Newton centring) and its implicit derivatives
-              with respect to b, A_0 and A_k (the differentiation row; not in the paper)
+              with respect to b, A_0 and A_k (an extension; not in the paper)
   certificate weak-duality bracket b^T z <= opt <= A_0 . X̄ for an iterate known on E
               (Grone's completion theorem, Sec. 2.1), for solves too large for the dense PDIPM
 

@@ -1,6 +1,6 @@
 """Test infrastructure (oracle): implicit differentiation of the central-path point.
 
-Not in the paper (the differentiation row of the build plan).  The point differentiated is the
+An extension beyond the paper (derivatives of the solution).  The point differentiated is the
 central-path point for a fixed mu > 0 of (P)/(D) (Sec. 1, Sec. 2.2):
 
     A(X) = b,   Y = A_0 - sum_k z_k A_k,   X Y = mu I,

@@ -1407,7 +1407,7 @@ mcsdp_status mcsdp_create(const mcsdp_problem *p, const mcsdp_options *opt, void
   if (c->S.max_ncol > 96 || c->S.max_nrow > 160)
     return fail(c, MCSDP_ERR_ARG, "a clique of " + std::to_string(c->S.max_nrow) + " rows / " +
                                       std::to_string(c->S.max_ncol) +
-                                      " columns exceeds this build's shared-memory kernels (160 / 96)");
+                                      " columns exceeds the library's shared-memory clique kernels (160 / 96)");
   // default dual start
   c->z0_default.assign(P.m, 0.0);
   if (c->S.unit_diag_constraints) {
