@@ -25,6 +25,16 @@
  *     entries above the diagonal of the leading ncol_s x ncol_s block are unused and zero.
  *     X̄, Y, dX, L̂ and N all use this layout (the memory of L̂ equals that of N, Sec. 3.1).
  *   - Constraint vectors (b, z, dz, g) are in the caller's constraint order.
+ *
+ * A solve, in order of calls (error checks left out):
+ *     mcsdp_problem p = {n, m, 1, b, nnz, mat, row, col, val};   // paper form, A_0 = mat 0
+ *     mcsdp_ctx *ctx;  mcsdp_create(&p, NULL, stream, &ctx);      // validation, host analysis
+ *     size_t bytes;    mcsdp_workspace_size(ctx, &bytes);
+ *     void *ws;        cudaMalloc(&ws, bytes);                     // caller-owned device memory
+ *     mcsdp_set_workspace(ctx, ws, bytes);                         // uploads the tables
+ *     mcsdp_result r;  mcsdp_solve(ctx, &r);                       // r.pobj, r.dobj, r.gap ...
+ *     mcsdp_get_iterate(ctx, Xbar_dev, z_dev, Y_dev);              // the final iterate
+ *     mcsdp_destroy(ctx);  cudaFree(ws);
  */
 #ifndef MCSDP_H
 #define MCSDP_H
