@@ -10,6 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__)
 sys.path.insert(0, ROOT)
 
 from instances import workload  # noqa: E402
+from instances import sdpa  # noqa: E402
 from oracle.sdp import SparseSym  # noqa: E402
 from oracle import pdipm  # noqa: E402
 
@@ -21,7 +22,9 @@ def main(names):
         t = time.time()
         res = pdipm.solve_dense(A, inst.b, inst.z0,
                                 log=lambda h: print(name, h, flush=True))
-        out = dict(workload=name, n=inst.n, m=inst.m, status=res["status"], pobj=res["pobj"],
+        out = dict(workload=name, n=inst.n, m=inst.m,
+                   instance_sha256=sdpa.content_hash(sdpa.to_text(inst)),
+                   status=res["status"], pobj=res["pobj"],
                    dobj=res["dobj"], gap=res["gap"], pinf=res["pinf"], dinf=res["dinf"],
                    iters=res["iters"], seconds=time.time() - t,
                    source="oracle.pdipm.solve_dense (dense FP64 HKM PDIPM, beta 0.1, gamma 0.9, "

@@ -157,3 +157,17 @@ def test_named_workload_hashes():
     assert set(want) == set(sdpa.NAMED)
     for name in sdpa.NAMED:
         assert sdpa.content_hash(sdpa.to_text(workload(name))) == want[name], name
+
+
+def test_golden_values_belong_to_the_current_inputs():
+    # the stored oracle optima were computed on exactly the instances the generators write now
+    import json
+    gdir = os.path.join(ROOT, "tests", "golden")
+    names = sorted(f[:-5] for f in os.listdir(gdir) if f.endswith(".json"))
+    assert names
+    for name in names:
+        with open(os.path.join(gdir, name + ".json")) as f:
+            g = json.load(f)
+        inst = workload(g["workload"])
+        assert (g["n"], g["m"]) == (inst.n, inst.m)
+        assert g["instance_sha256"] == sdpa.content_hash(sdpa.to_text(inst)), name
