@@ -368,9 +368,11 @@ std::string analyze(const ProblemData &P, const SymbolicOptions &o, Symbolic &S)
     }
     S.upd_ptr.assign(S.ns + 1, 0);
     S.upd_relptr.push_back(0);
+    std::vector<int> at_in_t(n, -1);  // position of a row inside the current target's clique
     for (int t = 0; t < S.ns; ++t) {
       int64_t tr0 = S.sn_rowptr[t];
       int tnrow = (int)(S.sn_rowptr[t + 1] - tr0);
+      for (int k = 0; k < tnrow; ++k) at_in_t[S.rows[tr0 + k]] = k;
       for (auto &e : lists[t]) {
         int s = e[0];
         S.upd_src.push_back(s);
@@ -378,15 +380,14 @@ std::string analyze(const ProblemData &P, const SymbolicOptions &o, Symbolic &S)
         S.upd_p2.push_back(e[2]);
         int64_t r0 = S.sn_rowptr[s];
         int nrow = (int)(S.sn_rowptr[s + 1] - r0);
-        int k = 0;
         for (int p = e[1]; p < nrow; ++p) {
-          int r = S.rows[r0 + p];
-          while (k < tnrow && S.rows[tr0 + k] < r) ++k;
-          if (k >= tnrow || S.rows[tr0 + k] != r) return "internal: update rows not in target clique";
+          const int k = at_in_t[S.rows[r0 + p]];
+          if (k < 0) return "internal: update rows not in target clique";
           S.upd_rel.push_back(k);
         }
         S.upd_relptr.push_back((int64_t)S.upd_rel.size());
       }
+      for (int k = 0; k < tnrow; ++k) at_in_t[S.rows[tr0 + k]] = -1;
       S.upd_ptr[t + 1] = (int)S.upd_src.size();
     }
   }
