@@ -103,12 +103,36 @@ void min_degree_bits(int n, const std::vector<std::vector<int>> &adj, std::vecto
   std::vector<uint64_t> nb(W);
   std::vector<int> nzw;  // words of nb that hold a neighbour
   nzw.reserve(W);
+  int last = -1;         // the vertex eliminated in the previous step
   while (!heap.empty()) {
     const int v = heap.pop();
     order.push_back(v);
     uint64_t *bv = bits.data() + (size_t)v * W;
-    std::copy(bv, bv + W, nb.begin());
     std::vector<int> &N = elim_struct[v];  // ascending
+    // After eliminating `last` with neighbours P, every u in P is adjacent to all of P \ {u}.
+    // If v is in P with degree |P| - 1, its neighbours are exactly P \ {v} and each of them
+    // already holds P \ {v} minus itself: eliminating v adds no fill, and the update reduces to
+    // taking v out of their rows (one degree less each) -- the same graph and degrees the
+    // general step below would produce, so the same order.  This is the common case inside a
+    // supernode, where the general step's word-wise OR would add nothing.
+    if (last >= 0) {
+      const std::vector<int> &P = elim_struct[last];
+      if (deg[v] == (int)P.size() - 1 && ((nb[v >> 6] >> (v & 63)) & 1)) {
+        for (int u : P)
+          if (u != v) N.push_back(u);
+        nb[v >> 6] &= ~(1ull << (v & 63));  // nb becomes the bitset of N
+        std::fill(bv, bv + W, 0ull);
+        for (int u : N) {
+          bits[(size_t)u * W + (v >> 6)] &= ~(1ull << (v & 63));
+          deg[u] -= 1;
+          heap.changed(u);
+        }
+        last = v;
+        continue;
+      }
+    }
+    last = v;
+    std::copy(bv, bv + W, nb.begin());
     nzw.clear();
     for (int w = 0; w < W; ++w) {
       if (nb[w]) nzw.push_back(w);
@@ -153,11 +177,29 @@ void min_degree(int n, std::vector<std::vector<int>> adj, std::vector<int> &orde
   order.reserve(n);
   elim_struct.assign(n, {});
   std::vector<int> tmp;
+  int last = -1;  // the vertex eliminated in the previous step
   while (!heap.empty()) {
     const int v = heap.pop();
     std::vector<int> N;
     N.swap(adj[v]);  // all live
     order.push_back(v);
+    // the no-fill step of min_degree_bits: v's neighbours are exactly the previous step's
+    // neighbours minus v, each already adjacent to all the others, so only v leaves their lists
+    if (last >= 0) {
+      const std::vector<int> &P = elim_struct[last];
+      if (deg[v] == (int)P.size() - 1 && std::binary_search(P.begin(), P.end(), v)) {
+        for (int u : N) {
+          auto &a = adj[u];
+          a.erase(std::lower_bound(a.begin(), a.end(), v));
+          deg[u] = (int)a.size();
+          heap.changed(u);
+        }
+        elim_struct[v] = std::move(N);
+        last = v;
+        continue;
+      }
+    }
+    last = v;
     for (int u : N) {
       // adj[u] := (adj[u] ∪ N) \ {u, v}
       tmp.clear();
