@@ -184,3 +184,21 @@ def test_input_validation(lib):
     assert st == 1
     st, msg = _raw_create(lib, 2, 1, [np.nan], *ok)
     assert st == 1
+
+
+@pytest.mark.parametrize("inst", [lattice_maxcut(6, 5, seed=3), block_arrow(6, 12, 4, 60, seed=5),
+                                  small_random_sdp(9, 12, 2)], ids=lambda i: i.name)
+def test_layout_index_covers_lower_E_once(inst):
+    # the binding's map from layout positions to (row, col) in the caller's indices, which the
+    # GPU parity tests use to compare layouts with dense oracle matrices: its valid positions are
+    # the entries of lower(E), each exactly once, rows >= columns in the elimination order
+    P = _problem(inst)
+    ro, co, valid, s = P.layout_index()
+    assert len(ro) == P.info["nnz_layout"]
+    cl = cliques_from_supernodes(s["sn_col"], s["sn_rowptr"], s["sn_rows"])
+    E_new = np.tril(pattern_from_cliques(inst.n, cl))
+    perm = s["perm"].astype(np.int64)
+    want = {(int(perm[i]), int(perm[j])) for i, j in zip(*np.nonzero(E_new))}
+    got = list(zip(ro[valid].tolist(), co[valid].tolist()))
+    assert len(got) == len(set(got)) == len(want) == P.info["nnz_lower_E"]
+    assert set(got) == want
