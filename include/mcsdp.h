@@ -267,6 +267,18 @@ mcsdp_status mcsdp_pivot_reciprocal(const double *d_dev, double *r_dev, int64_t 
  * MCSDP_ERR_ARG for m <= 0, rows < m or ntask NULL. */
 mcsdp_status mcsdp_chol_task_order(int32_t m, int32_t rows, int64_t *ntask, int32_t *tasks);
 
+/* The shared-memory layouts (byte offsets) of the staged supernodal level solves that evaluate
+ * the columns X̂ e_k and Y^{-1} e_k of Sec. 3.1, exposed so the host tests can check them for every
+ * admissible clique size: nc / nr = the level's largest |S_r| / |C_r|, cw / np = the update
+ * chunk's source-column / row bounds, with_d = the forward kernel stages the diagonal block,
+ * elem_size = 8 (FP64) or 4 (FP32).  fwd[7] = (acc, ds, meta, hdr, buf, bufsz, total) of the
+ * forward solve, bwd[6] = (ls, ds, acc, wv, rws, total) of the backward one, *cap (may be NULL)
+ * = the largest total a staged launch takes (larger FP64 levels use the unstaged kernels).
+ * Host only; MCSDP_ERR_ARG for nc <= 0, nr < nc, cw < 0, np < 0, another elem_size or a NULL
+ * fwd / bwd. */
+mcsdp_status mcsdp_lsolve_layout(int32_t nc, int32_t nr, int32_t cw, int32_t np, int32_t with_d,
+                                 int32_t elem_size, int32_t *fwd, int32_t *bwd, int32_t *cap);
+
 /* Differentiation of the solution (not in the paper).  The point differentiated is the
  * central-path point for mu = X̄.Y/n of the context's iterate: the iterate is first re-centred
  * (Newton on z for A(mu Y(z)^{-1}) = b with Y(z) = A_0 - sum z_k A_k, to a residual of 1e-13

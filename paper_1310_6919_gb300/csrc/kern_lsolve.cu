@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "../../include/mcsdp.h"
 #include "internal.h"
 
 namespace mcsdp {
@@ -727,3 +728,21 @@ template void launch_rhs_unit<double>(double *, int64_t, const int *, int, cudaS
 template void launch_rhs_unit<float>(float *, int64_t, const int *, int, cudaStream_t);
 
 }  // namespace mcsdp
+
+// Host only: the shared-memory layouts of the staged level solves, so that the host tests can
+// check them for every admissible clique size (see include/mcsdp.h).
+extern "C" mcsdp_status mcsdp_lsolve_layout(int32_t nc, int32_t nr, int32_t cw, int32_t np,
+                                            int32_t with_d, int32_t elem_size, int32_t *fwd,
+                                            int32_t *bwd, int32_t *cap) {
+  if (nc <= 0 || nr < nc || cw < 0 || np < 0 || (elem_size != 4 && elem_size != 8) || !fwd ||
+      !bwd)
+    return MCSDP_ERR_ARG;
+  const mcsdp::FwdLayout f = mcsdp::fwd_layout(nc, cw, np, with_d != 0, elem_size);
+  const int32_t fv[7] = {f.acc, f.ds, f.meta, f.hdr, f.buf, f.bufsz, f.total};
+  for (int i = 0; i < 7; ++i) fwd[i] = fv[i];
+  const mcsdp::BwdLayout b = mcsdp::bwd_layout(nr, nc, elem_size);
+  const int32_t bv[6] = {b.ls, b.ds, b.acc, b.wv, b.rws, b.total};
+  for (int i = 0; i < 6; ++i) bwd[i] = bv[i];
+  if (cap) *cap = mcsdp::LS_SMEM_CAP;
+  return MCSDP_OK;
+}
