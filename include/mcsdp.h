@@ -184,8 +184,9 @@ mcsdp_status mcsdp_get_iterate(const mcsdp_ctx *ctx, double *Xbar_layout_dev, do
  * K2 (Y = N N^T), K1 (Algorithm 1: L̂ from X̄), K3 (B_ij = A_i . (X̂ A_j Y^{-1})).
  * Writes the lower triangle (i >= j, caller's constraint order) of B into B_dev, column-major
  * with leading dimension ldb >= m; the strict upper triangle is not touched.
- * h_dev (may be NULL) receives h_i = A_i . Y^{-1}.  precision is 0 or 1: B is assembled in
- * FP64 in both forms (the mixed form lowers only the precision of its factorisation). */
+ * h_dev (may be NULL) receives h_i = A_i . Y^{-1}.  precision 0: the solves and the contraction
+ * run in FP64.  precision 1 (the mixed form): they run in FP32 from FP32 copies of L̂ and N (the
+ * factors themselves are computed in FP64), and the FP32 sums are stored as FP64 values. */
 mcsdp_status mcsdp_scm_assemble(mcsdp_ctx *ctx, const double *Xbar_layout_dev, const double *z_dev,
                                 double *B_dev, int64_t ldb, double *h_dev, int32_t precision);
 
@@ -238,8 +239,10 @@ mcsdp_status mcsdp_stats_reset(mcsdp_ctx *ctx);
  * must not pay for a synchronising allocation.  Its working copy of B and the inverses of the
  * diagonal blocks live in one file-scope device array of the library (about 8.9 MB per GPU that
  * loads the library, held until the process exits), so m <= MCSDP_SCE_NOALLOC_MAX_M; larger m is
- * rejected with MCSDP_ERR_ARG.  B and g are not modified.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) and must therefore come before any stream capture.
+ * rejected with MCSDP_ERR_ARG.  B and g are not modified.  Every call looks up the array's device
+ * address (cudaGetSymbolAddress; no allocation), so a device reset between calls is harmless; the
+ * first call on a device also loads the library's device code and must therefore come before any
+ * stream capture.
  * Every call reuses the same array, so calls whose GPU work overlaps (different streams, different
  * host threads) race; serialise them.  Returns MCSDP_ERR_NOT_PD if B is not positive definite.
  * cuda_stream is a cudaStream_t; the call synchronises it before returning. */
@@ -249,9 +252,10 @@ mcsdp_status mcsdp_sce_solve_noalloc(const double *B_dev, int64_t ldb, const dou
 
 /* The reciprocal that the factorisations' serial pivot loops use instead of a division (the
  * diagonal-block Cholesky of the SCM, Sec. 3.1 type (i), and the supernodal Cholesky of Y, type
- * (ii)): r[i] = 1/d[i] from an FP32 seed and one third-order series step in FP64, faithfully
- * rounded (error below 0.52 ulp) for positive normal d; outside [2^-120, 2^121) and for
- * non-positive or non-finite d it is the IEEE division.  Exposed so its accuracy can be checked
+ * (ii)): r[i] = 1/d[i] from the PTX approximate FP64 reciprocal (rcp.approx.ftz.f64, relative
+ * error about 2^-20) and one third-order series step in FP64, faithfully rounded (error below
+ * 0.52 ulp) for positive normal d; outside [2^-1000, 2^1000] and for non-positive or non-finite
+ * d it is the IEEE division.  Exposed so its accuracy can be checked
  * against division.  d and r are device arrays of n doubles; asynchronous on cuda_stream
  * (a cudaStream_t).  MCSDP_ERR_ARG for n < 0 or a NULL array with n > 0. */
 mcsdp_status mcsdp_pivot_reciprocal(const double *d_dev, double *r_dev, int64_t n,
@@ -281,8 +285,10 @@ mcsdp_status mcsdp_lsolve_layout(int32_t nc, int32_t nr, int32_t cw, int32_t np,
 
 /* Differentiation of the solution (not in the paper).  The point differentiated is the
  * central-path point for mu = X̄.Y/n of the context's iterate: the iterate is first re-centred
- * (Newton on z for A(mu Y(z)^{-1}) = b with Y(z) = A_0 - sum z_k A_k, to a residual of 1e-13
- * relative; the context's iterate becomes that point, X̄ = mu Y^{-1} on E).  For the loss
+ * (Newton on z for A(mu Y(z)^{-1}) = b with Y(z) = A_0 - sum z_k A_k, until the residual
+ * max|A(X) - b| / max(1, max|b|) is at most 1e-13, or, once a Newton step no longer halves it,
+ * is at most 1e-9 (the rounding level of its evaluation for an ill-conditioned Y); the context's
+ * iterate becomes that point, X̄ = mu Y^{-1} on E).  For the loss
  * l = sum over layout entries gX . X̄ + gz^T z, implicit differentiation of A(X) = b,
  * X = mu Y^{-1} gives, with R = sym(X̂ G Y^{-1}) (G the symmetric matrix of the weights gX),
  * v = B^{-1}(A(R) + gz) (B the SCM at the point), g_{A_0} = sym(X̂ (A^*(v) - G) Y^{-1}):

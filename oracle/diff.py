@@ -25,24 +25,35 @@ def _sym(M):
     return 0.5 * (M + M.T)
 
 
-def central_point(A, b, mu, z0, tol=1e-13, floor=1e-9, max_newton=60):
+def central_point(A, b, mu, z0, tol=1e-13, max_newton=60):
     """Newton on F(z) = A(mu Y(z)^{-1}) - b from a dual-feasible z0, halving the step until
-    Y stays positive definite, until max|F| <= tol max(1, max|b|), or until a step no longer
-    halves the residual once it is below floor (the rounding level of evaluating F).
-    Returns z, Y, X = mu Y^{-1}."""
+    Y stays positive definite, until max|F| <= tol max(1, max|b|).  If Newton stops gaining
+    (three steps in a row that do not halve the residual) the point is accepted only when the
+    residual is at the rounding level of evaluating F, rho = 64 eps cond(Y) max|A(X)| / max(1,
+    max|b|) (Y^{-1} is formed with relative error about eps cond(Y)); otherwise it raises.
+    Returns z, Y, X = mu Y^{-1} and the relative residual reached."""
     z = np.array(z0, dtype=np.float64)
     scale = max(1.0, float(np.max(np.abs(b))))
-    prev = None
+    eps = np.finfo(np.float64).eps
+    best = None
+    stalled = 0
     for _ in range(max_newton):
         Y = dual_slack(A, z)
         Yinv = np.linalg.inv(Y)
         Yinv = _sym(Yinv)
         X = mu * Yinv
-        F = A.op(X) - b
+        AX = A.op(X)
+        F = AX - b
         res = np.max(np.abs(F)) / scale
-        if res <= tol or (prev is not None and res > 0.5 * prev and res <= floor):
-            return z, Y, X
-        prev = res
+        if res <= tol:
+            return z, Y, X, res
+        stalled = stalled + 1 if best is not None and res > 0.5 * best else 0
+        best = res if best is None else min(best, res)
+        if stalled >= 3:
+            rho = 64.0 * eps * np.linalg.cond(Y) * max(1.0, float(np.max(np.abs(AX)))) / scale
+            if res <= rho:
+                return z, Y, X, res
+            raise RuntimeError("centring stalled above the rounding level")
         Bm = scm_dense(A, X, Yinv)
         dz = np.linalg.solve(Bm, -F)
         t = 1.0
@@ -83,5 +94,7 @@ def entry_gradients(A_inst, z, v, gA0, X):
 
 def loss(A, b, mu, z0, G, gz):
     """l at the central point for (A, b, mu), started from z0."""
-    z, Y, X = central_point(A, b, mu, z0)
+    z, Y, X, res = central_point(A, b, mu, z0)
+    if res > 1e-12:
+        raise RuntimeError(f"central point residual {res:.1e} too large for a finite difference")
     return float(np.sum(G * X) + gz @ z)

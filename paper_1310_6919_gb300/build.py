@@ -1,5 +1,6 @@
 """Builds libmcsdp.so in-tree for sm_103a: each CUDA/C++ translation unit is compiled in parallel
 with nvcc, then linked into paper_1310_6919_gb300/libmcsdp.so (static CUDA runtime)."""
+import hashlib
 import os
 import shutil
 import subprocess
@@ -9,6 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmcsdp.so")
+STAMP = os.path.join(HERE, "libmcsdp.so.sha256")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU = ["kern_sparse.cu", "kern_scm.cu", "kern_dense.cu", "kern_lsolve.cu", "mcsdp.cu"]
 CPP = ["symbolic.cpp"]
@@ -27,11 +29,27 @@ def _sources():
         os.path.join(HERE, "..", "include", "mcsdp.h")]
 
 
+COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC]
+
+
+def source_hash():
+    """SHA-256 over every source file's name and bytes and the compiler flags: the library is
+    rebuilt whenever any of them changes (file times are not trusted: copies and checkouts can
+    leave a stale library newer than its sources)."""
+    h = hashlib.sha256()
+    for s in sorted(_sources()):
+        h.update(os.path.basename(s).encode())
+        with open(s, "rb") as f:
+            h.update(f.read())
+    h.update(" ".join(ARCH + COMMON[:-1] + CU + CPP).encode())
+    return h.hexdigest()
+
+
 def up_to_date():
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(STAMP)):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(s) <= t for s in _sources())
+    with open(STAMP) as f:
+        return f.read().strip() == source_hash()
 
 
 def build(force=False, verbose=False):
@@ -39,7 +57,7 @@ def build(force=False, verbose=False):
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     nvcc = _nvcc()
-    common = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC]
+    common = COMMON
     jobs = []
     for f in CU:
         jobs.append([nvcc] + ARCH + common + ["-c", os.path.join(CSRC, f), "-o",
@@ -61,6 +79,8 @@ def build(force=False, verbose=False):
     tmp = LIB + ".tmp"
     run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs)
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(source_hash() + "\n")
     return LIB
 
 

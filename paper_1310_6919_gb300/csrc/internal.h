@@ -228,7 +228,7 @@ void launch_scm_tiles(const DevSym &S, const int2 *tiles, int ntiles, const T *W
 // ---------------- dense SCM factorisation (kern_dense.cu) ----------------
 // B internal, (m+1) x m lower, column-major, ld = ldb; row m holds g^T on entry and
 // (L^{-1} g)^T on exit.
-// Linv: ceil(m / 64) blocks of 64 x 64 doubles receiving the inverses of the diagonal blocks
+// Linv: ceil(m / 32) blocks of 32 x 32 (NB x NB) values receiving the inverses of the diagonal blocks
 // Streams of the blocked Cholesky with lookahead: the critical path (diagonal block, panel solve,
 // update of the next block column) on a high-priority stream, the rest of every trailing update
 // on a low-priority one, forked from and joined back into the caller's stream.

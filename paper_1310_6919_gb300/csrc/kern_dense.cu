@@ -949,7 +949,7 @@ int dense_chol_f32(float *B, int64_t ldb, int m, int *status, float *Linv_all, c
   return dense_chol_cached<float>(B, ldb, m, m, status, Linv_all, st, cs);
 }
 
-// Backward substitution L^T x = y, y = row m of B, blocks of 64 from the bottom; the diagonal
+// Backward substitution L^T x = y, y = row m of B, blocks of NB (32) from the bottom; the diagonal
 // block step is x_b <- Linv_b^T x_b with the inverses stored by the factorisation.
 __global__ void k_bs_diag(const double *__restrict__ Linv, int b0, int nb, double *x) {
   __shared__ double xs[NB];
@@ -1401,7 +1401,7 @@ int mixed_refine_step(const double *B, int64_t ldb, int m, const float *L32, con
 
 // ---------------------------------------------------------------------------------------------
 // Allocation-free Schur complement solve.  Working storage: the bordered copy of B
-// ((m+1) x m, leading dimension m+1), the inverses of the 64 x 64 diagonal blocks, and one
+// ((m+1) x m, leading dimension m+1), the inverses of the NB x NB (32 x 32) diagonal blocks, and one
 // status word, all in one file-scope device array.
 constexpr int NA_MAX_M = MCSDP_SCE_NOALLOC_MAX_M;
 constexpr size_t NA_B = (size_t)(NA_MAX_M + 1) * NA_MAX_M;
@@ -1426,27 +1426,18 @@ __global__ void k_noalloc_setup(double *Bw, int64_t ldw, const double *__restric
 
 }  // namespace mcsdp
 
-namespace {
-std::mutex g_na_mu;
-double *g_na_ptr[64] = {};  // device address of the scratch array, per device ordinal
-}  // namespace
-
 extern "C" mcsdp_status mcsdp_sce_solve_noalloc(const double *B, int64_t ldb, const double *g,
                                                 double *x, int32_t m, void *stream) {
   using namespace mcsdp;
   if (m <= 0 || m > NA_MAX_M || ldb < m || !B || !g || !x) return MCSDP_ERR_ARG;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MCSDP_ERR_CUDA;
-  double *base = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_na_mu);
-    if (!g_na_ptr[dev]) {
-      void *p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_sce_noalloc_scratch) != cudaSuccess || !p) return MCSDP_ERR_CUDA;
-      g_na_ptr[dev] = static_cast<double *>(p);
-    }
-    base = g_na_ptr[dev];
-  }
+  // errors left by earlier, unrelated work would otherwise be reported as this call's
+  (void)cudaGetLastError();
+  // The array's device address is looked up on every call (no allocation, no synchronisation):
+  // a cached address would go stale if the caller reset the device, since the module is then
+  // loaded again elsewhere.  On the first call on a device this also loads the module.
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_sce_noalloc_scratch) != cudaSuccess || !p) return MCSDP_ERR_CUDA;
+  double *base = static_cast<double *>(p);
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t ldw = (int64_t)m + 1;
   double *Bw = base;

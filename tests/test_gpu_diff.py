@@ -55,7 +55,8 @@ def test_backward_matches_oracle(mk):
     gX = np.where(c.valid, rng.standard_normal(c.valid.shape[0]), 0.0)
     gz = rng.standard_normal(inst.m)
     out = c.P.backward(torch.tensor(gX, device="cuda:0"), torch.tensor(gz, device="cuda:0"))
-    zc, Yc, Xc = diff.central_point(A, inst.b, mu, zn)
+    zc, Yc, Xc, res = diff.central_point(A, inst.b, mu, zn)
+    assert res <= 1e-12
     gb, gA0, gA = diff.backward(A, zc, Yc, Xc, _layout_to_sym(c, gX), gz)
     ge = diff.entry_gradients(inst, zc, gb, gA0, Xc)
     scale = max(np.max(np.abs(ge)), np.max(np.abs(gb)))
@@ -63,6 +64,10 @@ def test_backward_matches_oracle(mk):
     assert np.max(np.abs(out["g_entries"].cpu().numpy() - ge)) <= 1e-8 * scale
     # the context's iterate is now the central point
     X2, z2, _ = c.P.get_iterate()
+    # the library's own central point: its residual, evaluated here in FP64 on the CPU
+    z2n = z2.cpu().numpy()
+    F = A.op(mu * np.linalg.inv(dual_slack(A, z2n))) - inst.b
+    assert np.max(np.abs(F)) / max(1.0, np.max(np.abs(inst.b))) <= 1e-12
     assert np.max(np.abs(z2.cpu().numpy() - zc)) <= 1e-9 * max(1.0, np.max(np.abs(zc)))
     E = c.E
     assert np.max(np.abs(c.from_layout(X2)[E] - Xc[E])) <= 1e-9 * np.max(np.abs(Xc))

@@ -39,7 +39,8 @@ def test_centring_reaches_the_central_point(mk):
     inst = mk()
     A = SparseSym.from_instance(inst)
     mu = 0.3
-    z, Y, X = diff.central_point(A, inst.b, mu, inst.z0)
+    z, Y, X, res = diff.central_point(A, inst.b, mu, inst.z0)
+    assert res <= 1e-13
     assert np.max(np.abs(A.op(X) - inst.b)) <= 1e-12 * max(1, np.max(np.abs(inst.b)))
     assert np.linalg.eigvalsh(Y)[0] > 0
     assert np.allclose(X @ Y, mu * np.eye(inst.n), atol=1e-10)
@@ -53,7 +54,8 @@ def test_scalar_closed_form():
                        np.array([0, 0], np.int32), np.array([0, 0], np.int32),
                        np.array([c, a]), z0=np.array([0.0]), meta={})
     A = SparseSym.from_instance(inst)
-    z, Y, X = diff.central_point(A, inst.b, mu, inst.z0)
+    z, Y, X, res = diff.central_point(A, inst.b, mu, inst.z0)
+    assert res <= 1e-13
     assert abs(X[0, 0] - b / a) < 1e-13
     assert abs(z[0] - (c - mu * a / b) / a) < 1e-12
     G = np.array([[1.0]])
@@ -70,7 +72,10 @@ def test_gradients_match_central_differences(mk):
     inst = mk()
     A, G, gz = _loss_setup(inst, 3)
     mu = 0.3
-    z, Y, X = diff.central_point(A, inst.b, mu, inst.z0)
+    z, Y, X, res = diff.central_point(A, inst.b, mu, inst.z0)
+    # the finite differences below re-centre every perturbed problem; oracle.diff.loss raises
+    # unless each of those points also reaches a residual of 1e-12 or less
+    assert res <= 1e-12
     gb, gA0, gA = diff.backward(A, z, Y, X, G, gz)
     g_entries = diff.entry_gradients(inst, z, gb, gA0, X)
     h = 1e-6

@@ -220,7 +220,8 @@ def pins_diff(ns):
     G = 0.5 * (G + G.T)
     gz = rng.standard_normal(3)
     mu, h = 0.3, 1e-6
-    z, Y, X = ns["central_point"](A, inst.b, mu, inst.z0)
+    z, Y, X, res = ns["central_point"](A, inst.b, mu, inst.z0)
+    assert res <= 1e-12
     assert np.max(np.abs(A.op(X) - inst.b)) <= 1e-12 * max(1, np.max(np.abs(inst.b)))
     assert np.allclose(X @ Y, mu * np.eye(4), atol=1e-10)
     gb, gA0, _ = ns["backward"](A, z, Y, X, G, gz)

@@ -77,3 +77,21 @@ def test_noalloc_rejects_oversize_and_indefinite(lib):
     B = 2.0 * torch.eye(m, dtype=torch.float64, device="cuda:0")
     st, x = _call(lib, B, g, m)
     assert st == 0 and torch.allclose(x, 0.5 * g)
+
+
+def test_noalloc_at_the_maximum_size(lib):
+    """m = MCSDP_SCE_NOALLOC_MAX_M fills the bordered copy ((m+1) x m) and the diagonal-block
+    inverses of the fixed array exactly: a random SPD B = Q Q^T / m + I with a known x, checked
+    against torch.linalg.solve in FP64, twice in a row."""
+    m = 1024
+    gen = torch.Generator(device="cpu").manual_seed(11)
+    Q = torch.randn(m, m, generator=gen, dtype=torch.float64)
+    B = (Q @ Q.t() / m + torch.eye(m, dtype=torch.float64)).to("cuda:0")
+    xt = torch.randn(m, generator=gen, dtype=torch.float64).to("cuda:0")
+    g = (B @ xt).contiguous()
+    ref = torch.linalg.solve(B, g)
+    Bc = B.t().contiguous().t()
+    for _ in range(2):
+        st, x = _call(lib, Bc, g, m)
+        assert st == 0
+        assert torch.max(torch.abs(x - ref)) / torch.max(torch.abs(ref)) < 1e-10
