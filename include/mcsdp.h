@@ -106,6 +106,12 @@ typedef struct {
   int32_t solve_warps;   /* unused (kept for layout compatibility) */
   double mixed_gap;      /* mixed form: relative gap below which every stage runs in FP64
                             (default 1e-5) */
+  int32_t root_rows;     /* dense root: cliques with more than this many rows (or more than 96
+                            columns) are merged, with all their ancestors, into one root clique R
+                            handled by dense kernels; the other cliques keep the small-clique
+                            kernels.  0 = default (160, the small-clique kernels' limit),
+                            < 0 = never (such problems are then rejected), 1..160 = a lower
+                            threshold (smaller problems then also get a dense root) */
 } mcsdp_options;
 
 void mcsdp_default_options(mcsdp_options *opt);

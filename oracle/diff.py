@@ -28,15 +28,16 @@ def _sym(M):
 def central_point(A, b, mu, z0, tol=1e-13, max_newton=60):
     """Newton on F(z) = A(mu Y(z)^{-1}) - b from a dual-feasible z0, halving the step until
     Y stays positive definite, until max|F| <= tol max(1, max|b|).  If Newton stops gaining
-    (three steps in a row that do not halve the residual) the point is accepted only when the
-    residual is at the rounding level of evaluating F, rho = 64 eps cond(Y) max|A(X)| / max(1,
-    max|b|) (Y^{-1} is formed with relative error about eps cond(Y)); otherwise it raises.
+    (three full steps in a row that do not halve the residual) the point is accepted only when the
+    residual is at the rounding level of evaluating F, rho = 64 eps cond(Y) max_k |A_k|.|X| /
+    max(1, max|b|) (Y^{-1} is formed with relative error about eps cond(Y)); otherwise it raises.
     Returns z, Y, X = mu Y^{-1} and the relative residual reached."""
     z = np.array(z0, dtype=np.float64)
     scale = max(1.0, float(np.max(np.abs(b))))
     eps = np.finfo(np.float64).eps
     best = None
     stalled = 0
+    full = False
     for _ in range(max_newton):
         Y = dual_slack(A, z)
         Yinv = np.linalg.inv(Y)
@@ -47,10 +48,15 @@ def central_point(A, b, mu, z0, tol=1e-13, max_newton=60):
         res = np.max(np.abs(F)) / scale
         if res <= tol:
             return z, Y, X, res
-        stalled = stalled + 1 if best is not None and res > 0.5 * best else 0
+        # a full Newton step (t = 1) that does not halve the residual: rounding, not the
+        # damping that keeps Y positive definite far from the point, limits the progress
+        stalled = stalled + 1 if best is not None and full and res > 0.5 * best else 0
         best = res if best is None else min(best, res)
         if stalled >= 3:
-            rho = 64.0 * eps * np.linalg.cond(Y) * max(1.0, float(np.max(np.abs(AX)))) / scale
+            # |A|(|X|): the magnitudes the residual's rounding scales with
+            absAX = np.bincount(A.k, weights=np.abs(A.v) * np.abs(X[A.r, A.c]),
+                                minlength=A.m + 1)[1:]
+            rho = 64.0 * eps * np.linalg.cond(Y) * max(1.0, float(np.max(absAX))) / scale
             if res <= rho:
                 return z, Y, X, res
             raise RuntimeError("centring stalled above the rounding level")
@@ -66,6 +72,7 @@ def central_point(A, b, mu, z0, tol=1e-13, max_newton=60):
                 if t < 1e-12:
                     raise RuntimeError("centring step collapsed")
         z = z + t * dz
+        full = t == 1.0
     raise RuntimeError("centring did not converge")
 
 

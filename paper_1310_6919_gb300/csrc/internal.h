@@ -114,6 +114,35 @@ struct DevSym {
   const int64_t *pm_ptr;
   const int *pm_sn;
   const double *b;
+  // dense root (see kern_root.cu): the forest's supernodes are 0 .. nforest - 1; when nR > 0 the
+  // root is supernode ns - 1, columns [n - nR, n), a column-major nR x nR block at root_valp
+  int nforest, nR;
+  int64_t root_valp;
+};
+
+// Contributions of the forest's supernodes to the root block of Y (K2 at the root): entry e of
+// the root block (offset ent[e] in the column-major block) receives, for c in [ptr[e],
+// ptr[e + 1]), the product of rows a = ab[c] & 0xffff and b = ab[c] >> 16 of the block of update
+// u[c]'s source supernode (upd_meta), summed over its columns.
+struct RootGather {
+  int64_t nent;
+  const int64_t *ent, *ptr;
+  const int *u, *ab;
+};
+
+// C(i, j) = alpha sum_{l in [klo, K)} A[l + i lda] B[l + j ldb] + beta C(i, j), C(i, j) at
+// C[i cs_i + j cs_j] (kern_root.cu: k_gemm_tn)
+template <class T>
+struct GemmArgs {
+  int M, N, K, klo;
+  const T *A;
+  int64_t lda;
+  const T *B;
+  int64_t ldb;
+  T *C;
+  int64_t cs_i, cs_j;
+  T alpha, beta;
+  int lower, mirror, tri_a;
 };
 
 // Skip rule of the level-scheduled solves: (supernode t, tile) is processed only if bit t is set
@@ -214,16 +243,72 @@ void launch_update(const DevSym &S, double *Xbar, const double *dX, double ap, d
                    const double *dz, double ad, cudaStream_t st);
 void launch_set_identity(const DevSym &S, double *Xbar, cudaStream_t st);
 
+// ---------------- dense root (kern_root.cu) ----------------
+void launch_root_assemble(const DevSym &S, const RootGather &G, const double *Yb,
+                          const double *dY, double alpha, double *Nbuf, cudaStream_t st);
+template <class T>
+void gemm_tn(const GemmArgs<T> &g, cudaStream_t st);
+// X = L^{-1} (L dense lower with its rows mirrored above the diagonal, Linv its 32 x 32 diagonal
+// block inverses); returns launches
+template <class T>
+int dense_trtri(const T *L, int64_t ldl, const T *Linv, T *X, int64_t ldx, int n, cudaStream_t st);
+// lower triangle of X^T X at Z[i zs_i + j zs_j] (and mirrored)
+template <class T>
+int dense_lauum(const T *X, int64_t ldx, int n, T *Z, int64_t zs_i, int64_t zs_j, bool mirror,
+                cudaStream_t st);
+template <class Ti, class To>
+void copy_square(const Ti *src, int64_t lds, To *dst, int64_t ldd, int n, cudaStream_t st);
+template <class Ti, class To>
+void symmetrize(const Ti *src, int64_t lds, To *dst, int64_t ldd, int n, cudaStream_t st);
+template <class T>
+void dotcols(const T *A, int64_t ld, int ncol, int len, int range, const double *v, double *w,
+             double alpha, double beta, cudaStream_t st);
+void lz_alpha(int n, double *w, const double *gvj, const double *vj, const double *vjm1,
+              double *s, int j, cudaStream_t st);
+void lz_reorth(int n, int jcount, double *w, const double *Qd, const double *Q, cudaStream_t st);
+void lz_beta(int n, const double *w, const double *gw, double *vnext, double *gvnext, double *s,
+             int j, cudaStream_t st);
+void lz_normalise(int n, double *v, double *gv, cudaStream_t st);
+void copy_lower(const double *src, int64_t lds, double *dst, int64_t ldd, int n, cudaStream_t st);
+template <class T>
+void launch_unit_cols(T *W, int64_t ldw, const int *colw, int k0, int nk, cudaStream_t st);
+template <class T>
+void launch_root_rows_from_cols(T *W, int64_t ldw, const int *colw, int nR, int nF, cudaStream_t st);
+template <class T>
+void launch_extract_dense(const DevSym &S, const T *W, int64_t ldw, const int *colw, double *outE,
+                          cudaStream_t st);
+template <class T>
+void launch_times_pattern(const DevSym &S, const double *D, const T *W, T *V, int64_t ldw,
+                          const int *colw, cudaStream_t st);
+template <class T>
+void launch_forest_M(const DevSym &S, const T *V, const T *Wy, int64_t ldw, int ncolw,
+                     double *Mlow, double *Mup, cudaStream_t st);
+template <class T>
+void launch_root_M(const T *M, int nR, double *Mlow_root, double *Mup_root, cudaStream_t st);
+void launch_root_dx(int nR, double betamu, const double *X, const double *YinvE, const double *Mlow,
+                    const double *Mup, double *dX, cudaStream_t st);
+// mirror the strict lower triangle of a column-major square into its strict upper triangle
+template <class T>
+void mirror_lower(T *A, int64_t ld, int n, cudaStream_t st);
+// v[i] = a pseudo-random value in [-1, 1) from a counter-based hash of (i, seed)
+void fill_hash(double *v, int n, unsigned seed, cudaStream_t st);
+// dst[colw[k]] = src[k] (k < n)
+void permute_to_cols(const double *src, const int *colw, double *dst, int n, cudaStream_t st);
+// the dense Cholesky of an n x n column-major block (FP64 task queue; kern_dense.cu)
+int dense_potrf(double *A, int64_t ld, int n, int *status, double *Linv, cudaStream_t st, int *sync,
+                long long budget);
+
 // ---------------- SCM assembly (kern_scm.cu) ----------------
 // Tiles B[J_h, J_g] for the listed (h, g), h >= g, from WX = X̂[:, P_g] and WY = Y^{-1}[:, P_g]
 // (row-major, ld = ldw, the columns of group g start at goff[g]); h_i = A_i . Y^{-1} on the
 // diagonal tiles.
 size_t scm_tiles_smem_bytes(const DevSym &S, int pmax);
 // T = double: FP64 form; T = float: mixed form (FP32 operands and sums, entries stored in FP64)
+// colmap != nullptr (dense completion): the column of vertex k is colmap[k] (goff unused)
 template <class T>
 void launch_scm_tiles(const DevSym &S, const int2 *tiles, int ntiles, const T *WX, const T *WY,
                       int64_t ldw, const int *goff, double *B, int64_t ldb, double *hvec,
-                      int pmax, cudaStream_t st);
+                      int pmax, cudaStream_t st, const int *colmap = nullptr);
 
 // ---------------- dense SCM factorisation (kern_dense.cu) ----------------
 // B internal, (m+1) x m lower, column-major, ld = ldb; row m holds g^T on entry and

@@ -939,6 +939,11 @@ void chol_graphs_destroy(CholStreams *cs) {
   }
 }
 
+int dense_potrf(double *A, int64_t ld, int n, int *status, double *Linv, cudaStream_t st, int *sync,
+                long long budget) {
+  return dense_chol_dag<double>(A, ld, n, n, status, Linv, st, sync, budget);
+}
+
 int dense_chol_bordered(double *B, int64_t ldb, int m, int *status, double *Linv_all,
                         cudaStream_t st, CholStreams *cs) {
   return dense_chol_cached<double>(B, ldb, m, m + 1, status, Linv_all, st, cs);

@@ -1,0 +1,728 @@
+// Dense-root kernels.  When the chordal extension has cliques too large for the small-clique
+// (shared-memory) kernels, the symbolic analysis merges them, with their ancestors, into one
+// root supernode R whose clique is R itself (a dense |R| x |R| block of the layout, column-major).
+// Everything below R is a forest of small cliques handled by the level-scheduled kernels; this
+// file holds the dense work on R:
+//   * Y = N N^T at the root (type (v) of Sec. 3.1): the root block of Y minus the forest's
+//     contributions (gathered per entry in a fixed order), then a dense Cholesky;
+//   * X = L^{-1} of a dense Cholesky factor (blocked, right-looking) and Z = X^T X, which give
+//     (Y^{-1})_RR = N_RR^{-T} N_RR^{-1} and, for Algorithm 1 at the root, X̄_RR^{-1};
+//   * one GEMM shape C = alpha A^T B + beta C with A, B column-major (both operands K-major),
+//     used by the inverse, its product, and the P-MATRIX (eq. newdX2) on the root block;
+//   * matrix-vector products and vector kernels for the Lanczos step-length bounds.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "internal.h"
+
+namespace mcsdp {
+
+// ---------------------------------------------------------------------------------------------
+// K2 at the root
+
+// N_RR = Yb_RR + alpha dY_RR over the whole column-major block (its strict upper part is unused)
+__global__ void k_root_init(const double *__restrict__ Yb, const double *__restrict__ dY,
+                            double alpha, double *N, int64_t cnt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt;
+       i += (int64_t)gridDim.x * blockDim.x)
+    N[i] = dY ? fma(alpha, dY[i], Yb[i]) : Yb[i];
+}
+
+// N_RR(e) -= sum over the forest supernodes d whose clique meets R of N(a, S_d) . N(b, S_d),
+// (a, b) the rows of d's block landing on the entry; the contributions of every entry are
+// listed in a fixed order, so the sum is reproducible bit for bit
+__global__ void k_root_gather(const UpdMeta *__restrict__ meta, RootGather G,
+                              const double *__restrict__ Nsrc, double *Nroot) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < G.nent;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int64_t c = G.ptr[e]; c < G.ptr[e + 1]; ++c) {
+      const UpdMeta q = meta[G.u[c]];
+      const int ab = G.ab[c], a = ab & 0xffff, b = ab >> 16;
+      const double *col = Nsrc + q.valp;
+      for (int l = 0; l < q.dncol; ++l) {
+        const int64_t o = (int64_t)l * q.dnrow;
+        acc = fma(col[o + a], col[o + b], acc);
+      }
+    }
+    Nroot[G.ent[e]] -= acc;
+  }
+}
+
+void launch_root_assemble(const DevSym &S, const RootGather &G, const double *Yb,
+                          const double *dY, double alpha, double *Nbuf, cudaStream_t st) {
+  const int64_t cnt = (int64_t)S.nR * S.nR;
+  int blocks = (int)std::min<int64_t>(4096, (cnt + 255) / 256);
+  k_root_init<<<blocks, 256, 0, st>>>(Yb + S.root_valp, dY ? dY + S.root_valp : nullptr, alpha,
+                                      Nbuf + S.root_valp, cnt);
+  if (G.nent > 0) {
+    blocks = (int)std::min<int64_t>(4096, (G.nent + 255) / 256);
+    k_root_gather<<<blocks, 256, 0, st>>>(S.upd_meta, G, Nbuf, Nbuf + S.root_valp);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// GEMM C(i, j) = alpha sum_{l in [klo, K)} A[l + i lda] B[l + j ldb] + beta C(i, j), i < M, j < N.
+// Both operands column-major with the summation index l contiguous (C = A^T B).  C(i, j) is at
+// C[i cs_i + j cs_j] (column- or row-major).  lower: only i >= j is formed (tiles above the
+// diagonal skipped); mirror: C(j, i) is written too.  tri_a: A[l + i lda] = 0 for l < i (A^T
+// lower triangular), so a tile's sum starts at its first row.  64 x 64 tile per CTA, 256
+// threads, 4 x 4 outputs per thread, K in steps of 16 through shared memory.
+constexpr int GB = 64, GK = 16;
+
+template <class T>
+__global__ void __launch_bounds__(256) k_gemm_tn(GemmArgs<T> g) {
+  __shared__ T As[2][GK][GB + 1];
+  __shared__ T Bs[2][GK][GB + 1];
+  const int i0 = blockIdx.x * GB, j0 = blockIdx.y * GB;
+  if (g.lower && i0 + GB - 1 < j0) return;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  int klo = g.klo;
+  if (g.tri_a) klo = max(klo, i0);
+  T acc[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[p][q] = T(0);
+  // loader: element e = tid + 256 r (r < 4) of the 16 x 64 tile: l = e % 16, i = e / 16
+  T ra[4], rb[4];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int e = tid + 256 * r, l = e & (GK - 1), ii = e >> 4;
+      const int gl = k0 + l, gi = i0 + ii, gj = j0 + ii;
+      ra[r] = (gl < g.K && gi < g.M) ? g.A[gl + (int64_t)gi * g.lda] : T(0);
+      rb[r] = (gl < g.K && gj < g.N) ? g.B[gl + (int64_t)gj * g.ldb] : T(0);
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int e = tid + 256 * r, l = e & (GK - 1), ii = e >> 4;
+      As[buf][l][ii] = ra[r];
+      Bs[buf][l][ii] = rb[r];
+    }
+  };
+  int buf = 0;
+  if (klo < g.K) {
+    load(klo);
+    store(0);
+  }
+  __syncthreads();
+  for (int k0 = klo; k0 < g.K; k0 += GK) {
+    const bool more = k0 + GK < g.K;
+    if (more) load(k0 + GK);
+#pragma unroll
+    for (int l = 0; l < GK; ++l) {
+      T a[4], b[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) a[p] = As[buf][l][ty + 16 * p];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) b[q] = Bs[buf][l][tx + 16 * q];
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fma(a[p], b[q], acc[p][q]);
+    }
+    if (more) {
+      store(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const int i = i0 + ty + 16 * p;
+    if (i >= g.M) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = j0 + tx + 16 * q;
+      if (j >= g.N || (g.lower && i < j)) continue;
+      T *dst = g.C + (int64_t)i * g.cs_i + (int64_t)j * g.cs_j;
+      const T v = g.beta == T(0) ? g.alpha * acc[p][q] : fma(g.alpha, acc[p][q], g.beta * *dst);
+      *dst = v;
+      if (g.mirror && i != j) g.C[(int64_t)j * g.cs_i + (int64_t)i * g.cs_j] = v;
+    }
+  }
+}
+
+template <class T>
+void gemm_tn(const GemmArgs<T> &g, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0) return;
+  dim3 grid((g.M + GB - 1) / GB, (g.N + GB - 1) / GB);
+  k_gemm_tn<T><<<grid, 256, 0, st>>>(g);
+}
+
+// ---------------------------------------------------------------------------------------------
+// X = L^{-1} for a dense lower-triangular L (n x n, column-major, ld): L's rows are also held
+// transposed in its strict upper triangle (as the dense Cholesky leaves them), and Linv holds the
+// inverses of its 32 x 32 diagonal blocks (column-major, ld 32).  Blocked forward substitution of
+// L X = I by block rows, right-looking: X starts as I; at step k, block row k becomes
+// Linv_kk X_k (its columns 0 .. k), then the rows below are updated, X_i -= L_ik X_k, by the GEMM
+// (A(l, i) = L(i, l) from the transposed copy).  Only the lower triangle of X is written.
+
+template <class T>
+__global__ void k_set_unit_lower(T *X, int64_t ld, int n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    X[i + (int64_t)j * ld] = i == j ? T(1) : T(0);
+  }
+}
+
+// block row k (rows k0 .. k0 + nb): X[k0.., c0 .. c0 + 32) = Linv_k X[k0.., c0 .. c0 + 32)
+template <class T>
+__global__ void k_trtri_scale(const T *__restrict__ Linv_k, T *X, int64_t ld, int k0, int nb,
+                              int ncol) {
+  __shared__ T Ls[32][33];
+  __shared__ T Xs[32][33];
+  const int c0 = blockIdx.x * 32;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < 32 * 32; e += blockDim.x) {
+    const int r = e & 31, c = e >> 5;
+    Ls[r][c] = (r < nb && c < nb) ? Linv_k[r + c * 32] : T(0);
+    Xs[r][c] = (r < nb && c0 + c < ncol) ? X[(k0 + r) + (int64_t)(c0 + c) * ld] : T(0);
+  }
+  __syncthreads();
+  const int r = tid & 31, cq = tid >> 5;  // 8 warps, 4 columns each
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = cq * 4 + q;
+    T acc = T(0);
+#pragma unroll 8
+    for (int l = 0; l < 32; ++l) acc = fma(Ls[r][l], Xs[l][c], acc);
+    if (r < nb && c0 + c < ncol) X[(k0 + r) + (int64_t)(c0 + c) * ld] = acc;
+  }
+}
+
+template <class T>
+int dense_trtri(const T *L, int64_t ldl, const T *Linv, T *X, int64_t ldx, int n, cudaStream_t st) {
+  if (n <= 0) return 0;
+  const int64_t cnt = (int64_t)n * n;
+  const int blocks = (int)std::min<int64_t>(4096, (cnt + 255) / 256);
+  k_set_unit_lower<T><<<blocks, 256, 0, st>>>(X, ldx, n);
+  int nl = 1;
+  for (int k0 = 0, k = 0; k0 < n; k0 += 32, ++k) {
+    const int nb = std::min(32, n - k0), ncol = k0 + nb;
+    k_trtri_scale<T><<<(ncol + 31) / 32, 256, 0, st>>>(Linv + (int64_t)k * 1024, X, ldx, k0, nb,
+                                                       ncol);
+    ++nl;
+    const int r0 = k0 + nb;
+    if (r0 >= n) break;
+    GemmArgs<T> g{};
+    g.M = n - r0;
+    g.N = ncol;
+    g.K = nb;
+    g.A = L + k0 + (int64_t)r0 * ldl;  // A(l, i) = L(r0 + i, k0 + l), held at row k0 + l, column r0 + i
+    g.lda = ldl;
+    g.B = X + k0;  // B(l, j) = X(k0 + l, j)
+    g.ldb = ldx;
+    g.C = X + r0;  // C(i, j) = X(r0 + i, j)
+    g.cs_i = 1;
+    g.cs_j = ldx;
+    g.alpha = T(-1);
+    g.beta = T(1);
+    gemm_tn<T>(g, st);
+    ++nl;
+  }
+  return nl;
+}
+
+// Z = X^T X for a lower-triangular X (n x n, column-major, zero above the diagonal): the lower
+// triangle of Z at Z[i zs_i + j zs_j], mirrored when mirror is set
+template <class T>
+int dense_lauum(const T *X, int64_t ldx, int n, T *Z, int64_t zs_i, int64_t zs_j, bool mirror,
+                cudaStream_t st) {
+  GemmArgs<T> g{};
+  g.M = n;
+  g.N = n;
+  g.K = n;
+  g.A = X;
+  g.lda = ldx;
+  g.B = X;
+  g.ldb = ldx;
+  g.C = Z;
+  g.cs_i = zs_i;
+  g.cs_j = zs_j;
+  g.alpha = T(1);
+  g.beta = T(0);
+  g.lower = 1;
+  g.mirror = mirror ? 1 : 0;
+  g.tri_a = 1;
+  gemm_tn<T>(g, st);
+  return 1;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Copies and casts between the root block, the dense completion buffers and scratch
+
+// dst[i + j ld_d] = (To) src[i + j ld_s] for i, j < n (whole square)
+template <class Ti, class To>
+__global__ void k_copy_square(const Ti *__restrict__ src, int64_t lds, To *dst, int64_t ldd, int n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    dst[i + (int64_t)j * ldd] = (To)src[i + (int64_t)j * lds];
+  }
+}
+
+template <class Ti, class To>
+void copy_square(const Ti *src, int64_t lds, To *dst, int64_t ldd, int n, cudaStream_t st) {
+  if (n <= 0) return;
+  const int64_t cnt = (int64_t)n * n;
+  const int blocks = (int)std::min<int64_t>(4096, (cnt + 255) / 256);
+  k_copy_square<Ti, To><<<blocks, 256, 0, st>>>(src, lds, dst, ldd, n);
+}
+
+// full symmetric matrix from the lower triangle of a column-major block: dst(i, j) = src(max, min)
+template <class Ti, class To>
+__global__ void k_symmetrize(const Ti *__restrict__ src, int64_t lds, To *dst, int64_t ldd, int n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    const int a = i > j ? i : j, b = i > j ? j : i;
+    dst[i + (int64_t)j * ldd] = (To)src[a + (int64_t)b * lds];
+  }
+}
+
+template <class Ti, class To>
+void symmetrize(const Ti *src, int64_t lds, To *dst, int64_t ldd, int n, cudaStream_t st) {
+  if (n <= 0) return;
+  const int64_t cnt = (int64_t)n * n;
+  const int blocks = (int)std::min<int64_t>(4096, (cnt + 255) / 256);
+  k_symmetrize<Ti, To><<<blocks, 256, 0, st>>>(src, lds, dst, ldd, n);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Matrix-vector products for the Lanczos bounds
+// w_j = beta w_j + alpha sum_{i in range(j)} A[i + j ld] v_i, one warp per column j;
+// range: 0 -> [0, len), 1 -> [j, len) (A lower), 2 -> [0, j] (A upper)
+template <class T>
+__global__ void k_dotcols(const T *__restrict__ A, int64_t ld, int ncol, int len, int range,
+                          const double *__restrict__ v, double *w, double alpha, double beta) {
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= ncol) return;
+  const int lo = range == 1 ? j : 0, hi = range == 2 ? min(len, j + 1) : len;
+  const T *col = A + (int64_t)j * ld;
+  double acc = 0.0;
+  for (int i = lo + lane; i < hi; i += 32) acc = fma((double)col[i], v[i], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) w[j] = beta == 0.0 ? alpha * acc : fma(alpha, acc, beta * w[j]);
+}
+
+template <class T>
+void dotcols(const T *A, int64_t ld, int ncol, int len, int range, const double *v, double *w,
+             double alpha, double beta, cudaStream_t st) {
+  if (ncol <= 0) return;
+  k_dotcols<T><<<(ncol + 7) / 8, 256, 0, st>>>(A, ld, ncol, len, range, v, w, alpha, beta);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Lanczos vector kernels (one CTA; the vectors are short: n <= a few tens of thousands)
+// out[0] = sum_i x_i y_i (fixed order: per-thread strided sums, then a tree)
+__device__ double block_sum(double v, double *red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One three-term step.  w holds op(v_j) (already in place).  s[2j] = alpha_j = <w, v_j>_G with
+// Gw given as gw (G = I: gw = w), then w -= alpha_j v_j + beta_{j-1} v_{j-1}.
+__global__ void k_lz_alpha(int n, double *w, const double *__restrict__ gvj,
+                           const double *__restrict__ vj, const double *__restrict__ vjm1,
+                           double *s, int j) {
+  __shared__ double red[32];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a = fma(w[i], gvj[i], a);
+  a = block_sum(a, red);
+  __shared__ double sa;
+  if (threadIdx.x == 0) {
+    sa = a;
+    s[2 * j] = a;
+  }
+  __syncthreads();
+  const double b = j > 0 ? s[2 * j - 1] : 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double x = w[i] - sa * vj[i];
+    if (j > 0) x -= b * vjm1[i];
+    w[i] = x;
+  }
+}
+
+// full reorthogonalisation against v_0 .. v_{jcount-1}: h_c = <Qd_c, w>, w -= sum_c h_c Q_c
+// (Qd = G Q for the G-inner product, Q itself for the Euclidean one)
+__global__ void k_lz_reorth(int n, int jcount, double *w, const double *__restrict__ Qd,
+                            const double *__restrict__ Q) {
+  __shared__ double red[32];
+  __shared__ double h[128];
+  for (int c = 0; c < jcount; ++c) {
+    double a = 0.0;
+    const double *q = Qd + (int64_t)c * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) a = fma(q[i], w[i], a);
+    a = block_sum(a, red);
+    if (threadIdx.x == 0) h[c] = a;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double x = w[i];
+    for (int c = 0; c < jcount; ++c) x -= h[c] * Q[(int64_t)c * n + i];
+    w[i] = x;
+  }
+}
+
+// beta_j = sqrt(<w, w>_G) (gw = G w), s[2j+1] = beta_j, v_{j+1} = w / beta_j and
+// G v_{j+1} = gw / beta_j (gvnext may alias nothing else; both 0 if beta_j = 0)
+__global__ void k_lz_beta(int n, const double *__restrict__ w, const double *__restrict__ gw,
+                          double *vnext, double *gvnext, double *s, int j) {
+  __shared__ double red[32];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a = fma(w[i], gw[i], a);
+  a = block_sum(a, red);
+  __shared__ double sb;
+  if (threadIdx.x == 0) {
+    sb = sqrt(fmax(a, 0.0));
+    s[2 * j + 1] = sb;
+  }
+  __syncthreads();
+  const double inv = sb > 0.0 ? 1.0 / sb : 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    vnext[i] = w[i] * inv;
+    if (gvnext) gvnext[i] = gw[i] * inv;
+  }
+}
+
+// v <- v / sqrt(<v, v>_G), and gv = G v likewise (gv may be v itself)
+__global__ void k_lz_normalise(int n, double *v, double *gv) {
+  __shared__ double red[32];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a = fma(v[i], gv[i], a);
+  a = block_sum(a, red);
+  __shared__ double sc;
+  if (threadIdx.x == 0) sc = a > 0.0 ? 1.0 / sqrt(a) : 0.0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    v[i] *= sc;
+    if (gv != v) gv[i] *= sc;
+  }
+}
+
+void lz_alpha(int n, double *w, const double *gvj, const double *vj, const double *vjm1,
+              double *s, int j, cudaStream_t st) {
+  k_lz_alpha<<<1, 1024, 0, st>>>(n, w, gvj, vj, vjm1, s, j);
+}
+void lz_reorth(int n, int jcount, double *w, const double *Qd, const double *Q, cudaStream_t st) {
+  k_lz_reorth<<<1, 1024, 0, st>>>(n, jcount, w, Qd, Q);
+}
+void lz_beta(int n, const double *w, const double *gw, double *vnext, double *gvnext, double *s,
+             int j, cudaStream_t st) {
+  k_lz_beta<<<1, 1024, 0, st>>>(n, w, gw, vnext, gvnext, s, j);
+}
+void lz_normalise(int n, double *v, double *gv, cudaStream_t st) {
+  k_lz_normalise<<<1, 1024, 0, st>>>(n, v, gv);
+}
+
+// lower triangle of a column-major square copied, the strict upper triangle of dst set to zero
+__global__ void k_copy_lower(const double *__restrict__ src, int64_t lds, double *dst, int64_t ldd,
+                             int n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    dst[i + (int64_t)j * ldd] = i >= j ? src[i + (int64_t)j * lds] : 0.0;
+  }
+}
+void copy_lower(const double *src, int64_t lds, double *dst, int64_t ldd, int n, cudaStream_t st) {
+  if (n <= 0) return;
+  const int blocks = (int)std::min<int64_t>(4096, ((int64_t)n * n + 255) / 256);
+  k_copy_lower<<<blocks, 256, 0, st>>>(src, lds, dst, ldd, n);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Dense completion buffers (row-major n x ldw, column of vertex k at colw[k]; the root's
+// vertices occupy the first |R| columns)
+
+// W[i][colw[k]] = 1 for the rhs-th unit column k = k0 + rhs of the forest
+template <class T>
+__global__ void k_unit_cols(T *W, int64_t ldw, const int *__restrict__ colw, int k0, int nk) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < nk) W[(int64_t)(k0 + r) * ldw + colw[k0 + r]] = T(1);
+}
+
+// rows of the root, forest columns: W[rbase + i][colw[t]] = W[t][i] for t < nF, i < nR
+// (X̂_{R,t} = X̂_{t,R}^T, the symmetry of the completed matrix)
+template <class T>
+__global__ void k_root_rows_from_cols(T *W, int64_t ldw, const int *__restrict__ colw, int nR,
+                                      int nF) {
+  __shared__ T tile[32][33];
+  const int t0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    const int t = t0 + r, i = i0 + tx;
+    tile[r][tx] = (t < nF && i < nR) ? W[(int64_t)t * ldw + i] : T(0);
+  }
+  __syncthreads();
+  const int rbase = nF;
+  for (int r = ty; r < 32; r += 8) {
+    const int i = i0 + r, t = t0 + tx;
+    if (t < nF && i < nR) W[(int64_t)(rbase + i) * ldw + colw[t]] = tile[tx][r];
+  }
+}
+
+// lower(E) values of a dense completed matrix: outE at every layout entry (row r, column k of
+// supernode s, r >= k) = W[r][colw[k]]; root block included (the root occupies columns
+// [0, nR) and rows [nF, n))
+template <class T>
+__global__ void k_extract_dense(DevSym S, const T *__restrict__ W, int64_t ldw,
+                                const int *__restrict__ colw, double *outE) {
+  const int s = blockIdx.y;
+  const int64_t r0 = S.sn_rowptr[s];
+  const int nrow = (int)(S.sn_rowptr[s + 1] - r0);
+  const int c0 = S.sn_col[s], ncol = S.sn_col[s + 1] - c0;
+  const int64_t v0 = S.sn_valptr[s];
+  const int64_t cnt = (int64_t)nrow * ncol;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < cnt;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int p = (int)(e % nrow), lc = (int)(e / nrow);
+    if (p < lc) continue;
+    outE[v0 + e] = (double)W[(int64_t)S.rows[r0 + p] * ldw + colw[c0 + lc]];
+  }
+}
+
+// V[i][colw[b]] = sum_a W[i][colw[a]] D_ab on the aggregate pattern (V = W D, D symmetric held
+// on the layout at the aggregate positions), thread per (row i, column b)
+template <class T>
+__global__ void k_times_pattern(DevSym S, const double *__restrict__ D, const T *__restrict__ W,
+                                T *V, int64_t ldw, const int *__restrict__ colw) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= S.n) return;
+  for (int i = blockIdx.y; i < S.n; i += gridDim.y) {
+    const T *wr = W + (int64_t)i * ldw;
+    T acc = T(0);
+    for (int q = S.arow_ptr[b]; q < S.arow_ptr[b + 1]; ++q)
+      acc = fma((T)D[S.arow_off[q]], wr[colw[S.arow_col[q]]], acc);
+    V[(int64_t)i * ldw + colw[b]] = acc;
+  }
+}
+
+// M = X̂ D Y^{-1} on the forest's layout entries from the rows of V = X̂ D and of Wy = Y^{-1}:
+// Mlow at (r, k) = V[r] . Wy[k], Mup at (r, k) = V[k] . Wy[r] (rows dotted over all columns);
+// one CTA per forest supernode, the clique's rows staged in chunks of columns
+template <class T>
+__global__ void __launch_bounds__(256) k_forest_M(DevSym S, const T *__restrict__ V,
+                                                  const T *__restrict__ Wy, int64_t ldw,
+                                                  int ncolw, double *Mlow, double *Mup) {
+  constexpr int CH = 32, PER = 8;
+  extern __shared__ __align__(16) unsigned char smf[];
+  const int s = blockIdx.x;
+  const int64_t r0 = S.sn_rowptr[s];
+  const int nrow = (int)(S.sn_rowptr[s + 1] - r0);
+  const int ncol = S.sn_col[s + 1] - S.sn_col[s];
+  const int64_t v0 = S.sn_valptr[s];
+  T *Vs = reinterpret_cast<T *>(smf);  // [nrow][CH]
+  T *Ys = Vs + nrow * CH;               // [nrow][CH]
+  int *rw = reinterpret_cast<int *>(Ys + nrow * CH);
+  const int tid = threadIdx.x;
+  for (int p = tid; p < nrow; p += blockDim.x) rw[p] = S.rows[r0 + p];
+  const int nout = nrow * ncol;
+  __syncthreads();
+  // outputs in passes of 256 x PER; each thread keeps the lower and upper sums of PER of them
+  for (int pass = 0; pass * 256 * PER < nout; ++pass) {
+    double lo[PER], up[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) lo[q] = up[q] = 0.0;
+    for (int c0 = 0; c0 < ncolw; c0 += CH) {
+      for (int e = tid; e < nrow * CH; e += blockDim.x) {
+        const int p = e / CH, c = e % CH;
+        const int64_t o = (int64_t)rw[p] * ldw + c0 + c;
+        const bool in = c0 + c < ncolw;
+        Vs[e] = in ? V[o] : T(0);
+        Ys[e] = in ? Wy[o] : T(0);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int e = pass * 256 * PER + tid + q * 256;
+        if (e >= nout) break;
+        const int p = e % nrow, lc = e / nrow;
+        if (p < lc) continue;
+        const T *vp = Vs + p * CH, *yl = Ys + lc * CH, *vl = Vs + lc * CH, *yp = Ys + p * CH;
+        double a = lo[q], b = up[q];
+#pragma unroll 8
+        for (int c = 0; c < CH; ++c) {
+          a = fma((double)vp[c], (double)yl[c], a);
+          b = fma((double)vl[c], (double)yp[c], b);
+        }
+        lo[q] = a;
+        up[q] = b;
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = pass * 256 * PER + tid + q * 256;
+      if (e >= nout) break;
+      const int p = e % nrow, lc = e / nrow;
+      if (p < lc) continue;
+      Mlow[v0 + e] = lo[q];
+      Mup[v0 + e] = up[q];
+    }
+  }
+}
+
+// the root block's Mlow / Mup from the dense product M_RR (column-major, ld nR)
+template <class T>
+__global__ void k_root_M(const T *__restrict__ M, int nR, double *Mlow, double *Mup) {
+  const int64_t cnt = (int64_t)nR * nR;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < cnt;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % nR), j = (int)(e / nR);
+    if (i < j) continue;
+    Mlow[e] = (double)M[e];
+    Mup[e] = (double)M[j + (int64_t)i * nR];
+  }
+}
+
+// dX on the root block (lower part; the upper part zero): beta mu Y^{-1} - X̄ - sym(M)
+__global__ void k_root_dx(int nR, double betamu, const double *__restrict__ X,
+                          const double *__restrict__ YinvE, const double *__restrict__ Mlow,
+                          const double *__restrict__ Mup, double *dX) {
+  const int64_t cnt = (int64_t)nR * nR;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < cnt;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % nR), j = (int)(e / nR);
+    double v;
+    if (i < j) v = 0.0;
+    else if (i == j) v = betamu * YinvE[e] - X[e] - Mlow[e];
+    else v = betamu * YinvE[e] - X[e] - 0.5 * (Mlow[e] + Mup[e]);
+    dX[e] = v;
+  }
+}
+
+template <class T>
+void launch_unit_cols(T *W, int64_t ldw, const int *colw, int k0, int nk, cudaStream_t st) {
+  if (nk > 0) k_unit_cols<T><<<(nk + 255) / 256, 256, 0, st>>>(W, ldw, colw, k0, nk);
+}
+template <class T>
+void launch_root_rows_from_cols(T *W, int64_t ldw, const int *colw, int nR, int nF, cudaStream_t st) {
+  if (nR <= 0 || nF <= 0) return;
+  dim3 grid((nF + 31) / 32, (nR + 31) / 32), blk(32, 8);
+  k_root_rows_from_cols<T><<<grid, blk, 0, st>>>(W, ldw, colw, nR, nF);
+}
+template <class T>
+void launch_extract_dense(const DevSym &S, const T *W, int64_t ldw, const int *colw, double *outE,
+                          cudaStream_t st) {
+  // forest supernodes: one CTA each; the root block: many
+  if (S.nforest > 0) k_extract_dense<T><<<dim3(1, S.nforest), 256, 0, st>>>(S, W, ldw, colw, outE);
+  if (S.nR > 0) {
+    DevSym R = S;
+    // the root alone: shift the supernode index by launching with blockIdx.y = 0 on s = ns - 1
+    R.sn_rowptr = S.sn_rowptr + (S.ns - 1);
+    R.sn_col = S.sn_col + (S.ns - 1);
+    R.sn_valptr = S.sn_valptr + (S.ns - 1);
+    const int blocks = (int)std::min<int64_t>(4096, ((int64_t)S.nR * S.nR + 255) / 256);
+    k_extract_dense<T><<<dim3(blocks, 1), 256, 0, st>>>(R, W, ldw, colw, outE);
+  }
+}
+template <class T>
+void launch_times_pattern(const DevSym &S, const double *D, const T *W, T *V, int64_t ldw,
+                          const int *colw, cudaStream_t st) {
+  dim3 grid((S.n + 127) / 128, std::min(S.n, 65535));
+  k_times_pattern<T><<<grid, 128, 0, st>>>(S, D, W, V, ldw, colw);
+}
+template <class T>
+size_t forest_M_smem(const DevSym &S) {
+  return (size_t)2 * S.max_nrow * 32 * sizeof(T) + (size_t)S.max_nrow * 4 + 16;
+}
+template <class T>
+void launch_forest_M(const DevSym &S, const T *V, const T *Wy, int64_t ldw, int ncolw,
+                     double *Mlow, double *Mup, cudaStream_t st) {
+  if (S.nforest <= 0) return;
+  const size_t smem = forest_M_smem<T>(S);
+  smem_optin((const void *)k_forest_M<T>);
+  k_forest_M<T><<<S.nforest, 256, smem, st>>>(S, V, Wy, ldw, ncolw, Mlow, Mup);
+}
+template <class T>
+void launch_root_M(const T *M, int nR, double *Mlow_root, double *Mup_root, cudaStream_t st) {
+  if (nR <= 0) return;
+  const int blocks = (int)std::min<int64_t>(4096, ((int64_t)nR * nR + 255) / 256);
+  k_root_M<T><<<blocks, 256, 0, st>>>(M, nR, Mlow_root, Mup_root);
+}
+void launch_root_dx(int nR, double betamu, const double *X, const double *YinvE, const double *Mlow,
+                    const double *Mup, double *dX, cudaStream_t st) {
+  if (nR <= 0) return;
+  const int blocks = (int)std::min<int64_t>(4096, ((int64_t)nR * nR + 255) / 256);
+  k_root_dx<<<blocks, 256, 0, st>>>(nR, betamu, X, YinvE, Mlow, Mup, dX);
+}
+
+template <class T>
+__global__ void k_mirror_lower(T *A, int64_t ld, int n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    if (i > j) A[j + (int64_t)i * ld] = A[i + (int64_t)j * ld];
+  }
+}
+
+template <class T>
+void mirror_lower(T *A, int64_t ld, int n, cudaStream_t st) {
+  if (n <= 0) return;
+  const int blocks = (int)std::min<int64_t>(4096, ((int64_t)n * n + 255) / 256);
+  k_mirror_lower<T><<<blocks, 256, 0, st>>>(A, ld, n);
+}
+
+// SplitMix64 finaliser of (seed, i): a fixed start vector for the Lanczos iterations
+__global__ void k_fill_hash(double *v, int n, unsigned seed) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    unsigned long long z = ((unsigned long long)seed << 32) + (unsigned long long)i + 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    z ^= z >> 31;
+    v[i] = (double)(z >> 11) * 0x1.0p-52 - 1.0;
+  }
+}
+void fill_hash(double *v, int n, unsigned seed, cudaStream_t st) {
+  if (n > 0) k_fill_hash<<<(n + 255) / 256, 256, 0, st>>>(v, n, seed);
+}
+
+__global__ void k_permute_to_cols(const double *__restrict__ src, const int *__restrict__ colw,
+                                  double *dst, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) dst[colw[k]] = src[k];
+}
+void permute_to_cols(const double *src, const int *colw, double *dst, int n, cudaStream_t st) {
+  if (n > 0) k_permute_to_cols<<<(n + 255) / 256, 256, 0, st>>>(src, colw, dst, n);
+}
+
+#define MCSDP_ROOT_INST(T)                                                                       \
+  template void gemm_tn<T>(const GemmArgs<T> &, cudaStream_t);                                   \
+  template int dense_trtri<T>(const T *, int64_t, const T *, T *, int64_t, int, cudaStream_t);   \
+  template int dense_lauum<T>(const T *, int64_t, int, T *, int64_t, int64_t, bool, cudaStream_t); \
+  template void dotcols<T>(const T *, int64_t, int, int, int, const double *, double *, double,  \
+                           double, cudaStream_t);                                                \
+  template void launch_unit_cols<T>(T *, int64_t, const int *, int, int, cudaStream_t);          \
+  template void launch_root_rows_from_cols<T>(T *, int64_t, const int *, int, int, cudaStream_t); \
+  template void launch_extract_dense<T>(const DevSym &, const T *, int64_t, const int *, double *, \
+                                        cudaStream_t);                                           \
+  template void launch_times_pattern<T>(const DevSym &, const double *, const T *, T *, int64_t,  \
+                                        const int *, cudaStream_t);                              \
+  template void launch_forest_M<T>(const DevSym &, const T *, const T *, int64_t, int, double *,  \
+                                   double *, cudaStream_t);                                      \
+  template void launch_root_M<T>(const T *, int, double *, double *, cudaStream_t);        \
+  template void mirror_lower<T>(T *, int64_t, int, cudaStream_t);
+MCSDP_ROOT_INST(double)
+MCSDP_ROOT_INST(float)
+#undef MCSDP_ROOT_INST
+template void copy_square<double, double>(const double *, int64_t, double *, int64_t, int, cudaStream_t);
+template void copy_square<double, float>(const double *, int64_t, float *, int64_t, int, cudaStream_t);
+template void symmetrize<double, double>(const double *, int64_t, double *, int64_t, int, cudaStream_t);
+template void symmetrize<double, float>(const double *, int64_t, float *, int64_t, int, cudaStream_t);
+
+}  // namespace mcsdp

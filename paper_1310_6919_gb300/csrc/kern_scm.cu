@@ -28,21 +28,21 @@ template <class T>
 __global__ void k_scm_tiles(DevSym S, const int2 *__restrict__ tiles,
                             const T *__restrict__ WX, const T *__restrict__ WY,
                             int64_t ldw, const int *__restrict__ goff, double *B, int64_t ldb,
-                            double *hvec) {
+                            double *hvec, const int *__restrict__ colmap) {
   extern __shared__ __align__(16) unsigned char smr[];
   T *sm = reinterpret_cast<T *>(smr);
   const int2 tl = tiles[blockIdx.x];
   const int h = tl.x, g = tl.y;
   const int pbg = S.grp_pptr[g], pg = S.grp_pptr[g + 1] - pbg;
   const int pbh = S.grp_pptr[h], ph = S.grp_pptr[h + 1] - pbh;
-  const int cg = goff[g];
+  const int cg = colmap ? 0 : goff[g];
   T *Xs = sm;
   T *Ys = sm + ph * pg;
   const int tid = threadIdx.x, bd = blockDim.x;
   // X̂[P_h, P_g], Y^{-1}[P_h, P_g]: rows P_h of the group's solved columns
   for (int idx = tid; idx < ph * pg; idx += bd) {
     const int a = idx / pg, c = idx % pg;
-    const int64_t o = (int64_t)S.grp_cols[pbh + a] * ldw + cg + c;
+    const int64_t o = (int64_t)S.grp_cols[pbh + a] * ldw + (colmap ? colmap[S.grp_cols[pbg + c]] : cg + c);
     Xs[a + c * ph] = WX[o];
     Ys[a + c * ph] = WY[o];
   }
@@ -129,19 +129,19 @@ size_t scm_tiles_smem_bytes(const DevSym &S, int pmax) { return scm_tiles_smem_b
 template <class T>
 void launch_scm_tiles(const DevSym &S, const int2 *tiles, int ntiles, const T *WX,
                       const T *WY, int64_t ldw, const int *goff, double *B, int64_t ldb,
-                      double *hvec, int pmax, cudaStream_t st) {
+                      double *hvec, int pmax, cudaStream_t st, const int *colmap) {
   if (ntiles <= 0) return;
   // two |P_h| x |P_g| blocks, the nonzero lists of two groups, and the X̂-times-A_j products of
   // one batch of constraints (XW_CAP doubles, or one constraint's if larger) in shared memory
   const size_t smem = scm_tiles_smem_bytes(S, pmax, (int)sizeof(T));
   smem_optin((const void *)k_scm_tiles<T>);
-  k_scm_tiles<T><<<ntiles, 256, smem, st>>>(S, tiles, WX, WY, ldw, goff, B, ldb, hvec);
+  k_scm_tiles<T><<<ntiles, 256, smem, st>>>(S, tiles, WX, WY, ldw, goff, B, ldb, hvec, colmap);
 }
 template void launch_scm_tiles<double>(const DevSym &, const int2 *, int, const double *,
                                        const double *, int64_t, const int *, double *, int64_t,
-                                       double *, int, cudaStream_t);
+                                       double *, int, cudaStream_t, const int *);
 template void launch_scm_tiles<float>(const DevSym &, const int2 *, int, const float *,
                                       const float *, int64_t, const int *, double *, int64_t,
-                                      double *, int, cudaStream_t);
+                                      double *, int, cudaStream_t, const int *);
 
 }  // namespace mcsdp

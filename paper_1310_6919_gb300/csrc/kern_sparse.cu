@@ -334,9 +334,10 @@ size_t alg1_smem_bytes(const DevSym &S) {
 
 void launch_alg1(const DevSym &S, const double *X, double *Lh, double *DL, int *status,
                  cudaStream_t st) {
+  if (S.nforest <= 0) return;
   const size_t smem = alg1_smem_bytes(S);
   smem_optin((const void *)k_alg1);
-  k_alg1<<<S.ns, 256, smem, st>>>(S, X, Lh, DL, status);
+  k_alg1<<<S.nforest, 256, smem, st>>>(S, X, Lh, DL, status);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -457,7 +458,8 @@ __global__ void k_dx_combine(DevSym S, double betamu, const double *__restrict__
 
 void launch_dx_combine(const DevSym &S, double betamu, const double *X, const double *YinvE,
                        const double *Mlow, const double *Mup, double *dX, cudaStream_t st) {
-  k_dx_combine<<<S.ns, 128, 0, st>>>(S, betamu, X, YinvE, Mlow, Mup, dX);
+  if (S.nforest <= 0) return;
+  k_dx_combine<<<S.nforest, 128, 0, st>>>(S, betamu, X, YinvE, Mlow, Mup, dX);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -667,9 +669,10 @@ size_t primal_step_smem_bytes(const DevSym &S) {
 
 void launch_primal_step(const DevSym &S, const double *X, const double *D, double *alpha_r,
                         int *status, cudaStream_t st) {
+  if (S.nforest <= 0) return;
   const size_t smem = primal_step_smem_bytes(S);
   smem_optin((const void *)k_primal_step);
-  k_primal_step<<<S.ns, 256, smem, st>>>(S, X, D, alpha_r, status);
+  k_primal_step<<<S.nforest, 256, smem, st>>>(S, X, D, alpha_r, status);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -45,6 +45,7 @@ struct Chunk {
 };
 
 constexpr int NCAND = 16;  // candidates per dual step-length round
+constexpr int LZ_MAX = 64;  // Lanczos steps of the dense-root step-length bounds
 
 }  // namespace
 
@@ -133,6 +134,26 @@ struct mcsdp_ctx {
   int2 *tiles_dev = nullptr, *tkey_dev = nullptr, *pm_tkey_dev = nullptr;
   uint32_t *reach_bits_dev = nullptr, *need_bits_dev = nullptr, *pm_bits_dev = nullptr;
   uint32_t *pm_need_dev = nullptr;
+  // dense root (kern_root.cu): the root supernode's columns [nF, n) = R, nR = |R|; the dense
+  // completion buffers W1 (X̂), W2 (Y^{-1}), W3 (X̂ dY) are n x ldw row-major with vertex k's
+  // column at colw[k] (R first, the forest from column colF0 = nR rounded up to 32)
+  bool dense = false;
+  int nR = 0, nF = 0, colF0 = 0, nlev = 0;  // nlev: levels the small-clique kernels walk
+  std::vector<int> colw;
+  std::vector<int64_t> rg_ent, rg_ptr;
+  std::vector<int> rg_u, rg_ab;
+  RootGather rg{};
+  int *colw_dev = nullptr;
+  double *RS_X = nullptr, *RS_P = nullptr, *RS_T = nullptr, *RS_M = nullptr;
+  double *rLinvN = nullptr, *rLinvX = nullptr, *rLinv2 = nullptr;
+  float *rLinv32 = nullptr;
+  int *rsyncN = nullptr, *rsyncX = nullptr, *rsync2 = nullptr;
+  size_t rsync_words = 0;
+  double *lzQ = nullptr, *lzW = nullptr, *lzG = nullptr, *lzU = nullptr, *lzS = nullptr;
+  double *Xprev = nullptr, *zprev = nullptr;
+  double lz_last[4] = {0, 0, 0, 0};  // diagnostics of the last Lanczos bounds
+  const double *Xbar_cur = nullptr;   // the X̄ the factors were last formed from
+  double alpha_root_host = 1.0;       // source of the root clique's primal step copy
   // kernel statistics
   int64_t launches = 0;
   int64_t kcount[16] = {};
@@ -256,6 +277,11 @@ void plan_workspace(mcsdp_ctx *c) {
   const int n = S.n, m = S.m;
   size_t cur = 0;
   c->uploads.clear();
+  c->dense = S.dense_root;
+  c->nR = c->dense ? S.sn_col[S.ns] - S.sn_col[S.ns - 1] : 0;
+  c->nF = n - c->nR;
+  c->colF0 = (c->nR + 31) / 32 * 32;
+  c->nlev = c->dense ? S.height - 1 : S.height;
   plan_table(c, cur, "sn_col", S.sn_col);
   plan_table(c, cur, "sn_rowptr", S.sn_rowptr);
   plan_table(c, cur, "rows", S.rows);
@@ -326,6 +352,11 @@ void plan_workspace(mcsdp_ctx *c) {
         const int t = S.lvl_sn[q];
         const int tncol = S.sn_col[t + 1] - S.sn_col[t];
         const int tnrow = (int)(S.sn_rowptr[t + 1] - S.sn_rowptr[t]);
+        if (l >= c->nlev) {  // the dense root: its updates are gathered per entry instead
+          c->upd_c0end[t] = S.upd_ptr[t + 1];
+          c->xch_beg[t] = c->xch_end[t] = (int)c->xch_t.size();
+          continue;
+        }
         std::vector<int> cuts{S.upd_ptr[t]};
         double wsum = 0;
         for (int u = S.upd_ptr[t]; u < S.upd_ptr[t + 1]; ++u) {
@@ -384,6 +415,54 @@ void plan_workspace(mcsdp_ctx *c) {
     }
     (void)lvl_of;
   }
+  // dense root (K2 at the root): per entry of the root block, the contributions of the forest's
+  // supernodes, in the order (source update, row a, row b) -- bucketed by root column, then each
+  // column's entries ordered by row with a stable sort, so the order of every sum is fixed
+  c->rg_ent.clear();
+  c->rg_ptr.assign(1, 0);
+  c->rg_u.clear();
+  c->rg_ab.clear();
+  if (c->dense) {
+    const int rt = S.ns - 1, nR = c->nR;
+    struct Ctb {
+      int i, u, ab;
+    };
+    std::vector<int64_t> colcnt(nR + 1, 0);
+    for (int u = S.upd_ptr[rt]; u < S.upd_ptr[rt + 1]; ++u) {
+      const int np = S.upd_p2[u] - S.upd_p1[u];
+      const int *rel = S.upd_rel.data() + S.upd_relptr[u];
+      for (int bb = 0; bb < np; ++bb) colcnt[rel[bb] + 1] += np - bb;
+    }
+    for (int j = 0; j < nR; ++j) colcnt[j + 1] += colcnt[j];
+    std::vector<Ctb> all((size_t)colcnt[nR]);
+    std::vector<int64_t> at(colcnt.begin(), colcnt.end() - 1);
+    for (int u = S.upd_ptr[rt]; u < S.upd_ptr[rt + 1]; ++u) {
+      const int p1 = S.upd_p1[u], np = S.upd_p2[u] - p1;
+      const int *rel = S.upd_rel.data() + S.upd_relptr[u];
+      for (int aa = 0; aa < np; ++aa)
+        for (int bb = 0; bb <= aa; ++bb)
+          all[at[rel[bb]]++] = Ctb{rel[aa], u, (p1 + aa) | ((p1 + bb) << 16)};
+    }
+    for (int j = 0; j < nR; ++j) {
+      auto b0 = all.begin() + colcnt[j], b1 = all.begin() + colcnt[j + 1];
+      std::stable_sort(b0, b1, [](const Ctb &x, const Ctb &y) { return x.i < y.i; });
+      for (auto it = b0; it != b1;) {
+        auto e = it;
+        while (e != b1 && e->i == it->i) ++e;
+        c->rg_ent.push_back((int64_t)it->i + (int64_t)j * nR);
+        for (auto q = it; q != e; ++q) {
+          c->rg_u.push_back(q->u);
+          c->rg_ab.push_back(q->ab);
+        }
+        c->rg_ptr.push_back((int64_t)c->rg_u.size());
+        it = e;
+      }
+    }
+  }
+  plan_table(c, cur, "rg_ent", c->rg_ent);
+  plan_table(c, cur, "rg_ptr", c->rg_ptr);
+  plan_table(c, cur, "rg_u", c->rg_u);
+  plan_table(c, cur, "rg_ab", c->rg_ab);
   plan_table(c, cur, "upd_c0end", c->upd_c0end);
   plan_table(c, cur, "xch_beg", c->xch_beg);
   plan_table(c, cur, "xch_end", c->xch_end);
@@ -467,6 +546,8 @@ void plan_workspace(mcsdp_ctx *c) {
   c->goff_all.assign(S.ngroup, 0);
   c->pmax = 0;
   int max_rhs = 0;
+  // dense root: one chunk of every group (X̂ and Y^{-1} are formed whole)
+  const double chunk_budget = c->dense ? std::numeric_limits<double>::infinity() : budget;
   for (int g = 0; g < S.ngroup;) {
     Chunk ch{};
     ch.g0 = g;
@@ -478,7 +559,7 @@ void plan_workspace(mcsdp_ctx *c) {
     while (g < S.ngroup) {
       const int pg = S.grp_pptr[g + 1] - S.grp_pptr[g];
       const double bytes = 2.0 * n * 8.0 * (((nr + pg) + 31) / 32 * 32);
-      if (g > ch.g0 && bytes > budget) break;
+      if (g > ch.g0 && bytes > chunk_budget) break;
       c->goff_all[g] = nr;
       for (int q = 0; q < pg; ++q) {
         c->rowof_all.push_back(S.grp_cols[S.grp_pptr[g] + q]);
@@ -539,6 +620,13 @@ void plan_workspace(mcsdp_ctx *c) {
     for (int k = 0; k < n; ++k) c->pm_rowof[k] = k;
   }
   c->ldw = ((int64_t)std::max(max_rhs, c->pm_cols) + 31) / 32 * 32;
+  c->colw.clear();
+  if (c->dense) {
+    c->ldw = c->colF0 + ((int64_t)c->nF + 31) / 32 * 32;
+    c->colw.resize(n);
+    for (int k = 0; k < n; ++k) c->colw[k] = k < c->nF ? c->colF0 + k : k - c->nF;
+  }
+  plan_table(c, cur, "colw", c->colw);
   plan_table(c, cur, "rowof", c->rowof_all);
   plan_table(c, cur, "goff", c->goff_all);
   plan_table(c, cur, "tkey", c->tkey_all);
@@ -575,18 +663,41 @@ void plan_workspace(mcsdp_ctx *c) {
   plan_buf(c, cur, "W2", (size_t)n * c->ldw * 8);
   // one P-MATRIX block: its Y^{-1} columns get a buffer of their own, so they can be formed
   // while the SCE is solved
-  plan_buf(c, cur, "W3", c->pm_cols >= n ? (size_t)n * c->ldw * 8 : 0);
+  plan_buf(c, cur, "W3", (c->pm_cols >= n || c->dense) ? (size_t)n * c->ldw * 8 : 0);
   plan_buf(c, cur, "Pw", (size_t)std::max<int64_t>(1, c->nslotw) * c->ldw * 8);
   plan_buf(c, cur, "Pf", (size_t)std::max<int64_t>(1, c->nslotf) * NCAND * 8);
   plan_buf(c, cur, "xvalid", std::max<size_t>(1, c->xch_t.size()) * (size_t)(c->ldw / 32));
   // the side stream's own partial slots and marks (single P-MATRIX block: its Y^{-1} columns
   // are solved beside the SCM solves)
-  const bool side = c->pm_cols >= n;
+  const bool side = c->pm_cols >= n && !c->dense;
   plan_buf(c, cur, "Pw2", side ? (size_t)std::max<int64_t>(1, c->nslotw) * c->ldw * 8 : 0);
   plan_buf(c, cur, "xvalid2", side ? std::max<size_t>(1, c->xch_t.size()) * (size_t)(c->ldw / 32) : 0);
   plan_buf(c, cur, "Pw3", (size_t)std::max<int64_t>(1, c->nslotw) * c->ldw * 8);
   plan_buf(c, cur, "xvalid3", std::max<size_t>(1, c->xch_t.size()) * (size_t)(c->ldw / 32));
-  plan_buf(c, cur, "Ncand", (size_t)NCAND * nnzL * 8);
+  plan_buf(c, cur, "Ncand", c->dense ? 0 : (size_t)NCAND * nnzL * 8);
+  {
+    const size_t r2 = (size_t)c->nR * c->nR * 8, rl = (size_t)((c->nR + 31) / 32) * 1024;
+    c->rsync_words = c->dense ? chol_dag_words(c->nR, c->nR) : 0;
+    plan_buf(c, cur, "RS_X", r2);
+    plan_buf(c, cur, "RS_P", r2);
+    plan_buf(c, cur, "RS_T", r2);
+    plan_buf(c, cur, "RS_M", r2);
+    plan_buf(c, cur, "rLinvN", rl * 8);
+    plan_buf(c, cur, "rLinvX", rl * 8);
+    plan_buf(c, cur, "rLinv2", rl * 8);
+    plan_buf(c, cur, "rLinv32", rl * 4);
+    plan_buf(c, cur, "rsyncN", c->rsync_words * 4);
+    plan_buf(c, cur, "rsyncX", c->rsync_words * 4);
+    plan_buf(c, cur, "rsync2", c->rsync_words * 4);
+    const size_t nv = c->dense ? (size_t)n : 0;
+    plan_buf(c, cur, "lzQ", 2 * nv * (LZ_MAX + 1) * 8);
+    plan_buf(c, cur, "lzW", nv * 8);
+    plan_buf(c, cur, "lzG", nv * 8);
+    plan_buf(c, cur, "lzU", 2 * std::max<size_t>(nv, c->ldw) * 8);
+    plan_buf(c, cur, "lzS", 4 * LZ_MAX * 8);
+    plan_buf(c, cur, "Xprev", c->dense ? nnzL * 8 : 0);
+    plan_buf(c, cur, "zprev", c->dense ? (size_t)m * 8 : 0);
+  }
   plan_buf(c, cur, "alpha_c", NCAND * 8);
   plan_buf(c, cur, "alpha_r", (size_t)S.ns * 8);
   plan_buf(c, cur, "scal", (16 + 6 * 64) * 8);  // scalars, then the measures' partials
@@ -606,7 +717,7 @@ void plan_workspace(mcsdp_ctx *c) {
     plan_buf(c, cur, "N32", mx ? (size_t)nnzL * 4 : 0);
     plan_buf(c, cur, "dL32", mx ? (size_t)nnzD * 4 : 0);
     plan_buf(c, cur, "dN32", mx ? (size_t)nnzD * 4 : 0);
-    c->f32_solves = mx && lsolve_staged_fits(c->lvl_info.data(), S.height, 4);
+    c->f32_solves = mx && lsolve_staged_fits(c->lvl_info.data(), c->nlev, 4);
   }  // [0..3] phases, [8..8+NCAND) dual candidates
   c->ws_bytes = cur;
 }
@@ -623,8 +734,16 @@ void bind_pointers(mcsdp_ctx *c) {
   D.m = S.m;
   D.ns = S.ns;
   D.ngroup = S.ngroup;
-  D.max_nrow = S.max_nrow;
-  D.max_ncol = S.max_ncol;
+  // the small-clique kernels size their shared memory from the forest's cliques (the dense
+  // root has kernels of its own)
+  D.nforest = c->dense ? S.ns - 1 : S.ns;
+  D.nR = c->nR;
+  D.root_valp = c->dense ? S.sn_valptr[S.ns - 1] : 0;
+  D.max_nrow = D.max_ncol = 0;
+  for (int t = 0; t < D.nforest; ++t) {
+    D.max_nrow = std::max(D.max_nrow, (int)(S.sn_rowptr[t + 1] - S.sn_rowptr[t]));
+    D.max_ncol = std::max(D.max_ncol, S.sn_col[t + 1] - S.sn_col[t]);
+  }
   D.max_grp_nnz = 0;
   for (int g = 0; g < S.ngroup; ++g)
     D.max_grp_nnz = std::max(D.max_grp_nnz, S.anz_ptr[S.grp_cptr[g + 1]] - S.anz_ptr[S.grp_cptr[g]]);
@@ -705,10 +824,11 @@ void bind_pointers(mcsdp_ctx *c) {
   c->dz = wsp<double>(c, "dz");
   c->W1 = wsp<double>(c, "W1");
   c->W2 = wsp<double>(c, "W2");
-  c->W3 = c->pm_cols >= c->S.n ? wsp<double>(c, "W3") : nullptr;
+  c->W3 = (c->pm_cols >= c->S.n || c->dense) ? wsp<double>(c, "W3") : nullptr;
   c->Pw = wsp<double>(c, "Pw");
-  c->Pw2 = c->pm_cols >= c->S.n ? wsp<double>(c, "Pw2") : nullptr;
-  c->xvalid2 = c->pm_cols >= c->S.n ? wsp<unsigned char>(c, "xvalid2") : nullptr;
+  const bool side = c->pm_cols >= c->S.n && !c->dense;
+  c->Pw2 = side ? wsp<double>(c, "Pw2") : nullptr;
+  c->xvalid2 = side ? wsp<unsigned char>(c, "xvalid2") : nullptr;
   c->Pw3 = wsp<double>(c, "Pw3");
   c->xvalid3 = wsp<unsigned char>(c, "xvalid3");
   c->Pf = wsp<double>(c, "Pf");
@@ -758,6 +878,30 @@ void bind_pointers(mcsdp_ctx *c) {
   c->pm_need_dev = wsp<uint32_t>(c, "pm_need");
   c->pm_tkey_dev = wsp<int2>(c, "pm_tkey");
   c->pm_rowof_dev = wsp<int>(c, "pm_rowof");
+  c->colw_dev = wsp<int>(c, "colw");
+  c->rg.nent = (int64_t)c->rg_ent.size();
+  c->rg.ent = wsp<int64_t>(c, "rg_ent");
+  c->rg.ptr = wsp<int64_t>(c, "rg_ptr");
+  c->rg.u = wsp<int>(c, "rg_u");
+  c->rg.ab = wsp<int>(c, "rg_ab");
+  c->RS_X = wsp<double>(c, "RS_X");
+  c->RS_P = wsp<double>(c, "RS_P");
+  c->RS_T = wsp<double>(c, "RS_T");
+  c->RS_M = wsp<double>(c, "RS_M");
+  c->rLinvN = wsp<double>(c, "rLinvN");
+  c->rLinvX = wsp<double>(c, "rLinvX");
+  c->rLinv2 = wsp<double>(c, "rLinv2");
+  c->rLinv32 = wsp<float>(c, "rLinv32");
+  c->rsyncN = wsp<int>(c, "rsyncN");
+  c->rsyncX = wsp<int>(c, "rsyncX");
+  c->rsync2 = wsp<int>(c, "rsync2");
+  c->lzQ = wsp<double>(c, "lzQ");
+  c->lzW = wsp<double>(c, "lzW");
+  c->lzG = wsp<double>(c, "lzG");
+  c->lzU = wsp<double>(c, "lzU");
+  c->lzS = wsp<double>(c, "lzS");
+  c->Xprev = wsp<double>(c, "Xprev");
+  c->zprev = wsp<double>(c, "zprev");
 }
 
 mcsdp_status ready(mcsdp_ctx *c) {
@@ -792,9 +936,11 @@ mcsdp_status phase_ychol(mcsdp_ctx *c, int ncand, const double *alpha, const dou
   const Symbolic &S = c->S;
   if (ychol_smem_bytes(c->D) > 220 * 1024)
     return fail(c, MCSDP_ERR_ARG, "supernode too large for the shared-memory Cholesky kernel");
+  if (c->dense && (ncand != 1 || dY))
+    return fail(c, MCSDP_ERR_STATE, "internal: candidate factorisations with a dense root");
   KScope ks(c, ncand > 1 ? KC_DSTEP : KC_YCHOL);
   int nl = 0;
-  for (int l = 0; l < S.height; ++l) {
+  for (int l = 0; l < c->nlev; ++l) {
     const int xb = c->lvl_xptr[l], xc = c->lvl_xptr[l + 1] - xb;
     if (xc > 0) {
       launch_ychol_partials(c->D, xb, xc, c->lvl_fptr[l], c->lvl_fptr[l + 1] - c->lvl_fptr[l], ncand,
@@ -805,17 +951,39 @@ mcsdp_status phase_ychol(mcsdp_ctx *c, int ncand, const double *alpha, const dou
                        Nbuf, dinv, status, c->Pf, c->stream);
     ++nl;
   }
+  if (c->dense) {
+    // the root: its block of Y less the forest's contributions, then the dense Cholesky
+    launch_root_assemble(c->D, c->rg, Yb, nullptr, 0.0, Nbuf, c->stream);
+    nl += c->rg.nent > 0 ? 2 : 1;
+    nl += dense_potrf(Nbuf + c->D.root_valp, c->nR, c->nR, status, c->rLinvN, c->stream, c->rsyncN,
+                      c->opt.timeout_cycles);
+  }
   ks.done(nl);
   KCHECK(c);
   return MCSDP_OK;
 }
 
+// the dense root's clique of X̄ (Algorithm 1 at the root needs X̄_RR^{-1}; the primal step needs
+// a factor of X̄_RR): RS_X <- Cholesky factor of X̄_RR (positive definite, else status bit),
+// RS_P <- its inverse with the inverse's rows mirrored above the diagonal
+int factor_X_root(mcsdp_ctx *c, const double *Xbar, int *status, cudaStream_t st) {
+  const int nR = c->nR;
+  copy_square<double, double>(Xbar + c->D.root_valp, nR, c->RS_X, nR, nR, st);
+  int nl = 1 + dense_potrf(c->RS_X, nR, nR, status, c->rLinvX, st, c->rsyncX, c->opt.timeout_cycles);
+  nl += dense_trtri<double>(c->RS_X, nR, c->rLinvX, c->RS_P, nR, nR, st);
+  mirror_lower<double>(c->RS_P, nR, nR, st);
+  return nl + 1;
+}
+
 mcsdp_status factor_X(mcsdp_ctx *c, const double *Xbar) {
   if (alg1_smem_bytes(c->D) > 220 * 1024)
     return fail(c, MCSDP_ERR_ARG, "clique too large for the shared-memory Algorithm 1 kernel");
+  c->Xbar_cur = Xbar;
   KScope ks(c, KC_ALG1);
   launch_alg1(c->D, Xbar, c->Lh, c->dinvL, c->status + 1, c->stream);
-  ks.done(1);
+  int nl = 1;
+  if (c->dense) nl += factor_X_root(c, Xbar, c->status + 1, c->stream);
+  ks.done(nl);
   KCHECK(c);
   return MCSDP_OK;
 }
@@ -825,13 +993,16 @@ mcsdp_status factor_X(mcsdp_ctx *c, const double *Xbar) {
 mcsdp_status factor_YX(mcsdp_ctx *c, const double *Xbar) {
   if (alg1_smem_bytes(c->D) > 220 * 1024)
     return fail(c, MCSDP_ERR_ARG, "clique too large for the shared-memory Algorithm 1 kernel");
+  c->Xbar_cur = Xbar;
   CUDA_TRY(c, cudaMemsetAsync(c->status, 0, 8 * sizeof(int), c->stream));
   CUDA_TRY(c, cudaEventRecord(c->ev_f0, c->stream));
   CUDA_TRY(c, cudaStreamWaitEvent(c->st3, c->ev_f0, 0));
   {
     KScope ks(c, KC_ALG1, c->st3);
     launch_alg1(c->D, Xbar, c->Lh, c->dinvL, c->status + 1, c->st3);
-    ks.done(1);
+    int nl = 1;
+    if (c->dense) nl += factor_X_root(c, Xbar, c->status + 1, c->st3);
+    ks.done(nl);
   }
   CUDA_TRY(c, cudaEventRecord(c->ev_f1, c->st3));
   mcsdp_status s = phase_ychol(c, 1, nullptr, c->Ylay, nullptr, c->N, c->dinvN, c->status);
@@ -879,7 +1050,7 @@ int lsolve_c(mcsdp_ctx *c, bool fwd, const T *L, const T *Dinv, T *W, int ncols,
   if (hk.bits) {
     const int ntiles = (ncols + 31) / 32;
     c->lvl_active.assign(S.height, 0);
-    for (int l = 0; l < S.height; ++l)
+    for (int l = 0; l < c->nlev; ++l)
       for (int q = S.lvl_ptr[l]; q < S.lvl_ptr[l + 1]; ++q) {
         const int t = S.lvl_sn[q];
         for (int tl = 0; tl < ntiles; ++tl) {
@@ -893,14 +1064,99 @@ int lsolve_c(mcsdp_ctx *c, bool fwd, const T *L, const T *Dinv, T *W, int ncols,
       }
     active = c->lvl_active.data();
   }
+  if (c->nlev <= 0) return 0;
   return lsolve<T>(c->D, S.lvl_ptr.data(), c->lvl_xptr.data(), c->lvl_fptr.data(),
-                   c->lvl_info.data(), S.height, fwd, L, Dinv, W, c->ldw, ncols, sk,
+                   c->lvl_info.data(), c->nlev, fwd, L, Dinv, W, c->ldw, ncols, sk,
                    reinterpret_cast<T *>(c->Pw), active, c->stream);
+}
+
+// K3 with a dense root: X̂ and Y^{-1} formed whole in W1 and W2 (n x ldw, the column of vertex k
+// at colw[k]).  Their root blocks first: X̂_RR = X̄_RR (a clique block of E, so the completion
+// keeps it) and Y^{-1}_RR = (N_RR N_RR^T)^{-1} = X^T X with X = N_RR^{-1} (the trailing block of
+// the inverse of Y = N N^T).  The root's columns of the forest's rows then follow from one
+// backward level-scheduled solve each (Y^{-1}[:, R] = N^{-T} N^{-1} [:, R] has no forest part
+// before the backward step: N^{-1} maps R's unit vectors into R's rows); the forest's columns
+// from a forward solve over the forest, the root rows taken from the root columns already formed
+// (symmetry), and a backward solve.  No solve passes through the dense root.  Then the SCM tiles
+// (eq. newSCM2) read both matrices through the column map.
+template <class T>
+mcsdp_status phase_scm_dense(mcsdp_ctx *c) {
+  const int n = c->S.n, nR = c->nR, nF = c->nF;
+  const int64_t ldw = c->ldw;
+  const int64_t rv = c->D.root_valp;
+  const SolveFactors<T> f = factors_of(c, T());
+  T *W1 = reinterpret_cast<T *>(c->W1), *W2 = reinterpret_cast<T *>(c->W2);
+  const LsSkip none{nullptr, nullptr, 0};
+  const SkipHost hnone{nullptr, nullptr};
+  KScope k1(c, KC_PANEL);
+  int nl = 0;
+  CUDA_TRY(c, cudaMemsetAsync(W1, 0, (size_t)n * ldw * sizeof(T), c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(W2, 0, (size_t)n * ldw * sizeof(T), c->stream));
+  symmetrize<double, T>(c->Xbar_cur + rv, nR, W1 + (size_t)nF * ldw, ldw, nR, c->stream);
+  ++nl;
+  if constexpr (std::is_same<T, double>::value) {
+    nl += dense_trtri<double>(c->N + rv, nR, c->rLinvN, c->RS_T, nR, nR, c->stream);
+    nl += dense_lauum<double>(c->RS_T, nR, nR, W2 + (size_t)nF * ldw, ldw, 1, true, c->stream);
+  } else {
+    float *L32 = reinterpret_cast<float *>(c->RS_T), *X32 = L32 + (size_t)nR * nR;
+    copy_square<double, float>(c->N + rv, nR, L32, nR, nR, c->stream);
+    launch_cast_f32(c->rLinvN, c->rLinv32, (int64_t)((nR + 31) / 32) * 1024, c->stream);
+    nl += 2 + dense_trtri<float>(L32, nR, c->rLinv32, X32, nR, nR, c->stream);
+    nl += dense_lauum<float>(X32, nR, nR, W2 + (size_t)nF * ldw, ldw, 1, true, c->stream);
+  }
+  int r[6] = {0, 0, 0, 0, 0, 0};
+  if (nF > 0) {
+    LsSkip fw{c->pm_bits_dev, c->pm_tkey_dev, c->bit_words};
+    const SkipHost hfw{c->pm_bits.data(), c->pm_tkey.data()};
+    T *W1F = W1 + c->colF0, *W2F = W2 + c->colF0;
+    launch_unit_cols<T>(W1, ldw, c->colw_dev, 0, nF, c->stream);
+    launch_unit_cols<T>(W2, ldw, c->colw_dev, 0, nF, c->stream);
+    nl += 2;
+    // Y^{-1} on the side stream st4 (own partial slots and marks), X̂ here
+    CUDA_TRY(c, cudaEventRecord(c->ev_n0, c->stream));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->st4, c->ev_n0, 0));
+    {
+      cudaStream_t main_st = c->stream;
+      double *pw = c->Pw;
+      unsigned char *xv = c->D.xvalid;
+      c->stream = c->st4;
+      c->Pw = c->Pw3;
+      c->D.xvalid = c->xvalid3;
+      KScope kn(c, KC_PANEL_SIDE, c->st4);
+      r[3] = lsolve_c<T>(c, false, f.N, f.dinvN, W2, nR, none, hnone);
+      r[4] = lsolve_c<T>(c, true, f.N, f.dinvN, W2F, nF, fw, hfw);
+      launch_root_rows_from_cols<T>(W2, ldw, c->colw_dev, nR, nF, c->st4);
+      r[5] = lsolve_c<T>(c, false, f.N, f.dinvN, W2F, nF, none, hnone);
+      kn.done(1 + std::max(0, r[3]) + std::max(0, r[4]) + std::max(0, r[5]));
+      c->stream = main_st;
+      c->Pw = pw;
+      c->D.xvalid = xv;
+      CUDA_TRY(c, cudaEventRecord(c->ev_n1, c->st4));
+    }
+    r[0] = lsolve_c<T>(c, false, f.Lh, f.dinvL, W1, nR, none, hnone);
+    r[1] = lsolve_c<T>(c, true, f.Lh, f.dinvL, W1F, nF, fw, hfw);
+    launch_root_rows_from_cols<T>(W1, ldw, c->colw_dev, nR, nF, c->stream);
+    r[2] = lsolve_c<T>(c, false, f.Lh, f.dinvL, W1F, nF, none, hnone);
+    nl += 1 + std::max(0, r[0]) + std::max(0, r[1]) + std::max(0, r[2]);
+    CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->ev_n1, 0));
+  }
+  k1.done(nl);
+  for (int q = 0; q < 6; ++q)
+    if (r[q] < 0) return fail(c, MCSDP_ERR_ARG, "solve shape not supported in this precision");
+  KCHECK(c);
+  KScope k2(c, KC_TILE);
+  const Chunk &ch = c->chunks[0];
+  launch_scm_tiles(c->D, c->tiles_dev + ch.tile_begin, ch.ntiles, (const T *)W1, (const T *)W2,
+                   ldw, c->goff_dev, c->B, c->ldb, c->hvec, c->pmax, c->stream, c->colw_dev);
+  k2.done(1);
+  KCHECK(c);
+  return MCSDP_OK;
 }
 
 // K3 with solves in T (the W buffers and partial slots hold T; as FP32 they use half their size)
 template <class T>
 mcsdp_status phase_scm(mcsdp_ctx *c) {
+  if (c->dense) return phase_scm_dense<T>(c);
   const Symbolic &S = c->S;
   const int n = S.n;
   const SolveFactors<T> f = factors_of(c, T());
@@ -953,6 +1209,47 @@ mcsdp_status phase_scm(mcsdp_ctx *c) {
     k2.done(1);
     KCHECK(c);
   }
+  return MCSDP_OK;
+}
+
+// P-MATRIX (eq. newdX2) with a dense root, from the dense X̂ (W1) and Y^{-1} (W2) of the SCM
+// phase: V = X̂ dY (W3, rows of X̂ times the aggregate-pattern dY), M = X̂ dY Y^{-1} at (r, k) is
+// the dot product of row r of V with row k of Y^{-1} (Y^{-1} symmetric): on the root block one
+// GEMM M_RR = V_R Y^{-1}_R^T into RS_M, on the forest's entries of E the dot products of the
+// clique rows (Mlow at (r, k) and, transposed, Mup); Y^{-1} on E read from W2.  Then dX on E.
+template <class T>
+mcsdp_status phase_pmatrix_dense(mcsdp_ctx *c, double betamu, const double *Xbar) {
+  const int n = c->S.n, nR = c->nR, nF = c->nF;
+  const int64_t ldw = c->ldw, rv = c->D.root_valp;
+  const T *W1 = reinterpret_cast<const T *>(c->W1), *W2 = reinterpret_cast<const T *>(c->W2);
+  T *V = reinterpret_cast<T *>(c->W3);
+  T *M = reinterpret_cast<T *>(c->RS_M);
+  KScope k1(c, KC_PMAT);
+  CUDA_TRY(c, cudaMemsetAsync(V, 0, (size_t)n * ldw * sizeof(T), c->stream));
+  launch_times_pattern<T>(c->D, c->dY, W1, V, ldw, c->colw_dev, c->stream);
+  GemmArgs<T> g{};
+  g.M = g.N = nR;
+  g.K = (int)ldw;
+  g.A = V + (size_t)nF * ldw;
+  g.lda = ldw;
+  g.B = W2 + (size_t)nF * ldw;
+  g.ldb = ldw;
+  g.C = M;
+  g.cs_i = 1;
+  g.cs_j = nR;
+  g.alpha = T(1);
+  g.beta = T(0);
+  gemm_tn<T>(g, c->stream);
+  launch_extract_dense<T>(c->D, W2, ldw, c->colw_dev, c->YinvE, c->stream);
+  launch_forest_M<T>(c->D, V, W2, ldw, (int)ldw, c->Mlow, c->Mup, c->stream);
+  launch_root_M<T>(M, nR, c->Mlow + rv, c->Mup + rv, c->stream);
+  k1.done(6);
+  KScope k2(c, KC_MISC);
+  launch_dx_combine(c->D, betamu, Xbar, c->YinvE, c->Mlow, c->Mup, c->dX, c->stream);
+  launch_root_dx(nR, betamu, Xbar + rv, c->YinvE + rv, c->Mlow + rv, c->Mup + rv, c->dX + rv,
+                 c->stream);
+  k2.done(2);
+  KCHECK(c);
   return MCSDP_OK;
 }
 
@@ -1042,6 +1339,164 @@ mcsdp_status phase_pmatrix_yinv(mcsdp_ctx *c, int *nlaunch) {
   return MCSDP_OK;
 }
 
+// Smallest eigenvalue of the symmetric tridiagonal matrix with diagonal a[0..k) and off-diagonal
+// b[0..k-1), and the last component of its unit eigenvector, by cyclic Jacobi rotations on the
+// dense k x k matrix (k <= LZ_MAX: host work of microseconds)
+void tridiag_min(int k, const double *a, const double *b, double *lam, double *last) {
+  std::vector<double> A((size_t)k * k, 0.0), V((size_t)k * k, 0.0);
+  for (int i = 0; i < k; ++i) {
+    A[(size_t)i * k + i] = a[i];
+    if (i + 1 < k) A[(size_t)i * k + i + 1] = A[(size_t)(i + 1) * k + i] = b[i];
+    V[(size_t)i * k + i] = 1.0;
+  }
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int p = 0; p < k; ++p)
+      for (int q = 0; q < k; ++q) {
+        const double v = A[(size_t)p * k + q] * A[(size_t)p * k + q];
+        tot += v;
+        if (p != q) off += v;
+      }
+    if (off <= 1e-32 * tot) break;
+    for (int p = 0; p < k; ++p)
+      for (int q = p + 1; q < k; ++q) {
+        const double apq = A[(size_t)p * k + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        const double th = (A[(size_t)q * k + q] - A[(size_t)p * k + p]) / (2.0 * apq);
+        const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+        const double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
+        for (int r = 0; r < k; ++r) {  // columns p, q
+          const double x = A[(size_t)r * k + p], y = A[(size_t)r * k + q];
+          A[(size_t)r * k + p] = cs * x - sn * y;
+          A[(size_t)r * k + q] = sn * x + cs * y;
+        }
+        for (int r = 0; r < k; ++r) {  // rows p, q
+          const double x = A[(size_t)p * k + r], y = A[(size_t)q * k + r];
+          A[(size_t)p * k + r] = cs * x - sn * y;
+          A[(size_t)q * k + r] = sn * x + cs * y;
+        }
+        for (int r = 0; r < k; ++r) {
+          const double x = V[(size_t)r * k + p], y = V[(size_t)r * k + q];
+          V[(size_t)r * k + p] = cs * x - sn * y;
+          V[(size_t)r * k + q] = sn * x + cs * y;
+        }
+      }
+  }
+  int im = 0;
+  for (int i = 1; i < k; ++i)
+    if (A[(size_t)i * k + i] < A[(size_t)im * k + im]) im = i;
+  *lam = A[(size_t)im * k + im];
+  *last = V[(size_t)(k - 1) * k + im];
+}
+
+// Smallest eigenvalue of an operator self-adjoint in the inner product <u, v>_G = u^T G v, by
+// Lanczos with full reorthogonalisation from a fixed pseudo-random start: op(v, w) forms w = op v,
+// gmul(v, gv) forms gv = G v (has_g false: G = I), both on c->stream, vectors of length dim.
+// Stops at LZ_MAX steps, at an invariant subspace, or once the Ritz value's residual bound is
+// below tol max(1, |theta|) (tested every 8 steps).  *theta = smallest Ritz value, *bound = its
+// residual bound (an eigenvalue lies within bound of theta).
+template <class Op, class Gm>
+mcsdp_status lanczos_min(mcsdp_ctx *c, int dim, Op op, Gm gmul, bool has_g, double tol,
+                         unsigned seed, double *theta, double *bound, int *steps) {
+  double *Q = c->lzQ, *GQ = has_g ? c->lzQ + (size_t)dim * (LZ_MAX + 1) : c->lzQ;
+  double *w = c->lzW, *gw = has_g ? c->lzG : c->lzW;
+  const cudaStream_t st = c->stream;
+  fill_hash(Q, dim, seed, st);
+  if (has_g) gmul(Q, GQ);
+  lz_normalise(dim, Q, GQ, st);
+  double hs[2 * LZ_MAX + 2];
+  int k = 0;
+  *theta = 0.0;
+  *bound = 0.0;
+  for (int j = 0; j < LZ_MAX; ++j) {
+    double *vj = Q + (size_t)j * dim, *gvj = GQ + (size_t)j * dim;
+    op(vj, w);
+    lz_alpha(dim, w, gvj, vj, j > 0 ? vj - dim : nullptr, c->lzS, j, st);
+    lz_reorth(dim, j + 1, w, GQ, Q, st);
+    if (has_g) gmul(w, gw);
+    lz_beta(dim, w, gw, vj + dim, has_g ? gvj + dim : nullptr, c->lzS, j, st);
+    k = j + 1;
+    if (k % 8 == 0 || k == LZ_MAX || k == dim) {
+      CUDA_TRY(c, cudaMemcpyAsync(hs, c->lzS, 2 * k * 8, cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(c, cudaStreamSynchronize(st));
+      prof_flush(c);
+      double a[LZ_MAX], b[LZ_MAX];
+      for (int i = 0; i < k; ++i) {
+        a[i] = hs[2 * i];
+        b[i] = hs[2 * i + 1];
+      }
+      double lam, last;
+      tridiag_min(k, a, b, &lam, &last);
+      *theta = lam;
+      *bound = std::fabs(b[k - 1] * last);
+      if (!std::isfinite(lam)) return fail(c, MCSDP_ERR_NUMERIC, "NaN in a Lanczos step-length bound");
+      if (b[k - 1] <= 1e-14 * std::max(1.0, std::fabs(lam)) || k == dim) break;
+      if (*bound <= tol * std::max(1.0, std::fabs(lam))) break;
+    }
+  }
+  *steps = k;
+  return MCSDP_OK;
+}
+
+// max alpha in (0, 1] with I + alpha T psd for lambda_min(T) >= theta - bound
+double step_from_bound(double theta, double bound) {
+  const double lam = theta - bound;
+  return lam < -1.0 ? -1.0 / lam : 1.0;
+}
+
+// Step lengths with a dense root (SURVEY reading: Lanczos bounds).  Primal, root clique:
+// lambda_min(L^{-1} dX_RR L^{-T}) with X̄_RR = L L^T (RS_P holds L^{-1} and its rows mirrored),
+// dX_RR made full in RS_M.  Dual: lambda_min(Y^{-1} dY), self-adjoint in the Y-inner product, with
+// the dense Y^{-1} of the SCM phase (W2) and Y on the aggregate pattern.  Both are confirmed by
+// the next iteration's factorisations (a failure backtracks the step).
+template <class T>
+mcsdp_status dense_steps(mcsdp_ctx *c, double *alpha_root, double *alpha_dual) {
+  const int n = c->S.n, nR = c->nR;
+  const int64_t rv = c->D.root_valp;
+  double th, bd;
+  int steps = 0;
+  mcsdp_status s;
+  {
+    KScope ks(c, KC_PSTEP);
+    symmetrize<double, double>(c->dX + rv, nR, c->RS_M, nR, nR, c->stream);
+    double *u1 = c->lzU, *u2 = c->lzU + nR;
+    auto op = [&](const double *v, double *w) {
+      dotcols<double>(c->RS_P, nR, nR, nR, 1, v, u1, 1.0, 0.0, c->stream);
+      dotcols<double>(c->RS_M, nR, nR, nR, 0, u1, u2, 1.0, 0.0, c->stream);
+      dotcols<double>(c->RS_P, nR, nR, nR, 2, u2, w, 1.0, 0.0, c->stream);
+    };
+    auto gnone = [&](const double *, double *) {};
+    s = lanczos_min(c, nR, op, gnone, false, 1e-3, 7u, &th, &bd, &steps);
+    ks.done(1 + 8 * steps);
+    if (s) return s;
+    *alpha_root = step_from_bound(th, bd);
+    c->lz_last[0] = th;
+    c->lz_last[1] = bd;
+  }
+  {
+    KScope ks(c, KC_DSTEP);
+    const T *W2 = reinterpret_cast<const T *>(c->W2);
+    const int64_t ldw = c->ldw;
+    double *u = c->lzU, *ut = c->lzU + std::max<int64_t>(n, ldw);
+    CUDA_TRY(c, cudaMemsetAsync(ut, 0, ldw * 8, c->stream));
+    auto op = [&](const double *v, double *w) {
+      launch_dY_times<double>(c->D, c->dY, v, u, 1, 1, c->stream);
+      permute_to_cols(u, c->colw_dev, ut, n, c->stream);
+      dotcols<T>(W2, ldw, n, (int)ldw, 0, ut, w, 1.0, 0.0, c->stream);
+    };
+    auto gmul = [&](const double *v, double *gv) {
+      launch_dY_times<double>(c->D, c->Ylay, v, gv, 1, 1, c->stream);
+    };
+    s = lanczos_min(c, n, op, gmul, true, 1e-3, 11u, &th, &bd, &steps);
+    ks.done(1 + 9 * steps);
+    if (s) return s;
+    *alpha_dual = step_from_bound(th, bd);
+    c->lz_last[2] = th;
+    c->lz_last[3] = bd;
+  }
+  return MCSDP_OK;
+}
+
 struct IterOut {
   double mu, pobj, dobj, gap, pinf, ap, ad;
 };
@@ -1115,7 +1570,7 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
   // the P-MATRIX's Y^{-1} columns need only N: with a single block they are formed on the side
   // stream st3 (own solve buffer, partial slots and marks) beside the SCM solves, which are
   // latency-bound and leave most SMs idle
-  const bool yinv_early = c->W3 != nullptr;
+  const bool yinv_early = c->W3 != nullptr && !c->dense;
   const bool yinv_f32 = f32;
   mcsdp_status s = MCSDP_OK;
   if (yinv_early) {
@@ -1176,7 +1631,14 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
   KCHECK(c);
   cudaEventRecord(c->ev[2], c->stream);
   CUDA_TRY(c, cudaMemsetAsync(c->dY, 0, c->D.nnzL * 8, c->stream));
-  {
+  if (c->dense) {
+    KScope k0(c, KC_MISC);
+    launch_slot_combine(c->D, c->dY, c->dz, 0.0, -1.0, c->stream);
+    k0.done(1);
+    s = f32 ? phase_pmatrix_dense<float>(c, beta * mu, Xbar)
+            : phase_pmatrix_dense<double>(c, beta * mu, Xbar);
+    if (s) return s;
+  } else {
     KScope k0(c, KC_MISC);
     launch_slot_combine(c->D, c->dY, c->dz, 0.0, -1.0, c->stream);
     k0.done(1);
@@ -1207,12 +1669,22 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
   }
   CUDA_TRY(c, cudaEventRecord(c->ev[5], c->st2));
   KCHECK(c);
+  double lo = 0.0, hi = -1.0;  // dual step: largest passing, smallest failing candidate
+  if (c->dense) {
+    double ar = 1.0, ad = 1.0;
+    s = f32 ? dense_steps<float>(c, &ar, &ad) : dense_steps<double>(c, &ar, &ad);
+    if (s) return s;
+    c->alpha_root_host = ar;
+    CUDA_TRY(c, cudaMemcpyAsync(c->alpha_r + (c->S.ns - 1), &c->alpha_root_host, 8,
+                                cudaMemcpyHostToDevice, c->stream));
+    lo = ad;
+    hi = 2.0;
+  }
   // dual step: bisection on the success of Y + alpha dY = N N^T (K2 on candidates)
-  double lo = 0.0, hi = -1.0;  // largest passing, smallest failing
   double cand[NCAND];
   const double first[NCAND] = {1.0, 0.95, 0.9, 0.85, 0.8, 0.7, 0.6, 0.5,
                                0.4, 0.3, 0.2, 0.1, 0.05, 0.02, 0.01, 0.003};
-  for (int round = 0; round < 6; ++round) {
+  for (int round = 0; round < (c->dense ? 0 : 6); ++round) {
     if (round == 0) {
       for (int i = 0; i < NCAND; ++i) cand[i] = first[i];
     } else {
@@ -1273,7 +1745,8 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
 }
 
 // Y, N, L̂ and the scalars at the current iterate (c->Xbar, c->z)
-mcsdp_status prepare(mcsdp_ctx *c, const double *Xbar, const double *z, double *scal_host) {
+mcsdp_status prepare(mcsdp_ctx *c, const double *Xbar, const double *z, double *scal_host,
+                     int *failed = nullptr) {
   mcsdp_status s = phase_Y(c, z);
   if (s) return s;
   s = factor_YX(c, Xbar);
@@ -1289,6 +1762,8 @@ mcsdp_status prepare(mcsdp_ctx *c, const double *Xbar, const double *z, double *
   CUDA_TRY(c, cudaMemcpyAsync(st, c->status, 4 * 4, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   prof_flush(c);
+  if (failed) *failed = ((st[0] & ST_NOT_PD) ? 1 : 0) | ((st[1] & ST_NOT_PD) ? 2 : 0);
+  if ((st[0] | st[1]) & ST_TIMEOUT) return fail(c, MCSDP_ERR_TIMEOUT, "a dense factorisation: a bounded wait gave up");
   if (st[0] & ST_NOT_PD) return fail(c, MCSDP_ERR_NOT_PD, "Y = A_0 - sum z_k A_k is not positive definite");
   if (st[1] & ST_NOT_PD) return fail(c, MCSDP_ERR_NOT_PD, "a clique block of X̄ is not positive definite");
   return MCSDP_OK;
@@ -1331,6 +1806,7 @@ void mcsdp_default_options(mcsdp_options *o) {
   o->relax = 1;
   o->solve_warps = 0;
   o->mixed_gap = 1e-5;
+  o->root_rows = 0;
 }
 
 const char *mcsdp_last_error(const mcsdp_ctx *c) { return c ? c->err.c_str() : "null context"; }
@@ -1402,12 +1878,28 @@ mcsdp_status mcsdp_create(const mcsdp_problem *p, const mcsdp_options *opt, void
   so.panel_max = c->opt.panel_max;
   so.group_max = c->opt.group_max;
   so.relax = c->opt.relax;
+  if (c->opt.root_rows < 0) {
+    so.root_rows = so.root_cols = 0;
+  } else {
+    so.root_rows = c->opt.root_rows > 0 ? std::min(c->opt.root_rows, 160) : 160;
+    so.root_cols = 96;
+  }
   std::string e = analyze(P, so, c->S);
   if (!e.empty()) return fail(c, MCSDP_ERR_ARG, e);
-  if (c->S.max_ncol > 96 || c->S.max_nrow > 160)
-    return fail(c, MCSDP_ERR_ARG, "a clique of " + std::to_string(c->S.max_nrow) + " rows / " +
-                                      std::to_string(c->S.max_ncol) +
-                                      " columns exceeds the library's shared-memory clique kernels (160 / 96)");
+  {
+    // every clique but a dense root must fit the shared-memory clique kernels
+    const Symbolic &S = c->S;
+    const int nsmall = S.dense_root ? S.ns - 1 : S.ns;
+    int mr = 0, mc = 0;
+    for (int t = 0; t < nsmall; ++t) {
+      mr = std::max(mr, (int)(S.sn_rowptr[t + 1] - S.sn_rowptr[t]));
+      mc = std::max(mc, S.sn_col[t + 1] - S.sn_col[t]);
+    }
+    if (mc > 96 || mr > 160)
+      return fail(c, MCSDP_ERR_ARG, "a clique of " + std::to_string(mr) + " rows / " +
+                                        std::to_string(mc) +
+                                        " columns exceeds the library's shared-memory clique kernels (160 / 96)");
+  }
   // default dual start
   c->z0_default.assign(P.m, 0.0);
   if (c->S.unit_diag_constraints) {
@@ -1585,6 +2077,27 @@ mcsdp_status mcsdp_factors(mcsdp_ctx *c, const double *Xbar, const double *z, do
   if (s) return s;
   if (Lh) CUDA_TRY(c, cudaMemcpyAsync(Lh, c->Lh, c->D.nnzL * 8, cudaMemcpyDeviceToDevice, c->stream));
   if (N) CUDA_TRY(c, cudaMemcpyAsync(N, c->N, c->D.nnzL * 8, cudaMemcpyDeviceToDevice, c->stream));
+  if (c->dense) {
+    // Algorithm 1 at the root clique C = S = R: L̂_RR is the Cholesky factor of X̄_RR^{-1}
+    // (unique), X̄_RR^{-1} = X^T X with X = L^{-1} of X̄_RR = L L^T (RS_P, from prepare)
+    const int nR = c->nR;
+    const int64_t rv = c->D.root_valp;
+    CUDA_TRY(c, cudaMemsetAsync(c->status + 6, 0, sizeof(int), c->stream));
+    KScope ks(c, KC_ALG1);
+    // RS_P's upper triangle holds the mirror of its rows: the product must read a zero there
+    copy_lower(c->RS_P, nR, c->RS_T, nR, nR, c->stream);
+    int nl = 1 + dense_lauum<double>(c->RS_T, nR, nR, c->RS_M, 1, nR, true, c->stream);
+    nl += dense_potrf(c->RS_M, nR, nR, c->status + 6, c->rLinv2, c->stream, c->rsync2,
+                      c->opt.timeout_cycles);
+    if (Lh) copy_lower(c->RS_M, nR, Lh + rv, nR, nR, c->stream);
+    // the dense Cholesky keeps the factor's rows mirrored above the diagonal: export zeros there
+    if (N) copy_lower(c->N + rv, nR, N + rv, nR, nR, c->stream);
+    ks.done(nl + 2);
+    int st[8];
+    s = read_status(c, st, 8);
+    if (s) return s;
+    if (st[6] & ST_NOT_PD) return fail(c, MCSDP_ERR_NOT_PD, "X̄_RR^{-1} not positive definite");
+  }
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   prof_flush(c);
   return MCSDP_OK;
@@ -1667,9 +2180,25 @@ mcsdp_status mcsdp_solve(mcsdp_ctx *c, mcsdp_result *res) {
   cudaEventRecord(t0, c->stream);
   const int n = c->S.n;
   mcsdp_status final_status = MCSDP_ERR_MAXITER;
+  double last_ap = 0.0, last_ad = 0.0;
   for (int it = 0; it <= c->opt.max_iter; ++it) {
     double sc[8];
-    s = prepare(c, c->Xbar, c->z, sc);
+    int failed = 0;
+    s = prepare(c, c->Xbar, c->z, sc, &failed);
+    // dense root: the step lengths are Lanczos estimates, confirmed here by the factorisations at
+    // the new iterate; a failure halves the failing step (from the saved iterate) and retries
+    for (int bt = 0; s == MCSDP_ERR_NOT_PD && c->dense && it > 0 && bt < 10; ++bt) {
+      if (failed & 2) last_ap *= 0.5;
+      if (failed & 1) last_ad *= 0.5;
+      CUDA_TRY(c, cudaMemcpyAsync(c->Xbar, c->Xprev, c->D.nnzL * 8, cudaMemcpyDeviceToDevice, c->stream));
+      CUDA_TRY(c, cudaMemcpyAsync(c->z, c->zprev, (size_t)c->S.m * 8, cudaMemcpyDeviceToDevice, c->stream));
+      launch_update(c->D, c->Xbar, c->dX, c->opt.gamma * last_ap, c->z, c->dz, c->opt.gamma * last_ad,
+                    c->stream);
+      if (c->opt.verbose)
+        std::fprintf(stderr, "  backtrack: ap %.3e ad %.3e\n", last_ap, last_ad);
+      failed = 0;
+      s = prepare(c, c->Xbar, c->z, sc, &failed);
+    }
     if (s) {
       if (it == 0 && s == MCSDP_ERR_NOT_PD && c->err.find("Y =") != std::string::npos)
         c->err += " at the start: give a dual-feasible z with mcsdp_set_iterate";
@@ -1715,6 +2244,12 @@ mcsdp_status mcsdp_solve(mcsdp_ctx *c, mcsdp_result *res) {
     if (c->opt.verbose)
       std::fprintf(stderr, "it %3d pobj %+.10e dobj %+.10e gap %.2e pinf %.2e mu %.2e ap %.3f ad %.3f\n",
                    it, pobj, dobj, gap, pinf, mu, o.ap, o.ad);
+    if (c->dense) {
+      CUDA_TRY(c, cudaMemcpyAsync(c->Xprev, c->Xbar, c->D.nnzL * 8, cudaMemcpyDeviceToDevice, c->stream));
+      CUDA_TRY(c, cudaMemcpyAsync(c->zprev, c->z, (size_t)c->S.m * 8, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    last_ap = o.ap;
+    last_ad = o.ad;
     KScope ks(c, KC_MISC);
     launch_update(c->D, c->Xbar, c->dX, c->opt.gamma * o.ap, c->z, c->dz, c->opt.gamma * o.ad, c->stream);
     ks.done(1);
@@ -1906,6 +2441,8 @@ mcsdp_status mcsdp_backward(mcsdp_ctx *c, const double *gX, const double *gz, do
                             double *gb, double *gA) {
   mcsdp_status s = ready(c);
   if (s) return s;
+  if (c->dense)
+    return fail(c, MCSDP_ERR_STATE, "differentiation is not available with a dense root clique");
   if (!c->iterate_set) return fail(c, MCSDP_ERR_STATE, "no iterate: solve (or set an iterate) first");
   const Symbolic &S = c->S;
   const int n = S.n, m = S.m;

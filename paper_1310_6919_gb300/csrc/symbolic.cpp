@@ -343,6 +343,68 @@ std::string analyze(const ProblemData &P, const SymbolicOptions &o, Symbolic &S)
       for (int c = a.c0; c < a.c1; ++c) col2f[c] = pf;
     }
   }
+  // ---- dense root: every clique with more than root_rows rows or root_cols columns goes, with
+  // all its ancestors, into one root supernode whose clique is the union R of their columns.
+  // The merged set is closed under taking parents, so the other supernodes keep their columns,
+  // their relative order (still a postorder of the forest that remains) and their cliques; R is
+  // numbered last.  E grows by the pairs of R that were not yet in it: it stays chordal, with
+  // the new order as a perfect elimination order (a vertex outside R keeps its later
+  // neighbours, which are its etree ancestors and already a clique; R is a clique).  The clique
+  // kernels for small cliques then serve every supernode but the root, and the root is one dense
+  // block handled by dense kernels. ----
+  if (o.root_rows > 0 || o.root_cols > 0) {
+    const int nf = (int)F.size();
+    std::vector<int> fpar(nf, -1);
+    std::vector<char> big(nf, 0);
+    for (int f = 0; f < nf; ++f) {
+      if (!F[f].alive) continue;
+      const auto &U = sn_struct[F[f].c1 - 1];
+      if (!U.empty()) fpar[f] = col2f[U[0]];
+      const int ncol = F[f].c1 - F[f].c0, nrow = ncol + (int)U.size();
+      if ((o.root_rows > 0 && nrow > o.root_rows) || (o.root_cols > 0 && ncol > o.root_cols))
+        big[f] = 1;
+    }
+    for (int f = 0; f < nf; ++f)
+      if (big[f])
+        for (int a = fpar[f]; a >= 0 && !big[a]; a = fpar[a]) big[a] = 1;
+    int nroot = 0;
+    for (int f = 0; f < nf; ++f)
+      if (F[f].alive && big[f]) nroot += F[f].c1 - F[f].c0;
+    if (nroot > 0) {
+      // new number of every column: the columns outside R in order, then those of R in order
+      std::vector<char> inR(n, 0);
+      for (int f = 0; f < nf; ++f)
+        if (F[f].alive && big[f])
+          for (int c = F[f].c0; c < F[f].c1; ++c) inR[c] = 1;
+      std::vector<int> nq(n);
+      int a = 0, b = n - nroot;
+      for (int q = 0; q < n; ++q) nq[q] = inR[q] ? b++ : a++;
+      std::vector<int> perm2(n);
+      for (int q = 0; q < n; ++q) perm2[nq[q]] = S.perm[q];
+      S.perm = perm2;
+      for (int q = 0; q < n; ++q) S.iperm[S.perm[q]] = q;
+      std::vector<std::vector<int>> st2(n);
+      std::vector<SN> F2;
+      std::vector<int> col2f2(n, 0);
+      for (int f = 0; f < nf; ++f) {
+        if (!F[f].alive || big[f]) continue;
+        auto U = sn_struct[F[f].c1 - 1];
+        for (int &x : U) x = nq[x];
+        std::sort(U.begin(), U.end());
+        const int c0 = nq[F[f].c0], c1 = nq[F[f].c1 - 1] + 1;
+        if (c1 - c0 != F[f].c1 - F[f].c0) return "internal: a supernode outside the root split";
+        st2[c1 - 1] = std::move(U);
+        for (int c = c0; c < c1; ++c) col2f2[c] = (int)F2.size();
+        F2.push_back({c0, c1, 0.0, true});
+      }
+      for (int c = n - nroot; c < n; ++c) col2f2[c] = (int)F2.size();
+      F2.push_back({n - nroot, n, 0.0, true});
+      F.swap(F2);
+      col2f.swap(col2f2);
+      sn_struct.swap(st2);
+      S.dense_root = true;
+    }
+  }
   S.sn_col.push_back(0);
   std::vector<std::pair<int, int>> sns;  // (c0, c1) of the surviving supernodes
   for (auto &f : F)
@@ -356,7 +418,10 @@ std::string analyze(const ProblemData &P, const SymbolicOptions &o, Symbolic &S)
   S.sn_dptr.assign(S.ns + 1, 0);
   for (int s = 0; s < S.ns; ++s) {
     int c0 = S.sn_col[s], c1 = S.sn_col[s + 1];
-    S.sn_dptr[s + 1] = S.sn_dptr[s] + (int64_t)(c1 - c0) * (c1 - c0);
+    // (the dense root keeps no inverse of its diagonal block in this table: its dense kernels
+    // hold their own 32 x 32 block inverses)
+    const bool droot = S.dense_root && s == S.ns - 1;
+    S.sn_dptr[s + 1] = S.sn_dptr[s] + (droot ? 0 : (int64_t)(c1 - c0) * (c1 - c0));
     if (c0 != sns[s].first) return "internal: supernode partition not contiguous";
     for (int c = c0; c < c1; ++c) S.col2sn[c] = s;
     for (int c = c0; c < c1; ++c) S.rows.push_back(c);
@@ -384,6 +449,10 @@ std::string analyze(const ProblemData &P, const SymbolicOptions &o, Symbolic &S)
     std::vector<int> h(S.ns, 0);
     for (int s = 0; s < S.ns; ++s)  // children precede parents
       if (S.sn_parent[s] >= 0) h[S.sn_parent[s]] = std::max(h[S.sn_parent[s]], h[s] + 1);
+    // the dense root (the last supernode) alone in the top level, so the level-scheduled
+    // small-clique kernels can stop one level short of it
+    if (S.dense_root && S.ns > 1)
+      h[S.ns - 1] = *std::max_element(h.begin(), h.end() - 1) + 1;
     S.height = S.ns ? *std::max_element(h.begin(), h.end()) + 1 : 0;
     S.lvl_ptr.assign(S.height + 1, 0);
     for (int s = 0; s < S.ns; ++s) S.lvl_ptr[h[s] + 1]++;

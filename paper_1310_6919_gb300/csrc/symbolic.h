@@ -78,6 +78,8 @@ struct Symbolic {
   std::vector<int> reach_sn, need_sn;
   // max-cut shaped (every A_k = e_k e_k^T with value 1): used for the default dual start
   bool unit_diag_constraints = false;
+  // the last supernode is the dense root (cliques beyond the small-clique limits merged into it)
+  bool dense_root = false;
   bool a0_diag_dominant_start_ok = false;
 };
 
@@ -86,6 +88,10 @@ struct SymbolicOptions {
   int group_max = 64;
   int relax = 1;          // relaxed supernode amalgamation
   int max_clique = 96;    // amalgamation never makes a clique larger than this
+  // cliques with more rows / columns than these go, with their ancestors, into one dense root
+  // supernode (0 = no bound of that kind; both 0 = no dense root)
+  int root_rows = 160;
+  int root_cols = 96;
 };
 
 // Returns empty string on success, else an error message.
