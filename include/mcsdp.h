@@ -109,8 +109,8 @@ typedef struct {
   int32_t root_rows;     /* dense root: cliques with more than this many rows (or more than 96
                             columns) are merged, with all their ancestors, into one root clique R
                             handled by dense kernels; the other cliques keep the small-clique
-                            kernels.  0 = default (160, the small-clique kernels' limit),
-                            < 0 = never (such problems are then rejected), 1..160 = a lower
+                            kernels.  0 = default (112, the small-clique kernels' limit),
+                            < 0 = never (such problems are then rejected), 1..112 = a lower
                             threshold (smaller problems then also get a dense root) */
 } mcsdp_options;
 

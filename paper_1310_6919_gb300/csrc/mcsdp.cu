@@ -46,6 +46,9 @@ struct Chunk {
 
 constexpr int NCAND = 16;  // candidates per dual step-length round
 constexpr int LZ_MAX = 64;  // Lanczos steps of the dense-root step-length bounds
+// the largest clique (rows / columns) the shared-memory clique kernels take: Algorithm 1 and the
+// primal step stage two k x k FP64 blocks (2 k^2 8 B <= 208 KB at k = 112)
+constexpr int SMALL_ROWS = 112, SMALL_COLS = 96;
 
 }  // namespace
 
@@ -1881,8 +1884,8 @@ mcsdp_status mcsdp_create(const mcsdp_problem *p, const mcsdp_options *opt, void
   if (c->opt.root_rows < 0) {
     so.root_rows = so.root_cols = 0;
   } else {
-    so.root_rows = c->opt.root_rows > 0 ? std::min(c->opt.root_rows, 160) : 160;
-    so.root_cols = 96;
+    so.root_rows = c->opt.root_rows > 0 ? std::min(c->opt.root_rows, SMALL_ROWS) : SMALL_ROWS;
+    so.root_cols = SMALL_COLS;
   }
   std::string e = analyze(P, so, c->S);
   if (!e.empty()) return fail(c, MCSDP_ERR_ARG, e);
@@ -1895,10 +1898,11 @@ mcsdp_status mcsdp_create(const mcsdp_problem *p, const mcsdp_options *opt, void
       mr = std::max(mr, (int)(S.sn_rowptr[t + 1] - S.sn_rowptr[t]));
       mc = std::max(mc, S.sn_col[t + 1] - S.sn_col[t]);
     }
-    if (mc > 96 || mr > 160)
+    if (mc > SMALL_COLS || mr > SMALL_ROWS)
       return fail(c, MCSDP_ERR_ARG, "a clique of " + std::to_string(mr) + " rows / " +
                                         std::to_string(mc) +
-                                        " columns exceeds the library's shared-memory clique kernels (160 / 96)");
+                                        " columns exceeds the library's shared-memory clique kernels (" +
+                                        std::to_string(SMALL_ROWS) + " / " + std::to_string(SMALL_COLS) + ")");
   }
   // default dual start
   c->z0_default.assign(P.m, 0.0);

@@ -90,7 +90,7 @@ struct SymbolicOptions {
   int max_clique = 96;    // amalgamation never makes a clique larger than this
   // cliques with more rows / columns than these go, with their ancestors, into one dense root
   // supernode (0 = no bound of that kind; both 0 = no dense root)
-  int root_rows = 160;
+  int root_rows = 112;
   int root_cols = 96;
 };
 

@@ -1,5 +1,6 @@
 """Shared-memory layouts of the staged level solves (mcsdp_lsolve_layout, host only) for every
-admissible clique size (|C_r| <= 160 rows, |S_r| <= 96 columns, the limits create enforces):
+admissible clique size (|C_r| <= 160 rows, |S_r| <= 96 columns: a margin over the 112 / 96 that
+create enforces for the cliques outside a dense root):
 regions 16-byte aligned (cp.async destinations), in order and disjoint, each as large as the
 kernel's accesses (acc[j * 32 + lane] and the diagonal block for j < nc, the update ring's
 source values, factor rows and row indices, the backward solve's clique block and vectors), and
