@@ -112,6 +112,9 @@ typedef struct {
                             kernels.  0 = default (112, the small-clique kernels' limit),
                             < 0 = never (such problems are then rejected), 1..112 = a lower
                             threshold (smaller problems then also get a dense root) */
+  int32_t tensor_cores;  /* mixed form: 1 (default) = the FP32 SCM Cholesky's trailing updates
+                            on the tensor cores (tcgen05, three TF32 products per FP32 product)
+                            for m >= 512; 0 = on the CUDA cores */
 } mcsdp_options;
 
 void mcsdp_default_options(mcsdp_options *opt);
@@ -288,6 +291,21 @@ mcsdp_status mcsdp_chol_task_order(int32_t m, int32_t rows, int64_t *ntask, int3
  * fwd / bwd. */
 mcsdp_status mcsdp_lsolve_layout(int32_t nc, int32_t nr, int32_t cw, int32_t np, int32_t with_d,
                                  int32_t elem_size, int32_t *fwd, int32_t *bwd, int32_t *cap);
+
+/* The FP32 product that the mixed form's dense contractions run on the tensor cores (the SCM
+ * Cholesky's trailing updates, Sec. 3.1 computation type (i), and the dense root's products):
+ * C = alpha A^T B + beta C with A (K x M) and B (K x N) column-major (element (l, i) of A at
+ * A[l + i lda], lda >= K) and C (M x N) column-major (ldc >= M), all FP32 device arrays.  Each
+ * operand is split into two TF32 numbers (hi = tf32(a), lo = tf32(a - hi)) and
+ * A^T B ~ hi^T hi + hi^T lo + lo^T hi is formed by tcgen05 MMAs (kind::tf32) with FP32
+ * accumulation in tensor memory, operand tiles loaded by TMA: FP32-level accuracy.  work is a
+ * caller-owned device buffer of at least mcsdp_gemm_tc_work_size() bytes, 256-byte aligned (the
+ * split operands).  Synchronises cuda_stream.  MCSDP_ERR_ARG for bad sizes or buffers,
+ * MCSDP_ERR_TIMEOUT if one of the kernel's bounded waits ran out. */
+mcsdp_status mcsdp_gemm_tc_work_size(int32_t M, int32_t N, int32_t K, size_t *bytes);
+mcsdp_status mcsdp_gemm_tc(int32_t M, int32_t N, int32_t K, const float *A, int64_t lda,
+                           const float *B, int64_t ldb, float *C, int64_t ldc, float alpha,
+                           float beta, void *work, size_t work_bytes, void *cuda_stream);
 
 /* Differentiation of the solution (not in the paper).  The point differentiated is the
  * central-path point for mu = X̄.Y/n of the context's iterate: the iterate is first re-centred

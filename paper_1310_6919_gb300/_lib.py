@@ -19,7 +19,8 @@ class Options_t(C.Structure):
                 ("timeout_cycles", C.c_int64), ("device", C.c_int32), ("verbose", C.c_int32),
                 ("panel_max", C.c_int32), ("group_max", C.c_int32),
                 ("panel_budget_mb", C.c_double), ("profile", C.c_int32), ("relax", C.c_int32),
-                ("solve_warps", C.c_int32), ("mixed_gap", C.c_double), ("root_rows", C.c_int32)]
+                ("solve_warps", C.c_int32), ("mixed_gap", C.c_double), ("root_rows", C.c_int32),
+                ("tensor_cores", C.c_int32)]
 
 
 class Work_t(C.Structure):
@@ -59,7 +60,8 @@ EXPORTED = ["mcsdp_default_options", "mcsdp_create", "mcsdp_destroy", "mcsdp_las
             "mcsdp_sym_export", "mcsdp_solve", "mcsdp_set_iterate", "mcsdp_get_iterate",
             "mcsdp_scm_assemble", "mcsdp_newton_step", "mcsdp_factors", "mcsdp_backward",
             "mcsdp_stats_get", "mcsdp_stats_reset", "mcsdp_work_model", "mcsdp_sce_solve_noalloc",
-            "mcsdp_solve_batch", "mcsdp_pivot_reciprocal", "mcsdp_chol_task_order"]
+            "mcsdp_solve_batch", "mcsdp_pivot_reciprocal", "mcsdp_chol_task_order",
+            "mcsdp_gemm_tc_work_size", "mcsdp_gemm_tc"]
 
 _lib = None
 
@@ -102,6 +104,9 @@ def load():
     L.mcsdp_chol_task_order.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_int64), V]
     L.mcsdp_solve_batch.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.c_int32,
                                     C.POINTER(Result_t)]
+    L.mcsdp_gemm_tc_work_size.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]
+    L.mcsdp_gemm_tc.argtypes = [C.c_int32, C.c_int32, C.c_int32, V, C.c_int64, V, C.c_int64, V,
+                                C.c_int64, C.c_float, C.c_float, V, C.c_size_t, V]
     for f in EXPORTED:
         if getattr(L, f).restype is C.c_int or f not in ("mcsdp_default_options", "mcsdp_destroy",
                                                            "mcsdp_last_error"):

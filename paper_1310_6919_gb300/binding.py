@@ -251,3 +251,28 @@ def solve_batch(problems, nthreads=0):
         out.append(d)
     return out
 
+
+def gemm_tc(A, B, C_out=None, alpha=1.0, beta=0.0):
+    """C = alpha A^T B + beta C on the tensor cores (mcsdp_gemm_tc): A (K x M) and B (K x N) FP32
+    CUDA tensors whose columns are contiguous (A.t() of a row-major M x K tensor), C (M x N)
+    column-major.  Argument marshalling only."""
+    L = _lib.load()
+    K, M = A.shape
+    N = B.shape[1]
+    assert A.dtype == torch.float32 and B.dtype == torch.float32 and B.shape[0] == K
+    assert A.stride(0) == 1 and B.stride(0) == 1
+    if C_out is None:
+        C_out = torch.zeros((N, M), dtype=torch.float32, device=A.device).t()
+    assert C_out.stride(0) == 1
+    nb = C.c_size_t()
+    st = L.mcsdp_gemm_tc_work_size(M, N, K, C.byref(nb))
+    if st != 0:
+        raise MCSDPError(st, "gemm_tc: bad sizes")
+    work = torch.empty(int(nb.value), dtype=torch.uint8, device=A.device)
+    stream = torch.cuda.current_stream(A.device).cuda_stream
+    st = L.mcsdp_gemm_tc(M, N, K, _ptr(A), A.stride(1), _ptr(B), B.stride(1), _ptr(C_out),
+                         C_out.stride(1), alpha, beta, _ptr(work), work.numel(), C.c_void_p(stream))
+    if st != 0:
+        raise MCSDPError(st, "gemm_tc failed")
+    return C_out
+

@@ -12,7 +12,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmcsdp.so")
 STAMP = os.path.join(HERE, "libmcsdp.so.sha256")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU = ["kern_sparse.cu", "kern_scm.cu", "kern_dense.cu", "kern_lsolve.cu", "kern_root.cu", "mcsdp.cu"]
+CU = ["kern_sparse.cu", "kern_scm.cu", "kern_dense.cu", "kern_lsolve.cu", "kern_root.cu", "kern_tc.cu", "mcsdp.cu"]
 CPP = ["symbolic.cpp"]
 
 

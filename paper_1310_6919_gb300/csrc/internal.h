@@ -249,9 +249,10 @@ void launch_root_assemble(const DevSym &S, const RootGather &G, const double *Yb
 template <class T>
 void gemm_tn(const GemmArgs<T> &g, cudaStream_t st);
 // X = L^{-1} (L dense lower with its rows mirrored above the diagonal, Linv its 32 x 32 diagonal
-// block inverses); returns launches
+// block inverses; work: 256 (n + 256) values); returns launches
 template <class T>
-int dense_trtri(const T *L, int64_t ldl, const T *Linv, T *X, int64_t ldx, int n, cudaStream_t st);
+int dense_trtri(const T *L, int64_t ldl, const T *Linv, T *X, int64_t ldx, int n, T *work,
+                cudaStream_t st);
 // lower triangle of X^T X at Z[i zs_i + j zs_j] (and mirrored)
 template <class T>
 int dense_lauum(const T *X, int64_t ldx, int n, T *Z, int64_t zs_i, int64_t zs_j, bool mirror,
@@ -336,6 +337,12 @@ struct CholStreams {
   cudaEvent_t next[2] = {}, rest_ev[2] = {}, fork = nullptr, chain_done = nullptr;
   cudaEvent_t entry = nullptr, exit = nullptr;  // caller's stream -> chain stream -> caller's
   CholGraph graphs[4];
+  // FP32 factorisation with tensor-core trailing updates (kern_tc.cu): the split panel buffers
+  // (tc_rows rows of TC_PANEL values, hi and lo) and the error word of its bounded waits;
+  // nullptr: the FP32 factor stays on the CUDA cores
+  float *tc_hi = nullptr, *tc_lo = nullptr;
+  int tc_rows = 0;
+  int *tc_err = nullptr;
 };
 void chol_graphs_destroy(CholStreams *cs);
 // words of the task-queue factorisation's synchronisation buffer (m columns, rows rows)

@@ -18,6 +18,7 @@
 
 #include "../../include/mcsdp.h"
 #include "internal.h"
+#include "tc.h"
 
 namespace mcsdp {
 
@@ -791,6 +792,47 @@ static int dense_chol_dag(T *B, int64_t ldb, int m, int rows, int *status, T *Li
   return 1;  // kernel launches (the memset is not one of ours)
 }
 
+template <class T>
+static int dense_chol(T *B, int64_t ldb, int m, int rows, int *status, T *Linv_all,
+                      cudaStream_t st_caller, const CholStreams *cs);
+
+__global__ void k_or_status(int *status, int bits) { atomicOr(status, bits); }
+// a host-side failure inside a launch sequence (a tensor map that could not be made): reported
+// through the status word like a device failure
+static void atomic_status_host_fail(int *status, cudaStream_t st) {
+  k_or_status<<<1, 1, 0, st>>>(status, ST_NUMERIC);
+}
+
+// FP32 Cholesky of an m x m matrix with the trailing updates on the tensor cores: panels of
+// TC_PANEL columns, each factored by the 32-column kernels below (over all its rows), its rows
+// below the panel split into TF32 hi / lo K-major copies (and written transposed above the
+// diagonal, where the refinement's substitutions read L^T), then the trailing lower triangle
+// updated by the tcgen05 product C -= P P^T with K = the panel width.
+static int dense_chol_f32_tc(float *B, int64_t ldb, int m, int *status, float *Linv_all,
+                             cudaStream_t st, const CholStreams *cs) {
+  int nl = 0;
+  for (int k0 = 0; k0 < m; k0 += TC_PANEL) {
+    const int pw = std::min(TC_PANEL, m - k0);
+    nl += dense_chol<float>(B + k0 + (int64_t)k0 * ldb, ldb, pw, m - k0, status,
+                            Linv_all + (int64_t)(k0 / NB) * NB * NB, st, nullptr);
+    const int r0 = k0 + pw;
+    if (r0 >= m) break;
+    split_tf32(B + r0 + (int64_t)k0 * ldb, 1, ldb, m - r0, pw, cs->tc_hi, cs->tc_lo, TC_PANEL,
+               B + k0 + (int64_t)r0 * ldb, ldb, st);
+    TcOperand P;
+    P.x = P.y = 0;
+    if (!make_tmap_kmajor(&P.hi, cs->tc_hi, TC_PANEL, pw, m - r0) ||
+        !make_tmap_kmajor(&P.lo, cs->tc_lo, TC_PANEL, pw, m - r0)) {
+      atomic_status_host_fail(status, st);
+      return nl;
+    }
+    gemm_3xtf32(P, P, m - r0, m - r0, pw, B + r0 + (int64_t)r0 * ldb, 1, ldb, -1.f, 1.f, true,
+                false, cs->tc_err ? cs->tc_err : status, st);
+    nl += 2;
+  }
+  return nl;
+}
+
 // Right-looking blocked Cholesky of the leading m columns of a rows x m matrix (rows = m + 1 for
 // the bordered right-hand side, m otherwise) with lookahead: on st (the critical path) panel k is factored (potrf), its rows below are solved
 // (trsm) and its update is applied to block column k+1; the rest of its update (block columns
@@ -800,6 +842,10 @@ static int dense_chol_dag(T *B, int64_t ldb, int m, int rows, int *status, T *Li
 template <class T>
 static int dense_chol(T *B, int64_t ldb, int m, int rows, int *status, T *Linv_all,
                       cudaStream_t st_caller, const CholStreams *cs) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (cs && cs->tc_hi && rows == m && m >= 2 * TC_PANEL && m <= cs->tc_rows)
+      return dense_chol_f32_tc(B, ldb, m, status, Linv_all, st_caller, cs);
+  }
   // critical path on st (high priority), trailing updates on st2 (low priority)
   const bool la = cs != nullptr;
   cudaStream_t st = la ? cs->chain : st_caller, st2 = la ? cs->rest : nullptr;

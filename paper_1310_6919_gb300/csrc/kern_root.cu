@@ -71,6 +71,7 @@ void launch_root_assemble(const DevSym &S, const RootGather &G, const double *Yb
 // lower triangular), so a tile's sum starts at its first row.  64 x 64 tile per CTA, 256
 // threads, 4 x 4 outputs per thread, K in steps of 16 through shared memory.
 constexpr int GB = 64, GK = 16;
+constexpr int TRI_BLK = 256;  // block rows of the triangular inverse
 
 template <class T>
 __global__ void __launch_bounds__(256) k_gemm_tn(GemmArgs<T> g) {
@@ -197,29 +198,109 @@ __global__ void k_trtri_scale(const T *__restrict__ Linv_k, T *X, int64_t ld, in
   }
 }
 
+// the inverse of the kb x kb diagonal block of L at (k0, k0) into X's block at (k0, k0) (X's block
+// holds I on entry): 32-row steps of the substitution inside the block
 template <class T>
-int dense_trtri(const T *L, int64_t ldl, const T *Linv, T *X, int64_t ldx, int n, cudaStream_t st) {
+static int trtri_diag(const T *L, int64_t ldl, const T *Linv, T *X, int64_t ldx, int k0, int kb,
+                      cudaStream_t st) {
+  int nl = 0;
+  T *Xb = X + k0 + (int64_t)k0 * ldx;
+  const T *Lb = L + k0 + (int64_t)k0 * ldl;
+  for (int q0 = 0; q0 < kb; q0 += 32) {
+    const int nb = std::min(32, kb - q0), ncol = q0 + nb;
+    k_trtri_scale<T><<<(ncol + 31) / 32, 256, 0, st>>>(Linv + (int64_t)((k0 + q0) / 32) * 1024, Xb,
+                                                       ldx, q0, nb, ncol);
+    ++nl;
+    const int r0 = q0 + nb;
+    if (r0 >= kb) break;
+    GemmArgs<T> g{};
+    g.M = kb - r0;
+    g.N = ncol;
+    g.K = nb;
+    g.A = Lb + q0 + (int64_t)r0 * ldl;  // A(l, i) = L(r0 + i, q0 + l), held transposed above
+    g.lda = ldl;
+    g.B = Xb + q0;
+    g.ldb = ldx;
+    g.C = Xb + r0;
+    g.cs_i = 1;
+    g.cs_j = ldx;
+    g.alpha = T(-1);
+    g.beta = T(1);
+    gemm_tn<T>(g, st);
+    ++nl;
+  }
+  return nl;
+}
+
+// D^T of the kb x kb lower block at D (ld) into Dt (ld 256): Dt[l + i 256] = D(i, l)
+template <class T>
+__global__ void k_transpose_block(const T *__restrict__ D, int64_t ld, int kb, T *Dt) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < kb * kb; e += gridDim.x * blockDim.x) {
+    const int i = e % kb, l = e / kb;
+    Dt[l + (int64_t)i * TRI_BLK] = D[i + (int64_t)l * ld];
+  }
+}
+
+// X[k0 + i, j] = T[i + j 256] for i < kb, j < ncol
+template <class T>
+__global__ void k_copy_rows_back(const T *__restrict__ Tm, T *X, int64_t ldx, int k0, int kb, int ncol) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)kb * ncol;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % kb), j = (int)(e / kb);
+    X[k0 + i + (int64_t)j * ldx] = Tm[i + (int64_t)j * TRI_BLK];
+  }
+}
+
+// Blocked in two levels: 256-row block rows (products with K = 256 keep the GEMM efficient), and
+// inside each 256 x 256 diagonal block the 32-row substitution above.  Step K: the diagonal block's
+// inverse D_K; the block row X_K = D_K R_K (R_K its accumulated right-hand side, columns left of
+// the block) formed in work and copied back; then the rows below, R_I -= L_IK X_K.  work holds
+// 256 x n values plus a 256 x 256 block.
+template <class T>
+int dense_trtri(const T *L, int64_t ldl, const T *Linv, T *X, int64_t ldx, int n, T *work,
+                cudaStream_t st) {
   if (n <= 0) return 0;
   const int64_t cnt = (int64_t)n * n;
   const int blocks = (int)std::min<int64_t>(4096, (cnt + 255) / 256);
   k_set_unit_lower<T><<<blocks, 256, 0, st>>>(X, ldx, n);
   int nl = 1;
-  for (int k0 = 0, k = 0; k0 < n; k0 += 32, ++k) {
-    const int nb = std::min(32, n - k0), ncol = k0 + nb;
-    k_trtri_scale<T><<<(ncol + 31) / 32, 256, 0, st>>>(Linv + (int64_t)k * 1024, X, ldx, k0, nb,
-                                                       ncol);
-    ++nl;
-    const int r0 = k0 + nb;
+  T *Tm = work, *Dt = work + (size_t)TRI_BLK * n;
+  for (int k0 = 0; k0 < n; k0 += TRI_BLK) {
+    const int kb = std::min(TRI_BLK, n - k0);
+    nl += trtri_diag<T>(L, ldl, Linv, X, ldx, k0, kb, st);
+    if (k0 > 0) {
+      // X_K(:, 0 .. k0) = D_K R_K(:, 0 .. k0)
+      k_transpose_block<T><<<(kb * kb + 255) / 256, 256, 0, st>>>(X + k0 + (int64_t)k0 * ldx, ldx,
+                                                                   kb, Dt);
+      GemmArgs<T> g{};
+      g.M = kb;
+      g.N = k0;
+      g.K = kb;
+      g.A = Dt;
+      g.lda = TRI_BLK;
+      g.B = X + k0;
+      g.ldb = ldx;
+      g.C = Tm;
+      g.cs_i = 1;
+      g.cs_j = TRI_BLK;
+      g.alpha = T(1);
+      g.beta = T(0);
+      gemm_tn<T>(g, st);
+      k_copy_rows_back<T><<<(int)std::min<int64_t>(4096, ((int64_t)kb * k0 + 255) / 256), 256, 0,
+                            st>>>(Tm, X, ldx, k0, kb, k0);
+      nl += 3;
+    }
+    const int r0 = k0 + kb;
     if (r0 >= n) break;
     GemmArgs<T> g{};
     g.M = n - r0;
-    g.N = ncol;
-    g.K = nb;
-    g.A = L + k0 + (int64_t)r0 * ldl;  // A(l, i) = L(r0 + i, k0 + l), held at row k0 + l, column r0 + i
+    g.N = r0;
+    g.K = kb;
+    g.A = L + k0 + (int64_t)r0 * ldl;  // A(l, i) = L(r0 + i, k0 + l), held transposed above
     g.lda = ldl;
-    g.B = X + k0;  // B(l, j) = X(k0 + l, j)
+    g.B = X + k0;                       // B(l, j) = X(k0 + l, j), j < r0
     g.ldb = ldx;
-    g.C = X + r0;  // C(i, j) = X(r0 + i, j)
+    g.C = X + r0;
     g.cs_i = 1;
     g.cs_j = ldx;
     g.alpha = T(-1);
@@ -703,7 +784,7 @@ void permute_to_cols(const double *src, const int *colw, double *dst, int n, cud
 
 #define MCSDP_ROOT_INST(T)                                                                       \
   template void gemm_tn<T>(const GemmArgs<T> &, cudaStream_t);                                   \
-  template int dense_trtri<T>(const T *, int64_t, const T *, T *, int64_t, int, cudaStream_t);   \
+  template int dense_trtri<T>(const T *, int64_t, const T *, T *, int64_t, int, T *, cudaStream_t); \
   template int dense_lauum<T>(const T *, int64_t, int, T *, int64_t, int64_t, bool, cudaStream_t); \
   template void dotcols<T>(const T *, int64_t, int, int, int, const double *, double *, double,  \
                            double, cudaStream_t);                                                \

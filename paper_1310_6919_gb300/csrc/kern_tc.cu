@@ -19,9 +19,12 @@
 #include <cudaTypedefs.h>
 
 #include <cstdint>
+#include <algorithm>
 #include <mutex>
 
+#include "../../include/mcsdp.h"
 #include "internal.h"
+#include "tc.h"
 
 namespace mcsdp {
 
@@ -247,13 +250,21 @@ __global__ void __launch_bounds__(128, 1)
 }
 
 // hi = tf32(a), lo = tf32(a - hi) (round to nearest), element (r, c) of a rows x cols matrix
-// at a[r lda_r + c lda_c] into the K-major pair at hi/lo[c + r ldo] (row r, K index c)
+// at a[r lda_r + c lda_c] into the K-major pair at hi/lo[c + r ldo] (row r, K index c); with tdst
+// the value itself also goes to tdst[c + r tld]
 __global__ void k_split_tf32(const float *__restrict__ a, int64_t lda_r, int64_t lda_c, int rows,
-                            int cols, float *hi, float *lo, int64_t ldo) {
+                            int cols, float *hi, float *lo, int64_t ldo, float *tdst, int64_t tld) {
   const int64_t cnt = (int64_t)rows * cols;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < cnt;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e % cols), r = (int)(e / cols);
+    int c, r;
+    if (lda_r == 1) {  // column-major source: consecutive threads take consecutive rows
+      r = (int)(e % rows);
+      c = (int)(e / rows);
+    } else {
+      c = (int)(e % cols);
+      r = (int)(e / cols);
+    }
     const float x = a[r * lda_r + c * lda_c];
     uint32_t h, l;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
@@ -261,15 +272,16 @@ __global__ void k_split_tf32(const float *__restrict__ a, int64_t lda_r, int64_t
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(d));
     hi[c + r * ldo] = __uint_as_float(h);
     lo[c + r * ldo] = __uint_as_float(l);
+    if (tdst) tdst[c + r * tld] = x;
   }
 }
 
 void split_tf32(const float *a, int64_t lda_r, int64_t lda_c, int rows, int cols, float *hi,
-                float *lo, int64_t ldo, cudaStream_t st) {
+                float *lo, int64_t ldo, float *tdst, int64_t tld, cudaStream_t st) {
   const int64_t cnt = (int64_t)rows * cols;
   if (cnt <= 0) return;
   const int blocks = (int)std::min<int64_t>(8192, (cnt + 255) / 256);
-  k_split_tf32<<<blocks, 256, 0, st>>>(a, lda_r, lda_c, rows, cols, hi, lo, ldo);
+  k_split_tf32<<<blocks, 256, 0, st>>>(a, lda_r, lda_c, rows, cols, hi, lo, ldo, tdst, tld);
 }
 
 namespace {
@@ -304,11 +316,11 @@ bool make_tmap_kmajor(CUtensorMap *map, const float *base, int64_t ld, int64_t k
 }
 
 // C = alpha A^T B + beta C through the tensor maps (rows of A: the M index, rows of B: the N
-// index; x, y the first element's coordinates); false if the maps could not be made
-bool gemm_3xtf32(const TcOperand &A, const TcOperand &B, int M, int N, int K, float *C,
+// index; x, y the first element's coordinates)
+void gemm_3xtf32(const TcOperand &A, const TcOperand &B, int M, int N, int K, float *C,
                  int64_t cs_i, int64_t cs_j, float alpha, float beta, bool lower, bool mirror,
                  int *err, cudaStream_t st) {
-  if (M <= 0 || N <= 0 || K <= 0) return true;
+  if (M <= 0 || N <= 0 || K <= 0) return;
   static std::once_flag once;
   std::call_once(once, [] {
     cudaFuncSetAttribute(k_gemm_3xtf32, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
@@ -331,7 +343,48 @@ bool gemm_3xtf32(const TcOperand &A, const TcOperand &B, int M, int N, int K, fl
   g.err = err;
   dim3 grid((M + TC_BM - 1) / TC_BM, (N + TC_BN - 1) / TC_BN);
   k_gemm_3xtf32<<<grid, 128, TC_SMEM, st>>>(A.hi, A.lo, B.hi, B.lo, g);
-  return true;
 }
 
 }  // namespace mcsdp
+
+// ---------------------------------------------------------------------------------------------
+// C ABI: the tensor-core FP32 product on its own (for its accuracy test and roofline)
+extern "C" mcsdp_status mcsdp_gemm_tc_work_size(int32_t M, int32_t N, int32_t K, size_t *bytes) {
+  if (M <= 0 || N <= 0 || K <= 0 || !bytes) return MCSDP_ERR_ARG;
+  const int64_t kp = ((int64_t)K + 3) / 4 * 4;
+  *bytes = (size_t)(2 * ((int64_t)M + N) * kp * 4) + 1024;
+  return MCSDP_OK;
+}
+
+extern "C" mcsdp_status mcsdp_gemm_tc(int32_t M, int32_t N, int32_t K, const float *A, int64_t lda,
+                                      const float *B, int64_t ldb, float *C, int64_t ldc,
+                                      float alpha, float beta, void *work, size_t work_bytes,
+                                      void *stream) {
+  using namespace mcsdp;
+  size_t need = 0;
+  if (mcsdp_gemm_tc_work_size(M, N, K, &need) != MCSDP_OK || !A || !B || !C || !work ||
+      lda < K || ldb < K || ldc < M || work_bytes < need ||
+      (reinterpret_cast<uintptr_t>(work) & 255) != 0)
+    return MCSDP_ERR_ARG;
+  (void)cudaGetLastError();
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t kp = ((int64_t)K + 3) / 4 * 4;
+  float *ah = static_cast<float *>(work), *al = ah + (size_t)M * kp;
+  float *bh = al + (size_t)M * kp, *bl = bh + (size_t)N * kp;
+  int *err = reinterpret_cast<int *>(bl + (size_t)N * kp);
+  if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return MCSDP_ERR_CUDA;
+  split_tf32(A, lda, 1, M, K, ah, al, kp, nullptr, 0, st);
+  split_tf32(B, ldb, 1, N, K, bh, bl, kp, nullptr, 0, st);
+  TcOperand oa, ob;
+  oa.x = oa.y = ob.x = ob.y = 0;
+  if (!make_tmap_kmajor(&oa.hi, ah, kp, K, M) || !make_tmap_kmajor(&oa.lo, al, kp, K, M) ||
+      !make_tmap_kmajor(&ob.hi, bh, kp, K, N) || !make_tmap_kmajor(&ob.lo, bl, kp, K, N))
+    return MCSDP_ERR_CUDA;
+  gemm_3xtf32(oa, ob, M, N, K, C, 1, ldc, alpha, beta, false, false, err, st);
+  if (cudaGetLastError() != cudaSuccess) return MCSDP_ERR_CUDA;
+  int h = 0;
+  if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return MCSDP_ERR_CUDA;
+  return (h & ST_TIMEOUT) ? MCSDP_ERR_TIMEOUT : MCSDP_OK;
+}

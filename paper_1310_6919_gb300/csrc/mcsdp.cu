@@ -23,6 +23,7 @@
 #include "../../include/mcsdp.h"
 #include "internal.h"
 #include "symbolic.h"
+#include "tc.h"
 #include "warp_solve.cuh"
 
 using namespace mcsdp;
@@ -684,7 +685,8 @@ void plan_workspace(mcsdp_ctx *c) {
     plan_buf(c, cur, "RS_X", r2);
     plan_buf(c, cur, "RS_P", r2);
     plan_buf(c, cur, "RS_T", r2);
-    plan_buf(c, cur, "RS_M", r2);
+    // RS_M is also the triangular inverse's work area: 256 (nR + 256) values
+    plan_buf(c, cur, "RS_M", c->dense ? std::max(r2, (size_t)256 * (c->nR + 256) * 8) : 0);
     plan_buf(c, cur, "rLinvN", rl * 8);
     plan_buf(c, cur, "rLinvX", rl * 8);
     plan_buf(c, cur, "rLinv2", rl * 8);
@@ -716,6 +718,9 @@ void plan_workspace(mcsdp_ctx *c) {
     plan_buf(c, cur, "yref", mx ? (size_t)mixed_chunks(m) * m * 8 : 0);
     plan_buf(c, cur, "ayref", mx ? (size_t)mixed_chunks(m) * m * 8 : 0);
     plan_buf(c, cur, "nref", 4 * 8);
+    const bool tc = mx && c->opt.tensor_cores != 0 && m >= 2 * TC_PANEL;
+    plan_buf(c, cur, "tc_hi", tc ? (size_t)TC_PANEL * m * 4 : 0);
+    plan_buf(c, cur, "tc_lo", tc ? (size_t)TC_PANEL * m * 4 : 0);
     plan_buf(c, cur, "L32", mx ? (size_t)nnzL * 4 : 0);
     plan_buf(c, cur, "N32", mx ? (size_t)nnzL * 4 : 0);
     plan_buf(c, cur, "dL32", mx ? (size_t)nnzD * 4 : 0);
@@ -866,6 +871,13 @@ void bind_pointers(mcsdp_ctx *c) {
   c->yref = wsp<double>(c, "yref");
   c->ayref = wsp<double>(c, "ayref");
   c->nref = wsp<double>(c, "nref");
+  {
+    const bool tc = c->opt.precision == 1 && c->opt.tensor_cores != 0 && c->S.m >= 2 * TC_PANEL;
+    c->cs.tc_hi = tc ? wsp<float>(c, "tc_hi") : nullptr;
+    c->cs.tc_lo = tc ? wsp<float>(c, "tc_lo") : nullptr;
+    c->cs.tc_rows = tc ? c->S.m : 0;
+    c->cs.tc_err = nullptr;  // the factorisation's own status word
+  }
   c->L32 = wsp<float>(c, "L32");
   c->N32 = wsp<float>(c, "N32");
   c->dL32 = wsp<float>(c, "dL32");
@@ -973,7 +985,7 @@ int factor_X_root(mcsdp_ctx *c, const double *Xbar, int *status, cudaStream_t st
   const int nR = c->nR;
   copy_square<double, double>(Xbar + c->D.root_valp, nR, c->RS_X, nR, nR, st);
   int nl = 1 + dense_potrf(c->RS_X, nR, nR, status, c->rLinvX, st, c->rsyncX, c->opt.timeout_cycles);
-  nl += dense_trtri<double>(c->RS_X, nR, c->rLinvX, c->RS_P, nR, nR, st);
+  nl += dense_trtri<double>(c->RS_X, nR, c->rLinvX, c->RS_P, nR, nR, c->RS_M, st);
   mirror_lower<double>(c->RS_P, nR, nR, st);
   return nl + 1;
 }
@@ -1098,13 +1110,14 @@ mcsdp_status phase_scm_dense(mcsdp_ctx *c) {
   symmetrize<double, T>(c->Xbar_cur + rv, nR, W1 + (size_t)nF * ldw, ldw, nR, c->stream);
   ++nl;
   if constexpr (std::is_same<T, double>::value) {
-    nl += dense_trtri<double>(c->N + rv, nR, c->rLinvN, c->RS_T, nR, nR, c->stream);
+    nl += dense_trtri<double>(c->N + rv, nR, c->rLinvN, c->RS_T, nR, nR, c->RS_M, c->stream);
     nl += dense_lauum<double>(c->RS_T, nR, nR, W2 + (size_t)nF * ldw, ldw, 1, true, c->stream);
   } else {
     float *L32 = reinterpret_cast<float *>(c->RS_T), *X32 = L32 + (size_t)nR * nR;
     copy_square<double, float>(c->N + rv, nR, L32, nR, nR, c->stream);
     launch_cast_f32(c->rLinvN, c->rLinv32, (int64_t)((nR + 31) / 32) * 1024, c->stream);
-    nl += 2 + dense_trtri<float>(L32, nR, c->rLinv32, X32, nR, nR, c->stream);
+    nl += 2 + dense_trtri<float>(L32, nR, c->rLinv32, X32, nR, nR,
+                                 reinterpret_cast<float *>(c->RS_M), c->stream);
     nl += dense_lauum<float>(X32, nR, nR, W2 + (size_t)nF * ldw, ldw, 1, true, c->stream);
   }
   int r[6] = {0, 0, 0, 0, 0, 0};
@@ -1543,6 +1556,8 @@ mcsdp_status mixed_sce(mcsdp_ctx *c, bool b32, bool *solved) {
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     prof_flush(c);
     ++c->refine_steps;
+    if (fst & ST_TIMEOUT) return fail(c, MCSDP_ERR_TIMEOUT, "FP32 factorisation: a bounded wait gave up");
+    if (fst & ST_NUMERIC) return fail(c, MCSDP_ERR_CUDA, "FP32 factorisation: a tensor map could not be made");
     if (fst & ST_NOT_PD) return MCSDP_OK;  // FP32 factor broke down: promote
     const double omega = nr[0] / std::max(nr[1], std::numeric_limits<double>::min());
     if (!std::isfinite(omega)) return MCSDP_OK;
@@ -1810,6 +1825,7 @@ void mcsdp_default_options(mcsdp_options *o) {
   o->solve_warps = 0;
   o->mixed_gap = 1e-5;
   o->root_rows = 0;
+  o->tensor_cores = 1;
 }
 
 const char *mcsdp_last_error(const mcsdp_ctx *c) { return c ? c->err.c_str() : "null context"; }
@@ -2248,6 +2264,17 @@ mcsdp_status mcsdp_solve(mcsdp_ctx *c, mcsdp_result *res) {
     if (c->opt.verbose)
       std::fprintf(stderr, "it %3d pobj %+.10e dobj %+.10e gap %.2e pinf %.2e mu %.2e ap %.3f ad %.3f\n",
                    it, pobj, dobj, gap, pinf, mu, o.ap, o.ad);
+    if (c->opt.verbose > 1 && c->dense) {
+      // the step-length bounds: the root clique's and the dual Lanczos values, the forest's
+      // smallest clique step
+      std::vector<double> ar(c->S.ns);
+      CUDA_TRY(c, cudaMemcpy(ar.data(), c->alpha_r, c->S.ns * 8, cudaMemcpyDeviceToHost));
+      double fmin = 1.0;
+      for (int r = 0; r + 1 < c->S.ns; ++r) fmin = std::min(fmin, ar[r]);
+      std::fprintf(stderr, "    root: theta %.4e bound %.2e alpha %.4f | forest min alpha %.4f | "
+                   "dual: theta %.4e bound %.2e\n", c->lz_last[0], c->lz_last[1], ar[c->S.ns - 1],
+                   fmin, c->lz_last[2], c->lz_last[3]);
+    }
     if (c->dense) {
       CUDA_TRY(c, cudaMemcpyAsync(c->Xprev, c->Xbar, c->D.nnzL * 8, cudaMemcpyDeviceToDevice, c->stream));
       CUDA_TRY(c, cudaMemcpyAsync(c->zprev, c->z, (size_t)c->S.m * 8, cudaMemcpyDeviceToDevice, c->stream));
