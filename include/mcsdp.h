@@ -113,8 +113,12 @@ typedef struct {
                             < 0 = never (such problems are then rejected), 1..112 = a lower
                             threshold (smaller problems then also get a dense root) */
   int32_t tensor_cores;  /* mixed form: 1 (default) = the FP32 SCM Cholesky's trailing updates
-                            on the tensor cores (tcgen05, three TF32 products per FP32 product)
-                            for m >= 512; 0 = on the CUDA cores */
+                            and the dense root's FP32 products on the tensor cores (tcgen05, three
+                            TF32 products per FP32 product) for m >= 512; 0 = on the CUDA cores */
+  double mixed_asm_gap;  /* mixed form: relative gap below which the SCM and the P-MATRIX are
+                            assembled in FP64 while the SCE keeps the FP32 factor and FP64
+                            refinement (until promotion).  0 = default: 1e-1 with a dense root
+                            (its FP32 products run over all n terms), else mixed_gap */
 } mcsdp_options;
 
 void mcsdp_default_options(mcsdp_options *opt);
@@ -170,7 +174,8 @@ typedef struct {
   int32_t precision;     /* the option the solve ran with */
   int32_t promoted_iter; /* mixed form: first iteration solved with the FP64 factor, -1 if none */
   int32_t refine_steps;  /* mixed form: FP64 refinement steps over the solve */
-  int32_t reserved;
+  int32_t assembly_iter; /* mixed form: first iteration with the SCM and P-MATRIX in FP64, -1 if
+                            none */
 } mcsdp_result;
 mcsdp_status mcsdp_solve(mcsdp_ctx *ctx, mcsdp_result *res);
 

@@ -20,7 +20,7 @@ class Options_t(C.Structure):
                 ("panel_max", C.c_int32), ("group_max", C.c_int32),
                 ("panel_budget_mb", C.c_double), ("profile", C.c_int32), ("relax", C.c_int32),
                 ("solve_warps", C.c_int32), ("mixed_gap", C.c_double), ("root_rows", C.c_int32),
-                ("tensor_cores", C.c_int32)]
+                ("tensor_cores", C.c_int32), ("mixed_asm_gap", C.c_double)]
 
 
 class Work_t(C.Structure):
@@ -49,7 +49,7 @@ class Result_t(C.Structure):
                 ("t_scm", C.c_double), ("t_chol", C.c_double), ("t_pmat", C.c_double),
                 ("t_other", C.c_double), ("precision", C.c_int32),
                 ("promoted_iter", C.c_int32), ("refine_steps", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("assembly_iter", C.c_int32)]
 
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_NOT_PD", 3: "ERR_MAXITER", 4: "ERR_STALL",

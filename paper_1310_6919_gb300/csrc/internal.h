@@ -79,7 +79,7 @@ struct DevSym {
   const double *slot_val, *slot_a0;
   const int *con_ptr;
   const int64_t *con_off;
-  const double *con_w;
+  const double *con_w, *con_v;
   const int *arow_ptr, *arow_col;
   const int64_t *arow_off;
   const int *rs_ptr, *rs_col;
@@ -241,6 +241,9 @@ void launch_measures(const DevSym &S, const double *Xbar, const double *Ylay, co
                      const double *alpha_r, double *scal, cudaStream_t st);
 void launch_update(const DevSym &S, double *Xbar, const double *dX, double ap, double *z,
                    const double *dz, double ad, cudaStream_t st);
+// constraints with disjoint supports: dX += sum_k c_k A_k with c_k chosen so that
+// A_k . (X̄ + dX) = b_k exactly (the projection onto the primal affine set, A A^* diagonal)
+void launch_project_primal(const DevSym &S, const double *Xbar, double *dX, cudaStream_t st);
 void launch_set_identity(const DevSym &S, double *Xbar, cudaStream_t st);
 
 // ---------------- dense root (kern_root.cu) ----------------

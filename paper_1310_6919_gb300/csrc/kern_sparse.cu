@@ -774,6 +774,27 @@ void launch_update(const DevSym &S, double *X, const double *dX, double ap, doub
   k_update<<<blocks, 256, 0, st>>>(S.nnzL, X, dX, ap, S.m, z, dz, ad);
 }
 
+// one thread per constraint k: r = b_k - A_k . X̄ - A_k . dX, c = r / (A_k . A_k), dX += c A_k on
+// A_k's positions (no other constraint touches them)
+__global__ void k_project_primal(DevSym S, const double *__restrict__ X, double *dX) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= S.m) return;
+  double ax = 0.0, ad = 0.0, aa = 0.0;
+  for (int q = S.con_ptr[k]; q < S.con_ptr[k + 1]; ++q) {
+    const double w = S.con_w[q];
+    ax = fma(w, X[S.con_off[q]], ax);
+    ad = fma(w, dX[S.con_off[q]], ad);
+    aa = fma(w, S.con_v[q], aa);
+  }
+  if (aa == 0.0) return;
+  const double cc = (S.b[k] - ax - ad) / aa;
+  for (int q = S.con_ptr[k]; q < S.con_ptr[k + 1]; ++q) dX[S.con_off[q]] += cc * S.con_v[q];
+}
+
+void launch_project_primal(const DevSym &S, const double *Xbar, double *dX, cudaStream_t st) {
+  k_project_primal<<<(S.m + 255) / 256, 256, 0, st>>>(S, Xbar, dX);
+}
+
 __global__ void k_set_identity(DevSym S, double *X) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < S.n; j += gridDim.x * blockDim.x) {
     const int t = S.col2sn[j];

@@ -132,6 +132,8 @@ struct mcsdp_ctx {
   bool f32_solves = false;      // the FP32 SCM / P-MATRIX solves fit the staged kernels
   double *gref = nullptr, *rref = nullptr, *yref = nullptr, *ayref = nullptr, *nref = nullptr;
   bool promoted = false;        // the FP64 factor is used for the rest of the solve
+  bool fp64_asm = false;        // the SCM and the P-MATRIX are assembled in FP64 (mixed form)
+  int fp64_asm_iter = -1;
   int promoted_iter = -1, refine_steps = 0, cur_iter = 0;
   double *alpha_c = nullptr, *alpha_r = nullptr, *scal = nullptr;
   int *status = nullptr, *rowof_dev = nullptr, *goff_dev = nullptr, *pm_rowof_dev = nullptr;
@@ -156,8 +158,11 @@ struct mcsdp_ctx {
   double *lzQ = nullptr, *lzW = nullptr, *lzG = nullptr, *lzU = nullptr, *lzS = nullptr;
   double *Xprev = nullptr, *zprev = nullptr;
   double lz_last[4] = {0, 0, 0, 0};  // diagnostics of the last Lanczos bounds
+  int lz_steps[2] = {0, 0};           // steps of the last primal (root) and dual bounds
   const double *Xbar_cur = nullptr;   // the X̄ the factors were last formed from
   double alpha_root_host = 1.0;       // source of the root clique's primal step copy
+  float *tcr = nullptr;               // TF32 split operands of the root's tensor-core products
+  int64_t tcr_kp = 0;                 // their row length (>= ldw, nR; multiple of 4)
   // kernel statistics
   int64_t launches = 0;
   int64_t kcount[16] = {};
@@ -310,6 +315,7 @@ void plan_workspace(mcsdp_ctx *c) {
   plan_table(c, cur, "con_ptr", S.con_ptr);
   plan_table(c, cur, "con_off", S.con_off);
   plan_table(c, cur, "con_w", S.con_w);
+  plan_table(c, cur, "con_v", S.con_v);
   plan_table(c, cur, "arow_ptr", S.arow_ptr);
   plan_table(c, cur, "arow_col", S.arow_col);
   plan_table(c, cur, "arow_off", S.arow_off);
@@ -701,6 +707,12 @@ void plan_workspace(mcsdp_ctx *c) {
     plan_buf(c, cur, "lzU", 2 * std::max<size_t>(nv, c->ldw) * 8);
     plan_buf(c, cur, "lzS", 4 * LZ_MAX * 8);
     plan_buf(c, cur, "Xprev", c->dense ? nnzL * 8 : 0);
+    // mixed form with a dense root: the TF32 hi / lo parts of the root's product operands (the
+    // P-MATRIX's rows of X̂ dY and Y^{-1}, or the inverse factor for Y^{-1}_RR)
+    const bool rtc = c->dense && c->opt.precision == 1 && c->opt.tensor_cores != 0;
+    const size_t kp = ((size_t)std::max<int64_t>(c->ldw, c->nR) + 3) / 4 * 4;
+    c->tcr_kp = (int64_t)kp;
+    plan_buf(c, cur, "tcr", rtc ? 4 * (size_t)c->nR * kp * 4 + 256 : 0);
     plan_buf(c, cur, "zprev", c->dense ? (size_t)m * 8 : 0);
   }
   plan_buf(c, cur, "alpha_c", NCAND * 8);
@@ -784,6 +796,7 @@ void bind_pointers(mcsdp_ctx *c) {
   D.con_ptr = wsp<int>(c, "con_ptr");
   D.con_off = wsp<int64_t>(c, "con_off");
   D.con_w = wsp<double>(c, "con_w");
+  D.con_v = wsp<double>(c, "con_v");
   D.arow_ptr = wsp<int>(c, "arow_ptr");
   D.arow_col = wsp<int>(c, "arow_col");
   D.arow_off = wsp<int64_t>(c, "arow_off");
@@ -916,6 +929,8 @@ void bind_pointers(mcsdp_ctx *c) {
   c->lzU = wsp<double>(c, "lzU");
   c->lzS = wsp<double>(c, "lzS");
   c->Xprev = wsp<double>(c, "Xprev");
+  c->tcr = (c->dense && c->opt.precision == 1 && c->opt.tensor_cores != 0) ? wsp<float>(c, "tcr")
+                                                                            : nullptr;
   c->zprev = wsp<double>(c, "zprev");
 }
 
@@ -1085,6 +1100,30 @@ int lsolve_c(mcsdp_ctx *c, bool fwd, const T *L, const T *Dinv, T *W, int ncols,
                    reinterpret_cast<T *>(c->Pw), active, c->stream);
 }
 
+// C = alpha A^T B + beta C on the tensor cores for the dense root's FP32 products: operand rows
+// A(:, i) = A[i a_r + l a_c] (l < K), likewise B; both split into TF32 hi / lo copies in c->tcr
+// (one copy when A and B are the same operand), then the tcgen05 product
+void root_tc_gemm(mcsdp_ctx *c, const float *A, int64_t a_r, int64_t a_c, int M, const float *B,
+                  int64_t b_r, int64_t b_c, int N, int K, float *C, int64_t cs_i, int64_t cs_j,
+                  float alpha, float beta, bool lower, bool mirror) {
+  const int64_t kp = c->tcr_kp;
+  float *ah = c->tcr, *al = ah + (size_t)c->nR * kp;
+  float *bh = al + (size_t)c->nR * kp, *bl = bh + (size_t)c->nR * kp;
+  const bool same = A == B && a_r == b_r && a_c == b_c && M == N;
+  split_tf32(A, a_r, a_c, M, K, ah, al, kp, nullptr, 0, c->stream);
+  if (!same) split_tf32(B, b_r, b_c, N, K, bh, bl, kp, nullptr, 0, c->stream);
+  TcOperand oa, ob;
+  oa.x = oa.y = ob.x = ob.y = 0;
+  const bool ok = make_tmap_kmajor(&oa.hi, ah, kp, K, M) && make_tmap_kmajor(&oa.lo, al, kp, K, M) &&
+                  make_tmap_kmajor(&ob.hi, same ? ah : bh, kp, K, N) &&
+                  make_tmap_kmajor(&ob.lo, same ? al : bl, kp, K, N);
+  if (!ok) {
+    cudaMemsetAsync(c->status + 7, 0xff, sizeof(int), c->stream);  // reported by the caller
+    return;
+  }
+  gemm_3xtf32(oa, ob, M, N, K, C, cs_i, cs_j, alpha, beta, lower, mirror, c->status + 7, c->stream);
+}
+
 // K3 with a dense root: X̂ and Y^{-1} formed whole in W1 and W2 (n x ldw, the column of vertex k
 // at colw[k]).  Their root blocks first: X̂_RR = X̄_RR (a clique block of E, so the completion
 // keeps it) and Y^{-1}_RR = (N_RR N_RR^T)^{-1} = X^T X with X = N_RR^{-1} (the trailing block of
@@ -1118,7 +1157,13 @@ mcsdp_status phase_scm_dense(mcsdp_ctx *c) {
     launch_cast_f32(c->rLinvN, c->rLinv32, (int64_t)((nR + 31) / 32) * 1024, c->stream);
     nl += 2 + dense_trtri<float>(L32, nR, c->rLinv32, X32, nR, nR,
                                  reinterpret_cast<float *>(c->RS_M), c->stream);
-    nl += dense_lauum<float>(X32, nR, nR, W2 + (size_t)nF * ldw, ldw, 1, true, c->stream);
+    if (c->tcr) {  // X^T X on the tensor cores (the full square: K = nR for every tile)
+      root_tc_gemm(c, X32, nR, 1, nR, X32, nR, 1, nR, nR, reinterpret_cast<float *>(W2) + (size_t)nF * ldw,
+                   ldw, 1, 1.f, 0.f, true, true);
+      nl += 2;
+    } else {
+      nl += dense_lauum<float>(X32, nR, nR, W2 + (size_t)nF * ldw, ldw, 1, true, c->stream);
+    }
   }
   int r[6] = {0, 0, 0, 0, 0, 0};
   if (nF > 0) {
@@ -1243,19 +1288,26 @@ mcsdp_status phase_pmatrix_dense(mcsdp_ctx *c, double betamu, const double *Xbar
   KScope k1(c, KC_PMAT);
   CUDA_TRY(c, cudaMemsetAsync(V, 0, (size_t)n * ldw * sizeof(T), c->stream));
   launch_times_pattern<T>(c->D, c->dY, W1, V, ldw, c->colw_dev, c->stream);
-  GemmArgs<T> g{};
-  g.M = g.N = nR;
-  g.K = (int)ldw;
-  g.A = V + (size_t)nF * ldw;
-  g.lda = ldw;
-  g.B = W2 + (size_t)nF * ldw;
-  g.ldb = ldw;
-  g.C = M;
-  g.cs_i = 1;
-  g.cs_j = nR;
-  g.alpha = T(1);
-  g.beta = T(0);
-  gemm_tn<T>(g, c->stream);
+  if constexpr (std::is_same<T, float>::value) {
+    if (c->tcr)
+      root_tc_gemm(c, V + (size_t)nF * ldw, ldw, 1, nR, W2 + (size_t)nF * ldw, ldw, 1, nR, (int)ldw,
+                   M, 1, nR, 1.f, 0.f, false, false);
+  }
+  if (!(std::is_same<T, float>::value && c->tcr)) {
+    GemmArgs<T> g{};
+    g.M = g.N = nR;
+    g.K = (int)ldw;
+    g.A = V + (size_t)nF * ldw;
+    g.lda = ldw;
+    g.B = W2 + (size_t)nF * ldw;
+    g.ldb = ldw;
+    g.C = M;
+    g.cs_i = 1;
+    g.cs_j = nR;
+    g.alpha = T(1);
+    g.beta = T(0);
+    gemm_tn<T>(g, c->stream);
+  }
   launch_extract_dense<T>(c->D, W2, ldw, c->colw_dev, c->YinvE, c->stream);
   launch_forest_M<T>(c->D, V, W2, ldw, (int)ldw, c->Mlow, c->Mup, c->stream);
   launch_root_M<T>(M, nR, c->Mlow + rv, c->Mup + rv, c->stream);
@@ -1486,6 +1538,7 @@ mcsdp_status dense_steps(mcsdp_ctx *c, double *alpha_root, double *alpha_dual) {
     ks.done(1 + 8 * steps);
     if (s) return s;
     *alpha_root = step_from_bound(th, bd);
+    c->lz_steps[0] = steps;
     c->lz_last[0] = th;
     c->lz_last[1] = bd;
   }
@@ -1507,6 +1560,7 @@ mcsdp_status dense_steps(mcsdp_ctx *c, double *alpha_root, double *alpha_dual) {
     ks.done(1 + 9 * steps);
     if (s) return s;
     *alpha_dual = step_from_bound(th, bd);
+    c->lz_steps[1] = steps;
     c->lz_last[2] = th;
     c->lz_last[3] = bd;
   }
@@ -1582,8 +1636,9 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
   const double beta = c->opt.beta;
   const int m = c->S.m;
   cudaEventRecord(c->ev[0], c->stream);
+  CUDA_TRY(c, cudaMemsetAsync(c->status + 7, 0, sizeof(int), c->stream));
   // mixed form before promotion: FP32 solves and contraction from FP32 copies of the factors
-  bool f32 = c->opt.precision == 1 && !c->promoted && c->f32_solves;
+  bool f32 = c->opt.precision == 1 && !c->promoted && !c->fp64_asm && c->f32_solves;
   if (f32) cast_factors(c);
   // the P-MATRIX's Y^{-1} columns need only N: with a single block they are formed on the side
   // stream st3 (own solve buffer, partial slots and marks) beside the SCM solves, which are
@@ -1626,6 +1681,10 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
         // FP32-assembled B can be singular where the FP64 one is not)
         c->promoted = true;
         c->promoted_iter = c->cur_iter;
+        if (!c->fp64_asm) {
+          c->fp64_asm = true;
+          c->fp64_asm_iter = c->cur_iter;
+        }
         if (f32) {
           f32 = false;
           s = phase_scm<double>(c);  // (the side stream's FP32 Y^{-1} is redone below)
@@ -1674,6 +1733,15 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
     KScope k2(c, KC_MISC);
     launch_dx_combine(c->D, beta * mu, Xbar, c->YinvE, c->Mlow, c->Mup, c->dX, c->stream);
     k2.done(1);
+  }
+  // mixed form, FP32 phase: the FP32 products leave A(dX) off b - A(X̄) by their rounding (about
+  // 1e-6 relative), which the iterations would accumulate in the primal residual; with disjoint
+  // constraint supports (A A^* diagonal, e.g. max-cut) the direction is projected back onto the
+  // primal affine set in FP64
+  if (f32 && c->S.con_disjoint) {
+    KScope kp(c, KC_MISC);
+    launch_project_primal(c->D, Xbar, c->dX, c->stream);
+    kp.done(1);
   }
   KCHECK(c);
   cudaEventRecord(c->ev[3], c->stream);
@@ -1736,11 +1804,13 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
   }
   KCHECK(c);
   double sc[8];
-  int st[4];
+  int st[8];
   CUDA_TRY(c, cudaMemcpyAsync(sc, c->scal, 6 * 8, cudaMemcpyDeviceToHost, c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(st, c->status, 4 * 4, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(st, c->status, 8 * 4, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   prof_flush(c);
+  if (st[7] == -1) return fail(c, MCSDP_ERR_CUDA, "a tensor map of the root's products could not be made");
+  if (st[7] & ST_TIMEOUT) return fail(c, MCSDP_ERR_TIMEOUT, "tensor-core product: a bounded wait gave up");
   if (st[2] & ST_TIMEOUT) return fail(c, MCSDP_ERR_TIMEOUT, "SCM factorisation: a bounded wait gave up");
   if (st[2] & ST_NOT_PD) return fail(c, MCSDP_ERR_NOT_PD, "Schur complement matrix is not positive definite");
   o.ap = sc[5];
@@ -1826,6 +1896,7 @@ void mcsdp_default_options(mcsdp_options *o) {
   o->mixed_gap = 1e-5;
   o->root_rows = 0;
   o->tensor_cores = 1;
+  o->mixed_asm_gap = 0.0;
 }
 
 const char *mcsdp_last_error(const mcsdp_ctx *c) { return c ? c->err.c_str() : "null context"; }
@@ -2135,6 +2206,7 @@ mcsdp_status mcsdp_scm_assemble(mcsdp_ctx *c, const double *Xbar, const double *
   if (s) return s;
   if (precision == 1 && !(c->opt.precision == 1 && c->f32_solves))
     return fail(c, MCSDP_ERR_ARG, "precision 1 needs a context created with precision 1");
+  CUDA_TRY(c, cudaMemsetAsync(c->status + 7, 0, sizeof(int), c->stream));
   if (precision == 1) {
     cast_factors(c);
     s = phase_scm<float>(c);
@@ -2146,9 +2218,11 @@ mcsdp_status mcsdp_scm_assemble(mcsdp_ctx *c, const double *Xbar, const double *
   launch_B_to_user(c->D, c->B, c->ldb, Bout, ldb, c->hvec, h, c->stream);
   ks.done(1);
   KCHECK(c);
-  int st[4];
-  s = read_status(c, st, 4);
+  int st[8];
+  s = read_status(c, st, 8);
   if (s) return s;
+  if (st[7] == -1) return fail(c, MCSDP_ERR_CUDA, "a tensor map of the root's products could not be made");
+  if (st[7] & ST_TIMEOUT) return fail(c, MCSDP_ERR_TIMEOUT, "tensor-core product: a bounded wait gave up");
   if (st[0] & ST_NOT_PD) return fail(c, MCSDP_ERR_NOT_PD, "Y is not positive definite");
   if (st[1] & ST_NOT_PD) return fail(c, MCSDP_ERR_NOT_PD, "a clique block of X̄ is not positive definite");
   return MCSDP_OK;
@@ -2193,7 +2267,14 @@ mcsdp_status mcsdp_solve(mcsdp_ctx *c, mcsdp_result *res) {
   mcsdp_result r{};
   c->promoted = false;
   c->promoted_iter = -1;
+  c->fp64_asm = false;
+  c->fp64_asm_iter = -1;
   c->refine_steps = 0;
+  // the mixed form's FP64-assembly threshold: with a dense root the FP32 products run over all
+  // n terms (root GEMMs), and their rounding, relative to the shrinking direction, decides the
+  // root clique's primal step well before the FP32 factor stops refining
+  const double mixed_gap = c->opt.mixed_gap > 0 ? c->opt.mixed_gap : 1e-5;
+  const double asm_gap = c->opt.mixed_asm_gap > 0 ? c->opt.mixed_asm_gap : (c->dense ? 1e-1 : mixed_gap);
   double prev_pinf = -1.0;
   float tms[4] = {0, 0, 0, 0};
   cudaEvent_t t0 = c->ev[6], t1 = c->ev[7];
@@ -2231,10 +2312,13 @@ mcsdp_status mcsdp_solve(mcsdp_ctx *c, mcsdp_result *res) {
     // above the level the FP32 solves leave (about 1e-6 relative; it contracts by
     // (1 - gamma alpha_p) per iteration in exact arithmetic)
     if (c->opt.precision == 1 && !c->promoted &&
-        ((prev_pinf > 0 && pinf > 2.0 * prev_pinf && pinf > 1e-4) ||
-         gap < (c->opt.mixed_gap > 0 ? c->opt.mixed_gap : 1e-5))) {
+        ((prev_pinf > 0 && pinf > 2.0 * prev_pinf && pinf > 1e-4) || gap < mixed_gap)) {
       c->promoted = true;
       c->promoted_iter = it;
+    }
+    if (c->opt.precision == 1 && !c->fp64_asm && (c->promoted || gap < asm_gap)) {
+      c->fp64_asm = true;
+      c->fp64_asm_iter = it;
     }
     prev_pinf = pinf;
     c->cur_iter = it;
@@ -2299,6 +2383,7 @@ mcsdp_status mcsdp_solve(mcsdp_ctx *c, mcsdp_result *res) {
   r.status = final_status;
   r.precision = c->opt.precision;
   r.promoted_iter = c->opt.precision == 1 ? c->promoted_iter : -1;
+  r.assembly_iter = c->opt.precision == 1 ? c->fp64_asm_iter : -1;
   r.refine_steps = c->refine_steps;
   if (res) *res = r;
   return final_status;
@@ -2451,6 +2536,60 @@ mcsdp_status mcsdp_work_model(const mcsdp_ctx *c, mcsdp_work *w) {
   w->bytes[7] = 8 * 2 * nnzE;
   w->flops[8] = fy;
   w->bytes[8] = 8 * 3 * nnzE;
+  if (!c->dense) return MCSDP_OK;
+  // dense root R (nR = |R|): the forest's small-clique work plus the root's dense kernels; the
+  // dense completion forms X̂ and Y^{-1} whole (n x n, FP64 or FP32)
+  const double nR = c->nR, nF = c->nF, n = S.n;
+  const int rt = ns - 1;
+  double entF = 0;  // stored lower entries of the forest's blocks
+  for (int t = 0; t < rt; ++t) entF += ent[t];
+  double pathF = 0;  // forest part of the forward paths of the forest's unit columns
+  for (int j = 0; j < c->nF; ++j) {
+    int t = S.col2sn[j];
+    for (double cc = j - S.sn_col[t]; cc < ncol_of(t); cc += 1) pathF += nrow_of(t) - cc;
+    for (t = S.sn_parent[t]; t >= 0 && t != rt; t = S.sn_parent[t]) pathF += ent[t];
+  }
+  // K2: the forest's supernodal Cholesky, the gathered contributions, the root's Cholesky
+  double fy2 = 0;
+  for (int t = 0; t < rt; ++t) {
+    const double k = ncol_of(t), r = nrow_of(t);
+    fy2 += k * k * k / 3 + (r - k) * k * k;
+    for (int u = S.upd_ptr[t]; u < S.upd_ptr[t + 1]; ++u) {
+      const int src = S.upd_src[u];
+      const double na = nrow_of(src) - S.upd_p1[u], nb = S.upd_p2[u] - S.upd_p1[u];
+      fy2 += 2 * ncol_of(src) * (na * nb - nb * (nb - 1) / 2);
+    }
+  }
+  double gath = 0;
+  for (size_t q = 0; q < c->rg_u.size(); ++q) gath += 2 * c->upd_meta[c->rg_u[q]].dncol;
+  w->flops[0] = fy2 + gath + nR * nR * nR / 3;
+  w->bytes[0] = 8 * (2 * entF + nR * nR);
+  // K1: the forest's cliques (Algorithm 1), the root's Cholesky and triangular inverse
+  double f12 = 0;
+  for (int t = 0; t < rt; ++t) f12 += 2 * nrow_of(t) * nrow_of(t) * nrow_of(t) / 3;
+  w->flops[1] = f12 + 2 * nR * nR * nR / 3;
+  w->bytes[1] = 8 * (2 * entF + 2 * nR * nR);
+  // K3 panels: Y^{-1}_RR (triangular inverse + X^T X, 2 nR^3 / 3), then per factor the backward
+  // forest solves of the nR root columns and the forward + backward solves of the nF forest
+  // columns; X̂ and Y^{-1} written once
+  w->flops[2] = 2 * nR * nR * nR / 3 + 2 * (2 * nR * entF + 2 * (pathF + nF * entF));
+  w->bytes[2] = 8 * (2 * n * n + 2 * nnzE);
+  // K3 tiles: both dense matrices read once, lower(B) written once
+  w->bytes[3] = 8 * (2 * n * n + S.m * (S.m + 1.0) / 2);
+  // K6: V = X̂ dY, the root block's GEMM (2 nR^2 n), the forest's row dot products
+  double fM = 0;
+  for (int t = 0; t < rt; ++t) fM += 2 * 2 * ent[t] * n;
+  w->flops[6] = 2 * arow * n + 2 * nR * nR * n + fM;
+  w->bytes[6] = 8 * (3 * n * n + 4 * nnzE);
+  // K7: the forest's cliques as above; the root's Lanczos bound, 3 products with nR x nR
+  // matrices per step (the step count of the last bound)
+  double fps2 = 0;
+  for (int t = 0; t < rt; ++t) fps2 += (1.0 / 3 + 2.0 + 4.0 / 3) * nrow_of(t) * nrow_of(t) * nrow_of(t);
+  w->flops[7] = fps2 + 2 * 3 * nR * nR * std::max(1, c->lz_steps[0]);
+  w->bytes[7] = 8 * (2 * entF + 3 * nR * nR * std::max(1, c->lz_steps[0]));
+  // K8: the dual Lanczos bound, one n x n product per step
+  w->flops[8] = 2 * n * n * std::max(1, c->lz_steps[1]);
+  w->bytes[8] = 8 * n * n * std::max(1, c->lz_steps[1]);
   return MCSDP_OK;
 }
 

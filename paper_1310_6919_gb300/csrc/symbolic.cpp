@@ -566,17 +566,27 @@ std::string analyze(const ProblemData &P, const SymbolicOptions &o, Symbolic &S)
     }
     S.nslot = (int64_t)S.slot_off.size();
     // constraint lists
-    std::vector<std::vector<std::pair<int64_t, double>>> cl(m);
+    std::vector<std::vector<std::array<double, 3>>> cl(m);  // (offset, weight, value)
     for (size_t t = 0; t < ne; ++t) {
       if (P.mat[t] == 0) continue;
       double w = P.row[t] == P.col[t] ? P.val[t] : 2.0 * P.val[t];
-      cl[P.mat[t] - 1].push_back({off[t], w});
+      cl[P.mat[t] - 1].push_back({(double)off[t], w, P.val[t]});
     }
     S.con_ptr.assign(m + 1, 0);
+    S.con_disjoint = true;
     for (int k = 0; k < m; ++k) {
       std::sort(cl[k].begin(), cl[k].end());
-      for (auto &e : cl[k]) { S.con_off.push_back(e.first); S.con_w.push_back(e.second); }
+      for (auto &e : cl[k]) {
+        S.con_off.push_back((int64_t)e[0]);
+        S.con_w.push_back(e[1]);
+        S.con_v.push_back(e[2]);
+      }
       S.con_ptr[k + 1] = (int)S.con_off.size();
+    }
+    {
+      std::vector<int64_t> offs(S.con_off.begin(), S.con_off.end());
+      std::sort(offs.begin(), offs.end());
+      S.con_disjoint = std::adjacent_find(offs.begin(), offs.end()) == offs.end();
     }
     // symmetric row lists over slots
     std::vector<std::vector<std::pair<int, int64_t>>> rl(n);

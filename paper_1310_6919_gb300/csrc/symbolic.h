@@ -51,6 +51,8 @@ struct Symbolic {
   std::vector<int> con_ptr;                 // m+1
   std::vector<int64_t> con_off;
   std::vector<double> con_w;
+  std::vector<double> con_v;                // the entry's value itself
+  bool con_disjoint = false;                // no two constraints share a stored position
   // full symmetric row lists of the aggregate pattern for sparse products
   std::vector<int> arow_ptr;                // n+1
   std::vector<int> arow_col;
