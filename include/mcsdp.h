@@ -219,14 +219,15 @@ mcsdp_status mcsdp_factors(mcsdp_ctx *ctx, const double *Xbar_layout_dev, const 
  * launches the library issued (always counted) and, when options.profile = 1, the device time of
  * each kernel class measured with CUDA events recorded on the context's stream around the
  * launches of that class.  Classes: 0 K2 Y=NN^T, 1 K1 Algorithm 1, 2 SCM panel solves,
- * 3 SCM tile contraction, 4 SCM Cholesky (task queue; FP32: potrf/trsm/syrk), 5 SCE back
- * substitution, 6 P-MATRIX, 7 primal step length, 8 dual step length (candidate
- * factorisations), 9 other (pattern scatter, scalars, update), 10 P-MATRIX Y^{-1} columns on
- * a side stream (single column block: they run beside the SCM solves; their flops are counted
- * in class 6), 11 the SCM's N solves on a side stream (beside the L̂ solves of class 2; their
- * flops are counted in class 2).  Classes 1, 7, 10 and 11 run on side streams (class 1
- * beside class 0), so their times overlap the others'. */
-#define MCSDP_NCLASS 12
+ * 3 SCM tile contraction, 4 SCM Cholesky in FP64 (task queue), 5 SCE back substitution,
+ * 6 P-MATRIX, 7 primal step length, 8 dual step length (candidate factorisations, or the
+ * Lanczos bound with a dense root), 9 other (pattern scatter, scalars, update), 10 P-MATRIX
+ * Y^{-1} columns on a side stream (single column block: they run beside the SCM solves; their
+ * flops are counted in class 6), 11 the SCM's N solves on a side stream (beside the L̂ solves of
+ * class 2; their flops are counted in class 2), 12 the mixed form's FP32 SCM Cholesky (tensor
+ * cores for m >= 512; its work is class 4's).  Classes 1, 7, 10 and 11 run on side streams
+ * (class 1 beside class 0), so their times overlap the others'. */
+#define MCSDP_NCLASS 13
 typedef struct {
   int64_t launches;
   int64_t count[16];   /* launches per class */

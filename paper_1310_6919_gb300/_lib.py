@@ -32,7 +32,7 @@ class Stats_t(C.Structure):
 
 
 KCLASS = ["ychol", "alg1", "scm_panel", "scm_tile", "scm_chol", "sce_backsolve", "pmatrix",
-          "primal_step", "dual_step", "other", "pmatrix_side", "scm_panel_side"]
+          "primal_step", "dual_step", "other", "pmatrix_side", "scm_panel_side", "scm_chol32"]
 
 
 class SymInfo_t(C.Structure):

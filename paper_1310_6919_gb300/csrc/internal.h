@@ -269,7 +269,8 @@ void dotcols(const T *A, int64_t ld, int ncol, int len, int range, const double 
              double alpha, double beta, cudaStream_t st);
 void lz_alpha(int n, double *w, const double *gvj, const double *vj, const double *vjm1,
               double *s, int j, cudaStream_t st);
-void lz_reorth(int n, int jcount, double *w, const double *Qd, const double *Q, cudaStream_t st);
+void lz_reorth(int n, int jcount, double *w, const double *Qd, const double *Q, double *h,
+               cudaStream_t st);
 void lz_beta(int n, const double *w, const double *gw, double *vnext, double *gvnext, double *s,
              int j, cudaStream_t st);
 void lz_normalise(int n, double *v, double *gv, cudaStream_t st);
@@ -284,6 +285,10 @@ void launch_extract_dense(const DevSym &S, const T *W, int64_t ldw, const int *c
 template <class T>
 void launch_times_pattern(const DevSym &S, const double *D, const T *W, T *V, int64_t ldw,
                           const int *colw, cudaStream_t st);
+// the same for a D that is zero off the diagonal (dcol: ldw values of scratch)
+template <class T>
+void launch_times_diag(const DevSym &S, const double *D, const T *W, T *V, int64_t ldw,
+                       const int *colw, T *dcol, cudaStream_t st);
 template <class T>
 void launch_forest_M(const DevSym &S, const T *V, const T *Wy, int64_t ldw, int ncolw,
                      double *Mlow, double *Mup, cudaStream_t st);
@@ -308,6 +313,11 @@ int dense_potrf(double *A, int64_t ld, int n, int *status, double *Linv, cudaStr
 // diagonal tiles.
 size_t scm_tiles_smem_bytes(const DevSym &S, int pmax);
 // T = double: FP64 form; T = float: mixed form (FP32 operands and sums, entries stored in FP64)
+// max-cut-shaped constraints with X̂ and Y^{-1} formed whole: B_ij = X̂(v_i, v_j) Y^{-1}(v_i, v_j) for
+// internal constraints i >= j on vertices vtx[i], h_i = Y^{-1}(v_i, v_i)
+template <class T>
+void launch_scm_hadamard(const DevSym &S, const T *WX, const T *WY, int64_t ldw, const int *colw,
+                         const int *vtx, double *B, int64_t ldb, double *hvec, cudaStream_t st);
 // colmap != nullptr (dense completion): the column of vertex k is colmap[k] (goff unused)
 template <class T>
 void launch_scm_tiles(const DevSym &S, const int2 *tiles, int ntiles, const T *WX, const T *WY,

@@ -811,22 +811,23 @@ static void atomic_status_host_fail(int *status, cudaStream_t st) {
 static int dense_chol_f32_tc(float *B, int64_t ldb, int m, int *status, float *Linv_all,
                              cudaStream_t st, const CholStreams *cs) {
   int nl = 0;
-  for (int k0 = 0; k0 < m; k0 += TC_PANEL) {
-    const int pw = std::min(TC_PANEL, m - k0);
+  const int P = tc_panel(m);
+  for (int k0 = 0; k0 < m; k0 += P) {
+    const int pw = std::min(P, m - k0);
     nl += dense_chol<float>(B + k0 + (int64_t)k0 * ldb, ldb, pw, m - k0, status,
                             Linv_all + (int64_t)(k0 / NB) * NB * NB, st, nullptr);
     const int r0 = k0 + pw;
     if (r0 >= m) break;
-    split_tf32(B + r0 + (int64_t)k0 * ldb, 1, ldb, m - r0, pw, cs->tc_hi, cs->tc_lo, TC_PANEL,
+    split_tf32(B + r0 + (int64_t)k0 * ldb, 1, ldb, m - r0, pw, cs->tc_hi, cs->tc_lo, P,
                B + k0 + (int64_t)r0 * ldb, ldb, st);
-    TcOperand P;
-    P.x = P.y = 0;
-    if (!make_tmap_kmajor(&P.hi, cs->tc_hi, TC_PANEL, pw, m - r0) ||
-        !make_tmap_kmajor(&P.lo, cs->tc_lo, TC_PANEL, pw, m - r0)) {
+    TcOperand Op;
+    Op.x = Op.y = 0;
+    if (!make_tmap_kmajor(&Op.hi, cs->tc_hi, P, pw, m - r0) ||
+        !make_tmap_kmajor(&Op.lo, cs->tc_lo, P, pw, m - r0)) {
       atomic_status_host_fail(status, st);
       return nl;
     }
-    gemm_3xtf32(P, P, m - r0, m - r0, pw, B + r0 + (int64_t)r0 * ldb, 1, ldb, -1.f, 1.f, true,
+    gemm_3xtf32(Op, Op, m - r0, m - r0, pw, B + r0 + (int64_t)r0 * ldb, 1, ldb, -1.f, 1.f, true,
                 false, cs->tc_err ? cs->tc_err : status, st);
     nl += 2;
   }

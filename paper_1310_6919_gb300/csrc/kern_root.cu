@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -388,8 +389,23 @@ __global__ void k_dotcols(const T *__restrict__ A, int64_t ld, int ncol, int len
   if (j >= ncol) return;
   const int lo = range == 1 ? j : 0, hi = range == 2 ? min(len, j + 1) : len;
   const T *col = A + (int64_t)j * ld;
+  // four independent partial sums (four loads of the column in flight per lane), in T over
+  // blocks of 1024 entries (FP32 in the mixed form: the matrix is FP32 and FP64 arithmetic would
+  // run on the slow FP64 pipe), carried in FP64
   double acc = 0.0;
-  for (int i = lo + lane; i < hi; i += 32) acc = fma((double)col[i], v[i], acc);
+  int i = lo + lane;
+  while (i + 96 < hi) {
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+    const int iend = min(hi - 96, i + 1024);
+    for (; i < iend; i += 128) {
+      a0 = fma(__ldcs(col + i), (T)v[i], a0);
+      a1 = fma(__ldcs(col + i + 32), (T)v[i + 32], a1);
+      a2 = fma(__ldcs(col + i + 64), (T)v[i + 64], a2);
+      a3 = fma(__ldcs(col + i + 96), (T)v[i + 96], a3);
+    }
+    acc += (double)((a0 + a1) + (a2 + a3));
+  }
+  for (; i < hi; i += 32) acc = fma((double)col[i], v[i], acc);
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) w[j] = beta == 0.0 ? alpha * acc : fma(alpha, acc, beta * w[j]);
 }
@@ -500,8 +516,33 @@ void lz_alpha(int n, double *w, const double *gvj, const double *vj, const doubl
               double *s, int j, cudaStream_t st) {
   k_lz_alpha<<<1, 1024, 0, st>>>(n, w, gvj, vj, vjm1, s, j);
 }
-void lz_reorth(int n, int jcount, double *w, const double *Qd, const double *Q, cudaStream_t st) {
-  k_lz_reorth<<<1, 1024, 0, st>>>(n, jcount, w, Qd, Q);
+// h_c = <Qd_c, w> (one CTA per c), then w -= sum_c h_c Q_c (grid-stride): the reorthogonalisation
+// spread over the SMs
+__global__ void k_lz_dots(int n, const double *__restrict__ w, const double *__restrict__ Qd,
+                          double *h) {
+  __shared__ double red[32];
+  const int c = blockIdx.x;
+  const double *q = Qd + (int64_t)c * n;
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a = fma(q[i], w[i], a);
+  a = block_sum(a, red);
+  if (threadIdx.x == 0) h[c] = a;
+}
+__global__ void k_lz_sub(int n, int jcount, double *w, const double *__restrict__ Q,
+                         const double *__restrict__ h) {
+  __shared__ double hs[128];
+  for (int c = threadIdx.x; c < jcount; c += blockDim.x) hs[c] = h[c];
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double x = w[i];
+    for (int c = 0; c < jcount; ++c) x -= hs[c] * Q[(int64_t)c * n + i];
+    w[i] = x;
+  }
+}
+void lz_reorth(int n, int jcount, double *w, const double *Qd, const double *Q, double *h,
+               cudaStream_t st) {
+  k_lz_dots<<<jcount, 512, 0, st>>>(n, w, Qd, h);
+  k_lz_sub<<<(n + 255) / 256, 256, 0, st>>>(n, jcount, w, Q, h);
 }
 void lz_beta(int n, const double *w, const double *gw, double *vnext, double *gvnext, double *s,
              int j, cudaStream_t st) {
@@ -600,21 +641,25 @@ template <class T>
 __global__ void __launch_bounds__(256) k_forest_M(DevSym S, const T *__restrict__ V,
                                                   const T *__restrict__ Wy, int64_t ldw,
                                                   int ncolw, double *Mlow, double *Mup) {
-  constexpr int CH = 32, PER = 8;
+  constexpr int CH = 32, PER = 8, LDS = CH + 1;  // rows padded: threads of a warp take
+                                                  // consecutive rows p, so an unpadded stride
+                                                  // of 32 would put them in one bank
   extern __shared__ __align__(16) unsigned char smf[];
   const int s = blockIdx.x;
   const int64_t r0 = S.sn_rowptr[s];
   const int nrow = (int)(S.sn_rowptr[s + 1] - r0);
   const int ncol = S.sn_col[s + 1] - S.sn_col[s];
   const int64_t v0 = S.sn_valptr[s];
-  T *Vs = reinterpret_cast<T *>(smf);  // [nrow][CH]
-  T *Ys = Vs + nrow * CH;               // [nrow][CH]
-  int *rw = reinterpret_cast<int *>(Ys + nrow * CH);
+  T *Vs = reinterpret_cast<T *>(smf);  // [nrow][LDS]
+  T *Ys = Vs + nrow * LDS;              // [nrow][LDS]
+  int *rw = reinterpret_cast<int *>(Ys + nrow * LDS);
   const int tid = threadIdx.x;
   for (int p = tid; p < nrow; p += blockDim.x) rw[p] = S.rows[r0 + p];
   const int nout = nrow * ncol;
   __syncthreads();
   // outputs in passes of 256 x PER; each thread keeps the lower and upper sums of PER of them
+  // sums in T per chunk (FP32 in the mixed form: FP64 arithmetic would run on the slow FP64
+  // pipe), carried across chunks in FP64
   for (int pass = 0; pass * 256 * PER < nout; ++pass) {
     double lo[PER], up[PER];
 #pragma unroll
@@ -624,8 +669,8 @@ __global__ void __launch_bounds__(256) k_forest_M(DevSym S, const T *__restrict_
         const int p = e / CH, c = e % CH;
         const int64_t o = (int64_t)rw[p] * ldw + c0 + c;
         const bool in = c0 + c < ncolw;
-        Vs[e] = in ? V[o] : T(0);
-        Ys[e] = in ? Wy[o] : T(0);
+        Vs[p * LDS + c] = in ? V[o] : T(0);
+        Ys[p * LDS + c] = in ? Wy[o] : T(0);
       }
       __syncthreads();
 #pragma unroll
@@ -634,15 +679,15 @@ __global__ void __launch_bounds__(256) k_forest_M(DevSym S, const T *__restrict_
         if (e >= nout) break;
         const int p = e % nrow, lc = e / nrow;
         if (p < lc) continue;
-        const T *vp = Vs + p * CH, *yl = Ys + lc * CH, *vl = Vs + lc * CH, *yp = Ys + p * CH;
-        double a = lo[q], b = up[q];
+        const T *vp = Vs + p * LDS, *yl = Ys + lc * LDS, *vl = Vs + lc * LDS, *yp = Ys + p * LDS;
+        T a = T(0), b = T(0);
 #pragma unroll 8
         for (int c = 0; c < CH; ++c) {
-          a = fma((double)vp[c], (double)yl[c], a);
-          b = fma((double)vl[c], (double)yp[c], b);
+          a = fma(vp[c], yl[c], a);
+          b = fma(vl[c], yp[c], b);
         }
-        lo[q] = a;
-        up[q] = b;
+        lo[q] += (double)a;
+        up[q] += (double)b;
       }
       __syncthreads();
     }
@@ -712,6 +757,40 @@ void launch_extract_dense(const DevSym &S, const T *W, int64_t ldw, const int *c
     k_extract_dense<T><<<dim3(blocks, 1), 256, 0, st>>>(R, W, ldw, colw, outE);
   }
 }
+// V[i][colw[b]] = W[i][colw[b]] d_b for a diagonal D (d_b = D at the diagonal position of b):
+// one pass over W
+template <class T>
+__global__ void k_times_diag(const T *__restrict__ W, T *V, int64_t ldw, const T *__restrict__ dcol,
+                             int64_t total) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x)
+    V[e] = W[e] * dcol[e % ldw];
+}
+// dcol[colw[b]] = D at (b, b) (0 at padding columns)
+__global__ void k_diag_to_cols(DevSym S, const double *__restrict__ D, const int *__restrict__ colw,
+                               int64_t *diag_off, void *dcol, int fp32) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= S.n) return;
+  const int t = S.col2sn[b];
+  const int nrow = (int)(S.sn_rowptr[t + 1] - S.sn_rowptr[t]);
+  const int lc = b - S.sn_col[t];
+  const double v = D[S.sn_valptr[t] + lc + (int64_t)lc * nrow];
+  if (fp32) static_cast<float *>(dcol)[colw[b]] = (float)v;
+  else static_cast<double *>(dcol)[colw[b]] = v;
+  (void)diag_off;
+}
+
+template <class T>
+void launch_times_diag(const DevSym &S, const double *D, const T *W, T *V, int64_t ldw,
+                       const int *colw, T *dcol, cudaStream_t st) {
+  cudaMemsetAsync(dcol, 0, ldw * sizeof(T), st);
+  k_diag_to_cols<<<(S.n + 255) / 256, 256, 0, st>>>(S, D, colw, nullptr, dcol,
+                                                    std::is_same<T, float>::value ? 1 : 0);
+  const int64_t total = (int64_t)S.n * ldw;
+  const int blocks = (int)std::min<int64_t>(152 * 16, (total + 255) / 256);
+  k_times_diag<T><<<blocks, 256, 0, st>>>(W, V, ldw, dcol, total);
+}
+
 template <class T>
 void launch_times_pattern(const DevSym &S, const double *D, const T *W, T *V, int64_t ldw,
                           const int *colw, cudaStream_t st) {
@@ -720,7 +799,7 @@ void launch_times_pattern(const DevSym &S, const double *D, const T *W, T *V, in
 }
 template <class T>
 size_t forest_M_smem(const DevSym &S) {
-  return (size_t)2 * S.max_nrow * 32 * sizeof(T) + (size_t)S.max_nrow * 4 + 16;
+  return (size_t)2 * S.max_nrow * 33 * sizeof(T) + (size_t)S.max_nrow * 4 + 16;
 }
 template <class T>
 void launch_forest_M(const DevSym &S, const T *V, const T *Wy, int64_t ldw, int ncolw,
@@ -794,6 +873,8 @@ void permute_to_cols(const double *src, const int *colw, double *dst, int n, cud
                                         cudaStream_t);                                           \
   template void launch_times_pattern<T>(const DevSym &, const double *, const T *, T *, int64_t,  \
                                         const int *, cudaStream_t);                              \
+  template void launch_times_diag<T>(const DevSym &, const double *, const T *, T *, int64_t,     \
+                                     const int *, T *, cudaStream_t);                            \
   template void launch_forest_M<T>(const DevSym &, const T *, const T *, int64_t, int, double *,  \
                                    double *, cudaStream_t);                                      \
   template void launch_root_M<T>(const T *, int, double *, double *, cudaStream_t);        \

@@ -137,6 +137,46 @@ void launch_scm_tiles(const DevSym &S, const int2 *tiles, int ntiles, const T *W
   smem_optin((const void *)k_scm_tiles<T>);
   k_scm_tiles<T><<<ntiles, 256, smem, st>>>(S, tiles, WX, WY, ldw, goff, B, ldb, hvec, colmap);
 }
+// Max-cut-shaped constraints (every A_k = e_k e_k^T): eq. newSCM2 reduces to B = X̂ o Y^{-1} on the
+// constraints' vertices (the Hadamard product of Sec. 3.1's max-cut discussion).  With X̂ and Y^{-1}
+// formed whole (the dense-root path, row-major n x ldw, vertex k's column at colw[k]; both
+// symmetric) the lower triangle of B streams: column j of B reads row v_j of both matrices at the
+// columns of v_i, i >= j (consecutive i, consecutive columns), and writes B[i + j ldb]; h_i =
+// Y^{-1}(v_i, v_i).  Grid: x over the rows i of a column chunk, y over the columns j.
+template <class T>
+__global__ void __launch_bounds__(256) k_scm_hadamard(DevSym S, const T *__restrict__ WX,
+                                                      const T *__restrict__ WY, int64_t ldw,
+                                                      const int *__restrict__ colw,
+                                                      const int *__restrict__ vtx, double *B,
+                                                      int64_t ldb, double *hvec) {
+  const int m = S.m;
+  for (int j = blockIdx.y; j < m; j += gridDim.y) {
+    const int vj = vtx[j];
+    const T *xr = WX + (int64_t)vj * ldw, *yr = WY + (int64_t)vj * ldw;
+    double *bc = B + (int64_t)j * ldb;
+    for (int i = j + blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+      const int c = colw[vtx[i]];
+      const T v = xr[c] * yr[c];
+      bc[i] = (double)v;
+      if (i == j) hvec[i] = (double)yr[c];
+    }
+  }
+}
+
+template <class T>
+void launch_scm_hadamard(const DevSym &S, const T *WX, const T *WY, int64_t ldw, const int *colw,
+                         const int *vtx, double *B, int64_t ldb, double *hvec, cudaStream_t st) {
+  if (S.m <= 0) return;
+  dim3 grid(std::max(1, std::min(8, (S.m + 1023) / 1024)), std::min(S.m, 65535));
+  k_scm_hadamard<T><<<grid, 256, 0, st>>>(S, WX, WY, ldw, colw, vtx, B, ldb, hvec);
+}
+template void launch_scm_hadamard<double>(const DevSym &, const double *, const double *, int64_t,
+                                          const int *, const int *, double *, int64_t, double *,
+                                          cudaStream_t);
+template void launch_scm_hadamard<float>(const DevSym &, const float *, const float *, int64_t,
+                                         const int *, const int *, double *, int64_t, double *,
+                                         cudaStream_t);
+
 template void launch_scm_tiles<double>(const DevSym &, const int2 *, int, const double *,
                                        const double *, int64_t, const int *, double *, int64_t,
                                        double *, int, cudaStream_t, const int *);

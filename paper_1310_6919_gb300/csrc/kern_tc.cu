@@ -224,14 +224,23 @@ __global__ void __launch_bounds__(128, 1)
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     if (skip || i >= g.M) continue;
+    // the 32 old values first (independent loads in flight), then the updates
+    float old[32];
+    if (g.beta != 0.f) {
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int j = j0 + c0 + q;
+        old[q] = (j < g.N && !(g.lower && i < j))
+                     ? __ldcg(g.C + (int64_t)i * g.cs_i + (int64_t)j * g.cs_j) : 0.f;
+      }
+    }
 #pragma unroll
     for (int q = 0; q < 32; ++q) {
       const int j = j0 + c0 + q;
       if (j >= g.N || (g.lower && i < j)) continue;
-      float *dst = g.C + (int64_t)i * g.cs_i + (int64_t)j * g.cs_j;
       const float a = __uint_as_float(v[q]);
-      const float r = g.beta == 0.f ? g.alpha * a : fmaf(g.alpha, a, g.beta * *dst);
-      *dst = r;
+      const float r = g.beta == 0.f ? g.alpha * a : fmaf(g.alpha, a, g.beta * old[q]);
+      g.C[(int64_t)i * g.cs_i + (int64_t)j * g.cs_j] = r;
       if (g.mirror && i != j) g.C[(int64_t)j * g.cs_i + (int64_t)i * g.cs_j] = r;
     }
   }

@@ -145,7 +145,8 @@ struct mcsdp_ctx {
   // column at colw[k] (R first, the forest from column colF0 = nR rounded up to 32)
   bool dense = false;
   int nR = 0, nF = 0, colF0 = 0, nlev = 0;  // nlev: levels the small-clique kernels walk
-  std::vector<int> colw;
+  std::vector<int> colw, scm_vtx;
+  int *scm_vtx_dev = nullptr;
   std::vector<int64_t> rg_ent, rg_ptr;
   std::vector<int> rg_u, rg_ab;
   RootGather rg{};
@@ -210,7 +211,7 @@ mcsdp_status fail(mcsdp_ctx *c, mcsdp_status s, const std::string &msg) {
 size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
 
 enum KClass { KC_YCHOL = 0, KC_ALG1, KC_PANEL, KC_TILE, KC_CHOL, KC_BSOLVE, KC_PMAT, KC_PSTEP,
-              KC_DSTEP, KC_MISC, KC_PMAT_SIDE, KC_PANEL_SIDE };
+              KC_DSTEP, KC_MISC, KC_PMAT_SIDE, KC_PANEL_SIDE, KC_CHOL32 };
 
 cudaEvent_t ev_get(mcsdp_ctx *c) {
   if (c->evpool.empty()) {
@@ -637,6 +638,14 @@ void plan_workspace(mcsdp_ctx *c) {
     for (int k = 0; k < n; ++k) c->colw[k] = k < c->nF ? c->colF0 + k : k - c->nF;
   }
   plan_table(c, cur, "colw", c->colw);
+  // max-cut-shaped constraints on the dense path: the vertex (new index) of each internal
+  // constraint, for the streamed Hadamard SCM
+  c->scm_vtx.clear();
+  if (c->dense && S.unit_diag_constraints) {
+    c->scm_vtx.resize(m);
+    for (int i = 0; i < m; ++i) c->scm_vtx[i] = S.iperm[S.con_order[i]];
+  }
+  plan_table(c, cur, "scm_vtx", c->scm_vtx);
   plan_table(c, cur, "rowof", c->rowof_all);
   plan_table(c, cur, "goff", c->goff_all);
   plan_table(c, cur, "tkey", c->tkey_all);
@@ -705,7 +714,7 @@ void plan_workspace(mcsdp_ctx *c) {
     plan_buf(c, cur, "lzW", nv * 8);
     plan_buf(c, cur, "lzG", nv * 8);
     plan_buf(c, cur, "lzU", 2 * std::max<size_t>(nv, c->ldw) * 8);
-    plan_buf(c, cur, "lzS", 4 * LZ_MAX * 8);
+    plan_buf(c, cur, "lzS", (4 * LZ_MAX + 8) * 8);
     plan_buf(c, cur, "Xprev", c->dense ? nnzL * 8 : 0);
     // mixed form with a dense root: the TF32 hi / lo parts of the root's product operands (the
     // P-MATRIX's rows of X̂ dY and Y^{-1}, or the inverse factor for Y^{-1}_RR)
@@ -731,8 +740,8 @@ void plan_workspace(mcsdp_ctx *c) {
     plan_buf(c, cur, "ayref", mx ? (size_t)mixed_chunks(m) * m * 8 : 0);
     plan_buf(c, cur, "nref", 4 * 8);
     const bool tc = mx && c->opt.tensor_cores != 0 && m >= 2 * TC_PANEL;
-    plan_buf(c, cur, "tc_hi", tc ? (size_t)TC_PANEL * m * 4 : 0);
-    plan_buf(c, cur, "tc_lo", tc ? (size_t)TC_PANEL * m * 4 : 0);
+    plan_buf(c, cur, "tc_hi", tc ? (size_t)tc_panel(m) * m * 4 : 0);
+    plan_buf(c, cur, "tc_lo", tc ? (size_t)tc_panel(m) * m * 4 : 0);
     plan_buf(c, cur, "L32", mx ? (size_t)nnzL * 4 : 0);
     plan_buf(c, cur, "N32", mx ? (size_t)nnzL * 4 : 0);
     plan_buf(c, cur, "dL32", mx ? (size_t)nnzD * 4 : 0);
@@ -907,6 +916,7 @@ void bind_pointers(mcsdp_ctx *c) {
   c->pm_tkey_dev = wsp<int2>(c, "pm_tkey");
   c->pm_rowof_dev = wsp<int>(c, "pm_rowof");
   c->colw_dev = wsp<int>(c, "colw");
+  c->scm_vtx_dev = c->scm_vtx.empty() ? nullptr : wsp<int>(c, "scm_vtx");
   c->rg.nent = (int64_t)c->rg_ent.size();
   c->rg.ent = wsp<int64_t>(c, "rg_ent");
   c->rg.ptr = wsp<int64_t>(c, "rg_ptr");
@@ -1206,9 +1216,14 @@ mcsdp_status phase_scm_dense(mcsdp_ctx *c) {
     if (r[q] < 0) return fail(c, MCSDP_ERR_ARG, "solve shape not supported in this precision");
   KCHECK(c);
   KScope k2(c, KC_TILE);
-  const Chunk &ch = c->chunks[0];
-  launch_scm_tiles(c->D, c->tiles_dev + ch.tile_begin, ch.ntiles, (const T *)W1, (const T *)W2,
-                   ldw, c->goff_dev, c->B, c->ldb, c->hvec, c->pmax, c->stream, c->colw_dev);
+  if (c->scm_vtx_dev) {
+    launch_scm_hadamard<T>(c->D, W1, W2, ldw, c->colw_dev, c->scm_vtx_dev, c->B, c->ldb, c->hvec,
+                           c->stream);
+  } else {
+    const Chunk &ch = c->chunks[0];
+    launch_scm_tiles(c->D, c->tiles_dev + ch.tile_begin, ch.ntiles, (const T *)W1, (const T *)W2,
+                     ldw, c->goff_dev, c->B, c->ldb, c->hvec, c->pmax, c->stream, c->colw_dev);
+  }
   k2.done(1);
   KCHECK(c);
   return MCSDP_OK;
@@ -1287,7 +1302,11 @@ mcsdp_status phase_pmatrix_dense(mcsdp_ctx *c, double betamu, const double *Xbar
   T *M = reinterpret_cast<T *>(c->RS_M);
   KScope k1(c, KC_PMAT);
   CUDA_TRY(c, cudaMemsetAsync(V, 0, (size_t)n * ldw * sizeof(T), c->stream));
-  launch_times_pattern<T>(c->D, c->dY, W1, V, ldw, c->colw_dev, c->stream);
+  if (c->S.diag_constraints)  // dY = -sum dz_k A_k is diagonal: V = X̂ dY scales columns
+    launch_times_diag<T>(c->D, c->dY, W1, V, ldw, c->colw_dev, reinterpret_cast<T *>(c->lzU),
+                         c->stream);
+  else
+    launch_times_pattern<T>(c->D, c->dY, W1, V, ldw, c->colw_dev, c->stream);
   if constexpr (std::is_same<T, float>::value) {
     if (c->tcr)
       root_tc_gemm(c, V + (size_t)nF * ldw, ldw, 1, nR, W2 + (size_t)nF * ldw, ldw, 1, nR, (int)ldw,
@@ -1480,7 +1499,7 @@ mcsdp_status lanczos_min(mcsdp_ctx *c, int dim, Op op, Gm gmul, bool has_g, doub
     double *vj = Q + (size_t)j * dim, *gvj = GQ + (size_t)j * dim;
     op(vj, w);
     lz_alpha(dim, w, gvj, vj, j > 0 ? vj - dim : nullptr, c->lzS, j, st);
-    lz_reorth(dim, j + 1, w, GQ, Q, st);
+    lz_reorth(dim, j + 1, w, GQ, Q, c->lzS + 2 * LZ_MAX + 2, st);
     if (has_g) gmul(w, gw);
     lz_beta(dim, w, gw, vj + dim, has_g ? gvj + dim : nullptr, c->lzS, j, st);
     k = j + 1;
@@ -1586,7 +1605,7 @@ mcsdp_status mixed_sce(mcsdp_ctx *c, bool b32, bool *solved) {
   *solved = false;
   CUDA_TRY(c, cudaMemsetAsync(c->status + 4, 0, sizeof(int), c->stream));
   {
-    KScope k1(c, KC_CHOL);
+    KScope k1(c, KC_CHOL32);
     k1.done(mixed_factor(c->B, c->ldb, m, c->B32, c->Linv32, c->status + 4, c->gref, c->rref,
                          c->xs, c->stream, &c->cs));
   }

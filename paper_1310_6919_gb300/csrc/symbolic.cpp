@@ -631,6 +631,7 @@ std::string analyze(const ProblemData &P, const SymbolicOptions &o, Symbolic &S)
   {
     std::vector<std::vector<int>> supp(m);
     S.unit_diag_constraints = true;
+    S.diag_constraints = true;
     for (size_t t = 0; t < P.row.size(); ++t) {
       if (P.mat[t] == 0) continue;
       int k = P.mat[t] - 1;
@@ -643,6 +644,7 @@ std::string analyze(const ProblemData &P, const SymbolicOptions &o, Symbolic &S)
       int k = P.mat[t] - 1;
       cnt_entries[k]++;
       if (P.row[t] != P.col[t] || P.row[t] != k || P.val[t] != 1.0) S.unit_diag_constraints = false;
+      if (P.row[t] != P.col[t]) S.diag_constraints = false;
     }
     for (int k = 0; k < m; ++k) {
       if (cnt_entries[k] != 1) S.unit_diag_constraints = false;

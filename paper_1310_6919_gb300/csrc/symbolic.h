@@ -80,6 +80,7 @@ struct Symbolic {
   std::vector<int> reach_sn, need_sn;
   // max-cut shaped (every A_k = e_k e_k^T with value 1): used for the default dual start
   bool unit_diag_constraints = false;
+  bool diag_constraints = false;  // every A_k (k >= 1) is diagonal
   // the last supernode is the dense root (cliques beyond the small-clique limits merged into it)
   bool dense_root = false;
   bool a0_diag_dominant_start_ok = false;

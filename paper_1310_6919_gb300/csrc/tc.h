@@ -31,8 +31,12 @@ void gemm_3xtf32(const TcOperand &A, const TcOperand &B, int M, int N, int K, fl
                  int64_t cs_i, int64_t cs_j, float alpha, float beta, bool lower, bool mirror,
                  int *err, cudaStream_t st);
 
-// working storage of the tensor-core Cholesky: the split panel (TC_PANEL x rows, hi and lo)
-constexpr int TC_PANEL = 256;
+// working storage of the tensor-core Cholesky: the split panel (tc_panel(m) x rows, hi and lo);
+// wide panels for large m keep the trailing products' K long (their epilogue read-modify-write
+// of C is then amortised over more MMAs), narrow ones keep small factorisations on the tensor
+// cores at all
+constexpr int TC_PANEL = 256, TC_PANEL_WIDE = 1024;
+inline int tc_panel(int m) { return m >= 8 * TC_PANEL_WIDE ? TC_PANEL_WIDE : TC_PANEL; }
 struct TcWork {
   float *hi = nullptr, *lo = nullptr;
   int rows = 0;  // capacity in rows
