@@ -225,9 +225,10 @@ mcsdp_status mcsdp_factors(mcsdp_ctx *ctx, const double *Xbar_layout_dev, const 
  * Y^{-1} columns on a side stream (single column block: they run beside the SCM solves; their
  * flops are counted in class 6), 11 the SCM's N solves on a side stream (beside the L̂ solves of
  * class 2; their flops are counted in class 2), 12 the mixed form's FP32 SCM Cholesky (tensor
- * cores for m >= 512; its work is class 4's).  Classes 1, 7, 10 and 11 run on side streams
+ * cores for m >= 512; its work is class 4's), 13 the dense root's FP64 P-MATRIX GEMM
+ * X̂_RR T (its flops are counted in class 6).  Classes 1, 7, 10 and 11 run on side streams
  * (class 1 beside class 0), so their times overlap the others'. */
-#define MCSDP_NCLASS 13
+#define MCSDP_NCLASS 14
 typedef struct {
   int64_t launches;
   int64_t count[16];   /* launches per class */
@@ -316,9 +317,11 @@ mcsdp_status mcsdp_gemm_tc(int32_t M, int32_t N, int32_t K, const float *A, int6
 /* Differentiation of the solution (not in the paper).  The point differentiated is the
  * central-path point for mu = X̄.Y/n of the context's iterate: the iterate is first re-centred
  * (Newton on z for A(mu Y(z)^{-1}) = b with Y(z) = A_0 - sum z_k A_k, until the residual
- * max|A(X) - b| / max(1, max|b|) is at most 1e-13, or, once a Newton step no longer halves it,
- * is at most 1e-9 (the rounding level of its evaluation for an ill-conditioned Y); the context's
- * iterate becomes that point, X̄ = mu Y^{-1} on E).  For the loss
+ * max|A(X) - b| / max(1, max|b|) is at most 1e-13, or, once full Newton steps no longer halve
+ * it, is at the rounding level of its evaluation: at most 1e-9 after one such step, or at most
+ * 64 eps cond(Y) after three, cond(Y) estimated from below by (max_j N_jj / min_j N_jj)^2 (near
+ * the optimum cond(Y) grows like 1/mu, and the point, hence the gradients, carry that rounding);
+ * the context's iterate becomes that point, X̄ = mu Y^{-1} on E).  For the loss
  * l = sum over layout entries gX . X̄ + gz^T z, implicit differentiation of A(X) = b,
  * X = mu Y^{-1} gives, with R = sym(X̂ G Y^{-1}) (G the symmetric matrix of the weights gX),
  * v = B^{-1}(A(R) + gz) (B the SCM at the point), g_{A_0} = sym(X̂ (A^*(v) - G) Y^{-1}):

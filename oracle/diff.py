@@ -13,11 +13,13 @@ centring step of the method.  For a loss  l = <G, X> + g_z^T z  (G symmetric) th
     g_b = v,   g_{A_0} = sym(X (A^*(v) - G) Y^{-1}),   g_{A_k} = -z_k g_{A_0} - v_k X,
 
 (sym(M) = (M + M^T)/2, A^*(v) = sum_k v_k A_k), obtained by differentiating F(z; b, A_0, A_k) = 0
-and X = mu Y^{-1}.  Plain dense FP64, slow, for small instances.
+and X = mu Y^{-1}.  Plain dense FP64; B is formed row by row from the nonzeros of the A_k
+(oracle.scm.scm_sparse_rows, pinned against the definition scm_dense), so instances up to
+n = m = 1000 or so take seconds per Newton step.
 """
 import numpy as np
 
-from .scm import scm_dense
+from .scm import scm_sparse_rows
 from .sdp import dual_slack
 
 
@@ -30,7 +32,8 @@ def central_point(A, b, mu, z0, tol=1e-13, max_newton=60):
     Y stays positive definite, until max|F| <= tol max(1, max|b|).  If Newton stops gaining
     (three full steps in a row that do not halve the residual) the point is accepted only when the
     residual is at the rounding level of evaluating F, rho = 64 eps cond(Y) max_k |A_k|.|X| /
-    max(1, max|b|) (Y^{-1} is formed with relative error about eps cond(Y)); otherwise it raises.
+    max(1, max|b|) (Y^{-1} is formed with relative error about eps cond(Y)); above it Newton goes
+    on, and it raises after max_newton steps.
     Returns z, Y, X = mu Y^{-1} and the relative residual reached."""
     z = np.array(z0, dtype=np.float64)
     scale = max(1.0, float(np.max(np.abs(b))))
@@ -59,8 +62,10 @@ def central_point(A, b, mu, z0, tol=1e-13, max_newton=60):
             rho = 64.0 * eps * np.linalg.cond(Y) * max(1.0, float(np.max(absAX))) / scale
             if res <= rho:
                 return z, Y, X, res
-            raise RuntimeError("centring stalled above the rounding level")
-        Bm = scm_dense(A, X, Yinv)
+            # above the rounding level slow full steps are Newton's global phase (a start far
+            # from the central point), not a floor: keep iterating
+            stalled = 0
+        Bm = scm_sparse_rows(A, X, Yinv)
         dz = np.linalg.solve(Bm, -F)
         t = 1.0
         while True:
@@ -76,16 +81,18 @@ def central_point(A, b, mu, z0, tol=1e-13, max_newton=60):
     raise RuntimeError("centring did not converge")
 
 
-def backward(A, z, Y, X, G, gz):
+def backward(A, z, Y, X, G, gz, with_gA=True):
     """Gradients of l = <G, X> + gz^T z at the central point (z, Y, X): returns (g_b, g_{A_0},
     g_A) with g_A[k-1] the dense gradient with respect to A_k (symmetric matrices; the gradient
-    with respect to a stored off-diagonal entry that also sets its mirror is twice the entry)."""
+    with respect to a stored off-diagonal entry that also sets its mirror is twice the entry).
+    with_gA=False returns None for g_A (m dense n x n matrices; entry_gradients needs only
+    g_b, g_{A_0} and X)."""
     Yinv = _sym(np.linalg.inv(Y))
     R = _sym(X @ G @ Yinv)
-    Bm = scm_dense(A, X, Yinv)
+    Bm = scm_sparse_rows(A, X, Yinv)
     v = np.linalg.solve(Bm, A.op(R) + gz)
     gA0 = _sym(X @ (A.adjoint(v) - G) @ Yinv)
-    gA = [-z[k] * gA0 - v[k] * X for k in range(A.m)]
+    gA = [-z[k] * gA0 - v[k] * X for k in range(A.m)] if with_gA else None
     return v, gA0, gA
 
 

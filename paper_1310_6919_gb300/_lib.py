@@ -32,7 +32,8 @@ class Stats_t(C.Structure):
 
 
 KCLASS = ["ychol", "alg1", "scm_panel", "scm_tile", "scm_chol", "sce_backsolve", "pmatrix",
-          "primal_step", "dual_step", "other", "pmatrix_side", "scm_panel_side", "scm_chol32"]
+          "primal_step", "dual_step", "other", "pmatrix_side", "scm_panel_side", "scm_chol32",
+          "root_gemm"]
 
 
 class SymInfo_t(C.Structure):

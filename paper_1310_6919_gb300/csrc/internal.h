@@ -294,6 +294,15 @@ void launch_forest_M(const DevSym &S, const T *V, const T *Wy, int64_t ldw, int 
                      double *Mlow, double *Mup, cudaStream_t st);
 template <class T>
 void launch_root_M(const T *M, int nR, double *Mlow_root, double *Mup_root, cudaStream_t st);
+// out[0] = max_j |L_jj|, out[1] = min_j |L_jj| over the layout's diagonal (device doubles)
+void launch_diag_range(const DevSym &S, const double *L, double *out, cudaStream_t st);
+// the root block's P-MATRIX factor T = U_RR - L_RF Z, written transposed (Tt[j nR + r] = T_rj):
+// U = rows of W (root columns [0, nR)) holding dY Y^{-1}[:, R], its forest rows already replaced by
+// Z = L_FF^{-1} U_F; L_RF by root row r in CSR form (ptr[r] .. ptr[r + 1]: layout offset of the
+// entry of L in off, its forest row in frow)
+template <class T>
+void launch_root_pull(const int64_t *ptr, const int64_t *off, const int *frow, const T *L,
+                      const T *U, int64_t ldw, int nF, int nR, T *Tt, cudaStream_t st);
 void launch_root_dx(int nR, double betamu, const double *X, const double *YinvE, const double *Mlow,
                     const double *Mup, double *dX, cudaStream_t st);
 // mirror the strict lower triangle of a column-major square into its strict upper triangle
@@ -375,10 +384,11 @@ int mixed_factor(double *B, int64_t ldb, int m, float *B32, float *Linv32, int *
 // number of column chunks of the refinement's matrix-vector product (P, A hold chunks x m)
 int mixed_chunks(int m);
 // one refinement step: x += (L32 L32^T)^{-1} r, then r = g - B x (FP64) and
-// norms = (max|r|, max(|B||x| + |g|))
+// norms = (max|r|, max(|B||x| + |g|)); status gets ST_TIMEOUT if a bounded wait of the wide
+// substitutions (m >= 4096) ran out
 int mixed_refine_step(const double *B, int64_t ldb, int m, const float *L32, const float *Linv32,
                       const double *g, double *x, double *r, double *P, double *A, double *norms,
-                      cudaStream_t st);
+                      int *status, cudaStream_t st);
 void launch_rhs_border(const DevSym &S, double *B, int64_t ldb, const double *hvec, double betamu,
                        cudaStream_t st);
 void launch_dz_to_user(const DevSym &S, const double *dz_int, double *dz_user, cudaStream_t st);

@@ -808,14 +808,47 @@ static void atomic_status_host_fail(int *status, cudaStream_t st) {
 // below the panel split into TF32 hi / lo K-major copies (and written transposed above the
 // diagonal, where the refinement's substitutions read L^T), then the trailing lower triangle
 // updated by the tcgen05 product C -= P P^T with K = the panel width.
+// One panel of the tensor-core Cholesky: the leading pw columns of the rows x pw block Bp, in
+// sub-panels of TC_SUB columns: each factored by the 32-column kernels (its rows below solved),
+// the panel's columns right of it then updated on the tensor cores (C -= L_s L_s^T over the rows
+// from the next sub-panel down, K = TC_SUB), so the 32-column kernels' FFMA updates stay inside a
+// sub-panel.  The sub-panel's split also writes its rows transposed above the diagonal.
+static int panel_chol_tc(float *Bp, int64_t ldb, int pw, int rows, int *status, float *Linv,
+                         cudaStream_t st, const CholStreams *cs) {
+  constexpr int TC_SUB = 128;
+  int nl = 0;
+  for (int s0 = 0; s0 < pw; s0 += TC_SUB) {
+    const int sw = std::min(TC_SUB, pw - s0);
+    nl += dense_chol<float>(Bp + s0 + (int64_t)s0 * ldb, ldb, sw, rows - s0, status,
+                            Linv + (int64_t)(s0 / NB) * NB * NB, st, nullptr);
+    const int r0 = s0 + sw;
+    if (r0 >= pw) break;
+    split_tf32(Bp + r0 + (int64_t)s0 * ldb, 1, ldb, rows - r0, sw, cs->tc_hi, cs->tc_lo, TC_SUB,
+               Bp + s0 + (int64_t)r0 * ldb, ldb, st);
+    TcOperand Oa, Ob;
+    Oa.x = Oa.y = Ob.x = Ob.y = 0;
+    if (!make_tmap_kmajor(&Oa.hi, cs->tc_hi, TC_SUB, sw, rows - r0) ||
+        !make_tmap_kmajor(&Oa.lo, cs->tc_lo, TC_SUB, sw, rows - r0) ||
+        !make_tmap_kmajor(&Ob.hi, cs->tc_hi, TC_SUB, sw, pw - r0) ||
+        !make_tmap_kmajor(&Ob.lo, cs->tc_lo, TC_SUB, sw, pw - r0)) {
+      atomic_status_host_fail(status, st);
+      return nl;
+    }
+    gemm_3xtf32(Oa, Ob, rows - r0, pw - r0, sw, Bp + r0 + (int64_t)r0 * ldb, 1, ldb, -1.f, 1.f,
+                true, false, cs->tc_err ? cs->tc_err : status, st);
+    nl += 2;
+  }
+  return nl;
+}
+
 static int dense_chol_f32_tc(float *B, int64_t ldb, int m, int *status, float *Linv_all,
                              cudaStream_t st, const CholStreams *cs) {
   int nl = 0;
   const int P = tc_panel(m);
   for (int k0 = 0; k0 < m; k0 += P) {
     const int pw = std::min(P, m - k0);
-    nl += dense_chol<float>(B + k0 + (int64_t)k0 * ldb, ldb, pw, m - k0, status,
-                            Linv_all + (int64_t)(k0 / NB) * NB * NB, st, nullptr);
+    nl += panel_chol_tc(B + k0 + (int64_t)k0 * ldb, ldb, pw, m - k0, status,
+                        Linv_all + (int64_t)(k0 / NB) * NB * NB, st, cs);
     const int r0 = k0 + pw;
     if (r0 >= m) break;
     split_tf32(B + r0 + (int64_t)k0 * ldb, 1, ldb, m - r0, pw, cs->tc_hi, cs->tc_lo, P,
@@ -1340,6 +1373,102 @@ __global__ void __cluster_dims__(RCL, 1, 1) __launch_bounds__(RTH)
   cl.sync();  // no CTA leaves while another may still write into its shared memory
 }
 
+// The refinement's substitutions for large m, over all SMs: x += L^{-T} L^{-1} r (FP32 factor, ld
+// m, L^T in the strict upper triangle; FP64 r and x).  One CTA per row block of NB rows, in
+// ticket order (an atomic counter: every block a CTA waits on belongs to a CTA that started
+// before it, so the waits end whatever the residency).  Block i: each warp takes the earlier
+// blocks q = w, w + 8, ... (lane = row of block i), loads the NB factor entries of (i, q) before
+// it waits for q's flag, then adds their products with the published y_q; the warps' sums are
+// combined, the diagonal block's inverse applied, y_i published (fence, then the flag).  The
+// backward pass runs the blocks from the last with L^T (read from the upper triangle: the same
+// coalesced row segments).  Every wait is bounded (thread 0 of the warp polls; past the limit the
+// status gets ST_TIMEOUT and the abort word ends every wait; the results are then garbage, the
+// kernels still finish).
+constexpr int TW_WARPS = 8;
+constexpr int TRSV_WIDE_M = 4096;  // from here on the solves run over all SMs
+constexpr int64_t TW_SPIN_LIMIT = 1 << 22;
+
+struct TrsvWork {
+  float *y;      // m
+  int *flag;     // 2 x nblk: forward, backward
+  int *ticket;   // 2
+  int *abort;    // 1
+};
+
+__device__ __forceinline__ bool tw_wait(const int *flag, int *abort, int *status) {
+  unsigned ns = 32;
+  for (int64_t it = 0;; ++it) {
+    if (ld_acquire(flag)) return true;
+    if (ld_acquire(abort)) return false;
+    if (it >= TW_SPIN_LIMIT) break;
+    __nanosleep(ns);
+    if (ns < 256) ns <<= 1;
+  }
+  atomicExch(abort, 1);
+  atomicOr(status, ST_TIMEOUT);
+  return false;
+}
+
+template <bool FWD>
+__global__ void __launch_bounds__(TW_WARPS * 32)
+    k_trsv_wide_f32(const float *__restrict__ L, int m, const float *__restrict__ Linv,
+                    const double *__restrict__ r, double *x, TrsvWork w, int *status) {
+  __shared__ float red[TW_WARPS][NB + 1];
+  __shared__ int s_blk;
+  const int nblk = (m + NB - 1) / NB;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    const int t = atomicAdd(w.ticket + (FWD ? 0 : 1), 1);
+    s_blk = FWD ? t : nblk - 1 - t;
+  }
+  __syncthreads();
+  const int i = s_blk;
+  const int b0 = i * NB, row = b0 + lane;
+  const bool valid = row < m;
+  int *flags = w.flag + (FWD ? 0 : nblk);
+  float acc = 0.f;
+  // blocks this warp takes: forward q < i, backward q > i
+  const int q0 = FWD ? wp : i + 1 + wp, q1 = FWD ? i : nblk;
+  for (int q = q0; q < q1; q += TW_WARPS) {
+    const int c0 = q * NB, nc = min(NB, m - c0);
+    float lv[NB];
+    // row `row` of block (i, q): L[row][c0 + c] (forward, below the diagonal) or
+    // L^T[row][c0 + c] = L[c0 + c][row], held at [row + (c0 + c) m] above the diagonal
+#pragma unroll
+    for (int c = 0; c < NB; ++c) lv[c] = (valid && c < nc) ? L[row + (int64_t)(c0 + c) * m] : 0.f;
+    // (after an abort the values read are garbage; the kernel still runs to its end)
+    if (lane == 0) tw_wait(flags + q, w.abort, status);
+    __syncwarp();
+    // y_q: the forward result, overwritten by block q's backward result once it is published
+    const float yq = lane < nc ? __ldcg(w.y + c0 + lane) : 0.f;
+#pragma unroll
+    for (int c = 0; c < NB; ++c) acc = fmaf(lv[c], __shfl_sync(0xffffffffu, yq, c), acc);
+  }
+  red[wp][lane] = acc;
+  __syncthreads();
+  if (wp == 0) {
+    float a = 0.f;
+#pragma unroll
+    for (int q = 0; q < TW_WARPS; ++q) a += red[q][lane];
+    const float rhs = valid ? (FWD ? (float)r[row] : __ldcg(w.y + row)) - a : 0.f;
+    // diagonal block: y_i = Linv_ii rhs (forward), x_i = Linv_ii^T rhs (backward)
+    const float *Li = Linv + (int64_t)i * NB * NB;
+    float v = 0.f;
+#pragma unroll
+    for (int l = 0; l < NB; ++l) {
+      const float rl = __shfl_sync(0xffffffffu, rhs, l);
+      v = fmaf(FWD ? Li[lane + l * NB] : Li[l + lane * NB], rl, v);
+    }
+    if (valid) {
+      w.y[row] = v;
+      if (!FWD) x[row] = x[row] + (double)v;
+    }
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) atomicExch(flags + i, 1);
+  }
+}
+
 // Partial products of y = B x with the full symmetric FP64 B (column-major): CTA (row block of
 // 32, column chunk J of MV_CHUNK columns), 256 threads = 32 rows x 8 column phases; writes
 // P[J][i] = sum_{j in J} B_ij x_j and A[J][i] = sum_{j in J} |B_ij x_j|.
@@ -1441,14 +1570,29 @@ int mixed_factor(double *B, int64_t ldb, int m, float *B32, float *Linv32, int *
 
 int mixed_refine_step(const double *B, int64_t ldb, int m, const float *L32, const float *Linv32,
                       const double *g, double *x, double *r, double *P, double *A, double *norms,
-                      cudaStream_t st) {
-  const size_t smem = (size_t)m * sizeof(float);
-  if (smem > 48 * 1024) smem_optin((const void *)k_refine_solve_f32);
-  k_refine_solve_f32<<<RCL, RTH, smem, st>>>(L32, m, Linv32, r, x);
+                      int *status, cudaStream_t st) {
+  int nl = 3;
+  if (m >= TRSV_WIDE_M) {
+    // P (chunks x m doubles) is free until the product below: y, then the flags and tickets
+    const int nblk = (m + NB - 1) / NB;
+    TrsvWork w;
+    w.y = reinterpret_cast<float *>(P);
+    w.flag = reinterpret_cast<int *>(w.y + ((m + 63) / 64) * 64);
+    w.ticket = w.flag + 2 * nblk;
+    w.abort = w.ticket + 2;
+    cudaMemsetAsync(w.flag, 0, (2 * (size_t)nblk + 4) * sizeof(int), st);
+    k_trsv_wide_f32<true><<<nblk, TW_WARPS * 32, 0, st>>>(L32, m, Linv32, r, x, w, status);
+    k_trsv_wide_f32<false><<<nblk, TW_WARPS * 32, 0, st>>>(L32, m, Linv32, r, x, w, status);
+    ++nl;
+  } else {
+    const size_t smem = (size_t)m * sizeof(float);
+    if (smem > 48 * 1024) smem_optin((const void *)k_refine_solve_f32);
+    k_refine_solve_f32<<<RCL, RTH, smem, st>>>(L32, m, Linv32, r, x);
+  }
   const int nch = mixed_chunks(m);
   k_gemv_part<<<dim3((m + 31) / 32, nch), 256, 0, st>>>(B, ldb, m, x, P, A);
   k_resid<<<1, 1024, 0, st>>>(g, P, A, nch, r, m, norms);
-  return 3;
+  return nl;
 }
 
 // ---------------------------------------------------------------------------------------------

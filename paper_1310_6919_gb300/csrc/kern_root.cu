@@ -732,6 +732,92 @@ __global__ void k_root_dx(int nR, double betamu, const double *__restrict__ X,
   }
 }
 
+// Root block of the P-MATRIX: with X̂_FR = -L_FF^{-T} L_RF^T X̂_RR (the completion's forest
+// rows of the root columns, X̂^{-1} = L̂ L̂^T), (X̂ U)_RR = X̂_RR U_RR + X̂_RF U_FR
+// = X̂_RR (U_RR - L_RF L_FF^{-1} U_F) for any U.  One CTA per tile of 32 root rows x 32 columns:
+// a warp takes a root row at a time, lane = column, the row's L_RF entries broadcast; the tile
+// is transposed through shared memory.  Column tiles vary slowest across the grid, so the CTAs
+// resident together read one 32-column slice of Z (n_F x 32 values), which stays in L2.
+template <class T>
+__global__ void __launch_bounds__(256) k_root_pull(const int64_t *__restrict__ ptr,
+                                                   const int64_t *__restrict__ off,
+                                                   const int *__restrict__ frow,
+                                                   const T *__restrict__ L,
+                                                   const T *__restrict__ U, int64_t ldw, int nF,
+                                                   int nR, T *Tt) {
+  __shared__ T tile[32][33];
+  const int r0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int j = j0 + lane;
+  for (int rr = w; rr < 32; rr += 8) {
+    const int r = r0 + rr;
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+    if (r < nR && j < nR) {
+      a0 = U[(int64_t)(nF + r) * ldw + j];
+      int64_t e = ptr[r];
+      const int64_t e1 = ptr[r + 1];
+      for (; e + 4 <= e1; e += 4) {  // four independent chains
+        a0 = fma(-L[off[e]], U[(int64_t)frow[e] * ldw + j], a0);
+        a1 = fma(-L[off[e + 1]], U[(int64_t)frow[e + 1] * ldw + j], a1);
+        a2 = fma(-L[off[e + 2]], U[(int64_t)frow[e + 2] * ldw + j], a2);
+        a3 = fma(-L[off[e + 3]], U[(int64_t)frow[e + 3] * ldw + j], a3);
+      }
+      for (; e < e1; ++e) a0 = fma(-L[off[e]], U[(int64_t)frow[e] * ldw + j], a0);
+    }
+    tile[rr][lane] = (a0 + a1) + (a2 + a3);
+  }
+  __syncthreads();
+  for (int jj = w; jj < 32; jj += 8) {
+    const int jo = j0 + jj, r = r0 + lane;
+    if (jo < nR && r < nR) Tt[(int64_t)jo * nR + r] = tile[lane][jj];
+  }
+}
+
+template <class T>
+void launch_root_pull(const int64_t *ptr, const int64_t *off, const int *frow, const T *L,
+                      const T *U, int64_t ldw, int nF, int nR, T *Tt, cudaStream_t st) {
+  if (nR <= 0) return;
+  dim3 grid((nR + 31) / 32, (nR + 31) / 32);
+  k_root_pull<T><<<grid, 256, 0, st>>>(ptr, off, frow, L, U, ldw, nF, nR, Tt);
+}
+
+// range of the pivots of a Cholesky factor in the layout: out[0] = max_j |L_jj|, out[1] =
+// min_j |L_jj| (one CTA; (max/min)^2 is a lower bound on the condition number of L L^T)
+__global__ void k_diag_range(DevSym S, const double *__restrict__ L, double *out) {
+  __shared__ double smax[32], smin[32];
+  double mx = 0.0, mn = 1.0e300;
+  for (int j = threadIdx.x; j < S.n; j += blockDim.x) {
+    const int t = S.col2sn[j];
+    const int64_t nrow = S.sn_rowptr[t + 1] - S.sn_rowptr[t];
+    const int lc = j - S.sn_col[t];
+    const double v = fabs(L[S.sn_valptr[t] + lc + (int64_t)lc * nrow]);
+    mx = fmax(mx, v);
+    mn = fmin(mn, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    smax[w] = mx;
+    smin[w] = mn;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+      mx = fmax(mx, smax[q]);
+      mn = fmin(mn, smin[q]);
+    }
+    out[0] = mx;
+    out[1] = mn;
+  }
+}
+
+void launch_diag_range(const DevSym &S, const double *L, double *out, cudaStream_t st) {
+  k_diag_range<<<1, 1024, 0, st>>>(S, L, out);
+}
+
 template <class T>
 void launch_unit_cols(T *W, int64_t ldw, const int *colw, int k0, int nk, cudaStream_t st) {
   if (nk > 0) k_unit_cols<T><<<(nk + 255) / 256, 256, 0, st>>>(W, ldw, colw, k0, nk);
@@ -878,6 +964,8 @@ void permute_to_cols(const double *src, const int *colw, double *dst, int n, cud
   template void launch_forest_M<T>(const DevSym &, const T *, const T *, int64_t, int, double *,  \
                                    double *, cudaStream_t);                                      \
   template void launch_root_M<T>(const T *, int, double *, double *, cudaStream_t);        \
+  template void launch_root_pull<T>(const int64_t *, const int64_t *, const int *, const T *,     \
+                                    const T *, int64_t, int, int, T *, cudaStream_t);          \
   template void mirror_lower<T>(T *, int64_t, int, cudaStream_t);
 MCSDP_ROOT_INST(double)
 MCSDP_ROOT_INST(float)

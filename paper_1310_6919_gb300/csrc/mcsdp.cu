@@ -150,6 +150,11 @@ struct mcsdp_ctx {
   std::vector<int64_t> rg_ent, rg_ptr;
   std::vector<int> rg_u, rg_ab;
   RootGather rg{};
+  // the forest-to-root block L_RF of L̂ (and of N) by root row, for the root's P-MATRIX
+  std::vector<int64_t> lrf_ptr, lrf_off;
+  std::vector<int> lrf_row;
+  const int64_t *lrf_ptr_dev = nullptr, *lrf_off_dev = nullptr;
+  const int *lrf_row_dev = nullptr;
   int *colw_dev = nullptr;
   double *RS_X = nullptr, *RS_P = nullptr, *RS_T = nullptr, *RS_M = nullptr;
   double *rLinvN = nullptr, *rLinvX = nullptr, *rLinv2 = nullptr;
@@ -211,7 +216,7 @@ mcsdp_status fail(mcsdp_ctx *c, mcsdp_status s, const std::string &msg) {
 size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
 
 enum KClass { KC_YCHOL = 0, KC_ALG1, KC_PANEL, KC_TILE, KC_CHOL, KC_BSOLVE, KC_PMAT, KC_PSTEP,
-              KC_DSTEP, KC_MISC, KC_PMAT_SIDE, KC_PANEL_SIDE, KC_CHOL32 };
+              KC_DSTEP, KC_MISC, KC_PMAT_SIDE, KC_PANEL_SIDE, KC_CHOL32, KC_RGEMM };
 
 cudaEvent_t ev_get(mcsdp_ctx *c) {
   if (c->evpool.empty()) {
@@ -470,6 +475,40 @@ void plan_workspace(mcsdp_ctx *c) {
       }
     }
   }
+  // L_RF by root row: for every update u of the root from forest supernode d (rows p1 .. p2 of
+  // d, at root rows rel[]), the entries L_d[p, q] of d's columns q, in (u, q) order per row
+  c->lrf_ptr.assign(1, 0);
+  c->lrf_off.clear();
+  c->lrf_row.clear();
+  if (c->dense) {
+    const int rt = S.ns - 1, nR = c->nR;
+    std::vector<int64_t> cnt(nR + 1, 0);
+    for (int u = S.upd_ptr[rt]; u < S.upd_ptr[rt + 1]; ++u) {
+      const int d = S.upd_src[u], ncd = S.sn_col[d + 1] - S.sn_col[d];
+      const int *rel = S.upd_rel.data() + S.upd_relptr[u];
+      for (int p = 0; p < S.upd_p2[u] - S.upd_p1[u]; ++p) cnt[rel[p] + 1] += ncd;
+    }
+    for (int r = 0; r < nR; ++r) cnt[r + 1] += cnt[r];
+    c->lrf_off.resize((size_t)cnt[nR]);
+    c->lrf_row.resize((size_t)cnt[nR]);
+    std::vector<int64_t> at(cnt.begin(), cnt.end() - 1);
+    for (int u = S.upd_ptr[rt]; u < S.upd_ptr[rt + 1]; ++u) {
+      const int d = S.upd_src[u], c0 = S.sn_col[d], ncd = S.sn_col[d + 1] - c0;
+      const int64_t nrd = S.sn_rowptr[d + 1] - S.sn_rowptr[d];
+      const int *rel = S.upd_rel.data() + S.upd_relptr[u];
+      for (int p = S.upd_p1[u]; p < S.upd_p2[u]; ++p) {
+        const int r = rel[p - S.upd_p1[u]];
+        for (int q = 0; q < ncd; ++q) {
+          c->lrf_off[at[r]] = S.sn_valptr[d] + p + (int64_t)q * nrd;
+          c->lrf_row[at[r]++] = c0 + q;
+        }
+      }
+    }
+    c->lrf_ptr = cnt;
+  }
+  plan_table(c, cur, "lrf_ptr", c->lrf_ptr);
+  plan_table(c, cur, "lrf_off", c->lrf_off);
+  plan_table(c, cur, "lrf_row", c->lrf_row);
   plan_table(c, cur, "rg_ent", c->rg_ent);
   plan_table(c, cur, "rg_ptr", c->rg_ptr);
   plan_table(c, cur, "rg_u", c->rg_u);
@@ -922,6 +961,9 @@ void bind_pointers(mcsdp_ctx *c) {
   c->rg.ptr = wsp<int64_t>(c, "rg_ptr");
   c->rg.u = wsp<int>(c, "rg_u");
   c->rg.ab = wsp<int>(c, "rg_ab");
+  c->lrf_ptr_dev = wsp<int64_t>(c, "lrf_ptr");
+  c->lrf_off_dev = wsp<int64_t>(c, "lrf_off");
+  c->lrf_row_dev = wsp<int>(c, "lrf_row");
   c->RS_X = wsp<double>(c, "RS_X");
   c->RS_P = wsp<double>(c, "RS_P");
   c->RS_T = wsp<double>(c, "RS_T");
@@ -1289,10 +1331,13 @@ mcsdp_status phase_scm(mcsdp_ctx *c) {
 }
 
 // P-MATRIX (eq. newdX2) with a dense root, from the dense X̂ (W1) and Y^{-1} (W2) of the SCM
-// phase: V = X̂ dY (W3, rows of X̂ times the aggregate-pattern dY), M = X̂ dY Y^{-1} at (r, k) is
-// the dot product of row r of V with row k of Y^{-1} (Y^{-1} symmetric): on the root block one
-// GEMM M_RR = V_R Y^{-1}_R^T into RS_M, on the forest's entries of E the dot products of the
-// clique rows (Mlow at (r, k) and, transposed, Mup); Y^{-1} on E read from W2.  Then dX on E.
+// phase.  Forest entries of E: V = X̂ dY (W3, rows of X̂ times the aggregate-pattern dY), and
+// M = X̂ dY Y^{-1} at (r, k) is the dot product of row r of V with row k of Y^{-1} (Mlow at (r, k)
+// and, transposed, Mup); Y^{-1} on E read from W2.  Root block: with U = dY Y^{-1}[:, R] (W3 again)
+// and the completion's X̂_FR = -L_FF^{-T} L_RF^T X̂_RR, M_RR = X̂_RR (U_RR - L_RF L_FF^{-1} U_F):
+// a forward solve over the forest (n_R right-hand sides), the sparse L_RF product, and one
+// n_R x n_R x n_R GEMM, where the product over all n columns, X̂_R dY Y^{-1}_{:R}, would take
+// n / n_R times the flops.  Then dX on E.
 template <class T>
 mcsdp_status phase_pmatrix_dense(mcsdp_ctx *c, double betamu, const double *Xbar) {
   const int n = c->S.n, nR = c->nR, nF = c->nF;
@@ -1300,37 +1345,64 @@ mcsdp_status phase_pmatrix_dense(mcsdp_ctx *c, double betamu, const double *Xbar
   const T *W1 = reinterpret_cast<const T *>(c->W1), *W2 = reinterpret_cast<const T *>(c->W2);
   T *V = reinterpret_cast<T *>(c->W3);
   T *M = reinterpret_cast<T *>(c->RS_M);
+  T *Tt = reinterpret_cast<T *>(c->RS_T);
+  const SolveFactors<T> f = factors_of(c, T());
   KScope k1(c, KC_PMAT);
-  CUDA_TRY(c, cudaMemsetAsync(V, 0, (size_t)n * ldw * sizeof(T), c->stream));
-  if (c->S.diag_constraints)  // dY = -sum dz_k A_k is diagonal: V = X̂ dY scales columns
-    launch_times_diag<T>(c->D, c->dY, W1, V, ldw, c->colw_dev, reinterpret_cast<T *>(c->lzU),
-                         c->stream);
-  else
-    launch_times_pattern<T>(c->D, c->dY, W1, V, ldw, c->colw_dev, c->stream);
-  if constexpr (std::is_same<T, float>::value) {
-    if (c->tcr)
-      root_tc_gemm(c, V + (size_t)nF * ldw, ldw, 1, nR, W2 + (size_t)nF * ldw, ldw, 1, nR, (int)ldw,
-                   M, 1, nR, 1.f, 0.f, false, false);
+  int nl = 0;
+  if (nF > 0) {
+    CUDA_TRY(c, cudaMemsetAsync(V, 0, (size_t)n * ldw * sizeof(T), c->stream));
+    if (c->S.diag_constraints)  // dY = -sum dz_k A_k is diagonal: V = X̂ dY scales columns
+      launch_times_diag<T>(c->D, c->dY, W1, V, ldw, c->colw_dev, reinterpret_cast<T *>(c->lzU),
+                           c->stream);
+    else
+      launch_times_pattern<T>(c->D, c->dY, W1, V, ldw, c->colw_dev, c->stream);
+    launch_forest_M<T>(c->D, V, W2, ldw, (int)ldw, c->Mlow, c->Mup, c->stream);
+    nl += 4;
   }
+  launch_extract_dense<T>(c->D, W2, ldw, c->colw_dev, c->YinvE, c->stream);
+  // U = dY Y^{-1}[:, R] over the root's columns (the forest's use of W3 above is complete)
+  T *U = V;
+  launch_dY_times<T>(c->D, c->dY, W2, U, ldw, nR, c->stream);
+  nl += 2;
+  if (nF > 0) {
+    const LsSkip none{nullptr, nullptr, 0};
+    const SkipHost hnone{nullptr, nullptr};
+    const int r = lsolve_c<T>(c, true, f.Lh, f.dinvL, U, nR, none, hnone);
+    if (r < 0) return fail(c, MCSDP_ERR_ARG, "solve shape not supported in this precision");
+    nl += r;
+  }
+  launch_root_pull<T>(c->lrf_ptr_dev, c->lrf_off_dev, c->lrf_row_dev, f.Lh, U, ldw, nF, nR, Tt,
+                      c->stream);
+  ++nl;
+  if constexpr (std::is_same<T, float>::value) {
+    if (c->tcr) {
+      root_tc_gemm(c, W1 + (size_t)nF * ldw, ldw, 1, nR, Tt, nR, 1, nR, nR, M, 1, nR, 1.f, 0.f,
+                   false, false);
+      nl += 3;
+    }
+  }
+  k1.done(nl);
+  nl = 0;
   if (!(std::is_same<T, float>::value && c->tcr)) {
+    // the root block's GEMM on its own class (the FP64 form's largest product)
+    KScope kg(c, std::is_same<T, double>::value ? KC_RGEMM : KC_PMAT);
     GemmArgs<T> g{};
-    g.M = g.N = nR;
-    g.K = (int)ldw;
-    g.A = V + (size_t)nF * ldw;
+    g.M = g.N = g.K = nR;
+    g.A = W1 + (size_t)nF * ldw;
     g.lda = ldw;
-    g.B = W2 + (size_t)nF * ldw;
-    g.ldb = ldw;
+    g.B = Tt;
+    g.ldb = nR;
     g.C = M;
     g.cs_i = 1;
     g.cs_j = nR;
     g.alpha = T(1);
     g.beta = T(0);
     gemm_tn<T>(g, c->stream);
+    kg.done(1);
   }
-  launch_extract_dense<T>(c->D, W2, ldw, c->colw_dev, c->YinvE, c->stream);
-  launch_forest_M<T>(c->D, V, W2, ldw, (int)ldw, c->Mlow, c->Mup, c->stream);
+  KScope k3(c, KC_PMAT);
   launch_root_M<T>(M, nR, c->Mlow + rv, c->Mup + rv, c->stream);
-  k1.done(6);
+  k3.done(1);
   KScope k2(c, KC_MISC);
   launch_dx_combine(c->D, betamu, Xbar, c->YinvE, c->Mlow, c->Mup, c->dX, c->stream);
   launch_root_dx(nR, betamu, Xbar + rv, c->YinvE + rv, c->Mlow + rv, c->Mup + rv, c->dX + rv,
@@ -1619,7 +1691,7 @@ mcsdp_status mixed_sce(mcsdp_ctx *c, bool b32, bool *solved) {
     {
       KScope k2(c, KC_BSOLVE);
       k2.done(mixed_refine_step(c->B, c->ldb, m, c->B32, c->Linv32, c->gref, c->xs, c->rref,
-                                c->yref, c->ayref, c->nref, c->stream));
+                                c->yref, c->ayref, c->nref, c->status + 4, c->stream));
     }
     KCHECK(c);
     double nr[2];
@@ -2595,11 +2667,15 @@ mcsdp_status mcsdp_work_model(const mcsdp_ctx *c, mcsdp_work *w) {
   w->bytes[2] = 8 * (2 * n * n + 2 * nnzE);
   // K3 tiles: both dense matrices read once, lower(B) written once
   w->bytes[3] = 8 * (2 * n * n + S.m * (S.m + 1.0) / 2);
-  // K6: V = X̂ dY, the root block's GEMM (2 nR^2 n), the forest's row dot products
+  // K6: V = X̂ dY and the forest's row dot products; for the root block U = dY Y^{-1}[:, R],
+  // the forest's forward solve with nR right-hand sides, the L_RF product and the GEMM
+  // X̂_RR T (2 nR^3)
   double fM = 0;
   for (int t = 0; t < rt; ++t) fM += 2 * 2 * ent[t] * n;
-  w->flops[6] = 2 * arow * n + 2 * nR * nR * n + fM;
-  w->bytes[6] = 8 * (3 * n * n + 4 * nnzE);
+  const double lrf = (double)c->lrf_off.size();
+  w->flops[6] = 2 * arow * n + fM + 2 * arow * nR + 2 * nR * entF + 2 * lrf * nR +
+                2 * nR * nR * nR;
+  w->bytes[6] = 8 * (3 * n * n + 4 * nnzE + 3 * n * nR + 2 * nR * nR);
   // K7: the forest's cliques as above; the root's Lanczos bound, 3 products with nR x nR
   // matrices per step (the step count of the last bound)
   double fps2 = 0;
@@ -2646,21 +2722,33 @@ mcsdp_status mcsdp_backward(mcsdp_ctx *c, const double *gX, const double *gz, do
   // which is mu Y^{-1}); the Jacobian is the SCM at that X̄ and -F = b - mu h
   bool centred = false;
   double prev_res = -1.0;
-  for (int it = 0; it < 40 && !centred; ++it) {
+  int stalled = 0;
+  bool full = false;
+  for (int it = 0; it < 60 && !centred; ++it) {
     int nl = 0;
     s = phase_pmatrix<double>(c, &nl, nullptr, true);
     if (s) return s;
     CUDA_TRY(c, cudaMemsetAsync(c->Xbar, 0, nnzL * 8, c->stream));
     launch_axpy(nnzL, mu, c->YinvE, c->Xbar, c->stream);
     launch_measures(c->D, c->Xbar, c->Ylay, c->z, nullptr, c->scal, c->stream);
+    launch_diag_range(c->D, c->N, c->scal + 8, c->stream);
     KCHECK(c);
-    CUDA_TRY(c, cudaMemcpyAsync(sc, c->scal, 6 * 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(sc, c->scal, 8 * 8, cudaMemcpyDeviceToHost, c->stream));
+    double piv[2];
+    CUDA_TRY(c, cudaMemcpyAsync(piv, c->scal + 8, 2 * 8, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     prof_flush(c);
-    // done at 1e-13 relative, or once Newton stops gaining at the rounding level of the
-    // residual evaluation (below 1e-9 relative)
+    // done at 1e-13 relative; or once Newton stops gaining (a full step that does not halve
+    // the residual) at the rounding level of the residual's evaluation: below 1e-9 relative, or
+    // after three such steps below rho = 64 eps cond(Y), cond(Y) estimated from below by the
+    // pivot range (max_j N_jj / min_j N_jj)^2 (X = mu Y^{-1} is formed with relative error about
+    // eps cond(Y); near the optimum cond(Y) grows like 1/mu)
     const double res = sc[3] / std::max(1.0, sc[4]);
-    if (res <= 1e-13 || (prev_res >= 0 && res > 0.5 * prev_res && res <= 1e-9)) {
+    const bool slow = prev_res >= 0 && full && res > 0.5 * prev_res;
+    stalled = slow ? stalled + 1 : 0;
+    const double cnd = piv[1] > 0 ? (piv[0] / piv[1]) * (piv[0] / piv[1]) : 1e300;
+    const double rho = 64.0 * 2.220446049250313e-16 * cnd;
+    if (res <= 1e-13 || (slow && res <= 1e-9) || (stalled >= 3 && res <= rho)) {
       centred = true;
       break;
     }
@@ -2692,6 +2780,7 @@ mcsdp_status mcsdp_backward(mcsdp_ctx *c, const double *gX, const double *gz, do
       t *= 0.5;
       if (h > 40) return fail(c, MCSDP_ERR_STALL, "centring step collapsed");
     }
+    full = t == 1.0;
   }
   if (!centred) return fail(c, MCSDP_ERR_STALL, "centring did not converge");
   // at the central point: L̂ (Algorithm 1 on X̄ = mu Y^{-1} on E) and the SCM

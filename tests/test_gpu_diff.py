@@ -77,14 +77,32 @@ def test_backward_matches_oracle(mk):
 
 
 def test_autograd_layer():
+    """solve_layer's gradients (through torch.autograd) against the oracle's adjoint at the same
+    central point: loss = sum of W . X̄ over the layout entries + g . z, W and g seeded."""
     from paper_1310_6919_gb300.autograd import solve_layer
+    from tests.gpu_helpers import Case
     inst = small_random_sdp(9, 14, 2)
+    c = Case(inst, max_iter=6)  # the layout map (same symbolic analysis as the layer's)
     b = torch.tensor(inst.b, requires_grad=True)
     val = torch.tensor(inst.val, requires_grad=True)
     X, z = solve_layer(b, val, inst.n, inst.m, inst.mat, inst.row, inst.col,
                        z0=torch.tensor(inst.z0, device="cuda:0"), device=0, max_iter=6)
-    loss = X.sum() + z.sum()
+    rng = np.random.default_rng(8)
+    W = torch.tensor(np.where(c.valid, rng.standard_normal(c.valid.shape[0]), 0.0), device=X.device)
+    g = torch.tensor(rng.standard_normal(inst.m), device=z.device)
+    loss = (W * X).sum() + (g * z).sum()
     loss.backward()
-    assert b.grad is not None and val.grad is not None
-    assert torch.isfinite(b.grad).all() and torch.isfinite(val.grad).all()
     assert b.grad.shape == b.shape and val.grad.shape == val.shape
+    # the oracle at the central point for the forward iterate's mu
+    A = SparseSym.from_instance(inst)
+    Xd = c.from_layout(X.detach())
+    zn = z.detach().cpu().numpy()
+    mu = float(np.sum(Xd * dual_slack(A, zn))) / inst.n
+    zc, Yc, Xc, res = diff.central_point(A, inst.b, mu, zn)
+    assert res <= 1e-11
+    gb, gA0, _ = diff.backward(A, zc, Yc, Xc, _layout_to_sym(c, W.cpu().numpy()), g.cpu().numpy(),
+                               with_gA=False)
+    ge = diff.entry_gradients(inst, zc, gb, gA0, Xc)
+    scale = max(np.max(np.abs(ge)), np.max(np.abs(gb)))
+    assert np.max(np.abs(b.grad.numpy() - gb)) <= 1e-8 * scale
+    assert np.max(np.abs(val.grad.numpy() - ge)) <= 1e-8 * scale

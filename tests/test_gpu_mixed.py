@@ -61,8 +61,10 @@ def test_mixed_scm_matches_oracle(mk):
     assert np.max(np.abs(h.cpu().numpy() - href)) <= 1e-5 * np.max(np.abs(href))
 
 
-@pytest.mark.parametrize("mk", SMALL, ids=IDS)
+@pytest.mark.parametrize("mk", SMALL + [lambda: lattice_maxcut(70, 70)], ids=IDS + ["grid4900"])
 def test_mixed_newton_step_solves_its_sce(mk):
+    """grid4900: m = 4900 takes the refinement's wide substitutions (all SMs, ticket-ordered
+    row blocks) and the tensor-core FP32 factor."""
     from tests.gpu_helpers import Case, rel_err
     inst = mk()
     c = Case(inst, precision=1)
@@ -80,6 +82,10 @@ def test_mixed_newton_step_solves_its_sce(mk):
     assert omega <= 1e-10
     dz_exact = np.linalg.solve(Bs, g)
     assert rel_err(dz, dz_exact) < 1e-10 * np.linalg.cond(Bs) * 10
+    if inst.m >= 4096:
+        # the FP32 factor and its refinement solved it: no FP64 SCM factorisation ran
+        cnt = c.P.stats()["count"]
+        assert cnt["scm_chol32"] > 0 and cnt["scm_chol"] == 0
 
 
 def test_mixed_scm_full_size_sampled_entries():
