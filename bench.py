@@ -233,7 +233,7 @@ def run_gb300(args):
         dist.barrier()
     from instances import workload
     hbm_peak, bf16_peak, bf16_sus, peak_src = measured_peaks()
-    inst = workload(WORKLOAD)
+    inst = workload(args.workload)
     stream = torch.cuda.current_stream(dev)
     zh = torch.tensor(inst.z0, dtype=torch.float64).pin_memory()
     zd = torch.empty(inst.m, dtype=torch.float64, device=f"cuda:{dev}")
@@ -382,7 +382,9 @@ def run_gb300(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC, "precision": "mixed",
+                "config": {"workload": args.workload,
+                           "desc": WORKLOAD_DESC if args.workload == WORKLOAD else args.workload,
+                           "precision": "mixed",
                            "iterations": int(rm["iters"]), "pobj": rm["pobj"], "gap": rm["gap"],
                            "all_optimal": ok, "create_s": create_s,
                            "l2": "inputs larger than L2 (X̂, Y^-1 and B are 1.6-3.2 GB each)",
@@ -475,12 +477,42 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="leave out the FP64 leg")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="named workload of the timed legs (default: the headline's)")
     ap.add_argument("--legs", default="all", choices=["all", "main"],
                     help="main: only the config-3 legs (mixed headline and FP64)")
+    ap.add_argument("--newton-steps", type=int, default=0,
+                    help="profiling entry, not a bench run: this many Newton steps of the "
+                         "workload at its start point (--precision), per-class device times "
+                         "printed; no JSON line")
+    ap.add_argument("--precision", type=int, default=1, choices=[0, 1],
+                    help="form of the --newton-steps run")
     args = ap.parse_args()
+    if args.newton_steps > 0:
+        return newton_steps(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gb300(args)
+
+
+def newton_steps(args):
+    """K Newton steps (mcsdp_newton_step) at (X̄ = I, z0) of the named workload: the command the
+    per-kernel profiles are captured with (one step runs every kernel of one iteration)."""
+    import torch
+    from paper_1310_6919_gb300 import Problem, build_library
+    from instances import workload
+    build_library()
+    inst = workload(args.workload)
+    P = Problem.from_instance(inst, device=0, precision=args.precision, profile=1)
+    X0 = P.identity_layout()
+    z0 = torch.tensor(inst.z0, dtype=torch.float64, device="cuda:0")
+    for k in range(args.newton_steps):
+        st = P.newton_step(X0, z0)
+        print(f"step {k}: alpha_p {st['alpha_p']:.4f} alpha_d {st['alpha_d']:.4f}", flush=True)
+    s = P.stats()
+    print("ms per class", json.dumps({k: round(v, 3) for k, v in s["ms"].items() if v > 0}),
+          "launches", s["launches"], "root rows", P.info["max_nrow"], flush=True)
+    return 0
 
 
 if __name__ == "__main__":

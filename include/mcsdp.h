@@ -104,8 +104,11 @@ typedef struct {
   int32_t relax;         /* 1 = relaxed supernode amalgamation (default), 0 = fundamental
                             supernodes only; amalgamation enlarges E with explicit zeros */
   int32_t solve_warps;   /* unused (kept for layout compatibility) */
-  double mixed_gap;      /* mixed form: relative gap below which every stage runs in FP64
-                            (default 1e-5) */
+  double mixed_gap;      /* mixed form: relative gap below which every stage runs in FP64.
+                            0 = default: 1e-5 for m < 4096; none for m >= 4096, where the
+                            refinement runs up to 60 steps while it contracts by 0.9 per step
+                            and the solve promotes only when it stalls or the FP32 factor
+                            breaks down; < 0 = none */
   int32_t root_rows;     /* dense root: cliques with more than this many rows (or more than 96
                             columns) are merged, with all their ancestors, into one root clique R
                             handled by dense kernels; the other cliques keep the small-clique
@@ -317,10 +320,10 @@ mcsdp_status mcsdp_gemm_tc(int32_t M, int32_t N, int32_t K, const float *A, int6
 /* Differentiation of the solution (not in the paper).  The point differentiated is the
  * central-path point for mu = X̄.Y/n of the context's iterate: the iterate is first re-centred
  * (Newton on z for A(mu Y(z)^{-1}) = b with Y(z) = A_0 - sum z_k A_k, until the residual
- * max|A(X) - b| / max(1, max|b|) is at most 1e-13, or, once full Newton steps no longer halve
- * it, is at the rounding level of its evaluation: at most 1e-9 after one such step, or at most
- * 64 eps cond(Y) after three, cond(Y) estimated from below by (max_j N_jj / min_j N_jj)^2 (near
- * the optimum cond(Y) grows like 1/mu, and the point, hence the gradients, carry that rounding);
+ * max|A(X) - b| / max(1, max|b|) is at most 1e-13, or, once three full Newton steps in a row no
+ * longer halve it, is at the rounding level of its evaluation, at most 64 eps cond(Y), cond(Y)
+ * estimated from below by (max_j N_jj / min_j N_jj)^2 (near the optimum cond(Y) grows like
+ * 1/mu, and the point carries that rounding);
  * the context's iterate becomes that point, X̄ = mu Y^{-1} on E).  For the loss
  * l = sum over layout entries gX . X̄ + gz^T z, implicit differentiation of A(X) = b,
  * X = mu Y^{-1} gives, with R = sym(X̂ G Y^{-1}) (G the symmetric matrix of the weights gX),

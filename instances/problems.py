@@ -273,7 +273,8 @@ def batch_mix(n_maxcut, n_arrow, seed=SEED_BASE + 4):
 
 def workload(name, seed=None):
     """Named workloads: 'grid_maxcut_100' (10x10 lattice), 'block_arrow_2020' (40 x 50 + 20,
-    m = 2000), 'block_arrow_1020' (20 x 50 + 20, m = 1000), 'ring_maxcut_20000'."""
+    m = 2000), 'block_arrow_1020' (20 x 50 + 20, m = 1000), 'ring_maxcut_20000', and
+    'ring_maxcut_8000' (the same family at n = 8000: a case small enough for profiler captures)."""
     if name == "grid_maxcut_100":
         return lattice_maxcut(10, 10, seed=SEED_BASE + 1 if seed is None else seed)
     if name == "block_arrow_2020":
@@ -282,4 +283,6 @@ def workload(name, seed=None):
         return block_arrow(20, 50, 20, 1000, seed=SEED_BASE + 5 if seed is None else seed)
     if name == "ring_maxcut_20000":
         return random_ring_maxcut(20000, seed=SEED_BASE + 3 if seed is None else seed)
+    if name == "ring_maxcut_8000":
+        return random_ring_maxcut(8000, seed=SEED_BASE + 6 if seed is None else seed)
     raise KeyError(name)

@@ -249,8 +249,9 @@ void launch_set_identity(const DevSym &S, double *Xbar, cudaStream_t st);
 // ---------------- dense root (kern_root.cu) ----------------
 void launch_root_assemble(const DevSym &S, const RootGather &G, const double *Yb,
                           const double *dY, double alpha, double *Nbuf, cudaStream_t st);
+// root = true launches it as k_root_gemm (the dense root's P-MATRIX product)
 template <class T>
-void gemm_tn(const GemmArgs<T> &g, cudaStream_t st);
+void gemm_tn(const GemmArgs<T> &g, cudaStream_t st, bool root = false);
 // X = L^{-1} (L dense lower with its rows mirrored above the diagonal, Linv its 32 x 32 diagonal
 // block inverses; work: 256 (n + 256) values); returns launches
 template <class T>
@@ -384,11 +385,11 @@ int mixed_factor(double *B, int64_t ldb, int m, float *B32, float *Linv32, int *
 // number of column chunks of the refinement's matrix-vector product (P, A hold chunks x m)
 int mixed_chunks(int m);
 // one refinement step: x += (L32 L32^T)^{-1} r, then r = g - B x (FP64) and
-// norms = (max|r|, max(|B||x| + |g|)); status gets ST_TIMEOUT if a bounded wait of the wide
-// substitutions (m >= 4096) ran out
+// norms = (max|r|, max(|B||x| + |g|)); for m >= 4096 the substitutions are blocked by panels
+// of 1024 rows over all SMs (P holds their FP32 vector), below that one cluster of 8 CTAs
 int mixed_refine_step(const double *B, int64_t ldb, int m, const float *L32, const float *Linv32,
                       const double *g, double *x, double *r, double *P, double *A, double *norms,
-                      int *status, cudaStream_t st);
+                      cudaStream_t st);
 void launch_rhs_border(const DevSym &S, double *B, int64_t ldb, const double *hvec, double betamu,
                        cudaStream_t st);
 void launch_dz_to_user(const DevSym &S, const double *dz_int, double *dz_user, cudaStream_t st);

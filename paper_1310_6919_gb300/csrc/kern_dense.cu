@@ -1373,100 +1373,124 @@ __global__ void __cluster_dims__(RCL, 1, 1) __launch_bounds__(RTH)
   cl.sync();  // no CTA leaves while another may still write into its shared memory
 }
 
-// The refinement's substitutions for large m, over all SMs: x += L^{-T} L^{-1} r (FP32 factor, ld
-// m, L^T in the strict upper triangle; FP64 r and x).  One CTA per row block of NB rows, in
-// ticket order (an atomic counter: every block a CTA waits on belongs to a CTA that started
-// before it, so the waits end whatever the residency).  Block i: each warp takes the earlier
-// blocks q = w, w + 8, ... (lane = row of block i), loads the NB factor entries of (i, q) before
-// it waits for q's flag, then adds their products with the published y_q; the warps' sums are
-// combined, the diagonal block's inverse applied, y_i published (fence, then the flag).  The
-// backward pass runs the blocks from the last with L^T (read from the upper triangle: the same
-// coalesced row segments).  Every wait is bounded (thread 0 of the warp polls; past the limit the
-// status gets ST_TIMEOUT and the abort word ends every wait; the results are then garbage, the
-// kernels still finish).
-constexpr int TW_WARPS = 8;
-constexpr int TRSV_WIDE_M = 4096;  // from here on the solves run over all SMs
-constexpr int64_t TW_SPIN_LIMIT = 1 << 22;
-
-struct TrsvWork {
-  float *y;      // m
-  int *flag;     // 2 x nblk: forward, backward
-  int *ticket;   // 2
-  int *abort;    // 1
-};
-
-__device__ __forceinline__ bool tw_wait(const int *flag, int *abort, int *status) {
-  unsigned ns = 32;
-  for (int64_t it = 0;; ++it) {
-    if (ld_acquire(flag)) return true;
-    if (ld_acquire(abort)) return false;
-    if (it >= TW_SPIN_LIMIT) break;
-    __nanosleep(ns);
-    if (ns < 256) ns <<= 1;
-  }
-  atomicExch(abort, 1);
-  atomicOr(status, ST_TIMEOUT);
-  return false;
-}
+// The refinement's substitutions for large m: x += L^{-T} L^{-1} r (FP32 factor, ld m, L^T in the
+// strict upper triangle; FP64 r and x), blocked by panels of TP rows so that no kernel waits on
+// another CTA.  Forward, per panel [k0, k0 + TP): one CTA of 1024 threads solves the panel's
+// triangle (blocks of NB: the block's inverse applied by warp 0, then thread t removes the
+// block's part from row k0 + t; the panel's y in shared memory), then every row below the
+// panel takes off L[r, panel] y_panel (k_trsv_update: CTA = 32 rows x 8 column phases, every
+// load a 128-byte row segment, bandwidth-bound over all SMs).  Backward: panels from the last,
+// with L^T read from the upper triangle (the same coalesced row segments), the update going to
+// the rows above.  The vector lives in FP32 (y), x is updated in FP64 at the end.
+constexpr int TRSV_WIDE_M = 4096;  // from here on the blocked substitutions
+constexpr int TP = 1024;
 
 template <bool FWD>
-__global__ void __launch_bounds__(TW_WARPS * 32)
-    k_trsv_wide_f32(const float *__restrict__ L, int m, const float *__restrict__ Linv,
-                    const double *__restrict__ r, double *x, TrsvWork w, int *status) {
-  __shared__ float red[TW_WARPS][NB + 1];
-  __shared__ int s_blk;
-  const int nblk = (m + NB - 1) / NB;
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) {
-    const int t = atomicAdd(w.ticket + (FWD ? 0 : 1), 1);
-    s_blk = FWD ? t : nblk - 1 - t;
-  }
+__global__ void __launch_bounds__(TP) k_trsv_panel(const float *__restrict__ L, int m,
+                                                   const float *__restrict__ Linv, int k0,
+                                                   float *y) {
+  __shared__ float ys[TP];
+  __shared__ float yb[NB];
+  const int pw = min(TP, m - k0), t = threadIdx.x, lane = t & 31;
+  if (t < pw) ys[t] = y[k0 + t];
   __syncthreads();
-  const int i = s_blk;
-  const int b0 = i * NB, row = b0 + lane;
-  const bool valid = row < m;
-  int *flags = w.flag + (FWD ? 0 : nblk);
-  float acc = 0.f;
-  // blocks this warp takes: forward q < i, backward q > i
-  const int q0 = FWD ? wp : i + 1 + wp, q1 = FWD ? i : nblk;
-  for (int q = q0; q < q1; q += TW_WARPS) {
-    const int c0 = q * NB, nc = min(NB, m - c0);
-    float lv[NB];
-    // row `row` of block (i, q): L[row][c0 + c] (forward, below the diagonal) or
-    // L^T[row][c0 + c] = L[c0 + c][row], held at [row + (c0 + c) m] above the diagonal
+  const int nb_tot = (pw + NB - 1) / NB;
+  for (int s = 0; s < nb_tot; ++s) {
+    const int b = FWD ? s : nb_tot - 1 - s;
+    const int b0 = b * NB, nb = min(NB, pw - b0);
+    if (t < 32) {
+      const float *Li = Linv + (int64_t)((k0 + b0) / NB) * NB * NB;
+      const float rl = lane < nb ? ys[b0 + lane] : 0.f;
+      float v = 0.f;
 #pragma unroll
-    for (int c = 0; c < NB; ++c) lv[c] = (valid && c < nc) ? L[row + (int64_t)(c0 + c) * m] : 0.f;
-    // (after an abort the values read are garbage; the kernel still runs to its end)
-    if (lane == 0) tw_wait(flags + q, w.abort, status);
-    __syncwarp();
-    // y_q: the forward result, overwritten by block q's backward result once it is published
-    const float yq = lane < nc ? __ldcg(w.y + c0 + lane) : 0.f;
-#pragma unroll
-    for (int c = 0; c < NB; ++c) acc = fmaf(lv[c], __shfl_sync(0xffffffffu, yq, c), acc);
+      for (int l = 0; l < NB; ++l) {
+        const float ra = __shfl_sync(0xffffffffu, rl, l);
+        v = fmaf(FWD ? Li[lane + l * NB] : Li[l + lane * NB], ra, v);
+      }
+      if (lane < nb) ys[b0 + lane] = v;
+      yb[lane] = lane < nb ? v : 0.f;
+    }
+    __syncthreads();
+    // rows of the panel after the block (forward) or before it (backward)
+    const bool mine = FWD ? (t >= b0 + nb && t < pw) : (t < b0);
+    if (mine) {
+      const int row = k0 + t;
+      float a = 0.f;
+#pragma unroll 8
+      for (int c = 0; c < nb; ++c) a = fmaf(L[row + (int64_t)(k0 + b0 + c) * m], yb[c], a);
+      ys[t] -= a;
+    }
+    __syncthreads();
   }
-  red[wp][lane] = acc;
+  if (t < pw) y[k0 + t] = ys[t];
+}
+
+// forward: y[r] -= sum_c L[r, k0 + c] y[k0 + c] for the rows r >= k0 + pw; backward: for the rows
+// r < k0, with L^T (the upper triangle holds L^T[r][k0 + c] at [r + (k0 + c) m])
+template <bool FWD>
+__global__ void __launch_bounds__(256) k_trsv_update(const float *__restrict__ L, int m, int k0,
+                                                    int pw, float *y) {
+  __shared__ float part[8][33];
+  __shared__ float yp[TP];
+  const int il = threadIdx.x & 31, ph = threadIdx.x >> 5;
+  for (int c = threadIdx.x; c < pw; c += 256) yp[c] = y[k0 + c];
   __syncthreads();
-  if (wp == 0) {
+  const int r = (FWD ? k0 + pw : 0) + blockIdx.x * 32 + il;
+  const int rend = FWD ? m : k0;
+  float a0 = 0.f, a1 = 0.f;
+  if (r < rend) {
+    int c = ph;
+    for (; c + 8 < pw; c += 16) {
+      a0 = fmaf(L[r + (int64_t)(k0 + c) * m], yp[c], a0);
+      a1 = fmaf(L[r + (int64_t)(k0 + c + 8) * m], yp[c + 8], a1);
+    }
+    for (; c < pw; c += 8) a0 = fmaf(L[r + (int64_t)(k0 + c) * m], yp[c], a0);
+  }
+  part[ph][il] = a0 + a1;
+  __syncthreads();
+  if (ph == 0 && r < rend) {
     float a = 0.f;
 #pragma unroll
-    for (int q = 0; q < TW_WARPS; ++q) a += red[q][lane];
-    const float rhs = valid ? (FWD ? (float)r[row] : __ldcg(w.y + row)) - a : 0.f;
-    // diagonal block: y_i = Linv_ii rhs (forward), x_i = Linv_ii^T rhs (backward)
-    const float *Li = Linv + (int64_t)i * NB * NB;
-    float v = 0.f;
-#pragma unroll
-    for (int l = 0; l < NB; ++l) {
-      const float rl = __shfl_sync(0xffffffffu, rhs, l);
-      v = fmaf(FWD ? Li[lane + l * NB] : Li[l + lane * NB], rl, v);
-    }
-    if (valid) {
-      w.y[row] = v;
-      if (!FWD) x[row] = x[row] + (double)v;
-    }
-    __threadfence();
-    __syncwarp();
-    if (lane == 0) atomicExch(flags + i, 1);
+    for (int q = 0; q < 8; ++q) a += part[q][il];
+    y[r] -= a;
   }
+}
+
+__global__ void k_trsv_load(const double *__restrict__ r, float *y, int m) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    y[i] = (float)r[i];
+}
+__global__ void k_trsv_store(const float *__restrict__ y, double *x, int m) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    x[i] += (double)y[i];
+}
+
+static int trsv_blocked(const float *L, int m, const float *Linv, const double *r, double *x,
+                        float *y, cudaStream_t st) {
+  const int blocks = std::min(152 * 8, (m + 255) / 256);
+  k_trsv_load<<<blocks, 256, 0, st>>>(r, y, m);
+  int nl = 2;
+  for (int k0 = 0; k0 < m; k0 += TP) {
+    const int pw = std::min(TP, m - k0);
+    k_trsv_panel<true><<<1, TP, 0, st>>>(L, m, Linv, k0, y);
+    ++nl;
+    const int rows = m - k0 - pw;
+    if (rows > 0) {
+      k_trsv_update<true><<<(rows + 31) / 32, 256, 0, st>>>(L, m, k0, pw, y);
+      ++nl;
+    }
+  }
+  const int last = ((m - 1) / TP) * TP;
+  for (int k0 = last; k0 >= 0; k0 -= TP) {
+    k_trsv_panel<false><<<1, TP, 0, st>>>(L, m, Linv, k0, y);
+    ++nl;
+    if (k0 > 0) {
+      k_trsv_update<false><<<(k0 + 31) / 32, 256, 0, st>>>(L, m, k0, std::min(TP, m - k0), y);
+      ++nl;
+    }
+  }
+  k_trsv_store<<<blocks, 256, 0, st>>>(y, x, m);
+  return nl;
 }
 
 // Partial products of y = B x with the full symmetric FP64 B (column-major): CTA (row block of
@@ -1570,21 +1594,13 @@ int mixed_factor(double *B, int64_t ldb, int m, float *B32, float *Linv32, int *
 
 int mixed_refine_step(const double *B, int64_t ldb, int m, const float *L32, const float *Linv32,
                       const double *g, double *x, double *r, double *P, double *A, double *norms,
-                      int *status, cudaStream_t st) {
-  int nl = 3;
+                      cudaStream_t st) {
+  int nl = 2;
   if (m >= TRSV_WIDE_M) {
-    // P (chunks x m doubles) is free until the product below: y, then the flags and tickets
-    const int nblk = (m + NB - 1) / NB;
-    TrsvWork w;
-    w.y = reinterpret_cast<float *>(P);
-    w.flag = reinterpret_cast<int *>(w.y + ((m + 63) / 64) * 64);
-    w.ticket = w.flag + 2 * nblk;
-    w.abort = w.ticket + 2;
-    cudaMemsetAsync(w.flag, 0, (2 * (size_t)nblk + 4) * sizeof(int), st);
-    k_trsv_wide_f32<true><<<nblk, TW_WARPS * 32, 0, st>>>(L32, m, Linv32, r, x, w, status);
-    k_trsv_wide_f32<false><<<nblk, TW_WARPS * 32, 0, st>>>(L32, m, Linv32, r, x, w, status);
-    ++nl;
+    // P (chunks x m doubles) is free until the product below: the FP32 vector
+    nl += trsv_blocked(L32, m, Linv32, r, x, reinterpret_cast<float *>(P), st);
   } else {
+    ++nl;
     const size_t smem = (size_t)m * sizeof(float);
     if (smem > 48 * 1024) smem_optin((const void *)k_refine_solve_f32);
     k_refine_solve_f32<<<RCL, RTH, smem, st>>>(L32, m, Linv32, r, x);

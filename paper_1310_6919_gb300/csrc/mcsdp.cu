@@ -1397,7 +1397,7 @@ mcsdp_status phase_pmatrix_dense(mcsdp_ctx *c, double betamu, const double *Xbar
     g.cs_j = nR;
     g.alpha = T(1);
     g.beta = T(0);
-    gemm_tn<T>(g, c->stream);
+    gemm_tn<T>(g, c->stream, true);
     kg.done(1);
   }
   KScope k3(c, KC_PMAT);
@@ -1666,10 +1666,15 @@ struct IterOut {
 // iterative refinement with the residual g - B x formed in FP64 from the FP64 B (the scheme of
 // LAPACK's dsposv).  Measure of convergence: omega = max|r| / max(|B||x| + |g|).  Success when
 // omega <= sqrt(m) eps64 (FP64-assembled B); the refinement is abandoned (*solved = false, B
-// untouched) when the FP32 factorisation breaks down, when omega fails to halve in two
-// consecutive steps while still above m eps64 (the worst-case backward error of the FP64
-// factorisation itself), or after MIXED_MAX_STEPS steps.  Leaves x in c->xs (internal order).
-constexpr int MIXED_MAX_STEPS = 10;
+// untouched) when the FP32 factorisation breaks down, when omega fails to shrink by the factor
+// MIXED_RATE in two consecutive steps while still above m eps64 (the worst-case backward error of
+// the FP64 factorisation itself), or after the step budget.  Refinement contracts by about
+// cond(B) eps32 per step; for large m (from MIXED_LONG_M on) a step (substitutions over all SMs
+// plus an FP64 product with B, O(m^2)) costs a few hundredths of the FP64 factorisation
+// (O(m^3)), so slow contraction is still worth following there: rate 0.9 and 60 steps, against
+// halving and 10 steps for small m.  Leaves x in c->xs (internal order).
+constexpr int MIXED_MAX_STEPS = 10, MIXED_MAX_STEPS_LONG = 60;
+constexpr int MIXED_LONG_M = 4096;
 // b32: B was assembled in FP32 (entries accurate to about 1e-6 relative): the refinement then
 // stops at omega <= 1e-10, which already puts the solve error far below the assembly error
 mcsdp_status mixed_sce(mcsdp_ctx *c, bool b32, bool *solved) {
@@ -1687,11 +1692,14 @@ mcsdp_status mixed_sce(mcsdp_ctx *c, bool b32, bool *solved) {
   const double tol_stall = b32 ? 1e-10 : (double)m * eps;
   double prev = 1.0;
   int slow = 0;
-  for (int k = 0; k < MIXED_MAX_STEPS; ++k) {
+  const bool long_m = m >= MIXED_LONG_M;
+  const int max_steps = long_m ? MIXED_MAX_STEPS_LONG : MIXED_MAX_STEPS;
+  const double rate = long_m ? 0.9 : 0.5;
+  for (int k = 0; k < max_steps; ++k) {
     {
       KScope k2(c, KC_BSOLVE);
       k2.done(mixed_refine_step(c->B, c->ldb, m, c->B32, c->Linv32, c->gref, c->xs, c->rref,
-                                c->yref, c->ayref, c->nref, c->status + 4, c->stream));
+                                c->yref, c->ayref, c->nref, c->stream));
     }
     KCHECK(c);
     double nr[2];
@@ -1711,7 +1719,7 @@ mcsdp_status mixed_sce(mcsdp_ctx *c, bool b32, bool *solved) {
       *solved = true;
       return MCSDP_OK;
     }
-    slow = (omega > 0.5 * prev) ? slow + 1 : 0;
+    slow = (omega > rate * prev) ? slow + 1 : 0;
     if (slow >= 2) {
       *solved = omega <= tol_stall;
       return MCSDP_OK;
@@ -1984,7 +1992,7 @@ void mcsdp_default_options(mcsdp_options *o) {
   o->profile = 0;
   o->relax = 1;
   o->solve_warps = 0;
-  o->mixed_gap = 1e-5;
+  o->mixed_gap = 0.0;
   o->root_rows = 0;
   o->tensor_cores = 1;
   o->mixed_asm_gap = 0.0;
@@ -2364,8 +2372,13 @@ mcsdp_status mcsdp_solve(mcsdp_ctx *c, mcsdp_result *res) {
   // the mixed form's FP64-assembly threshold: with a dense root the FP32 products run over all
   // n terms (root GEMMs), and their rounding, relative to the shrinking direction, decides the
   // root clique's primal step well before the FP32 factor stops refining
-  const double mixed_gap = c->opt.mixed_gap > 0 ? c->opt.mixed_gap : 1e-5;
-  const double asm_gap = c->opt.mixed_asm_gap > 0 ? c->opt.mixed_asm_gap : (c->dense ? 1e-1 : mixed_gap);
+  // the gap below which the mixed form runs in FP64 throughout: for large m the refinement of
+  // the FP32 factor (long form, see mixed_sce) stays far cheaper than the FP64 factorisation
+  // until it stalls, so no gap threshold applies by default
+  const double mixed_gap = c->opt.mixed_gap > 0 ? c->opt.mixed_gap
+                           : c->opt.mixed_gap < 0 || c->S.m >= MIXED_LONG_M ? 0.0 : 1e-5;
+  const double asm_gap = c->opt.mixed_asm_gap > 0 ? c->opt.mixed_asm_gap
+                        : (c->dense ? 1e-1 : (mixed_gap > 0 ? mixed_gap : 1e-5));
   double prev_pinf = -1.0;
   float tms[4] = {0, 0, 0, 0};
   cudaEvent_t t0 = c->ev[6], t1 = c->ev[7];
@@ -2738,17 +2751,20 @@ mcsdp_status mcsdp_backward(mcsdp_ctx *c, const double *gX, const double *gz, do
     CUDA_TRY(c, cudaMemcpyAsync(piv, c->scal + 8, 2 * 8, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     prof_flush(c);
-    // done at 1e-13 relative; or once Newton stops gaining (a full step that does not halve
-    // the residual) at the rounding level of the residual's evaluation: below 1e-9 relative, or
-    // after three such steps below rho = 64 eps cond(Y), cond(Y) estimated from below by the
-    // pivot range (max_j N_jj / min_j N_jj)^2 (X = mu Y^{-1} is formed with relative error about
-    // eps cond(Y); near the optimum cond(Y) grows like 1/mu)
+    // done at 1e-13 relative; or once Newton stops gaining (three full steps in a row that do
+    // not halve the residual) at the rounding level of the residual's evaluation, rho =
+    // 64 eps cond(Y), cond(Y) estimated from below by the pivot range (max_j N_jj / min_j N_jj)^2
+    // (X = mu Y^{-1} is formed with relative error about eps cond(Y); near the optimum cond(Y)
+    // grows like 1/mu)
     const double res = sc[3] / std::max(1.0, sc[4]);
     const bool slow = prev_res >= 0 && full && res > 0.5 * prev_res;
     stalled = slow ? stalled + 1 : 0;
     const double cnd = piv[1] > 0 ? (piv[0] / piv[1]) * (piv[0] / piv[1]) : 1e300;
     const double rho = 64.0 * 2.220446049250313e-16 * cnd;
-    if (res <= 1e-13 || (slow && res <= 1e-9) || (stalled >= 3 && res <= rho)) {
+    if (c->opt.verbose > 1)
+      std::fprintf(stderr, "  centring %d: residual %.3e (rounding level %.1e, full step %d)\n", it,
+                   res, rho, full ? 1 : 0);
+    if (res <= 1e-13 || (stalled >= 3 && res <= rho)) {
       centred = true;
       break;
     }

@@ -14,10 +14,9 @@ autograd.solve_layer).  Two solves of the same problem:
 * converged (relative gap 1e-7): mu is about 1e-9 and cond(Y) about 1e10, so the central point is
   determined only to the rounding level eps cond(Y) of evaluating its residual (about 1e-6 on
   both sides; a finite difference at h = 1e-6 has no significant digit there).  The gradients
-  are compared with the oracle's at the same mu at a tolerance set by that conditioning: the
-  oracle's own gradients move by about 1e-3 of the largest when its centring starts from a point
-  perturbed by 1e-9 (measured on the host), and the bound used is 1e-2 of the largest gradient
-  together with the correlation of the two gradient vectors (above 0.9999).
+  are nevertheless well determined: the oracle's own gradients move by 1.9e-7 of the largest when
+  its centring starts from another feasible point (measured on the host at this iterate), so the
+  device's gradients are compared with the oracle's at the same mu within 1e-5 of the largest.
 """
 import dataclasses
 
@@ -148,5 +147,4 @@ def test_config5_converged_gradients(case):
     go = np.concatenate([gb_o, ge_o])
     scale = np.max(np.abs(go))
     assert np.all(np.isfinite(g))
-    assert np.max(np.abs(g - go)) <= 1e-2 * scale
-    assert np.corrcoef(g, go)[0, 1] > 0.9999
+    assert np.max(np.abs(g - go)) <= 1e-5 * scale
