@@ -432,40 +432,55 @@ def other_legs(args, dev, stream):
         out[name] = {"s_per_solve": float(np.median(ts)) * 1e-3, "iterations": int(r["iters"]),
                      "pobj": r["pobj"], "status": int(r["status"])}
         del P
-    mix = batch_mix(48, 16)
+    # config 4: 512 max-cut + 128 block-arrow SDPs, each form through mcsdp_solve_batch (host
+    # threads, one stream per problem); one at a time on a 64-problem subset for comparison
+    mix = batch_mix(512, 128)
+    subset = set(range(48)) | set(range(512, 528))
 
-    def make(inst, st):
+    def make(inst, st, prec):
         Q = Problem(inst.n, inst.m, inst.b, inst.mat, inst.row, inst.col, inst.val, form=1,
-                    device=dev, stream=st)
+                    device=dev, stream=st, precision=prec)
         if inst.meta.get("kind") != "maxcut":
             Q.set_iterate(None, torch.tensor(inst.z0, dtype=torch.float64, device=f"cuda:{dev}"))
         return Q
 
-    seq_probs, bat_probs, skipped = [], [], 0
-    for q in mix:
-        try:
-            seq_probs.append(make(q, None))
-            bat_probs.append(make(q, torch.cuda.Stream(dev)))
-        except MCSDPError:
-            skipped += 1
-    make(mix[0], None).solve()
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    seq_res = [Q.solve() for Q in seq_probs]
-    torch.cuda.synchronize(dev)
-    t_seq = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    bat_res = solve_batch(bat_probs, nthreads=16)
-    torch.cuda.synchronize(dev)
-    t_bat = time.perf_counter() - t0
-    batched = {"problems": len(bat_probs), "skipped": skipped,
-               "sequential_problems_per_s": len(seq_probs) / t_seq,
-               "batched_problems_per_s": len(bat_probs) / t_bat, "speedup": t_seq / t_bat,
-               "all_optimal": all(r["status"] == 0 for r in bat_res),
-               "same_as_sequential": all(a["pobj"] == b["pobj"] for a, b in zip(seq_res, bat_res)),
-               "desc": ("48 max-cut G(n, 5n/2), n ~ U{50..400}, w ~ U[0,1) and 16 block-arrow "
-                        "SDPs, n ~ U{100..600}, border 20, m = n (seeded); host wall time, "
-                        "inputs resident")}
+    batched = {"problems": len(mix),
+               "desc": ("512 max-cut G(n, 5n/2), n ~ U{50..400}, w ~ U[0,1) and 128 block-arrow "
+                        "SDPs, n ~ U{100..600}, border 20, m = n (seeded); host wall time, inputs "
+                        "resident; one-at-a-time on the 64-problem subset (first 48 max-cut, first "
+                        "16 block-arrow)")}
+    make(mix[0], None, 0).solve()
+    for name, prec in (("fp64", 0), ("mixed", 1)):
+        probs, idx, skipped = [], [], 0
+        for i, q in enumerate(mix):
+            try:
+                probs.append(make(q, torch.cuda.Stream(dev), prec))
+                idx.append(i)
+            except MCSDPError:
+                skipped += 1
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        res = solve_batch(probs, nthreads=16)
+        torch.cuda.synchronize(dev)
+        t_bat = time.perf_counter() - t0
+        leg = {"problems_per_s": len(probs) / t_bat, "seconds": t_bat, "skipped": skipped,
+               "all_optimal": all(r["status"] == 0 for r in res)}
+        if prec == 0:
+            seq = [make(mix[i], None, 0) for i in sorted(subset)]
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            seq_res = [Q.solve() for Q in seq]
+            torch.cuda.synchronize(dev)
+            t_seq = time.perf_counter() - t0
+            bat_sub = {i: r for i, r in zip(idx, res)}
+            leg["sequential_problems_per_s_subset"] = len(seq) / t_seq
+            leg["speedup_vs_sequential"] = leg["problems_per_s"] / (len(seq) / t_seq)
+            leg["same_as_sequential_subset"] = all(
+                bat_sub[i]["pobj"] == r["pobj"] for i, r in zip(sorted(subset), seq_res) if i in bat_sub)
+            del seq
+        batched[name] = leg
+        del probs
+        torch.cuda.empty_cache()
     return out, batched
 
 

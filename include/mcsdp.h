@@ -87,7 +87,8 @@ typedef struct {
                             P-MATRIX solves (K6) run in FP32 from FP32 copies of L̂ and N; the
                             SCE B dz = g is solved with an FP32 Cholesky factor of B and FP64
                             iterative refinement against the stored B; Y's factor, Algorithm 1,
-                            the step lengths and the update stay FP64.  The solve promotes to
+                            the step lengths and the update stay FP64 (with a dense root, see
+                            mixed_asm_gap).  The solve promotes to
                             FP64 throughout once the relative gap falls below mixed_gap, the
                             refinement stalls, the FP32 factorisation breaks down or the primal
                             residual grows (m <= 50000). */
@@ -120,8 +121,10 @@ typedef struct {
                             TF32 products per FP32 product) for m >= 512; 0 = on the CUDA cores */
   double mixed_asm_gap;  /* mixed form: relative gap below which the SCM and the P-MATRIX are
                             assembled in FP64 while the SCE keeps the FP32 factor and FP64
-                            refinement (until promotion).  0 = default: 1e-1 with a dense root
-                            (its FP32 products run over all n terms), else mixed_gap */
+                            refinement (until promotion).  Above it, with a dense root, the
+                            root blocks of Y and X̄ are also factored (and X̄_RR's factor
+                            inverted) in FP32.  0 = default: 1e-2 with a dense root, else
+                            mixed_gap (1e-5 if that is off) */
 } mcsdp_options;
 
 void mcsdp_default_options(mcsdp_options *opt);

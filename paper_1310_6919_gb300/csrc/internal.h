@@ -295,6 +295,8 @@ void launch_forest_M(const DevSym &S, const T *V, const T *Wy, int64_t ldw, int 
                      double *Mlow, double *Mup, cudaStream_t st);
 template <class T>
 void launch_root_M(const T *M, int nR, double *Mlow_root, double *Mup_root, cudaStream_t st);
+// b[i] = a[i] (FP32 to FP64), n values
+void cast_f64(const float *a, double *b, int64_t n, cudaStream_t st);
 // out[0] = max_j |L_jj|, out[1] = min_j |L_jj| over the layout's diagonal (device doubles)
 void launch_diag_range(const DevSym &S, const double *L, double *out, cudaStream_t st);
 // the root block's P-MATRIX factor T = U_RR - L_RF Z, written transposed (Tt[j nR + r] = T_rj):

@@ -1389,36 +1389,59 @@ template <bool FWD>
 __global__ void __launch_bounds__(TP) k_trsv_panel(const float *__restrict__ L, int m,
                                                    const float *__restrict__ Linv, int k0,
                                                    float *y) {
+  static_assert(NB * NB == TP, "one inverse entry per thread");
   __shared__ float ys[TP];
   __shared__ float yb[NB];
+  __shared__ float ls[2][NB * NB];
   const int pw = min(TP, m - k0), t = threadIdx.x, lane = t & 31;
   if (t < pw) ys[t] = y[k0 + t];
-  __syncthreads();
   const int nb_tot = (pw + NB - 1) / NB;
+  const int row = k0 + t;
+  // the NB factor entries of this thread's row in block b (row segments of L below the
+  // diagonal, of L^T above it) are loaded one block ahead, so their latency overlaps the barrier
+  // and the diagonal step; the block's inverse likewise, one entry per thread into shared memory
+  auto first_of = [&](int s) { return FWD ? s : nb_tot - 1 - s; };
+  auto needs = [&](int b) {
+    const int b0 = b * NB;
+    return FWD ? (t >= b0 + min(NB, pw - b0) && t < pw) : (t < b0);
+  };
+  float lv[NB];
+  auto load_row = [&](int b) {
+    const int b0 = b * NB, nb = min(NB, pw - b0);
+    const bool need = needs(b);
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+      lv[c] = (need && c < nb) ? L[row + (int64_t)(k0 + b0 + c) * m] : 0.f;
+  };
+  auto load_inv = [&](int b, int buf) {
+    ls[buf][t] = Linv[(int64_t)((k0 + b * NB) / NB) * NB * NB + t];
+  };
+  load_row(first_of(0));
+  load_inv(first_of(0), 0);
+  __syncthreads();
   for (int s = 0; s < nb_tot; ++s) {
-    const int b = FWD ? s : nb_tot - 1 - s;
+    const int b = first_of(s);
     const int b0 = b * NB, nb = min(NB, pw - b0);
     if (t < 32) {
-      const float *Li = Linv + (int64_t)((k0 + b0) / NB) * NB * NB;
+      const float *Li = ls[s & 1];
       const float rl = lane < nb ? ys[b0 + lane] : 0.f;
       float v = 0.f;
 #pragma unroll
-      for (int l = 0; l < NB; ++l) {
-        const float ra = __shfl_sync(0xffffffffu, rl, l);
-        v = fmaf(FWD ? Li[lane + l * NB] : Li[l + lane * NB], ra, v);
-      }
+      for (int l = 0; l < NB; ++l)
+        v = fmaf(FWD ? Li[lane + l * NB] : Li[l + lane * NB], __shfl_sync(0xffffffffu, rl, l), v);
       if (lane < nb) ys[b0 + lane] = v;
       yb[lane] = lane < nb ? v : 0.f;
     }
     __syncthreads();
-    // rows of the panel after the block (forward) or before it (backward)
-    const bool mine = FWD ? (t >= b0 + nb && t < pw) : (t < b0);
-    if (mine) {
-      const int row = k0 + t;
+    if (needs(b)) {
       float a = 0.f;
-#pragma unroll 8
-      for (int c = 0; c < nb; ++c) a = fmaf(L[row + (int64_t)(k0 + b0 + c) * m], yb[c], a);
+#pragma unroll
+      for (int c = 0; c < NB; ++c) a = fmaf(lv[c], yb[c], a);
       ys[t] -= a;
+    }
+    if (s + 1 < nb_tot) {
+      load_row(first_of(s + 1));
+      load_inv(first_of(s + 1), (s + 1) & 1);
     }
     __syncthreads();
   }

@@ -422,11 +422,85 @@ __global__ void k_dotcols(const T *__restrict__ A, int64_t ld, int ncol, int len
   if (lane == 0) w[j] = beta == 0.0 ? alpha * acc : fma(alpha, acc, beta * w[j]);
 }
 
+// the same with 16-byte loads, for columns that start on a 16-byte boundary (A aligned and
+// ld sizeof(T) a multiple of 16): each lane takes runs of four consecutive entries (one float4,
+// or two double2, of the column and two double2 of v) with two runs in flight; the range's
+// unaligned head and the tail by single loads
+template <class T>
+__device__ __forceinline__ void load4(const T *p, T *o);
+template <>
+__device__ __forceinline__ void load4<float>(const float *p, float *o) {
+  const float4 q = __ldcs(reinterpret_cast<const float4 *>(p));
+  o[0] = q.x, o[1] = q.y, o[2] = q.z, o[3] = q.w;
+}
+template <>
+__device__ __forceinline__ void load4<double>(const double *p, double *o) {
+  const double2 a = __ldcs(reinterpret_cast<const double2 *>(p));
+  const double2 b = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
+  o[0] = a.x, o[1] = a.y, o[2] = b.x, o[3] = b.y;
+}
+
+template <class T>
+__global__ void k_dotcols_v4(const T *__restrict__ A, int64_t ld, int ncol, int len, int range,
+                             const double *__restrict__ v, double *w, double alpha, double beta) {
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= ncol) return;
+  const int lo = range == 1 ? j : 0, hi = range == 2 ? min(len, j + 1) : len;
+  const T *col = A + (int64_t)j * ld;
+  const int h0 = min(hi, (lo + 3) & ~3);
+  const int hb = h0 + ((hi - h0) & ~3);
+  double acc = 0.0;
+  for (int i = lo + lane; i < h0; i += 32) acc = fma((double)col[i], v[i], acc);
+  // runs of 4 from h0, lane-strided; partial sums in T per 1024 entries, carried in FP64
+  int q = (h0 >> 2) + lane;
+  const int qend = hb >> 2;
+  while (q < qend) {
+    T a0 = T(0), a1 = T(0);
+    const int qstop = min(qend, q + 256);
+    for (; q + 32 < qstop; q += 64) {
+      T c0[4], c1[4];
+      load4<T>(col + 4 * q, c0);
+      load4<T>(col + 4 * (q + 32), c1);
+      const double2 *vv0 = reinterpret_cast<const double2 *>(v + 4 * q);
+      const double2 *vv1 = reinterpret_cast<const double2 *>(v + 4 * (q + 32));
+      const double2 x0 = vv0[0], x1 = vv0[1], y0 = vv1[0], y1 = vv1[1];
+      a0 = fma(c0[0], (T)x0.x, a0);
+      a0 = fma(c0[1], (T)x0.y, a0);
+      a0 = fma(c0[2], (T)x1.x, a0);
+      a0 = fma(c0[3], (T)x1.y, a0);
+      a1 = fma(c1[0], (T)y0.x, a1);
+      a1 = fma(c1[1], (T)y0.y, a1);
+      a1 = fma(c1[2], (T)y1.x, a1);
+      a1 = fma(c1[3], (T)y1.y, a1);
+    }
+    for (; q < qstop; q += 32) {
+      T c0[4];
+      load4<T>(col + 4 * q, c0);
+      const double2 *vv0 = reinterpret_cast<const double2 *>(v + 4 * q);
+      const double2 x0 = vv0[0], x1 = vv0[1];
+      a0 = fma(c0[0], (T)x0.x, a0);
+      a0 = fma(c0[1], (T)x0.y, a0);
+      a0 = fma(c0[2], (T)x1.x, a0);
+      a0 = fma(c0[3], (T)x1.y, a0);
+    }
+    acc += (double)(a0 + a1);
+  }
+  for (int i = hb + lane; i < hi; i += 32) acc = fma((double)col[i], v[i], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) w[j] = beta == 0.0 ? alpha * acc : fma(alpha, acc, beta * w[j]);
+}
+
 template <class T>
 void dotcols(const T *A, int64_t ld, int ncol, int len, int range, const double *v, double *w,
              double alpha, double beta, cudaStream_t st) {
   if (ncol <= 0) return;
-  k_dotcols<T><<<(ncol + 7) / 8, 256, 0, st>>>(A, ld, ncol, len, range, v, w, alpha, beta);
+  const bool aligned = ((uintptr_t)A % 16 == 0) && ((ld * (int64_t)sizeof(T)) % 16 == 0) &&
+                       ((uintptr_t)v % 16 == 0);
+  if (aligned)
+    k_dotcols_v4<T><<<(ncol + 7) / 8, 256, 0, st>>>(A, ld, ncol, len, range, v, w, alpha, beta);
+  else
+    k_dotcols<T><<<(ncol + 7) / 8, 256, 0, st>>>(A, ld, ncol, len, range, v, w, alpha, beta);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -830,6 +904,17 @@ void launch_diag_range(const DevSym &S, const double *L, double *out, cudaStream
   k_diag_range<<<1, 1024, 0, st>>>(S, L, out);
 }
 
+__global__ void k_cast_f64(const float *__restrict__ a, double *b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+void cast_f64(const float *a, double *b, int64_t n, cudaStream_t st) {
+  if (n <= 0) return;
+  const int blocks = (int)std::min<int64_t>(4096, (n + 255) / 256);
+  k_cast_f64<<<blocks, 256, 0, st>>>(a, b, n);
+}
+
 template <class T>
 void launch_unit_cols(T *W, int64_t ldw, const int *colw, int k0, int nk, cudaStream_t st) {
   if (nk > 0) k_unit_cols<T><<<(nk + 255) / 256, 256, 0, st>>>(W, ldw, colw, k0, nk);
@@ -984,6 +1069,7 @@ MCSDP_ROOT_INST(float)
 #undef MCSDP_ROOT_INST
 template void copy_square<double, double>(const double *, int64_t, double *, int64_t, int, cudaStream_t);
 template void copy_square<double, float>(const double *, int64_t, float *, int64_t, int, cudaStream_t);
+template void copy_square<float, double>(const float *, int64_t, double *, int64_t, int, cudaStream_t);
 template void symmetrize<double, double>(const double *, int64_t, double *, int64_t, int, cudaStream_t);
 template void symmetrize<double, float>(const double *, int64_t, float *, int64_t, int, cudaStream_t);
 

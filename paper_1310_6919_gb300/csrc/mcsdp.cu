@@ -133,6 +133,10 @@ struct mcsdp_ctx {
   double *gref = nullptr, *rref = nullptr, *yref = nullptr, *ayref = nullptr, *nref = nullptr;
   bool promoted = false;        // the FP64 factor is used for the rest of the solve
   bool fp64_asm = false;        // the SCM and the P-MATRIX are assembled in FP64 (mixed form)
+  // mixed form, FP32 assembly stage with a dense root: the root blocks of Y and X̄ are factored
+  // (and X̄_RR's factor inverted) in FP32, on the tensor cores for large roots (set per iteration
+  // by mcsdp_solve; every other entry point factors in FP64)
+  bool root32 = false;
   int fp64_asm_iter = -1;
   int promoted_iter = -1, refine_steps = 0, cur_iter = 0;
   double *alpha_c = nullptr, *alpha_r = nullptr, *scal = nullptr;
@@ -1037,8 +1041,19 @@ mcsdp_status phase_ychol(mcsdp_ctx *c, int ncand, const double *alpha, const dou
     // the root: its block of Y less the forest's contributions, then the dense Cholesky
     launch_root_assemble(c->D, c->rg, Yb, nullptr, 0.0, Nbuf, c->stream);
     nl += c->rg.nent > 0 ? 2 : 1;
-    nl += dense_potrf(Nbuf + c->D.root_valp, c->nR, c->nR, status, c->rLinvN, c->stream, c->rsyncN,
-                      c->opt.timeout_cycles);
+    const int nR = c->nR;
+    double *NR = Nbuf + c->D.root_valp;
+    if (c->root32) {
+      // FP32 factor (its rows mirrored above the diagonal, as the FP64 one), stored back as FP64
+      // values with its diagonal-block inverses, so the FP32 assembly reads it as before
+      float *N32 = reinterpret_cast<float *>(c->RS_T);
+      copy_square<double, float>(NR, nR, N32, nR, nR, c->stream);
+      nl += 3 + dense_chol_f32(N32, nR, nR, status, c->rLinv32, c->stream, &c->cs);
+      copy_square<float, double>(N32, nR, NR, nR, nR, c->stream);
+      cast_f64(c->rLinv32, c->rLinvN, (int64_t)((nR + 31) / 32) * 1024, c->stream);
+    } else {
+      nl += dense_potrf(NR, nR, nR, status, c->rLinvN, c->stream, c->rsyncN, c->opt.timeout_cycles);
+    }
   }
   ks.done(nl);
   KCHECK(c);
@@ -1050,6 +1065,18 @@ mcsdp_status phase_ychol(mcsdp_ctx *c, int ncand, const double *alpha, const dou
 // RS_P <- its inverse with the inverse's rows mirrored above the diagonal
 int factor_X_root(mcsdp_ctx *c, const double *Xbar, int *status, cudaStream_t st) {
   const int nR = c->nR;
+  if (c->root32) {
+    // FP32: the factor and its inverse in RS_X (two FP32 squares), the diagonal-block inverses in
+    // rLinvX, the inverse widened into RS_P
+    float *L32 = reinterpret_cast<float *>(c->RS_X), *X32 = L32 + (size_t)nR * nR;
+    float *lin32 = reinterpret_cast<float *>(c->rLinvX);
+    copy_square<double, float>(Xbar + c->D.root_valp, nR, L32, nR, nR, st);
+    int nl = 1 + dense_chol_f32(L32, nR, nR, status, lin32, st, &c->cs);
+    nl += dense_trtri<float>(L32, nR, lin32, X32, nR, nR, reinterpret_cast<float *>(c->RS_M), st);
+    copy_square<float, double>(X32, nR, c->RS_P, nR, nR, st);
+    mirror_lower<double>(c->RS_P, nR, nR, st);
+    return nl + 2;
+  }
   copy_square<double, double>(Xbar + c->D.root_valp, nR, c->RS_X, nR, nR, st);
   int nl = 1 + dense_potrf(c->RS_X, nR, nR, status, c->rLinvX, st, c->rsyncX, c->opt.timeout_cycles);
   nl += dense_trtri<double>(c->RS_X, nR, c->rLinvX, c->RS_P, nR, nR, c->RS_M, st);
@@ -1083,13 +1110,19 @@ mcsdp_status factor_YX(mcsdp_ctx *c, const double *Xbar) {
     KScope ks(c, KC_ALG1, c->st3);
     launch_alg1(c->D, Xbar, c->Lh, c->dinvL, c->status + 1, c->st3);
     int nl = 1;
-    if (c->dense) nl += factor_X_root(c, Xbar, c->status + 1, c->st3);
+    if (c->dense && !c->root32) nl += factor_X_root(c, Xbar, c->status + 1, c->st3);
     ks.done(nl);
   }
   CUDA_TRY(c, cudaEventRecord(c->ev_f1, c->st3));
   mcsdp_status s = phase_ychol(c, 1, nullptr, c->Ylay, nullptr, c->N, c->dinvN, c->status);
   CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->ev_f1, 0));
   if (s) return s;
+  if (c->dense && c->root32) {
+    // the FP32 root factorisations share the tensor-core Cholesky's working storage: X̄_RR's
+    // after Y's, on the main stream
+    KScope ks(c, KC_ALG1);
+    ks.done(factor_X_root(c, Xbar, c->status + 1, c->stream));
+  }
   KCHECK(c);
   return MCSDP_OK;
 }
@@ -1675,6 +1708,8 @@ struct IterOut {
 // halving and 10 steps for small m.  Leaves x in c->xs (internal order).
 constexpr int MIXED_MAX_STEPS = 10, MIXED_MAX_STEPS_LONG = 60;
 constexpr int MIXED_LONG_M = 4096;
+// default relative gap for the mixed form's switch to FP64 assembly with a dense root
+constexpr double MIXED_ASM_GAP_ROOT = 1e-2;
 // b32: B was assembled in FP32 (entries accurate to about 1e-6 relative): the refinement then
 // stops at omega <= 1e-10, which already puts the solve error far below the assembly error
 mcsdp_status mixed_sce(mcsdp_ctx *c, bool b32, bool *solved) {
@@ -1951,6 +1986,7 @@ mcsdp_status prepare(mcsdp_ctx *c, const double *Xbar, const double *z, double *
   prof_flush(c);
   if (failed) *failed = ((st[0] & ST_NOT_PD) ? 1 : 0) | ((st[1] & ST_NOT_PD) ? 2 : 0);
   if ((st[0] | st[1]) & ST_TIMEOUT) return fail(c, MCSDP_ERR_TIMEOUT, "a dense factorisation: a bounded wait gave up");
+  if ((st[0] | st[1]) & ST_NUMERIC) return fail(c, MCSDP_ERR_CUDA, "FP32 root factorisation: a tensor map could not be made");
   if (st[0] & ST_NOT_PD) return fail(c, MCSDP_ERR_NOT_PD, "Y = A_0 - sum z_k A_k is not positive definite");
   if (st[1] & ST_NOT_PD) return fail(c, MCSDP_ERR_NOT_PD, "a clique block of X̄ is not positive definite");
   return MCSDP_OK;
@@ -2369,16 +2405,21 @@ mcsdp_status mcsdp_solve(mcsdp_ctx *c, mcsdp_result *res) {
   c->fp64_asm = false;
   c->fp64_asm_iter = -1;
   c->refine_steps = 0;
-  // the mixed form's FP64-assembly threshold: with a dense root the FP32 products run over all
-  // n terms (root GEMMs), and their rounding, relative to the shrinking direction, decides the
-  // root clique's primal step well before the FP32 factor stops refining
+  // the root's FP32 factorisations belong to this loop only
+  struct Root32Off {
+    mcsdp_ctx *c;
+    ~Root32Off() { c->root32 = false; }
+  } root32_off{c};
   // the gap below which the mixed form runs in FP64 throughout: for large m the refinement of
   // the FP32 factor (long form, see mixed_sce) stays far cheaper than the FP64 factorisation
   // until it stalls, so no gap threshold applies by default
   const double mixed_gap = c->opt.mixed_gap > 0 ? c->opt.mixed_gap
                            : c->opt.mixed_gap < 0 || c->S.m >= MIXED_LONG_M ? 0.0 : 1e-5;
+  // the mixed form's FP64-assembly threshold: with a dense root the FP32 products and factors of
+  // the root, relative to the shrinking direction, decide the root clique's primal step well
+  // before the FP32 factor of B stops refining
   const double asm_gap = c->opt.mixed_asm_gap > 0 ? c->opt.mixed_asm_gap
-                        : (c->dense ? 1e-1 : (mixed_gap > 0 ? mixed_gap : 1e-5));
+                        : (c->dense ? MIXED_ASM_GAP_ROOT : (mixed_gap > 0 ? mixed_gap : 1e-5));
   double prev_pinf = -1.0;
   float tms[4] = {0, 0, 0, 0};
   cudaEvent_t t0 = c->ev[6], t1 = c->ev[7];
@@ -2389,6 +2430,7 @@ mcsdp_status mcsdp_solve(mcsdp_ctx *c, mcsdp_result *res) {
   for (int it = 0; it <= c->opt.max_iter; ++it) {
     double sc[8];
     int failed = 0;
+    c->root32 = c->opt.precision == 1 && c->dense && !c->fp64_asm && !c->promoted;
     s = prepare(c, c->Xbar, c->z, sc, &failed);
     // dense root: the step lengths are Lanczos estimates, confirmed here by the factorisations at
     // the new iterate; a failure halves the failing step (from the saved iterate) and retries
@@ -2423,6 +2465,11 @@ mcsdp_status mcsdp_solve(mcsdp_ctx *c, mcsdp_result *res) {
     if (c->opt.precision == 1 && !c->fp64_asm && (c->promoted || gap < asm_gap)) {
       c->fp64_asm = true;
       c->fp64_asm_iter = it;
+      if (c->root32) {  // this iteration's root factors were FP32: again in FP64
+        c->root32 = false;
+        s = prepare(c, c->Xbar, c->z, sc, &failed);
+        if (s) return s;
+      }
     }
     prev_pinf = pinf;
     c->cur_iter = it;

@@ -5,7 +5,8 @@ The point differentiated is the central-path point for the iterate's mu (mcsdp_b
 autograd.solve_layer).  Two solves of the same problem:
 
 * stopped after 16 iterations (relative gap about 0.07, mu about 3e-3, cond(Y) about 5e4): there
-  the central point is computed to a residual of 1e-12 or better, so (a) central finite
+  both centrings reach their rounding level (about 1e-10 relative on the device, whose Y^{-1}
+  comes from sparse triangular solves, below that on the host), so (a) central finite
   differences of the device path itself at h = 1e-6 (each perturbed problem re-centred on the
   device at the same mu) match the gradients within 1e-5 of the largest gradient, for 4 entries
   of b and 4 input entries (diagonal and off-diagonal, of A_0 and of the A_k), and (b) the
@@ -96,9 +97,11 @@ def test_config5_early_finite_differences(case):
     A = SparseSym.from_instance(inst)
     n = inst.n
     mu = float(np.sum(Xc * dual_slack(A, zc))) / n
-    # the residual of that point, evaluated here in FP64
+    # the residual of that point, evaluated here in FP64 (the device's centring stops at its own
+    # rounding level, about 1e-10 here: eps cond(Y) |A||X| / |b| with cond(Y) about 5e4)
     F = A.op(mu * np.linalg.inv(dual_slack(A, zc))) - inst.b
-    assert np.max(np.abs(F)) / max(1.0, np.max(np.abs(inst.b))) <= 1e-12
+    res = np.max(np.abs(F)) / max(1.0, np.max(np.abs(inst.b)))
+    assert res <= 1e-9
 
     def central_loss(inst2):
         A2 = SparseSym.from_instance(inst2)
@@ -118,7 +121,7 @@ def test_config5_early_finite_differences(case):
         bm[p] -= h
         fd = (central_loss(dataclasses.replace(inst, b=bp)) -
               central_loss(dataclasses.replace(inst, b=bm))) / (2 * h)
-        assert abs(fd - gb[p]) <= 1e-5 * scale, (p, fd, gb[p])
+        assert abs(fd - gb[p]) <= 1e-5 * scale, (p, fd, gb[p], scale, res)
     mats, rows, cols = inst.mat, inst.row, inst.col
     picks = [int(np.flatnonzero((mats == 0) & (rows == cols))[3]),
              int(np.flatnonzero((mats == 0) & (rows != cols))[5]),
@@ -130,12 +133,12 @@ def test_config5_early_finite_differences(case):
         vm[e] -= h
         fd = (central_loss(dataclasses.replace(inst, val=vp)) -
               central_loss(dataclasses.replace(inst, val=vm))) / (2 * h)
-        assert abs(fd - ge[e]) <= 1e-5 * scale, (e, fd, ge[e])
+        assert abs(fd - ge[e]) <= 1e-5 * scale, (e, fd, ge[e], scale, res)
     # the oracle's adjoint at the same mu
     gb_o, ge_o, mu_o, res = _oracle_grads(c, inst, W, X, z)
-    assert res <= 1e-12
-    assert np.max(np.abs(gb - gb_o)) <= 1e-8 * scale
-    assert np.max(np.abs(ge - ge_o)) <= 1e-8 * scale
+    assert res <= 1e-9
+    assert np.max(np.abs(gb - gb_o)) <= 1e-8 * scale, np.max(np.abs(gb - gb_o)) / scale
+    assert np.max(np.abs(ge - ge_o)) <= 1e-8 * scale, np.max(np.abs(ge - ge_o)) / scale
 
 
 def test_config5_converged_gradients(case):
