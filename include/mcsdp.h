@@ -86,7 +86,8 @@ typedef struct {
   int32_t precision;     /* 0 = FP64.  1 = mixed: the SCM solves and contraction (K3) and the
                             P-MATRIX solves (K6) run in FP32 from FP32 copies of L̂ and N; the
                             SCE B dz = g is solved with an FP32 Cholesky factor of B and FP64
-                            iterative refinement against the stored B; Y's factor, Algorithm 1,
+                            iterative refinement against the stored B (for m >= 4096: the factor
+                            of the diagonally equilibrated B, and GMRES preconditioned by it); Y's factor, Algorithm 1,
                             the step lengths and the update stay FP64 (with a dense root, see
                             mixed_asm_gap).  The solve promotes to
                             FP64 throughout once the relative gap falls below mixed_gap, the
@@ -107,9 +108,9 @@ typedef struct {
   int32_t solve_warps;   /* unused (kept for layout compatibility) */
   double mixed_gap;      /* mixed form: relative gap below which every stage runs in FP64.
                             0 = default: 1e-5 for m < 4096; none for m >= 4096, where the
-                            refinement runs up to 60 steps while it contracts by 0.9 per step
-                            and the solve promotes only when it stalls or the FP32 factor
-                            breaks down; < 0 = none */
+                            correction is GMRES preconditioned by the FP32 factor and the solve
+                            promotes only when it stalls or the FP32 factor breaks down;
+                            < 0 = none */
   int32_t root_rows;     /* dense root: cliques with more than this many rows (or more than 96
                             columns) are merged, with all their ancestors, into one root clique R
                             handled by dense kernels; the other cliques keep the small-clique
@@ -179,7 +180,8 @@ typedef struct {
                                             rest), CUDA events */
   int32_t precision;     /* the option the solve ran with */
   int32_t promoted_iter; /* mixed form: first iteration solved with the FP64 factor, -1 if none */
-  int32_t refine_steps;  /* mixed form: FP64 refinement steps over the solve */
+  int32_t refine_steps;  /* mixed form: FP64 refinement steps over the solve (GMRES steps for
+                            m >= 4096) */
   int32_t assembly_iter; /* mixed form: first iteration with the SCM and P-MATRIX in FP64, -1 if
                             none */
 } mcsdp_result;

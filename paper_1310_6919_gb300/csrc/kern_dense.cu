@@ -1227,7 +1227,8 @@ void launch_B_to_user(const DevSym &S, const double *Bi, int64_t ldi, double *Bo
 // tile rounded to FP32 (ld m), and the FP64 B made fully symmetric (the tile's transpose written
 // into the strict upper triangle, staged through shared memory so both sides are coalesced), so
 // the refinement's matrix-vector product is a plain column-major product.
-__global__ void k_mixed_prep(double *B, int64_t ldb, float *B32, int m) {
+__global__ void k_mixed_prep(double *B, int64_t ldb, float *B32, int m,
+                             const double *__restrict__ dsc, double shift) {
   __shared__ double t[32][33];
   const int ti = blockIdx.x, tj = blockIdx.y;
   if (ti < tj) return;
@@ -1238,7 +1239,7 @@ __global__ void k_mixed_prep(double *B, int64_t ldb, float *B32, int m) {
     double v = 0.0;
     if (i < m && j < m && i >= j) {
       v = B[i + (int64_t)j * ldb];
-      B32[i + (int64_t)j * m] = (float)v;
+      B32[i + (int64_t)j * m] = (float)((dsc ? v * dsc[i] * dsc[j] : v) + (i == j ? shift : 0.0));
     }
     t[lx][c] = v;
   }
@@ -1392,7 +1393,7 @@ __global__ void __launch_bounds__(TP) k_trsv_panel(const float *__restrict__ L, 
   static_assert(NB * NB == TP, "one inverse entry per thread");
   __shared__ float ys[TP];
   __shared__ float yb[NB];
-  __shared__ float ls[2][NB * NB];
+  __shared__ float ls[2][NB * (NB + 1)];  // row r of the inverse at r (NB + 1): conflict-free
   const int pw = min(TP, m - k0), t = threadIdx.x, lane = t & 31;
   if (t < pw) ys[t] = y[k0 + t];
   const int nb_tot = (pw + NB - 1) / NB;
@@ -1414,7 +1415,8 @@ __global__ void __launch_bounds__(TP) k_trsv_panel(const float *__restrict__ L, 
       lv[c] = (need && c < nb) ? L[row + (int64_t)(k0 + b0 + c) * m] : 0.f;
   };
   auto load_inv = [&](int b, int buf) {
-    ls[buf][t] = Linv[(int64_t)((k0 + b * NB) / NB) * NB * NB + t];
+    // Linv column-major (entry (r, c) at r + c NB), stored at r + c (NB + 1)
+    ls[buf][(t % NB) + (t / NB) * (NB + 1)] = Linv[(int64_t)((k0 + b * NB) / NB) * NB * NB + t];
   };
   load_row(first_of(0));
   load_inv(first_of(0), 0);
@@ -1428,7 +1430,8 @@ __global__ void __launch_bounds__(TP) k_trsv_panel(const float *__restrict__ L, 
       float v = 0.f;
 #pragma unroll
       for (int l = 0; l < NB; ++l)
-        v = fmaf(FWD ? Li[lane + l * NB] : Li[l + lane * NB], __shfl_sync(0xffffffffu, rl, l), v);
+        v = fmaf(FWD ? Li[lane + l * (NB + 1)] : Li[l + lane * (NB + 1)],
+                 __shfl_sync(0xffffffffu, rl, l), v);
       if (lane < nb) ys[b0 + lane] = v;
       yb[lane] = lane < nb ? v : 0.f;
     }
@@ -1479,19 +1482,22 @@ __global__ void __launch_bounds__(256) k_trsv_update(const float *__restrict__ L
   }
 }
 
-__global__ void k_trsv_load(const double *__restrict__ r, float *y, int m) {
+// y = S r in FP32, and x += S y in FP64, S = diag(dsc) (the factor's equilibration; none if null)
+__global__ void k_trsv_load(const double *__restrict__ r, float *y, int m,
+                            const double *__restrict__ dsc) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
-    y[i] = (float)r[i];
+    y[i] = (float)(dsc ? r[i] * dsc[i] : r[i]);
 }
-__global__ void k_trsv_store(const float *__restrict__ y, double *x, int m) {
+__global__ void k_trsv_store(const float *__restrict__ y, double *x, int m,
+                             const double *__restrict__ dsc) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
-    x[i] += (double)y[i];
+    x[i] += dsc ? (double)y[i] * dsc[i] : (double)y[i];
 }
 
 static int trsv_blocked(const float *L, int m, const float *Linv, const double *r, double *x,
-                        float *y, cudaStream_t st) {
+                        float *y, const double *dsc, cudaStream_t st) {
   const int blocks = std::min(152 * 8, (m + 255) / 256);
-  k_trsv_load<<<blocks, 256, 0, st>>>(r, y, m);
+  k_trsv_load<<<blocks, 256, 0, st>>>(r, y, m, dsc);
   int nl = 2;
   for (int k0 = 0; k0 < m; k0 += TP) {
     const int pw = std::min(TP, m - k0);
@@ -1512,7 +1518,7 @@ static int trsv_blocked(const float *L, int m, const float *Linv, const double *
       ++nl;
     }
   }
-  k_trsv_store<<<blocks, 256, 0, st>>>(y, x, m);
+  k_trsv_store<<<blocks, 256, 0, st>>>(y, x, m, dsc);
   return nl;
 }
 
@@ -1606,22 +1612,33 @@ __global__ void k_mixed_init(const double *__restrict__ B, int64_t ldb, int m, d
 
 int mixed_chunks(int m) { return (m + MV_CHUNK - 1) / MV_CHUNK; }
 
+// dsc[i] = 1 / sqrt(B_ii) (1 where B_ii <= 0: the factorisation then reports the breakdown)
+__global__ void k_mixed_scale(const double *__restrict__ B, int64_t ldb, int m, double *dsc) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    const double d = B[i + (int64_t)i * ldb];
+    dsc[i] = d > 0.0 ? 1.0 / sqrt(d) : 1.0;
+  }
+}
+
 int mixed_factor(double *B, int64_t ldb, int m, float *B32, float *Linv32, int *status,
-                 double *g, double *r, double *x, cudaStream_t st, CholStreams *cs) {
+                 double *g, double *r, double *x, double *dsc, double shift, cudaStream_t st,
+                 CholStreams *cs) {
   k_mixed_init<<<(m + 255) / 256, 256, 0, st>>>(B, ldb, m, g, r, x);
   const int nt = (m + 31) / 32;
-  k_mixed_prep<<<dim3(nt, nt), 256, 0, st>>>(B, ldb, B32, m);
+  const bool eq = dsc && m >= TRSV_WIDE_M;
+  if (eq) k_mixed_scale<<<(m + 255) / 256, 256, 0, st>>>(B, ldb, m, dsc);
+  k_mixed_prep<<<dim3(nt, nt), 256, 0, st>>>(B, ldb, B32, m, eq ? dsc : nullptr, shift);
   // the factorisation leaves L^T in the strict upper triangle of B32 as well
-  return 2 + dense_chol_f32(B32, m, m, status, Linv32, st, cs);
+  return 2 + (eq ? 1 : 0) + dense_chol_f32(B32, m, m, status, Linv32, st, cs);
 }
 
 int mixed_refine_step(const double *B, int64_t ldb, int m, const float *L32, const float *Linv32,
                       const double *g, double *x, double *r, double *P, double *A, double *norms,
-                      cudaStream_t st) {
+                      const double *dsc, cudaStream_t st) {
   int nl = 2;
   if (m >= TRSV_WIDE_M) {
     // P (chunks x m doubles) is free until the product below: the FP32 vector
-    nl += trsv_blocked(L32, m, Linv32, r, x, reinterpret_cast<float *>(P), st);
+    nl += trsv_blocked(L32, m, Linv32, r, x, reinterpret_cast<float *>(P), dsc, st);
   } else {
     ++nl;
     const size_t smem = (size_t)m * sizeof(float);
@@ -1632,6 +1649,40 @@ int mixed_refine_step(const double *B, int64_t ldb, int m, const float *L32, con
   k_gemv_part<<<dim3((m + 31) / 32, nch), 256, 0, st>>>(B, ldb, m, x, P, A);
   k_resid<<<1, 1024, 0, st>>>(g, P, A, nch, r, m, norms);
   return nl;
+}
+
+// The pieces of the GMRES form of the mixed SCE solve (large m): out = B v (the full symmetric
+// FP64 B, the refinement's partial products summed per row in a fixed order), w = S M^{-1} S u
+// with M = L32 L32^T the FP32 factor of the equilibrated S B S (the blocked substitutions), and
+// the true residual r = g - B x with its norms.
+__global__ void k_sum_parts(const double *__restrict__ P, int nchunk, int m, double *out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    double y = 0.0;
+    for (int q = 0; q < nchunk; ++q) y += P[(int64_t)q * m + i];
+    out[i] = y;
+  }
+}
+
+int mixed_matvec(const double *B, int64_t ldb, int m, const double *v, double *out, double *P,
+                 double *A, cudaStream_t st) {
+  const int nch = mixed_chunks(m);
+  k_gemv_part<<<dim3((m + 31) / 32, nch), 256, 0, st>>>(B, ldb, m, v, P, A);
+  k_sum_parts<<<std::min(152 * 8, (m + 255) / 256), 256, 0, st>>>(P, nch, m, out);
+  return 2;
+}
+
+int mixed_precond(const float *L32, int m, const float *Linv32, const double *u, double *w,
+                  double *P, const double *dsc, cudaStream_t st) {
+  cudaMemsetAsync(w, 0, (size_t)m * sizeof(double), st);
+  return trsv_blocked(L32, m, Linv32, u, w, reinterpret_cast<float *>(P), dsc, st);
+}
+
+int mixed_residual(const double *B, int64_t ldb, int m, const double *g, const double *x,
+                   double *r, double *P, double *A, double *norms, cudaStream_t st) {
+  const int nch = mixed_chunks(m);
+  k_gemv_part<<<dim3((m + 31) / 32, nch), 256, 0, st>>>(B, ldb, m, x, P, A);
+  k_resid<<<1, 1024, 0, st>>>(g, P, A, nch, r, m, norms);
+  return 2;
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -630,6 +630,9 @@ void lz_reorth(int n, int jcount, double *w, const double *Qd, const double *Q, 
   k_lz_dots<<<jcount, 512, 0, st>>>(n, w, Qd, h);
   k_lz_sub<<<(n + 255) / 256, 256, 0, st>>>(n, jcount, w, Q, h);
 }
+void lz_sub(int n, int jcount, double *w, const double *Q, const double *h, cudaStream_t st) {
+  k_lz_sub<<<(n + 255) / 256, 256, 0, st>>>(n, jcount, w, Q, h);
+}
 void lz_beta(int n, const double *w, const double *gw, double *vnext, double *gvnext, double *s,
              int j, cudaStream_t st) {
   k_lz_beta<<<1, 1024, 0, st>>>(n, w, gw, vnext, gvnext, s, j);

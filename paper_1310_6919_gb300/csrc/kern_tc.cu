@@ -285,10 +285,42 @@ __global__ void k_split_tf32(const float *__restrict__ a, int64_t lda_r, int64_t
   }
 }
 
+// the same for a column-major source (lda_r = 1), through 32 x 32 shared-memory tiles: reads run
+// down the source's columns and the K-major writes (and the transposed copy) along the rows, both
+// coalesced
+__global__ void k_split_tf32_cm(const float *__restrict__ a, int64_t lda_c, int rows, int cols,
+                                float *hi, float *lo, int64_t ldo, float *tdst, int64_t tld) {
+  __shared__ float t[32][33];
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int cc = ty; cc < 32; cc += 8) {
+    const int r = r0 + tx, c = c0 + cc;
+    t[cc][tx] = (r < rows && c < cols) ? a[r + (int64_t)c * lda_c] : 0.f;
+  }
+  __syncthreads();
+  for (int rr = ty; rr < 32; rr += 8) {
+    const int r = r0 + rr, c = c0 + tx;
+    if (r >= rows || c >= cols) continue;
+    const float x = t[tx][rr];
+    uint32_t h, l;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    const float d = x - __uint_as_float(h);
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(d));
+    hi[c + (int64_t)r * ldo] = __uint_as_float(h);
+    lo[c + (int64_t)r * ldo] = __uint_as_float(l);
+    if (tdst) tdst[c + (int64_t)r * tld] = x;
+  }
+}
+
 void split_tf32(const float *a, int64_t lda_r, int64_t lda_c, int rows, int cols, float *hi,
                 float *lo, int64_t ldo, float *tdst, int64_t tld, cudaStream_t st) {
   const int64_t cnt = (int64_t)rows * cols;
   if (cnt <= 0) return;
+  if (lda_r == 1 && cols <= 32 * 65535) {
+    dim3 grid((rows + 31) / 32, (cols + 31) / 32), blk(32, 8);
+    k_split_tf32_cm<<<grid, blk, 0, st>>>(a, lda_c, rows, cols, hi, lo, ldo, tdst, tld);
+    return;
+  }
   const int blocks = (int)std::min<int64_t>(8192, (cnt + 255) / 256);
   k_split_tf32<<<blocks, 256, 0, st>>>(a, lda_r, lda_c, rows, cols, hi, lo, ldo, tdst, tld);
 }

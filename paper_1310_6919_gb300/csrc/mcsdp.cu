@@ -47,6 +47,9 @@ struct Chunk {
 
 constexpr int NCAND = 16;  // candidates per dual step-length round
 constexpr int LZ_MAX = 64;  // Lanczos steps of the dense-root step-length bounds
+// mixed form: from this m on the SCE is solved by GMRES preconditioned with the FP32 factor
+constexpr int MIXED_LONG_M = 4096;
+constexpr int GM_K = 40, GM_CYCLES = 8;  // GMRES restart length and cycles
 // the largest clique (rows / columns) the shared-memory clique kernels take: Algorithm 1 and the
 // primal step stage two k x k FP64 blocks (2 k^2 8 B <= 208 KB at k = 112)
 constexpr int SMALL_ROWS = 112, SMALL_COLS = 96;
@@ -131,6 +134,8 @@ struct mcsdp_ctx {
   float *L32 = nullptr, *N32 = nullptr, *dL32 = nullptr, *dN32 = nullptr;  // FP32 factor copies
   bool f32_solves = false;      // the FP32 SCM / P-MATRIX solves fit the staged kernels
   double *gref = nullptr, *rref = nullptr, *yref = nullptr, *ayref = nullptr, *nref = nullptr;
+  double *dscl = nullptr;  // the mixed factor's equilibration (large m)
+  double *gmV = nullptr, *gmH = nullptr;  // GMRES basis and small vectors (large m)
   bool promoted = false;        // the FP64 factor is used for the rest of the solve
   bool fp64_asm = false;        // the SCM and the P-MATRIX are assembled in FP64 (mixed form)
   // mixed form, FP32 assembly stage with a dense root: the root blocks of Y and X̄ are factored
@@ -782,6 +787,10 @@ void plan_workspace(mcsdp_ctx *c) {
     plan_buf(c, cur, "yref", mx ? (size_t)mixed_chunks(m) * m * 8 : 0);
     plan_buf(c, cur, "ayref", mx ? (size_t)mixed_chunks(m) * m * 8 : 0);
     plan_buf(c, cur, "nref", 4 * 8);
+    plan_buf(c, cur, "dscl", mx ? (size_t)m * 8 : 0);
+    const bool gm = mx && m >= MIXED_LONG_M;
+    plan_buf(c, cur, "gmV", gm ? (size_t)(GM_K + 2) * m * 8 : 0);
+    plan_buf(c, cur, "gmH", gm ? (size_t)6 * (GM_K + 2) * 8 : 0);
     const bool tc = mx && c->opt.tensor_cores != 0 && m >= 2 * TC_PANEL;
     plan_buf(c, cur, "tc_hi", tc ? (size_t)tc_panel(m) * m * 4 : 0);
     plan_buf(c, cur, "tc_lo", tc ? (size_t)tc_panel(m) * m * 4 : 0);
@@ -936,6 +945,9 @@ void bind_pointers(mcsdp_ctx *c) {
   c->yref = wsp<double>(c, "yref");
   c->ayref = wsp<double>(c, "ayref");
   c->nref = wsp<double>(c, "nref");
+  c->dscl = wsp<double>(c, "dscl");
+  c->gmV = wsp<double>(c, "gmV");
+  c->gmH = wsp<double>(c, "gmH");
   {
     const bool tc = c->opt.precision == 1 && c->opt.tensor_cores != 0 && c->S.m >= 2 * TC_PANEL;
     c->cs.tc_hi = tc ? wsp<float>(c, "tc_hi") : nullptr;
@@ -1695,46 +1707,79 @@ struct IterOut {
   double mu, pobj, dobj, gap, pinf, ap, ad;
 };
 
-// Mixed form of the SCE solve B dz = g (eq. SCE): Cholesky factor of B rounded to FP32, then
-// iterative refinement with the residual g - B x formed in FP64 from the FP64 B (the scheme of
-// LAPACK's dsposv).  Measure of convergence: omega = max|r| / max(|B||x| + |g|).  Success when
-// omega <= sqrt(m) eps64 (FP64-assembled B); the refinement is abandoned (*solved = false, B
-// untouched) when the FP32 factorisation breaks down, when omega fails to shrink by the factor
-// MIXED_RATE in two consecutive steps while still above m eps64 (the worst-case backward error of
-// the FP64 factorisation itself), or after the step budget.  Refinement contracts by about
-// cond(B) eps32 per step; for large m (from MIXED_LONG_M on) a step (substitutions over all SMs
-// plus an FP64 product with B, O(m^2)) costs a few hundredths of the FP64 factorisation
-// (O(m^3)), so slow contraction is still worth following there: rate 0.9 and 60 steps, against
-// halving and 10 steps for small m.  Leaves x in c->xs (internal order).
-constexpr int MIXED_MAX_STEPS = 10, MIXED_MAX_STEPS_LONG = 60;
-constexpr int MIXED_LONG_M = 4096;
+// Mixed form of the SCE solve B dz = g (eq. SCE): Cholesky factor of B rounded to FP32 (for
+// m >= MIXED_LONG_M of the equilibrated S B S, S = diag(B_ii^{-1/2}), on the tensor cores), then an
+// FP64 correction against the stored B.  Measure of convergence: omega = max|r| / max(|B||x| + |g|)
+// with r = g - B x formed in FP64.  Success when omega <= sqrt(m) eps64 (FP64-assembled B) or
+// 1e-10 (b32: B was assembled in FP32, entries accurate to about 1e-6 relative, so the solve
+// error is then far below the assembly error); otherwise (*solved = false, B untouched) the
+// caller promotes to the FP64 factorisation, as it does when the FP32 factorisation breaks down.
+//   small m: iterative refinement (the scheme of LAPACK's dsposv), abandoned when omega fails to
+//   halve in two consecutive steps while above m eps64 (the worst-case backward error of the FP64
+//   factorisation itself), or after MIXED_MAX_STEPS steps;
+//   large m: refinement contracts by about cond(B) eps32 per step, slowly near the optimum, so the
+//   correction is restarted GMRES(GM_K) on B x = g left-preconditioned by the FP32 factor (the
+//   GMRES-based refinement of Carson and Higham), Arnoldi in FP64 with classical Gram-Schmidt
+//   applied twice, the small least-squares problem by Givens rotations on the host, omega from
+//   the true residual after each cycle (a cycle stops once the preconditioned residual has
+//   fallen by 1e-7: the FP32 preconditioner bounds what one cycle gains); abandoned when a cycle
+//   fails to halve omega above m eps64 or after GM_CYCLES cycles.  When the FP32 factor of S B S
+//   breaks down near the optimum, the factor of S B S + sigma I (sigma = 1e-6, then 1e-4)
+//   preconditions the same GMRES on B.  An Arnoldi step (the substitutions over all SMs and one
+//   FP64 product with B, O(m^2)) costs about a thousandth of the FP64 factorisation (O(m^3)).
+// Leaves x in c->xs (internal order).
+constexpr int MIXED_MAX_STEPS = 10;
 // default relative gap for the mixed form's switch to FP64 assembly with a dense root
 constexpr double MIXED_ASM_GAP_ROOT = 1e-2;
-// b32: B was assembled in FP32 (entries accurate to about 1e-6 relative): the refinement then
-// stops at omega <= 1e-10, which already puts the solve error far below the assembly error
+
+mcsdp_status mixed_gmres(mcsdp_ctx *c, double tol_ok, double tol_stall, bool *solved);
+
 mcsdp_status mixed_sce(mcsdp_ctx *c, bool b32, bool *solved) {
   const int m = c->S.m;
   *solved = false;
+  const double eps = std::ldexp(1.0, -53);
+  const double tol_ok = b32 ? 1e-10 : std::sqrt((double)m) * eps;
+  const double tol_stall = b32 ? 1e-10 : (double)m * eps;
+  if (m >= MIXED_LONG_M && c->gmV) {
+    // GMRES form: when the FP32 factor of S B S breaks down, that of S B S + sigma I (unit
+    // diagonal, sigma = 1e-6, then 1e-4) still preconditions GMRES on B itself
+    const double shifts[3] = {0.0, 1e-6, 1e-4};
+    for (double sigma : shifts) {
+      CUDA_TRY(c, cudaMemsetAsync(c->status + 4, 0, sizeof(int), c->stream));
+      {
+        KScope k1(c, KC_CHOL32);
+        k1.done(mixed_factor(c->B, c->ldb, m, c->B32, c->Linv32, c->status + 4, c->gref, c->rref,
+                             c->xs, c->dscl, sigma, c->stream, &c->cs));
+      }
+      KCHECK(c);
+      int fst = 0;
+      CUDA_TRY(c, cudaMemcpyAsync(&fst, c->status + 4, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+      CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+      prof_flush(c);
+      if (fst & ST_TIMEOUT) return fail(c, MCSDP_ERR_TIMEOUT, "FP32 factorisation: a bounded wait gave up");
+      if (fst & ST_NUMERIC) return fail(c, MCSDP_ERR_CUDA, "FP32 factorisation: a tensor map could not be made");
+      if (fst & ST_NOT_PD) {
+        if (c->opt.verbose > 1) std::fprintf(stderr, "  FP32 factor (shift %.0e) broke down\n", sigma);
+        continue;
+      }
+      return mixed_gmres(c, tol_ok, tol_stall, solved);
+    }
+    return MCSDP_OK;  // every FP32 factor broke down: promote
+  }
   CUDA_TRY(c, cudaMemsetAsync(c->status + 4, 0, sizeof(int), c->stream));
   {
     KScope k1(c, KC_CHOL32);
     k1.done(mixed_factor(c->B, c->ldb, m, c->B32, c->Linv32, c->status + 4, c->gref, c->rref,
-                         c->xs, c->stream, &c->cs));
+                         c->xs, c->dscl, 0.0, c->stream, &c->cs));
   }
   KCHECK(c);
-  const double eps = std::ldexp(1.0, -53);
-  const double tol_ok = b32 ? 1e-10 : std::sqrt((double)m) * eps;
-  const double tol_stall = b32 ? 1e-10 : (double)m * eps;
   double prev = 1.0;
   int slow = 0;
-  const bool long_m = m >= MIXED_LONG_M;
-  const int max_steps = long_m ? MIXED_MAX_STEPS_LONG : MIXED_MAX_STEPS;
-  const double rate = long_m ? 0.9 : 0.5;
-  for (int k = 0; k < max_steps; ++k) {
+  for (int k = 0; k < MIXED_MAX_STEPS; ++k) {
     {
       KScope k2(c, KC_BSOLVE);
       k2.done(mixed_refine_step(c->B, c->ldb, m, c->B32, c->Linv32, c->gref, c->xs, c->rref,
-                                c->yref, c->ayref, c->nref, c->stream));
+                                c->yref, c->ayref, c->nref, c->dscl, c->stream));
     }
     KCHECK(c);
     double nr[2];
@@ -1754,8 +1799,106 @@ mcsdp_status mixed_sce(mcsdp_ctx *c, bool b32, bool *solved) {
       *solved = true;
       return MCSDP_OK;
     }
-    slow = (omega > rate * prev) ? slow + 1 : 0;
+    slow = (omega > 0.5 * prev) ? slow + 1 : 0;
     if (slow >= 2) {
+      *solved = omega <= tol_stall;
+      return MCSDP_OK;
+    }
+    prev = omega;
+  }
+  return MCSDP_OK;
+}
+
+// the GMRES form (see mixed_sce).  On entry x = 0, r = g.  Device vectors: V holds the basis
+// (GM_K + 1 vectors of m) and a work vector; H the two Gram-Schmidt passes' coefficients, the
+// norms and the update's coefficients.
+mcsdp_status mixed_gmres(mcsdp_ctx *c, double tol_ok, double tol_stall, bool *solved) {
+  const int m = c->S.m;
+  const cudaStream_t st = c->stream;
+  double *V = c->gmV, *tv = c->gmV + (size_t)(GM_K + 1) * m;
+  double *h1 = c->gmH, *h2 = h1 + (GM_K + 2), *sn = h2 + (GM_K + 2), *yd = sn + 2 * (GM_K + 2);
+  double prev = -1.0;
+  for (int cyc = 0; cyc < GM_CYCLES; ++cyc) {
+    // v_0 = M^{-1} r / beta_0
+    double Hc[GM_K + 1][GM_K], gv[GM_K + 1], cs[GM_K], snr[GM_K];
+    double beta0 = 0.0;
+    int k = 0;
+    {
+      KScope kb(c, KC_BSOLVE);
+      int nl = mixed_precond(c->B32, m, c->Linv32, c->rref, V, c->yref, c->dscl, st);
+      lz_beta(m, V, V, V, nullptr, sn, GM_K, st);
+      double b = 0.0;
+      CUDA_TRY(c, cudaMemcpyAsync(&b, sn + 2 * GM_K + 1, 8, cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(c, cudaStreamSynchronize(st));
+      beta0 = b;
+      gv[0] = beta0;
+      for (int j = 0; j < GM_K && beta0 > 0.0; ++j) {
+        double *vj = V + (size_t)j * m, *w = V + (size_t)(j + 1) * m;
+        nl += mixed_matvec(c->B, c->ldb, m, vj, tv, c->yref, c->ayref, st);
+        nl += mixed_precond(c->B32, m, c->Linv32, tv, w, c->yref, c->dscl, st);
+        lz_reorth(m, j + 1, w, V, V, h1, st);
+        lz_reorth(m, j + 1, w, V, V, h2, st);
+        lz_beta(m, w, w, w, nullptr, sn, j, st);
+        nl += 5;
+        double hh[3 * (GM_K + 2)];
+        CUDA_TRY(c, cudaMemcpyAsync(hh, h1, 2 * (GM_K + 2) * 8, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(c, cudaMemcpyAsync(hh + 2 * (GM_K + 2), sn + 2 * j + 1, 8, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(c, cudaStreamSynchronize(st));
+        ++c->refine_steps;
+        double col[GM_K + 1];
+        for (int i = 0; i <= j; ++i) col[i] = hh[i] + hh[(GM_K + 2) + i];
+        col[j + 1] = hh[2 * (GM_K + 2)];
+        // previous rotations, then the new one zeroing col[j + 1]
+        for (int i = 0; i < j; ++i) {
+          const double a = cs[i] * col[i] + snr[i] * col[i + 1];
+          col[i + 1] = -snr[i] * col[i] + cs[i] * col[i + 1];
+          col[i] = a;
+        }
+        const double rr = std::hypot(col[j], col[j + 1]);
+        cs[j] = rr > 0.0 ? col[j] / rr : 1.0;
+        snr[j] = rr > 0.0 ? col[j + 1] / rr : 0.0;
+        col[j] = rr;
+        gv[j + 1] = -snr[j] * gv[j];
+        gv[j] = cs[j] * gv[j];
+        for (int i = 0; i <= j; ++i) Hc[i][j] = col[i];
+        k = j + 1;
+        if (!std::isfinite(rr)) return MCSDP_OK;
+        // the preconditioned residual: far enough below for this cycle, or a breakdown
+        // (the preconditioner runs in FP32, so a cycle gains about that much on the true
+        // residual; the restarts refine further)
+        if (std::fabs(gv[j + 1]) <= 1e-7 * beta0 || hh[2 * (GM_K + 2)] <= 1e-14 * beta0) break;
+      }
+      // y = H^{-1} gv (upper triangular), x += V y
+      double y[GM_K];
+      for (int i = k - 1; i >= 0; --i) {
+        double a = gv[i];
+        for (int q = i + 1; q < k; ++q) a -= Hc[i][q] * y[q];
+        y[i] = Hc[i][i] != 0.0 ? a / Hc[i][i] : 0.0;
+      }
+      double ny[GM_K];
+      for (int i = 0; i < k; ++i) ny[i] = -y[i];
+      if (k > 0) {
+        CUDA_TRY(c, cudaMemcpyAsync(yd, ny, k * 8, cudaMemcpyHostToDevice, st));
+        lz_sub(m, k, c->xs, V, yd, st);
+      }
+      nl += 1 + mixed_residual(c->B, c->ldb, m, c->gref, c->xs, c->rref, c->yref, c->ayref,
+                               c->nref, st);
+      kb.done(nl);
+    }
+    KCHECK(c);
+    double nr[2];
+    CUDA_TRY(c, cudaMemcpyAsync(nr, c->nref, 2 * 8, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    prof_flush(c);
+    const double omega = nr[0] / std::max(nr[1], std::numeric_limits<double>::min());
+    if (c->opt.verbose > 1)
+      std::fprintf(stderr, "  gmres cycle %d: %d steps, omega %.3e\n", cyc, k, omega);
+    if (!std::isfinite(omega)) return MCSDP_OK;
+    if (omega <= tol_ok) {
+      *solved = true;
+      return MCSDP_OK;
+    }
+    if (prev >= 0.0 && omega > 0.5 * prev) {
       *solved = omega <= tol_stall;
       return MCSDP_OK;
     }
