@@ -41,6 +41,12 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop 
 FP64_PEAK_SOURCE = ("derived: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz = 1.26 TFLOP/s "
                     "(nominal 1.25; no measured FP64 peak on this pool)")
 TF32_BF16_RATIO = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates (recipe table)
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, from ncu captures on
+# ring_maxcut_8000 (nR = 3158, m = 8000; the current kernel sources), per unit of work, scaled to
+# a full launch by the work it does (nR^3 for the root GEMM, m^3 for the SCM Cholesky: both tile
+# their operands through L2 the same way at either size)
+TRAFFIC_PER_UNIT = {"root_gemm": (1.238365e9 + 77.669888e6) / 3158 ** 3,
+                    "scm_chol": (14.103590e9 + 19.115887e9) / 8000 ** 3}
 ORACLE_ITER_OVER_CHOL = 13.0 / (1.0 / 3.0)  # dense oracle iteration flops / SCM Cholesky flops
 KCLASS_DESC = {"ychol": "k_ychol + k_root_gather + k_chol_dag (Y = N N^T, root FP64 Cholesky)",
                "alg1": "k_alg1 + k_chol_dag + k_gemm_tn<double> (Algorithm 1; root Cholesky and "
@@ -312,7 +318,9 @@ def run_gb300(args):
         ach = (m ** 3 / 3.0) / (avg * 1e-3) / 1e12
         kern["scm_chol"] = {"bound": "alu", "kernel": KCLASS_DESC["scm_chol"], "achieved": ach,
                             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                            "traffic": None, "avg_launch_ms": avg, "launches": nfac64,
+                            "traffic": TRAFFIC_PER_UNIT["scm_chol"] * m ** 3,
+                            "traffic_note": "ncu on ring_maxcut_8000 scaled by m^3",
+                            "avg_launch_ms": avg, "launches": nfac64,
                             "total_ms": mms["scm_chol"], "peak_source": FP64_PEAK_SOURCE}
     if mms["root_gemm"] > 0:
         cnt = max(1, mstats["count"]["root_gemm"])
@@ -320,7 +328,9 @@ def run_gb300(args):
         ach = (2.0 * nR ** 3) / (avg * 1e-3) / 1e12
         kern["root_gemm"] = {"bound": "alu", "kernel": KCLASS_DESC["root_gemm"], "achieved": ach,
                              "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                             "traffic": None, "avg_launch_ms": avg, "launches": cnt,
+                             "traffic": TRAFFIC_PER_UNIT["root_gemm"] * nR ** 3,
+                             "traffic_note": "ncu on ring_maxcut_8000 scaled by nR^3",
+                             "avg_launch_ms": avg, "launches": cnt,
                              "total_ms": mms["root_gemm"], "peak_source": FP64_PEAK_SOURCE}
     if chol32_ms > 0:
         kern["scm_chol32"] = {"bound": "tensor", "kernel": KCLASS_DESC["scm_chol32"],
