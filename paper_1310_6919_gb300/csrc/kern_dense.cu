@@ -786,8 +786,11 @@ static int dense_chol_dag(T *B, int64_t ldb, int m, int rows, int *status, T *Li
   cudaMemsetAsync(sync, 0, chol_dag_words(m, rows) * sizeof(int), st);
   DagSync q{sync, sync + 1, sync + 8, sync + 8 + (size_t)R * C, sync + 8 + 2 * (size_t)R * C, C,
             budget > 0 ? budget : DAG_DEFAULT_BUDGET};
-  // two CTAs per SM: one loads or waits while the other computes
-  const int grid = (int)std::min<int64_t>(2 * (int64_t)nsm, total);
+  // two CTAs per SM: one loads or waits while the other computes.  A small matrix (C tile
+  // columns) never has more than about C^2 / 4 tasks ready at once, so its grid stops there: the
+  // CTAs it would not use would hold registers that concurrent solves (mcsdp_solve_batch) need
+  const int64_t useful = std::max<int64_t>(8, (int64_t)C * C / 4);
+  const int grid = (int)std::min<int64_t>(std::min<int64_t>(2 * (int64_t)nsm, useful), total);
   k_chol_dag<T><<<grid, DAG_THREADS, smem, st>>>(B, ldb, m, rows, status, Linv_all, q, total);
   return 1;  // kernel launches (the memset is not one of ours)
 }

@@ -142,6 +142,9 @@ struct mcsdp_ctx {
   // (and X̄_RR's factor inverted) in FP32, on the tensor cores for large roots (set per iteration
   // by mcsdp_solve; every other entry point factors in FP64)
   bool root32 = false;
+  // mixed form after the FP32 stage: X̄_RR's factor FP64, its inverse (the primal Lanczos
+  // operator) FP32 (set per iteration by mcsdp_solve)
+  bool inv32 = false;
   int fp64_asm_iter = -1;
   int promoted_iter = -1, refine_steps = 0, cur_iter = 0;
   double *alpha_c = nullptr, *alpha_r = nullptr, *scal = nullptr;
@@ -1091,7 +1094,18 @@ int factor_X_root(mcsdp_ctx *c, const double *Xbar, int *status, cudaStream_t st
   }
   copy_square<double, double>(Xbar + c->D.root_valp, nR, c->RS_X, nR, nR, st);
   int nl = 1 + dense_potrf(c->RS_X, nR, nR, status, c->rLinvX, st, c->rsyncX, c->opt.timeout_cycles);
-  nl += dense_trtri<double>(c->RS_X, nR, c->rLinvX, c->RS_P, nR, nR, c->RS_M, st);
+  if (c->inv32) {
+    // FP64 factor (the iterate's PD certificate), its inverse in FP32: the inverse only applies
+    // the Lanczos operator of the step-length bound
+    float *L32 = reinterpret_cast<float *>(c->RS_T), *X32 = L32 + (size_t)nR * nR;
+    copy_square<double, float>(c->RS_X, nR, L32, nR, nR, st);
+    launch_cast_f32(c->rLinvX, c->rLinv32, (int64_t)((nR + 31) / 32) * 1024, st);
+    nl += 2 + dense_trtri<float>(L32, nR, c->rLinv32, X32, nR, nR,
+                                 reinterpret_cast<float *>(c->RS_M), st);
+    copy_square<float, double>(X32, nR, c->RS_P, nR, nR, st);
+  } else {
+    nl += dense_trtri<double>(c->RS_X, nR, c->rLinvX, c->RS_P, nR, nR, c->RS_M, st);
+  }
   mirror_lower<double>(c->RS_P, nR, nR, st);
   return nl + 1;
 }
@@ -2551,7 +2565,7 @@ mcsdp_status mcsdp_solve(mcsdp_ctx *c, mcsdp_result *res) {
   // the root's FP32 factorisations belong to this loop only
   struct Root32Off {
     mcsdp_ctx *c;
-    ~Root32Off() { c->root32 = false; }
+    ~Root32Off() { c->root32 = c->inv32 = false; }
   } root32_off{c};
   // the gap below which the mixed form runs in FP64 throughout: for large m the refinement of
   // the FP32 factor (long form, see mixed_sce) stays far cheaper than the FP64 factorisation
@@ -2574,6 +2588,7 @@ mcsdp_status mcsdp_solve(mcsdp_ctx *c, mcsdp_result *res) {
     double sc[8];
     int failed = 0;
     c->root32 = c->opt.precision == 1 && c->dense && !c->fp64_asm && !c->promoted;
+    c->inv32 = c->opt.precision == 1 && c->dense && !c->root32;
     s = prepare(c, c->Xbar, c->z, sc, &failed);
     // dense root: the step lengths are Lanczos estimates, confirmed here by the factorisations at
     // the new iterate; a failure halves the failing step (from the saved iterate) and retries
@@ -2610,6 +2625,7 @@ mcsdp_status mcsdp_solve(mcsdp_ctx *c, mcsdp_result *res) {
       c->fp64_asm_iter = it;
       if (c->root32) {  // this iteration's root factors were FP32: again in FP64
         c->root32 = false;
+        c->inv32 = true;
         s = prepare(c, c->Xbar, c->z, sc, &failed);
         if (s) return s;
       }
