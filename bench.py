@@ -447,9 +447,9 @@ def other_legs(args, dev, stream):
     mix = batch_mix(512, 128)
     subset = set(range(48)) | set(range(512, 528))
 
-    def make(inst, st, prec):
+    def make(inst, st, prec, graph=0):
         Q = Problem(inst.n, inst.m, inst.b, inst.mat, inst.row, inst.col, inst.val, form=1,
-                    device=dev, stream=st, precision=prec)
+                    device=dev, stream=st, precision=prec, graph=graph)
         if inst.meta.get("kind") != "maxcut":
             Q.set_iterate(None, torch.tensor(inst.z0, dtype=torch.float64, device=f"cuda:{dev}"))
         return Q
@@ -460,11 +460,13 @@ def other_legs(args, dev, stream):
                         "resident; one-at-a-time on the 64-problem subset (first 48 max-cut, first "
                         "16 block-arrow)")}
     make(mix[0], None, 0).solve()
-    for name, prec in (("fp64", 0), ("mixed", 1)):
+    # fp64: iterations replayed as captured CUDA graphs (options.graph); fp64_host_loop: the
+    # host-driven loop (about a hundred launches and eight synchronisations per iteration)
+    for name, prec, graph in (("fp64", 0, 1), ("fp64_host_loop", 0, 0), ("mixed", 1, 0)):
         probs, idx, skipped = [], [], 0
         for i, q in enumerate(mix):
             try:
-                probs.append(make(q, torch.cuda.Stream(dev), prec))
+                probs.append(make(q, torch.cuda.Stream(dev), prec, graph))
                 idx.append(i)
             except MCSDPError:
                 skipped += 1
@@ -475,7 +477,7 @@ def other_legs(args, dev, stream):
         t_bat = time.perf_counter() - t0
         leg = {"problems_per_s": len(probs) / t_bat, "seconds": t_bat, "skipped": skipped,
                "all_optimal": all(r["status"] == 0 for r in res)}
-        if prec == 0:
+        if name == "fp64":
             seq = [make(mix[i], None, 0) for i in sorted(subset)]
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()

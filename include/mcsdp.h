@@ -126,6 +126,13 @@ typedef struct {
                             root blocks of Y and X̄ are also factored (and X̄_RR's factor
                             inverted) in FP32.  0 = default: 1e-2 with a dense root, else
                             mixed_gap (1e-5 if that is off) */
+  int32_t graph;         /* 1 = after the first iteration, each iteration (the direction, the
+                            update with step lengths chosen on the device, and the factors at
+                            the new iterate) is captured once into a CUDA graph and replayed: one
+                            graph launch and one host synchronisation per iteration instead of
+                            about a hundred launches and eight synchronisations; same iterates as
+                            0.  FP64 form without a dense root only (else ignored); per-class
+                            times (profile) are then not measured.  0 (default) = off */
 } mcsdp_options;
 
 void mcsdp_default_options(mcsdp_options *opt);

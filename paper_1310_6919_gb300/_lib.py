@@ -20,7 +20,7 @@ class Options_t(C.Structure):
                 ("panel_max", C.c_int32), ("group_max", C.c_int32),
                 ("panel_budget_mb", C.c_double), ("profile", C.c_int32), ("relax", C.c_int32),
                 ("solve_warps", C.c_int32), ("mixed_gap", C.c_double), ("root_rows", C.c_int32),
-                ("tensor_cores", C.c_int32), ("mixed_asm_gap", C.c_double)]
+                ("tensor_cores", C.c_int32), ("mixed_asm_gap", C.c_double), ("graph", C.c_int32)]
 
 
 class Work_t(C.Structure):

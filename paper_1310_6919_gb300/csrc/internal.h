@@ -229,8 +229,10 @@ void launch_entry_grads(int64_t nnz, const int64_t *off, const int *k, const int
                         const double *v, double *gC, double *gA, cudaStream_t st);
 // out = (float) in, n entries (FP32 copies of the factors for the mixed form's solves)
 void launch_cast_f32(const double *in, float *out, int64_t n, cudaStream_t st);
+// betamu_dev (may be null): beta mu read from the device instead
 void launch_dx_combine(const DevSym &S, double betamu, const double *Xbar, const double *YinvE,
-                       const double *Mlow, const double *Mup, double *dX, cudaStream_t st);
+                       const double *Mlow, const double *Mup, double *dX, cudaStream_t st,
+                       const double *betamu_dev = nullptr);
 // clique-wise primal step length (eq. primal_length2): alpha_r per clique
 void launch_primal_step(const DevSym &S, const double *Xbar, const double *dX, double *alpha_r,
                         int *status, cudaStream_t st);
@@ -239,8 +241,20 @@ size_t primal_step_smem_bytes(const DevSym &S);
 // (scal holds 16 + 6 x 64 doubles: the partials of the first stage follow the 16 scalars)
 void launch_measures(const DevSym &S, const double *Xbar, const double *Ylay, const double *z,
                      const double *alpha_r, double *scal, cudaStream_t st);
+// steps_dev (may be null): (gamma alpha_p, gamma alpha_d, failure) from the device; a non-zero
+// failure leaves the iterate unchanged
 void launch_update(const DevSym &S, double *Xbar, const double *dX, double ap, double *z,
-                   const double *dz, double ad, cudaStream_t st);
+                   const double *dz, double ad, cudaStream_t st, const double *steps_dev = nullptr);
+// the graph form of an iteration (device step lengths; the layout of g in kern_sparse.cu)
+void launch_graph_betamu(const double *scal, int n, double beta, double *g, cudaStream_t st);
+struct DualTables {
+  double first[16], geo[16];
+};
+void launch_dual_cands(const double *g, int round, double *cand, int ncand, const DualTables &t,
+                       int *cst, cudaStream_t st);
+void launch_dual_update(const int *cst, const double *cand, int ncand, double *g, cudaStream_t st);
+void launch_graph_steps(const double *scal, const int *status, double gamma, double *g,
+                        cudaStream_t st);
 // constraints with disjoint supports: dX += sum_k c_k A_k with c_k chosen so that
 // A_k . (X̄ + dX) = b_k exactly (the projection onto the primal affine set, A A^* diagonal)
 void launch_project_primal(const DevSym &S, const double *Xbar, double *dX, cudaStream_t st);
@@ -409,7 +423,7 @@ int mixed_precond(const float *L32, int m, const float *Linv32, const double *u,
 int mixed_residual(const double *B, int64_t ldb, int m, const double *g, const double *x,
                    double *r, double *P, double *A, double *norms, cudaStream_t st);
 void launch_rhs_border(const DevSym &S, double *B, int64_t ldb, const double *hvec, double betamu,
-                       cudaStream_t st);
+                       cudaStream_t st, const double *betamu_dev = nullptr);
 void launch_dz_to_user(const DevSym &S, const double *dz_int, double *dz_user, cudaStream_t st);
 void launch_B_to_user(const DevSym &S, const double *Bint, int64_t ldi, double *Bout, int64_t ldo,
                       const double *h_int, double *h_out, cudaStream_t st);

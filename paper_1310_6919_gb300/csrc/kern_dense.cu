@@ -1178,14 +1178,16 @@ int dense_backsolve(const double *B, int64_t ldb, int m, const double *Linv_all,
 }
 
 // row m of B <- g_i = b_{user(i)} - beta mu h_i   (internal order)
-__global__ void k_rhs_border(DevSym S, double *B, int64_t ldb, const double *hvec, double betamu) {
+__global__ void k_rhs_border(DevSym S, double *B, int64_t ldb, const double *hvec, double betamu,
+                             const double *__restrict__ betamu_dev) {
+  if (betamu_dev) betamu = *betamu_dev;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.m; i += gridDim.x * blockDim.x)
     B[S.m + (int64_t)i * ldb] = S.b[S.con_order[i]] - betamu * hvec[i];
 }
 
 void launch_rhs_border(const DevSym &S, double *B, int64_t ldb, const double *hvec, double betamu,
-                       cudaStream_t st) {
-  k_rhs_border<<<(S.m + 255) / 256, 256, 0, st>>>(S, B, ldb, hvec, betamu);
+                       cudaStream_t st, const double *betamu_dev) {
+  k_rhs_border<<<(S.m + 255) / 256, 256, 0, st>>>(S, B, ldb, hvec, betamu, betamu_dev);
 }
 
 __global__ void k_dz_to_user(DevSym S, const double *x, double *dz) {

@@ -440,7 +440,9 @@ void launch_cast_f32(const double *in, float *out, int64_t n, cudaStream_t st) {
 // dX on lower(E): beta mu Y^{-1} - X̄ - (M + M^T)/2   (eq. dX with the symmetrisation)
 __global__ void k_dx_combine(DevSym S, double betamu, const double *__restrict__ X,
                              const double *__restrict__ YinvE, const double *__restrict__ Mlow,
-                             const double *__restrict__ Mup, double *dX) {
+                             const double *__restrict__ Mup, double *dX,
+                             const double *__restrict__ betamu_dev) {
+  if (betamu_dev) betamu = *betamu_dev;
   const int s = blockIdx.x;
   const int nrow = (int)(S.sn_rowptr[s + 1] - S.sn_rowptr[s]);
   const int ncol = S.sn_col[s + 1] - S.sn_col[s];
@@ -457,9 +459,10 @@ __global__ void k_dx_combine(DevSym S, double betamu, const double *__restrict__
 }
 
 void launch_dx_combine(const DevSym &S, double betamu, const double *X, const double *YinvE,
-                       const double *Mlow, const double *Mup, double *dX, cudaStream_t st) {
+                       const double *Mlow, const double *Mup, double *dX, cudaStream_t st,
+                       const double *betamu_dev) {
   if (S.nforest <= 0) return;
-  k_dx_combine<<<S.nforest, 128, 0, st>>>(S, betamu, X, YinvE, Mlow, Mup, dX);
+  k_dx_combine<<<S.nforest, 128, 0, st>>>(S, betamu, X, YinvE, Mlow, Mup, dX, betamu_dev);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -758,7 +761,13 @@ void launch_measures(const DevSym &S, const double *X, const double *Y, const do
 }
 
 __global__ void k_update(int64_t nnz, double *X, const double *__restrict__ dX, double ap, int m,
-                         double *z, const double *__restrict__ dz, double ad) {
+                         double *z, const double *__restrict__ dz, double ad,
+                         const double *__restrict__ steps_dev) {
+  if (steps_dev) {  // (gamma alpha_p, gamma alpha_d, failure): nothing moves after a failure
+    if (steps_dev[2] != 0.0) return;
+    ap = steps_dev[0];
+    ad = steps_dev[1];
+  }
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nnz;
        i += (int64_t)gridDim.x * blockDim.x)
     X[i] = fma(ap, dX[i], X[i]);
@@ -768,10 +777,89 @@ __global__ void k_update(int64_t nnz, double *X, const double *__restrict__ dX, 
 }
 
 void launch_update(const DevSym &S, double *X, const double *dX, double ap, double *z,
-                   const double *dz, double ad, cudaStream_t st) {
+                   const double *dz, double ad, cudaStream_t st, const double *steps_dev) {
   int blocks = (int)((S.nnzL + 255) / 256);
   if (blocks > 2048) blocks = 2048;
-  k_update<<<blocks, 256, 0, st>>>(S.nnzL, X, dX, ap, S.m, z, dz, ad);
+  k_update<<<blocks, 256, 0, st>>>(S.nnzL, X, dX, ap, S.m, z, dz, ad, steps_dev);
+}
+
+// ---- the graph form of an iteration (FP64, no dense root): step lengths on the device ----
+// g[0] beta mu; g[3] lo, g[4] hi (< 0: none failed yet), g[5] bracket frozen; g[6] gamma alpha_p,
+// g[7] gamma alpha_d, g[8] failure (1: dual step collapsed, 2: SCM not positive definite or a
+// factorisation timed out); g[9] alpha_p, g[10] alpha_d; g[11] the SCM factorisation's status
+__global__ void k_graph_betamu(const double *__restrict__ scal, int n, double beta, double *g) {
+  if (threadIdx.x == 0) {
+    g[0] = beta * (scal[0] / n);  // the host loop's order: mu first
+    g[3] = 0.0;
+    g[4] = -1.0;
+    g[5] = 0.0;
+  }
+}
+// round r's NCAND candidates from the bracket (the host loop's rule: fixed first round, then
+// equal spacing inside (lo, hi], or geometric below hi while everything failed)
+// (first: the first round's candidates; geo: 0.3^(i+1), both from the host, so that every
+// candidate is the host loop's value bit for bit; the rounded operations below keep its order)
+__global__ void k_dual_cands(const double *__restrict__ g, int round, double *cand, int ncand,
+                             DualTables t, int *cst) {
+  const int i = threadIdx.x;
+  if (i >= ncand) return;
+  // the candidates' statuses: cleared, or, once the bracket is frozen, marked failed so that the
+  // round's factorisation kernels return at once (their CTAs test the status first)
+  cst[i] = g[5] != 0.0 ? ST_NOT_PD : 0;
+  const double lo = g[3], hi = g[4];
+  double v;
+  if (round == 0) {
+    v = t.first[i];
+  } else if (lo == 0.0 && hi > 0) {
+    v = __dmul_rn(hi, t.geo[i]);
+  } else {
+    const double H = hi < 0 ? 1.0 : hi;
+    v = __dadd_rn(lo, __ddiv_rn(__dmul_rn(__dsub_rn(H, lo), (double)(i + 1)), (double)(ncand + 1)));
+  }
+  cand[i] = v;
+}
+// the bracket from the candidates' factorisation statuses (0 = positive definite); frozen once
+// the host loop would have stopped (lo >= 1, or the bracket within 1e-3 of lo)
+__global__ void k_dual_update(const int *__restrict__ cst, const double *__restrict__ cand,
+                              int ncand, double *g) {
+  if (threadIdx.x != 0 || g[5] != 0.0) return;
+  double lo = g[3], hi = g[4];
+  for (int i = 0; i < ncand; ++i) {
+    if (cst[i] == 0) lo = fmax(lo, cand[i]);
+    else hi = hi < 0 ? cand[i] : fmin(hi, cand[i]);
+  }
+  g[3] = lo;
+  g[4] = hi;
+  if (lo >= 1.0 || (lo > 0 && hi > 0 && (hi - lo) <= 1e-3 * lo)) g[5] = 1.0;
+}
+__global__ void k_graph_steps(const double *__restrict__ scal, const int *__restrict__ status,
+                              double gamma, double *g) {
+  if (threadIdx.x != 0) return;
+  const double ap = scal[5], lo = g[3];
+  const double ad = fmin(lo, 1.0);
+  double fail = 0.0;
+  if (lo <= 0.0) fail = 1.0;
+  if (status[2] & (ST_NOT_PD | ST_TIMEOUT)) fail = 2.0;
+  g[6] = gamma * ap;
+  g[7] = gamma * ad;
+  g[8] = fail;
+  g[9] = ap;
+  g[10] = ad;
+  g[11] = (double)status[2];
+}
+void launch_graph_betamu(const double *scal, int n, double beta, double *g, cudaStream_t st) {
+  k_graph_betamu<<<1, 32, 0, st>>>(scal, n, beta, g);
+}
+void launch_dual_cands(const double *g, int round, double *cand, int ncand, const DualTables &t,
+                       int *cst, cudaStream_t st) {
+  k_dual_cands<<<1, 32, 0, st>>>(g, round, cand, ncand, t, cst);
+}
+void launch_dual_update(const int *cst, const double *cand, int ncand, double *g, cudaStream_t st) {
+  k_dual_update<<<1, 32, 0, st>>>(cst, cand, ncand, g);
+}
+void launch_graph_steps(const double *scal, const int *status, double gamma, double *g,
+                        cudaStream_t st) {
+  k_graph_steps<<<1, 32, 0, st>>>(scal, status, gamma, g);
 }
 
 // one thread per constraint k: r = b_k - A_k . X̄ - A_k . dX, c = r / (A_k . A_k), dX += c A_k on

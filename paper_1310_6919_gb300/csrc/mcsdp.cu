@@ -109,8 +109,17 @@ struct mcsdp_ctx {
   double *ent_f_dev = nullptr, *zsave = nullptr, *bwd_g = nullptr, *vrhs = nullptr;
   bool iterate_set = false;
   cudaEvent_t ev[8] = {};
+  // the graph form of an iteration (options.graph): g = device step-length scalars, the
+  // instantiated graph, and the launches it holds (per class) for the statistics
+  double *gsc = nullptr;
+  cudaGraphExec_t iter_exec = nullptr;
+  bool graph_failed = false;  // capture not possible: iterate without the graph
+  int64_t graph_launches = 0;
+  int64_t graph_kcount[16] = {};
   cudaStream_t st2 = nullptr;                  // low priority: trailing updates, primal step
   cudaStream_t st1 = nullptr;                  // high priority: the Cholesky's critical path
+  cudaStream_t stc = nullptr;                  // the graph iteration's capture (owned: a caller's
+                                               // stream may be shared with other contexts)
   cudaStream_t st3 = nullptr;                  // low priority: the P-MATRIX's Y^{-1} columns
   cudaEvent_t ev_yinv = nullptr;               // st3 done with them
   cudaStream_t st4 = nullptr;                  // low priority: the SCM's N solves
@@ -776,6 +785,7 @@ void plan_workspace(mcsdp_ctx *c) {
     plan_buf(c, cur, "zprev", c->dense ? (size_t)m * 8 : 0);
   }
   plan_buf(c, cur, "alpha_c", NCAND * 8);
+  plan_buf(c, cur, "gsc", 16 * 8);
   plan_buf(c, cur, "alpha_r", (size_t)S.ns * 8);
   plan_buf(c, cur, "scal", (16 + 6 * 64) * 8);  // scalars, then the measures' partials
   plan_buf(c, cur, "chol_sync", chol_dag_words(m, m + 1) * 4);
@@ -935,6 +945,7 @@ void bind_pointers(mcsdp_ctx *c) {
   D.nslotf = c->nslotf;
   c->Ncand = wsp<double>(c, "Ncand");
   c->alpha_c = wsp<double>(c, "alpha_c");
+  c->gsc = wsp<double>(c, "gsc");
   c->alpha_r = wsp<double>(c, "alpha_r");
   c->scal = wsp<double>(c, "scal");
   c->status = wsp<int>(c, "status");
@@ -2123,7 +2134,163 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
   return MCSDP_OK;
 }
 
+mcsdp_status factor_YX(mcsdp_ctx *c, const double *Xbar);
+mcsdp_status phase_Y(mcsdp_ctx *c, const double *z);
+
+// The graph form of one iteration (options.graph; FP64, no dense root), recorded on c->stream
+// with no host synchronisation: the direction at the current iterate as in direction() with
+// beta mu read from the device, the primal step beside it, the dual step's candidate rounds
+// with the bracket kept on the device (the host loop's rule, frozen where the host loop would
+// stop, so the steps are the same), the update with gamma alpha_p and gamma alpha_d from the
+// device (skipped after a failure), then Y, N, L̂ and the scalars at the new iterate.
+mcsdp_status graph_body(mcsdp_ctx *c) {
+  const int n = c->S.n, m = c->S.m;
+  double *g = c->gsc;
+  mcsdp_status s;
+  launch_graph_betamu(c->scal, n, c->opt.beta, g, c->stream);
+  CUDA_TRY(c, cudaMemsetAsync(c->status + 7, 0, sizeof(int), c->stream));
+  const bool yinv_early = c->W3 != nullptr;
+  if (yinv_early) {
+    CUDA_TRY(c, cudaEventRecord(c->ev_yinv, c->stream));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->st3, c->ev_yinv, 0));
+    cudaStream_t main_st = c->stream;
+    double *pw = c->Pw;
+    unsigned char *xv = c->D.xvalid;
+    c->stream = c->st3;
+    c->Pw = c->Pw2;
+    c->D.xvalid = c->xvalid2;
+    KScope ky(c, KC_PMAT_SIDE, c->st3);
+    int nly = 0;
+    s = phase_pmatrix_yinv<double>(c, &nly);
+    ky.done(nly);
+    c->stream = main_st;
+    c->Pw = pw;
+    c->D.xvalid = xv;
+    if (s) return s;
+    CUDA_TRY(c, cudaEventRecord(c->ev_yinv, c->st3));
+  }
+  s = phase_scm<double>(c);
+  if (s) return s;
+  {
+    KScope k0(c, KC_MISC);
+    launch_rhs_border(c->D, c->B, c->ldb, c->hvec, 0.0, c->stream, g);
+    k0.done(1);
+    KScope k1(c, KC_CHOL);
+    k1.done(dense_chol_bordered(c->B, c->ldb, m, c->status + 2, c->Binv, c->stream, &c->cs));
+    KScope k2(c, KC_BSOLVE);
+    k2.done(dense_backsolve(c->B, c->ldb, m, c->Binv, c->xs, c->stream));
+    KScope k3(c, KC_MISC);
+    launch_dz_to_user(c->D, c->xs, c->dz, c->stream);
+    k3.done(1);
+  }
+  CUDA_TRY(c, cudaMemsetAsync(c->dY, 0, c->D.nnzL * 8, c->stream));
+  {
+    KScope k0(c, KC_MISC);
+    launch_slot_combine(c->D, c->dY, c->dz, 0.0, -1.0, c->stream);
+    k0.done(1);
+    KScope k1(c, KC_PMAT);
+    int nl = 0;
+    if (yinv_early) CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->ev_yinv, 0));
+    s = yinv_early ? phase_pmatrix<double>(c, &nl, nullptr, false, c->W3)
+                   : phase_pmatrix<double>(c, &nl);
+    if (s) return s;
+    k1.done(nl);
+    KScope k2(c, KC_MISC);
+    launch_dx_combine(c->D, 0.0, c->Xbar, c->YinvE, c->Mlow, c->Mup, c->dX, c->stream, g);
+    k2.done(1);
+  }
+  CUDA_TRY(c, cudaEventRecord(c->ev[3], c->stream));
+  CUDA_TRY(c, cudaStreamWaitEvent(c->st2, c->ev[3], 0));
+  {
+    KScope k1(c, KC_PSTEP, c->st2);
+    launch_primal_step(c->D, c->Xbar, c->dX, c->alpha_r, c->status + 3, c->st2);
+    k1.done(1);
+  }
+  CUDA_TRY(c, cudaEventRecord(c->ev[5], c->st2));
+  DualTables tab;
+  const double first[NCAND] = {1.0, 0.95, 0.9, 0.85, 0.8, 0.7, 0.6, 0.5,
+                               0.4, 0.3, 0.2, 0.1, 0.05, 0.02, 0.01, 0.003};
+  for (int i = 0; i < NCAND; ++i) {
+    tab.first[i] = first[i];
+    tab.geo[i] = std::pow(0.3, i + 1);
+  }
+  for (int round = 0; round < 6; ++round) {
+    launch_dual_cands(g, round, c->alpha_c, NCAND, tab, c->status + 8, c->stream);
+    s = phase_ychol(c, NCAND, c->alpha_c, c->Ylay, c->dY, c->Ncand, nullptr, c->status + 8);
+    if (s) return s;
+    launch_dual_update(c->status + 8, c->alpha_c, NCAND, g, c->stream);
+  }
+  CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->ev[5], 0));
+  {
+    KScope k2(c, KC_MISC);
+    launch_measures(c->D, c->Xbar, c->Ylay, c->z, c->alpha_r, c->scal, c->stream);
+    launch_graph_steps(c->scal, c->status, c->opt.gamma, g, c->stream);
+    launch_update(c->D, c->Xbar, c->dX, 0.0, c->z, c->dz, 0.0, c->stream, g + 6);
+    k2.done(4 + 6 * 2);
+  }
+  s = phase_Y(c, c->z);
+  if (s) return s;
+  s = factor_YX(c, c->Xbar);
+  if (s) return s;
+  KScope k3(c, KC_MISC);
+  launch_measures(c->D, c->Xbar, c->Ylay, c->z, nullptr, c->scal, c->stream);
+  k3.done(2);
+  return MCSDP_OK;
+}
+
+// Runs one iteration through the graph (captured on first use); false when it cannot be
+// captured (the caller then iterates without it)
+bool graph_iteration(mcsdp_ctx *c, mcsdp_status *s) {
+  *s = MCSDP_OK;
+  if (!c->iter_exec) {
+    const int64_t l0 = c->launches;
+    int64_t k0[16];
+    for (int q = 0; q < 16; ++q) k0[q] = c->kcount[q];
+    const int prof = c->opt.profile;
+    c->opt.profile = 0;  // no timing events inside the graph
+    // captured on the context's own stream: work other contexts put on a shared caller stream
+    // meanwhile must not enter the graph
+    cudaStream_t user = c->stream;
+    c->stream = c->stc;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(c->stc, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      (void)cudaGetLastError();
+      c->opt.profile = prof;
+      c->stream = user;
+      return false;
+    }
+    const mcsdp_status bs = graph_body(c);
+    const cudaError_t ec = cudaStreamEndCapture(c->stc, &graph);
+    c->stream = user;
+    c->opt.profile = prof;
+    c->graph_launches = c->launches - l0;
+    for (int q = 0; q < 16; ++q) {
+      c->graph_kcount[q] = c->kcount[q] - k0[q];
+      c->kcount[q] = k0[q];
+    }
+    c->launches = l0;
+    if (bs != MCSDP_OK || ec != cudaSuccess || !graph ||
+        cudaGraphInstantiate(&c->iter_exec, graph, 0) != cudaSuccess) {
+      (void)cudaGetLastError();
+      if (graph) cudaGraphDestroy(graph);
+      c->iter_exec = nullptr;
+      c->err.clear();
+      return false;
+    }
+    cudaGraphDestroy(graph);
+  }
+  if (cudaGraphLaunch(c->iter_exec, c->stream) != cudaSuccess) {
+    *s = fail(c, MCSDP_ERR_CUDA, "graph launch failed");
+    return true;
+  }
+  c->launches += c->graph_launches;
+  for (int q = 0; q < 16; ++q) c->kcount[q] += c->graph_kcount[q];
+  return true;
+}
+
 // Y, N, L̂ and the scalars at the current iterate (c->Xbar, c->z)
+mcsdp_status prepare_read(mcsdp_ctx *c, double *scal_host, int *failed);
+
 mcsdp_status prepare(mcsdp_ctx *c, const double *Xbar, const double *z, double *scal_host,
                      int *failed = nullptr) {
   mcsdp_status s = phase_Y(c, z);
@@ -2136,6 +2303,11 @@ mcsdp_status prepare(mcsdp_ctx *c, const double *Xbar, const double *z, double *
     k2.done(2);
   }
   KCHECK(c);
+  return prepare_read(c, scal_host, failed);
+}
+
+// the host side of prepare: the scalars and the factorisations' statuses
+mcsdp_status prepare_read(mcsdp_ctx *c, double *scal_host, int *failed) {
   int st[4];
   if (scal_host) CUDA_TRY(c, cudaMemcpyAsync(scal_host, c->scal, 6 * 8, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(st, c->status, 4 * 4, cudaMemcpyDeviceToHost, c->stream));
@@ -2313,6 +2485,7 @@ mcsdp_status mcsdp_create(const mcsdp_problem *p, const mcsdp_options *opt, void
     CUDA_TRY(c, cudaStreamCreateWithPriority(&c->st2, cudaStreamNonBlocking, prio_lo));
     CUDA_TRY(c, cudaStreamCreateWithPriority(&c->st1, cudaStreamNonBlocking, prio_hi));
     CUDA_TRY(c, cudaStreamCreateWithPriority(&c->st3, cudaStreamNonBlocking, prio_lo));
+    CUDA_TRY(c, cudaStreamCreateWithFlags(&c->stc, cudaStreamNonBlocking));
     CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_yinv, cudaEventDisableTiming));
     CUDA_TRY(c, cudaStreamCreateWithPriority(&c->st4, cudaStreamNonBlocking, prio_lo));
     CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_n0, cudaEventDisableTiming));
@@ -2340,6 +2513,7 @@ void mcsdp_destroy(mcsdp_ctx *c) {
   if (!c) return;
   if (!c->host_only && c->device >= 0) {
     cudaSetDevice(c->device);
+    if (c->iter_exec) cudaGraphExecDestroy(c->iter_exec);
     for (int i = 0; i < 8; ++i)
       if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     if (!c->pending.empty()) {
@@ -2354,6 +2528,7 @@ void mcsdp_destroy(mcsdp_ctx *c) {
     if (c->st2) cudaStreamDestroy(c->st2);
     if (c->st1) cudaStreamDestroy(c->st1);
     if (c->st3) cudaStreamDestroy(c->st3);
+    if (c->stc) cudaStreamDestroy(c->stc);
     if (c->ev_yinv) cudaEventDestroy(c->ev_yinv);
     if (c->st4) cudaStreamDestroy(c->st4);
     if (c->ev_n0) cudaEventDestroy(c->ev_n0);
@@ -2584,12 +2759,32 @@ mcsdp_status mcsdp_solve(mcsdp_ctx *c, mcsdp_result *res) {
   const int n = c->S.n;
   mcsdp_status final_status = MCSDP_ERR_MAXITER;
   double last_ap = 0.0, last_ad = 0.0;
+  const bool use_graph = c->opt.graph == 1 && !c->dense && c->opt.precision == 0;
+  bool graph_prepared = false;
   for (int it = 0; it <= c->opt.max_iter; ++it) {
     double sc[8];
     int failed = 0;
     c->root32 = c->opt.precision == 1 && c->dense && !c->fp64_asm && !c->promoted;
     c->inv32 = c->opt.precision == 1 && c->dense && !c->root32;
-    s = prepare(c, c->Xbar, c->z, sc, &failed);
+    if (graph_prepared) {
+      // the graph ran the previous iteration's direction and update and these factors
+      double gh[12];
+      CUDA_TRY(c, cudaMemcpyAsync(gh, c->gsc, 12 * 8, cudaMemcpyDeviceToHost, c->stream));
+      s = prepare_read(c, sc, &failed);
+      if (s == MCSDP_OK && gh[8] == 2.0)
+        s = fail(c, (((int)gh[11]) & ST_TIMEOUT) ? MCSDP_ERR_TIMEOUT : MCSDP_ERR_NOT_PD,
+                 "Schur complement matrix is not positive definite");
+      if (s == MCSDP_OK && gh[8] == 1.0) s = fail(c, MCSDP_ERR_STALL, "dual step length collapsed");
+      if (s) {
+        final_status = s;
+        break;
+      }
+      if (c->opt.verbose)
+        std::fprintf(stderr, "it %3d (graph) ap %.3f ad %.3f\n", it - 1, gh[9], gh[10]);
+    } else {
+      s = prepare(c, c->Xbar, c->z, sc, &failed);
+    }
+    graph_prepared = false;
     // dense root: the step lengths are Lanczos estimates, confirmed here by the factorisations at
     // the new iterate; a failure halves the failing step (from the saved iterate) and retries
     for (int bt = 0; s == MCSDP_ERR_NOT_PD && c->dense && it > 0 && bt < 10; ++bt) {
@@ -2649,6 +2844,17 @@ mcsdp_status mcsdp_solve(mcsdp_ctx *c, mcsdp_result *res) {
       break;
     }
     if (it == c->opt.max_iter) break;
+    if (use_graph && it >= 1 && !c->graph_failed) {
+      if (graph_iteration(c, &s)) {
+        if (s) {
+          final_status = s;
+          break;
+        }
+        graph_prepared = true;
+        continue;
+      }
+      c->graph_failed = true;  // not capturable here: the iteration runs without the graph
+    }
     IterOut o{};
     s = direction(c, c->Xbar, mu, o, tms);
     if (s) {
