@@ -817,7 +817,7 @@ static void atomic_status_host_fail(int *status, cudaStream_t st) {
 // from the next sub-panel down, K = TC_SUB), so the 32-column kernels' FFMA updates stay inside a
 // sub-panel.  The sub-panel's split also writes its rows transposed above the diagonal.
 static int panel_chol_tc(float *Bp, int64_t ldb, int pw, int rows, int *status, float *Linv,
-                         cudaStream_t st, const CholStreams *cs) {
+                         cudaStream_t st, const CholStreams *cs, float *sub_hi, float *sub_lo) {
   constexpr int TC_SUB = 128;
   int nl = 0;
   for (int s0 = 0; s0 < pw; s0 += TC_SUB) {
@@ -826,14 +826,14 @@ static int panel_chol_tc(float *Bp, int64_t ldb, int pw, int rows, int *status, 
                             Linv + (int64_t)(s0 / NB) * NB * NB, st, nullptr);
     const int r0 = s0 + sw;
     if (r0 >= pw) break;
-    split_tf32(Bp + r0 + (int64_t)s0 * ldb, 1, ldb, rows - r0, sw, cs->tc_hi, cs->tc_lo, TC_SUB,
+    split_tf32(Bp + r0 + (int64_t)s0 * ldb, 1, ldb, rows - r0, sw, sub_hi, sub_lo, TC_SUB,
                Bp + s0 + (int64_t)r0 * ldb, ldb, st);
     TcOperand Oa, Ob;
     Oa.x = Oa.y = Ob.x = Ob.y = 0;
-    if (!make_tmap_kmajor(&Oa.hi, cs->tc_hi, TC_SUB, sw, rows - r0) ||
-        !make_tmap_kmajor(&Oa.lo, cs->tc_lo, TC_SUB, sw, rows - r0) ||
-        !make_tmap_kmajor(&Ob.hi, cs->tc_hi, TC_SUB, sw, pw - r0) ||
-        !make_tmap_kmajor(&Ob.lo, cs->tc_lo, TC_SUB, sw, pw - r0)) {
+    if (!make_tmap_kmajor(&Oa.hi, sub_hi, TC_SUB, sw, rows - r0) ||
+        !make_tmap_kmajor(&Oa.lo, sub_lo, TC_SUB, sw, rows - r0) ||
+        !make_tmap_kmajor(&Ob.hi, sub_hi, TC_SUB, sw, pw - r0) ||
+        !make_tmap_kmajor(&Ob.lo, sub_lo, TC_SUB, sw, pw - r0)) {
       atomic_status_host_fail(status, st);
       return nl;
     }
@@ -844,29 +844,65 @@ static int panel_chol_tc(float *Bp, int64_t ldb, int pw, int rows, int *status, 
   return nl;
 }
 
+// The tensor-core FP32 Cholesky, right-looking by panels of P columns with lookahead of one
+// panel.  On st (the chain): F(k) factors panel k (panel_chol_tc), S(k) splits its rows below
+// into buffer k % 2 (and writes them transposed above the diagonal), N(k) updates panel k + 1's
+// columns.  On cs->rest: R(k) updates every column beyond panel k + 1, so the chain's
+// F(k + 1), S(k + 1) overlap R(k).  Order: F(k) and S(k) after R(k - 2) (it updates panel k and
+// read buffer k % 2), N(k) after R(k - 1) (both update panel k + 1), R(k) after S(k).
 static int dense_chol_f32_tc(float *B, int64_t ldb, int m, int *status, float *Linv_all,
                              cudaStream_t st, const CholStreams *cs) {
   int nl = 0;
   const int P = tc_panel(m);
-  for (int k0 = 0; k0 < m; k0 += P) {
-    const int pw = std::min(P, m - k0);
+  const int np = (m + P - 1) / P;
+  const int64_t bufsz = (int64_t)P * m;
+  cudaStream_t rs = cs->rest;
+  int *err = cs->tc_err ? cs->tc_err : status;
+  cudaEventRecord(cs->fork, st);
+  cudaStreamWaitEvent(rs, cs->fork, 0);
+  for (int k = 0; k < np; ++k) {
+    const int k0 = k * P, pw = std::min(P, m - k0), r0 = k0 + pw;
+    float *hi = cs->tc_hi + (k & 1) * bufsz, *lo = cs->tc_lo + (k & 1) * bufsz;
+    if (k >= 2) cudaStreamWaitEvent(st, cs->rest_ev[k & 1], 0);  // R(k - 2) done
     nl += panel_chol_tc(B + k0 + (int64_t)k0 * ldb, ldb, pw, m - k0, status,
-                        Linv_all + (int64_t)(k0 / NB) * NB * NB, st, cs);
-    const int r0 = k0 + pw;
+                        Linv_all + (int64_t)(k0 / NB) * NB * NB, st, cs, hi, lo);
     if (r0 >= m) break;
-    split_tf32(B + r0 + (int64_t)k0 * ldb, 1, ldb, m - r0, pw, cs->tc_hi, cs->tc_lo, P,
-               B + k0 + (int64_t)r0 * ldb, ldb, st);
-    TcOperand Op;
-    Op.x = Op.y = 0;
-    if (!make_tmap_kmajor(&Op.hi, cs->tc_hi, P, pw, m - r0) ||
-        !make_tmap_kmajor(&Op.lo, cs->tc_lo, P, pw, m - r0)) {
+    split_tf32(B + r0 + (int64_t)k0 * ldb, 1, ldb, m - r0, pw, hi, lo, P, B + k0 + (int64_t)r0 * ldb,
+               ldb, st);
+    cudaEventRecord(cs->next[k & 1], st);  // S(k) done
+    const int pn = std::min(P, m - r0);    // width of panel k + 1
+    TcOperand Oa, Ob;
+    Oa.x = Oa.y = Ob.x = Ob.y = 0;
+    if (!make_tmap_kmajor(&Oa.hi, hi, P, pw, m - r0) || !make_tmap_kmajor(&Oa.lo, lo, P, pw, m - r0) ||
+        !make_tmap_kmajor(&Ob.hi, hi, P, pw, pn) || !make_tmap_kmajor(&Ob.lo, lo, P, pw, pn)) {
       atomic_status_host_fail(status, st);
-      return nl;
+      break;
     }
-    gemm_3xtf32(Op, Op, m - r0, m - r0, pw, B + r0 + (int64_t)r0 * ldb, 1, ldb, -1.f, 1.f, true,
-                false, cs->tc_err ? cs->tc_err : status, st);
+    // N(k): panel k + 1's columns, every row from r0 down
+    if (k >= 1) cudaStreamWaitEvent(st, cs->rest_ev[(k - 1) & 1], 0);  // R(k - 1) done
+    gemm_3xtf32(Oa, Ob, m - r0, pn, pw, B + r0 + (int64_t)r0 * ldb, 1, ldb, -1.f, 1.f, true, false,
+                err, st);
     nl += 2;
+    // R(k): the columns beyond panel k + 1, rows from r2 down (buffer rows from r2 - r0)
+    const int r2 = r0 + pn;
+    if (r2 < m) {
+      TcOperand Oc;
+      Oc.x = Oc.y = 0;
+      const int64_t off = (int64_t)(r2 - r0) * P;
+      if (!make_tmap_kmajor(&Oc.hi, hi + off, P, pw, m - r2) ||
+          !make_tmap_kmajor(&Oc.lo, lo + off, P, pw, m - r2)) {
+        atomic_status_host_fail(status, st);
+        break;
+      }
+      cudaStreamWaitEvent(rs, cs->next[k & 1], 0);
+      gemm_3xtf32(Oc, Oc, m - r2, m - r2, pw, B + r2 + (int64_t)r2 * ldb, 1, ldb, -1.f, 1.f, true,
+                  false, err, rs);
+      ++nl;
+    }
+    cudaEventRecord(cs->rest_ev[k & 1], rs);
   }
+  cudaEventRecord(cs->chain_done, rs);
+  cudaStreamWaitEvent(st, cs->chain_done, 0);
   return nl;
 }
 
@@ -1000,7 +1036,9 @@ static int dense_chol_graph(T *B, int64_t ldb, int m, int rows, int *status, T *
       g->runs = -1;
       return dense_chol<T>(B, ldb, m, rows, status, Linv, st, cs);
     }
-    if (cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) {
+    // node priorities from the capturing streams: the chain's kernels go ahead of the trailing
+    // updates when both wait for an SM
+    if (cudaGraphInstantiate(&g->exec, graph, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess) {
       (void)cudaGetLastError();
       g->exec = nullptr;
     }

@@ -805,8 +805,9 @@ void plan_workspace(mcsdp_ctx *c) {
     plan_buf(c, cur, "gmV", gm ? (size_t)(GM_K + 2) * m * 8 : 0);
     plan_buf(c, cur, "gmH", gm ? (size_t)6 * (GM_K + 2) * 8 : 0);
     const bool tc = mx && c->opt.tensor_cores != 0 && m >= 2 * TC_PANEL;
-    plan_buf(c, cur, "tc_hi", tc ? (size_t)tc_panel(m) * m * 4 : 0);
-    plan_buf(c, cur, "tc_lo", tc ? (size_t)tc_panel(m) * m * 4 : 0);
+    // two buffers each: the chain splits panel k + 1 while panel k's update still reads k's
+    plan_buf(c, cur, "tc_hi", tc ? (size_t)2 * tc_panel(m) * m * 4 : 0);
+    plan_buf(c, cur, "tc_lo", tc ? (size_t)2 * tc_panel(m) * m * 4 : 0);
     plan_buf(c, cur, "L32", mx ? (size_t)nnzL * 4 : 0);
     plan_buf(c, cur, "N32", mx ? (size_t)nnzL * 4 : 0);
     plan_buf(c, cur, "dL32", mx ? (size_t)nnzD * 4 : 0);
@@ -2270,7 +2271,8 @@ bool graph_iteration(mcsdp_ctx *c, mcsdp_status *s) {
     }
     c->launches = l0;
     if (bs != MCSDP_OK || ec != cudaSuccess || !graph ||
-        cudaGraphInstantiate(&c->iter_exec, graph, 0) != cudaSuccess) {
+        cudaGraphInstantiate(&c->iter_exec, graph, cudaGraphInstantiateFlagUseNodePriority) !=
+            cudaSuccess) {
       (void)cudaGetLastError();
       if (graph) cudaGraphDestroy(graph);
       c->iter_exec = nullptr;
