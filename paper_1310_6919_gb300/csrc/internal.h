@@ -402,9 +402,13 @@ int dense_chol_f32(float *B, int64_t ldb, int m, int *status, float *Linv, cudaS
 // dsc_i = 1 / sqrt(B_ii) (a unit diagonal: the scales of B's rows no longer spend FP32 range),
 // and the refinement solves through S (pass the same dsc to mixed_refine_step).  shift is added
 // to the diagonal of the matrix factored (a preconditioner when the FP32 factor of B breaks down).
+// tinv (may be null; m >= 4096): the inverses of the factor's diagonal blocks of 1024 rows are
+// formed there for the substitutions (trsv_tinv_buffer_floats(m) floats)
 int mixed_factor(double *B, int64_t ldb, int m, float *B32, float *Linv32, int *status,
-                 double *g, double *r, double *x, double *dsc, double shift, cudaStream_t st,
-                 CholStreams *cs);
+                 double *g, double *r, double *x, double *dsc, double shift, float *tinv,
+                 cudaStream_t st, CholStreams *cs);
+int64_t trsv_tinv_floats(int m);
+int64_t trsv_tinv_buffer_floats(int m);
 // number of column chunks of the refinement's matrix-vector product (P, A hold chunks x m)
 int mixed_chunks(int m);
 // one refinement step: x += (L32 L32^T)^{-1} r, then r = g - B x (FP64) and
@@ -412,14 +416,14 @@ int mixed_chunks(int m);
 // of 1024 rows over all SMs (P holds their FP32 vector), below that one cluster of 8 CTAs
 int mixed_refine_step(const double *B, int64_t ldb, int m, const float *L32, const float *Linv32,
                       const double *g, double *x, double *r, double *P, double *A, double *norms,
-                      const double *dsc, cudaStream_t st);
+                      const double *dsc, const float *tinv, cudaStream_t st);
 // GMRES form of the mixed SCE solve (m >= 4096): out = B v; w = S (L32 L32^T)^{-1} S u (the
 // preconditioner: the FP32 factor of the equilibrated S B S, S = diag(dsc)); r = g - B x with
 // norms = (max|r|, max(|B||x| + |g|)).  P and A are the refinement's partial-product buffers.
 int mixed_matvec(const double *B, int64_t ldb, int m, const double *v, double *out, double *P,
                  double *A, cudaStream_t st);
 int mixed_precond(const float *L32, int m, const float *Linv32, const double *u, double *w,
-                  double *P, const double *dsc, cudaStream_t st);
+                  double *P, const double *dsc, const float *tinv, cudaStream_t st);
 int mixed_residual(const double *B, int64_t ldb, int m, const double *g, const double *x,
                    double *r, double *P, double *A, double *norms, cudaStream_t st);
 void launch_rhs_border(const DevSym &S, double *B, int64_t ldb, const double *hvec, double betamu,

@@ -1498,11 +1498,11 @@ __global__ void __launch_bounds__(TP) k_trsv_panel(const float *__restrict__ L, 
 // r < k0, with L^T (the upper triangle holds L^T[r][k0 + c] at [r + (k0 + c) m])
 template <bool FWD>
 __global__ void __launch_bounds__(256) k_trsv_update(const float *__restrict__ L, int m, int k0,
-                                                    int pw, float *y) {
+                                                    int pw, const float *ysrc, float *y) {
   __shared__ float part[8][33];
   __shared__ float yp[TP];
   const int il = threadIdx.x & 31, ph = threadIdx.x >> 5;
-  for (int c = threadIdx.x; c < pw; c += 256) yp[c] = y[k0 + c];
+  for (int c = threadIdx.x; c < pw; c += 256) yp[c] = ysrc[k0 + c];
   __syncthreads();
   const int r = (FWD ? k0 + pw : 0) + blockIdx.x * 32 + il;
   const int rend = FWD ? m : k0;
@@ -1548,7 +1548,7 @@ static int trsv_blocked(const float *L, int m, const float *Linv, const double *
     ++nl;
     const int rows = m - k0 - pw;
     if (rows > 0) {
-      k_trsv_update<true><<<(rows + 31) / 32, 256, 0, st>>>(L, m, k0, pw, y);
+      k_trsv_update<true><<<(rows + 31) / 32, 256, 0, st>>>(L, m, k0, pw, y, y);
       ++nl;
     }
   }
@@ -1557,11 +1557,89 @@ static int trsv_blocked(const float *L, int m, const float *Linv, const double *
     k_trsv_panel<false><<<1, TP, 0, st>>>(L, m, Linv, k0, y);
     ++nl;
     if (k0 > 0) {
-      k_trsv_update<false><<<(k0 + 31) / 32, 256, 0, st>>>(L, m, k0, std::min(TP, m - k0), y);
+      k_trsv_update<false><<<(k0 + 31) / 32, 256, 0, st>>>(L, m, k0, std::min(TP, m - k0), y, y);
       ++nl;
     }
   }
   k_trsv_store<<<blocks, 256, 0, st>>>(y, x, m, dsc);
+  return nl;
+}
+
+// The same substitutions with the inverses T_p of the factor's diagonal blocks of TP rows
+// precomputed (trsv_prepare_blocks): each panel is one product with T_p (FWD: T_p y, lower; BWD:
+// T_p^T y) instead of a serial chain of 32-row blocks, so a solve is 2 x 2 x (m / TP) launches
+// of bandwidth-bound work.  The panel's values are read from src and written to dst (no CTA
+// overwrites what another still reads).
+template <bool FWD>
+__global__ void __launch_bounds__(256) k_trsv_diag(const float *__restrict__ T, int pw,
+                                                  const float *__restrict__ src, float *dst) {
+  __shared__ float ys[TP];
+  __shared__ float part[8][33];
+  for (int c = threadIdx.x; c < pw; c += 256) ys[c] = src[c];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (FWD) {  // CTA = 32 rows x 8 column phases; lanes take consecutive rows of a column of T
+    const int r = blockIdx.x * 32 + lane;
+    float a = 0.f;
+    if (r < pw)
+      for (int c = w; c <= r; c += 8) a = fmaf(T[r + (int64_t)c * TP], ys[c], a);
+    part[w][lane] = a;
+    __syncthreads();
+    if (w == 0 && r < pw) {
+      float t = 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) t += part[q][lane];
+      dst[r] = t;
+    }
+  } else {  // a warp per output r: column r of T (rows c >= r, contiguous), lanes along it
+    const int r = blockIdx.x * 8 + w;
+    if (r >= pw) return;
+    float a = 0.f;
+    for (int c = r + lane; c < pw; c += 32) a = fmaf(T[c + (int64_t)r * TP], ys[c], a);
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) dst[r] = a;
+  }
+}
+
+// T_p = inverse of the factor's diagonal block p (TP x TP, lower; column-major, ld TP, at
+// tinv + p TP^2), from the 32 x 32 block inverses; work: 256 (TP + 256) floats
+int trsv_prepare_blocks(const float *L, int m, const float *Linv, float *tinv, float *work,
+                        cudaStream_t st) {
+  int nl = 0;
+  for (int k0 = 0, p = 0; k0 < m; k0 += TP, ++p)
+    nl += dense_trtri<float>(L + k0 + (int64_t)k0 * m, m, Linv + (int64_t)(k0 / NB) * NB * NB,
+                             tinv + (int64_t)p * TP * TP, TP, std::min(TP, m - k0), work, st);
+  return nl;
+}
+
+static int trsv_blocked_inv(const float *L, int m, const float *tinv, const double *r, double *x,
+                            float *ya, float *yb, const double *dsc, cudaStream_t st) {
+  const int blocks = std::min(152 * 8, (m + 255) / 256);
+  k_trsv_load<<<blocks, 256, 0, st>>>(r, ya, m, dsc);
+  int nl = 2;
+  const int np = (m + TP - 1) / TP;
+  for (int p = 0; p < np; ++p) {  // forward: yb_p = T_p ya_p, then the rows below in ya
+    const int k0 = p * TP, pw = std::min(TP, m - k0);
+    k_trsv_diag<true><<<(pw + 31) / 32, 256, 0, st>>>(tinv + (int64_t)p * TP * TP, pw, ya + k0,
+                                                      yb + k0);
+    ++nl;
+    const int rows = m - k0 - pw;
+    if (rows > 0) {
+      k_trsv_update<true><<<(rows + 31) / 32, 256, 0, st>>>(L, m, k0, pw, yb, ya);
+      ++nl;
+    }
+  }
+  for (int p = np - 1; p >= 0; --p) {  // backward: ya_p = T_p^T yb_p, then the rows above in yb
+    const int k0 = p * TP, pw = std::min(TP, m - k0);
+    k_trsv_diag<false><<<(pw + 7) / 8, 256, 0, st>>>(tinv + (int64_t)p * TP * TP, pw, yb + k0,
+                                                     ya + k0);
+    ++nl;
+    if (k0 > 0) {
+      k_trsv_update<false><<<(k0 + 31) / 32, 256, 0, st>>>(L, m, k0, pw, ya, yb);
+      ++nl;
+    }
+  }
+  k_trsv_store<<<blocks, 256, 0, st>>>(ya, x, m, dsc);
   return nl;
 }
 
@@ -1664,24 +1742,32 @@ __global__ void k_mixed_scale(const double *__restrict__ B, int64_t ldb, int m, 
 }
 
 int mixed_factor(double *B, int64_t ldb, int m, float *B32, float *Linv32, int *status,
-                 double *g, double *r, double *x, double *dsc, double shift, cudaStream_t st,
-                 CholStreams *cs) {
+                 double *g, double *r, double *x, double *dsc, double shift, float *tinv,
+                 cudaStream_t st, CholStreams *cs) {
   k_mixed_init<<<(m + 255) / 256, 256, 0, st>>>(B, ldb, m, g, r, x);
   const int nt = (m + 31) / 32;
   const bool eq = dsc && m >= TRSV_WIDE_M;
   if (eq) k_mixed_scale<<<(m + 255) / 256, 256, 0, st>>>(B, ldb, m, dsc);
   k_mixed_prep<<<dim3(nt, nt), 256, 0, st>>>(B, ldb, B32, m, eq ? dsc : nullptr, shift);
   // the factorisation leaves L^T in the strict upper triangle of B32 as well
-  return 2 + (eq ? 1 : 0) + dense_chol_f32(B32, m, m, status, Linv32, st, cs);
+  int nl = 2 + (eq ? 1 : 0) + dense_chol_f32(B32, m, m, status, Linv32, st, cs);
+  if (tinv && m >= TRSV_WIDE_M)
+    nl += trsv_prepare_blocks(B32, m, Linv32, tinv, tinv + trsv_tinv_floats(m), st);
+  return nl;
 }
+
+int64_t trsv_tinv_floats(int m) { return (int64_t)((m + TP - 1) / TP) * TP * TP; }
+int64_t trsv_tinv_buffer_floats(int m) { return trsv_tinv_floats(m) + (int64_t)256 * (TP + 256); }
 
 int mixed_refine_step(const double *B, int64_t ldb, int m, const float *L32, const float *Linv32,
                       const double *g, double *x, double *r, double *P, double *A, double *norms,
-                      const double *dsc, cudaStream_t st) {
+                      const double *dsc, const float *tinv, cudaStream_t st) {
   int nl = 2;
   if (m >= TRSV_WIDE_M) {
-    // P (chunks x m doubles) is free until the product below: the FP32 vector
-    nl += trsv_blocked(L32, m, Linv32, r, x, reinterpret_cast<float *>(P), dsc, st);
+    // P (chunks x m doubles) is free until the product below: the FP32 vectors
+    float *ya = reinterpret_cast<float *>(P);
+    nl += tinv ? trsv_blocked_inv(L32, m, tinv, r, x, ya, ya + m, dsc, st)
+               : trsv_blocked(L32, m, Linv32, r, x, ya, dsc, st);
   } else {
     ++nl;
     const size_t smem = (size_t)m * sizeof(float);
@@ -1715,9 +1801,11 @@ int mixed_matvec(const double *B, int64_t ldb, int m, const double *v, double *o
 }
 
 int mixed_precond(const float *L32, int m, const float *Linv32, const double *u, double *w,
-                  double *P, const double *dsc, cudaStream_t st) {
+                  double *P, const double *dsc, const float *tinv, cudaStream_t st) {
   cudaMemsetAsync(w, 0, (size_t)m * sizeof(double), st);
-  return trsv_blocked(L32, m, Linv32, u, w, reinterpret_cast<float *>(P), dsc, st);
+  float *ya = reinterpret_cast<float *>(P);
+  return tinv ? trsv_blocked_inv(L32, m, tinv, u, w, ya, ya + m, dsc, st)
+              : trsv_blocked(L32, m, Linv32, u, w, ya, dsc, st);
 }
 
 int mixed_residual(const double *B, int64_t ldb, int m, const double *g, const double *x,

@@ -145,6 +145,7 @@ struct mcsdp_ctx {
   double *gref = nullptr, *rref = nullptr, *yref = nullptr, *ayref = nullptr, *nref = nullptr;
   double *dscl = nullptr;  // the mixed factor's equilibration (large m)
   double *gmV = nullptr, *gmH = nullptr;  // GMRES basis and small vectors (large m)
+  float *tinv = nullptr;  // the FP32 factor's diagonal-block inverses (large m)
   bool promoted = false;        // the FP64 factor is used for the rest of the solve
   bool fp64_asm = false;        // the SCM and the P-MATRIX are assembled in FP64 (mixed form)
   // mixed form, FP32 assembly stage with a dense root: the root blocks of Y and X̄ are factored
@@ -804,6 +805,7 @@ void plan_workspace(mcsdp_ctx *c) {
     const bool gm = mx && m >= MIXED_LONG_M;
     plan_buf(c, cur, "gmV", gm ? (size_t)(GM_K + 2) * m * 8 : 0);
     plan_buf(c, cur, "gmH", gm ? (size_t)6 * (GM_K + 2) * 8 : 0);
+    plan_buf(c, cur, "tinv", gm ? (size_t)trsv_tinv_buffer_floats(m) * 4 : 0);
     const bool tc = mx && c->opt.tensor_cores != 0 && m >= 2 * TC_PANEL;
     // two buffers each: the chain splits panel k + 1 while panel k's update still reads k's
     plan_buf(c, cur, "tc_hi", tc ? (size_t)2 * tc_panel(m) * m * 4 : 0);
@@ -963,6 +965,7 @@ void bind_pointers(mcsdp_ctx *c) {
   c->dscl = wsp<double>(c, "dscl");
   c->gmV = wsp<double>(c, "gmV");
   c->gmH = wsp<double>(c, "gmH");
+  c->tinv = c->gmV ? wsp<float>(c, "tinv") : nullptr;
   {
     const bool tc = c->opt.precision == 1 && c->opt.tensor_cores != 0 && c->S.m >= 2 * TC_PANEL;
     c->cs.tc_hi = tc ? wsp<float>(c, "tc_hi") : nullptr;
@@ -1775,7 +1778,7 @@ mcsdp_status mixed_sce(mcsdp_ctx *c, bool b32, bool *solved) {
       {
         KScope k1(c, KC_CHOL32);
         k1.done(mixed_factor(c->B, c->ldb, m, c->B32, c->Linv32, c->status + 4, c->gref, c->rref,
-                             c->xs, c->dscl, sigma, c->stream, &c->cs));
+                             c->xs, c->dscl, sigma, c->tinv, c->stream, &c->cs));
       }
       KCHECK(c);
       int fst = 0;
@@ -1796,7 +1799,7 @@ mcsdp_status mixed_sce(mcsdp_ctx *c, bool b32, bool *solved) {
   {
     KScope k1(c, KC_CHOL32);
     k1.done(mixed_factor(c->B, c->ldb, m, c->B32, c->Linv32, c->status + 4, c->gref, c->rref,
-                         c->xs, c->dscl, 0.0, c->stream, &c->cs));
+                         c->xs, c->dscl, 0.0, c->tinv, c->stream, &c->cs));
   }
   KCHECK(c);
   double prev = 1.0;
@@ -1805,7 +1808,7 @@ mcsdp_status mixed_sce(mcsdp_ctx *c, bool b32, bool *solved) {
     {
       KScope k2(c, KC_BSOLVE);
       k2.done(mixed_refine_step(c->B, c->ldb, m, c->B32, c->Linv32, c->gref, c->xs, c->rref,
-                                c->yref, c->ayref, c->nref, c->dscl, c->stream));
+                                c->yref, c->ayref, c->nref, c->dscl, c->tinv, c->stream));
     }
     KCHECK(c);
     double nr[2];
@@ -1851,7 +1854,7 @@ mcsdp_status mixed_gmres(mcsdp_ctx *c, double tol_ok, double tol_stall, bool *so
     int k = 0;
     {
       KScope kb(c, KC_BSOLVE);
-      int nl = mixed_precond(c->B32, m, c->Linv32, c->rref, V, c->yref, c->dscl, st);
+      int nl = mixed_precond(c->B32, m, c->Linv32, c->rref, V, c->yref, c->dscl, c->tinv, st);
       lz_beta(m, V, V, V, nullptr, sn, GM_K, st);
       double b = 0.0;
       CUDA_TRY(c, cudaMemcpyAsync(&b, sn + 2 * GM_K + 1, 8, cudaMemcpyDeviceToHost, st));
@@ -1861,7 +1864,7 @@ mcsdp_status mixed_gmres(mcsdp_ctx *c, double tol_ok, double tol_stall, bool *so
       for (int j = 0; j < GM_K && beta0 > 0.0; ++j) {
         double *vj = V + (size_t)j * m, *w = V + (size_t)(j + 1) * m;
         nl += mixed_matvec(c->B, c->ldb, m, vj, tv, c->yref, c->ayref, st);
-        nl += mixed_precond(c->B32, m, c->Linv32, tv, w, c->yref, c->dscl, st);
+        nl += mixed_precond(c->B32, m, c->Linv32, tv, w, c->yref, c->dscl, c->tinv, st);
         lz_reorth(m, j + 1, w, V, V, h1, st);
         lz_reorth(m, j + 1, w, V, V, h2, st);
         lz_beta(m, w, w, w, nullptr, sn, j, st);
