@@ -49,7 +49,7 @@ constexpr int NCAND = 16;  // candidates per dual step-length round
 constexpr int LZ_MAX = 64;  // Lanczos steps of the dense-root step-length bounds
 // mixed form: from this m on the SCE is solved by GMRES preconditioned with the FP32 factor
 constexpr int MIXED_LONG_M = 4096;
-constexpr int GM_K = 40, GM_CYCLES = 8;  // GMRES restart length and cycles
+constexpr int GM_K = 40, GM_CYCLES = 8;  // GMRES restart length (<= 128) and cycles
 // the largest clique (rows / columns) the shared-memory clique kernels take: Algorithm 1 and the
 // primal step stage two k x k FP64 blocks (2 k^2 8 B <= 208 KB at k = 112)
 constexpr int SMALL_ROWS = 112, SMALL_COLS = 96;
@@ -1753,8 +1753,9 @@ struct IterOut {
 //   the true residual after each cycle (a cycle stops once the preconditioned residual has
 //   fallen by 1e-7: the FP32 preconditioner bounds what one cycle gains); abandoned when a cycle
 //   fails to halve omega above m eps64 or after GM_CYCLES cycles.  When the FP32 factor of S B S
-//   breaks down near the optimum, the factor of S B S + sigma I (sigma = 1e-6, then 1e-4)
-//   preconditions the same GMRES on B.  An Arnoldi step (the substitutions over all SMs and one
+//   breaks down near the optimum, the factor of S B S + sigma I (sigma = 1e-5, 1e-4, then 1e-3)
+//   preconditions the same GMRES on B (such a preconditioner leaves the eigenvalues of S B S below
+//   sigma to the Krylov space: a longer restart, 100, was measured no better on config 3).  An Arnoldi step (the substitutions over all SMs and one
 //   FP64 product with B, O(m^2)) costs about a thousandth of the FP64 factorisation (O(m^3)).
 // Leaves x in c->xs (internal order).
 constexpr int MIXED_MAX_STEPS = 10;
@@ -1771,8 +1772,8 @@ mcsdp_status mixed_sce(mcsdp_ctx *c, bool b32, bool *solved) {
   const double tol_stall = b32 ? 1e-10 : (double)m * eps;
   if (m >= MIXED_LONG_M && c->gmV) {
     // GMRES form: when the FP32 factor of S B S breaks down, that of S B S + sigma I (unit
-    // diagonal, sigma = 1e-6, then 1e-4) still preconditions GMRES on B itself
-    const double shifts[3] = {0.0, 1e-6, 1e-4};
+    // diagonal, sigma = 1e-5, 1e-4, then 1e-3) still preconditions GMRES on B itself
+    const double shifts[4] = {0.0, 1e-5, 1e-4, 1e-3};
     for (double sigma : shifts) {
       CUDA_TRY(c, cudaMemsetAsync(c->status + 4, 0, sizeof(int), c->stream));
       {
