@@ -37,6 +37,7 @@ WORKLOAD_DESC = ("max-cut SDP of a random sparse graph: Hamiltonian ring over a 
                  "+ 2n distinct random edges (average degree 6), w ~ U[0,1), C = -L/4, "
                  "A_k = e_k e_k^T, b = 1, n = m = 20000, seed 20131104")
 CONTEXT_WORKLOAD = "block_arrow_2020"
+BLOCKS_WORKLOAD = "maxcut_sum_64"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_SOURCE = ("derived: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz = 1.26 TFLOP/s "
                     "(nominal 1.25; no measured FP64 peak on this pool)")
@@ -493,7 +494,50 @@ def other_legs(args, dev, stream):
         batched[name] = leg
         del probs
         torch.cuda.empty_cache()
+    out["scm_blocks"] = blocks_leg(dev, stream)
     return out, batched
+
+
+def blocks_leg(dev, stream):
+    """The block-diagonal SCM (the sparse-SCM case): 64 random max-cut SDPs as one SDP, solved
+    with B assembled and factored block by block, and the whole-matrix factorisation of the same
+    B for three iterations (its per-iteration time; a whole solve would take minutes)."""
+    import torch
+    from instances import workload
+    from paper_1310_6919_gb300 import Problem
+    inst = workload(BLOCKS_WORKLOAD)
+    z0 = torch.tensor(inst.z0, dtype=torch.float64, device=f"cuda:{dev}")
+
+    def run(max_iter, **o):
+        P = Problem.from_instance(inst, device=dev, profile=1, max_iter=max_iter, **o)
+        P.set_iterate(None, z0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = P.solve()
+        e1.record(stream)
+        e1.synchronize()
+        st = P.stats()
+        it = max(1, int(r["iters"]))
+        chol = (st["ms"]["scm_chol"] + st["ms"]["sce_backsolve"]) / it
+        return r, e0.elapsed_time(e1), chol, P.info
+
+    run(100)  # warm-up (kernel attributes, first-use paths)
+    r, ms, chol, info = run(100)
+    it = max(1, int(r["iters"]))
+    out = {"workload": BLOCKS_WORKLOAD, "n": inst.n, "m": inst.m, "components": info["ncomp"],
+           "scm_density": float(sum(p[2] ** 2 for p in inst.meta["parts"])) / inst.m ** 2,
+           "blocks": {"s_per_solve": ms * 1e-3, "iterations": it, "status": int(r["status"]),
+                      "pobj": r["pobj"], "gap": r["gap"], "ms_per_iter": ms / it,
+                      "scm_factor_solve_ms_per_iter": chol}}
+    r1, ms1, chol1, _ = run(3, scm_blocks=1)
+    it1 = max(1, int(r1["iters"]))
+    out["whole"] = {"iterations": it1, "ms_per_iter": ms1 / it1, "scm_factor_solve_ms_per_iter": chol1}
+    out["factor_solve_speedup"] = chol1 / chol if chol > 0 else None
+    out["timing"] = ("CUDA events around mcsdp_solve with per-class profiling on (profile = 1); "
+                     "the factor+solve figures are the scm_chol + sce_backsolve classes")
+    torch.cuda.empty_cache()
+    return out
 
 
 def main():

@@ -133,6 +133,15 @@ typedef struct {
                             about a hundred launches and eight synchronisations; same iterates as
                             0.  FP64 form without a dense root only (else ignored); per-class
                             times (profile) are then not measured.  0 (default) = off */
+  int32_t scm_blocks;    /* block-diagonal SCM (the sparse-SCM case of Sec. 3.1: B_pq = 0 when
+                            A_p and A_q lie in different connected components of the aggregate
+                            pattern, X̂ and Y^{-1} being block-diagonal over them; components are
+                            joined through each constraint's support).  0 (default) = when the
+                            constraints fall into more than one component, the cross-component
+                            blocks of B are neither assembled nor factored: one bordered Cholesky
+                            and one backward substitution per diagonal block, in FP64 (the mixed
+                            form's FP32 factor then does not apply; its FP32 solves do); 1 = one
+                            factorisation of the whole m x m matrix, as for a connected pattern */
 } mcsdp_options;
 
 void mcsdp_default_options(mcsdp_options *opt);
@@ -160,6 +169,9 @@ typedef struct {
   int64_t nnz_lower_E;  /* entries of lower(E) including the diagonal */
   int64_t nslot;        /* distinct lower positions of the aggregate pattern */
   int64_t table_bytes;  /* bytes of symbolic tables mcsdp_set_workspace copies host -> device */
+  int32_t ncomp;        /* connected components holding constraints (the diagonal blocks of B;
+                           internal constraint order keeps each one contiguous) */
+  int32_t scm_blocks;   /* 1 = B is assembled and factored block by block (options.scm_blocks) */
 } mcsdp_sym_info;
 mcsdp_status mcsdp_sym_info_get(const mcsdp_ctx *ctx, mcsdp_sym_info *info);
 

@@ -6,8 +6,9 @@ paper's notation (Sec. 1, problems (P)/(D)); it holds none of the method's arith
 from .rng import Xoshiro256ss
 from .problems import (SDPInstance, lattice_maxcut, cycle_maxcut, complete_maxcut, graph_maxcut,
                        block_arrow, random_ring_maxcut, random_gnm_maxcut, small_random_sdp,
-                       diagonal_lp_sdp, batch_mix, workload)
+                       diagonal_lp_sdp, batch_mix, direct_sum, maxcut_direct_sum, workload)
 
 __all__ = ["Xoshiro256ss", "SDPInstance", "lattice_maxcut", "cycle_maxcut", "complete_maxcut",
            "graph_maxcut", "block_arrow", "random_ring_maxcut", "random_gnm_maxcut",
-           "small_random_sdp", "diagonal_lp_sdp", "batch_mix", "workload"]
+           "small_random_sdp", "diagonal_lp_sdp", "batch_mix", "direct_sum",
+           "maxcut_direct_sum", "workload"]

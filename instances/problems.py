@@ -271,10 +271,48 @@ def batch_mix(n_maxcut, n_arrow, seed=SEED_BASE + 4):
     return out
 
 
+def direct_sum(parts, name=None):
+    """Block-diagonal SDP from independent ones: part p's matrices on rows/columns offset by
+    n_0 + .. + n_{p-1}, its constraints numbered after the earlier parts' (A_0 is the sum of the
+    parts' A_0), b and z0 concatenated.  Its aggregate pattern, X̂, Y^{-1} and Schur complement
+    matrix are block-diagonal over the parts, and its optimal value is the sum of theirs."""
+    mats, rows, cols, vals, bs, z0s = [], [], [], [], [], []
+    no = mo = 0
+    for inst in parts:
+        mats.append(np.where(inst.mat > 0, inst.mat + mo, 0).astype(np.int32))
+        rows.append(inst.row + no)
+        cols.append(inst.col + no)
+        vals.append(inst.val)
+        bs.append(inst.b)
+        z0s.append(inst.z0)
+        no += inst.n
+        mo += inst.m
+    mat, row, col = np.concatenate(mats), np.concatenate(rows), np.concatenate(cols)
+    order = np.lexsort((col, row, mat))
+    z0 = None if any(z is None for z in z0s) else np.concatenate(z0s)
+    meta = {"kind": "direct_sum", "parts": [(p.name, p.n, p.m) for p in parts]}
+    return SDPInstance(name or f"direct_sum_{len(parts)}", no, mo, np.concatenate(bs),
+                       mat[order].astype(np.int32), row[order].astype(np.int32),
+                       col[order].astype(np.int32), np.concatenate(vals)[order], z0, meta)
+
+
+def maxcut_direct_sum(k, seed=SEED_BASE + 7):
+    """Direct sum of k max-cut relaxations on G(n, floor(5n/2)) with n ~ U{50..400}, weights
+    U[0,1) (the max-cut half of the batched configuration's mix, as one SDP): a problem whose
+    Schur complement matrix is block-diagonal with k blocks.  Part p draws from seed + 1000 + p."""
+    rng = Xoshiro256ss(seed)
+    parts = []
+    for p in range(k):
+        n = 50 + rng.below(351)
+        parts.append(random_gnm_maxcut(n, (5 * n) // 2, seed + 1000 + p))
+    return direct_sum(parts, name=f"maxcut_sum_{k}")
+
+
 def workload(name, seed=None):
     """Named workloads: 'grid_maxcut_100' (10x10 lattice), 'block_arrow_2020' (40 x 50 + 20,
     m = 2000), 'block_arrow_1020' (20 x 50 + 20, m = 1000), 'ring_maxcut_20000', and
-    'ring_maxcut_8000' (the same family at n = 8000: a case small enough for profiler captures)."""
+    'ring_maxcut_8000' (the same family at n = 8000: a case small enough for profiler captures),
+    and 'maxcut_sum_64' (64 random max-cut SDPs as one block-diagonal SDP)."""
     if name == "grid_maxcut_100":
         return lattice_maxcut(10, 10, seed=SEED_BASE + 1 if seed is None else seed)
     if name == "block_arrow_2020":
@@ -285,4 +323,6 @@ def workload(name, seed=None):
         return random_ring_maxcut(20000, seed=SEED_BASE + 3 if seed is None else seed)
     if name == "ring_maxcut_8000":
         return random_ring_maxcut(8000, seed=SEED_BASE + 6 if seed is None else seed)
+    if name == "maxcut_sum_64":
+        return maxcut_direct_sum(64, seed=SEED_BASE + 7 if seed is None else seed)
     raise KeyError(name)

@@ -20,7 +20,8 @@ class Options_t(C.Structure):
                 ("panel_max", C.c_int32), ("group_max", C.c_int32),
                 ("panel_budget_mb", C.c_double), ("profile", C.c_int32), ("relax", C.c_int32),
                 ("solve_warps", C.c_int32), ("mixed_gap", C.c_double), ("root_rows", C.c_int32),
-                ("tensor_cores", C.c_int32), ("mixed_asm_gap", C.c_double), ("graph", C.c_int32)]
+                ("tensor_cores", C.c_int32), ("mixed_asm_gap", C.c_double), ("graph", C.c_int32),
+                ("scm_blocks", C.c_int32)]
 
 
 class Work_t(C.Structure):
@@ -40,7 +41,8 @@ class SymInfo_t(C.Structure):
     _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("nsuper", C.c_int32),
                 ("ngroup", C.c_int32), ("max_nrow", C.c_int32), ("max_ncol", C.c_int32),
                 ("tree_height", C.c_int32), ("nnz_layout", C.c_int64),
-                ("nnz_lower_E", C.c_int64), ("nslot", C.c_int64), ("table_bytes", C.c_int64)]
+                ("nnz_lower_E", C.c_int64), ("nslot", C.c_int64), ("table_bytes", C.c_int64),
+                ("ncomp", C.c_int32), ("scm_blocks", C.c_int32)]
 
 
 class Result_t(C.Structure):

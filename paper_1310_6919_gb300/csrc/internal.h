@@ -85,6 +85,8 @@ struct DevSym {
   const int *rs_ptr, *rs_col;
   const int64_t *rs_off;
   const int *con_order, *grp_cptr, *grp_pptr, *grp_cols;
+  // block-diagonal SCM: row of B holding internal constraint i's right-hand side (nullptr: m)
+  const int *bord;
   const int64_t *grp_rowoff;
   const int *anz_ptr;
   const int16_t *anz_a, *anz_b;

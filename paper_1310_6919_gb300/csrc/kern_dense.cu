@@ -1215,12 +1215,13 @@ int dense_backsolve(const double *B, int64_t ldb, int m, const double *Linv_all,
   return launches;
 }
 
-// row m of B <- g_i = b_{user(i)} - beta mu h_i   (internal order)
+// row m of B <- g_i = b_{user(i)} - beta mu h_i   (internal order; with a block-diagonal B, row
+// S.bord[i], the row after i's diagonal block)
 __global__ void k_rhs_border(DevSym S, double *B, int64_t ldb, const double *hvec, double betamu,
                              const double *__restrict__ betamu_dev) {
   if (betamu_dev) betamu = *betamu_dev;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.m; i += gridDim.x * blockDim.x)
-    B[S.m + (int64_t)i * ldb] = S.b[S.con_order[i]] - betamu * hvec[i];
+    B[(S.bord ? S.bord[i] : S.m) + (int64_t)i * ldb] = S.b[S.con_order[i]] - betamu * hvec[i];
 }
 
 void launch_rhs_border(const DevSym &S, double *B, int64_t ldb, const double *hvec, double betamu,
@@ -1246,7 +1247,10 @@ __global__ void k_B_to_user(DevSym S, const double *Bi, int64_t ldi, double *Bo,
     if (i < j) continue;
     const int ui = S.con_order[i], uj = S.con_order[j];
     const int r = ui > uj ? ui : uj, c = ui > uj ? uj : ui;
-    Bo[r + (int64_t)c * ldo] = Bi[i + (int64_t)j * ldi];
+    // a block-diagonal B stores nothing between components (those entries are zero; the
+    // right-hand side of a block may sit there)
+    const bool cross = S.bord && S.bord[i] != S.bord[j];
+    Bo[r + (int64_t)c * ldo] = cross ? 0.0 : Bi[i + (int64_t)j * ldi];
   }
   if (ho)
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;

@@ -989,10 +989,11 @@ void launch_con_apply(const DevSym &S, const double *M, const double *add, doubl
   k_con_apply<<<(S.m + 255) / 256, 256, 0, st>>>(S, M, add, out);
 }
 
-// row m of B <- rhs (caller order) in the internal constraint order
+// row m of B (row S.bord[i] for a block-diagonal B) <- rhs (caller order) in the internal
+// constraint order
 __global__ void k_border_from_user(DevSym S, double *B, int64_t ldb, const double *__restrict__ rhs) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.m; i += gridDim.x * blockDim.x)
-    B[S.m + (int64_t)i * ldb] = rhs[S.con_order[i]];
+    B[(S.bord ? S.bord[i] : S.m) + (int64_t)i * ldb] = rhs[S.con_order[i]];
 }
 void launch_border_from_user(const DevSym &S, double *B, int64_t ldb, const double *rhs,
                              cudaStream_t st) {

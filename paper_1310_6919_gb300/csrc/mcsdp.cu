@@ -96,6 +96,13 @@ struct mcsdp_ctx {
   SolveCfg scfg{};
   int num_sms = 152;
   std::vector<int2> tiles_all;
+  // block-diagonal SCM (more than one component, options.scm_blocks = 0): per internal
+  // constraint, the row of B that holds its right-hand side (its component's end: a row of that
+  // block's columns outside every diagonal block, or m for the last component); per component,
+  // the offset of its diagonal-tile inverses in Binv (ncomp + 1 entries)
+  bool blocks = false;
+  std::vector<int> bord;
+  std::vector<int64_t> binv_off;
   std::vector<double> z0_default;
   bool z0_ok = false;
   // the input entries as given (caller order), for per-entry gradients
@@ -319,6 +326,7 @@ void plan_workspace(mcsdp_ctx *c) {
   c->nF = n - c->nR;
   c->colF0 = (c->nR + 31) / 32 * 32;
   c->nlev = c->dense ? S.height - 1 : S.height;
+  c->blocks = S.ncomp > 1 && c->opt.scm_blocks == 0;
   plan_table(c, cur, "sn_col", S.sn_col);
   plan_table(c, cur, "sn_rowptr", S.sn_rowptr);
   plan_table(c, cur, "rows", S.rows);
@@ -639,7 +647,12 @@ void plan_workspace(mcsdp_ctx *c) {
       }
       nr += pg;
       c->pmax = std::max(c->pmax, pg);
-      for (int h = g; h < S.ngroup; ++h) c->tiles_all.push_back(make_int2(h, g));
+      // groups are contiguous per component: the tiles below the first group of another
+      // component are zero blocks of B
+      for (int h = g; h < S.ngroup; ++h) {
+        if (c->blocks && S.grp_comp[h] != S.grp_comp[g]) break;
+        c->tiles_all.push_back(make_int2(h, g));
+      }
       ++g;
     }
     ch.g1 = g;
@@ -736,7 +749,16 @@ void plan_workspace(mcsdp_ctx *c) {
   plan_buf(c, cur, "Mup", nnzL * 8);
   plan_buf(c, cur, "B", (size_t)c->ldb * m * 8);
   plan_buf(c, cur, "hvec", (size_t)m * 8);
-  plan_buf(c, cur, "Binv", (size_t)((m + 63) / 64) * 64 * 64 * 8);
+  c->binv_off.assign(1, 0);
+  c->bord.clear();
+  for (int q = 0; q < (c->blocks ? S.ncomp : 1); ++q) {
+    const int o = c->blocks ? S.comp_cptr[q] : 0, e = c->blocks ? S.comp_cptr[q + 1] : m;
+    if (c->blocks)
+      for (int i = o; i < e; ++i) c->bord.push_back(e);
+    c->binv_off.push_back(c->binv_off.back() + (int64_t)((e - o + 63) / 64) * 64 * 64);
+  }
+  plan_table(c, cur, "bord", c->bord);
+  plan_buf(c, cur, "Binv", (size_t)c->binv_off.back() * 8);
   plan_buf(c, cur, "xs", (size_t)m * 8);
   plan_buf(c, cur, "dz", (size_t)m * 8);
   plan_buf(c, cur, "W1", (size_t)n * c->ldw * 8);
@@ -881,6 +903,7 @@ void bind_pointers(mcsdp_ctx *c) {
   D.rs_col = wsp<int>(c, "rs_col");
   D.rs_off = wsp<int64_t>(c, "rs_off");
   D.con_order = wsp<int>(c, "con_order");
+  D.bord = c->blocks ? wsp<int>(c, "bord") : nullptr;
   D.grp_cptr = wsp<int>(c, "grp_cptr");
   D.grp_pptr = wsp<int>(c, "grp_pptr");
   D.grp_cols = wsp<int>(c, "grp_cols");
@@ -1677,7 +1700,7 @@ double step_from_bound(double theta, double bound) {
   return lam < -1.0 ? -1.0 / lam : 1.0;
 }
 
-// Step lengths with a dense root (SURVEY reading: Lanczos bounds).  Primal, root clique:
+// Step lengths with a dense root (Lanczos bounds of eq. primal_length2).  Primal, root clique:
 // lambda_min(L^{-1} dX_RR L^{-T}) with X̄_RR = L L^T (RS_P holds L^{-1} and its rows mirrored),
 // dX_RR made full in RS_M.  Dual: lambda_min(Y^{-1} dY), self-adjoint in the Y-inner product, with
 // the dense Y^{-1} of the SCM phase (W2) and Y on the aggregate pattern.  Both are confirmed by
@@ -1763,6 +1786,37 @@ constexpr int MIXED_MAX_STEPS = 10;
 constexpr double MIXED_ASM_GAP_ROOT = 1e-2;
 
 mcsdp_status mixed_gmres(mcsdp_ctx *c, double tol_ok, double tol_stall, bool *solved);
+
+// K4 and K5 in FP64: the bordered Cholesky factorisation of B (the right-hand side in its border
+// row) and the backward substitution; x in c->xs (internal order).  A block-diagonal B
+// (c->blocks): one of each per component q, on the diagonal block at (o, o), o = comp_cptr[q],
+// whose right-hand side k_rhs_border put in row comp_cptr[q + 1] of the block's columns (the row
+// after the block, outside every diagonal block), so that the block is itself a bordered matrix of
+// leading dimension ldb.  The blocks are independent; they run in component order.
+void scm_chol_solve(mcsdp_ctx *c) {
+  const Symbolic &S = c->S;
+  const int nblk = c->blocks ? S.ncomp : 1;
+  auto range = [&](int q, int *o, int *mc) {
+    *o = c->blocks ? S.comp_cptr[q] : 0;
+    *mc = (c->blocks ? S.comp_cptr[q + 1] : S.m) - *o;
+  };
+  int o, mc, nl = 0;
+  KScope k1(c, KC_CHOL);
+  for (int q = 0; q < nblk; ++q) {
+    range(q, &o, &mc);
+    nl += dense_chol_bordered(c->B + o + (int64_t)o * c->ldb, c->ldb, mc, c->status + 2,
+                              c->Binv + c->binv_off[q], c->stream, &c->cs);
+  }
+  k1.done(nl);
+  nl = 0;
+  KScope k2(c, KC_BSOLVE);
+  for (int q = 0; q < nblk; ++q) {
+    range(q, &o, &mc);
+    nl += dense_backsolve(c->B + o + (int64_t)o * c->ldb, c->ldb, mc, c->Binv + c->binv_off[q],
+                          c->xs + o, c->stream);
+  }
+  k2.done(nl);
+}
 
 mcsdp_status mixed_sce(mcsdp_ctx *c, bool b32, bool *solved) {
   const int m = c->S.m;
@@ -1980,7 +2034,8 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
     launch_rhs_border(c->D, c->B, c->ldb, c->hvec, beta * mu, c->stream);
     k0.done(1);
     bool solved = false;
-    if (c->opt.precision == 1 && !c->promoted) {
+    // (a block-diagonal B keeps the FP64 factor: its blocks are small)
+    if (c->opt.precision == 1 && !c->promoted && !c->blocks) {
       s = mixed_sce(c, f32, &solved);
       if (s) return s;
       if (!solved) {
@@ -2002,12 +2057,7 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
         }
       }
     }
-    if (!solved) {
-      KScope k1(c, KC_CHOL);
-      k1.done(dense_chol_bordered(c->B, c->ldb, m, c->status + 2, c->Binv, c->stream, &c->cs));
-      KScope k2(c, KC_BSOLVE);
-      k2.done(dense_backsolve(c->B, c->ldb, m, c->Binv, c->xs, c->stream));
-    }
+    if (!solved) scm_chol_solve(c);
     KScope k3(c, KC_MISC);
     launch_dz_to_user(c->D, c->xs, c->dz, c->stream);
     k3.done(1);
@@ -2180,10 +2230,7 @@ mcsdp_status graph_body(mcsdp_ctx *c) {
     KScope k0(c, KC_MISC);
     launch_rhs_border(c->D, c->B, c->ldb, c->hvec, 0.0, c->stream, g);
     k0.done(1);
-    KScope k1(c, KC_CHOL);
-    k1.done(dense_chol_bordered(c->B, c->ldb, m, c->status + 2, c->Binv, c->stream, &c->cs));
-    KScope k2(c, KC_BSOLVE);
-    k2.done(dense_backsolve(c->B, c->ldb, m, c->Binv, c->xs, c->stream));
+    scm_chol_solve(c);
     KScope k3(c, KC_MISC);
     launch_dz_to_user(c->D, c->xs, c->dz, c->stream);
     k3.done(1);
@@ -2367,6 +2414,7 @@ void mcsdp_default_options(mcsdp_options *o) {
   o->root_rows = 0;
   o->tensor_cores = 1;
   o->mixed_asm_gap = 0.0;
+  o->scm_blocks = 0;
 }
 
 const char *mcsdp_last_error(const mcsdp_ctx *c) { return c ? c->err.c_str() : "null context"; }
@@ -2591,6 +2639,8 @@ mcsdp_status mcsdp_sym_info_get(const mcsdp_ctx *c, mcsdp_sym_info *info) {
   info->nslot = S.nslot;
   info->table_bytes = 0;
   for (const Upload &u : c->uploads) info->table_bytes += (int64_t)u.bytes;
+  info->ncomp = S.ncomp;
+  info->scm_blocks = c->blocks ? 1 : 0;
   return MCSDP_OK;
 }
 
@@ -3015,31 +3065,44 @@ mcsdp_status mcsdp_work_model(const mcsdp_ctx *c, mcsdp_work *w) {
   w->bytes[1] = b1;
   // K3 panels: 2 |P_g| right-hand sides per group, forward along each column's own path,
   // backward over the supernodes needed by the rows of P_h, h >= g
+  // (a block-diagonal B: the tiles, factorisations and substitutions of each diagonal block)
+  const int nblk = c->blocks ? S.ncomp : 1;
+  std::vector<int> gend(S.ngroup, S.ngroup);  // first group after g's block
+  for (int g = S.ngroup - 1; g >= 0; --g)
+    if (c->blocks && g + 1 < S.ngroup && S.grp_comp[g + 1] == S.grp_comp[g]) gend[g] = gend[g + 1];
+    else if (c->blocks) gend[g] = g + 1;
   double fp = 0, bp = 0;
-  const int R = S.grp_pptr[S.ngroup];
   for (int g = 0; g < S.ngroup; ++g) {
     double need = 0;
     for (int64_t t = S.need_ptr[g]; t < S.need_ptr[g + 1]; ++t) need += ent[S.need_sn[t]];
     for (int p = S.grp_pptr[g]; p < S.grp_pptr[g + 1]; ++p) fp += 2 * 2 * (path_entries(S.grp_cols[p]) + need);
-    bp += 8.0 * 2 * (R - S.grp_pptr[g]) * (S.grp_pptr[g + 1] - S.grp_pptr[g]);
+    bp += 8.0 * 2 * (S.grp_pptr[gend[g]] - S.grp_pptr[g]) * (S.grp_pptr[g + 1] - S.grp_pptr[g]);
   }
   w->flops[2] = fp;
   w->bytes[2] = bp + 8 * 2 * nnzE;  // panels written once, both factors read once
   // K3 tiles: one multiply-add per pair of nonzeros of (A_i, A_j), i >= j
-  double ft = 0;
+  double ft = 0, lowB = 0;
   std::vector<double> cnt(S.m);
   for (int i = 0; i < S.m; ++i) cnt[i] = S.anz_ptr[i + 1] - S.anz_ptr[i];
   std::vector<double> suffix(S.m + 1, 0.0);
   for (int i = S.m - 1; i >= 0; --i) suffix[i] = suffix[i + 1] + cnt[i];
-  for (int j = 0; j < S.m; ++j) ft += 2 * cnt[j] * suffix[j];
+  double f4 = 0, b4 = 0, f5 = 0;
+  for (int q = 0; q < nblk; ++q) {
+    const int o = c->blocks ? S.comp_cptr[q] : 0, e = c->blocks ? S.comp_cptr[q + 1] : S.m;
+    for (int j = o; j < e; ++j) ft += 2 * cnt[j] * (suffix[j] - suffix[e]);
+    // K4: dense Cholesky with the bordered right-hand side; K5: back substitution
+    const double mc = e - o;
+    lowB += mc * (mc + 1) / 2;
+    f4 += mc * mc * mc / 3 + mc * mc;
+    b4 += 8 * 2 * (mc * (mc + 1) / 2);
+    f5 += mc * mc;
+  }
   w->flops[3] = ft;
-  w->bytes[3] = bp + 8.0 * S.m * (S.m + 1) / 2;  // panels read once, lower(B) written once
-  // K4: dense Cholesky with the bordered right-hand side, back substitution
-  const double m = S.m;
-  w->flops[4] = m * m * m / 3 + m * m;
-  w->bytes[4] = 8 * 2 * (m * (m + 1) / 2);
-  w->flops[5] = m * m;
-  w->bytes[5] = 8 * m * (m + 1) / 2;
+  w->bytes[3] = bp + 8.0 * lowB;  // panels read once, lower(B) written once
+  w->flops[4] = f4;
+  w->bytes[4] = b4;
+  w->flops[5] = f5;
+  w->bytes[5] = 8 * lowB;
   // K6: per column: N forward along the path, N backward, dY product, L̂ forward and backward
   double fpm = 0;
   const double arow = (double)S.arow_col.size();
@@ -3192,8 +3255,7 @@ mcsdp_status mcsdp_backward(mcsdp_ctx *c, const double *gX, const double *gz, do
     s = phase_scm<double>(c);
     if (s) return s;
     launch_rhs_border(c->D, c->B, c->ldb, c->hvec, mu, c->stream);
-    dense_chol_bordered(c->B, c->ldb, m, c->status + 2, c->Binv, c->stream, &c->cs);
-    dense_backsolve(c->B, c->ldb, m, c->Binv, c->xs, c->stream);
+    scm_chol_solve(c);
     launch_dz_to_user(c->D, c->xs, c->dz, c->stream);
     CUDA_TRY(c, cudaMemcpyAsync(c->zsave, c->z, (size_t)m * 8, cudaMemcpyDeviceToDevice, c->stream));
     double t = 1.0;
@@ -3233,8 +3295,7 @@ mcsdp_status mcsdp_backward(mcsdp_ctx *c, const double *gX, const double *gz, do
   // v = B^{-1} (A(R) + g_z)
   launch_con_apply(c->D, c->bwd_g, gz, c->vrhs, c->stream);
   launch_border_from_user(c->D, c->B, c->ldb, c->vrhs, c->stream);
-  dense_chol_bordered(c->B, c->ldb, m, c->status + 2, c->Binv, c->stream, &c->cs);
-  dense_backsolve(c->B, c->ldb, m, c->Binv, c->xs, c->stream);
+  scm_chol_solve(c);
   launch_dz_to_user(c->D, c->xs, c->dz, c->stream);  // v, caller order
   // g_{A_0} = sym(X̂ (A^*(v) - G) Y^{-1}) on E
   CUDA_TRY(c, cudaMemsetAsync(c->dY, 0, nnzL * 8, c->stream));

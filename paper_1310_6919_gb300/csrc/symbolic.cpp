@@ -656,12 +656,40 @@ std::string analyze(const ProblemData &P, const SymbolicOptions &o, Symbolic &S)
         return "constraint A_" + std::to_string(k + 1) + " touches " + std::to_string(s.size()) +
                " rows/columns; the SCM panel limit is " + std::to_string(o.panel_max);
     }
+    // connected components of the SCM's nonzero structure: union-find over every input entry
+    // (elimination numbering) and over each constraint's support (an A_k with only diagonal
+    // entries, on rows of different pattern components, couples them through B_kq)
+    std::vector<int> uf(n);
+    std::iota(uf.begin(), uf.end(), 0);
+    auto find = [&](int x) {
+      while (uf[x] != x) {
+        uf[x] = uf[uf[x]];
+        x = uf[x];
+      }
+      return x;
+    };
+    for (size_t t = 0; t < P.row.size(); ++t) {
+      const int a = find(S.iperm[P.row[t]]), b = find(S.iperm[P.col[t]]);
+      if (a != b) uf[std::max(a, b)] = std::min(a, b);
+    }
+    for (int k = 0; k < m; ++k)
+      for (size_t q = 1; q < supp[k].size(); ++q) {
+        const int a = find(supp[k][0]), b = find(supp[k][q]);
+        if (a != b) uf[std::max(a, b)] = std::min(a, b);
+      }
+    std::vector<int> ccomp(m);
+    for (int k = 0; k < m; ++k) ccomp[k] = find(supp[k][0]);
     std::vector<int> ord(m);
     std::iota(ord.begin(), ord.end(), 0);
     std::sort(ord.begin(), ord.end(), [&](int a, int b) {
+      if (ccomp[a] != ccomp[b]) return ccomp[a] < ccomp[b];
       if (supp[a][0] != supp[b][0]) return supp[a][0] < supp[b][0];
       return a < b;
     });
+    S.comp_cptr.assign(1, 0);
+    for (int i = 1; i <= m; ++i)
+      if (i == m || ccomp[ord[i]] != ccomp[ord[i - 1]]) S.comp_cptr.push_back(i);
+    S.ncomp = (int)S.comp_cptr.size() - 1;
     S.con_order = ord;
     S.con_internal.assign(m, 0);
     for (int i = 0; i < m; ++i) S.con_internal[ord[i]] = i;
@@ -680,7 +708,8 @@ std::string analyze(const ProblemData &P, const SymbolicOptions &o, Symbolic &S)
       const auto &s = supp[ord[i]];
       tmp.clear();
       std::set_union(U.begin(), U.end(), s.begin(), s.end(), std::back_inserter(tmp));
-      if (i > gstart && ((int)tmp.size() > o.panel_max || i - gstart >= o.group_max)) {
+      const bool new_comp = i > gstart && ccomp[ord[i]] != ccomp[ord[i - 1]];
+      if (i > gstart && ((int)tmp.size() > o.panel_max || i - gstart >= o.group_max || new_comp)) {
         close_group(i);
         U = s;
       } else {
@@ -689,6 +718,11 @@ std::string analyze(const ProblemData &P, const SymbolicOptions &o, Symbolic &S)
     }
     close_group(m);
     S.ngroup = (int)S.grp_cptr.size() - 1;
+    S.grp_comp.assign(S.ngroup, 0);
+    for (int g = 0, cc = 0; g < S.ngroup; ++g) {
+      while (S.comp_cptr[cc + 1] <= S.grp_cptr[g]) ++cc;
+      S.grp_comp[g] = cc;
+    }
     S.grp_rowoff.assign(S.ngroup + 1, 0);
     for (int g = 0; g < S.ngroup; ++g)
       S.grp_rowoff[g + 1] = S.grp_rowoff[g] + (S.grp_pptr[g + 1] - S.grp_pptr[g]);

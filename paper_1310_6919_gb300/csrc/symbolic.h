@@ -61,6 +61,13 @@ struct Symbolic {
   std::vector<int> rs_ptr;                  // n+1
   std::vector<int> rs_col;
   std::vector<int64_t> rs_off;
+  // connected components of the aggregate sparsity pattern that carry constraints: X̂ and Y^{-1}
+  // are block-diagonal over them, so B is too (B_pq = 0 for A_p, A_q in different components).
+  // Internal constraint order keeps each component contiguous: component c is internal
+  // [comp_cptr[c], comp_cptr[c + 1]); no SCM group spans two components
+  int ncomp = 1;
+  std::vector<int> comp_cptr;               // ncomp+1
+  std::vector<int> grp_comp;                // ngroup: component of each group
   // SCM groups: constraints in internal order con_order, group g = internal [grp_cptr[g], ..)
   int ngroup = 0;
   std::vector<int> con_order;               // internal -> caller
