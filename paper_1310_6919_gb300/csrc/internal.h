@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <vector>
 
 namespace mcsdp {
 
@@ -388,6 +389,33 @@ struct CholStreams {
   int *tc_err = nullptr;
 };
 void chol_graphs_destroy(CholStreams *cs);
+// The diagonal blocks of a block-diagonal SCM for one task-queue launch and one batched back
+// substitution (kern_dense.cu): block b at rows and columns off[b], mb[b] of them, bordered by
+// the row after it; tile counters from word soff[b] of the synchronisation buffer's tile area;
+// diagonal-tile inverses at loff[b]; the queue's segments (the blocks' ticket phases
+// interleaved, see DagBlocks in kern_dense.cu).  Device arrays.
+struct DagBlockTables {
+  int nblk = 0, max_m = 0, nseg = 0;
+  const int *off = nullptr, *mb = nullptr;
+  const int64_t *soff = nullptr, *loff = nullptr;
+  const int64_t *seg_start = nullptr, *seg_l0 = nullptr;
+  const int *seg_blk = nullptr, *seg_k = nullptr;
+  int64_t total = 0;        // tickets over all blocks
+  size_t tile_words = 0;    // counters over all blocks (2 R_b C_b each)
+  size_t words = 0;         // the synchronisation buffer (chol_dag_blocks_words)
+  int64_t useful_ctas = 0;  // sum of C_b^2 / 4: tasks the blocks can have ready at once
+};
+// tickets of each phase of one factorisation: the prefix, then iterations 0 .. C-2
+void chol_dag_phases(int m, int rows, std::vector<int64_t> &sizes);
+size_t chol_dag_tile_words(int m, int rows);
+size_t chol_dag_blocks_words(size_t tile_words);
+// every block's bordered factorisation in one launch (FP64)
+int dense_chol_dag_blocks(double *B, int64_t ldb, const DagBlockTables &bt, int *status,
+                          double *Linv_all, cudaStream_t st, int *sync, long long budget);
+// every block's back substitution in one launch (one cluster per block); -1 if a block is too
+// large for the cluster kernel's shared-memory vector
+int dense_backsolve_blocks(const double *B, int64_t ldb, const DagBlockTables &bt,
+                           const double *Linv_all, double *x, cudaStream_t st);
 // words of the task-queue factorisation's synchronisation buffer (m columns, rows rows)
 size_t chol_dag_words(int m, int rows);
 // cs == nullptr: everything on st, no lookahead, no graph

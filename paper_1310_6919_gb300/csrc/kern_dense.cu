@@ -666,24 +666,73 @@ __device__ void dag_upd(T *B, int64_t ldb, int i0, int h, int j0, int w, int k0,
   }
 }
 
+// Several independent factorisations in one queue (the diagonal blocks of a block-diagonal B):
+// block b is the bordered matrix at rows and columns off[b] (mb[b] columns, its right-hand side
+// in row off[b] + mb[b]); its tile counters (upd, then fin) start at word soff[b] after the
+// queue's eight header words, its diagonal-tile inverses at Linv_all + loff[b].  Each block's
+// tickets fall into phases (the prefix, then iteration k = 0 .. C-2 of its single-matrix order);
+// the queue interleaves the blocks phase by phase: segment s (ordered by seg_start) holds the
+// tickets of block seg_blk[s] from its local ticket seg_l0[s] on, its iteration seg_k[s] (-1 for
+// the prefix).  A block's own tickets keep their order and blocks share no dependency, so every
+// dependency still precedes its dependants, and the blocks' chains run side by side instead of
+// one block at a time.  nblk = 0: one matrix.
+struct DagBlocks {
+  int nblk = 0, nseg = 0;
+  const int *off = nullptr, *mb = nullptr;
+  const int64_t *soff = nullptr, *loff = nullptr;
+  const int64_t *seg_start = nullptr, *seg_l0 = nullptr;  // nseg + 1 / nseg
+  const int *seg_blk = nullptr, *seg_k = nullptr;          // nseg
+};
+
 template <class T>
 __global__ void __launch_bounds__(DAG_THREADS, 2)
-    k_chol_dag(T *B, int64_t ldb, int m, int rows, int *status, T *Linv_all, DagSync q,
-               int64_t total) {
+    k_chol_dag(T *B0, int64_t ldb, int m, int rows, int *status, T *Linv0, DagSync q,
+               int64_t total, DagBlocks bl) {
   extern __shared__ __align__(16) unsigned char smd_raw[];
   T *sm = reinterpret_cast<T *>(smd_raw);
   __shared__ int s_task[3];  // [0] first ticket, [1] next ticket, [2] dependencies met
   const int tid = threadIdx.x;
-  const int R = (rows + NB - 1) / NB, C = q.C;
-  const DagPrefix pf = dag_prefix(R, C);
+  T *B = B0, *Linv_all = Linv0;
+  int R = (rows + NB - 1) / NB, C = q.C;
+  DagPrefix pf = dag_prefix(R, C);
   int kcur = 0;
   int64_t kstart = pf.pre;  // first ticket of iteration kcur
+  int blk = -1;
+  int *const upd0 = q.upd;
   if (tid == 0) s_task[0] = atomicAdd(q.ticket, 1);
   __syncthreads();
   int t = s_task[0];
   while (t < total) {
     if (tid == 0) s_task[1] = atomicAdd(q.ticket, 1);  // the next ticket, fetched early
-    const DagTask task = dag_decode(t, R, C, pf, kcur, kstart);
+    int64_t tl = t;
+    if (bl.nblk > 0) {  // block mode: the segment holding t, its block and local ticket
+      int lo = 0, hi = bl.nseg - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bl.seg_start[mid] <= t) lo = mid;
+        else hi = mid - 1;
+      }
+      if (bl.seg_blk[lo] != blk) {
+        blk = bl.seg_blk[lo];
+        const int o = bl.off[blk];
+        m = bl.mb[blk];
+        rows = m + 1;
+        B = B0 + o + (int64_t)o * ldb;
+        Linv_all = Linv0 + bl.loff[blk];
+        R = (rows + NB - 1) / NB;
+        C = (m + NB - 1) / NB;
+        q.C = C;
+        q.upd = upd0 + bl.soff[blk];
+        q.fin = q.upd + (int64_t)R * C;
+        pf = dag_prefix(R, C);
+      }
+      tl = bl.seg_l0[lo] + (t - bl.seg_start[lo]);
+      if (bl.seg_k[lo] >= 0) {  // dag_decode's search starts at the segment's iteration
+        kcur = bl.seg_k[lo];
+        kstart = bl.seg_l0[lo];
+      }
+    }
+    const DagTask task = dag_decode(tl, R, C, pf, kcur, kstart);
     const int type = task.type, ti = task.i, tj = task.j, tk = task.k;
     // dependencies (thread 0 waits, the CTA follows)
     bool ok = true;
@@ -791,8 +840,52 @@ static int dense_chol_dag(T *B, int64_t ldb, int m, int rows, int *status, T *Li
   // CTAs it would not use would hold registers that concurrent solves (mcsdp_solve_batch) need
   const int64_t useful = std::max<int64_t>(8, (int64_t)C * C / 4);
   const int grid = (int)std::min<int64_t>(std::min<int64_t>(2 * (int64_t)nsm, useful), total);
-  k_chol_dag<T><<<grid, DAG_THREADS, smem, st>>>(B, ldb, m, rows, status, Linv_all, q, total);
+  k_chol_dag<T><<<grid, DAG_THREADS, smem, st>>>(B, ldb, m, rows, status, Linv_all, q, total,
+                                                  DagBlocks{});
   return 1;  // kernel launches (the memset is not one of ours)
+}
+
+void chol_dag_phases(int m, int rows, std::vector<int64_t> &sizes) {
+  const int R = (rows + NB - 1) / NB, C = (m + NB - 1) / NB;
+  sizes.assign(1, dag_prefix(R, C).pre);
+  for (int64_t k = 0; k + 1 < C; ++k) sizes.push_back(dag_iter_size(k, R, C));
+}
+
+size_t chol_dag_tile_words(int m, int rows) {
+  return 2 * (size_t)((rows + NB - 1) / NB) * (size_t)((m + NB - 1) / NB);
+}
+
+size_t chol_dag_blocks_words(size_t tile_words) { return 8 + tile_words + DAG_MAX_SM; }
+
+int dense_chol_dag_blocks(double *B, int64_t ldb, const DagBlockTables &bt, int *status,
+                          double *Linv_all, cudaStream_t st, int *sync, long long budget) {
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+  }
+  const size_t smem = std::max(sizeof(PotrfSmem<double>), (size_t)2 * NB * (NB + 1) * sizeof(double));
+  cudaMemsetAsync(sync, 0, bt.words * sizeof(int), st);
+  DagSync q{sync, sync + 1, sync + 8, nullptr, sync + 8 + bt.tile_words, 0,
+            budget > 0 ? budget : DAG_DEFAULT_BUDGET};
+  DagBlocks bl;
+  bl.nblk = bt.nblk;
+  bl.nseg = bt.nseg;
+  bl.off = bt.off;
+  bl.mb = bt.mb;
+  bl.soff = bt.soff;
+  bl.loff = bt.loff;
+  bl.seg_start = bt.seg_start;
+  bl.seg_l0 = bt.seg_l0;
+  bl.seg_blk = bt.seg_blk;
+  bl.seg_k = bt.seg_k;
+  const int64_t useful = std::max<int64_t>(8, bt.useful_ctas);
+  const int grid = (int)std::min<int64_t>(std::min<int64_t>(2 * (int64_t)nsm, useful), bt.total);
+  k_chol_dag<double><<<grid, DAG_THREADS, smem, st>>>(B, ldb, 0, 0, status, Linv_all, q, bt.total,
+                                                      bl);
+  return 1;
 }
 
 template <class T>
@@ -1121,11 +1214,22 @@ __global__ void k_copy_border(const double *B, int64_t ldb, int m, double *x) {
 // hardware cluster barrier.
 constexpr int BCL = 8;
 constexpr int BTH = 256;
+// Block mode (boff != nullptr): cluster b solves the diagonal block b of a block-diagonal B (rows
+// and columns from boff[b], bm[b] of them, right-hand side in the row after the block, inverses
+// at Linv + bloff[b]) into x + boff[b].
 __global__ void __cluster_dims__(BCL, 1, 1) __launch_bounds__(BTH)
     k_backsolve_cluster(const double *__restrict__ B, int64_t ldb, int m,
-                        const double *__restrict__ Linv, double *x) {
+                        const double *__restrict__ Linv, double *x, const int *__restrict__ boff,
+                        const int *__restrict__ bm, const int64_t *__restrict__ bloff) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
+  if (boff) {
+    const int b = blockIdx.x / BCL, o = boff[b];
+    m = bm[b];
+    B += o + (int64_t)o * ldb;
+    Linv += bloff[b];
+    x += o;
+  }
   extern __shared__ double yv[];  // m doubles; the CTA's own rows are used
   __shared__ double xb[2][NB];
   __shared__ double tb[NB];
@@ -1196,7 +1300,7 @@ int dense_backsolve(const double *B, int64_t ldb, int m, const double *Linv_all,
   if (m <= BS_CLUSTER_MAX_M) {
     const size_t smem = (size_t)m * sizeof(double);
     if (smem > 48 * 1024) smem_optin((const void *)k_backsolve_cluster);
-    k_backsolve_cluster<<<BCL, BTH, smem, st>>>(B, ldb, m, Linv_all, x);
+    k_backsolve_cluster<<<BCL, BTH, smem, st>>>(B, ldb, m, Linv_all, x, nullptr, nullptr, nullptr);
     return 1;
   }
   k_copy_border<<<(m + 255) / 256, 256, 0, st>>>(B, ldb, m, x);
@@ -1213,6 +1317,16 @@ int dense_backsolve(const double *B, int64_t ldb, int m, const double *Linv_all,
     }
   }
   return launches;
+}
+
+int dense_backsolve_blocks(const double *B, int64_t ldb, const DagBlockTables &bt,
+                           const double *Linv_all, double *x, cudaStream_t st) {
+  if (bt.max_m > BS_CLUSTER_MAX_M) return -1;
+  const size_t smem = (size_t)bt.max_m * sizeof(double);
+  if (smem > 48 * 1024) smem_optin((const void *)k_backsolve_cluster);
+  k_backsolve_cluster<<<BCL * bt.nblk, BTH, smem, st>>>(B, ldb, 0, Linv_all, x, bt.off, bt.mb,
+                                                        bt.loff);
+  return 1;
 }
 
 // row m of B <- g_i = b_{user(i)} - beta mu h_i   (internal order; with a block-diagonal B, row

@@ -103,6 +103,10 @@ struct mcsdp_ctx {
   bool blocks = false;
   std::vector<int> bord;
   std::vector<int64_t> binv_off;
+  // and the blocks' tables for the one-launch factorisation and back substitution
+  std::vector<int> bt_off, bt_m, bt_seg_blk, bt_seg_k;
+  std::vector<int64_t> bt_soff, bt_seg_start, bt_seg_l0;
+  DagBlockTables bt{};
   std::vector<double> z0_default;
   bool z0_ok = false;
   // the input entries as given (caller order), for per-entry gradients
@@ -759,6 +763,59 @@ void plan_workspace(mcsdp_ctx *c) {
   }
   plan_table(c, cur, "bord", c->bord);
   plan_buf(c, cur, "Binv", (size_t)c->binv_off.back() * 8);
+  c->bt = DagBlockTables{};
+  c->bt_off.clear();
+  c->bt_m.clear();
+  c->bt_soff.clear();
+  c->bt_seg_blk.clear();
+  c->bt_seg_k.clear();
+  c->bt_seg_start.clear();
+  c->bt_seg_l0.clear();
+  if (c->blocks) {
+    // the blocks' ticket phases (prefix, iteration 0, 1, ...), interleaved phase by phase
+    int64_t useful = 0;
+    size_t tw = 0;
+    std::vector<std::vector<int64_t>> ph(S.ncomp);
+    size_t nph = 0;
+    for (int q = 0; q < S.ncomp; ++q) {
+      const int o = S.comp_cptr[q], mc = S.comp_cptr[q + 1] - o, ct = (mc + 31) / 32;
+      c->bt_off.push_back(o);
+      c->bt_m.push_back(mc);
+      c->bt_soff.push_back((int64_t)tw);
+      tw += chol_dag_tile_words(mc, mc + 1);
+      useful += (int64_t)ct * ct / 4;
+      c->bt.max_m = std::max(c->bt.max_m, mc);
+      chol_dag_phases(mc, mc + 1, ph[q]);
+      nph = std::max(nph, ph[q].size());
+    }
+    std::vector<int64_t> lstart(S.ncomp, 0);
+    int64_t tk = 0;
+    for (size_t p = 0; p < nph; ++p)
+      for (int q = 0; q < S.ncomp; ++q) {
+        if (p >= ph[q].size() || ph[q][p] == 0) continue;
+        c->bt_seg_start.push_back(tk);
+        c->bt_seg_l0.push_back(lstart[q]);
+        c->bt_seg_blk.push_back(q);
+        c->bt_seg_k.push_back((int)p - 1);
+        tk += ph[q][p];
+        lstart[q] += ph[q][p];
+      }
+    c->bt_seg_start.push_back(tk);
+    c->bt.nblk = S.ncomp;
+    c->bt.nseg = (int)c->bt_seg_blk.size();
+    c->bt.total = tk;
+    c->bt.tile_words = tw;
+    c->bt.words = chol_dag_blocks_words(tw);
+    c->bt.useful_ctas = useful;
+  }
+  plan_table(c, cur, "bt_off", c->bt_off);
+  plan_table(c, cur, "bt_m", c->bt_m);
+  plan_table(c, cur, "bt_soff", c->bt_soff);
+  plan_table(c, cur, "bt_loff", c->binv_off);
+  plan_table(c, cur, "bt_seg_start", c->bt_seg_start);
+  plan_table(c, cur, "bt_seg_l0", c->bt_seg_l0);
+  plan_table(c, cur, "bt_seg_blk", c->bt_seg_blk);
+  plan_table(c, cur, "bt_seg_k", c->bt_seg_k);
   plan_buf(c, cur, "xs", (size_t)m * 8);
   plan_buf(c, cur, "dz", (size_t)m * 8);
   plan_buf(c, cur, "W1", (size_t)n * c->ldw * 8);
@@ -811,7 +868,7 @@ void plan_workspace(mcsdp_ctx *c) {
   plan_buf(c, cur, "gsc", 16 * 8);
   plan_buf(c, cur, "alpha_r", (size_t)S.ns * 8);
   plan_buf(c, cur, "scal", (16 + 6 * 64) * 8);  // scalars, then the measures' partials
-  plan_buf(c, cur, "chol_sync", chol_dag_words(m, m + 1) * 4);
+  plan_buf(c, cur, "chol_sync", std::max(chol_dag_words(m, m + 1), c->bt.words) * 4);
   plan_buf(c, cur, "status", (8 + NCAND) * 4);  // [0..3] phases, [4] FP32 factor, [8..8+NCAND) dual candidates
   {
     const bool mx = c->opt.precision == 1;
@@ -976,7 +1033,17 @@ void bind_pointers(mcsdp_ctx *c) {
   c->scal = wsp<double>(c, "scal");
   c->status = wsp<int>(c, "status");
   c->cs.dag_sync = wsp<int>(c, "chol_sync");
-  c->cs.dag_words = chol_dag_words(c->S.m, c->S.m + 1);
+  c->cs.dag_words = std::max(chol_dag_words(c->S.m, c->S.m + 1), c->bt.words);
+  if (c->blocks) {
+    c->bt.off = wsp<int>(c, "bt_off");
+    c->bt.mb = wsp<int>(c, "bt_m");
+    c->bt.soff = wsp<int64_t>(c, "bt_soff");
+    c->bt.loff = wsp<int64_t>(c, "bt_loff");
+    c->bt.seg_start = wsp<int64_t>(c, "bt_seg_start");
+    c->bt.seg_l0 = wsp<int64_t>(c, "bt_seg_l0");
+    c->bt.seg_blk = wsp<int>(c, "bt_seg_blk");
+    c->bt.seg_k = wsp<int>(c, "bt_seg_k");
+  }
   c->cs.dag_budget = c->opt.timeout_cycles;
   c->B32 = wsp<float>(c, "B32");
   c->Linv32 = wsp<float>(c, "Linv32");
@@ -1792,7 +1859,9 @@ mcsdp_status mixed_gmres(mcsdp_ctx *c, double tol_ok, double tol_stall, bool *so
 // (c->blocks): one of each per component q, on the diagonal block at (o, o), o = comp_cptr[q],
 // whose right-hand side k_rhs_border put in row comp_cptr[q + 1] of the block's columns (the row
 // after the block, outside every diagonal block), so that the block is itself a bordered matrix of
-// leading dimension ldb.  The blocks are independent; they run in component order.
+// leading dimension ldb.  The blocks are independent: all their factorisations share one
+// task-queue launch (their tickets concatenated), all their substitutions one launch of a
+// cluster per block.
 void scm_chol_solve(mcsdp_ctx *c) {
   const Symbolic &S = c->S;
   const int nblk = c->blocks ? S.ncomp : 1;
@@ -1801,19 +1870,32 @@ void scm_chol_solve(mcsdp_ctx *c) {
     *mc = (c->blocks ? S.comp_cptr[q + 1] : S.m) - *o;
   };
   int o, mc, nl = 0;
-  KScope k1(c, KC_CHOL);
-  for (int q = 0; q < nblk; ++q) {
-    range(q, &o, &mc);
-    nl += dense_chol_bordered(c->B + o + (int64_t)o * c->ldb, c->ldb, mc, c->status + 2,
-                              c->Binv + c->binv_off[q], c->stream, &c->cs);
+  {
+    KScope k1(c, KC_CHOL);
+    if (c->blocks && c->cs.dag_sync) {
+      // every block in one task-queue launch: the blocks' chains overlap instead of running one
+      // after another
+      nl = dense_chol_dag_blocks(c->B, c->ldb, c->bt, c->status + 2, c->Binv, c->stream,
+                                 c->cs.dag_sync, c->cs.dag_budget);
+    } else {
+      for (int q = 0; q < nblk; ++q) {
+        range(q, &o, &mc);
+        nl += dense_chol_bordered(c->B + o + (int64_t)o * c->ldb, c->ldb, mc, c->status + 2,
+                                  c->Binv + c->binv_off[q], c->stream, &c->cs);
+      }
+    }
+    k1.done(nl);
   }
-  k1.done(nl);
-  nl = 0;
   KScope k2(c, KC_BSOLVE);
-  for (int q = 0; q < nblk; ++q) {
-    range(q, &o, &mc);
-    nl += dense_backsolve(c->B + o + (int64_t)o * c->ldb, c->ldb, mc, c->Binv + c->binv_off[q],
-                          c->xs + o, c->stream);
+  // one cluster per block in one launch, unless a block exceeds the cluster kernel's vector
+  nl = c->blocks ? dense_backsolve_blocks(c->B, c->ldb, c->bt, c->Binv, c->xs, c->stream) : -1;
+  if (nl < 0) {
+    nl = 0;
+    for (int q = 0; q < nblk; ++q) {
+      range(q, &o, &mc);
+      nl += dense_backsolve(c->B + o + (int64_t)o * c->ldb, c->ldb, mc, c->Binv + c->binv_off[q],
+                            c->xs + o, c->stream);
+    }
   }
   k2.done(nl);
 }
