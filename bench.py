@@ -419,7 +419,7 @@ def other_legs(args, dev, stream):
     the batched form on a mix of small SDPs."""
     import torch
     from instances import workload, batch_mix
-    from paper_1310_6919_gb300 import Problem, solve_batch, MCSDPError
+    from paper_1310_6919_gb300 import Problem, solve_batch, MCSDPError, tune, tune_cache_clear
     inst = workload(CONTEXT_WORKLOAD)
     z0 = torch.tensor(inst.z0, dtype=torch.float64, device=f"cuda:{dev}")
     out = {"workload": CONTEXT_WORKLOAD}
@@ -448,9 +448,9 @@ def other_legs(args, dev, stream):
     mix = batch_mix(512, 128)
     subset = set(range(48)) | set(range(512, 528))
 
-    def make(inst, st, prec, graph=0):
+    def make(inst, st, prec, graph=0, **opts):
         Q = Problem(inst.n, inst.m, inst.b, inst.mat, inst.row, inst.col, inst.val, form=1,
-                    device=dev, stream=st, precision=prec, graph=graph)
+                    device=dev, stream=st, precision=prec, graph=graph, **opts)
         if inst.meta.get("kind") != "maxcut":
             Q.set_iterate(None, torch.tensor(inst.z0, dtype=torch.float64, device=f"cuda:{dev}"))
         return Q
@@ -462,12 +462,29 @@ def other_legs(args, dev, stream):
                         "16 block-arrow)")}
     make(mix[0], None, 0).solve()
     # fp64: iterations replayed as captured CUDA graphs (options.graph); fp64_host_loop: the
-    # host-driven loop (about a hundred launches and eight synchronisations per iteration)
-    for name, prec, graph in (("fp64", 0, 1), ("fp64_host_loop", 0, 0), ("mixed", 1, 0)):
+    # host-driven loop (about a hundred launches and eight synchronisations per iteration);
+    # fp64_tuned: the graph form with each problem's SCM grouping from the tile-shape tuner
+    # (mcsdp_tune, cached per (n, m, largest clique) bucket; tuning time reported apart)
+    tuned, keys, t_tune = {}, set(), 0.0
+    tune_cache_clear()
+    t0 = time.perf_counter()
+    for i, q in enumerate(mix):
+        try:
+            o, info = tune(q, z0=None if q.meta.get("kind") == "maxcut" else q.z0, iters=3,
+                           device=dev, graph=1)
+            tuned[i] = {"group_max": o["group_max"], "panel_max": o["panel_max"]}
+            keys.add(tuple(info["key"]))
+        except MCSDPError:
+            pass
+    torch.cuda.synchronize(dev)
+    t_tune = time.perf_counter() - t0
+    for name, prec, graph in (("fp64", 0, 1), ("fp64_host_loop", 0, 0), ("mixed", 1, 0),
+                              ("fp64_tuned", 0, 1)):
         probs, idx, skipped = [], [], 0
         for i, q in enumerate(mix):
             try:
-                probs.append(make(q, torch.cuda.Stream(dev), prec, graph))
+                extra = tuned.get(i, {}) if name == "fp64_tuned" else {}
+                probs.append(make(q, torch.cuda.Stream(dev), prec, graph, **extra))
                 idx.append(i)
             except MCSDPError:
                 skipped += 1
@@ -491,6 +508,15 @@ def other_legs(args, dev, stream):
             leg["same_as_sequential_subset"] = all(
                 bat_sub[i]["pobj"] == r["pobj"] for i, r in zip(sorted(subset), seq_res) if i in bat_sub)
             del seq
+        if name == "fp64_tuned":
+            leg["tuning_seconds"] = t_tune
+            leg["tuned_keys"] = len(keys)
+            choice = {}
+            for v in tuned.values():
+                k = f"{v['group_max']}x{v['panel_max']}"
+                choice[k] = choice.get(k, 0) + 1
+            leg["choices"] = choice
+            leg["speedup_vs_fp64"] = leg["problems_per_s"] / batched["fp64"]["problems_per_s"]
         batched[name] = leg
         del probs
         torch.cuda.empty_cache()

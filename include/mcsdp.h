@@ -362,6 +362,34 @@ mcsdp_status mcsdp_gemm_tc(int32_t M, int32_t N, int32_t K, const float *A, int6
 mcsdp_status mcsdp_backward(mcsdp_ctx *ctx, const double *gX_layout_dev, const double *gz_dev,
                             double *gC_dev, double *gb_dev, double *gA_dev);
 
+/* Tile-shape tuner for the batched form (many small SDPs; the paper's FCFS task queue of
+ * Algorithm 2 lifted to problems leaves the tile shapes to be chosen per problem size).  The SCM
+ * grouping sets the shapes of the level solves' right-hand-side tiles and of the tile
+ * contraction: group_max constraints per group, at most panel_max columns per group.
+ * mcsdp_tune times `iters` iterations (after one untimed run of the same length) of the problem
+ * under each candidate (group_max, panel_max) in {(64, 80), (32, 80), (16, 80), (64, 96),
+ * (32, 48)}, skipping candidates the problem's constraints do not fit, and writes the fastest
+ * into opt->group_max and opt->panel_max.  The choice is cached process-wide under the key
+ * (n, m, largest clique of the default analysis), each rounded up to a power of two: a later
+ * problem with the same key takes it without timing (info->cached = 1).  z0_dev: a dual-feasible
+ * start (device, m values), or NULL for the library's default start.  ws: device buffer of at
+ * least mcsdp_tune_workspace_size bytes, 256-byte aligned; its contents are overwritten.  The
+ * other options (precision, graph, ...) are used as given.  MCSDP_ERR_ARG if no candidate
+ * runs. */
+typedef struct {
+  int32_t group_max, panel_max;  /* the choice */
+  int32_t cached;                /* 1 = taken from the cache without timing */
+  int32_t ncand;                 /* candidates timed (0 when cached) */
+  double ms_per_iter[8];         /* per candidate in the order above; < 0 = skipped */
+  int64_t key[3];                /* n, m, largest clique, rounded up to powers of two */
+} mcsdp_tune_info;
+mcsdp_status mcsdp_tune_workspace_size(const mcsdp_problem *prob, const mcsdp_options *opt,
+                                       size_t *bytes);
+mcsdp_status mcsdp_tune(const mcsdp_problem *prob, mcsdp_options *opt, const double *z0_dev,
+                        void *cuda_stream, void *ws, size_t ws_bytes, int32_t iters,
+                        mcsdp_tune_info *info);
+void mcsdp_tune_cache_clear(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,6 +55,11 @@ class Result_t(C.Structure):
                 ("assembly_iter", C.c_int32)]
 
 
+class TuneInfo_t(C.Structure):
+    _fields_ = [("group_max", C.c_int32), ("panel_max", C.c_int32), ("cached", C.c_int32),
+                ("ncand", C.c_int32), ("ms_per_iter", C.c_double * 8), ("key", C.c_int64 * 3)]
+
+
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_NOT_PD", 3: "ERR_MAXITER", 4: "ERR_STALL",
           5: "ERR_NUMERIC", 6: "ERR_CUDA", 7: "ERR_OOM", 8: "ERR_TIMEOUT", 9: "ERR_STATE"}
 
@@ -64,7 +69,8 @@ EXPORTED = ["mcsdp_default_options", "mcsdp_create", "mcsdp_destroy", "mcsdp_las
             "mcsdp_scm_assemble", "mcsdp_newton_step", "mcsdp_factors", "mcsdp_backward",
             "mcsdp_stats_get", "mcsdp_stats_reset", "mcsdp_work_model", "mcsdp_sce_solve_noalloc",
             "mcsdp_solve_batch", "mcsdp_pivot_reciprocal", "mcsdp_chol_task_order",
-            "mcsdp_gemm_tc_work_size", "mcsdp_gemm_tc"]
+            "mcsdp_gemm_tc_work_size", "mcsdp_gemm_tc", "mcsdp_tune_workspace_size",
+            "mcsdp_tune", "mcsdp_tune_cache_clear"]
 
 _lib = None
 
@@ -110,10 +116,17 @@ def load():
     L.mcsdp_gemm_tc_work_size.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]
     L.mcsdp_gemm_tc.argtypes = [C.c_int32, C.c_int32, C.c_int32, V, C.c_int64, V, C.c_int64, V,
                                 C.c_int64, C.c_float, C.c_float, V, C.c_size_t, V]
+    L.mcsdp_tune_workspace_size.argtypes = [C.POINTER(Problem_t), C.POINTER(Options_t),
+                                            C.POINTER(C.c_size_t)]
+    L.mcsdp_tune.argtypes = [C.POINTER(Problem_t), C.POINTER(Options_t), V, V, V, C.c_size_t,
+                             C.c_int32, C.POINTER(TuneInfo_t)]
+    L.mcsdp_tune_cache_clear.argtypes = []
+    L.mcsdp_tune_cache_clear.restype = None
     for f in EXPORTED:
         if getattr(L, f).restype is C.c_int or f not in ("mcsdp_default_options", "mcsdp_destroy",
                                                            "mcsdp_last_error"):
-            if f not in ("mcsdp_default_options", "mcsdp_destroy", "mcsdp_last_error"):
+            if f not in ("mcsdp_default_options", "mcsdp_destroy", "mcsdp_last_error",
+                         "mcsdp_tune_cache_clear"):
                 getattr(L, f).restype = C.c_int
     _lib = L
     return L

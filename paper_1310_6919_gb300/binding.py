@@ -233,6 +233,54 @@ class Problem:
         return Lh, N
 
 
+def _problem_t(n, m, b, mat, row, col, val, form):
+    """The host arrays (kept alive by the caller through the returned tuple) and Problem_t."""
+    arrs = (np.ascontiguousarray(b, dtype=np.float64), np.ascontiguousarray(mat, dtype=np.int32),
+            np.ascontiguousarray(row, dtype=np.int32), np.ascontiguousarray(col, dtype=np.int32),
+            np.ascontiguousarray(val, dtype=np.float64))
+    prob = _lib.Problem_t(int(n), int(m), int(form), arrs[0].ctypes.data_as(C.POINTER(C.c_double)),
+                          len(arrs[4]), arrs[1].ctypes.data_as(C.POINTER(C.c_int32)),
+                          arrs[2].ctypes.data_as(C.POINTER(C.c_int32)),
+                          arrs[3].ctypes.data_as(C.POINTER(C.c_int32)),
+                          arrs[4].ctypes.data_as(C.POINTER(C.c_double)))
+    return arrs, prob
+
+
+def tune(inst, z0=None, iters=3, device=0, form=1, **options):
+    """mcsdp_tune on an instance (n, m, b, mat, row, col, val): the (group_max, panel_max) the
+    library's tile-shape tuner picks, cached by the library per (n, m, largest clique) rounded up
+    to powers of two.  Returns (options dict with the choice, info dict).  Marshalling only."""
+    L = _lib.load()
+    arrs, prob = _problem_t(inst.n, inst.m, inst.b, inst.mat, inst.row, inst.col, inst.val, form)
+    opt = _lib.Options_t()
+    L.mcsdp_default_options(C.byref(opt))
+    for k, v in options.items():
+        setattr(opt, k, v)
+    opt.device = int(device)
+    nb = C.c_size_t()
+    st = L.mcsdp_tune_workspace_size(C.byref(prob), C.byref(opt), C.byref(nb))
+    if st != 0:
+        raise MCSDPError(st, "tune: no candidate fits the problem")
+    dev = torch.device("cuda", int(device))
+    ws = torch.empty(max(int(nb.value), 256), dtype=torch.uint8, device=dev)
+    z = None if z0 is None else torch.as_tensor(z0, dtype=torch.float64, device=dev)
+    info = _lib.TuneInfo_t()
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    st = L.mcsdp_tune(C.byref(prob), C.byref(opt), _ptr(z), C.c_void_p(stream), _ptr(ws),
+                      ws.numel(), int(iters), C.byref(info))
+    if st != 0:
+        raise MCSDPError(st, "tune failed")
+    out = dict(options)
+    out["group_max"], out["panel_max"] = int(opt.group_max), int(opt.panel_max)
+    return out, {"group_max": info.group_max, "panel_max": info.panel_max,
+                 "cached": bool(info.cached), "ncand": info.ncand,
+                 "ms_per_iter": list(info.ms_per_iter)[:5], "key": list(info.key)}
+
+
+def tune_cache_clear():
+    _lib.load().mcsdp_tune_cache_clear()
+
+
 def solve_batch(problems, nthreads=0):
     """Solves the problems concurrently (mcsdp_solve_batch): host threads each take the next
     unsolved problem; create each Problem with its own stream (stream=torch.cuda.Stream()) for

@@ -258,6 +258,10 @@ void launch_dual_cands(const double *g, int round, double *cand, int ncand, cons
 void launch_dual_update(const int *cst, const double *cand, int ncand, double *g, cudaStream_t st);
 void launch_graph_steps(const double *scal, const int *status, double gamma, double *g,
                         cudaStream_t st);
+// the solve graph's loop test (kern_sparse.cu k_graph_cond)
+void launch_graph_cond(cudaGraphConditionalHandle h, const double *scal, const int *status,
+                       const double *g, int *cnt, int n, double gap_tol, double feas_tol,
+                       cudaStream_t st);
 // constraints with disjoint supports: dX += sum_k c_k A_k with c_k chosen so that
 // A_k . (X̄ + dX) = b_k exactly (the projection onto the primal affine set, A A^* diagonal)
 void launch_project_primal(const DevSym &S, const double *Xbar, double *dX, cudaStream_t st);

@@ -862,6 +862,32 @@ void launch_graph_steps(const double *scal, const int *status, double gamma, dou
   k_graph_steps<<<1, 32, 0, st>>>(scal, status, gamma, g);
 }
 
+// The loop test of the solve graph (options.graph = 2), after each iteration it ran: the host
+// loop's own tests at the top of its next iteration, on the new iterate's scalars (the same
+// FP64 operations in the same order, so the same decisions) — a failed step (g[8]), a failed
+// factorisation of Y or of a clique block of X̄ (status words 0 and 1), a non-finite scalar,
+// convergence (relative gap and primal residual), or the iteration limit (cnt[1] iterations in
+// this launch) — ends the loop.  cnt[0] counts the iterations run.
+__global__ void k_graph_cond(cudaGraphConditionalHandle h, const double *__restrict__ scal,
+                             const int *__restrict__ status, const double *__restrict__ g,
+                             int *cnt, int n, double gap_tol, double feas_tol) {
+  if (threadIdx.x != 0) return;
+  const int k = ++cnt[0];
+  const double mu = scal[0] / n, pobj = scal[1], dobj = scal[2];
+  const double gap = fabs(pobj - dobj) / fmax(1.0, (fabs(pobj) + fabs(dobj)) / 2);
+  const double pinf = scal[3] / fmax(1.0, scal[4]);
+  const int bad = (status[0] | status[1]) & (ST_NOT_PD | ST_TIMEOUT | ST_NUMERIC);
+  const bool stop = g[8] != 0.0 || bad != 0 || !isfinite(pobj) || !isfinite(dobj) ||
+                    !isfinite(mu) || (gap <= gap_tol && pinf <= feas_tol) || k >= cnt[1];
+  cudaGraphSetConditional(h, stop ? 0u : 1u);
+}
+
+void launch_graph_cond(cudaGraphConditionalHandle h, const double *scal, const int *status,
+                       const double *g, int *cnt, int n, double gap_tol, double feas_tol,
+                       cudaStream_t st) {
+  k_graph_cond<<<1, 32, 0, st>>>(h, scal, status, g, cnt, n, gap_tol, feas_tol);
+}
+
 // one thread per constraint k: r = b_k - A_k . X̄ - A_k . dX, c = r / (A_k . A_k), dX += c A_k on
 // A_k's positions (no other constraint touches them)
 __global__ void k_project_primal(DevSym S, const double *__restrict__ X, double *dX) {

@@ -3398,4 +3398,123 @@ mcsdp_status mcsdp_backward(mcsdp_ctx *c, const double *gX, const double *gz, do
   return MCSDP_OK;
 }
 
+// ---- tile-shape tuner (batched form) ----
+static const int TUNE_CAND[5][2] = {{64, 80}, {32, 80}, {16, 80}, {64, 96}, {32, 48}};
+static std::mutex g_tune_mu;
+static std::map<std::array<int64_t, 3>, std::array<int, 2>> g_tune_cache;
+
+static int64_t tune_pow2(int64_t v) {
+  int64_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+mcsdp_status mcsdp_tune_workspace_size(const mcsdp_problem *prob, const mcsdp_options *opt,
+                                       size_t *bytes) {
+  if (!prob || !bytes) return MCSDP_ERR_ARG;
+  mcsdp_options o;
+  if (opt) o = *opt;
+  else mcsdp_default_options(&o);
+  o.device = -1;
+  size_t need = 0;
+  bool any = false;
+  for (const auto &cand : TUNE_CAND) {
+    o.group_max = cand[0];
+    o.panel_max = cand[1];
+    mcsdp_ctx *c = nullptr;
+    if (mcsdp_create(prob, &o, nullptr, &c) == MCSDP_OK) {
+      need = std::max(need, c->ws_bytes);
+      any = true;
+    }
+    mcsdp_destroy(c);
+  }
+  if (!any) return MCSDP_ERR_ARG;
+  *bytes = need;
+  return MCSDP_OK;
+}
+
+mcsdp_status mcsdp_tune(const mcsdp_problem *prob, mcsdp_options *opt, const double *z0_dev,
+                        void *cuda_stream, void *ws, size_t ws_bytes, int32_t iters,
+                        mcsdp_tune_info *info) {
+  if (!prob || !opt || !ws || iters <= 0 || opt->device < 0) return MCSDP_ERR_ARG;
+  mcsdp_tune_info inf{};
+  for (double &v : inf.ms_per_iter) v = -1.0;
+  {  // the key: the clique structure does not depend on the SCM grouping
+    mcsdp_options o = *opt;
+    o.device = -1;
+    o.group_max = 64;
+    o.panel_max = 96;
+    mcsdp_ctx *c = nullptr;
+    const mcsdp_status s = mcsdp_create(prob, &o, nullptr, &c);
+    if (s == MCSDP_OK) {
+      inf.key[0] = tune_pow2(prob->n);
+      inf.key[1] = tune_pow2(prob->m);
+      inf.key[2] = tune_pow2(c->S.max_nrow);
+    }
+    mcsdp_destroy(c);
+    if (s != MCSDP_OK) return s;
+  }
+  const std::array<int64_t, 3> key{inf.key[0], inf.key[1], inf.key[2]};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      opt->group_max = inf.group_max = it->second[0];
+      opt->panel_max = inf.panel_max = it->second[1];
+      inf.cached = 1;
+      if (info) *info = inf;
+      return MCSDP_OK;
+    }
+  }
+  int best = -1;
+  mcsdp_status last = MCSDP_ERR_ARG;
+  for (int q = 0; q < 5; ++q) {
+    mcsdp_options o = *opt;
+    o.group_max = TUNE_CAND[q][0];
+    o.panel_max = TUNE_CAND[q][1];
+    o.max_iter = iters;
+    o.profile = 0;
+    o.verbose = 0;
+    mcsdp_ctx *c = nullptr;
+    double ms = -1.0;
+    mcsdp_status s = mcsdp_create(prob, &o, cuda_stream, &c);
+    if (s == MCSDP_OK && c->ws_bytes > ws_bytes) s = MCSDP_ERR_OOM;
+    if (s == MCSDP_OK) s = mcsdp_set_workspace(c, ws, ws_bytes);
+    // one untimed run (first-use work: shared-memory attributes, graph capture), one timed
+    for (int rep = 0; rep < 2 && s == MCSDP_OK; ++rep) {
+      s = set_default_start(c);
+      if (s == MCSDP_OK && z0_dev)
+        s = cudaMemcpyAsync(c->z, z0_dev, (size_t)c->S.m * 8, cudaMemcpyDeviceToDevice,
+                            c->stream) == cudaSuccess ? MCSDP_OK : MCSDP_ERR_CUDA;
+      if (s != MCSDP_OK) break;
+      c->iterate_set = true;
+      mcsdp_result r{};
+      s = mcsdp_solve(c, &r);
+      if (s == MCSDP_ERR_MAXITER) s = MCSDP_OK;
+      if (s == MCSDP_OK && rep == 1) ms = r.seconds * 1e3 / std::max(1, (int)r.iters);
+    }
+    if (s != MCSDP_OK) last = s;
+    mcsdp_destroy(c);
+    inf.ms_per_iter[q] = ms;
+    if (ms > 0) {
+      ++inf.ncand;
+      if (best < 0 || ms < inf.ms_per_iter[best]) best = q;
+    }
+  }
+  if (best < 0) return last;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = {TUNE_CAND[best][0], TUNE_CAND[best][1]};
+  }
+  opt->group_max = inf.group_max = TUNE_CAND[best][0];
+  opt->panel_max = inf.panel_max = TUNE_CAND[best][1];
+  if (info) *info = inf;
+  return MCSDP_OK;
+}
+
+void mcsdp_tune_cache_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache.clear();
+}
+
 }  // extern "C"
