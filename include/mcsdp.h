@@ -131,8 +131,13 @@ typedef struct {
                             the new iterate) is captured once into a CUDA graph and replayed: one
                             graph launch and one host synchronisation per iteration instead of
                             about a hundred launches and eight synchronisations; same iterates as
-                            0.  FP64 form without a dense root only (else ignored); per-class
-                            times (profile) are then not measured.  0 (default) = off */
+                            0.  2 = that iteration as the body of a WHILE conditional node whose
+                            loop test runs on the device (the host loop's tests of failure,
+                            convergence and the iteration limit on the new iterate): the rest of
+                            the solve is one graph launch and one synchronisation (falls back to
+                            1 where the graph cannot be built); same iterates as 0.  FP64 form
+                            without a dense root only (else ignored); per-class times (profile)
+                            are then not measured.  0 (default) = off */
   int32_t scm_blocks;    /* block-diagonal SCM (the sparse-SCM case of Sec. 3.1: B_pq = 0 when
                             A_p and A_q lie in different connected components of the aggregate
                             pattern, X̂ and Y^{-1} being block-diagonal over them; components are

@@ -127,6 +127,13 @@ struct mcsdp_ctx {
   bool graph_failed = false;  // capture not possible: iterate without the graph
   int64_t graph_launches = 0;
   int64_t graph_kcount[16] = {};
+  // the solve graph (options.graph = 2): a WHILE node around the iteration and its loop test;
+  // gcnt[0] iterations run, gcnt[1] the launch's iteration limit
+  cudaGraphExec_t solve_exec = nullptr;
+  bool solve_graph_failed = false;
+  int *gcnt = nullptr;
+  int64_t sgraph_launches = 0;
+  int64_t sgraph_kcount[16] = {};
   cudaStream_t st2 = nullptr;                  // low priority: trailing updates, primal step
   cudaStream_t st1 = nullptr;                  // high priority: the Cholesky's critical path
   cudaStream_t stc = nullptr;                  // the graph iteration's capture (owned: a caller's
@@ -866,6 +873,7 @@ void plan_workspace(mcsdp_ctx *c) {
   }
   plan_buf(c, cur, "alpha_c", NCAND * 8);
   plan_buf(c, cur, "gsc", 16 * 8);
+  plan_buf(c, cur, "gcnt", 16);
   plan_buf(c, cur, "alpha_r", (size_t)S.ns * 8);
   plan_buf(c, cur, "scal", (16 + 6 * 64) * 8);  // scalars, then the measures' partials
   plan_buf(c, cur, "chol_sync", std::max(chol_dag_words(m, m + 1), c->bt.words) * 4);
@@ -1029,6 +1037,7 @@ void bind_pointers(mcsdp_ctx *c) {
   c->Ncand = wsp<double>(c, "Ncand");
   c->alpha_c = wsp<double>(c, "alpha_c");
   c->gsc = wsp<double>(c, "gsc");
+  c->gcnt = wsp<int>(c, "gcnt");
   c->alpha_r = wsp<double>(c, "alpha_r");
   c->scal = wsp<double>(c, "scal");
   c->status = wsp<int>(c, "status");
@@ -2423,6 +2432,83 @@ bool graph_iteration(mcsdp_ctx *c, mcsdp_status *s) {
   return true;
 }
 
+// Runs iterations through the solve graph (built on first use): a WHILE conditional node whose
+// body is the iteration of graph_body followed by k_graph_cond, which applies the host loop's
+// tests to the new iterate and ends the loop, so that one graph launch and one synchronisation
+// run the solve to its end (at most it_left iterations).  *ran: the iterations run.  False when
+// the graph cannot be built (the caller then uses the per-iteration graph).
+bool solve_graph(mcsdp_ctx *c, int it_left, int *ran, mcsdp_status *s) {
+  *s = MCSDP_OK;
+  *ran = 0;
+  if (!c->solve_exec) {
+    const int64_t l0 = c->launches;
+    int64_t k0[16];
+    for (int q = 0; q < 16; ++q) k0[q] = c->kcount[q];
+    cudaGraph_t outer = nullptr;
+    cudaGraphConditionalHandle h{};
+    cudaGraphNodeParams np{};
+    cudaGraphNode_t node = nullptr;
+    bool ok = cudaGraphCreate(&outer, 0) == cudaSuccess &&
+              cudaGraphConditionalHandleCreate(&h, outer, 1, cudaGraphCondAssignDefault) ==
+                  cudaSuccess;
+    if (ok) {
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = h;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      ok = cudaGraphAddNode(&node, outer, nullptr, nullptr, 0, &np) == cudaSuccess;
+    }
+    if (ok) {
+      const int prof = c->opt.profile;
+      c->opt.profile = 0;
+      cudaStream_t user = c->stream;
+      c->stream = c->stc;
+      ok = cudaStreamBeginCaptureToGraph(c->stc, np.conditional.phGraph_out[0], nullptr, nullptr,
+                                         0, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        const mcsdp_status bs = graph_body(c);
+        launch_graph_cond(h, c->scal, c->status, c->gsc, c->gcnt, c->S.n, c->opt.gap_tol,
+                          c->opt.feas_tol, c->stc);
+        ++c->launches;
+        cudaGraph_t body = nullptr;
+        ok = cudaStreamEndCapture(c->stc, &body) == cudaSuccess && bs == MCSDP_OK;
+      }
+      c->stream = user;
+      c->opt.profile = prof;
+    }
+    c->sgraph_launches = c->launches - l0;
+    for (int q = 0; q < 16; ++q) {
+      c->sgraph_kcount[q] = c->kcount[q] - k0[q];
+      c->kcount[q] = k0[q];
+    }
+    c->launches = l0;
+    if (ok)
+      ok = cudaGraphInstantiate(&c->solve_exec, outer, cudaGraphInstantiateFlagUseNodePriority) ==
+           cudaSuccess;
+    if (outer) cudaGraphDestroy(outer);
+    if (!ok) {
+      (void)cudaGetLastError();
+      c->solve_exec = nullptr;
+      c->err.clear();
+      return false;
+    }
+  }
+  const int lim[2] = {0, it_left};
+  int cnt[2] = {0, 0};
+  if (cudaMemcpyAsync(c->gcnt, lim, sizeof(lim), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+      cudaGraphLaunch(c->solve_exec, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(cnt, c->gcnt, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    *s = fail(c, MCSDP_ERR_CUDA, "solve graph launch failed");
+    return true;
+  }
+  *ran = cnt[0];
+  c->launches += c->sgraph_launches * cnt[0];
+  for (int q = 0; q < 16; ++q) c->kcount[q] += c->sgraph_kcount[q] * cnt[0];
+  if (cnt[0] < 1) *s = fail(c, MCSDP_ERR_CUDA, "solve graph ran no iteration");
+  return true;
+}
+
 // Y, N, L̂ and the scalars at the current iterate (c->Xbar, c->z)
 mcsdp_status prepare_read(mcsdp_ctx *c, double *scal_host, int *failed);
 
@@ -2650,6 +2736,7 @@ void mcsdp_destroy(mcsdp_ctx *c) {
   if (!c->host_only && c->device >= 0) {
     cudaSetDevice(c->device);
     if (c->iter_exec) cudaGraphExecDestroy(c->iter_exec);
+    if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
     for (int i = 0; i < 8; ++i)
       if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     if (!c->pending.empty()) {
@@ -2897,7 +2984,7 @@ mcsdp_status mcsdp_solve(mcsdp_ctx *c, mcsdp_result *res) {
   const int n = c->S.n;
   mcsdp_status final_status = MCSDP_ERR_MAXITER;
   double last_ap = 0.0, last_ad = 0.0;
-  const bool use_graph = c->opt.graph == 1 && !c->dense && c->opt.precision == 0;
+  const bool use_graph = c->opt.graph >= 1 && !c->dense && c->opt.precision == 0;
   bool graph_prepared = false;
   for (int it = 0; it <= c->opt.max_iter; ++it) {
     double sc[8];
@@ -2982,6 +3069,19 @@ mcsdp_status mcsdp_solve(mcsdp_ctx *c, mcsdp_result *res) {
       break;
     }
     if (it == c->opt.max_iter) break;
+    if (use_graph && it >= 1 && c->opt.graph == 2 && !c->solve_graph_failed) {
+      int ran = 0;
+      if (solve_graph(c, c->opt.max_iter - it, &ran, &s)) {
+        if (s) {
+          final_status = s;
+          break;
+        }
+        it += ran - 1;  // the loop's top reads the state the graph left, as after one iteration
+        graph_prepared = true;
+        continue;
+      }
+      c->solve_graph_failed = true;  // not buildable here: the per-iteration graph
+    }
     if (use_graph && it >= 1 && !c->graph_failed) {
       if (graph_iteration(c, &s)) {
         if (s) {
