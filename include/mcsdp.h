@@ -319,6 +319,14 @@ mcsdp_status mcsdp_pivot_reciprocal(const double *d_dev, double *r_dev, int64_t 
  * MCSDP_ERR_ARG for m <= 0, rows < m or ntask NULL. */
 mcsdp_status mcsdp_chol_task_order(int32_t m, int32_t rows, int64_t *ntask, int32_t *tasks);
 
+/* The same for the block-diagonal SCM's one-launch factorisation of nblk bordered blocks of mb[b]
+ * columns (each with its right-hand-side row): the blocks' tickets interleaved phase by phase
+ * (every block's prefix, then every block's iteration 0, ...).  tasks[5 t ..] = (block, type, i,
+ * j, k) of ticket t, decoded by the kernel's own lookup; each block's tasks keep the order
+ * mcsdp_chol_task_order gives for (mb[b], mb[b] + 1).  tasks NULL: only *ntask.  Host only. */
+mcsdp_status mcsdp_chol_block_task_order(int32_t nblk, const int32_t *mb, int64_t *ntask,
+                                         int32_t *tasks);
+
 /* The shared-memory layouts (byte offsets) of the staged supernodal level solves that evaluate
  * the columns X̂ e_k and Y^{-1} e_k of Sec. 3.1, exposed so the host tests can check them for every
  * admissible clique size: nc / nr = the level's largest |S_r| / |C_r|, cw / np = the update

@@ -70,7 +70,7 @@ EXPORTED = ["mcsdp_default_options", "mcsdp_create", "mcsdp_destroy", "mcsdp_las
             "mcsdp_stats_get", "mcsdp_stats_reset", "mcsdp_work_model", "mcsdp_sce_solve_noalloc",
             "mcsdp_solve_batch", "mcsdp_pivot_reciprocal", "mcsdp_chol_task_order",
             "mcsdp_gemm_tc_work_size", "mcsdp_gemm_tc", "mcsdp_tune_workspace_size",
-            "mcsdp_tune", "mcsdp_tune_cache_clear"]
+            "mcsdp_tune", "mcsdp_tune_cache_clear", "mcsdp_chol_block_task_order"]
 
 _lib = None
 
@@ -111,6 +111,7 @@ def load():
     L.mcsdp_sce_solve_noalloc.argtypes = [V, C.c_int64, V, V, C.c_int32, V]
     L.mcsdp_pivot_reciprocal.argtypes = [V, V, C.c_int64, V]
     L.mcsdp_chol_task_order.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_int64), V]
+    L.mcsdp_chol_block_task_order.argtypes = [C.c_int32, V, C.POINTER(C.c_int64), V]
     L.mcsdp_solve_batch.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.c_int32,
                                     C.POINTER(Result_t)]
     L.mcsdp_gemm_tc_work_size.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]

@@ -409,9 +409,15 @@ struct DagBlockTables {
   size_t words = 0;         // the synchronisation buffer (chol_dag_blocks_words)
   int64_t useful_ctas = 0;  // sum of C_b^2 / 4: tasks the blocks can have ready at once
 };
-// tickets of each phase of one factorisation: the prefix, then iterations 0 .. C-2
-void chol_dag_phases(int m, int rows, std::vector<int64_t> &sizes);
-size_t chol_dag_tile_words(int m, int rows);
+// the block queue's host tables for blocks of mb[b] columns (each bordered by one row): tile
+// counter offsets, the interleaved segments (see DagBlocks in kern_dense.cu), ticket total
+struct DagBlockPlan {
+  std::vector<int64_t> soff, seg_start, seg_l0;
+  std::vector<int> seg_blk, seg_k;
+  int64_t total = 0, useful_ctas = 0;
+  size_t tile_words = 0, words = 0;
+};
+void chol_dag_block_plan(const std::vector<int> &mb, DagBlockPlan &pl);
 size_t chol_dag_blocks_words(size_t tile_words);
 // every block's bordered factorisation in one launch (FP64)
 int dense_chol_dag_blocks(double *B, int64_t ldb, const DagBlockTables &bt, int *status,

@@ -684,6 +684,18 @@ struct DagBlocks {
   const int *seg_blk = nullptr, *seg_k = nullptr;          // nseg
 };
 
+// the segment of block-queue ticket t: the last one starting at or before it
+__device__ __host__ __forceinline__ int dag_block_segment(int64_t t, const int64_t *seg_start,
+                                                          int nseg) {
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (seg_start[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 template <class T>
 __global__ void __launch_bounds__(DAG_THREADS, 2)
     k_chol_dag(T *B0, int64_t ldb, int m, int rows, int *status, T *Linv0, DagSync q,
@@ -706,12 +718,7 @@ __global__ void __launch_bounds__(DAG_THREADS, 2)
     if (tid == 0) s_task[1] = atomicAdd(q.ticket, 1);  // the next ticket, fetched early
     int64_t tl = t;
     if (bl.nblk > 0) {  // block mode: the segment holding t, its block and local ticket
-      int lo = 0, hi = bl.nseg - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (bl.seg_start[mid] <= t) lo = mid;
-        else hi = mid - 1;
-      }
+      const int lo = dag_block_segment(t, bl.seg_start, bl.nseg);
       if (bl.seg_blk[lo] != blk) {
         blk = bl.seg_blk[lo];
         const int o = bl.off[blk];
@@ -845,14 +852,33 @@ static int dense_chol_dag(T *B, int64_t ldb, int m, int rows, int *status, T *Li
   return 1;  // kernel launches (the memset is not one of ours)
 }
 
-void chol_dag_phases(int m, int rows, std::vector<int64_t> &sizes) {
-  const int R = (rows + NB - 1) / NB, C = (m + NB - 1) / NB;
-  sizes.assign(1, dag_prefix(R, C).pre);
-  for (int64_t k = 0; k + 1 < C; ++k) sizes.push_back(dag_iter_size(k, R, C));
-}
-
-size_t chol_dag_tile_words(int m, int rows) {
-  return 2 * (size_t)((rows + NB - 1) / NB) * (size_t)((m + NB - 1) / NB);
+void chol_dag_block_plan(const std::vector<int> &mb, DagBlockPlan &pl) {
+  const int nblk = (int)mb.size();
+  pl = DagBlockPlan{};
+  std::vector<std::vector<int64_t>> ph(nblk);  // per block: prefix, iteration 0, 1, ...
+  size_t nph = 0;
+  for (int b = 0; b < nblk; ++b) {
+    const int R = (mb[b] + 1 + NB - 1) / NB, C = (mb[b] + NB - 1) / NB;
+    pl.soff.push_back((int64_t)pl.tile_words);
+    pl.tile_words += 2 * (size_t)R * C;
+    pl.useful_ctas += (int64_t)C * C / 4;
+    ph[b].assign(1, dag_prefix(R, C).pre);
+    for (int64_t k = 0; k + 1 < C; ++k) ph[b].push_back(dag_iter_size(k, R, C));
+    nph = std::max(nph, ph[b].size());
+  }
+  std::vector<int64_t> local(nblk, 0);
+  for (size_t p = 0; p < nph; ++p)
+    for (int b = 0; b < nblk; ++b) {
+      if (p >= ph[b].size() || ph[b][p] == 0) continue;
+      pl.seg_start.push_back(pl.total);
+      pl.seg_l0.push_back(local[b]);
+      pl.seg_blk.push_back(b);
+      pl.seg_k.push_back((int)p - 1);
+      pl.total += ph[b][p];
+      local[b] += ph[b][p];
+    }
+  pl.seg_start.push_back(pl.total);
+  pl.words = chol_dag_blocks_words(pl.tile_words);
 }
 
 size_t chol_dag_blocks_words(size_t tile_words) { return 8 + tile_words + DAG_MAX_SM; }
@@ -2007,6 +2033,43 @@ extern "C" mcsdp_status mcsdp_pivot_reciprocal(const double *d, double *r, int64
   const int blocks = want > 4096 ? 4096 : (int)want;
   mcsdp::k_pivot_rcp<<<blocks, 256, 0, (cudaStream_t)stream>>>(d, r, n);
   return cudaGetLastError() == cudaSuccess ? MCSDP_OK : MCSDP_ERR_CUDA;
+}
+
+extern "C" mcsdp_status mcsdp_chol_block_task_order(int32_t nblk, const int32_t *mb,
+                                                    int64_t *ntask, int32_t *tasks) {
+  if (nblk <= 0 || !mb || !ntask) return MCSDP_ERR_ARG;
+  for (int b = 0; b < nblk; ++b)
+    if (mb[b] <= 0) return MCSDP_ERR_ARG;
+  mcsdp::DagBlockPlan pl;
+  mcsdp::chol_dag_block_plan(std::vector<int>(mb, mb + nblk), pl);
+  *ntask = pl.total;
+  if (!tasks) return MCSDP_OK;
+  // the kernel's decode: segment lookup, then the block's own decode started at the segment
+  int blk = -1, R = 0, C = 0, kcur = 0;
+  int64_t kstart = 0;
+  mcsdp::DagPrefix pf{};
+  const int nseg = (int)pl.seg_blk.size();
+  for (int64_t t = 0; t < pl.total; ++t) {
+    const int sg = mcsdp::dag_block_segment(t, pl.seg_start.data(), nseg);
+    if (pl.seg_blk[sg] != blk) {
+      blk = pl.seg_blk[sg];
+      R = (mb[blk] + 1 + mcsdp::NB - 1) / mcsdp::NB;
+      C = (mb[blk] + mcsdp::NB - 1) / mcsdp::NB;
+      pf = mcsdp::dag_prefix(R, C);
+    }
+    const int64_t tl = pl.seg_l0[sg] + (t - pl.seg_start[sg]);
+    if (pl.seg_k[sg] >= 0) {
+      kcur = pl.seg_k[sg];
+      kstart = pl.seg_l0[sg];
+    }
+    const mcsdp::DagTask d = mcsdp::dag_decode(tl, R, C, pf, kcur, kstart);
+    tasks[5 * t] = blk;
+    tasks[5 * t + 1] = d.type;
+    tasks[5 * t + 2] = d.i;
+    tasks[5 * t + 3] = d.j;
+    tasks[5 * t + 4] = d.k;
+  }
+  return MCSDP_OK;
 }
 
 extern "C" mcsdp_status mcsdp_chol_task_order(int32_t m, int32_t rows, int64_t *ntask,

@@ -779,41 +779,24 @@ void plan_workspace(mcsdp_ctx *c) {
   c->bt_seg_start.clear();
   c->bt_seg_l0.clear();
   if (c->blocks) {
-    // the blocks' ticket phases (prefix, iteration 0, 1, ...), interleaved phase by phase
-    int64_t useful = 0;
-    size_t tw = 0;
-    std::vector<std::vector<int64_t>> ph(S.ncomp);
-    size_t nph = 0;
     for (int q = 0; q < S.ncomp; ++q) {
-      const int o = S.comp_cptr[q], mc = S.comp_cptr[q + 1] - o, ct = (mc + 31) / 32;
-      c->bt_off.push_back(o);
-      c->bt_m.push_back(mc);
-      c->bt_soff.push_back((int64_t)tw);
-      tw += chol_dag_tile_words(mc, mc + 1);
-      useful += (int64_t)ct * ct / 4;
-      c->bt.max_m = std::max(c->bt.max_m, mc);
-      chol_dag_phases(mc, mc + 1, ph[q]);
-      nph = std::max(nph, ph[q].size());
+      c->bt_off.push_back(S.comp_cptr[q]);
+      c->bt_m.push_back(S.comp_cptr[q + 1] - S.comp_cptr[q]);
+      c->bt.max_m = std::max(c->bt.max_m, c->bt_m.back());
     }
-    std::vector<int64_t> lstart(S.ncomp, 0);
-    int64_t tk = 0;
-    for (size_t p = 0; p < nph; ++p)
-      for (int q = 0; q < S.ncomp; ++q) {
-        if (p >= ph[q].size() || ph[q][p] == 0) continue;
-        c->bt_seg_start.push_back(tk);
-        c->bt_seg_l0.push_back(lstart[q]);
-        c->bt_seg_blk.push_back(q);
-        c->bt_seg_k.push_back((int)p - 1);
-        tk += ph[q][p];
-        lstart[q] += ph[q][p];
-      }
-    c->bt_seg_start.push_back(tk);
+    DagBlockPlan pl;
+    chol_dag_block_plan(c->bt_m, pl);
+    c->bt_soff = pl.soff;
+    c->bt_seg_start = pl.seg_start;
+    c->bt_seg_l0 = pl.seg_l0;
+    c->bt_seg_blk = pl.seg_blk;
+    c->bt_seg_k = pl.seg_k;
     c->bt.nblk = S.ncomp;
-    c->bt.nseg = (int)c->bt_seg_blk.size();
-    c->bt.total = tk;
-    c->bt.tile_words = tw;
-    c->bt.words = chol_dag_blocks_words(tw);
-    c->bt.useful_ctas = useful;
+    c->bt.nseg = (int)pl.seg_blk.size();
+    c->bt.total = pl.total;
+    c->bt.tile_words = pl.tile_words;
+    c->bt.words = pl.words;
+    c->bt.useful_ctas = pl.useful_ctas;
   }
   plan_table(c, cur, "bt_off", c->bt_off);
   plan_table(c, cur, "bt_m", c->bt_m);

@@ -132,3 +132,42 @@ def test_bad_arguments(lib):
     assert lib.mcsdp_chol_task_order(0, 1, C.byref(n), None) != 0
     assert lib.mcsdp_chol_task_order(5, 4, C.byref(n), None) != 0
     assert lib.mcsdp_chol_task_order(5, 6, None, None) != 0
+
+
+def _block_order(lib, mb):
+    arr = np.array(mb, np.int32)
+    n = C.c_int64(-1)
+    assert lib.mcsdp_chol_block_task_order(len(mb), C.c_void_p(arr.ctypes.data), C.byref(n),
+                                           None) == 0
+    t = np.full((n.value, 5), -7, np.int32)
+    assert lib.mcsdp_chol_block_task_order(len(mb), C.c_void_p(arr.ctypes.data), C.byref(n),
+                                           C.c_void_p(t.ctypes.data)) == 0
+    return t
+
+
+@pytest.mark.parametrize("mb", [[1], [1, 1, 1], [31, 32, 33], [64, 1, 100, 7, 400, 33],
+                                [5] * 40 + [200], list(range(1, 70, 3))],
+                         ids=["one", "ones", "tile_edges", "mixed", "many_small", "ramp"])
+def test_block_queue_keeps_each_blocks_order(lib, mb):
+    """The block-diagonal SCM's one-launch factorisation interleaves the blocks' tickets phase by
+    phase.  Blocks share no data, so the queue is deadlock-free if each block's tasks appear in
+    its own single-matrix order (checked above for every size): then the smallest unfinished
+    ticket's inputs are earlier tasks of its block, all finished."""
+    t = _block_order(lib, mb)
+    assert (t[:, 0] >= 0).all() and (t[:, 0] < len(mb)).all()
+    for b, m in enumerate(mb):
+        own = [tuple(int(v) for v in r) for r in t[t[:, 0] == b, 1:]]
+        assert own == _order(lib, m, m + 1), b
+    # interleaved, not concatenated: every block starts before any block of three or more tile
+    # columns (whose tickets span more than the first phase) has finished
+    first = [int(np.flatnonzero(t[:, 0] == b)[0]) for b in range(len(mb))]
+    last = [int(np.flatnonzero(t[:, 0] == b)[-1]) for b in range(len(mb))]
+    for b, m in enumerate(mb):
+        if m > 64:
+            assert max(first) < last[b]
+
+
+def test_block_queue_rejects_bad_sizes(lib):
+    arr = np.array([3, 0], np.int32)
+    n = C.c_int64(-1)
+    assert lib.mcsdp_chol_block_task_order(2, C.c_void_p(arr.ctypes.data), C.byref(n), None) == 1
