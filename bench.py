@@ -520,7 +520,10 @@ def other_legs(args, dev, stream):
         batched[name] = leg
         del probs
         torch.cuda.empty_cache()
-    out["scm_blocks"] = blocks_leg(dev, stream)
+    try:
+        out["scm_blocks"] = blocks_leg(dev, stream)
+    except Exception as e:  # a failed side leg is reported, not allowed to drop the line
+        out["scm_blocks"] = {"error": f"{type(e).__name__}: {e}"}
     return out, batched
 
 

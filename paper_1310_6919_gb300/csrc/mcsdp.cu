@@ -2108,10 +2108,22 @@ mcsdp_status direction(mcsdp_ctx *c, const double *Xbar, double mu, IterOut &o, 
     launch_rhs_border(c->D, c->B, c->ldb, c->hvec, beta * mu, c->stream);
     k0.done(1);
     bool solved = false;
-    // (a block-diagonal B keeps the FP64 factor: its blocks are small)
-    if (c->opt.precision == 1 && !c->promoted && !c->blocks) {
-      s = mixed_sce(c, f32, &solved);
-      if (s) return s;
+    if (c->opt.precision == 1 && !c->promoted) {
+      if (c->blocks) {
+        // a block-diagonal B keeps the FP64 factor (its blocks are small); an FP32-assembled B
+        // that it finds not positive definite promotes the solve, as a broken-down FP32 factor
+        // does
+        scm_chol_solve(c);
+        int st2 = 0;
+        CUDA_TRY(c, cudaMemcpyAsync(&st2, c->status + 2, sizeof(int), cudaMemcpyDeviceToHost,
+                                    c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        solved = !(f32 && (st2 & ST_NOT_PD));
+        if (!solved) CUDA_TRY(c, cudaMemsetAsync(c->status + 2, 0, sizeof(int), c->stream));
+      } else {
+        s = mixed_sce(c, f32, &solved);
+        if (s) return s;
+      }
       if (!solved) {
         // promotion: from here on everything in FP64, starting with this iteration's SCM (an
         // FP32-assembled B can be singular where the FP64 one is not)
