@@ -383,12 +383,15 @@ def run_gb300(args):
                  "speedup_vs_fp64": (fp64["value"] / value) if fp64 else None,
                  "pobj_diff_vs_fp64": abs(rm["pobj"] - fp64["pobj"]) if fp64 else None,
                  "phases_ms_per_solve": {k: v / args.steps for k, v in mms.items()},
-                 "desc": ("FP32 stage (relative gap above 1e-1): X̂ and Y^-1 formed in FP32, the "
+                 "desc": ("FP32 stage (relative gap above 1e-2): X̂ and Y^-1 formed in FP32, the "
+                          "root blocks of Y and X̄ factored (X̄_RR's factor inverted) in FP32, the "
                           "root's products and the SCM Cholesky's trailing updates on the tensor "
-                          "cores (three TF32 products), FP64 refinement of the SCE, the direction "
+                          "cores (three TF32 products), the SCE corrected in FP64 by GMRES "
+                          "preconditioned by the equilibrated FP32 factor, the direction "
                           "projected onto the primal affine set in FP64; then FP64 assembly with "
-                          "the FP32 tensor-core factor; FP64 throughout once refinement stalls; "
-                          "Y's and X̄'s factors, step-length bounds and update FP64")}
+                          "the FP32 tensor-core factor and GMRES; FP64 factorisations of B once "
+                          "GMRES stalls or the FP32 factor breaks down; the forest's factors, "
+                          "step-length bounds and update FP64")}
         line = {"metric": METRIC, "value": value, "unit": "s/solve", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
