@@ -47,7 +47,7 @@ TF32_BF16_RATIO = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates (recipe t
 # a full launch by the work it does (nR^3 for the root GEMM, m^3 for the SCM Cholesky: both tile
 # their operands through L2 the same way at either size)
 TRAFFIC_PER_UNIT = {"root_gemm": (1.238365e9 + 77.669888e6) / 3158 ** 3,
-                    "scm_chol": (14.103590e9 + 19.115887e9) / 8000 ** 3}
+                    "scm_chol": (13.867930e9 + 18.936653e9) / 8000 ** 3}
 ORACLE_ITER_OVER_CHOL = 13.0 / (1.0 / 3.0)  # dense oracle iteration flops / SCM Cholesky flops
 KCLASS_DESC = {"ychol": "k_ychol + k_root_gather + k_chol_dag (Y = N N^T, root FP64 Cholesky)",
                "alg1": "k_alg1 + k_chol_dag + k_gemm_tn<double> (Algorithm 1; root Cholesky and "
