@@ -2,7 +2,7 @@
 
 These checks pin the input recipe, not the method: the sizes and patterns of the max-cut lattice
 of Sec. 4, the block-arrow SDPs with their strictly feasible start (X0 = I, Y0 = I), the ring
-max-cut graph and the batched mix.  Dense matrices are built here with plain numpy from the
+max-cut graph, the batched mix and the 64-part direct sum.  Dense matrices are built here with plain numpy from the
 instance arrays (paper notation: Y(z) = A_0 - sum_k z_k A_k, A_k . X = b_k).
 """
 import numpy as np
@@ -130,3 +130,41 @@ def test_batch_mix_recipe():
         assert len(sizes) == -(-(inst.n - 20) // 50) and max(sizes) - min(sizes) <= 1
         Y = dual_slack_dense(inst, inst.z0)
         assert np.max(np.abs(Y - np.eye(inst.n))) < 1e-12
+
+
+def test_direct_sum_recipe():
+    """maxcut_sum_64: 64 max-cut SDPs of the batch mix's max-cut kind, part p on rows offset by
+    the earlier parts' sizes, its constraints after theirs; no entry crosses two parts, b = 1 and
+    z0 is the parts' z0 (Y0 strictly diagonally dominant)."""
+    from instances.problems import Xoshiro256ss, SEED_BASE, random_gnm_maxcut
+    inst = workload("maxcut_sum_64")
+    parts = inst.meta["parts"]
+    assert len(parts) == 64 and inst.n == inst.m == sum(p[1] for p in parts)
+    rng = Xoshiro256ss(SEED_BASE + 7)
+    sizes = [50 + rng.below(351) for _ in range(64)]
+    assert [p[1] for p in parts] == sizes and all(50 <= s <= 400 for s in sizes)
+    offs = np.cumsum([0] + sizes)
+    part_of = np.searchsorted(offs, np.arange(inst.n), side="right") - 1
+    assert np.array_equal(part_of[inst.row], part_of[inst.col])  # block-diagonal data
+    k = inst.mat > 0
+    assert np.array_equal(inst.row[k], inst.mat[k] - 1) and np.array_equal(inst.col[k], inst.row[k])
+    assert np.all(inst.b == 1.0)
+    # part 5 as generated on its own, shifted into place
+    p = 5
+    one = random_gnm_maxcut(sizes[p], (5 * sizes[p]) // 2, SEED_BASE + 7 + 1000 + p)
+    sel = (inst.mat == 0) & (part_of[inst.row] == p)
+    got = sorted(zip(inst.row[sel] - offs[p], inst.col[sel] - offs[p], inst.val[sel]))
+    want = sorted(zip(*one.matrix_entries(0)))
+    assert got == want
+    assert np.array_equal(inst.z0[offs[p]:offs[p + 1]], one.z0)
+    # Y0 = A_0 - diag(z0) strictly diagonally dominant with positive diagonal
+    diag = np.zeros(inst.n)
+    off = np.zeros(inst.n)
+    a0 = inst.mat == 0
+    for r, c, v in zip(inst.row[a0], inst.col[a0], inst.val[a0]):
+        if r == c:
+            diag[r] += v
+        else:
+            off[r] += abs(v)
+            off[c] += abs(v)
+    assert np.all(diag - inst.z0 > off)
