@@ -229,7 +229,9 @@ mcsdp_status mcsdp_get_iterate(const mcsdp_ctx *ctx, double *Xbar_layout_dev, do
 /* SCM assembly at the iterate (X̄ on E, z) given in device memory (eq. newSCM2, Sec. 3.1):
  * K2 (Y = N N^T), K1 (Algorithm 1: L̂ from X̄), K3 (B_ij = A_i . (X̂ A_j Y^{-1})).
  * Writes the lower triangle (i >= j, caller's constraint order) of B into B_dev, column-major
- * with leading dimension ldb >= m; the strict upper triangle is not touched.
+ * with leading dimension ldb >= m; the strict upper triangle is not touched.  With a
+ * block-diagonal B (options.scm_blocks) the entries between components are written as zeros
+ * (they are neither assembled nor factored).
  * h_dev (may be NULL) receives h_i = A_i . Y^{-1}.  precision 0: the solves and the contraction
  * run in FP64.  precision 1 (the mixed form): they run in FP32 from FP32 copies of L̂ and N (the
  * factors themselves are computed in FP64), and the FP32 sums are stored as FP64 values. */
