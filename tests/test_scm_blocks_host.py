@@ -158,3 +158,73 @@ def test_oracle_scm_of_direct_sum_is_block_diagonal():
                 assert np.allclose(blk, Bparts[a], rtol=1e-13, atol=1e-13 * np.abs(blk).max())
             else:
                 assert not blk.any()
+
+
+def _components_reference(inst):
+    """Connected components of the SCM structure, by breadth-first search over a graph on the
+    vertices: an edge for every input entry (i, j) and between all vertices one constraint
+    touches; a constraint's component is that of its vertices."""
+    n = inst.n
+    adj = [set() for _ in range(n)]
+    supp = [set() for _ in range(inst.m)]
+    for k, i, j in zip(inst.mat, inst.row, inst.col):
+        adj[i].add(j)
+        adj[j].add(i)
+        if k > 0:
+            supp[k - 1].update((int(i), int(j)))
+    for s in supp:
+        s = sorted(s)
+        for a in s[1:]:
+            adj[s[0]].add(a)
+            adj[a].add(s[0])
+    comp = [-1] * n
+    nc = 0
+    for v in range(n):
+        if comp[v] >= 0:
+            continue
+        stack = [v]
+        comp[v] = nc
+        while stack:
+            u = stack.pop()
+            for w in adj[u]:
+                if comp[w] < 0:
+                    comp[w] = nc
+                    stack.append(w)
+        nc += 1
+    return [comp[min(s)] for s in supp]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_components_match_a_graph_search(seed):
+    # random direct sums of small SDPs, plus random diagonal-only constraints that may bridge
+    # parts (joining their components through the constraint's support alone)
+    rng = np.random.default_rng(seed)
+    ps = []
+    for q in range(int(rng.integers(2, 6))):
+        kind = int(rng.integers(0, 3))
+        if kind == 0:
+            ps.append(lattice_maxcut(int(rng.integers(2, 5)), int(rng.integers(2, 5)), seed=seed + q))
+        elif kind == 1:
+            ps.append(random_gnm_maxcut(int(rng.integers(8, 30)), int(rng.integers(4, 20)), seed + q))
+        else:
+            ps.append(small_random_sdp(int(rng.integers(3, 7)), int(rng.integers(2, 6)), seed + q))
+    d = direct_sum(ps)
+    extra = int(rng.integers(0, 3))
+    mat, row, col, val = list(d.mat), list(d.row), list(d.col), list(d.val)
+    for e in range(extra):
+        for v in rng.choice(d.n, size=2, replace=False):
+            mat.append(d.m + e + 1)
+            row.append(int(v))
+            col.append(int(v))
+            val.append(1.0)
+    inst = SDPInstance("bridged", d.n, d.m + extra, np.ones(d.m + extra),
+                       np.array(mat, np.int32), np.array(row, np.int32), np.array(col, np.int32),
+                       np.array(val), z0=None, meta={})
+    ref = _components_reference(inst)
+    P = _problem(inst)
+    assert P.info["ncomp"] == len(set(ref))
+    order = P.sym_export()["con_order"]
+    labels = [ref[k] for k in order]
+    # each component's constraints are contiguous in the internal order
+    runs = [labels[0]] + [b for a, b in zip(labels, labels[1:]) if a != b]
+    assert len(runs) == len(set(runs))
