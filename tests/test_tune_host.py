@@ -70,3 +70,16 @@ def test_tune_needs_a_device(lib):
     buf = C.create_string_buffer(256)
     assert lib.mcsdp_tune(C.byref(prob), C.byref(opt), None, None, buf, 256, 3,
                           C.byref(info)) == 1  # MCSDP_ERR_ARG
+
+
+def test_tune_workspace_when_no_candidate_fits(lib):
+    # one constraint touching 97 rows: wider than every candidate's panel (and the limit, 96)
+    n = 100
+    inst = type("I", (), {})()
+    inst.n, inst.m = n, 1
+    inst.b = np.array([1.0])
+    inst.mat = np.array([0] * n + [1] * 97, np.int32)
+    inst.row = np.array(list(range(n)) + list(range(97)), np.int32)
+    inst.col, inst.val = inst.row.copy(), np.ones(n + 97)
+    st, _ = _ws(lib, inst)
+    assert st == 1  # MCSDP_ERR_ARG
